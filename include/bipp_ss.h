@@ -1,0 +1,162 @@
+/*
+ * bipp_ss.h — C ABI of the B300-native Bluebild standard-synthesis library
+ * (libbipp_ss.so). BIPP, arXiv:2310.09200.
+ *
+ * The library computes, per time step t (Algorithm 1 "Standard Synthesis"):
+ *   1. the Gram matrix G_ij = sinc(2 ||p_i - p_j|| / wl), sinc(x) = sin(pi x)/(pi x)
+ *      (Sec. 2.2, Eq. gram; App. A),
+ *   2. the generalised Hermitian eigenpairs V a = mu G a with A^H G A = I
+ *      (Sec. 2.3, Eq. eigenvaleq),
+ *   3. the n_eig algebraically largest pairs, their filter weights d_e
+ *      (LSQ: d = mu, STD: d = 1) and levels [lo, hi) (Sec. 2.6),
+ *   4. the level images I_l(r) += sum_{e in l} d_e |sum_i exp(-j 2 pi <r, p_i>/wl) a_ie|^2
+ *      (Sec. 2.4, Eq. standard_synthesis; Algorithm 2 "GEMMEXP"),
+ * accumulated over collect() calls (Sec. 2.3: the time-integrated image is the
+ * sum of the per-step images).
+ *
+ * Conventions
+ *   - All arrays are column-major (Sec. 3.2 "Input data"). An n x 3 position
+ *     array holds x[0..n), then y[0..n), then z[0..n). Complex arrays are
+ *     interleaved (re, im) doubles.
+ *   - Pixel directions are unit vectors; station positions are in metres;
+ *     wl is the wavelength in metres.
+ *   - Level l takes every kept eigenvalue mu with lo_l <= mu < hi_l (first
+ *     matching level); eigenpairs outside every interval are dropped. Bounds
+ *     may be +-INFINITY.
+ *   - Images are n_pix x n_level, column-major.
+ *
+ * Ownership: the caller owns every input and output buffer. create() copies
+ * pixels and bounds to the device; collect*() consumes its inputs before it
+ * returns (host variants) or in stream order (device variant); get*() writes
+ * caller memory. The handle owns its device buffers until destroy().
+ *
+ * Errors: every call returns BIPP_OK (0) or a negative BIPP_ERR_* code and
+ * records a message readable with bipp_ss_last_error(h). No C++ exception
+ * crosses this boundary. A collect that fails leaves the accumulated images
+ * unchanged (a batch commits only when every step in it succeeded).
+ *
+ * Threads: a handle is not thread-safe; distinct handles are independent.
+ * Each handle owns one CUDA stream on its device.
+ */
+#ifndef BIPP_SS_H
+#define BIPP_SS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BIPP_OK 0
+#define BIPP_ERR_INVALID_ARG (-1)       /* bad size, pointer, value or option */
+#define BIPP_ERR_CUDA (-2)              /* a CUDA runtime call failed */
+#define BIPP_ERR_OUT_OF_MEMORY (-3)     /* device allocation failed */
+#define BIPP_ERR_GRAM_NOT_PD (-4)       /* Cholesky of G met a non-positive (or NaN) pivot */
+#define BIPP_ERR_EIG_NOT_CONVERGED (-5) /* Jacobi hit max_jacobi_sweeps */
+#define BIPP_ERR_DEVICE_TIMEOUT (-6)    /* a bounded device-side wait gave up */
+#define BIPP_ERR_UNSUPPORTED (-7)       /* e.g. n_eig > n_st, sizes beyond limits */
+
+/* Arithmetic of the synthesis stage (steps 1-3 always reach FP64 accuracy). */
+#define BIPP_PREC_FP64 0       /* FP64 phases, sincos and sums (CUDA cores) */
+#define BIPP_PREC_FP32 1       /* exact phase reduction, SFU sincos, FP32 CUDA-core sums */
+#define BIPP_PREC_SPLIT_BF16 2 /* exact phase reduction, SFU sincos, tcgen05 hi/lo BF16 x3, FP32 accumulate */
+#define BIPP_PREC_SPLIT_FP16 3 /* as SPLIT_BF16 with FP16 hi/lo operands (scaled W) */
+
+#define BIPP_FILTER_LSQ 0 /* d_e = mu_e (Sec. 2.6, least-squares image) */
+#define BIPP_FILTER_STD 1 /* d_e = 1    (Sec. 2.6, standardised image) */
+
+#define BIPP_EIG_JACOBI64 0 /* FP64 parallel-order Jacobi on the reduced matrix */
+#define BIPP_EIG_MIXED 1    /* FP32 Jacobi, then FP64 refinement of the kept pairs */
+
+typedef struct bipp_ss* bipp_ss_t;
+
+typedef struct {
+  int32_t n_eig;             /* eigenpairs kept per step (Sec. 2.6 "Truncation"); 0 = all */
+  int32_t precision;         /* BIPP_PREC_*; default BIPP_PREC_FP32 */
+  int32_t filter;            /* BIPP_FILTER_*; default LSQ */
+  int32_t gram_identity;     /* 1: G = I (back-projection decomposition, Sec. 6.3); default 0 */
+  int32_t max_jacobi_sweeps; /* default 40 */
+  double jacobi_tol;         /* stop when off(C) <= tol * ||C||_F; default 1e-13 */
+  int32_t device;            /* CUDA device ordinal; default -1 = current device */
+  int32_t eig_mode;          /* BIPP_EIG_*; default BIPP_EIG_JACOBI64 */
+  int32_t reserved[6];       /* must be zero */
+} bipp_ss_options;
+
+/* Fill *opt with the defaults listed above. */
+void bipp_ss_default_options(bipp_ss_options* opt);
+
+/* Create an imaging handle (the paper's StandardSynthesis object, Sec. 3.1).
+ *   pix_xyz      n_pix x 3 unit vectors (host), copied; must be finite.
+ *   wl           wavelength [m], finite and > 0.
+ *   level_bounds n_level x 2 (host): column 0 = lo, column 1 = hi; copied.
+ *   opt          NULL for defaults.
+ * n_pix >= 1, 1 <= n_level <= 16. Images start at zero. */
+int bipp_ss_create(bipp_ss_t* out, int64_t n_pix, const double* pix_xyz, double wl,
+                   int32_t n_level, const double* level_bounds, const bipp_ss_options* opt);
+
+/* Collect one time step (Algorithm 1 "collect"), host buffers.
+ *   st_xyz  n_st x 3 station positions [m] (must be finite).
+ *   vis     n_st x n_st Hermitian visibility matrix, complex128 interleaved.
+ * 1 <= n_eig <= n_st <= 1024. Synchronous: returns after the step is
+ * accumulated (or failed). */
+int bipp_ss_collect(bipp_ss_t h, int32_t n_st, const double* st_xyz, const double* vis);
+
+/* Collect n_t time steps in one batched launch sequence, host buffers.
+ * Step t has n_st[t] stations (ragged, e.g. after flagging) and keeps
+ * n_eig[t] eigenpairs (n_eig == NULL: the handle's n_eig for every step).
+ *   st_xyz  n_t blocks, block t = n_st_max x 3 (only the first n_st[t] rows
+ *           of each column are read).
+ *   vis     n_t blocks, block t = n_st_max x n_st_max complex128 (leading
+ *           n_st[t] x n_st[t] submatrix read).
+ * Commits all n_t steps or none. */
+int bipp_ss_collect_batch(bipp_ss_t h, int32_t n_t, int32_t n_st_max, const int32_t* n_st,
+                          const int32_t* n_eig, const double* st_xyz, const double* vis);
+
+/* As bipp_ss_collect_batch with the position and visibility blocks already
+ * on the device (e.g. memory owned by PyTorch), stream-ordered on `stream`
+ * (a cudaStream_t; NULL = the handle's stream). n_st / n_eig are host arrays
+ * of n_t int32 (n_eig NULL = handle default). Values are not inspected on the
+ * host: a non-finite position surfaces as BIPP_ERR_GRAM_NOT_PD. Returns after
+ * the batch has run and its per-step status was read (one host sync). */
+int bipp_ss_collect_device(bipp_ss_t h, int32_t n_t, int32_t n_st_max, const int32_t* n_st,
+                           const int32_t* n_eig, const double* d_st_xyz, const double* d_vis,
+                           void* stream);
+
+/* Copy the accumulated images (n_pix x n_level, column-major) to host memory. */
+int bipp_ss_get(bipp_ss_t h, float* out);
+int bipp_ss_get_f64(bipp_ss_t h, double* out);
+
+/* Copy the accumulated images to device memory d_out (n_pix x n_level FP64),
+ * ordered on `stream` (NULL = the handle's stream). */
+int bipp_ss_get_device_f64(bipp_ss_t h, double* d_out, void* stream);
+
+/* Zero the accumulated images. */
+int bipp_ss_reset(bipp_ss_t h);
+
+/* Replace the accumulated images (checkpoint/resume: images are additive
+ * over steps), host n_pix x n_level FP64. */
+int bipp_ss_set_images(bipp_ss_t h, const double* img);
+
+/* Diagnostics of the most recent batch: for step t < n_t_cap, the kept
+ * eigenvalues mu (descending) and their level ids (-1 = dropped) into
+ * mu[t * n_eig_cap + e], level[t * n_eig_cap + e]; n_kept[t] = eigenpairs
+ * kept; *n_t_out = steps in that batch. Any output pointer may be NULL. */
+int bipp_ss_last_eigvals(bipp_ss_t h, int32_t n_t_cap, int32_t n_eig_cap, int32_t* n_t_out,
+                         int32_t* n_kept, double* mu, int32_t* level);
+
+/* Device time [ms] of the most recent batch per stage:
+ * ms[0] Gram + Cholesky + reduction, ms[1] eigensolve, ms[2] select/pack,
+ * ms[3] synthesis, ms[4] Jacobi sweeps used (max over steps). */
+int bipp_ss_get_timings(bipp_ss_t h, double* ms5);
+
+/* Release the handle and its device memory. NULL is accepted. */
+int bipp_ss_destroy(bipp_ss_t h);
+
+/* Message of the last failing call on h (or of the last failing create when
+ * h is NULL); valid until the next call on h. Never NULL. */
+const char* bipp_ss_last_error(bipp_ss_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

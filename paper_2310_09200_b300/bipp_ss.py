@@ -1,0 +1,315 @@
+"""ctypes binding of libbipp_ss.so (C ABI in include/bipp_ss.h).
+
+Argument marshalling only: every stage of standard synthesis runs in the CUDA
+library. The library is required: importing works without a GPU, but any
+compute call raises if ``libbipp_ss.so`` is missing or no CUDA device is
+present — there is no CPU fallback.
+
+Array conventions follow the ABI (column-major, Sec. 3.2 of BIPP): positions
+are given here as ``(n, 3)`` float64 arrays, visibilities as ``(n, n)``
+complex128, images come back as ``(n_pix, n_level)``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from typing import Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libbipp_ss.so")
+
+BIPP_OK = 0
+BIPP_ERR_INVALID_ARG = -1
+BIPP_ERR_CUDA = -2
+BIPP_ERR_OUT_OF_MEMORY = -3
+BIPP_ERR_GRAM_NOT_PD = -4
+BIPP_ERR_EIG_NOT_CONVERGED = -5
+BIPP_ERR_DEVICE_TIMEOUT = -6
+BIPP_ERR_UNSUPPORTED = -7
+
+BIPP_PREC_FP64, BIPP_PREC_FP32, BIPP_PREC_SPLIT_BF16, BIPP_PREC_SPLIT_FP16 = 0, 1, 2, 3
+PRECISIONS = {"fp64": 0, "fp32": 1, "split_bf16": 2, "split_fp16": 3}
+BIPP_FILTER_LSQ, BIPP_FILTER_STD = 0, 1
+FILTERS = {"lsq": 0, "std": 1}
+BIPP_EIG_JACOBI64, BIPP_EIG_MIXED = 0, 1
+EIG_MODES = {"jacobi64": 0, "mixed": 1}
+
+ERROR_NAMES = {
+    -1: "BIPP_ERR_INVALID_ARG", -2: "BIPP_ERR_CUDA", -3: "BIPP_ERR_OUT_OF_MEMORY",
+    -4: "BIPP_ERR_GRAM_NOT_PD", -5: "BIPP_ERR_EIG_NOT_CONVERGED", -6: "BIPP_ERR_DEVICE_TIMEOUT",
+    -7: "BIPP_ERR_UNSUPPORTED",
+}
+
+EXPORTED = [
+    "bipp_ss_default_options", "bipp_ss_create", "bipp_ss_collect", "bipp_ss_collect_batch",
+    "bipp_ss_collect_device", "bipp_ss_get", "bipp_ss_get_f64", "bipp_ss_get_device_f64", "bipp_ss_reset",
+    "bipp_ss_set_images", "bipp_ss_last_eigvals", "bipp_ss_get_timings", "bipp_ss_destroy",
+    "bipp_ss_last_error",
+]
+
+
+class BippError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class bipp_ss_options(C.Structure):
+    _fields_ = [
+        ("n_eig", C.c_int32), ("precision", C.c_int32), ("filter", C.c_int32), ("gram_identity", C.c_int32),
+        ("max_jacobi_sweeps", C.c_int32), ("jacobi_tol", C.c_double), ("device", C.c_int32),
+        ("eig_mode", C.c_int32), ("reserved", C.c_int32 * 6),
+    ]
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libbipp_ss.so (raises if it is missing: no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing; build it with `python -m paper_2310_09200_b300.build`")
+    L = C.CDLL(path)
+    dp, ip, vp, i32, i64 = C.POINTER(C.c_double), C.POINTER(C.c_int32), C.c_void_p, C.c_int32, C.c_int64
+    H = C.c_void_p
+    L.bipp_ss_default_options.argtypes = [C.POINTER(bipp_ss_options)]
+    L.bipp_ss_default_options.restype = None
+    L.bipp_ss_create.argtypes = [C.POINTER(H), i64, dp, C.c_double, i32, dp, C.POINTER(bipp_ss_options)]
+    L.bipp_ss_collect.argtypes = [H, i32, dp, dp]
+    L.bipp_ss_collect_batch.argtypes = [H, i32, i32, ip, ip, dp, dp]
+    L.bipp_ss_collect_device.argtypes = [H, i32, i32, ip, ip, vp, vp, vp]
+    L.bipp_ss_get.argtypes = [H, C.POINTER(C.c_float)]
+    L.bipp_ss_get_f64.argtypes = [H, dp]
+    L.bipp_ss_get_device_f64.argtypes = [H, vp, vp]
+    L.bipp_ss_reset.argtypes = [H]
+    L.bipp_ss_set_images.argtypes = [H, dp]
+    L.bipp_ss_last_eigvals.argtypes = [H, i32, i32, ip, ip, dp, ip]
+    L.bipp_ss_get_timings.argtypes = [H, dp]
+    L.bipp_ss_destroy.argtypes = [H]
+    L.bipp_ss_last_error.argtypes = [H]
+    L.bipp_ss_last_error.restype = C.c_char_p
+    for name in EXPORTED:
+        if name not in ("bipp_ss_default_options", "bipp_ss_last_error"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ip(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+def bipp_ss_last_error(h) -> str:
+    return load().bipp_ss_last_error(h).decode()
+
+
+def _check(h, rc):
+    if rc != BIPP_OK:
+        raise BippError(rc, bipp_ss_last_error(h))
+
+
+def bipp_ss_default_options(**kw) -> bipp_ss_options:
+    o = bipp_ss_options()
+    load().bipp_ss_default_options(C.byref(o))
+    names = {"precision": PRECISIONS, "filter": FILTERS, "eig_mode": EIG_MODES}
+    for k, v in kw.items():
+        if k in names and isinstance(v, str):
+            v = names[k][v]
+        setattr(o, k, v)
+    return o
+
+
+def _colmajor_xyz(xyz) -> np.ndarray:
+    a = np.asarray(xyz, dtype=np.float64)
+    if a.ndim != 2 or a.shape[1] != 3:
+        raise ValueError("positions must be (n, 3)")
+    return np.ascontiguousarray(a.T)  # memory layout == column-major (n, 3)
+
+
+def bipp_ss_create(pix_xyz, wl: float, level_bounds, **opts) -> C.c_void_p:
+    """Create a handle. level_bounds: (n_level, 2) rows [lo, hi)."""
+    L = load()
+    pix = _colmajor_xyz(pix_xyz)
+    b = np.asarray(level_bounds, dtype=np.float64)
+    if b.ndim != 2 or b.shape[1] != 2:
+        raise ValueError("level_bounds must be (n_level, 2)")
+    bc = np.ascontiguousarray(b.T)
+    o = bipp_ss_default_options(**opts)
+    h = C.c_void_p()
+    rc = L.bipp_ss_create(C.byref(h), pix.shape[1], _dp(pix), float(wl), b.shape[0], _dp(bc), C.byref(o))
+    if rc != BIPP_OK:
+        raise BippError(rc, bipp_ss_last_error(None))
+    return h
+
+
+def pack_batch(st_xyz: Sequence[np.ndarray], vis: Sequence[np.ndarray], n_st_max: int | None = None):
+    """Ragged steps -> the ABI's block layout (n_t blocks of n_st_max x 3 and
+    n_st_max x n_st_max complex128, each column-major)."""
+    n_t = len(st_xyz)
+    nst = np.array([p.shape[0] for p in st_xyz], dtype=np.int32)
+    N = int(n_st_max or nst.max())
+    st = np.zeros((n_t, 3, N), dtype=np.float64)
+    V = np.zeros((n_t, N, N), dtype=np.complex128)  # V[t] holds vis[t].T: column-major block
+    for t in range(n_t):
+        n = nst[t]
+        st[t, :, :n] = np.asarray(st_xyz[t], dtype=np.float64).T
+        V[t, :n, :n] = np.asarray(vis[t], dtype=np.complex128).T
+    return nst, N, st, V
+
+
+def bipp_ss_collect(h, st_xyz, vis) -> None:
+    p = _colmajor_xyz(st_xyz)
+    V = np.ascontiguousarray(np.asarray(vis, dtype=np.complex128).T)
+    _check(h, load().bipp_ss_collect(h, p.shape[1], _dp(p), _dp(V.view(np.float64))))
+
+
+def bipp_ss_collect_batch(h, st_xyz: Sequence[np.ndarray], vis: Sequence[np.ndarray], n_eig=None) -> None:
+    nst, N, st, V = pack_batch(st_xyz, vis)
+    ne = None if n_eig is None else np.ascontiguousarray(n_eig, dtype=np.int32)
+    rc = load().bipp_ss_collect_batch(h, len(nst), N, _ip(nst), None if ne is None else _ip(ne), _dp(st),
+                                      _dp(V.view(np.float64)))
+    _check(h, rc)
+
+
+def bipp_ss_collect_device(h, n_st, d_st, d_vis, n_eig=None, stream=None) -> None:
+    """Device variant. d_st: torch float64 (T, 3, N) contiguous; d_vis: torch
+    complex128 (T, N, N) holding each block column-major (i.e. V[t].T, as
+    ``pack_batch`` returns); n_st / n_eig host int sequences; stream: a
+    torch.cuda.Stream or None (the handle's stream)."""
+    nst = np.ascontiguousarray(n_st, dtype=np.int32)
+    ne = None if n_eig is None else np.ascontiguousarray(n_eig, dtype=np.int32)
+    N = int(d_st.shape[-1])
+    sp = None if stream is None else C.c_void_p(stream.cuda_stream)
+    rc = load().bipp_ss_collect_device(h, len(nst), N, _ip(nst), None if ne is None else _ip(ne),
+                                       C.c_void_p(d_st.data_ptr()), C.c_void_p(d_vis.data_ptr()), sp)
+    _check(h, rc)
+
+
+def bipp_ss_get(h, n_pix: int, n_level: int) -> np.ndarray:
+    out = np.zeros((n_level, n_pix), dtype=np.float32)
+    _check(h, load().bipp_ss_get(h, out.ctypes.data_as(C.POINTER(C.c_float))))
+    return out.T
+
+
+def bipp_ss_get_f64(h, n_pix: int, n_level: int) -> np.ndarray:
+    out = np.zeros((n_level, n_pix), dtype=np.float64)
+    _check(h, load().bipp_ss_get_f64(h, _dp(out)))
+    return out.T
+
+
+def bipp_ss_get_device_f64(h, d_out, stream=None) -> None:
+    """d_out: torch float64 (n_level, n_pix) contiguous on the handle's device."""
+    sp = None if stream is None else C.c_void_p(stream.cuda_stream)
+    _check(h, load().bipp_ss_get_device_f64(h, C.c_void_p(d_out.data_ptr()), sp))
+
+
+def bipp_ss_reset(h) -> None:
+    _check(h, load().bipp_ss_reset(h))
+
+
+def bipp_ss_set_images(h, img) -> None:
+    a = np.ascontiguousarray(np.asarray(img, dtype=np.float64).T)
+    _check(h, load().bipp_ss_set_images(h, _dp(a)))
+
+
+def bipp_ss_last_eigvals(h, n_t_cap: int, n_eig_cap: int):
+    nt = C.c_int32(0)
+    nk = np.zeros(n_t_cap, dtype=np.int32)
+    mu = np.zeros((n_t_cap, n_eig_cap), dtype=np.float64)
+    lv = np.zeros((n_t_cap, n_eig_cap), dtype=np.int32)
+    _check(h, load().bipp_ss_last_eigvals(h, n_t_cap, n_eig_cap, C.byref(nt), _ip(nk), _dp(mu), _ip(lv)))
+    return nt.value, nk, mu, lv
+
+
+def bipp_ss_get_timings(h) -> dict:
+    a = np.zeros(5, dtype=np.float64)
+    _check(h, load().bipp_ss_get_timings(h, _dp(a)))
+    return {"gram_reduce_ms": a[0], "eig_ms": a[1], "select_ms": a[2], "synth_ms": a[3], "sweeps": int(a[4])}
+
+
+def bipp_ss_destroy(h) -> None:
+    if h:
+        load().bipp_ss_destroy(h)
+
+
+class StandardSynthesis:
+    """Handle wrapper: create once, collect per step (or per batch), get images."""
+
+    def __init__(self, pix_xyz, wl, level_bounds, **opts):
+        self.n_pix = int(np.asarray(pix_xyz).shape[0])
+        self.n_level = int(np.asarray(level_bounds).shape[0])
+        self.h = None
+        self.h = bipp_ss_create(pix_xyz, wl, level_bounds, **opts)
+
+    def collect(self, st_xyz, vis):
+        bipp_ss_collect(self.h, st_xyz, vis)
+
+    def collect_batch(self, st_xyz, vis, n_eig=None):
+        bipp_ss_collect_batch(self.h, st_xyz, vis, n_eig)
+
+    def get(self, f64=True):
+        if f64:
+            return bipp_ss_get_f64(self.h, self.n_pix, self.n_level)
+        return bipp_ss_get(self.h, self.n_pix, self.n_level)
+
+    def reset(self):
+        bipp_ss_reset(self.h)
+
+    def timings(self):
+        return bipp_ss_get_timings(self.h)
+
+    def close(self):
+        if self.h:
+            bipp_ss_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def quantile_level_bounds(pooled_mu, n_level: int) -> np.ndarray:
+    """Level intervals from pooled eigenvalues: inner edges at the 1/n_level
+    quantiles, each moved to the midpoint between the two nearest pooled
+    values; outer edges +-inf; level 0 holds the largest eigenvalues."""
+    v = np.sort(np.asarray(pooled_mu, dtype=np.float64))
+    edges = []
+    for q in range(1, n_level):
+        k = min(max(int(round(q * len(v) / n_level)), 1), len(v) - 1)
+        edges.append(0.5 * (v[k - 1] + v[k]))
+    edges = sorted(edges)
+    lo = [-math.inf] + edges
+    hi = edges + [math.inf]
+    return np.array(list(zip(lo, hi)))[::-1].copy()
+
+
+def estimate_level_bounds(st_xyz, vis, wl, n_eig, n_level, **opts):
+    """Parameter-estimation pre-pass (Table tts): run the GPU Gram + eigensolve
+    on the given steps (synthesis on one pixel only), pool the kept
+    eigenvalues and derive quantile level bounds. Returns (bounds, pooled)."""
+    one_px = np.array([[0.0, 0.0, 1.0]])
+    opts = {k: v for k, v in opts.items() if k != "n_eig"}
+    with StandardSynthesis(one_px, wl, np.array([[-math.inf, math.inf]]), n_eig=n_eig, **opts) as ss:
+        ss.collect_batch(st_xyz, vis)
+        nt, nk, mu, _ = bipp_ss_last_eigvals(ss.h, len(vis), n_eig)
+    pooled = np.concatenate([mu[t, : nk[t]] for t in range(nt)])
+    return quantile_level_bounds(pooled, n_level), pooled

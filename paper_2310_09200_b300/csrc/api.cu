@@ -1,0 +1,453 @@
+// api.cu — the C ABI of libbipp_ss.so (declared in include/bipp_ss.h).
+//
+// A handle is the paper's StandardSynthesis imaging object (Sec. 3.1): it
+// holds the pixel grid, the level intervals and the accumulated images on
+// one device, plus a batch workspace that grows to the largest batch seen.
+// collect() runs Algorithm 1 for one or many steps as a stream-ordered chain
+// of kernels with no host round trip until the final status check; the
+// synthesis kernel reads a device flag and commits nothing if any step of
+// the batch failed.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "bipp_internal.cuh"
+#include "bipp_ss.h"
+#include "synth_tc.cuh"
+
+using namespace bipp;
+
+struct bipp_ss {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int64_t n_pix = 0;
+  int n_level = 0;
+  double wl = 0.0;
+  bipp_ss_options opt{};
+  double* d_pix = nullptr;     // [3][n_pix]
+  float* d_pix_hl = nullptr;   // [6][n_pix]
+  double* d_img = nullptr;     // [n_level][n_pix]
+  double* d_bounds = nullptr;  // [2][n_level]
+  // batch workspace
+  int cap_T = 0, cap_N = 0, cap_K = 0;
+  double* d_st = nullptr;
+  double2* d_vis = nullptr;
+  double* d_G = nullptr;
+  double* d_Linv = nullptr;
+  double2* d_X = nullptr;
+  double2* d_C = nullptr;
+  double2* d_Q = nullptr;
+  double* d_mu = nullptr;
+  int* d_status = nullptr;
+  int* d_sweeps = nullptr;
+  int* d_nkept = nullptr;
+  double* d_sel_mu = nullptr;
+  int* d_level = nullptr;
+  double* d_wt = nullptr;
+  double2* d_W64 = nullptr;
+  float2* d_W32 = nullptr;
+  float* d_q = nullptr;
+  int* d_nst = nullptr;
+  int* d_neig = nullptr;
+  int* d_flag = nullptr;
+  TcWorkspace tc{};
+  // last batch
+  int last_T = 0, last_N = 0, last_K = 0;
+  double timings[5] = {0, 0, 0, 0, 0};
+  cudaEvent_t ev[5] = {};
+  std::string err;
+};
+
+static std::string g_create_err = "no error";
+
+static int fail(bipp_ss* h, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (h) h->err = buf; else g_create_err = buf;
+  return code;
+}
+
+#define CUDA_TRY(h, call)                                                                        \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess) {                                                                     \
+      return fail((h), e_ == cudaErrorMemoryAllocation ? BIPP_ERR_OUT_OF_MEMORY : BIPP_ERR_CUDA, \
+                  "%s failed: %s", #call, cudaGetErrorString(e_));                               \
+    }                                                                                            \
+  } while (0)
+
+template <typename T>
+static cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+static void free_batch(bipp_ss* h) {
+  void* ptrs[] = {h->d_st, h->d_vis, h->d_G, h->d_Linv, h->d_X, h->d_C, h->d_Q, h->d_mu, h->d_status,
+                  h->d_sweeps, h->d_nkept, h->d_sel_mu, h->d_level, h->d_wt, h->d_W64, h->d_W32, h->d_q,
+                  h->d_nst, h->d_neig, h->d_flag};
+  for (void* p : ptrs) if (p) cudaFree(p);
+  h->d_st = nullptr; h->d_vis = nullptr; h->d_G = nullptr; h->d_Linv = nullptr; h->d_X = nullptr;
+  h->d_C = nullptr; h->d_Q = nullptr; h->d_mu = nullptr; h->d_status = nullptr; h->d_sweeps = nullptr;
+  h->d_nkept = nullptr; h->d_sel_mu = nullptr; h->d_level = nullptr; h->d_wt = nullptr; h->d_W64 = nullptr;
+  h->d_W32 = nullptr; h->d_q = nullptr; h->d_nst = nullptr; h->d_neig = nullptr; h->d_flag = nullptr;
+  tc_free(&h->tc);
+  h->cap_T = h->cap_N = h->cap_K = 0;
+}
+
+static int ensure_batch(bipp_ss* h, int T, int N, int K) {
+  if (T <= h->cap_T && N <= h->cap_N && K <= h->cap_K) return BIPP_OK;
+  T = std::max(T, h->cap_T);
+  N = std::max(N, h->cap_N);
+  K = std::max(K, h->cap_K);
+  free_batch(h);
+  const size_t NN = (size_t)N * N;
+  CUDA_TRY(h, dalloc(&h->d_st, (size_t)T * 3 * N));
+  CUDA_TRY(h, dalloc(&h->d_vis, (size_t)T * NN));
+  CUDA_TRY(h, dalloc(&h->d_G, (size_t)T * NN));
+  CUDA_TRY(h, dalloc(&h->d_Linv, (size_t)T * NN));
+  CUDA_TRY(h, dalloc(&h->d_X, (size_t)T * NN));
+  CUDA_TRY(h, dalloc(&h->d_C, (size_t)T * NN));
+  CUDA_TRY(h, dalloc(&h->d_Q, (size_t)T * NN));
+  CUDA_TRY(h, dalloc(&h->d_mu, (size_t)T * N));
+  CUDA_TRY(h, dalloc(&h->d_status, (size_t)T));
+  CUDA_TRY(h, dalloc(&h->d_sweeps, (size_t)T));
+  CUDA_TRY(h, dalloc(&h->d_nkept, (size_t)T));
+  CUDA_TRY(h, dalloc(&h->d_sel_mu, (size_t)T * K));
+  CUDA_TRY(h, dalloc(&h->d_level, (size_t)T * K));
+  CUDA_TRY(h, dalloc(&h->d_wt, (size_t)T * K));
+  CUDA_TRY(h, dalloc(&h->d_W64, (size_t)T * K * N));
+  CUDA_TRY(h, dalloc(&h->d_W32, (size_t)T * K * N));
+  CUDA_TRY(h, dalloc(&h->d_q, (size_t)T * 6 * N));
+  CUDA_TRY(h, dalloc(&h->d_nst, (size_t)T));
+  CUDA_TRY(h, dalloc(&h->d_neig, (size_t)T));
+  CUDA_TRY(h, dalloc(&h->d_flag, 1));
+  if (tc_alloc(&h->tc, T, N, K)) return fail(h, BIPP_ERR_OUT_OF_MEMORY, "tensor-core workspace allocation failed");
+  h->cap_T = T;
+  h->cap_N = N;
+  h->cap_K = K;
+  return BIPP_OK;
+}
+
+static Batch make_batch(bipp_ss* h, int T, int N, int K, const double* st, const double2* vis) {
+  Batch b;
+  b.T = T; b.n_max = N; b.k_max = K;
+  b.nst = h->d_nst; b.neig = h->d_neig;
+  b.st = st; b.vis = vis;
+  b.G = h->d_G; b.Linv = h->d_Linv; b.X = h->d_X; b.C = h->d_C; b.Q = h->d_Q; b.mu = h->d_mu;
+  b.status = h->d_status; b.sweeps = h->d_sweeps; b.nkept = h->d_nkept;
+  b.sel_mu = h->d_sel_mu; b.level = h->d_level; b.wt = h->d_wt; b.W64 = h->d_W64; b.W32 = h->d_W32;
+  b.q = h->d_q; b.flag = h->d_flag;
+  return b;
+}
+
+extern "C" void bipp_ss_default_options(bipp_ss_options* opt) {
+  if (!opt) return;
+  memset(opt, 0, sizeof(*opt));
+  opt->n_eig = 0;
+  opt->precision = BIPP_PREC_FP32;
+  opt->filter = BIPP_FILTER_LSQ;
+  opt->gram_identity = 0;
+  opt->max_jacobi_sweeps = 40;
+  opt->jacobi_tol = 1e-13;
+  opt->device = -1;
+  opt->eig_mode = BIPP_EIG_JACOBI64;
+}
+
+extern "C" int bipp_ss_destroy(bipp_ss_t h) {
+  if (!h) return BIPP_OK;
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  free_batch(h);
+  if (h->d_pix) cudaFree(h->d_pix);
+  if (h->d_pix_hl) cudaFree(h->d_pix_hl);
+  if (h->d_img) cudaFree(h->d_img);
+  if (h->d_bounds) cudaFree(h->d_bounds);
+  for (auto& e : h->ev) if (e) cudaEventDestroy(e);
+  if (h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+  return BIPP_OK;
+}
+
+extern "C" int bipp_ss_create(bipp_ss_t* out, int64_t n_pix, const double* pix_xyz, double wl, int32_t n_level,
+                              const double* level_bounds, const bipp_ss_options* opt) {
+  if (!out) return fail(nullptr, BIPP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (n_pix < 1 || !pix_xyz) return fail(nullptr, BIPP_ERR_INVALID_ARG, "need n_pix >= 1 and pix_xyz");
+  if (!(wl > 0.0) || !isfinite(wl)) return fail(nullptr, BIPP_ERR_INVALID_ARG, "wavelength must be finite and > 0");
+  if (n_level < 1 || n_level > kMaxLevels || !level_bounds)
+    return fail(nullptr, BIPP_ERR_INVALID_ARG, "need 1 <= n_level <= %d and level_bounds", kMaxLevels);
+  bipp_ss_options o;
+  if (opt) o = *opt; else bipp_ss_default_options(&o);
+  for (int i = 0; i < 6; ++i)
+    if (o.reserved[i]) return fail(nullptr, BIPP_ERR_INVALID_ARG, "reserved option fields must be zero");
+  if (o.precision < BIPP_PREC_FP64 || o.precision > BIPP_PREC_SPLIT_FP16)
+    return fail(nullptr, BIPP_ERR_INVALID_ARG, "unknown precision %d", o.precision);
+  if (o.filter != BIPP_FILTER_LSQ && o.filter != BIPP_FILTER_STD)
+    return fail(nullptr, BIPP_ERR_INVALID_ARG, "unknown filter %d", o.filter);
+  if (o.eig_mode != BIPP_EIG_JACOBI64 && o.eig_mode != BIPP_EIG_MIXED)
+    return fail(nullptr, BIPP_ERR_INVALID_ARG, "unknown eig_mode %d", o.eig_mode);
+  if (o.n_eig < 0 || o.max_jacobi_sweeps < 1 || !(o.jacobi_tol > 0.0))
+    return fail(nullptr, BIPP_ERR_INVALID_ARG, "bad n_eig / max_jacobi_sweeps / jacobi_tol");
+  for (int l = 0; l < n_level; ++l)
+    if (isnan(level_bounds[l]) || isnan(level_bounds[n_level + l]))
+      return fail(nullptr, BIPP_ERR_INVALID_ARG, "level bound %d is NaN", l);
+  for (int64_t i = 0; i < 3 * n_pix; ++i)
+    if (!isfinite(pix_xyz[i]))
+      return fail(nullptr, BIPP_ERR_INVALID_ARG, "pixel coordinate %lld is not finite", (long long)i);
+
+  bipp_ss* h = new bipp_ss();
+  h->opt = o;
+  h->n_pix = n_pix;
+  h->n_level = n_level;
+  h->wl = wl;
+  if (o.device >= 0 && cudaSetDevice(o.device) != cudaSuccess) {
+    delete h;
+    return fail(nullptr, BIPP_ERR_CUDA, "cudaSetDevice(%d) failed", o.device);
+  }
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    delete h;
+    return fail(nullptr, BIPP_ERR_CUDA, "no CUDA device");
+  }
+  auto bail = [&](int code, const char* what, cudaError_t e) {
+    fail(nullptr, code, "%s: %s", what, cudaGetErrorString(e));
+    bipp_ss_destroy(h);
+    return code;
+  };
+  cudaError_t e;
+  if ((e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)) != cudaSuccess) return bail(BIPP_ERR_CUDA, "stream", e);
+  for (auto& ev : h->ev)
+    if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(BIPP_ERR_CUDA, "event", e);
+  if ((e = dalloc(&h->d_pix, (size_t)3 * n_pix)) != cudaSuccess) return bail(BIPP_ERR_OUT_OF_MEMORY, "pixels", e);
+  if ((e = dalloc(&h->d_pix_hl, (size_t)6 * n_pix)) != cudaSuccess) return bail(BIPP_ERR_OUT_OF_MEMORY, "pixels", e);
+  if ((e = dalloc(&h->d_img, (size_t)n_level * n_pix)) != cudaSuccess) return bail(BIPP_ERR_OUT_OF_MEMORY, "images", e);
+  if ((e = dalloc(&h->d_bounds, (size_t)2 * n_level)) != cudaSuccess) return bail(BIPP_ERR_OUT_OF_MEMORY, "bounds", e);
+  if ((e = cudaMemcpy(h->d_pix, pix_xyz, sizeof(double) * 3 * n_pix, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return bail(BIPP_ERR_CUDA, "pixel upload", e);
+  if ((e = cudaMemcpy(h->d_bounds, level_bounds, sizeof(double) * 2 * n_level, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return bail(BIPP_ERR_CUDA, "bounds upload", e);
+  if ((e = cudaMemset(h->d_img, 0, sizeof(double) * n_level * n_pix)) != cudaSuccess) return bail(BIPP_ERR_CUDA, "memset", e);
+  launch_pixel_split(h->d_pix, h->d_pix_hl, n_pix, h->stream);
+  if ((e = cudaGetLastError()) != cudaSuccess) return bail(BIPP_ERR_CUDA, "pixel split launch", e);
+  if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(BIPP_ERR_CUDA, "pixel split", e);
+  *out = h;
+  return BIPP_OK;
+}
+
+// Validate the ragged batch description; returns K_max or a negative code.
+static int check_sizes(bipp_ss* h, int n_t, int n_st_max, const int32_t* n_st, const int32_t* n_eig,
+                       std::vector<int>& nst_v, std::vector<int>& neig_v) {
+  if (n_t < 1) return fail(h, BIPP_ERR_INVALID_ARG, "n_t must be >= 1");
+  if (n_st_max < 1 || n_st_max > kMaxStations)
+    return fail(h, BIPP_ERR_UNSUPPORTED, "n_st_max must be in [1, %d]", kMaxStations);
+  if (!n_st) return fail(h, BIPP_ERR_INVALID_ARG, "n_st is NULL");
+  nst_v.resize(n_t);
+  neig_v.resize(n_t);
+  int kmax = 1;
+  for (int t = 0; t < n_t; ++t) {
+    const int n = n_st[t];
+    if (n < 1 || n > n_st_max) return fail(h, BIPP_ERR_INVALID_ARG, "step %d: n_st=%d outside [1, %d]", t, n, n_st_max);
+    const int k = n_eig ? n_eig[t] : (h->opt.n_eig > 0 ? h->opt.n_eig : n);
+    if (k < 1) return fail(h, BIPP_ERR_INVALID_ARG, "step %d: n_eig=%d must be >= 1", t, k);
+    if (k > n) return fail(h, BIPP_ERR_UNSUPPORTED, "step %d: n_eig=%d exceeds n_st=%d", t, k, n);
+    nst_v[t] = n;
+    neig_v[t] = k;
+    kmax = std::max(kmax, k);
+  }
+  return kmax;
+}
+
+static int run_batch(bipp_ss* h, int n_t, int N, const std::vector<int>& nst_v, const std::vector<int>& neig_v,
+                     int K, const double* d_st, const double2* d_vis, cudaStream_t s) {
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_nst, nst_v.data(), sizeof(int) * n_t, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_neig, neig_v.data(), sizeof(int) * n_t, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int) * n_t, s));
+  CUDA_TRY(h, cudaMemsetAsync(h->d_sweeps, 0, sizeof(int) * n_t, s));
+  CUDA_TRY(h, cudaMemsetAsync(h->d_flag, 0, sizeof(int), s));
+  Batch b = make_batch(h, n_t, N, K, d_st, d_vis);
+  const int gi = h->opt.gram_identity;
+  CUDA_TRY(h, cudaEventRecord(h->ev[0], s));
+  launch_gram(b, h->wl, gi, s);
+  launch_cholesky(b, gi, s);
+  launch_reduce(b, gi, s);
+  CUDA_TRY(h, cudaEventRecord(h->ev[1], s));
+  launch_jacobi(b, h->opt.jacobi_tol, h->opt.max_jacobi_sweeps, s);
+  CUDA_TRY(h, cudaEventRecord(h->ev[2], s));
+  launch_select(b, h->wl, h->n_level, h->d_bounds, h->opt.filter, s);
+  CUDA_TRY(h, cudaEventRecord(h->ev[3], s));
+  Pixels px{h->n_pix, h->d_pix, h->d_pix_hl};
+  switch (h->opt.precision) {
+    case BIPP_PREC_FP64:
+      launch_synth_simt_f64(b, px, h->wl, h->n_level, h->d_img, s);
+      break;
+    case BIPP_PREC_FP32:
+      launch_synth_simt_f32(b, px, h->n_level, h->d_img, s);
+      break;
+    default: {
+      int rc = launch_synth_tc(b, px, h->n_level, h->d_img, h->opt.precision == BIPP_PREC_SPLIT_FP16, &h->tc, s);
+      if (rc) {
+        cudaStreamSynchronize(s);
+        return fail(h, BIPP_ERR_UNSUPPORTED, "tensor-core synthesis is not available (code %d)", rc);
+      }
+    }
+  }
+  CUDA_TRY(h, cudaGetLastError());
+  CUDA_TRY(h, cudaEventRecord(h->ev[4], s));
+  CUDA_TRY(h, cudaStreamSynchronize(s));
+  h->last_T = n_t;
+  h->last_N = N;
+  h->last_K = K;
+  float ms[4] = {0, 0, 0, 0};
+  for (int i = 0; i < 4; ++i) cudaEventElapsedTime(&ms[i], h->ev[i], h->ev[i + 1]);
+  std::vector<int> status(n_t), sweeps(n_t);
+  CUDA_TRY(h, cudaMemcpy(status.data(), h->d_status, sizeof(int) * n_t, cudaMemcpyDeviceToHost));
+  CUDA_TRY(h, cudaMemcpy(sweeps.data(), h->d_sweeps, sizeof(int) * n_t, cudaMemcpyDeviceToHost));
+  const int tc_status = (h->opt.precision >= BIPP_PREC_SPLIT_BF16) ? tc_read_status(&h->tc) : 0;
+  for (int i = 0; i < 4; ++i) h->timings[i] = ms[i];
+  h->timings[4] = *std::max_element(sweeps.begin(), sweeps.end());
+  for (int t = 0; t < n_t; ++t) {
+    if (status[t] & kStatusNotPD)
+      return fail(h, BIPP_ERR_GRAM_NOT_PD, "step %d: Gram matrix is not positive definite (Cholesky pivot <= 0 or NaN)", t);
+    if (status[t] & kStatusNotConverged)
+      return fail(h, BIPP_ERR_EIG_NOT_CONVERGED, "step %d: Jacobi did not converge in %d sweeps", t,
+                  h->opt.max_jacobi_sweeps);
+  }
+  if (tc_status) return fail(h, BIPP_ERR_DEVICE_TIMEOUT, "tensor-core synthesis: bounded wait gave up (code %d)", tc_status);
+  return BIPP_OK;
+}
+
+extern "C" int bipp_ss_collect_batch(bipp_ss_t h, int32_t n_t, int32_t n_st_max, const int32_t* n_st,
+                                     const int32_t* n_eig, const double* st_xyz, const double* vis) {
+  if (!h) return fail(nullptr, BIPP_ERR_INVALID_ARG, "handle is NULL");
+  if (!st_xyz || !vis) return fail(h, BIPP_ERR_INVALID_ARG, "st_xyz / vis is NULL");
+  std::vector<int> nst_v, neig_v;
+  const int K = check_sizes(h, n_t, n_st_max, n_st, n_eig, nst_v, neig_v);
+  if (K < 0) return K;
+  for (int t = 0; t < n_t; ++t)
+    for (int c = 0; c < 3; ++c)
+      for (int i = 0; i < nst_v[t]; ++i)
+        if (!isfinite(st_xyz[((size_t)t * 3 + c) * n_st_max + i]))
+          return fail(h, BIPP_ERR_INVALID_ARG, "step %d: station %d coordinate %d is not finite", t, i, c);
+  CUDA_TRY(h, cudaSetDevice(h->device));
+  int rc = ensure_batch(h, n_t, n_st_max, K);
+  if (rc) return rc;
+  const size_t N = (size_t)n_st_max;
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_st, st_xyz, sizeof(double) * 3 * N * n_t, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_vis, vis, sizeof(double2) * N * N * n_t, cudaMemcpyHostToDevice, h->stream));
+  return run_batch(h, n_t, n_st_max, nst_v, neig_v, K, h->d_st, h->d_vis, h->stream);
+}
+
+extern "C" int bipp_ss_collect(bipp_ss_t h, int32_t n_st, const double* st_xyz, const double* vis) {
+  return bipp_ss_collect_batch(h, 1, n_st, &n_st, nullptr, st_xyz, vis);
+}
+
+extern "C" int bipp_ss_collect_device(bipp_ss_t h, int32_t n_t, int32_t n_st_max, const int32_t* n_st,
+                                      const int32_t* n_eig, const double* d_st_xyz, const double* d_vis,
+                                      void* stream) {
+  if (!h) return fail(nullptr, BIPP_ERR_INVALID_ARG, "handle is NULL");
+  if (!d_st_xyz || !d_vis) return fail(h, BIPP_ERR_INVALID_ARG, "d_st_xyz / d_vis is NULL");
+  std::vector<int> nst_v, neig_v;
+  const int K = check_sizes(h, n_t, n_st_max, n_st, n_eig, nst_v, neig_v);
+  if (K < 0) return K;
+  CUDA_TRY(h, cudaSetDevice(h->device));
+  cudaPointerAttributes a1{}, a2{};
+  if (cudaPointerGetAttributes(&a1, d_st_xyz) != cudaSuccess || cudaPointerGetAttributes(&a2, d_vis) != cudaSuccess ||
+      a1.type != cudaMemoryTypeDevice || a2.type != cudaMemoryTypeDevice || a1.device != h->device ||
+      a2.device != h->device) {
+    cudaGetLastError();
+    return fail(h, BIPP_ERR_INVALID_ARG, "d_st_xyz and d_vis must be device memory on device %d", h->device);
+  }
+  int rc = ensure_batch(h, n_t, n_st_max, K);
+  if (rc) return rc;
+  cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
+  return run_batch(h, n_t, n_st_max, nst_v, neig_v, K, d_st_xyz, reinterpret_cast<const double2*>(d_vis), s);
+}
+
+extern "C" int bipp_ss_get_f64(bipp_ss_t h, double* out) {
+  if (!h) return fail(nullptr, BIPP_ERR_INVALID_ARG, "handle is NULL");
+  if (!out) return fail(h, BIPP_ERR_INVALID_ARG, "out is NULL");
+  CUDA_TRY(h, cudaSetDevice(h->device));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  CUDA_TRY(h, cudaMemcpy(out, h->d_img, sizeof(double) * h->n_level * h->n_pix, cudaMemcpyDeviceToHost));
+  return BIPP_OK;
+}
+
+extern "C" int bipp_ss_get(bipp_ss_t h, float* out) {
+  if (!h) return fail(nullptr, BIPP_ERR_INVALID_ARG, "handle is NULL");
+  if (!out) return fail(h, BIPP_ERR_INVALID_ARG, "out is NULL");
+  std::vector<double> tmp((size_t)h->n_level * h->n_pix);
+  const int rc = bipp_ss_get_f64(h, tmp.data());
+  if (rc) return rc;
+  for (size_t i = 0; i < tmp.size(); ++i) out[i] = (float)tmp[i];
+  return BIPP_OK;
+}
+
+extern "C" int bipp_ss_get_device_f64(bipp_ss_t h, double* d_out, void* stream) {
+  if (!h) return fail(nullptr, BIPP_ERR_INVALID_ARG, "handle is NULL");
+  if (!d_out) return fail(h, BIPP_ERR_INVALID_ARG, "d_out is NULL");
+  CUDA_TRY(h, cudaSetDevice(h->device));
+  cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(d_out, h->d_img, sizeof(double) * h->n_level * h->n_pix, cudaMemcpyDeviceToDevice, s));
+  return BIPP_OK;
+}
+
+extern "C" int bipp_ss_reset(bipp_ss_t h) {
+  if (!h) return fail(nullptr, BIPP_ERR_INVALID_ARG, "handle is NULL");
+  CUDA_TRY(h, cudaSetDevice(h->device));
+  CUDA_TRY(h, cudaMemsetAsync(h->d_img, 0, sizeof(double) * h->n_level * h->n_pix, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return BIPP_OK;
+}
+
+extern "C" int bipp_ss_set_images(bipp_ss_t h, const double* img) {
+  if (!h) return fail(nullptr, BIPP_ERR_INVALID_ARG, "handle is NULL");
+  if (!img) return fail(h, BIPP_ERR_INVALID_ARG, "img is NULL");
+  CUDA_TRY(h, cudaSetDevice(h->device));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  CUDA_TRY(h, cudaMemcpy(h->d_img, img, sizeof(double) * h->n_level * h->n_pix, cudaMemcpyHostToDevice));
+  return BIPP_OK;
+}
+
+extern "C" int bipp_ss_last_eigvals(bipp_ss_t h, int32_t n_t_cap, int32_t n_eig_cap, int32_t* n_t_out,
+                                    int32_t* n_kept, double* mu, int32_t* level) {
+  if (!h) return fail(nullptr, BIPP_ERR_INVALID_ARG, "handle is NULL");
+  if (n_t_out) *n_t_out = h->last_T;
+  if (h->last_T == 0) return BIPP_OK;
+  CUDA_TRY(h, cudaSetDevice(h->device));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  const int T = std::min(n_t_cap, h->last_T), K = h->last_K;
+  if (T <= 0) return BIPP_OK;
+  std::vector<int> nk(h->last_T);
+  std::vector<double> m((size_t)h->last_T * K);
+  std::vector<int> lv((size_t)h->last_T * K);
+  CUDA_TRY(h, cudaMemcpy(nk.data(), h->d_nkept, sizeof(int) * h->last_T, cudaMemcpyDeviceToHost));
+  CUDA_TRY(h, cudaMemcpy(m.data(), h->d_sel_mu, sizeof(double) * m.size(), cudaMemcpyDeviceToHost));
+  CUDA_TRY(h, cudaMemcpy(lv.data(), h->d_level, sizeof(int) * lv.size(), cudaMemcpyDeviceToHost));
+  for (int t = 0; t < T; ++t) {
+    if (n_kept) n_kept[t] = nk[t];
+    for (int e = 0; e < std::min(n_eig_cap, K); ++e) {
+      if (mu) mu[(size_t)t * n_eig_cap + e] = m[(size_t)t * K + e];
+      if (level) level[(size_t)t * n_eig_cap + e] = lv[(size_t)t * K + e];
+    }
+  }
+  return BIPP_OK;
+}
+
+extern "C" int bipp_ss_get_timings(bipp_ss_t h, double* ms5) {
+  if (!h) return fail(nullptr, BIPP_ERR_INVALID_ARG, "handle is NULL");
+  if (!ms5) return fail(h, BIPP_ERR_INVALID_ARG, "ms5 is NULL");
+  for (int i = 0; i < 5; ++i) ms5[i] = h->timings[i];
+  return BIPP_OK;
+}
+
+extern "C" const char* bipp_ss_last_error(bipp_ss_t h) { return h ? h->err.c_str() : g_create_err.c_str(); }

@@ -1,0 +1,69 @@
+// bipp_internal.cuh — shared declarations of the B300 standard-synthesis
+// library (device layouts, kernel launchers). Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bipp {
+
+constexpr int kMaxStations = 1024;  // per step
+constexpr int kMaxLevels = 16;
+constexpr int kMaxEig = 1024;
+
+// Per-step status bits written by the device stages.
+constexpr int kStatusNotPD = 1;         // Cholesky met a non-positive (or NaN) pivot
+constexpr int kStatusNotConverged = 2;  // Jacobi hit its sweep cap
+constexpr int kStatusTimeout = 4;       // a bounded device wait gave up
+
+// Device-side view of one batch of T steps. Step t uses the leading
+// nst[t] x nst[t] block of every per-step N x N array (N = n_max).
+struct Batch {
+  int T;          // steps in the batch
+  int n_max;      // leading dimension of per-step station arrays
+  int k_max;      // leading dimension of per-step eigen arrays
+  const int* nst;   // [T] stations per step
+  const int* neig;  // [T] eigenpairs requested per step
+  const double* st;   // [T][3][n_max] station xyz (metres), column-major per step
+  const double2* vis; // [T][n_max][n_max] visibilities, column-major per step
+  double* G;      // [T][n_max][n_max] Gram matrix, then its Cholesky factor L (lower)
+  double* Linv;   // [T][n_max][n_max] row-major L^{-1}: Linv[t][i*n_max + j] = (L^{-1})_ij
+  double2* X;     // [T][n_max][n_max] scratch: L^{-1} V (column-major)
+  double2* C;     // [T][n_max][n_max] reduced matrix L^{-1} V L^{-T} (column-major), Jacobi in place
+  double2* Q;     // [T][n_max][n_max] Jacobi rotations (column-major)
+  double* mu;     // [T][n_max] Jacobi eigenvalues (unsorted)
+  int* status;    // [T] status bits
+  int* sweeps;    // [T] Jacobi sweeps used
+  // selection / packing outputs
+  int* nkept;     // [T] eigenpairs kept (== neig[t] on success, 0 on failure)
+  double* sel_mu; // [T][k_max] kept eigenvalues, descending
+  int* level;     // [T][k_max] level id, -1 = dropped
+  double* wt;     // [T][k_max] filter weight d_e
+  double2* W64;   // [T][k_max][n_max] kept eigenvectors a_e (G-orthonormal), e-major
+  float2* W32;    // [T][n_max][k_max] FP32 copy, station-major
+  float* q;       // [T][6][n_max] station p/wl as float hi/lo: xh,yh,zh,xl,yl,zl
+  int* flag;      // [1] OR of all step statuses (synthesis skips the batch if set)
+};
+
+struct Pixels {
+  int64_t n;
+  const double* xyz;  // [3][n] FP64 unit vectors (column-major)
+  const float* hl;    // [6][n] float hi/lo split: xh,yh,zh,xl,yl,zl
+};
+
+// ---- launchers (stream-ordered, no synchronisation) ----
+void launch_gram(const Batch& b, double wl, int gram_identity, cudaStream_t s);
+void launch_cholesky(const Batch& b, int gram_identity, cudaStream_t s);
+void launch_reduce(const Batch& b, int gram_identity, cudaStream_t s);
+void launch_jacobi(const Batch& b, double tol, int max_sweeps, cudaStream_t s);
+void launch_select(const Batch& b, double wl, int n_level, const double* d_bounds, int filter,
+                   cudaStream_t s);
+void launch_pixel_split(const double* d_xyz, float* d_hl, int64_t n, cudaStream_t s);
+
+// Synthesis of a whole batch into img (n_pix x n_level FP64, accumulated).
+void launch_synth_simt_f64(const Batch& b, const Pixels& px, double wl, int n_level, double* img,
+                           cudaStream_t s);
+void launch_synth_simt_f32(const Batch& b, const Pixels& px, int n_level, double* img,
+                           cudaStream_t s);
+
+}  // namespace bipp

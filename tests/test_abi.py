@@ -1,0 +1,132 @@
+"""Host-side checks of the C-ABI library (no GPU compute): it loads, exports
+every entry point declared in include/bipp_ss.h, and rejects invalid
+arguments before touching a device."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2310_09200_b300 import bipp_ss, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(bipp_\w+)\s*\(", txt))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return bipp_ss.load()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    declared = _declared()
+    assert "bipp_ss_create" in declared and "bipp_ss_collect" in declared
+    out = subprocess.run(["nm", "-D", "--defined-only", bipp_ss.LIB_PATH], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\bT (bipp_\w+)", out))
+    missing = declared - exported
+    assert not missing, f"declared but not exported: {missing}"
+    for name in declared:
+        getattr(lib, name)
+
+
+def test_binding_names_match_abi():
+    assert set(bipp_ss.EXPORTED) == _declared()
+    for name in bipp_ss.EXPORTED:
+        assert hasattr(bipp_ss, name), name
+
+
+def test_library_does_not_use_the_oracle():
+    out = subprocess.run(["ldd", bipp_ss.LIB_PATH], capture_output=True, text=True).stdout
+    assert "oracle" not in out
+    syms = subprocess.run(["nm", "-D", bipp_ss.LIB_PATH], capture_output=True, text=True).stdout
+    assert "orc_" not in syms
+
+
+def test_default_options(lib):
+    o = bipp_ss.bipp_ss_default_options()
+    assert o.precision == bipp_ss.BIPP_PREC_FP32 and o.filter == bipp_ss.BIPP_FILTER_LSQ
+    assert o.max_jacobi_sweeps == 40 and abs(o.jacobi_tol - 1e-13) < 1e-30 and o.gram_identity == 0
+    assert o.device == -1 and o.eig_mode == bipp_ss.BIPP_EIG_JACOBI64
+
+
+@pytest.mark.parametrize("case", ["n_pix", "wl", "levels", "precision", "reserved", "nan_bound", "nan_pix"])
+def test_create_rejects_invalid_arguments_before_device_use(lib, case):
+    pix = np.array([[0.0, 0.0, 1.0], [0.1, 0.0, 0.99]])
+    b = np.array([[-np.inf, np.inf]])
+    kw = {}
+    wl = 2.0
+    if case == "n_pix":
+        pix = np.zeros((0, 3))
+    elif case == "wl":
+        wl = -1.0
+    elif case == "levels":
+        b = np.zeros((17, 2))
+    elif case == "precision":
+        kw["precision"] = 9
+    elif case == "reserved":
+        o = bipp_ss.bipp_ss_default_options()
+        o.reserved[2] = 1
+        h = C.c_void_p()
+        pc = np.ascontiguousarray(pix.T)
+        bc = np.ascontiguousarray(b.T)
+        rc = lib.bipp_ss_create(C.byref(h), 2, pc.ctypes.data_as(C.POINTER(C.c_double)), 2.0, 1,
+                                bc.ctypes.data_as(C.POINTER(C.c_double)), C.byref(o))
+        assert rc == bipp_ss.BIPP_ERR_INVALID_ARG
+        assert "reserved" in bipp_ss.bipp_ss_last_error(None)
+        return
+    elif case == "nan_bound":
+        b = np.array([[np.nan, 1.0]])
+    elif case == "nan_pix":
+        pix = pix.copy()
+        pix[1, 2] = np.nan
+    with pytest.raises(bipp_ss.BippError) as e:
+        bipp_ss.bipp_ss_create(pix, wl, b, **kw)
+    assert e.value.code == bipp_ss.BIPP_ERR_INVALID_ARG
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    assert lib.bipp_ss_collect(None, 3, None, None) == bipp_ss.BIPP_ERR_INVALID_ARG
+    assert lib.bipp_ss_get(None, None) == bipp_ss.BIPP_ERR_INVALID_ARG
+    assert lib.bipp_ss_destroy(None) == bipp_ss.BIPP_OK
+    assert isinstance(bipp_ss.bipp_ss_last_error(None), str)
+
+
+def test_pack_batch_layout_is_column_major():
+    rng = np.random.default_rng(0)
+    st = [rng.normal(size=(3, 3)), rng.normal(size=(2, 3))]
+    V = [rng.normal(size=(3, 3)) + 1j * rng.normal(size=(3, 3)), rng.normal(size=(2, 2)) + 0j]
+    nst, N, stp, Vp = bipp_ss.pack_batch(st, V)
+    assert list(nst) == [3, 2] and N == 3
+    flat_st = stp.reshape(2, -1)
+    flat_V = Vp.reshape(2, -1)
+    for t in range(2):
+        n = nst[t]
+        for i in range(n):
+            for c in range(3):
+                assert flat_st[t, i + c * N] == st[t][i, c]
+            for j in range(n):
+                assert flat_V[t, i + j * N] == V[t][i, j]
+
+
+def test_quantile_level_bounds_host_logic():
+    mu = np.arange(1.0, 13.0)
+    b = bipp_ss.quantile_level_bounds(mu, 4)
+    assert b.shape == (4, 2)
+    assert b[0, 1] == np.inf and b[-1, 0] == -np.inf
+    np.testing.assert_allclose(b[:, 0][:3], [9.5, 6.5, 3.5])
+    np.testing.assert_allclose(b[1:, 1], [9.5, 6.5, 3.5])
