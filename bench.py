@@ -1,0 +1,315 @@
+#!/usr/bin/env python
+"""Benchmark of the standard-synthesis hot path on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One bench step = one whole imaging job of the SKA-Low-like workload: 100 time
+steps of (Gram matrix, generalised eigensolve, selection + levels, synthesis
+of 1024^2 pixels from 512 stations with 64 eigenvectors in 4 levels). The
+metric is synthesized pixel x eigvec x station products per second over the
+whole path. Inputs (positions, 400 MB of visibilities) are resident in HBM
+for `value` and are larger than L2, so every step streams them from DRAM;
+`e2e` repeats the measurement through the host-buffer C ABI with the
+host->device copies and the image read-back inside the timed region.
+
+`--impl reference` times the FP64 CPU oracle (the only other place this
+script runs it) on a bounded sample of the same workload on the host cores.
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "synthesized pixel*eigvec*station products/s"
+UNIT = "products/s"
+
+# FP64 pipe of a B300: 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz (unit count and
+# maximum SM clock); FP32 pipe: 148 x 128 FFMA/clk x 2 x 2.032 GHz.
+SMS = 148
+SM_MAX_GHZ = 2.032
+FP64_PEAK_FLOPS = SMS * 2 * 2 * SM_MAX_GHZ * 1e9
+FP32_PEAK_FLOPS = SMS * 128 * 2 * SM_MAX_GHZ * 1e9
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--n-t", type=int, default=100, help="time steps per imaging job")
+    ap.add_argument("--side", type=int, default=1024, help="image side in pixels")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_2310_09200_b300 import inputs
+    inp = inputs.make_config(1, n_t=args.n_t, n_side=args.side)
+    return inp
+
+
+def config_dict(args, inp, precision):
+    return {
+        "workload": (f"SKA-Low-like standard synthesis: {inp.st_xyz[0].shape[0]} stations (lognormal to 65 km), "
+                     f"{args.side}^2 px in a 20 deg cap, N_eig {inp.n_eig}, {inp.n_level} levels, "
+                     f"{inp.n_t} time steps per job, wl 2 m"),
+        "n_st": int(inp.st_xyz[0].shape[0]), "n_pix": int(inp.n_pix), "n_eig": int(inp.n_eig),
+        "n_level": int(inp.n_level), "n_t": int(inp.n_t), "synthesis": precision,
+        "eigensolve": "fp64 parallel-order Jacobi",
+        "l2": "inputs larger than L2 (visibilities 400 MB per job)",
+    }
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 7:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_sample(inp, bounds, n_sub_side=64):
+    """Oracle on a bounded sample: Gram + eigensolve of one time step plus the
+    synthesis of a strided n_sub_side^2 pixel subset; returns timings and the
+    products/s of one full time step extrapolated linearly in pixels."""
+    import oracle
+    side = int(round(math.sqrt(inp.n_pix)))
+    stride = max(1, side // n_sub_side)
+    sel = (np.arange(0, side, stride)[:, None] * side + np.arange(0, side, stride)[None, :]).ravel()
+    pix = inp.pix[sel]
+    p, V = inp.st_xyz[0], inp.vis[0]
+    t0 = time.perf_counter()
+    G = oracle.gram(p, inp.wl)
+    mu, A, _ = oracle.geneig(V, G)
+    t1 = time.perf_counter()
+    d = mu[: inp.n_eig]
+    lev = oracle.select_levels(d, bounds)
+    oracle.synth_levels(pix, p, inp.wl, A[:, : inp.n_eig], d, lev, bounds.shape[0])
+    t2 = time.perf_counter()
+    t_eig, t_syn = t1 - t0, t2 - t1
+    full_step = t_eig + t_syn * (inp.n_pix / len(sel))
+    prods = inp.n_pix * inp.n_eig * p.shape[0]
+    return {"t_eig_s": t_eig, "t_synth_sub_s": t_syn, "n_sub": int(len(sel)), "full_step_s": full_step,
+            "value": prods / full_step}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        return reference_main(args, ws, rank)
+    return ours_main(args, ws, rank, local)
+
+
+def reference_main(args, ws, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    inp = workload(args)
+    # level bounds from the oracle's own pre-pass over a few steps (no GPU input)
+    pooled = []
+    for t in range(0, inp.n_t, max(1, inp.n_t // 4))[:4]:
+        mu, _, _ = oracle.geneig(inp.vis[t], oracle.gram(inp.st_xyz[t], inp.wl))
+        pooled.extend(mu[: inp.n_eig])
+    from paper_2310_09200_b300.bipp_ss import quantile_level_bounds
+    bounds = quantile_level_bounds(pooled, inp.n_level)
+    samples = []
+    for i in range(args.warmup + args.steps):
+        s = cpu_sample(inp, bounds)
+        if i >= args.warmup:
+            samples.append(s)
+    value = statistics.median(s["value"] for s in samples)
+    full_job_ms = inp.n_t * statistics.median(s["full_step_s"] for s in samples) * 1e3
+    cores = os.cpu_count()
+    sample = (f"1 of {inp.n_t} time steps per bench step: FP64 Gram + Jacobi eigensolve (single thread) of 512 "
+              f"stations, then synthesis of a strided {samples[0]['n_sub']}-pixel subset (OpenMP over pixels); "
+              f"per-step time extrapolated linearly to {inp.n_pix} pixels and to {inp.n_t} steps")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": full_job_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": config_dict(args, inp, "fp64 (oracle)"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def ours_main(args, ws, rank, local):
+    import torch
+
+    from paper_2310_09200_b300 import bipp_ss, build
+    build.build()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    inp = workload(args)
+    n_st = inp.st_xyz[0].shape[0]
+    # level bounds: the library's own parameter-estimation pre-pass on every 10th step
+    bounds, _ = bipp_ss.estimate_level_bounds(inp.st_xyz[::10], inp.vis[::10], inp.wl, inp.n_eig, inp.n_level)
+    nst, N, st, V = bipp_ss.pack_batch(inp.st_xyz, inp.vis)
+    d_st = torch.from_numpy(st).to(f"cuda:{local}")
+    d_V = torch.from_numpy(V).to(f"cuda:{local}")
+    stream = torch.cuda.Stream()
+    ss = bipp_ss.StandardSynthesis(inp.pix, inp.wl, bounds, n_eig=inp.n_eig, precision=args.precision,
+                                   device=local)
+
+    def one_step():
+        bipp_ss.bipp_ss_collect_device(ss.h, nst, d_st, d_V, stream=stream)
+        return ss.timings()
+
+    for _ in range(args.warmup):
+        one_step()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    stage = np.zeros(4)
+    sweeps = 0
+    launches = 0
+    e0.record(stream)
+    for _ in range(args.steps):
+        t = one_step()
+        stage += [t["gram_reduce_ms"], t["eig_ms"], t["select_ms"], t["synth_ms"]]
+        sweeps += t["sweeps_total"]
+        launches += t["launches"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    if dist:
+        dist.barrier()
+    ms_total = e0.elapsed_time(e1)
+    if dist:
+        x = torch.tensor([ms_total], device=f"cuda:{local}")
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        ms_total = float(x.item())
+    ms_step = ms_total / args.steps
+    prods = inp.n_pix * inp.n_eig * n_st * inp.n_t
+    value = prods * ws / (ms_step / 1e3)
+
+    # ---- roofline of the dominant kernel and of the synthesis kernel
+    K = args.steps
+    eig_ms, syn_ms = stage[1] / K, stage[3] / K
+    jac_flops = 20.0 * n_st ** 2 * (n_st - 1) * (sweeps / K)  # Hermitian two-sided rotations + Q, per launch
+    syn_flops = 8.0 * prods  # one complex multiply-add per product
+    roof_jacobi = {"kernel": "k_jacobi", "bound": "alu", "achieved": jac_flops / (eig_ms / 1e3) / 1e12,
+                   "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s", "traffic": None,
+                   "peak_note": "FP64 pipe, 148 SM x 2 DFMA/clk x 2 flop x 2.032 GHz"}
+    roof_jacobi["frac"] = roof_jacobi["achieved"] / roof_jacobi["peak"]
+    roof_synth = {"kernel": "k_synth_f32" if args.precision == "fp32" else "synth_tc", "bound": "alu",
+                  "achieved": syn_flops / (syn_ms / 1e3) / 1e12, "peak": FP32_PEAK_FLOPS / 1e12,
+                  "unit": "TFLOP/s", "traffic": None,
+                  "peak_note": "FP32 pipe, 148 SM x 128 FFMA/clk x 2 flop x 2.032 GHz"}
+    roof_synth["frac"] = roof_synth["achieved"] / roof_synth["peak"]
+    dominant = roof_jacobi if eig_ms >= syn_ms else roof_synth
+
+    # ---- end to end through the host-buffer C ABI (pinned host inputs, images read back)
+    e2e = None
+    if not args.no_e2e:
+        st_h = torch.from_numpy(st).pin_memory()
+        V_h = torch.from_numpy(V).pin_memory()
+        img_h = np.zeros((inp.n_level, inp.n_pix))
+        bipp_ss.bipp_ss_collect_batch_packed(ss.h, nst, N, st_h.data_ptr(), V_h.data_ptr())
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        lib = bipp_ss.load()
+        img_ptr = img_h.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        for _ in range(args.steps):
+            bipp_ss.bipp_ss_collect_batch_packed(ss.h, nst, N, st_h.data_ptr(), V_h.data_ptr())
+            if lib.bipp_ss_get_f64(ss.h, img_ptr) != 0:
+                raise RuntimeError(bipp_ss.bipp_ss_last_error(ss.h))
+        dt = (time.perf_counter() - t0) / args.steps
+        if dist:
+            x = torch.tensor([dt], device=f"cuda:{local}")
+            dist.all_reduce(x, op=dist.ReduceOp.MAX)
+            dt = float(x.item())
+        e2e = {"value": prods * ws / dt, "unit": UNIT, "h2d_bytes_per_step": int(st.nbytes + V.nbytes),
+               "d2h_bytes_per_step": int(img_h.nbytes)}
+    ss.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        s = cpu_sample(inp, bounds)
+        cpu = {"value": s["value"], "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": (f"one time step: FP64 Gram + Jacobi of {n_st} stations (single thread, "
+                          f"{s['t_eig_s']:.1f} s) + synthesis of a strided {s['n_sub']}-pixel subset "
+                          f"(OpenMP, {s['t_synth_sub_s']:.2f} s), extrapolated linearly to {inp.n_pix} pixels")}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+                "config": config_dict(args, inp, args.precision),
+                "stage_ms_per_step": {"gram_chol_reduce": stage[0] / K, "jacobi": eig_ms,
+                                      "select_pack": stage[2] / K, "synthesis": syn_ms},
+                "synthesis_only_value": prods / (syn_ms / 1e3),
+                "roofline": dominant, "roofline_synthesis": roof_synth, "roofline_jacobi": roof_jacobi,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

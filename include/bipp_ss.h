@@ -144,10 +144,11 @@ int bipp_ss_set_images(bipp_ss_t h, const double* img);
 int bipp_ss_last_eigvals(bipp_ss_t h, int32_t n_t_cap, int32_t n_eig_cap, int32_t* n_t_out,
                          int32_t* n_kept, double* mu, int32_t* level);
 
-/* Device time [ms] of the most recent batch per stage:
- * ms[0] Gram + Cholesky + reduction, ms[1] eigensolve, ms[2] select/pack,
- * ms[3] synthesis, ms[4] Jacobi sweeps used (max over steps). */
-int bipp_ss_get_timings(bipp_ss_t h, double* ms5);
+/* Statistics of the most recent batch, measured with CUDA events on the
+ * stream the batch ran on: out[0] Gram + Cholesky + reduction [ms],
+ * out[1] eigensolve [ms], out[2] select/pack [ms], out[3] synthesis [ms],
+ * out[4] Jacobi sweeps summed over the steps, out[5] kernels launched. */
+int bipp_ss_get_timings(bipp_ss_t h, double* out6);
 
 /* Release the handle and its device memory. NULL is accepted. */
 int bipp_ss_destroy(bipp_ss_t h);

@@ -182,6 +182,17 @@ def bipp_ss_collect_batch(h, st_xyz: Sequence[np.ndarray], vis: Sequence[np.ndar
     _check(h, rc)
 
 
+def bipp_ss_collect_batch_packed(h, nst, n_st_max: int, st_addr: int, vis_addr: int, n_eig=None) -> None:
+    """bipp_ss_collect_batch on buffers already in the ABI block layout (e.g.
+    pinned host tensors); st_addr / vis_addr are host addresses."""
+    nst = np.ascontiguousarray(nst, dtype=np.int32)
+    ne = None if n_eig is None else np.ascontiguousarray(n_eig, dtype=np.int32)
+    rc = load().bipp_ss_collect_batch(h, len(nst), int(n_st_max), _ip(nst), None if ne is None else _ip(ne),
+                                      C.cast(C.c_void_p(st_addr), C.POINTER(C.c_double)),
+                                      C.cast(C.c_void_p(vis_addr), C.POINTER(C.c_double)))
+    _check(h, rc)
+
+
 def bipp_ss_collect_device(h, n_st, d_st, d_vis, n_eig=None, stream=None) -> None:
     """Device variant. d_st: torch float64 (T, 3, N) contiguous; d_vis: torch
     complex128 (T, N, N) holding each block column-major (i.e. V[t].T, as
@@ -233,9 +244,10 @@ def bipp_ss_last_eigvals(h, n_t_cap: int, n_eig_cap: int):
 
 
 def bipp_ss_get_timings(h) -> dict:
-    a = np.zeros(5, dtype=np.float64)
+    a = np.zeros(6, dtype=np.float64)
     _check(h, load().bipp_ss_get_timings(h, _dp(a)))
-    return {"gram_reduce_ms": a[0], "eig_ms": a[1], "select_ms": a[2], "synth_ms": a[3], "sweeps": int(a[4])}
+    return {"gram_reduce_ms": a[0], "eig_ms": a[1], "select_ms": a[2], "synth_ms": a[3], "sweeps_total": int(a[4]),
+            "launches": int(a[5])}
 
 
 def bipp_ss_destroy(h) -> None:

@@ -58,7 +58,7 @@ struct bipp_ss {
   TcWorkspace tc{};
   // last batch
   int last_T = 0, last_N = 0, last_K = 0;
-  double timings[5] = {0, 0, 0, 0, 0};
+  double timings[6] = {0, 0, 0, 0, 0, 0};
   cudaEvent_t ev[5] = {};
   std::string err;
 };
@@ -313,7 +313,9 @@ static int run_batch(bipp_ss* h, int n_t, int N, const std::vector<int>& nst_v, 
   CUDA_TRY(h, cudaMemcpy(sweeps.data(), h->d_sweeps, sizeof(int) * n_t, cudaMemcpyDeviceToHost));
   const int tc_status = (h->opt.precision >= BIPP_PREC_SPLIT_BF16) ? tc_read_status(&h->tc) : 0;
   for (int i = 0; i < 4; ++i) h->timings[i] = ms[i];
-  h->timings[4] = *std::max_element(sweeps.begin(), sweeps.end());
+  h->timings[4] = 0;
+  for (int t = 0; t < n_t; ++t) h->timings[4] += sweeps[t];
+  h->timings[5] = gi ? 6 : 9;  // gram, [cholesky], trinv, [2 reduction GEMMs], hermitize, jacobi, select, synthesis
   for (int t = 0; t < n_t; ++t) {
     if (status[t] & kStatusNotPD)
       return fail(h, BIPP_ERR_GRAM_NOT_PD, "step %d: Gram matrix is not positive definite (Cholesky pivot <= 0 or NaN)", t);
@@ -443,10 +445,10 @@ extern "C" int bipp_ss_last_eigvals(bipp_ss_t h, int32_t n_t_cap, int32_t n_eig_
   return BIPP_OK;
 }
 
-extern "C" int bipp_ss_get_timings(bipp_ss_t h, double* ms5) {
+extern "C" int bipp_ss_get_timings(bipp_ss_t h, double* out6) {
   if (!h) return fail(nullptr, BIPP_ERR_INVALID_ARG, "handle is NULL");
-  if (!ms5) return fail(h, BIPP_ERR_INVALID_ARG, "ms5 is NULL");
-  for (int i = 0; i < 5; ++i) ms5[i] = h->timings[i];
+  if (!out6) return fail(h, BIPP_ERR_INVALID_ARG, "out6 is NULL");
+  for (int i = 0; i < 6; ++i) out6[i] = h->timings[i];
   return BIPP_OK;
 }
 
