@@ -150,6 +150,40 @@ int bipp_ss_last_eigvals(bipp_ss_t h, int32_t n_t_cap, int32_t n_eig_cap, int32_
  * out[4] Jacobi sweeps summed over the steps, out[5] kernels launched. */
 int bipp_ss_get_timings(bipp_ss_t h, double* out6);
 
+/* No-allocation variant of one collect() step. The paper has no counterpart:
+ * this entry point exists for callers that may not allocate device memory,
+ * e.g. a real-time pipeline that reserves all of its GPU memory at start-up
+ * and forbids later allocation, or a host framework that owns the device
+ * memory budget. It runs Gram, eigensolve, selection and FP64 synthesis of
+ * one step with every intermediate held in one fixed array of
+ * BIPP_NOALLOC_SCRATCH_BYTES that the library keeps in device memory (every
+ * GPU that loads the library holds it until the process exits); it calls no
+ * cudaMalloc/cudaFree and no allocating library routine.
+ *   d_pix_xyz    n_pix x 3 FP64 unit vectors (device, column-major).
+ *   level_bounds n_level x 2 (host), as in bipp_ss_create.
+ *   n_eig, filter (BIPP_FILTER_*), gram_identity: as in bipp_ss_options.
+ *   d_st_xyz     n_st x 3 FP64 (device); d_vis n_st x n_st complex128 (device).
+ *   d_img        n_pix x n_level FP64 (device): the step's level images are
+ *                ADDED to it (the caller zeroes it before the first step).
+ *   stream       cudaStream_t or NULL; work runs on the current device.
+ *   err_msg      optional buffer of err_len bytes for a message (may be NULL).
+ * Limits: 1 <= n_eig <= n_st <= BIPP_NOALLOC_MAX_STATIONS,
+ * n_eig <= BIPP_NOALLOC_MAX_EIG, 1 <= n_level <= 16; larger sizes return
+ * BIPP_ERR_UNSUPPORTED with a message naming the limit. The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.
+ * Every call shares the one array and the array keeps the last call's
+ * contents (the call resets what must start at zero itself), so calls that
+ * overlap on the same GPU race: serialise them. Returns after the step has
+ * run (one stream synchronisation), with the same error codes as collect(). */
+#define BIPP_NOALLOC_MAX_STATIONS 128
+#define BIPP_NOALLOC_MAX_EIG 128
+#define BIPP_NOALLOC_SCRATCH_BYTES (1536 * 1024)
+int bipp_ss_collect_noalloc(int64_t n_pix, const double* d_pix_xyz, double wl, int32_t n_level,
+                            const double* level_bounds, int32_t n_eig, int32_t filter, int32_t gram_identity,
+                            int32_t n_st, const double* d_st_xyz, const double* d_vis, double* d_img,
+                            void* stream, char* err_msg, int32_t err_len);
+
 /* Release the handle and its device memory. NULL is accepted. */
 int bipp_ss_destroy(bipp_ss_t h);
 

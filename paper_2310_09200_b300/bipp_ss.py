@@ -47,8 +47,11 @@ EXPORTED = [
     "bipp_ss_default_options", "bipp_ss_create", "bipp_ss_collect", "bipp_ss_collect_batch",
     "bipp_ss_collect_device", "bipp_ss_get", "bipp_ss_get_f64", "bipp_ss_get_device_f64", "bipp_ss_reset",
     "bipp_ss_set_images", "bipp_ss_last_eigvals", "bipp_ss_get_timings", "bipp_ss_destroy",
-    "bipp_ss_last_error",
+    "bipp_ss_last_error", "bipp_ss_collect_noalloc",
 ]
+
+BIPP_NOALLOC_MAX_STATIONS = 128
+BIPP_NOALLOC_MAX_EIG = 128
 
 
 class BippError(RuntimeError):
@@ -95,6 +98,8 @@ def load(path: str | None = None):
     L.bipp_ss_destroy.argtypes = [H]
     L.bipp_ss_last_error.argtypes = [H]
     L.bipp_ss_last_error.restype = C.c_char_p
+    L.bipp_ss_collect_noalloc.argtypes = [i64, vp, C.c_double, i32, dp, i32, i32, i32, i32, vp, vp, vp, vp,
+                                          C.c_char_p, i32]
     for name in EXPORTED:
         if name not in ("bipp_ss_default_options", "bipp_ss_last_error"):
             getattr(L, name).restype = C.c_int
@@ -253,6 +258,30 @@ def bipp_ss_get_timings(h) -> dict:
 def bipp_ss_destroy(h) -> None:
     if h:
         load().bipp_ss_destroy(h)
+
+
+def bipp_ss_collect_noalloc(d_pix, wl, level_bounds, n_eig, d_st, d_vis, d_img, filter="lsq",
+                            gram_identity=False, stream=None) -> None:
+    """One collect() step that allocates no device memory, for callers that
+    may not allocate (e.g. a pipeline whose device memory is fixed at
+    start-up). All intermediates live in a fixed array inside the library
+    (at most BIPP_NOALLOC_MAX_STATIONS stations); calls share it, so do not
+    let two calls overlap on one GPU.
+
+    d_pix: torch float64 (3, n_pix) contiguous (column-major n_pix x 3);
+    d_st: torch float64 (3, n_st); d_vis: torch complex128 (n_st, n_st)
+    holding vis.T (column-major); d_img: torch float64 (n_level, n_pix),
+    to which the step's level images are added."""
+    b = np.asarray(level_bounds, dtype=np.float64)
+    bc = np.ascontiguousarray(b.T)
+    msg = C.create_string_buffer(512)
+    sp = None if stream is None else C.c_void_p(stream.cuda_stream)
+    rc = load().bipp_ss_collect_noalloc(int(d_pix.shape[1]), C.c_void_p(d_pix.data_ptr()), float(wl), b.shape[0],
+                                        _dp(bc), int(n_eig), FILTERS[filter] if isinstance(filter, str) else int(filter),
+                                        int(bool(gram_identity)), int(d_st.shape[1]), C.c_void_p(d_st.data_ptr()),
+                                        C.c_void_p(d_vis.data_ptr()), C.c_void_p(d_img.data_ptr()), sp, msg, 512)
+    if rc != BIPP_OK:
+        raise BippError(rc, msg.value.decode())
 
 
 class StandardSynthesis:
