@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--precision", default="fp32")
     ap.add_argument("--n-t", type=int, default=100, help="time steps per imaging job")
     ap.add_argument("--side", type=int, default=1024, help="image side in pixels")
+    ap.add_argument("--n-st", type=int, default=0, help="keep only the first n stations (small profiling cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -63,6 +64,10 @@ def parse():
 def workload(args):
     from paper_2310_09200_b300 import inputs
     inp = inputs.make_config(1, n_t=args.n_t, n_side=args.side)
+    if args.n_st:
+        n = args.n_st
+        inp.st_xyz = [p[:n] for p in inp.st_xyz]
+        inp.vis = [V[:n, :n] for V in inp.vis]
     return inp
 
 
