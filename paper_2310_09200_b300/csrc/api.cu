@@ -293,10 +293,13 @@ static int run_batch(bipp_ss* h, int n_t, int N, const std::vector<int>& nst_v, 
       launch_synth_simt_f32(b, px, h->n_level, h->d_img, s);
       break;
     default: {
-      int rc = launch_synth_tc(b, px, h->n_level, h->d_img, h->opt.precision == BIPP_PREC_SPLIT_FP16, &h->tc, s);
+      const int rc = launch_synth_tc(b, nst_v, neig_v, px, h->n_level, h->d_img,
+                                     h->opt.precision == BIPP_PREC_SPLIT_FP16, &h->tc, s);
       if (rc) {
         cudaStreamSynchronize(s);
-        return fail(h, BIPP_ERR_UNSUPPORTED, "tensor-core synthesis is not available (code %d)", rc);
+        if (rc == -3)
+          return fail(h, BIPP_ERR_UNSUPPORTED, "split precisions support n_eig <= %d per step", kTcMaxEig);
+        return fail(h, BIPP_ERR_CUDA, "tensor-core synthesis launch failed (code %d)", rc);
       }
     }
   }

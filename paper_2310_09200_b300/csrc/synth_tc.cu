@@ -1,15 +1,564 @@
-// synth_tc.cu — tcgen05 synthesis path: not built yet; every launch reports
-// failure so that the split precisions return an error instead of running.
+// synth_tc.cu — fused standard synthesis on the tcgen05 tensor cores.
+//
+// Per time step the synthesis of Eq. standard_synthesis (Algorithm 2,
+// "GEMMEXP") is the real GEMM
+//     [z_r | z_i](r, e) = sum_k A(r, k) B(k, n),
+//     A(r, 2i) = cos th_ri, A(r, 2i+1) = sin th_ri,  th_ri = 2 pi <r, p_i>/wl,
+//     B(2i, 2e) = Re a_ie, B(2i+1, 2e) = Im a_ie, B(2i, 2e+1) = Im a_ie, B(2i+1, 2e+1) = -Re a_ie,
+// so that z_e(r) = sum_i exp(-j th_ri) a_ie, followed by the level reduction
+// I_l(r) += sum_{e in l} d_e |z_e(r)|^2 (Algorithm 1) and the sum over steps.
+//
+// Kernel structure (one persistent CTA per SM, 18 warps):
+//   warps 0-15 (4 warpgroups) generate A for a 128-pixel tile on the fly:
+//              thread = pixel row, warpgroup g = stations 8g..8g+7 of the
+//              stage; exact phase reduction, SFU sincos, split into hi + lo
+//              (BF16 or FP16), written into shared memory in the UMMA K-major
+//              128-byte swizzled layout (one 128-byte row per pixel, 32
+//              stations per stage). They also run the epilogue: tcgen05.ld of
+//              the FP32 accumulator (pixel row = TMEM lane, warpgroup g takes
+//              column blocks g, g+4, ...), |z|^2, weights and levels in
+//              registers, accumulated over all steps and added to the FP64
+//              image once per tile.
+//   warp 16    allocates TMEM (two accumulator buffers) and issues, per
+//              16-wide K slice, three tcgen05.mma: A_hi*B_hi + A_hi*B_lo +
+//              A_lo*B_hi into the FP32 accumulator.
+//   warp 17    streams the pre-packed, pre-swizzled B chunks of the step with
+//              cp.async.bulk into the stage ring.
+// Stage handoff uses mbarriers; every wait is bounded (clock64 budget) and on
+// expiry sets a device error word, drains its own in-flight work, frees TMEM
+// and returns.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <math.h>
+
+#include <algorithm>
+#include <type_traits>
+
+#include "phase.cuh"
 #include "synth_tc.cuh"
 
 namespace bipp {
 
+namespace {
+
+constexpr int kProdWarps = 16;  // 4 warpgroups
+constexpr int kThreads = (kProdWarps + 2) * 32;
+constexpr int kMmaWarp = kProdWarps, kLoadWarp = kProdWarps + 1;
+constexpr int kRows = 128;            // pixels per tile = UMMA M
+constexpr int kStations = 32;         // stations per stage (64 K-elements)
+constexpr int kABytes = kRows * 128;  // one A operand image per stage (hi or lo)
+constexpr int kMaxStages = 4;
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+// ---------------------------------------------------------------- PTX wrappers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t a, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint32_t a, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Bounded wait for the phase of the given parity; false on expiry or abort.
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_test(a, parity)) return true;
+  const long long t0 = clock64();
+  for (;;) {
+    if (mbar_test(a, parity)) return true;
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      *abort_flag = 1;
+      return false;
+    }
+  }
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// UMMA shared-memory descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SBO), version 1, leading offset unused for this layout.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// hi/lo split of two values into packed 16-bit pairs (element 0 in the low half).
+template <bool FP16>
+__device__ __forceinline__ void split2(float x0, float x1, uint32_t* hi, uint32_t* lo) {
+  if constexpr (FP16) {
+    __half2 h = __floats2half2_rn(x0, x1);
+    __half2 l = __floats2half2_rn(x0 - __low2float(h), x1 - __high2float(h));
+    *hi = *reinterpret_cast<uint32_t*>(&h);
+    *lo = *reinterpret_cast<uint32_t*>(&l);
+  } else {
+    __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+    __nv_bfloat162 l = __floats2bfloat162_rn(x0 - __low2float(h), x1 - __high2float(h));
+    *hi = *reinterpret_cast<uint32_t*>(&h);
+    *lo = *reinterpret_cast<uint32_t*>(&l);
+  }
+}
+
+__device__ __forceinline__ void st_shared_v4(uint32_t a, const uint32_t (&w)[4]) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3])
+               : "memory");
+}
+
+template <int MAXL>
+__device__ __forceinline__ void level_add(float (&acc)[MAXL], int lev, float v) {
+#pragma unroll
+  for (int l = 0; l < MAXL; ++l) acc[l] += (lev == l) ? v : 0.0f;
+}
+
+// ---------------------------------------------------------------- the fused kernel
+
+template <int MAXL, bool FP16>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_synth_tc(Batch b, Pixels px, int n_level, double* img, const TcStep* __restrict__ steps,
+               const unsigned char* __restrict__ Bpack, const float* __restrict__ scales, int n_stages,
+               int stage_bytes, int ncols_buf, int* status) {
+  if (*b.flag) return;  // a step of the batch failed: commit nothing
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t bar_fullA[kMaxStages], bar_fullB[kMaxStages], bar_empty[kMaxStages];
+  __shared__ __align__(8) uint64_t bar_accf[2], bar_acce[2], bar_drain;
+  __shared__ uint32_t s_taddr;
+  __shared__ volatile int s_abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kMaxStages; ++s) {
+      mbar_init(smem_u32(&bar_fullA[s]), kProdWarps);
+      mbar_init(smem_u32(&bar_fullB[s]), 1);
+      mbar_init(smem_u32(&bar_empty[s]), 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(smem_u32(&bar_accf[i]), 1);
+      mbar_init(smem_u32(&bar_acce[i]), kProdWarps);
+    }
+    mbar_init(smem_u32(&bar_drain), 1);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fence_async_smem();
+  }
+  if (warp == kMmaWarp) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_taddr)),
+                 "r"(2 * ncols_buf));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr = s_taddr;
+  const uint32_t smem0 = smem_u32(smem);
+  const int n_tiles = (int)((px.n + kRows - 1) / kRows);
+  const int T = b.T, KM = b.k_max, N = b.n_max;
+
+  if (warp < kProdWarps) {
+    // ------------------------------------------------ A producer + epilogue
+    const int row = threadIdx.x & (kRows - 1);
+    const int wg = threadIdx.x >> 7;  // warpgroup: stations 8wg..8wg+7 of a stage, column blocks wg + 4j
+    uint32_t ctr = 0;
+    int unit = 0;
+    int pend_tile = -1, pend_t = -1;
+    float lacc[MAXL];
+#pragma unroll
+    for (int l = 0; l < MAXL; ++l) lacc[l] = 0.0f;
+    bool ok = true;
+
+    auto epilogue = [&](int tile, int t, int u) -> bool {
+      const int bb = u & 1;
+      if (!mbar_wait(smem_u32(&bar_accf[bb]), (uint32_t)((u >> 1) & 1), &s_abort)) return false;
+      tc_fence_after();
+      const TcStep st = steps[t];
+      const int K = b.nkept[t];
+      const float inv2 = FP16 ? 1.0f / (scales[t] * scales[t]) : 1.0f;
+      const uint32_t tbase = taddr + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(bb * ncols_buf);
+      for (int cb = wg; cb < st.ncols / 16; cb += 4) {
+        float v[16];
+        tmem_ld16(tbase + cb * 16, v);
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+          const int e = cb * 8 + p;
+          if (e < K) {
+            const int lev = b.level[(size_t)t * KM + e];
+            if (lev >= 0) {
+              const float w = (float)b.wt[(size_t)t * KM + e] * inv2;
+              level_add<MAXL>(lacc, lev, w * fmaf(v[2 * p], v[2 * p], v[2 * p + 1] * v[2 * p + 1]));
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bar_acce[bb]));
+      if (t == T - 1) {
+        const int64_t r = (int64_t)tile * kRows + row;
+        if (r < px.n)
+          for (int l = 0; l < n_level; ++l)
+            if (lacc[l] != 0.0f) atomicAdd(img + (size_t)l * px.n + r, (double)lacc[l]);
+#pragma unroll
+        for (int l = 0; l < MAXL; ++l) lacc[l] = 0.0f;
+      }
+      return true;
+    };
+
+    for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+      const int64_t r = (int64_t)tile * kRows + row;
+      float rr[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) rr[c] = (r < px.n) ? px.hl[(size_t)c * px.n + r] : 0.0f;
+      for (int t = 0; t < T && ok; ++t) {
+        const int nch = steps[t].n_chunks;
+        const int n = b.nst[t];
+        const float* qv = b.q + (size_t)t * 6 * N;
+        for (int c = 0; c < nch; ++c, ++ctr) {
+          const uint32_t s = ctr % (uint32_t)n_stages, rnd = ctr / (uint32_t)n_stages;
+          if (!mbar_wait(smem_u32(&bar_empty[s]), (rnd & 1) ^ 1, &s_abort)) {
+            ok = false;
+            break;
+          }
+          const uint32_t a_hi = smem0 + s * stage_bytes + row * 128;
+          const uint32_t a_lo = a_hi + kABytes;
+#pragma unroll
+          for (int qp = 2 * wg; qp < 2 * wg + 2; ++qp) {
+            uint32_t hw[4], lw[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const int i = c * kStations + qp * 4 + j;
+              float cs = 0.0f, sn = 0.0f;
+              if (i < n) {
+                float qq[6];
+#pragma unroll
+                for (int k = 0; k < 6; ++k) qq[k] = __ldg(qv + (size_t)k * N + i);
+                sincos_cycles(phase_frac_f32(rr, qq), &sn, &cs);
+              }
+              split2<FP16>(cs, sn, &hw[j], &lw[j]);
+            }
+            const uint32_t phys = (uint32_t)((qp ^ (row & 7)) << 4);
+            st_shared_v4(a_hi + phys, hw);
+            st_shared_v4(a_lo + phys, lw);
+          }
+          fence_async_smem();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(&bar_fullA[s]));
+        }
+        if (!ok) break;
+        if (pend_tile >= 0 && !epilogue(pend_tile, pend_t, unit - 1)) {
+          ok = false;
+          break;
+        }
+        pend_tile = tile;
+        pend_t = t;
+        ++unit;
+      }
+    }
+    if (ok && pend_tile >= 0) ok = epilogue(pend_tile, pend_t, unit - 1);
+    if (!ok) s_abort = 1;
+  } else if (warp == kMmaWarp) {
+    // ------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      uint32_t ctr = 0;
+      int unit = 0;
+      bool ok = true;
+      bool issued = false;
+      for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+        for (int t = 0; t < T && ok; ++t, ++unit) {
+          const TcStep st = steps[t];
+          const int bb = unit & 1;
+          if (!mbar_wait(smem_u32(&bar_acce[bb]), (uint32_t)(((unit >> 1) & 1) ^ 1), &s_abort)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t d = taddr + (uint32_t)(bb * ncols_buf);
+          for (int c = 0; c < st.n_chunks; ++c, ++ctr) {
+            const uint32_t s = ctr % (uint32_t)n_stages, rnd = ctr / (uint32_t)n_stages;
+            if (!mbar_wait(smem_u32(&bar_fullA[s]), rnd & 1, &s_abort) ||
+                !mbar_wait(smem_u32(&bar_fullB[s]), rnd & 1, &s_abort)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t a_hi = smem0 + s * stage_bytes, a_lo = a_hi + kABytes;
+            const uint32_t b_hi = a_hi + 2 * kABytes, b_lo = b_hi + (uint32_t)st.ncols * 128u;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint32_t ko = kk * 32;
+              const uint64_t dah = umma_desc(a_hi + ko), dal = umma_desc(a_lo + ko);
+              const uint64_t dbh = umma_desc(b_hi + ko), dbl = umma_desc(b_lo + ko);
+              umma_f16(d, dah, dbh, st.idesc, (c | kk) != 0);
+              umma_f16(d, dah, dbl, st.idesc, 1);
+              umma_f16(d, dal, dbh, st.idesc, 1);
+            }
+            issued = true;
+            umma_commit(smem_u32(&bar_empty[s]));
+          }
+          if (!ok) break;
+          umma_commit(smem_u32(&bar_accf[bb]));
+        }
+      }
+      if (!ok) {
+        s_abort = 1;
+        if (issued) {  // wait for the MMAs already issued before TMEM is released
+          umma_commit(smem_u32(&bar_drain));
+          const long long t0 = clock64();
+          while (!mbar_test(smem_u32(&bar_drain), 0) && clock64() - t0 < kWaitCycles) {
+          }
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == kLoadWarp) {
+    // ------------------------------------------------ B loader
+    if (lane == 0) {
+      uint32_t ctr = 0;
+      bool ok = true;
+      uint32_t last_round[kMaxStages];
+      bool used[kMaxStages] = {false, false, false, false};
+      for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+        for (int t = 0; t < T && ok; ++t) {
+          const TcStep st = steps[t];
+          const uint32_t bytes = (uint32_t)st.ncols * 256u;
+          for (int c = 0; c < st.n_chunks; ++c, ++ctr) {
+            const uint32_t s = ctr % (uint32_t)n_stages, rnd = ctr / (uint32_t)n_stages;
+            if (!mbar_wait(smem_u32(&bar_empty[s]), (rnd & 1) ^ 1, &s_abort)) {
+              ok = false;
+              break;
+            }
+            const uint32_t bar = smem_u32(&bar_fullB[s]);
+            mbar_arrive_tx(bar, bytes);
+            bulk_g2s(smem0 + s * stage_bytes + 2 * kABytes, Bpack + st.b_off + (long long)c * bytes, bytes, bar);
+            used[s] = true;
+            last_round[s] = rnd;
+          }
+        }
+      }
+      if (!ok) {
+        s_abort = 1;
+        for (int s = 0; s < n_stages; ++s) {  // let the copies already issued land
+          if (!used[s]) continue;
+          const long long t0 = clock64();
+          while (!mbar_test(smem_u32(&bar_fullB[s]), last_round[s] & 1) && clock64() - t0 < kWaitCycles) {
+          }
+        }
+      }
+    }
+    __syncwarp();
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == kMmaWarp) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(2 * ncols_buf));
+  if (threadIdx.x == 0 && s_abort) atomicExch(status, 1);
+}
+
+// ---------------------------------------------------------------- operand packing
+
+// FP16 variant: per-step power-of-two scale so that max |W| * scale <= 2^14.
+__global__ void k_tc_scale(Batch b, float* scales) {
+  const int t = blockIdx.x;
+  const int n = b.nst[t], K = b.nkept[t], KM = b.k_max, N = b.n_max;
+  __shared__ double red[256];
+  double m = 0.0;
+  for (int w = threadIdx.x; w < n * K; w += blockDim.x) {
+    const int i = w % n, e = w / n;
+    const double2 a = b.W64[((size_t)t * KM + e) * N + i];
+    m = fmax(m, fmax(fabs(a.x), fabs(a.y)));
+  }
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double mx = red[0];
+    float s = 1.0f;
+    if (mx > 0.0) s = (float)exp2(floor(log2(16384.0 / mx)));
+    scales[t] = s;
+  }
+}
+
+// B chunk c of step t: rows n < ncols (K-major, 128 bytes = 64 K-elements),
+// hi image then lo image, 16-byte pieces XOR-swizzled by (row & 7).
+template <bool FP16>
+__global__ void k_tc_pack(Batch b, const TcStep* steps, unsigned char* Bpack, const float* scales) {
+  const int t = blockIdx.y, c = blockIdx.x;
+  const TcStep st = steps[t];
+  if (c >= st.n_chunks) return;
+  const int n = b.nst[t], K = b.nkept[t], KM = b.k_max, N = b.n_max;
+  const double scale = FP16 ? (double)scales[t] : 1.0;
+  unsigned char* base = Bpack + st.b_off + (size_t)c * st.ncols * 256;
+  for (int w = threadIdx.x; w < st.ncols * 8; w += blockDim.x) {
+    const int nn = w >> 3, qp = w & 7;
+    const int e = nn >> 1, comp = nn & 1;
+    uint32_t hw[4], lw[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int i = c * kStations + qp * 4 + j;
+      double2 a = make_double2(0.0, 0.0);
+      if (i < n && e < K) a = b.W64[((size_t)t * KM + e) * N + i];
+      const double wr = a.x * scale, wi = a.y * scale;
+      const double v0 = comp ? wi : wr;   // B(2i, n)
+      const double v1 = comp ? -wr : wi;  // B(2i+1, n)
+      if constexpr (FP16) {
+        __half2 h = __floats2half2_rn((float)v0, (float)v1);
+        __half2 l = __floats2half2_rn((float)(v0 - (double)__low2float(h)), (float)(v1 - (double)__high2float(h)));
+        hw[j] = *reinterpret_cast<uint32_t*>(&h);
+        lw[j] = *reinterpret_cast<uint32_t*>(&l);
+      } else {
+        __nv_bfloat162 h = __floats2bfloat162_rn((float)v0, (float)v1);
+        __nv_bfloat162 l =
+            __floats2bfloat162_rn((float)(v0 - (double)__low2float(h)), (float)(v1 - (double)__high2float(h)));
+        hw[j] = *reinterpret_cast<uint32_t*>(&h);
+        lw[j] = *reinterpret_cast<uint32_t*>(&l);
+      }
+    }
+    const size_t off = (size_t)nn * 128 + (size_t)((qp ^ (nn & 7)) << 4);
+    *reinterpret_cast<uint4*>(base + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    *reinterpret_cast<uint4*>(base + (size_t)st.ncols * 128 + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+  }
+}
+
+inline int ncols_for(int k) { return std::max(16, ((2 * k + 15) / 16) * 16); }
+inline int n_chunks_for(int n) { return (n + kStations - 1) / kStations; }
+
+uint32_t make_idesc(int ncols, bool fp16) {
+  const uint32_t fmt = fp16 ? 0u : 1u;  // A/B: 0 = F16, 1 = BF16
+  return (1u << 4)                      // D = F32
+         | (fmt << 7) | (fmt << 10)     // A, B formats; both K-major (bits 15, 16 = 0)
+         | ((uint32_t)(ncols >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
+}
+
+template <typename F>
+void dispatch(int n_level, bool fp16, F&& f) {
+  auto lv = [&](auto FPV) {
+    if (n_level <= 4) f(std::integral_constant<int, 4>{}, FPV);
+    else if (n_level <= 8) f(std::integral_constant<int, 8>{}, FPV);
+    else f(std::integral_constant<int, 16>{}, FPV);
+  };
+  if (fp16) lv(std::true_type{});
+  else lv(std::false_type{});
+}
+
+}  // namespace
+
 int tc_alloc(TcWorkspace* w, int T, int N, int K) {
-  w->cap_T = T; w->cap_N = N; w->cap_K = K;
+  tc_free(w);
+  const int kk = std::min(K, kTcMaxEig);
+  const size_t bytes = (size_t)T * n_chunks_for(N) * ncols_for(kk) * 256;
+  if (cudaMalloc(&w->B, bytes) != cudaSuccess) return -1;
+  w->B_bytes = bytes;
+  if (cudaMalloc(&w->steps, sizeof(TcStep) * T) != cudaSuccess) return -1;
+  if (cudaMalloc(&w->scale, sizeof(float) * T) != cudaSuccess) return -1;
+  if (cudaMalloc(&w->status, sizeof(int)) != cudaSuccess) return -1;
+  w->cap_T = T;
   return 0;
 }
-void tc_free(TcWorkspace* w) { *w = TcWorkspace{}; }
-int tc_read_status(TcWorkspace*) { return 0; }
-int launch_synth_tc(const Batch&, const Pixels&, int, double*, bool, TcWorkspace*, cudaStream_t) { return -1; }
+
+void tc_free(TcWorkspace* w) {
+  if (w->B) cudaFree(w->B);
+  if (w->steps) cudaFree(w->steps);
+  if (w->scale) cudaFree(w->scale);
+  if (w->status) cudaFree(w->status);
+  *w = TcWorkspace{};
+}
+
+int tc_read_status(TcWorkspace* w) {
+  int v = 0;
+  if (!w->status || cudaMemcpy(&v, w->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+  return v;
+}
+
+int launch_synth_tc(const Batch& b, const std::vector<int>& nst, const std::vector<int>& neig, const Pixels& px,
+                    int n_level, double* img, bool fp16, TcWorkspace* w, cudaStream_t s) {
+  const int T = b.T;
+  if (T > w->cap_T) return -2;
+  std::vector<TcStep> st(T);
+  long long off = 0;
+  int ncols_max = 16, max_chunks = 1;
+  for (int t = 0; t < T; ++t) {
+    if (neig[t] > kTcMaxEig) return -3;
+    st[t].b_off = off;
+    st[t].n_chunks = n_chunks_for(nst[t]);
+    st[t].ncols = ncols_for(neig[t]);
+    st[t].idesc = make_idesc(st[t].ncols, fp16);
+    st[t].pad = 0;
+    off += (long long)st[t].n_chunks * st[t].ncols * 256;
+    ncols_max = std::max(ncols_max, st[t].ncols);
+    max_chunks = std::max(max_chunks, st[t].n_chunks);
+  }
+  if ((size_t)off > w->B_bytes) return -4;
+  if (cudaMemcpyAsync(w->steps, st.data(), sizeof(TcStep) * T, cudaMemcpyHostToDevice, s) != cudaSuccess) return -5;
+  if (cudaMemsetAsync(w->status, 0, sizeof(int), s) != cudaSuccess) return -5;
+  if (fp16) k_tc_scale<<<T, 256, 0, s>>>(b, w->scale);
+  if (fp16) k_tc_pack<true><<<dim3(max_chunks, T), 256, 0, s>>>(b, w->steps, w->B, w->scale);
+  else k_tc_pack<false><<<dim3(max_chunks, T), 256, 0, s>>>(b, w->steps, w->B, w->scale);
+
+  int ncols_buf = 32;
+  while (ncols_buf < ncols_max) ncols_buf <<= 1;  // 2 * ncols_buf TMEM columns, a power of two <= 512
+  const int stage_bytes = 2 * kABytes + 2 * ncols_max * 128;
+  const int n_stages = std::min(kMaxStages, (220 * 1024) / stage_bytes);
+  if (n_stages < 2) return -6;
+  const size_t smem = (size_t)n_stages * stage_bytes + 1024;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int n_tiles = (int)((px.n + kRows - 1) / kRows);
+  const int grid = std::min(n_tiles, sms);
+  int rc = 0;
+  dispatch(n_level, fp16, [&](auto L, auto FPV) {
+    constexpr int ML = decltype(L)::value;
+    constexpr bool F16 = decltype(FPV)::value;
+    if (cudaFuncSetAttribute(k_synth_tc<ML, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
+      rc = -7;
+      return;
+    }
+    k_synth_tc<ML, F16><<<grid, kThreads, smem, s>>>(b, px, n_level, img, w->steps, w->B, w->scale, n_stages,
+                                                     stage_bytes, ncols_buf, w->status);
+  });
+  return rc;
+}
 
 }  // namespace bipp

@@ -224,3 +224,74 @@ def test_rank1_source_peak_on_gpu():
             img = ss.get()[:, 0]
         assert int(np.argmax(img)) == j0
         assert abs(img[j0] - n * n) <= 1e-4 * n * n
+
+
+# ---------------------------------------------------------------- tensor-core (split) precisions
+
+@pytest.mark.parametrize("precision", ["split_bf16", "split_fp16"])
+def test_split_config0_end_to_end(cfg0, precision):
+    inp, bounds, want, _, _ = cfg0
+    with bipp_ss.StandardSynthesis(inp.pix, inp.wl, bounds, n_eig=inp.n_eig, precision=precision) as ss:
+        ss.collect_batch(inp.st_xyz, inp.vis)
+        got = ss.get()
+    err = rel_l2_per_level(got, want)
+    assert np.all(err <= TOL[precision]), (precision, err)
+
+
+@pytest.mark.parametrize("precision", ["split_bf16", "split_fp16"])
+def test_split_ragged_batch(precision):
+    """Odd and ragged station counts (partial 32-station chunks), ragged
+    n_eig (N = 2 n_eig padded to 16), 13^2 pixels (a single ragged tile)."""
+    rng = np.random.default_rng(23)
+    base = inputs.make_config(0, n_t=3, n_side=13)
+    st, vis, ne = [], [], []
+    for t, n in enumerate([17, 24, 13]):
+        keep = np.sort(rng.choice(24, n, replace=False))
+        st.append(base.st_xyz[t][keep])
+        vis.append(base.vis[t][np.ix_(keep, keep)])
+        ne.append([9, 24, 5][t])
+    inp = inputs.SSInput("ragged", base.wl, base.pix, st, vis, 24, 3)
+    bounds = np.array([[50.0, np.inf], [0.0, 50.0], [-np.inf, 0.0]])
+    want, _, _ = oracle_images(inp, bounds, n_eig=ne)
+    with bipp_ss.StandardSynthesis(inp.pix, inp.wl, bounds, precision=precision) as ss:
+        ss.collect_batch(st, vis, n_eig=ne)
+        got = ss.get()
+    err = rel_l2_per_level(got, want)
+    assert np.all(err <= TOL[precision]), (precision, err)
+
+
+@pytest.mark.parametrize("precision", ["split_bf16", "split_fp16"])
+def test_split_full_station_count_sampled_pixels(precision):
+    """512 stations, N_eig 64 (N = 128), 4133 pixels (33 tiles, ragged last), 2 steps."""
+    inp = inputs.make_config(1, n_t=2)
+    side = inp.extra["n_side"]
+    sel = (np.arange(0, side, 16)[:, None] * side + np.arange(0, side, 16)[None, :]).ravel()
+    sel = np.concatenate([sel, np.arange(side * side - 37, side * side)])
+    pix = inp.pix[sel]
+    bounds, _ = helpers.oracle_prepass_bounds(inp)
+    want, _, _ = oracle_images(inp, bounds, pix=pix)
+    with bipp_ss.StandardSynthesis(pix, inp.wl, bounds, n_eig=inp.n_eig, precision=precision) as ss:
+        ss.collect_batch(inp.st_xyz, inp.vis)
+        got = ss.get()
+    err = rel_l2_per_level(got, want)
+    assert np.all(err <= TOL[precision]), (precision, err)
+
+
+def test_split_widest_accumulator_and_limit():
+    """N_eig 128 (N = 256: two stages of 96 KB, all 512 TMEM columns) matches
+    the FP64 path; N_eig 129 is rejected on the split path."""
+    inp = inputs.make_config(1, n_t=1, n_side=12)
+    p, V = inp.st_xyz[0][:160], inp.vis[0][:160, :160]
+    b = np.array([[1000.0, np.inf], [-np.inf, 1000.0]])
+    with bipp_ss.StandardSynthesis(inp.pix, inp.wl, b, n_eig=128, precision="fp64") as ss:
+        ss.collect(p, V)
+        want = ss.get()
+    for precision in ("split_bf16", "split_fp16"):
+        with bipp_ss.StandardSynthesis(inp.pix, inp.wl, b, n_eig=128, precision=precision) as ss:
+            ss.collect(p, V)
+            got = ss.get()
+        assert np.all(rel_l2_per_level(got, want) <= TOL[precision]), precision
+    with bipp_ss.StandardSynthesis(inp.pix, inp.wl, b, n_eig=129, precision="split_bf16") as ss:
+        with pytest.raises(bipp_ss.BippError) as e:
+            ss.collect(p, V)
+        assert e.value.code == bipp_ss.BIPP_ERR_UNSUPPORTED
