@@ -150,6 +150,34 @@ int bipp_ss_last_eigvals(bipp_ss_t h, int32_t n_t_cap, int32_t n_eig_cap, int32_
  * out[4] Jacobi sweeps summed over the steps, out[5] kernels launched. */
 int bipp_ss_get_timings(bipp_ss_t h, double* out6);
 
+/* Differentiable synthesis with complex station gains (device pointers,
+ * e.g. PyTorch memory; stream-ordered on `stream`, NULL = default stream;
+ * returns after the work has finished).
+ *   z_te(r) = sum_i conj(g_i exp(j 2 pi <r, p_ti>/wl)) W_t[i,e]       (Sec. 2.1 gains in the
+ *   I_l(r)  = sum_t sum_{e: level[t,e] = l} d[t,e] |z_te(r)|^2         sampling operator, Eq.
+ *                                                                      standard_synthesis, Alg. 1)
+ *   d_pix     n_pix x 3 FP64 unit vectors (column-major).
+ *   d_st_xyz  n_t blocks of n_st x 3 FP64 [m];  d_W: n_t blocks of n_st x n_eig complex128
+ *             (column-major);  d_d: n_t x n_eig FP64 weights (row t contiguous);
+ *   d_level   n_t x n_eig int32 level ids (-1 = dropped);  d_gains: n_st complex128.
+ * bipp_ss_synth_levels_device writes d_img (n_pix x n_level FP64, overwritten).
+ * Arithmetic: exact phase reduction, SFU sincos, FP32 sums.
+ * 1 <= n_eig <= n_st <= 1024, 1 <= n_level <= 16. */
+int bipp_ss_synth_levels_device(int64_t n_pix, const double* d_pix, double wl, int32_t n_t, int32_t n_st,
+                                int32_t n_eig, int32_t n_level, const double* d_st_xyz, const double* d_W,
+                                const double* d_d, const int32_t* d_level, const double* d_gains, double* d_img,
+                                void* stream);
+
+/* Adjoint of bipp_ss_synth_levels_device: given d_grad_img = dL/dI (n_pix x
+ * n_level FP64) of a real loss L, writes the complex gradients (convention
+ * dL/dRe + j dL/dIm) d_grad_W (n_t blocks of n_st x n_eig complex128) and
+ * d_grad_g (n_st complex128). The phase matrix is recomputed, not stored;
+ * the pixel reduction is deterministic (fixed-order two-stage sum). */
+int bipp_ss_synth_adjoint_device(int64_t n_pix, const double* d_pix, double wl, int32_t n_t, int32_t n_st,
+                                 int32_t n_eig, int32_t n_level, const double* d_st_xyz, const double* d_W,
+                                 const double* d_d, const int32_t* d_level, const double* d_gains,
+                                 const double* d_grad_img, double* d_grad_W, double* d_grad_g, void* stream);
+
 /* No-allocation variant of one collect() step. The paper has no counterpart:
  * this entry point exists for callers that may not allocate device memory,
  * e.g. a real-time pipeline that reserves all of its GPU memory at start-up

@@ -47,7 +47,8 @@ EXPORTED = [
     "bipp_ss_default_options", "bipp_ss_create", "bipp_ss_collect", "bipp_ss_collect_batch",
     "bipp_ss_collect_device", "bipp_ss_get", "bipp_ss_get_f64", "bipp_ss_get_device_f64", "bipp_ss_reset",
     "bipp_ss_set_images", "bipp_ss_last_eigvals", "bipp_ss_get_timings", "bipp_ss_destroy",
-    "bipp_ss_last_error", "bipp_ss_collect_noalloc",
+    "bipp_ss_last_error", "bipp_ss_collect_noalloc", "bipp_ss_synth_levels_device",
+    "bipp_ss_synth_adjoint_device",
 ]
 
 BIPP_NOALLOC_MAX_STATIONS = 128
@@ -100,6 +101,9 @@ def load(path: str | None = None):
     L.bipp_ss_last_error.restype = C.c_char_p
     L.bipp_ss_collect_noalloc.argtypes = [i64, vp, C.c_double, i32, dp, i32, i32, i32, i32, vp, vp, vp, vp,
                                           C.c_char_p, i32]
+    L.bipp_ss_synth_levels_device.argtypes = [i64, vp, C.c_double, i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]
+    L.bipp_ss_synth_adjoint_device.argtypes = [i64, vp, C.c_double, i32, i32, i32, i32, vp, vp, vp, vp, vp, vp,
+                                               vp, vp, vp]
     for name in EXPORTED:
         if name not in ("bipp_ss_default_options", "bipp_ss_last_error"):
             getattr(L, name).restype = C.c_int
@@ -282,6 +286,40 @@ def bipp_ss_collect_noalloc(d_pix, wl, level_bounds, n_eig, d_st, d_vis, d_img, 
                                         C.c_void_p(d_vis.data_ptr()), C.c_void_p(d_img.data_ptr()), sp, msg, 512)
     if rc != BIPP_OK:
         raise BippError(rc, msg.value.decode())
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    return None if stream is None else C.c_void_p(stream.cuda_stream)
+
+
+def bipp_ss_synth_levels_device(pix_cm, wl, st_cm, W_cm, d, level, gains, img, stream=None) -> None:
+    """Forward of the differentiable synthesis on torch CUDA tensors in the ABI
+    layout: pix_cm (3, n_pix) f64, st_cm (T, 3, n_st) f64, W_cm (T, n_eig, n_st)
+    c128 (column-major blocks), d (T, n_eig) f64, level (T, n_eig) int32,
+    gains (n_st,) c128, img (n_level, n_pix) f64 output."""
+    T, K, N = W_cm.shape
+    rc = load().bipp_ss_synth_levels_device(int(pix_cm.shape[1]), _ptr(pix_cm), float(wl), T, N, K,
+                                            int(img.shape[0]), _ptr(st_cm), _ptr(W_cm), _ptr(d), _ptr(level),
+                                            _ptr(gains), _ptr(img), _stream_ptr(stream))
+    if rc != BIPP_OK:
+        raise BippError(rc, "synth_levels_device failed")
+
+
+def bipp_ss_synth_adjoint_device(pix_cm, wl, st_cm, W_cm, d, level, gains, grad_img, grad_W_cm, grad_g,
+                                 stream=None) -> None:
+    """Adjoint of bipp_ss_synth_levels_device; grad_img (n_level, n_pix) f64,
+    outputs grad_W_cm (T, n_eig, n_st) c128 and grad_g (n_st,) c128."""
+    T, K, N = W_cm.shape
+    rc = load().bipp_ss_synth_adjoint_device(int(pix_cm.shape[1]), _ptr(pix_cm), float(wl), T, N, K,
+                                             int(grad_img.shape[0]), _ptr(st_cm), _ptr(W_cm), _ptr(d),
+                                             _ptr(level), _ptr(gains), _ptr(grad_img), _ptr(grad_W_cm),
+                                             _ptr(grad_g), _stream_ptr(stream))
+    if rc != BIPP_OK:
+        raise BippError(rc, "synth_adjoint_device failed")
 
 
 class StandardSynthesis:
