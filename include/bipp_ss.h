@@ -79,7 +79,10 @@ typedef struct {
   double jacobi_tol;         /* stop when off(C) <= tol * ||C||_F; default 1e-13 */
   int32_t device;            /* CUDA device ordinal; default -1 = current device */
   int32_t eig_mode;          /* BIPP_EIG_*; default BIPP_EIG_JACOBI64 */
-  int32_t reserved[6];       /* must be zero */
+  int32_t use_graph;         /* 1: capture each batch geometry once in a CUDA graph and replay it; default 1 */
+  int32_t autotune;          /* 1: time the tensor-core kernel's stage count on the first batch of a
+                                geometry and keep the fastest; default 1 */
+  int32_t reserved[4];       /* must be zero */
 } bipp_ss_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -93,6 +96,25 @@ void bipp_ss_default_options(bipp_ss_options* opt);
  * n_pix >= 1, 1 <= n_level <= 16. Images start at zero. */
 int bipp_ss_create(bipp_ss_t* out, int64_t n_pix, const double* pix_xyz, double wl,
                    int32_t n_level, const double* level_bounds, const bipp_ss_options* opt);
+
+/* Create a handle for n_chan frequency channels sharing one pixel grid
+ * (Sec. 2.3: the eigendecomposition is repeated per step and per frequency
+ * band). Channel c has wavelength wl[c] [m], its own level intervals (block c
+ * of level_bounds, each block n_level x 2 as in bipp_ss_create) and its own
+ * level images: get*() returns n_chan consecutive n_pix x n_level blocks.
+ * bipp_ss_create is the n_chan = 1 case. 1 <= n_chan <= 4096. */
+int bipp_ss_create_channels(bipp_ss_t* out, int64_t n_pix, const double* pix_xyz, int32_t n_chan,
+                            const double* wl, int32_t n_level, const double* level_bounds,
+                            const bipp_ss_options* opt);
+
+/* Collect a batch of steps from any channels in one launch sequence: step t
+ * belongs to channel chan[t]; steps must be grouped by channel in
+ * non-decreasing order. Layout and the other arguments as in
+ * bipp_ss_collect_batch (on_device = 0, host buffers) or
+ * bipp_ss_collect_device (on_device = 1, device buffers ordered on stream). */
+int bipp_ss_collect_channels(bipp_ss_t h, int32_t n_t, int32_t n_st_max, const int32_t* chan,
+                             const int32_t* n_st, const int32_t* n_eig, const double* st_xyz, const double* vis,
+                             int32_t on_device, void* stream);
 
 /* Collect one time step (Algorithm 1 "collect"), host buffers.
  *   st_xyz  n_st x 3 station positions [m] (must be finite).
@@ -122,7 +144,8 @@ int bipp_ss_collect_device(bipp_ss_t h, int32_t n_t, int32_t n_st_max, const int
                            const int32_t* n_eig, const double* d_st_xyz, const double* d_vis,
                            void* stream);
 
-/* Copy the accumulated images (n_pix x n_level, column-major) to host memory. */
+/* Copy the accumulated images (n_pix x n_level column-major per channel,
+ * channels consecutive) to host memory. */
 int bipp_ss_get(bipp_ss_t h, float* out);
 int bipp_ss_get_f64(bipp_ss_t h, double* out);
 

@@ -48,7 +48,7 @@ EXPORTED = [
     "bipp_ss_collect_device", "bipp_ss_get", "bipp_ss_get_f64", "bipp_ss_get_device_f64", "bipp_ss_reset",
     "bipp_ss_set_images", "bipp_ss_last_eigvals", "bipp_ss_get_timings", "bipp_ss_destroy",
     "bipp_ss_last_error", "bipp_ss_collect_noalloc", "bipp_ss_synth_levels_device",
-    "bipp_ss_synth_adjoint_device",
+    "bipp_ss_synth_adjoint_device", "bipp_ss_create_channels", "bipp_ss_collect_channels",
 ]
 
 BIPP_NOALLOC_MAX_STATIONS = 128
@@ -65,7 +65,7 @@ class bipp_ss_options(C.Structure):
     _fields_ = [
         ("n_eig", C.c_int32), ("precision", C.c_int32), ("filter", C.c_int32), ("gram_identity", C.c_int32),
         ("max_jacobi_sweeps", C.c_int32), ("jacobi_tol", C.c_double), ("device", C.c_int32),
-        ("eig_mode", C.c_int32), ("reserved", C.c_int32 * 6),
+        ("eig_mode", C.c_int32), ("use_graph", C.c_int32), ("autotune", C.c_int32), ("reserved", C.c_int32 * 4),
     ]
 
 
@@ -102,6 +102,8 @@ def load(path: str | None = None):
     L.bipp_ss_collect_noalloc.argtypes = [i64, vp, C.c_double, i32, dp, i32, i32, i32, i32, vp, vp, vp, vp,
                                           C.c_char_p, i32]
     L.bipp_ss_synth_levels_device.argtypes = [i64, vp, C.c_double, i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]
+    L.bipp_ss_create_channels.argtypes = [C.POINTER(H), i64, dp, i32, dp, i32, dp, C.POINTER(bipp_ss_options)]
+    L.bipp_ss_collect_channels.argtypes = [H, i32, i32, ip, ip, ip, vp, vp, i32, vp]
     L.bipp_ss_synth_adjoint_device.argtypes = [i64, vp, C.c_double, i32, i32, i32, i32, vp, vp, vp, vp, vp, vp,
                                                vp, vp, vp]
     for name in EXPORTED:
@@ -162,6 +164,47 @@ def bipp_ss_create(pix_xyz, wl: float, level_bounds, **opts) -> C.c_void_p:
     return h
 
 
+def bipp_ss_create_channels(pix_xyz, wl, level_bounds, **opts) -> C.c_void_p:
+    """Multi-channel handle. wl: (n_chan,) metres; level_bounds: (n_chan,
+    n_level, 2) rows [lo, hi) per channel."""
+    L = load()
+    pix = _colmajor_xyz(pix_xyz)
+    wl = np.ascontiguousarray(wl, dtype=np.float64)
+    b = np.asarray(level_bounds, dtype=np.float64)
+    if b.ndim != 3 or b.shape[0] != wl.shape[0] or b.shape[2] != 2:
+        raise ValueError("level_bounds must be (n_chan, n_level, 2)")
+    bc = np.ascontiguousarray(np.transpose(b, (0, 2, 1)))  # per channel: column-major n_level x 2
+    o = bipp_ss_default_options(**opts)
+    h = C.c_void_p()
+    rc = L.bipp_ss_create_channels(C.byref(h), pix.shape[1], _dp(pix), wl.shape[0], _dp(wl), b.shape[1], _dp(bc),
+                                   C.byref(o))
+    if rc != BIPP_OK:
+        raise BippError(rc, bipp_ss_last_error(None))
+    return h
+
+
+def bipp_ss_collect_channels(h, chan, st_xyz, vis, n_eig=None) -> None:
+    """Host variant: steps from several channels (chan non-decreasing)."""
+    nst, N, st, V = pack_batch(st_xyz, vis)
+    ch = np.ascontiguousarray(chan, dtype=np.int32)
+    ne = None if n_eig is None else np.ascontiguousarray(n_eig, dtype=np.int32)
+    rc = load().bipp_ss_collect_channels(h, len(nst), N, _ip(ch), _ip(nst), None if ne is None else _ip(ne),
+                                         C.c_void_p(st.ctypes.data), C.c_void_p(V.ctypes.data), 0, None)
+    _check(h, rc)
+
+
+def bipp_ss_collect_channels_device(h, chan, n_st, d_st, d_vis, n_eig=None, stream=None) -> None:
+    """Device variant of bipp_ss_collect_channels (layout as collect_device)."""
+    ch = np.ascontiguousarray(chan, dtype=np.int32)
+    nst = np.ascontiguousarray(n_st, dtype=np.int32)
+    ne = None if n_eig is None else np.ascontiguousarray(n_eig, dtype=np.int32)
+    N = int(d_st.shape[-1])
+    sp = None if stream is None else C.c_void_p(stream.cuda_stream)
+    rc = load().bipp_ss_collect_channels(h, len(nst), N, _ip(ch), _ip(nst), None if ne is None else _ip(ne),
+                                         C.c_void_p(d_st.data_ptr()), C.c_void_p(d_vis.data_ptr()), 1, sp)
+    _check(h, rc)
+
+
 def pack_batch(st_xyz: Sequence[np.ndarray], vis: Sequence[np.ndarray], n_st_max: int | None = None):
     """Ragged steps -> the ABI's block layout (n_t blocks of n_st_max x 3 and
     n_st_max x n_st_max complex128, each column-major)."""
@@ -216,16 +259,19 @@ def bipp_ss_collect_device(h, n_st, d_st, d_vis, n_eig=None, stream=None) -> Non
     _check(h, rc)
 
 
-def bipp_ss_get(h, n_pix: int, n_level: int) -> np.ndarray:
-    out = np.zeros((n_level, n_pix), dtype=np.float32)
+def bipp_ss_get(h, n_pix: int, n_level: int, n_chan: int = 1) -> np.ndarray:
+    """Images as (n_pix, n_level) (one channel) or (n_chan, n_pix, n_level)."""
+    out = np.zeros((n_chan, n_level, n_pix), dtype=np.float32)
     _check(h, load().bipp_ss_get(h, out.ctypes.data_as(C.POINTER(C.c_float))))
-    return out.T
+    out = np.transpose(out, (0, 2, 1))
+    return out[0] if n_chan == 1 else out
 
 
-def bipp_ss_get_f64(h, n_pix: int, n_level: int) -> np.ndarray:
-    out = np.zeros((n_level, n_pix), dtype=np.float64)
+def bipp_ss_get_f64(h, n_pix: int, n_level: int, n_chan: int = 1) -> np.ndarray:
+    out = np.zeros((n_chan, n_level, n_pix), dtype=np.float64)
     _check(h, load().bipp_ss_get_f64(h, _dp(out)))
-    return out.T
+    out = np.transpose(out, (0, 2, 1))
+    return out[0] if n_chan == 1 else out
 
 
 def bipp_ss_get_device_f64(h, d_out, stream=None) -> None:

@@ -256,6 +256,8 @@ cudaError_t prep(Scratch* s, int64_t n_pix, const double* d_pix, double wl, int 
   b.T = T;
   b.n_max = N;
   b.k_max = K;
+  b.wl = nullptr;    // the FP32 synthesis reads station coordinates already divided by wl
+  b.chan = nullptr;  // one channel
   b.W32 = reinterpret_cast<float2*>(take(sizeof(float2) * (size_t)T * N * K));
   b.wt = reinterpret_cast<double*>(take(sizeof(double) * (size_t)T * K));
   b.level = reinterpret_cast<int*>(take(sizeof(int) * (size_t)T * K));

@@ -1,12 +1,15 @@
 // api.cu — the C ABI of libbipp_ss.so (declared in include/bipp_ss.h).
 //
-// A handle is the paper's StandardSynthesis imaging object (Sec. 3.1): it
-// holds the pixel grid, the level intervals and the accumulated images on
-// one device, plus a batch workspace that grows to the largest batch seen.
-// collect() runs Algorithm 1 for one or many steps as a stream-ordered chain
-// of kernels with no host round trip until the final status check; the
-// synthesis kernel reads a device flag and commits nothing if any step of
-// the batch failed.
+// A handle is the paper's StandardSynthesis imaging object (Sec. 3.1),
+// generalised to n_chan frequency channels that share one pixel grid: it
+// holds the pixels, per-channel wavelengths, level intervals and level
+// images on one device, plus a batch workspace that grows to the largest
+// batch seen. collect() runs Algorithm 1 for a batch of steps (any mix of
+// channels, ragged station counts and n_eig) as one stream-ordered chain of
+// kernels with no host round trip until the final status check; the
+// synthesis kernels read a device flag and commit nothing if any step of the
+// batch failed. A batch geometry seen a second time is captured into a CUDA
+// graph and replayed from then on.
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -22,17 +25,36 @@
 
 using namespace bipp;
 
+namespace {
+
+// Everything that determines the kernels and arguments of a batch.
+struct GraphKey {
+  int T = 0, N = 0, K = 0;
+  const void* st = nullptr;
+  const void* vis = nullptr;
+  cudaStream_t stream = nullptr;
+  std::vector<int> nst, neig, chan;
+  int n_stages = 0;
+  bool operator==(const GraphKey& o) const {
+    return T == o.T && N == o.N && K == o.K && st == o.st && vis == o.vis && stream == o.stream && nst == o.nst &&
+           neig == o.neig && chan == o.chan && n_stages == o.n_stages;
+  }
+};
+
+}  // namespace
+
 struct bipp_ss {
   int device = 0;
   cudaStream_t stream = nullptr;
   int64_t n_pix = 0;
   int n_level = 0;
-  double wl = 0.0;
+  int n_chan = 1;
+  std::vector<double> wl;      // [n_chan]
   bipp_ss_options opt{};
   double* d_pix = nullptr;     // [3][n_pix]
   float* d_pix_hl = nullptr;   // [6][n_pix]
-  double* d_img = nullptr;     // [n_level][n_pix]
-  double* d_bounds = nullptr;  // [2][n_level]
+  double* d_img = nullptr;     // [n_chan][n_level][n_pix]
+  double* d_bounds = nullptr;  // [n_chan][2][n_level]
   // batch workspace
   int cap_T = 0, cap_N = 0, cap_K = 0;
   double* d_st = nullptr;
@@ -54,8 +76,20 @@ struct bipp_ss {
   float* d_q = nullptr;
   int* d_nst = nullptr;
   int* d_neig = nullptr;
+  int* d_chan = nullptr;
+  double* d_wl = nullptr;
   int* d_flag = nullptr;
+  // pinned host staging of the per-step tables (sources of graph memcpy nodes)
+  int* h_nst = nullptr;
+  int* h_neig = nullptr;
+  int* h_chan = nullptr;
+  double* h_wl = nullptr;
   TcWorkspace tc{};
+  // graph cache: the last geometry seen, and the captured graph of it
+  GraphKey last_key;
+  bool have_key = false;
+  GraphKey graph_key;
+  cudaGraphExec_t graph = nullptr;
   // last batch
   int last_T = 0, last_N = 0, last_K = 0;
   double timings[6] = {0, 0, 0, 0, 0, 0};
@@ -91,15 +125,26 @@ static cudaError_t dalloc(T** p, size_t count) {
   return cudaMalloc((void**)p, count * sizeof(T));
 }
 
+static void drop_graph(bipp_ss* h) {
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  h->graph = nullptr;
+  h->have_key = false;
+}
+
 static void free_batch(bipp_ss* h) {
+  drop_graph(h);
   void* ptrs[] = {h->d_st, h->d_vis, h->d_G, h->d_Linv, h->d_X, h->d_C, h->d_Q, h->d_mu, h->d_status,
                   h->d_sweeps, h->d_nkept, h->d_sel_mu, h->d_level, h->d_wt, h->d_W64, h->d_W32, h->d_q,
-                  h->d_nst, h->d_neig, h->d_flag};
+                  h->d_nst, h->d_neig, h->d_chan, h->d_wl, h->d_flag};
   for (void* p : ptrs) if (p) cudaFree(p);
+  void* hp[] = {h->h_nst, h->h_neig, h->h_chan, h->h_wl};
+  for (void* p : hp) if (p) cudaFreeHost(p);
   h->d_st = nullptr; h->d_vis = nullptr; h->d_G = nullptr; h->d_Linv = nullptr; h->d_X = nullptr;
   h->d_C = nullptr; h->d_Q = nullptr; h->d_mu = nullptr; h->d_status = nullptr; h->d_sweeps = nullptr;
   h->d_nkept = nullptr; h->d_sel_mu = nullptr; h->d_level = nullptr; h->d_wt = nullptr; h->d_W64 = nullptr;
-  h->d_W32 = nullptr; h->d_q = nullptr; h->d_nst = nullptr; h->d_neig = nullptr; h->d_flag = nullptr;
+  h->d_W32 = nullptr; h->d_q = nullptr; h->d_nst = nullptr; h->d_neig = nullptr; h->d_chan = nullptr;
+  h->d_wl = nullptr; h->d_flag = nullptr;
+  h->h_nst = nullptr; h->h_neig = nullptr; h->h_chan = nullptr; h->h_wl = nullptr;
   tc_free(&h->tc);
   h->cap_T = h->cap_N = h->cap_K = 0;
 }
@@ -130,7 +175,13 @@ static int ensure_batch(bipp_ss* h, int T, int N, int K) {
   CUDA_TRY(h, dalloc(&h->d_q, (size_t)T * 6 * N));
   CUDA_TRY(h, dalloc(&h->d_nst, (size_t)T));
   CUDA_TRY(h, dalloc(&h->d_neig, (size_t)T));
+  CUDA_TRY(h, dalloc(&h->d_chan, (size_t)T));
+  CUDA_TRY(h, dalloc(&h->d_wl, (size_t)T));
   CUDA_TRY(h, dalloc(&h->d_flag, 1));
+  CUDA_TRY(h, cudaMallocHost(&h->h_nst, sizeof(int) * T));
+  CUDA_TRY(h, cudaMallocHost(&h->h_neig, sizeof(int) * T));
+  CUDA_TRY(h, cudaMallocHost(&h->h_chan, sizeof(int) * T));
+  CUDA_TRY(h, cudaMallocHost(&h->h_wl, sizeof(double) * T));
   if (tc_alloc(&h->tc, T, N, K)) return fail(h, BIPP_ERR_OUT_OF_MEMORY, "tensor-core workspace allocation failed");
   h->cap_T = T;
   h->cap_N = N;
@@ -141,7 +192,7 @@ static int ensure_batch(bipp_ss* h, int T, int N, int K) {
 static Batch make_batch(bipp_ss* h, int T, int N, int K, const double* st, const double2* vis) {
   Batch b;
   b.T = T; b.n_max = N; b.k_max = K;
-  b.nst = h->d_nst; b.neig = h->d_neig;
+  b.nst = h->d_nst; b.neig = h->d_neig; b.wl = h->d_wl; b.chan = h->d_chan;
   b.st = st; b.vis = vis;
   b.G = h->d_G; b.Linv = h->d_Linv; b.X = h->d_X; b.C = h->d_C; b.Q = h->d_Q; b.mu = h->d_mu;
   b.status = h->d_status; b.sweeps = h->d_sweeps; b.nkept = h->d_nkept;
@@ -161,6 +212,8 @@ extern "C" void bipp_ss_default_options(bipp_ss_options* opt) {
   opt->jacobi_tol = 1e-13;
   opt->device = -1;
   opt->eig_mode = BIPP_EIG_JACOBI64;
+  opt->use_graph = 1;
+  opt->autotune = 1;
 }
 
 extern "C" int bipp_ss_destroy(bipp_ss_t h) {
@@ -178,17 +231,21 @@ extern "C" int bipp_ss_destroy(bipp_ss_t h) {
   return BIPP_OK;
 }
 
-extern "C" int bipp_ss_create(bipp_ss_t* out, int64_t n_pix, const double* pix_xyz, double wl, int32_t n_level,
-                              const double* level_bounds, const bipp_ss_options* opt) {
+extern "C" int bipp_ss_create_channels(bipp_ss_t* out, int64_t n_pix, const double* pix_xyz, int32_t n_chan,
+                                       const double* wl, int32_t n_level, const double* level_bounds,
+                                       const bipp_ss_options* opt) {
   if (!out) return fail(nullptr, BIPP_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (n_pix < 1 || !pix_xyz) return fail(nullptr, BIPP_ERR_INVALID_ARG, "need n_pix >= 1 and pix_xyz");
-  if (!(wl > 0.0) || !isfinite(wl)) return fail(nullptr, BIPP_ERR_INVALID_ARG, "wavelength must be finite and > 0");
+  if (n_chan < 1 || n_chan > 4096 || !wl) return fail(nullptr, BIPP_ERR_INVALID_ARG, "need 1 <= n_chan <= 4096 and wl");
+  for (int c = 0; c < n_chan; ++c)
+    if (!(wl[c] > 0.0) || !isfinite(wl[c]))
+      return fail(nullptr, BIPP_ERR_INVALID_ARG, "wavelength of channel %d must be finite and > 0", c);
   if (n_level < 1 || n_level > kMaxLevels || !level_bounds)
     return fail(nullptr, BIPP_ERR_INVALID_ARG, "need 1 <= n_level <= %d and level_bounds", kMaxLevels);
   bipp_ss_options o;
   if (opt) o = *opt; else bipp_ss_default_options(&o);
-  for (int i = 0; i < 6; ++i)
+  for (int i = 0; i < 4; ++i)
     if (o.reserved[i]) return fail(nullptr, BIPP_ERR_INVALID_ARG, "reserved option fields must be zero");
   if (o.precision < BIPP_PREC_FP64 || o.precision > BIPP_PREC_SPLIT_FP16)
     return fail(nullptr, BIPP_ERR_INVALID_ARG, "unknown precision %d", o.precision);
@@ -198,18 +255,19 @@ extern "C" int bipp_ss_create(bipp_ss_t* out, int64_t n_pix, const double* pix_x
     return fail(nullptr, BIPP_ERR_INVALID_ARG, "unknown eig_mode %d", o.eig_mode);
   if (o.n_eig < 0 || o.max_jacobi_sweeps < 1 || !(o.jacobi_tol > 0.0))
     return fail(nullptr, BIPP_ERR_INVALID_ARG, "bad n_eig / max_jacobi_sweeps / jacobi_tol");
-  for (int l = 0; l < n_level; ++l)
-    if (isnan(level_bounds[l]) || isnan(level_bounds[n_level + l]))
-      return fail(nullptr, BIPP_ERR_INVALID_ARG, "level bound %d is NaN", l);
+  for (int64_t i = 0; i < (int64_t)2 * n_level * n_chan; ++i)
+    if (isnan(level_bounds[i])) return fail(nullptr, BIPP_ERR_INVALID_ARG, "level bound %lld is NaN", (long long)i);
   for (int64_t i = 0; i < 3 * n_pix; ++i)
     if (!isfinite(pix_xyz[i]))
       return fail(nullptr, BIPP_ERR_INVALID_ARG, "pixel coordinate %lld is not finite", (long long)i);
 
+  (void)cudaGetLastError();  // errors of earlier, unrelated calls are not ours to report
   bipp_ss* h = new bipp_ss();
   h->opt = o;
   h->n_pix = n_pix;
   h->n_level = n_level;
-  h->wl = wl;
+  h->n_chan = n_chan;
+  h->wl.assign(wl, wl + n_chan);
   if (o.device >= 0 && cudaSetDevice(o.device) != cudaSuccess) {
     delete h;
     return fail(nullptr, BIPP_ERR_CUDA, "cudaSetDevice(%d) failed", o.device);
@@ -223,19 +281,21 @@ extern "C" int bipp_ss_create(bipp_ss_t* out, int64_t n_pix, const double* pix_x
     bipp_ss_destroy(h);
     return code;
   };
+  const size_t n_img = (size_t)n_chan * n_level * n_pix;
   cudaError_t e;
   if ((e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)) != cudaSuccess) return bail(BIPP_ERR_CUDA, "stream", e);
   for (auto& ev : h->ev)
     if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(BIPP_ERR_CUDA, "event", e);
   if ((e = dalloc(&h->d_pix, (size_t)3 * n_pix)) != cudaSuccess) return bail(BIPP_ERR_OUT_OF_MEMORY, "pixels", e);
   if ((e = dalloc(&h->d_pix_hl, (size_t)6 * n_pix)) != cudaSuccess) return bail(BIPP_ERR_OUT_OF_MEMORY, "pixels", e);
-  if ((e = dalloc(&h->d_img, (size_t)n_level * n_pix)) != cudaSuccess) return bail(BIPP_ERR_OUT_OF_MEMORY, "images", e);
-  if ((e = dalloc(&h->d_bounds, (size_t)2 * n_level)) != cudaSuccess) return bail(BIPP_ERR_OUT_OF_MEMORY, "bounds", e);
+  if ((e = dalloc(&h->d_img, n_img)) != cudaSuccess) return bail(BIPP_ERR_OUT_OF_MEMORY, "images", e);
+  if ((e = dalloc(&h->d_bounds, (size_t)2 * n_level * n_chan)) != cudaSuccess) return bail(BIPP_ERR_OUT_OF_MEMORY, "bounds", e);
   if ((e = cudaMemcpy(h->d_pix, pix_xyz, sizeof(double) * 3 * n_pix, cudaMemcpyHostToDevice)) != cudaSuccess)
     return bail(BIPP_ERR_CUDA, "pixel upload", e);
-  if ((e = cudaMemcpy(h->d_bounds, level_bounds, sizeof(double) * 2 * n_level, cudaMemcpyHostToDevice)) != cudaSuccess)
+  if ((e = cudaMemcpy(h->d_bounds, level_bounds, sizeof(double) * 2 * n_level * n_chan, cudaMemcpyHostToDevice)) !=
+      cudaSuccess)
     return bail(BIPP_ERR_CUDA, "bounds upload", e);
-  if ((e = cudaMemset(h->d_img, 0, sizeof(double) * n_level * n_pix)) != cudaSuccess) return bail(BIPP_ERR_CUDA, "memset", e);
+  if ((e = cudaMemset(h->d_img, 0, sizeof(double) * n_img)) != cudaSuccess) return bail(BIPP_ERR_CUDA, "memset", e);
   launch_pixel_split(h->d_pix, h->d_pix_hl, n_pix, h->stream);
   if ((e = cudaGetLastError()) != cudaSuccess) return bail(BIPP_ERR_CUDA, "pixel split launch", e);
   if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(BIPP_ERR_CUDA, "pixel split", e);
@@ -243,15 +303,22 @@ extern "C" int bipp_ss_create(bipp_ss_t* out, int64_t n_pix, const double* pix_x
   return BIPP_OK;
 }
 
+extern "C" int bipp_ss_create(bipp_ss_t* out, int64_t n_pix, const double* pix_xyz, double wl, int32_t n_level,
+                              const double* level_bounds, const bipp_ss_options* opt) {
+  return bipp_ss_create_channels(out, n_pix, pix_xyz, 1, &wl, n_level, level_bounds, opt);
+}
+
 // Validate the ragged batch description; returns K_max or a negative code.
-static int check_sizes(bipp_ss* h, int n_t, int n_st_max, const int32_t* n_st, const int32_t* n_eig,
-                       std::vector<int>& nst_v, std::vector<int>& neig_v) {
+static int check_sizes(bipp_ss* h, int n_t, int n_st_max, const int32_t* chan, const int32_t* n_st,
+                       const int32_t* n_eig, std::vector<int>& nst_v, std::vector<int>& neig_v,
+                       std::vector<int>& chan_v) {
   if (n_t < 1) return fail(h, BIPP_ERR_INVALID_ARG, "n_t must be >= 1");
   if (n_st_max < 1 || n_st_max > kMaxStations)
     return fail(h, BIPP_ERR_UNSUPPORTED, "n_st_max must be in [1, %d]", kMaxStations);
   if (!n_st) return fail(h, BIPP_ERR_INVALID_ARG, "n_st is NULL");
   nst_v.resize(n_t);
   neig_v.resize(n_t);
+  chan_v.resize(n_t);
   int kmax = 1;
   for (int t = 0; t < n_t; ++t) {
     const int n = n_st[t];
@@ -259,66 +326,148 @@ static int check_sizes(bipp_ss* h, int n_t, int n_st_max, const int32_t* n_st, c
     const int k = n_eig ? n_eig[t] : (h->opt.n_eig > 0 ? h->opt.n_eig : n);
     if (k < 1) return fail(h, BIPP_ERR_INVALID_ARG, "step %d: n_eig=%d must be >= 1", t, k);
     if (k > n) return fail(h, BIPP_ERR_UNSUPPORTED, "step %d: n_eig=%d exceeds n_st=%d", t, k, n);
+    const int c = chan ? chan[t] : 0;
+    if (c < 0 || c >= h->n_chan) return fail(h, BIPP_ERR_INVALID_ARG, "step %d: channel %d outside [0, %d)", t, c, h->n_chan);
+    if (t > 0 && c < chan_v[t - 1])
+      return fail(h, BIPP_ERR_INVALID_ARG, "steps must be grouped by channel in non-decreasing order (step %d)", t);
+    if (h->opt.precision >= BIPP_PREC_SPLIT_BF16 && k > kTcMaxEig)
+      return fail(h, BIPP_ERR_UNSUPPORTED, "step %d: split precisions support n_eig <= %d", t, kTcMaxEig);
     nst_v[t] = n;
     neig_v[t] = k;
+    chan_v[t] = c;
     kmax = std::max(kmax, k);
   }
   return kmax;
 }
 
-static int run_batch(bipp_ss* h, int n_t, int N, const std::vector<int>& nst_v, const std::vector<int>& neig_v,
-                     int K, const double* d_st, const double2* d_vis, cudaStream_t s) {
-  CUDA_TRY(h, cudaMemcpyAsync(h->d_nst, nst_v.data(), sizeof(int) * n_t, cudaMemcpyHostToDevice, s));
-  CUDA_TRY(h, cudaMemcpyAsync(h->d_neig, neig_v.data(), sizeof(int) * n_t, cudaMemcpyHostToDevice, s));
-  CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int) * n_t, s));
-  CUDA_TRY(h, cudaMemsetAsync(h->d_sweeps, 0, sizeof(int) * n_t, s));
+// Stage-timing events: recorded as external event nodes when captured, so
+// that they are also recorded when the graph is replayed.
+static cudaError_t record(cudaEvent_t ev, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(s, &cs);
+  if (e != cudaSuccess) return e;
+  return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal)
+                                             : cudaEventRecord(ev, s);
+}
+
+// Everything between the per-step table upload and the synthesis: stream
+// ordered, no host synchronisation, so it can be captured into a graph.
+static int enqueue_batch(bipp_ss* h, const Batch& b, const TcPlan& plan, cudaStream_t s) {
+  const int T = b.T;
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_nst, h->h_nst, sizeof(int) * T, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_neig, h->h_neig, sizeof(int) * T, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_chan, h->h_chan, sizeof(int) * T, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_wl, h->h_wl, sizeof(double) * T, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int) * T, s));
+  CUDA_TRY(h, cudaMemsetAsync(h->d_sweeps, 0, sizeof(int) * T, s));
   CUDA_TRY(h, cudaMemsetAsync(h->d_flag, 0, sizeof(int), s));
-  Batch b = make_batch(h, n_t, N, K, d_st, d_vis);
   const int gi = h->opt.gram_identity;
-  CUDA_TRY(h, cudaEventRecord(h->ev[0], s));
-  launch_gram(b, h->wl, gi, s);
+  CUDA_TRY(h, record(h->ev[0], s));
+  launch_gram(b, gi, s);
   launch_cholesky(b, gi, s);
   launch_reduce(b, gi, s);
-  CUDA_TRY(h, cudaEventRecord(h->ev[1], s));
+  CUDA_TRY(h, record(h->ev[1], s));
   launch_jacobi(b, h->opt.jacobi_tol, h->opt.max_jacobi_sweeps, s);
-  CUDA_TRY(h, cudaEventRecord(h->ev[2], s));
-  launch_select(b, h->wl, h->n_level, h->d_bounds, h->opt.filter, s);
-  CUDA_TRY(h, cudaEventRecord(h->ev[3], s));
+  CUDA_TRY(h, record(h->ev[2], s));
+  launch_select(b, h->n_level, h->d_bounds, h->opt.filter, s);
+  const bool tc = h->opt.precision >= BIPP_PREC_SPLIT_BF16;
+  if (tc && tc_enqueue_pack(b, plan, &h->tc, s)) return fail(h, BIPP_ERR_CUDA, "operand packing launch failed");
+  CUDA_TRY(h, record(h->ev[3], s));
   Pixels px{h->n_pix, h->d_pix, h->d_pix_hl};
   switch (h->opt.precision) {
-    case BIPP_PREC_FP64:
-      launch_synth_simt_f64(b, px, h->wl, h->n_level, h->d_img, s);
-      break;
-    case BIPP_PREC_FP32:
-      launch_synth_simt_f32(b, px, h->n_level, h->d_img, s);
-      break;
-    default: {
-      const int rc = launch_synth_tc(b, nst_v, neig_v, px, h->n_level, h->d_img,
-                                     h->opt.precision == BIPP_PREC_SPLIT_FP16, &h->tc, s);
-      if (rc) {
-        cudaStreamSynchronize(s);
-        if (rc == -3)
-          return fail(h, BIPP_ERR_UNSUPPORTED, "split precisions support n_eig <= %d per step", kTcMaxEig);
-        return fail(h, BIPP_ERR_CUDA, "tensor-core synthesis launch failed (code %d)", rc);
-      }
-    }
+    case BIPP_PREC_FP64: launch_synth_simt_f64(b, px, h->n_level, h->d_img, s); break;
+    case BIPP_PREC_FP32: launch_synth_simt_f32(b, px, h->n_level, h->d_img, s); break;
+    default:
+      if (tc_enqueue_synth(b, px, h->n_level, h->d_img, plan, &h->tc, s))
+        return fail(h, BIPP_ERR_CUDA, "tensor-core synthesis launch failed");
   }
   CUDA_TRY(h, cudaGetLastError());
-  CUDA_TRY(h, cudaEventRecord(h->ev[4], s));
+  CUDA_TRY(h, record(h->ev[4], s));
+  return BIPP_OK;
+}
+
+static int run_batch(bipp_ss* h, int n_t, int N, const std::vector<int>& nst_v, const std::vector<int>& neig_v,
+                     const std::vector<int>& chan_v, int K, const double* d_st, const double2* d_vis,
+                     cudaStream_t s) {
+  (void)cudaGetLastError();  // errors of earlier, unrelated calls are not ours to report
+  for (int t = 0; t < n_t; ++t) {
+    h->h_nst[t] = nst_v[t];
+    h->h_neig[t] = neig_v[t];
+    h->h_chan[t] = chan_v[t];
+    h->h_wl[t] = h->wl[chan_v[t]];
+  }
+  Batch b = make_batch(h, n_t, N, K, d_st, d_vis);
+  const bool tc = h->opt.precision >= BIPP_PREC_SPLIT_BF16;
+  TcPlan plan;
+  if (tc) {
+    const int rc = tc_prepare(nst_v, neig_v, h->opt.precision == BIPP_PREC_SPLIT_FP16, &h->tc, &plan);
+    if (rc == -3) return fail(h, BIPP_ERR_UNSUPPORTED, "split precisions support n_eig <= %d per step", kTcMaxEig);
+    if (rc) return fail(h, BIPP_ERR_CUDA, "tensor-core plan failed (%d)", rc);
+  }
+  GraphKey key;
+  key.T = n_t; key.N = N; key.K = K; key.st = d_st; key.vis = d_vis; key.stream = s;
+  key.nst = nst_v; key.neig = neig_v; key.chan = chan_v; key.n_stages = tc ? plan.n_stages : 0;
+
+  if (tc && h->opt.autotune && !plan.tuned) {
+    // first batch of this accumulator width: run up to the packing, tune, then synthesise
+    Batch bb = b;
+    int rc = enqueue_batch(h, bb, plan, s);  // ... runs the synthesis with the default plan too
+    if (rc) return rc;
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+    const int chan_sub = chan_v[std::min(n_t, 4) - 1] + 1;
+    Pixels px{h->n_pix, h->d_pix, h->d_pix_hl};
+    if (tc_autotune(b, px, h->n_level, chan_sub, &plan, &h->tc, s)) {
+      cudaGetLastError();
+      // keep the default stage count; tuning failure is not a collect failure
+    }
+  } else if (h->opt.use_graph && h->graph && key == h->graph_key) {
+    CUDA_TRY(h, cudaGraphLaunch(h->graph, s));
+  } else if (h->opt.use_graph && h->have_key && key == h->last_key) {
+    // second batch of the same geometry: capture once, replay from now on
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(h, cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+    const int rc = enqueue_batch(h, b, plan, s);
+    const cudaError_t ce = cudaStreamEndCapture(s, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (ce != cudaSuccess) return fail(h, BIPP_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+    const cudaError_t ie = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+      h->graph = nullptr;
+      return fail(h, BIPP_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ie));
+    }
+    h->graph_key = key;
+    CUDA_TRY(h, cudaGraphLaunch(h->graph, s));
+  } else {
+    const int rc = enqueue_batch(h, b, plan, s);
+    if (rc) return rc;
+  }
+  h->last_key = key;
+  h->have_key = true;
   CUDA_TRY(h, cudaStreamSynchronize(s));
   h->last_T = n_t;
   h->last_N = N;
   h->last_K = K;
   float ms[4] = {0, 0, 0, 0};
-  for (int i = 0; i < 4; ++i) cudaEventElapsedTime(&ms[i], h->ev[i], h->ev[i + 1]);
+  for (int i = 0; i < 4; ++i)
+    if (cudaEventElapsedTime(&ms[i], h->ev[i], h->ev[i + 1]) != cudaSuccess) {
+      ms[i] = NAN;
+      (void)cudaGetLastError();  // a missing timing is not a collect failure
+    }
   std::vector<int> status(n_t), sweeps(n_t);
   CUDA_TRY(h, cudaMemcpy(status.data(), h->d_status, sizeof(int) * n_t, cudaMemcpyDeviceToHost));
   CUDA_TRY(h, cudaMemcpy(sweeps.data(), h->d_sweeps, sizeof(int) * n_t, cudaMemcpyDeviceToHost));
-  const int tc_status = (h->opt.precision >= BIPP_PREC_SPLIT_BF16) ? tc_read_status(&h->tc) : 0;
+  const int tc_status = tc ? tc_read_status(&h->tc) : 0;
   for (int i = 0; i < 4; ++i) h->timings[i] = ms[i];
   h->timings[4] = 0;
   for (int t = 0; t < n_t; ++t) h->timings[4] += sweeps[t];
-  h->timings[5] = gi ? 6 : 9;  // gram, [cholesky], trinv, [2 reduction GEMMs], hermitize, jacobi, select, synthesis
+  // gram, [cholesky], trinv, [2 reduction GEMMs], hermitize, jacobi, select, [scale], [pack], synthesis
+  h->timings[5] = (h->opt.gram_identity ? 6 : 9) + (tc ? 1 + (h->opt.precision == BIPP_PREC_SPLIT_FP16) : 0);
   for (int t = 0; t < n_t; ++t) {
     if (status[t] & kStatusNotPD)
       return fail(h, BIPP_ERR_GRAM_NOT_PD, "step %d: Gram matrix is not positive definite (Cholesky pivot <= 0 or NaN)", t);
@@ -330,25 +479,45 @@ static int run_batch(bipp_ss* h, int n_t, int N, const std::vector<int>& nst_v, 
   return BIPP_OK;
 }
 
-extern "C" int bipp_ss_collect_batch(bipp_ss_t h, int32_t n_t, int32_t n_st_max, const int32_t* n_st,
-                                     const int32_t* n_eig, const double* st_xyz, const double* vis) {
+static int collect_common(bipp_ss_t h, int32_t n_t, int32_t n_st_max, const int32_t* chan, const int32_t* n_st,
+                          const int32_t* n_eig, const double* st_xyz, const double* vis, int on_device,
+                          void* stream) {
   if (!h) return fail(nullptr, BIPP_ERR_INVALID_ARG, "handle is NULL");
   if (!st_xyz || !vis) return fail(h, BIPP_ERR_INVALID_ARG, "st_xyz / vis is NULL");
-  std::vector<int> nst_v, neig_v;
-  const int K = check_sizes(h, n_t, n_st_max, n_st, n_eig, nst_v, neig_v);
+  std::vector<int> nst_v, neig_v, chan_v;
+  const int K = check_sizes(h, n_t, n_st_max, chan, n_st, n_eig, nst_v, neig_v, chan_v);
   if (K < 0) return K;
-  for (int t = 0; t < n_t; ++t)
-    for (int c = 0; c < 3; ++c)
-      for (int i = 0; i < nst_v[t]; ++i)
-        if (!isfinite(st_xyz[((size_t)t * 3 + c) * n_st_max + i]))
-          return fail(h, BIPP_ERR_INVALID_ARG, "step %d: station %d coordinate %d is not finite", t, i, c);
   CUDA_TRY(h, cudaSetDevice(h->device));
+  if (on_device) {
+    cudaPointerAttributes a1{}, a2{};
+    if (cudaPointerGetAttributes(&a1, st_xyz) != cudaSuccess || cudaPointerGetAttributes(&a2, vis) != cudaSuccess ||
+        a1.type != cudaMemoryTypeDevice || a2.type != cudaMemoryTypeDevice || a1.device != h->device ||
+        a2.device != h->device) {
+      cudaGetLastError();
+      return fail(h, BIPP_ERR_INVALID_ARG, "st_xyz and vis must be device memory on device %d", h->device);
+    }
+  } else {
+    for (int t = 0; t < n_t; ++t)
+      for (int c = 0; c < 3; ++c)
+        for (int i = 0; i < nst_v[t]; ++i)
+          if (!isfinite(st_xyz[((size_t)t * 3 + c) * n_st_max + i]))
+            return fail(h, BIPP_ERR_INVALID_ARG, "step %d: station %d coordinate %d is not finite", t, i, c);
+  }
   int rc = ensure_batch(h, n_t, n_st_max, K);
   if (rc) return rc;
+  if (on_device) {
+    cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
+    return run_batch(h, n_t, n_st_max, nst_v, neig_v, chan_v, K, st_xyz, reinterpret_cast<const double2*>(vis), s);
+  }
   const size_t N = (size_t)n_st_max;
   CUDA_TRY(h, cudaMemcpyAsync(h->d_st, st_xyz, sizeof(double) * 3 * N * n_t, cudaMemcpyHostToDevice, h->stream));
   CUDA_TRY(h, cudaMemcpyAsync(h->d_vis, vis, sizeof(double2) * N * N * n_t, cudaMemcpyHostToDevice, h->stream));
-  return run_batch(h, n_t, n_st_max, nst_v, neig_v, K, h->d_st, h->d_vis, h->stream);
+  return run_batch(h, n_t, n_st_max, nst_v, neig_v, chan_v, K, h->d_st, h->d_vis, h->stream);
+}
+
+extern "C" int bipp_ss_collect_batch(bipp_ss_t h, int32_t n_t, int32_t n_st_max, const int32_t* n_st,
+                                     const int32_t* n_eig, const double* st_xyz, const double* vis) {
+  return collect_common(h, n_t, n_st_max, nullptr, n_st, n_eig, st_xyz, vis, 0, nullptr);
 }
 
 extern "C" int bipp_ss_collect(bipp_ss_t h, int32_t n_st, const double* st_xyz, const double* vis) {
@@ -358,38 +527,31 @@ extern "C" int bipp_ss_collect(bipp_ss_t h, int32_t n_st, const double* st_xyz, 
 extern "C" int bipp_ss_collect_device(bipp_ss_t h, int32_t n_t, int32_t n_st_max, const int32_t* n_st,
                                       const int32_t* n_eig, const double* d_st_xyz, const double* d_vis,
                                       void* stream) {
-  if (!h) return fail(nullptr, BIPP_ERR_INVALID_ARG, "handle is NULL");
-  if (!d_st_xyz || !d_vis) return fail(h, BIPP_ERR_INVALID_ARG, "d_st_xyz / d_vis is NULL");
-  std::vector<int> nst_v, neig_v;
-  const int K = check_sizes(h, n_t, n_st_max, n_st, n_eig, nst_v, neig_v);
-  if (K < 0) return K;
-  CUDA_TRY(h, cudaSetDevice(h->device));
-  cudaPointerAttributes a1{}, a2{};
-  if (cudaPointerGetAttributes(&a1, d_st_xyz) != cudaSuccess || cudaPointerGetAttributes(&a2, d_vis) != cudaSuccess ||
-      a1.type != cudaMemoryTypeDevice || a2.type != cudaMemoryTypeDevice || a1.device != h->device ||
-      a2.device != h->device) {
-    cudaGetLastError();
-    return fail(h, BIPP_ERR_INVALID_ARG, "d_st_xyz and d_vis must be device memory on device %d", h->device);
-  }
-  int rc = ensure_batch(h, n_t, n_st_max, K);
-  if (rc) return rc;
-  cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
-  return run_batch(h, n_t, n_st_max, nst_v, neig_v, K, d_st_xyz, reinterpret_cast<const double2*>(d_vis), s);
+  return collect_common(h, n_t, n_st_max, nullptr, n_st, n_eig, d_st_xyz, d_vis, 1, stream);
 }
+
+extern "C" int bipp_ss_collect_channels(bipp_ss_t h, int32_t n_t, int32_t n_st_max, const int32_t* chan,
+                                        const int32_t* n_st, const int32_t* n_eig, const double* st_xyz,
+                                        const double* vis, int32_t on_device, void* stream) {
+  if (h && !chan) return fail(h, BIPP_ERR_INVALID_ARG, "chan is NULL");
+  return collect_common(h, n_t, n_st_max, chan, n_st, n_eig, st_xyz, vis, on_device, stream);
+}
+
+static size_t n_img(const bipp_ss* h) { return (size_t)h->n_chan * h->n_level * h->n_pix; }
 
 extern "C" int bipp_ss_get_f64(bipp_ss_t h, double* out) {
   if (!h) return fail(nullptr, BIPP_ERR_INVALID_ARG, "handle is NULL");
   if (!out) return fail(h, BIPP_ERR_INVALID_ARG, "out is NULL");
   CUDA_TRY(h, cudaSetDevice(h->device));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-  CUDA_TRY(h, cudaMemcpy(out, h->d_img, sizeof(double) * h->n_level * h->n_pix, cudaMemcpyDeviceToHost));
+  CUDA_TRY(h, cudaMemcpy(out, h->d_img, sizeof(double) * n_img(h), cudaMemcpyDeviceToHost));
   return BIPP_OK;
 }
 
 extern "C" int bipp_ss_get(bipp_ss_t h, float* out) {
   if (!h) return fail(nullptr, BIPP_ERR_INVALID_ARG, "handle is NULL");
   if (!out) return fail(h, BIPP_ERR_INVALID_ARG, "out is NULL");
-  std::vector<double> tmp((size_t)h->n_level * h->n_pix);
+  std::vector<double> tmp(n_img(h));
   const int rc = bipp_ss_get_f64(h, tmp.data());
   if (rc) return rc;
   for (size_t i = 0; i < tmp.size(); ++i) out[i] = (float)tmp[i];
@@ -402,14 +564,14 @@ extern "C" int bipp_ss_get_device_f64(bipp_ss_t h, double* d_out, void* stream) 
   CUDA_TRY(h, cudaSetDevice(h->device));
   cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-  CUDA_TRY(h, cudaMemcpyAsync(d_out, h->d_img, sizeof(double) * h->n_level * h->n_pix, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(h, cudaMemcpyAsync(d_out, h->d_img, sizeof(double) * n_img(h), cudaMemcpyDeviceToDevice, s));
   return BIPP_OK;
 }
 
 extern "C" int bipp_ss_reset(bipp_ss_t h) {
   if (!h) return fail(nullptr, BIPP_ERR_INVALID_ARG, "handle is NULL");
   CUDA_TRY(h, cudaSetDevice(h->device));
-  CUDA_TRY(h, cudaMemsetAsync(h->d_img, 0, sizeof(double) * h->n_level * h->n_pix, h->stream));
+  CUDA_TRY(h, cudaMemsetAsync(h->d_img, 0, sizeof(double) * n_img(h), h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   return BIPP_OK;
 }
@@ -419,7 +581,7 @@ extern "C" int bipp_ss_set_images(bipp_ss_t h, const double* img) {
   if (!img) return fail(h, BIPP_ERR_INVALID_ARG, "img is NULL");
   CUDA_TRY(h, cudaSetDevice(h->device));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-  CUDA_TRY(h, cudaMemcpy(h->d_img, img, sizeof(double) * h->n_level * h->n_pix, cudaMemcpyHostToDevice));
+  CUDA_TRY(h, cudaMemcpy(h->d_img, img, sizeof(double) * n_img(h), cudaMemcpyHostToDevice));
   return BIPP_OK;
 }
 

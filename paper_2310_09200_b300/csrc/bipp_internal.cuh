@@ -24,6 +24,8 @@ struct Batch {
   int k_max;      // leading dimension of per-step eigen arrays
   const int* nst;   // [T] stations per step
   const int* neig;  // [T] eigenpairs requested per step
+  const double* wl; // [T] wavelength of each step [m]
+  const int* chan;  // [T] channel of each step (non-decreasing), or nullptr = all channel 0
   const double* st;   // [T][3][n_max] station xyz (metres), column-major per step
   const double2* vis; // [T][n_max][n_max] visibilities, column-major per step
   double* G;      // [T][n_max][n_max] Gram matrix, then its Cholesky factor L (lower)
@@ -51,19 +53,25 @@ struct Pixels {
   const float* hl;    // [6][n] float hi/lo split: xh,yh,zh,xl,yl,zl
 };
 
+// Channel of step t and whether t is the last step of its channel in the batch
+// (the synthesis kernels flush their per-channel register sums there).
+__device__ __forceinline__ int step_chan(const Batch& b, int t) { return b.chan ? b.chan[t] : 0; }
+__device__ __forceinline__ bool last_of_chan(const Batch& b, int t) {
+  return t == b.T - 1 || (b.chan && b.chan[t + 1] != b.chan[t]);
+}
+
 // ---- launchers (stream-ordered, no synchronisation) ----
-void launch_gram(const Batch& b, double wl, int gram_identity, cudaStream_t s);
+void launch_gram(const Batch& b, int gram_identity, cudaStream_t s);
 void launch_cholesky(const Batch& b, int gram_identity, cudaStream_t s);
 void launch_reduce(const Batch& b, int gram_identity, cudaStream_t s);
 void launch_jacobi(const Batch& b, double tol, int max_sweeps, cudaStream_t s);
-void launch_select(const Batch& b, double wl, int n_level, const double* d_bounds, int filter,
-                   cudaStream_t s);
+// d_bounds: per channel, n_level x 2 column-major blocks.
+void launch_select(const Batch& b, int n_level, const double* d_bounds, int filter, cudaStream_t s);
 void launch_pixel_split(const double* d_xyz, float* d_hl, int64_t n, cudaStream_t s);
 
-// Synthesis of a whole batch into img (n_pix x n_level FP64, accumulated).
-void launch_synth_simt_f64(const Batch& b, const Pixels& px, double wl, int n_level, double* img,
-                           cudaStream_t s);
-void launch_synth_simt_f32(const Batch& b, const Pixels& px, int n_level, double* img,
-                           cudaStream_t s);
+// Synthesis of a whole batch into img (per channel c: n_pix x n_level FP64 at
+// img + c * n_level * n_pix, accumulated).
+void launch_synth_simt_f64(const Batch& b, const Pixels& px, int n_level, double* img, cudaStream_t s);
+void launch_synth_simt_f32(const Batch& b, const Pixels& px, int n_level, double* img, cudaStream_t s);
 
 }  // namespace bipp

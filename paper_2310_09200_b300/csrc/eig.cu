@@ -21,9 +21,10 @@ __device__ __forceinline__ size_t mat_off(int t, int n_max) { return (size_t)t *
 // ---------------------------------------------------------------- Gram
 
 // G_ij = sinc(2 ||p_i - p_j|| / wl) with sinc(x) = sin(pi x)/(pi x) (Eq. gram, App. A).
-__global__ void k_gram(Batch b, double wl, int gram_identity) {
+__global__ void k_gram(Batch b, int gram_identity) {
   const int t = blockIdx.z;
   const int n = b.nst[t];
+  const double wl = b.wl[t];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= n || j >= n) return;
@@ -387,12 +388,14 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi(Batch b, double tol, 
 // Keep the n_eig algebraically largest eigenvalues (descending, ties by lower
 // Jacobi index), assign filter weights and levels, back-transform the kept
 // eigenvectors a = L^{-T} q, and pack them for the synthesis kernels.
-__global__ void k_select(Batch b, double wl, int n_level, const double* bounds, int filter) {
+__global__ void k_select(Batch b, int n_level, const double* all_bounds, int filter) {
   const int t = blockIdx.x;
   const int n = b.nst[t];
   const int N = b.n_max;
   const int K = b.neig[t];
   const int KM = b.k_max;
+  const double wl = b.wl[t];
+  const double* bounds = all_bounds + (size_t)step_chan(b, t) * 2 * n_level;
   __shared__ int idx[kMaxEig];
   const int st = b.status[t];
   if (st) {
@@ -474,9 +477,9 @@ __global__ void k_pixel_split(const double* xyz, float* hl, int64_t n) {
 
 }  // namespace
 
-void launch_gram(const Batch& b, double wl, int gram_identity, cudaStream_t s) {
+void launch_gram(const Batch& b, int gram_identity, cudaStream_t s) {
   dim3 blk(16, 16), grd((b.n_max + 15) / 16, (b.n_max + 15) / 16, b.T);
-  k_gram<<<grd, blk, 0, s>>>(b, wl, gram_identity);
+  k_gram<<<grd, blk, 0, s>>>(b, gram_identity);
 }
 
 void launch_cholesky(const Batch& b, int gram_identity, cudaStream_t s) {
@@ -500,8 +503,8 @@ void launch_jacobi(const Batch& b, double tol, int max_sweeps, cudaStream_t s) {
   k_jacobi<<<b.T, kJacobiThreads, 0, s>>>(b, tol, max_sweeps);
 }
 
-void launch_select(const Batch& b, double wl, int n_level, const double* d_bounds, int filter, cudaStream_t s) {
-  k_select<<<b.T, 256, 0, s>>>(b, wl, n_level, d_bounds, filter);
+void launch_select(const Batch& b, int n_level, const double* d_bounds, int filter, cudaStream_t s) {
+  k_select<<<b.T, 256, 0, s>>>(b, n_level, d_bounds, filter);
 }
 
 void launch_pixel_split(const double* d_xyz, float* d_hl, int64_t n, cudaStream_t s) {

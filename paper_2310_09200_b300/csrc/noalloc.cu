@@ -46,7 +46,8 @@ constexpr size_t kOffWt = kOffLevel + up((size_t)kK * sizeof(int));
 constexpr size_t kOffW64 = kOffWt + up((size_t)kK * sizeof(double));
 constexpr size_t kOffW32 = kOffW64 + up((size_t)kK * kN * sizeof(double2));
 constexpr size_t kOffQst = kOffW32 + up((size_t)kK * kN * sizeof(float2));
-constexpr size_t kScratchBytes = kOffQst + up((size_t)6 * kN * sizeof(float));
+constexpr size_t kOffWl = kOffQst + up((size_t)6 * kN * sizeof(float));  // the step's wavelength
+constexpr size_t kScratchBytes = kOffWl + up(sizeof(double));
 static_assert(kScratchBytes <= (size_t)BIPP_NOALLOC_SCRATCH_BYTES, "scratch layout exceeds the stated size");
 
 // The scratch itself. In host code this name is only a stand-in for the
@@ -107,7 +108,7 @@ extern "C" int bipp_ss_collect_noalloc(int64_t n_pix, const double* d_pix_xyz, d
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
   int* ints = reinterpret_cast<int*>(base + kOffInts);
-  Batch b;
+  Batch b{};
   b.T = 1;
   b.n_max = n_st;
   b.k_max = n_eig;
@@ -131,6 +132,9 @@ extern "C" int bipp_ss_collect_noalloc(int64_t n_pix, const double* d_pix_xyz, d
   b.W64 = reinterpret_cast<double2*>(base + kOffW64);
   b.W32 = reinterpret_cast<float2*>(base + kOffW32);
   b.q = reinterpret_cast<float*>(base + kOffQst);
+  double* d_wl = reinterpret_cast<double*>(base + kOffWl);
+  b.wl = d_wl;
+  b.chan = nullptr;
   double* d_bounds = reinterpret_cast<double*>(base + kOffBounds);
 
   // sizes and level bounds into the scratch; status words start at zero
@@ -141,15 +145,16 @@ extern "C" int bipp_ss_collect_noalloc(int64_t n_pix, const double* d_pix_xyz, d
     memcpy(bnd, level_bounds, sizeof(double) * 2 * n_level);
     e = cudaMemcpyAsync(d_bounds, bnd, sizeof(double) * 2 * n_level, cudaMemcpyHostToDevice, s);
   }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_wl, &wl, sizeof(double), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return report(err_msg, err_len, BIPP_ERR_CUDA, "upload: %s", cudaGetErrorString(e));
 
-  launch_gram(b, wl, gram_identity, s);
+  launch_gram(b, gram_identity, s);
   launch_cholesky(b, gram_identity, s);
   launch_reduce(b, gram_identity, s);
   launch_jacobi(b, 1e-13, 40, s);
-  launch_select(b, wl, n_level, d_bounds, filter, s);
+  launch_select(b, n_level, d_bounds, filter, s);
   Pixels px{n_pix, d_pix_xyz, nullptr};
-  launch_synth_simt_f64(b, px, wl, n_level, d_img, s);
+  launch_synth_simt_f64(b, px, n_level, d_img, s);
   if ((e = cudaGetLastError()) != cudaSuccess)
     return report(err_msg, err_len, BIPP_ERR_CUDA, "launch: %s", cudaGetErrorString(e));
   int status = 0;

@@ -62,9 +62,25 @@ __global__ void __launch_bounds__(kThreads) k_synth_f32(Batch b, Pixels px, int 
   for (int l = 0; l < MAXL; ++l) lacc[l] = 0.0f;
 
   const int N = b.n_max, KM = b.k_max;
+  // reduce the 4 eigenvector groups, then one FP64 read-modify-write per pixel and level
+  auto flush = [&](int chan) {
+#pragma unroll
+    for (int l = 0; l < MAXL; ++l) sh_red[(eg * MAXL + l) * kPix + pl] = lacc[l];
+    __syncthreads();
+    if (eg == 0 && valid) {
+      double* im = img + (size_t)chan * n_level * px.n;
+      for (int l = 0; l < n_level; ++l) {
+        float s = 0.0f;
+        for (int g = 0; g < kThreads / kPix; ++g) s += sh_red[(g * MAXL + l) * kPix + pl];
+        im[(size_t)l * px.n + r] += (double)s;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int l = 0; l < MAXL; ++l) lacc[l] = 0.0f;
+  };
   for (int t = 0; t < b.T; ++t) {
     const int n = b.nst[t], K = b.nkept[t];
-    if (K == 0) continue;
     const float* q = b.q + (size_t)t * 6 * N;
     for (int e0 = 0; e0 < K; e0 += kEigBlk) {
       float zr[kEigPerThr], zi[kEigPerThr];
@@ -115,17 +131,7 @@ __global__ void __launch_bounds__(kThreads) k_synth_f32(Batch b, Pixels px, int 
         }
       }
     }
-  }
-  // reduce the 4 eigenvector groups, then one FP64 read-modify-write per pixel and level
-#pragma unroll
-  for (int l = 0; l < MAXL; ++l) sh_red[(eg * MAXL + l) * kPix + pl] = lacc[l];
-  __syncthreads();
-  if (eg == 0 && valid) {
-    for (int l = 0; l < n_level; ++l) {
-      float s = 0.0f;
-      for (int g = 0; g < kThreads / kPix; ++g) s += sh_red[(g * MAXL + l) * kPix + pl];
-      img[(size_t)l * px.n + r] += (double)s;
-    }
+    if (last_of_chan(b, t)) flush(step_chan(b, t));
   }
 }
 
@@ -134,7 +140,7 @@ __global__ void __launch_bounds__(kThreads) k_synth_f32(Batch b, Pixels px, int 
 constexpr int kStChunk64 = 32;
 
 template <int MAXL>
-__global__ void __launch_bounds__(kThreads) k_synth_f64(Batch b, Pixels px, double wl, int n_level, double* img) {
+__global__ void __launch_bounds__(kThreads) k_synth_f64(Batch b, Pixels px, int n_level, double* img) {
   if (*b.flag) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* sh_c = reinterpret_cast<double*>(smem_raw);                    // [kStChunk64][kPix]
@@ -147,15 +153,30 @@ __global__ void __launch_bounds__(kThreads) k_synth_f64(Batch b, Pixels px, doub
   const bool valid = r < px.n;
   const double rx = valid ? px.xyz[r] : 0.0, ry = valid ? px.xyz[px.n + r] : 0.0,
                rz = valid ? px.xyz[2 * px.n + r] : 0.0;
-  const double k = 2.0 * M_PI / wl;
 
   double lacc[MAXL];
 #pragma unroll
   for (int l = 0; l < MAXL; ++l) lacc[l] = 0.0;
   const int N = b.n_max, KM = b.k_max;
+  auto flush = [&](int chan) {
+#pragma unroll
+    for (int l = 0; l < MAXL; ++l) sh_red[(eg * MAXL + l) * kPix + pl] = lacc[l];
+    __syncthreads();
+    if (eg == 0 && valid) {
+      double* im = img + (size_t)chan * n_level * px.n;
+      for (int l = 0; l < n_level; ++l) {
+        double s = 0.0;
+        for (int g = 0; g < kThreads / kPix; ++g) s += sh_red[(g * MAXL + l) * kPix + pl];
+        im[(size_t)l * px.n + r] += s;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int l = 0; l < MAXL; ++l) lacc[l] = 0.0;
+  };
   for (int t = 0; t < b.T; ++t) {
     const int n = b.nst[t], K = b.nkept[t];
-    if (K == 0) continue;
+    const double k = 2.0 * M_PI / b.wl[t];
     const double* p = b.st + (size_t)t * 3 * N;
     for (int e0 = 0; e0 < K; e0 += kEigBlk) {
       double zr[kEigPerThr], zi[kEigPerThr];
@@ -201,16 +222,7 @@ __global__ void __launch_bounds__(kThreads) k_synth_f64(Batch b, Pixels px, doub
         }
       }
     }
-  }
-#pragma unroll
-  for (int l = 0; l < MAXL; ++l) sh_red[(eg * MAXL + l) * kPix + pl] = lacc[l];
-  __syncthreads();
-  if (eg == 0 && valid) {
-    for (int l = 0; l < n_level; ++l) {
-      double s = 0.0;
-      for (int g = 0; g < kThreads / kPix; ++g) s += sh_red[(g * MAXL + l) * kPix + pl];
-      img[(size_t)l * px.n + r] += s;
-    }
+    if (last_of_chan(b, t)) flush(step_chan(b, t));
   }
 }
 
@@ -233,13 +245,13 @@ void launch_synth_simt_f32(const Batch& b, const Pixels& px, int n_level, double
   });
 }
 
-void launch_synth_simt_f64(const Batch& b, const Pixels& px, double wl, int n_level, double* img, cudaStream_t s) {
+void launch_synth_simt_f64(const Batch& b, const Pixels& px, int n_level, double* img, cudaStream_t s) {
   const size_t smem = (size_t)kStChunk64 * kPix * 8 * 2 + (size_t)kStChunk64 * kEigBlk * 16;
   const unsigned grid = (unsigned)((px.n + kPix - 1) / kPix);
   dispatch_levels(n_level, [&](auto L) {
     constexpr int ML = decltype(L)::value;
     cudaFuncSetAttribute(k_synth_f64<ML>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_synth_f64<ML><<<grid, kThreads, smem, s>>>(b, px, wl, n_level, img);
+    k_synth_f64<ML><<<grid, kThreads, smem, s>>>(b, px, n_level, img);
   });
 }
 

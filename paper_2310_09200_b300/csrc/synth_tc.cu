@@ -32,6 +32,8 @@
 #include <math.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <type_traits>
 
 #include "phase.cuh"
@@ -230,11 +232,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&bar_acce[bb]));
-      if (t == T - 1) {
+      if (last_of_chan(b, t)) {
         const int64_t r = (int64_t)tile * kRows + row;
+        double* im = img + (size_t)step_chan(b, t) * n_level * px.n;
         if (r < px.n)
           for (int l = 0; l < n_level; ++l)
-            if (lacc[l] != 0.0f) atomicAdd(img + (size_t)l * px.n + r, (double)lacc[l]);
+            if (lacc[l] != 0.0f) atomicAdd(im + (size_t)l * px.n + r, (double)lacc[l]);
 #pragma unroll
         for (int l = 0; l < MAXL; ++l) lacc[l] = 0.0f;
       }
@@ -490,6 +493,7 @@ int tc_alloc(TcWorkspace* w, int T, int N, int K) {
   if (cudaMalloc(&w->B, bytes) != cudaSuccess) return -1;
   w->B_bytes = bytes;
   if (cudaMalloc(&w->steps, sizeof(TcStep) * T) != cudaSuccess) return -1;
+  if (cudaMallocHost(&w->h_steps, sizeof(TcStep) * T) != cudaSuccess) return -1;
   if (cudaMalloc(&w->scale, sizeof(float) * T) != cudaSuccess) return -1;
   if (cudaMalloc(&w->status, sizeof(int)) != cudaSuccess) return -1;
   w->cap_T = T;
@@ -499,6 +503,7 @@ int tc_alloc(TcWorkspace* w, int T, int N, int K) {
 void tc_free(TcWorkspace* w) {
   if (w->B) cudaFree(w->B);
   if (w->steps) cudaFree(w->steps);
+  if (w->h_steps) cudaFreeHost(w->h_steps);
   if (w->scale) cudaFree(w->scale);
   if (w->status) cudaFree(w->status);
   *w = TcWorkspace{};
@@ -510,36 +515,19 @@ int tc_read_status(TcWorkspace* w) {
   return v;
 }
 
-int launch_synth_tc(const Batch& b, const std::vector<int>& nst, const std::vector<int>& neig, const Pixels& px,
-                    int n_level, double* img, bool fp16, TcWorkspace* w, cudaStream_t s) {
-  const int T = b.T;
-  if (T > w->cap_T) return -2;
-  std::vector<TcStep> st(T);
-  long long off = 0;
-  int ncols_max = 16, max_chunks = 1;
-  for (int t = 0; t < T; ++t) {
-    if (neig[t] > kTcMaxEig) return -3;
-    st[t].b_off = off;
-    st[t].n_chunks = n_chunks_for(nst[t]);
-    st[t].ncols = ncols_for(neig[t]);
-    st[t].idesc = make_idesc(st[t].ncols, fp16);
-    st[t].pad = 0;
-    off += (long long)st[t].n_chunks * st[t].ncols * 256;
-    ncols_max = std::max(ncols_max, st[t].ncols);
-    max_chunks = std::max(max_chunks, st[t].n_chunks);
-  }
-  if ((size_t)off > w->B_bytes) return -4;
-  if (cudaMemcpyAsync(w->steps, st.data(), sizeof(TcStep) * T, cudaMemcpyHostToDevice, s) != cudaSuccess) return -5;
-  if (cudaMemsetAsync(w->status, 0, sizeof(int), s) != cudaSuccess) return -5;
-  if (fp16) k_tc_scale<<<T, 256, 0, s>>>(b, w->scale);
-  if (fp16) k_tc_pack<true><<<dim3(max_chunks, T), 256, 0, s>>>(b, w->steps, w->B, w->scale);
-  else k_tc_pack<false><<<dim3(max_chunks, T), 256, 0, s>>>(b, w->steps, w->B, w->scale);
+namespace {
 
-  int ncols_buf = 32;
-  while (ncols_buf < ncols_max) ncols_buf <<= 1;  // 2 * ncols_buf TMEM columns, a power of two <= 512
-  const int stage_bytes = 2 * kABytes + 2 * ncols_max * 128;
-  const int n_stages = std::min(kMaxStages, (220 * 1024) / stage_bytes);
-  if (n_stages < 2) return -6;
+int stage_bytes_for(int ncols_max) { return 2 * kABytes + 2 * ncols_max * 128; }
+int max_stages_for(int ncols_max) { return std::min(kMaxStages, (220 * 1024) / stage_bytes_for(ncols_max)); }
+
+// Autotuned stage counts, keyed by (accumulator width, operand type): the
+// tuned value holds for every batch with the same key in this process.
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, int> g_tuned_stages;
+
+int launch_kernel(const Batch& b, const Pixels& px, int n_level, double* img, const TcPlan& p, int n_stages,
+                  TcWorkspace* w, cudaStream_t s) {
+  const int stage_bytes = stage_bytes_for(p.ncols_max);
   const size_t smem = (size_t)n_stages * stage_bytes + 1024;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
@@ -547,7 +535,7 @@ int launch_synth_tc(const Batch& b, const std::vector<int>& nst, const std::vect
   const int n_tiles = (int)((px.n + kRows - 1) / kRows);
   const int grid = std::min(n_tiles, sms);
   int rc = 0;
-  dispatch(n_level, fp16, [&](auto L, auto FPV) {
+  dispatch(n_level, p.fp16, [&](auto L, auto FPV) {
     constexpr int ML = decltype(L)::value;
     constexpr bool F16 = decltype(FPV)::value;
     if (cudaFuncSetAttribute(k_synth_tc<ML, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
@@ -556,9 +544,103 @@ int launch_synth_tc(const Batch& b, const std::vector<int>& nst, const std::vect
       return;
     }
     k_synth_tc<ML, F16><<<grid, kThreads, smem, s>>>(b, px, n_level, img, w->steps, w->B, w->scale, n_stages,
-                                                     stage_bytes, ncols_buf, w->status);
+                                                     stage_bytes, p.ncols_buf, w->status);
   });
   return rc;
+}
+
+}  // namespace
+
+int tc_prepare(const std::vector<int>& nst, const std::vector<int>& neig, bool fp16, TcWorkspace* w, TcPlan* p) {
+  const int T = (int)nst.size();
+  if (T > w->cap_T) return -2;
+  long long off = 0;
+  int ncols_max = 16, max_chunks = 1;
+  for (int t = 0; t < T; ++t) {
+    if (neig[t] > kTcMaxEig) return -3;
+    TcStep& st = w->h_steps[t];
+    st.b_off = off;
+    st.n_chunks = n_chunks_for(nst[t]);
+    st.ncols = ncols_for(neig[t]);
+    st.idesc = make_idesc(st.ncols, fp16);
+    st.pad = 0;
+    off += (long long)st.n_chunks * st.ncols * 256;
+    ncols_max = std::max(ncols_max, st.ncols);
+    max_chunks = std::max(max_chunks, st.n_chunks);
+  }
+  if ((size_t)off > w->B_bytes) return -4;
+  p->fp16 = fp16;
+  p->ncols_max = ncols_max;
+  p->max_chunks = max_chunks;
+  p->ncols_buf = 32;
+  while (p->ncols_buf < ncols_max) p->ncols_buf <<= 1;  // 2 * ncols_buf TMEM columns, a power of two <= 512
+  const int smax = max_stages_for(ncols_max);
+  if (smax < 2) return -6;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tuned_stages.find({ncols_max, (int)fp16});
+  p->tuned = it != g_tuned_stages.end();
+  p->n_stages = p->tuned ? it->second : smax;
+  return 0;
+}
+
+int tc_enqueue_pack(const Batch& b, const TcPlan& p, TcWorkspace* w, cudaStream_t s) {
+  const int T = b.T;
+  if (cudaMemcpyAsync(w->steps, w->h_steps, sizeof(TcStep) * T, cudaMemcpyHostToDevice, s) != cudaSuccess) return -5;
+  if (cudaMemsetAsync(w->status, 0, sizeof(int), s) != cudaSuccess) return -5;
+  if (p.fp16) k_tc_scale<<<T, 256, 0, s>>>(b, w->scale);
+  if (p.fp16) k_tc_pack<true><<<dim3(p.max_chunks, T), 256, 0, s>>>(b, w->steps, w->B, w->scale);
+  else k_tc_pack<false><<<dim3(p.max_chunks, T), 256, 0, s>>>(b, w->steps, w->B, w->scale);
+  return cudaGetLastError() == cudaSuccess ? 0 : -5;
+}
+
+int tc_enqueue_synth(const Batch& b, const Pixels& px, int n_level, double* img, const TcPlan& p, TcWorkspace* w,
+                     cudaStream_t s) {
+  return launch_kernel(b, px, n_level, img, p, p.n_stages, w, s);
+}
+
+int tc_autotune(const Batch& b, const Pixels& px, int n_level, int n_chan_sub, TcPlan* p, TcWorkspace* w,
+                cudaStream_t s) {
+  // Time each feasible stage count on the first steps of the batch and a
+  // pixel subset, into a scratch image (the real images are not touched).
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  Batch bs = b;
+  bs.T = std::min(b.T, 4);
+  Pixels ps = px;
+  ps.n = std::min<int64_t>(px.n, (int64_t)4 * sms * kRows);
+  double* scratch = nullptr;
+  const size_t bytes = sizeof(double) * (size_t)std::max(1, n_chan_sub) * n_level * ps.n;
+  if (cudaMallocAsync(&scratch, bytes, s) != cudaSuccess) return -8;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int best = p->n_stages;
+  float best_ms = 1e30f;
+  int rc = 0;
+  for (int ns = 2; ns <= max_stages_for(p->ncols_max) && rc == 0; ++ns) {
+    rc = launch_kernel(bs, ps, n_level, scratch, *p, ns, w, s);  // warm-up
+    cudaEventRecord(e0, s);
+    if (rc == 0) rc = launch_kernel(bs, ps, n_level, scratch, *p, ns, w, s);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rc == 0 && ms < best_ms) {
+      best_ms = ms;
+      best = ns;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(scratch, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return -9;
+  if (rc) return rc;
+  p->n_stages = best;
+  p->tuned = true;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tuned_stages[{p->ncols_max, (int)p->fp16}] = best;
+  return 0;
 }
 
 }  // namespace bipp

@@ -27,18 +27,38 @@ struct TcStep {
 struct TcWorkspace {
   unsigned char* B = nullptr;  // packed, pre-swizzled hi/lo operand chunks of every step
   size_t B_bytes = 0;
-  TcStep* steps = nullptr;     // [cap_T]
+  TcStep* steps = nullptr;     // [cap_T] device copy of the step table
+  TcStep* h_steps = nullptr;   // [cap_T] pinned host step table (source of the copy, graph-safe)
   float* scale = nullptr;      // [cap_T] operand scale of the FP16 variant (W * scale)
   int* status = nullptr;       // [1] device error word (0 = ok)
   int cap_T = 0;
 };
 
+// Launch geometry of one batch.
+struct TcPlan {
+  bool fp16 = false;
+  int ncols_max = 16;   // widest accumulator (2 * n_eig rounded to 16)
+  int max_chunks = 1;   // most 32-station chunks of a step
+  int ncols_buf = 32;   // TMEM columns per accumulator buffer (power of two)
+  int n_stages = 2;     // shared-memory ring depth
+  bool tuned = false;   // n_stages comes from the autotuner
+};
+
 int tc_alloc(TcWorkspace* w, int T, int N, int K);
 void tc_free(TcWorkspace* w);
 int tc_read_status(TcWorkspace* w);  // 0 or the device error word
-// Returns 0, or a negative value if the batch exceeds the path's limits
-// (n_eig > kTcMaxEig) or a CUDA call failed.
-int launch_synth_tc(const Batch& b, const std::vector<int>& nst, const std::vector<int>& neig, const Pixels& px,
-                    int n_level, double* img, bool fp16, TcWorkspace* w, cudaStream_t s);
+// Host side: step table into pinned memory and the launch plan. Returns 0,
+// -3 if some step has n_eig > kTcMaxEig, other negatives on capacity errors.
+int tc_prepare(const std::vector<int>& nst, const std::vector<int>& neig, bool fp16, TcWorkspace* w, TcPlan* p);
+// Stream-ordered (graph-capturable): step table upload, FP16 scales, operand packing.
+int tc_enqueue_pack(const Batch& b, const TcPlan& p, TcWorkspace* w, cudaStream_t s);
+// Stream-ordered (graph-capturable): the fused synthesis kernel.
+int tc_enqueue_synth(const Batch& b, const Pixels& px, int n_level, double* img, const TcPlan& p, TcWorkspace* w,
+                     cudaStream_t s);
+// Not capturable (synchronises): time each feasible stage count on a subset
+// of the packed batch into a scratch image, keep the fastest in p and in a
+// process-wide cache keyed by (ncols_max, operand type).
+int tc_autotune(const Batch& b, const Pixels& px, int n_level, int n_chan_sub, TcPlan* p, TcWorkspace* w,
+                cudaStream_t s);
 
 }  // namespace bipp
