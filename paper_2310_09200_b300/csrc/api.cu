@@ -85,6 +85,8 @@ struct bipp_ss {
   int* h_chan = nullptr;
   double* h_wl = nullptr;
   TcWorkspace tc{};
+  MixedWs mx{};
+  int mixed_kp = 0;  // KP of the current batch when the mixed eigensolver runs, else 0
   // graph cache: the last geometry seen, and the captured graph of it
   GraphKey last_key;
   bool have_key = false;
@@ -135,8 +137,10 @@ static void free_batch(bipp_ss* h) {
   drop_graph(h);
   void* ptrs[] = {h->d_st, h->d_vis, h->d_G, h->d_Linv, h->d_X, h->d_C, h->d_Q, h->d_mu, h->d_status,
                   h->d_sweeps, h->d_nkept, h->d_sel_mu, h->d_level, h->d_wt, h->d_W64, h->d_W32, h->d_q,
-                  h->d_nst, h->d_neig, h->d_chan, h->d_wl, h->d_flag};
+                  h->d_nst, h->d_neig, h->d_chan, h->d_wl, h->d_flag, h->mx.kp, h->mx.sel, h->mx.theta,
+                  h->mx.rnorm, h->mx.cnorm, h->mx.st2, h->mx.sw2};
   for (void* p : ptrs) if (p) cudaFree(p);
+  h->mx = MixedWs{};
   void* hp[] = {h->h_nst, h->h_neig, h->h_chan, h->h_wl};
   for (void* p : hp) if (p) cudaFreeHost(p);
   h->d_st = nullptr; h->d_vis = nullptr; h->d_G = nullptr; h->d_Linv = nullptr; h->d_X = nullptr;
@@ -178,6 +182,13 @@ static int ensure_batch(bipp_ss* h, int T, int N, int K) {
   CUDA_TRY(h, dalloc(&h->d_chan, (size_t)T));
   CUDA_TRY(h, dalloc(&h->d_wl, (size_t)T));
   CUDA_TRY(h, dalloc(&h->d_flag, 1));
+  CUDA_TRY(h, dalloc(&h->mx.kp, (size_t)T));
+  CUDA_TRY(h, dalloc(&h->mx.sel, (size_t)T * N));
+  CUDA_TRY(h, dalloc(&h->mx.theta, (size_t)T * N));
+  CUDA_TRY(h, dalloc(&h->mx.rnorm, (size_t)T * N));
+  CUDA_TRY(h, dalloc(&h->mx.cnorm, (size_t)T));
+  CUDA_TRY(h, dalloc(&h->mx.st2, (size_t)T));
+  CUDA_TRY(h, dalloc(&h->mx.sw2, (size_t)T));
   CUDA_TRY(h, cudaMallocHost(&h->h_nst, sizeof(int) * T));
   CUDA_TRY(h, cudaMallocHost(&h->h_neig, sizeof(int) * T));
   CUDA_TRY(h, cudaMallocHost(&h->h_chan, sizeof(int) * T));
@@ -367,7 +378,13 @@ static int enqueue_batch(bipp_ss* h, const Batch& b, const TcPlan& plan, cudaStr
   launch_cholesky(b, gi, s);
   launch_reduce(b, gi, s);
   CUDA_TRY(h, record(h->ev[1], s));
-  launch_jacobi(b, h->opt.jacobi_tol, h->opt.max_jacobi_sweeps, s);
+  if (h->mixed_kp > 0) {
+    MixedWs w = h->mx;
+    w.KP = h->mixed_kp;
+    launch_eig_mixed(b, w, h->opt.jacobi_tol, h->opt.max_jacobi_sweeps, s);
+  } else {
+    launch_jacobi(b, h->opt.jacobi_tol, h->opt.max_jacobi_sweeps, s);
+  }
   CUDA_TRY(h, record(h->ev[2], s));
   launch_select(b, h->n_level, h->d_bounds, h->opt.filter, s);
   const bool tc = h->opt.precision >= BIPP_PREC_SPLIT_BF16;
@@ -397,6 +414,13 @@ static int run_batch(bipp_ss* h, int n_t, int N, const std::vector<int>& nst_v, 
     h->h_wl[t] = h->wl[chan_v[t]];
   }
   Batch b = make_batch(h, n_t, N, K, d_st, d_vis);
+  // mixed-precision eigensolve when asked for and its scratch fits the batch buffers
+  h->mixed_kp = 0;
+  if (h->opt.eig_mode == BIPP_EIG_MIXED) {
+    int kp = 1;
+    for (int t = 0; t < n_t; ++t) kp = std::max(kp, std::min(nst_v[t], neig_v[t] + 16));
+    if (eig_mixed_fits(N, kp)) h->mixed_kp = kp;
+  }
   const bool tc = h->opt.precision >= BIPP_PREC_SPLIT_BF16;
   TcPlan plan;
   if (tc) {
@@ -467,7 +491,8 @@ static int run_batch(bipp_ss* h, int n_t, int N, const std::vector<int>& nst_v, 
   h->timings[4] = 0;
   for (int t = 0; t < n_t; ++t) h->timings[4] += sweeps[t];
   // gram, [cholesky], trinv, [2 reduction GEMMs], hermitize, jacobi, select, [scale], [pack], synthesis
-  h->timings[5] = (h->opt.gram_identity ? 6 : 9) + (tc ? 1 + (h->opt.precision == BIPP_PREC_SPLIT_FP16) : 0);
+  h->timings[5] = (h->opt.gram_identity ? 6 : 9) + (tc ? 1 + (h->opt.precision == BIPP_PREC_SPLIT_FP16) : 0) +
+                  (h->mixed_kp > 0 ? kMixedLaunches - 1 : 0);
   for (int t = 0; t < n_t; ++t) {
     if (status[t] & kStatusNotPD)
       return fail(h, BIPP_ERR_GRAM_NOT_PD, "step %d: Gram matrix is not positive definite (Cholesky pivot <= 0 or NaN)", t);

@@ -47,6 +47,18 @@ struct Batch {
   int* flag;      // [1] OR of all step statuses (synthesis skips the batch if set)
 };
 
+// Small per-step arrays of the mixed-precision eigensolver (eig_mixed.cu).
+struct MixedWs {
+  int KP;          // leading dimension of the per-step kp-sized arrays (max kp of the batch)
+  int* kp;         // [T] pairs refined per step: min(n, n_eig + 16)
+  int* sel;        // [T][n_max] rank of each FP32 eigenpair among the kept ones, -1 if not kept
+  double* theta;   // [T][KP] refined eigenvalues
+  double* rnorm;   // [T][KP] residual norms of the last pass
+  double* cnorm;   // [T] ||C||_F
+  int* st2;        // [T] status of the small FP64 Jacobi solves
+  int* sw2;        // [T] their sweeps
+};
+
 struct Pixels {
   int64_t n;
   const double* xyz;  // [3][n] FP64 unit vectors (column-major)
@@ -65,6 +77,12 @@ void launch_gram(const Batch& b, int gram_identity, cudaStream_t s);
 void launch_cholesky(const Batch& b, int gram_identity, cudaStream_t s);
 void launch_reduce(const Batch& b, int gram_identity, cudaStream_t s);
 void launch_jacobi(const Batch& b, double tol, int max_sweeps, cudaStream_t s);
+// Mixed-precision eigensolve (FP32 Jacobi + FP64 refinement of the leading
+// pairs); needs the X and Q buffers of the batch as scratch, which fits when
+// eig_mixed_fits(n_max, KP).
+bool eig_mixed_fits(int n_max, int KP);
+constexpr int kMixedLaunches = 56;  // kernels launched by launch_eig_mixed
+void launch_eig_mixed(const Batch& b, const MixedWs& w, double tol, int max_sweeps, cudaStream_t s);
 // d_bounds: per channel, n_level x 2 column-major blocks.
 void launch_select(const Batch& b, int n_level, const double* d_bounds, int filter, cudaStream_t s);
 void launch_pixel_split(const double* d_xyz, float* d_hl, int64_t n, cudaStream_t s);

@@ -11,6 +11,7 @@
 #include <math.h>
 
 #include "bipp_internal.cuh"
+#include "jacobi.cuh"
 
 namespace bipp {
 
@@ -195,194 +196,6 @@ __global__ void k_hermitize(Batch b, int from_vis) {
   C[(size_t)j + (size_t)i * N] = make_double2(h.x, -h.y);
 }
 
-// ---------------------------------------------------------------- Jacobi
-
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {  // a * conj(b)
-  return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
-}
-__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-
-// Round-robin ("circle method") pairing of m (even) indices: in round r the
-// pairs are (m-1, r) and ((r+k) mod (m-1), (r-k) mod (m-1)) for k = 1..m/2-1.
-// Every pair meets exactly once in m-1 rounds, and the m/2 pairs of a round
-// are disjoint, so their rotations commute and are applied together.
-__device__ __forceinline__ void rr_pair(int r, int k, int m, int* p, int* q) {
-  int a, bb;
-  if (k == 0) {
-    a = m - 1;
-    bb = r;
-  } else {
-    a = (r + k) % (m - 1);
-    bb = (r - k + (m - 1)) % (m - 1);
-  }
-  *p = min(a, bb);
-  *q = max(a, bb);
-}
-
-constexpr int kJacobiThreads = 512;
-
-// Parallel-order complex Jacobi on the Hermitian C of one step (one CTA).
-// For pivot (p,q), a = C_pp, b = C_qq, C_pq = r e^{i phi}, the rotation
-//   J = [[c, sigma], [-conj(sigma), c]],  sigma = s e^{i phi},
-// with (c, s) the symmetric Schur rotation of [[a, r], [r, b]] zeroes C_pq
-// (Golub & Van Loan Sec. 8.5 carried over to the Hermitian case). A round
-// applies m/2 disjoint rotations: C <- J^H C J block by block, Q <- Q J.
-// For odd n a phantom index n pairs with one real index per round (no-op).
-__global__ void __launch_bounds__(kJacobiThreads) k_jacobi(Batch b, double tol, int max_sweeps) {
-  const int t = blockIdx.x;
-  const int n = b.nst[t];
-  const int N = b.n_max;
-  if (b.status[t]) return;
-  double2* C = b.C + mat_off(t, N);
-  double2* Q = b.Q + mat_off(t, N);
-  const int m = n + (n & 1);
-  const int np = m / 2;
-
-  __shared__ int sp[kMaxStations / 2], sq[kMaxStations / 2];
-  __shared__ double sc[kMaxStations / 2];
-  __shared__ double2 ssig[kMaxStations / 2];
-  __shared__ double sdiag_p[kMaxStations / 2], sdiag_q[kMaxStations / 2];
-  __shared__ double red[kJacobiThreads / 32];
-  __shared__ double s_fro, s_off;
-
-  double fro = 0.0;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    int i = e % n, j = e / n;
-    Q[(size_t)i + (size_t)j * N] = make_double2(i == j ? 1.0 : 0.0, 0.0);
-    double2 v = C[(size_t)i + (size_t)j * N];
-    fro += v.x * v.x + v.y * v.y;
-  }
-  auto block_sum = [&](double v) -> double {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x < 32) {
-      s = (threadIdx.x < (int)(blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    }
-    __syncthreads();
-    return s;  // valid in warp 0
-  };
-  fro = block_sum(fro);
-  if (threadIdx.x == 0) s_fro = sqrt(fro);
-  __syncthreads();
-  const double thresh = tol * s_fro;
-
-  int sweep = 0;
-  bool converged = false;
-  for (;;) {
-    double off = 0.0;
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-      int i = e % n, j = e / n;
-      if (i != j) {
-        double2 v = C[(size_t)i + (size_t)j * N];
-        off += v.x * v.x + v.y * v.y;
-      }
-    }
-    off = block_sum(off);
-    if (threadIdx.x == 0) s_off = sqrt(off);
-    __syncthreads();
-    if (s_off <= thresh || s_fro == 0.0) {
-      converged = true;
-      break;
-    }
-    if (sweep >= max_sweeps) break;
-    ++sweep;
-    for (int r = 0; r < m - 1; ++r) {
-      for (int k = threadIdx.x; k < np; k += blockDim.x) {
-        int p, q;
-        rr_pair(r, k, m, &p, &q);
-        sp[k] = p;
-        sq[k] = q;
-        double c = 1.0;
-        double2 sig = make_double2(0.0, 0.0);
-        double dp = C[(size_t)p + (size_t)p * N].x, dq = 0.0;  // p < n always
-        if (q < n) {
-          const double a = dp;
-          const double bq = C[(size_t)q + (size_t)q * N].x;
-          const double2 x = C[(size_t)p + (size_t)q * N];
-          const double rr = hypot(x.x, x.y);
-          dq = bq;
-          if (rr > 0.0) {
-            double tau = (bq - a) / (2.0 * rr);
-            double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + hypot(1.0, tau));
-            c = 1.0 / sqrt(1.0 + tt * tt);
-            double s = tt * c;
-            sig = make_double2(s * x.x / rr, s * x.y / rr);
-            dp = a - tt * rr;
-            dq = bq + tt * rr;
-          }
-        }
-        sc[k] = c;
-        ssig[k] = sig;
-        sdiag_p[k] = dp;
-        sdiag_q[k] = dq;
-      }
-      __syncthreads();
-      // C <- J^H C J on every 2x2 block (pair k1 rows, pair k2 columns)
-      for (int e = threadIdx.x; e < np * np; e += blockDim.x) {
-        const int k1 = e % np, k2 = e / np;
-        const int p1 = sp[k1], q1 = sq[k1], p2 = sp[k2], q2 = sq[k2];
-        const bool v1 = q1 < n, v2 = q2 < n;
-        if (k1 == k2) {
-          C[(size_t)p1 + (size_t)p1 * N] = make_double2(sdiag_p[k1], 0.0);
-          if (v1) {
-            C[(size_t)q1 + (size_t)q1 * N] = make_double2(sdiag_q[k1], 0.0);
-            C[(size_t)p1 + (size_t)q1 * N] = make_double2(0.0, 0.0);
-            C[(size_t)q1 + (size_t)p1 * N] = make_double2(0.0, 0.0);
-          }
-          continue;
-        }
-        const double c1 = sc[k1], c2 = sc[k2];
-        const double2 g1 = ssig[k1], g2 = ssig[k2];
-        double2 x11 = C[(size_t)p1 + (size_t)p2 * N];
-        double2 x12 = v2 ? C[(size_t)p1 + (size_t)q2 * N] : make_double2(0.0, 0.0);
-        double2 x21 = v1 ? C[(size_t)q1 + (size_t)p2 * N] : make_double2(0.0, 0.0);
-        double2 x22 = (v1 && v2) ? C[(size_t)q1 + (size_t)q2 * N] : make_double2(0.0, 0.0);
-        // Y = X J2: col p2 -> c2 x_p2 - conj(g2) x_q2 ; col q2 -> g2 x_p2 + c2 x_q2
-        double2 y11 = csub(cscale(x11, c2), cmulc(x12, g2));
-        double2 y12 = cadd(cmul(x11, g2), cscale(x12, c2));
-        double2 y21 = csub(cscale(x21, c2), cmulc(x22, g2));
-        double2 y22 = cadd(cmul(x21, g2), cscale(x22, c2));
-        // Z = J1^H Y: row p1 -> c1 y_p1 - g1 y_q1 ; row q1 -> conj(g1) y_p1 + c1 y_q1
-        double2 z11 = csub(cscale(y11, c1), cmul(g1, y21));
-        double2 z12 = csub(cscale(y12, c1), cmul(g1, y22));
-        double2 g1c = make_double2(g1.x, -g1.y);
-        double2 z21 = cadd(cmul(g1c, y11), cscale(y21, c1));
-        double2 z22 = cadd(cmul(g1c, y12), cscale(y22, c1));
-        C[(size_t)p1 + (size_t)p2 * N] = z11;
-        if (v2) C[(size_t)p1 + (size_t)q2 * N] = z12;
-        if (v1) C[(size_t)q1 + (size_t)p2 * N] = z21;
-        if (v1 && v2) C[(size_t)q1 + (size_t)q2 * N] = z22;
-      }
-      // Q <- Q J on every row and pair
-      for (int e = threadIdx.x; e < n * np; e += blockDim.x) {
-        const int i = e % n, k = e / n;
-        const int p = sp[k], q = sq[k];
-        if (q >= n) continue;
-        const double c = sc[k];
-        const double2 g = ssig[k];
-        double2 a = Q[(size_t)i + (size_t)p * N];
-        double2 bq = Q[(size_t)i + (size_t)q * N];
-        Q[(size_t)i + (size_t)p * N] = csub(cscale(a, c), cmulc(bq, g));
-        Q[(size_t)i + (size_t)q * N] = cadd(cmul(a, g), cscale(bq, c));
-      }
-      __syncthreads();
-    }
-  }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) b.mu[(size_t)t * N + i] = C[(size_t)i + (size_t)i * N].x;
-  if (threadIdx.x == 0) {
-    b.sweeps[t] = sweep;
-    if (!converged) b.status[t] |= kStatusNotConverged;
-  }
-}
-
 // ---------------------------------------------------------------- select + pack
 
 // Keep the n_eig algebraically largest eigenvalues (descending, ties by lower
@@ -500,7 +313,17 @@ void launch_reduce(const Batch& b, int gram_identity, cudaStream_t s) {
 }
 
 void launch_jacobi(const Batch& b, double tol, int max_sweeps, cudaStream_t s) {
-  k_jacobi<<<b.T, kJacobiThreads, 0, s>>>(b, tol, max_sweeps);
+  JacobiArgs a;
+  a.C = b.C;
+  a.Q = b.Q;
+  a.mu = b.mu;
+  a.status = b.status;
+  a.sweeps = b.sweeps;
+  a.n = b.nst;
+  a.ld = b.n_max;
+  a.stride = (size_t)b.n_max * b.n_max;
+  a.report_nonconv = 1;
+  launch_jacobi_args(a, b.T, false, tol, max_sweeps, s);
 }
 
 void launch_select(const Batch& b, int n_level, const double* d_bounds, int filter, cudaStream_t s) {

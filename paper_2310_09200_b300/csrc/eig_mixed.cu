@@ -1,0 +1,390 @@
+// eig_mixed.cu — mixed-precision generalised eigensolve (BIPP_EIG_MIXED).
+//
+// Same result as the FP64 Jacobi of Sec. 2.3 (Eq. eigenvaleq) for the pairs
+// that are kept, at a fraction of the FP64 work, which matters on B300 where
+// the FP64 pipe runs at 1/58 of the FP32 rate:
+//   1. the reduced matrix C = L^{-1} V L^{-T} (formed in FP64) is rounded to
+//      FP32 and diagonalised by the same parallel-order Jacobi in FP32:
+//      C ~ Q32 diag(mu32) Q32^H, accurate to ~1e-6;
+//   2. the kp = min(n, n_eig + 16) leading approximate eigenvectors X are
+//      refined in FP64 with the operator C itself:
+//        orthonormalise X (Cholesky QR), Y = C X, H = X^H Y,
+//        H = U diag(theta) U^H (FP64 Jacobi on kp x kp), X <- X U, Y <- Y U,
+//        R = Y - X diag(theta) (residuals),
+//        X <- X - Q32 T,  T[m, j] = (Q32^H R)[m, j] / (mu32[m] - theta[j]) for
+//        the directions m outside the kept set (the FP32 decomposition acts as
+//        an approximate inverse of C - theta I on the complement),
+//      repeated a fixed number of times; each pass contracts the error by the
+//      FP32 preconditioner's relative accuracy over the spectral gap.
+//   3. theta and X replace the Jacobi eigenvalues and eigenvectors; the
+//      residual of the last pass is checked against 1e3 * jacobi_tol * ||C||_F.
+// FP64 cost per pass is O(n^2 kp) (two n x n by n x kp products) instead of
+// the O(n^3) of every FP64 Jacobi sweep.
+#include <math.h>
+
+#include <algorithm>
+
+#include "bipp_internal.cuh"
+#include "jacobi.cuh"
+
+namespace bipp {
+namespace {
+
+constexpr int kPad = 16;       // extra leading pairs refined beyond n_eig
+constexpr int kPasses = 4;     // refinement passes
+constexpr int GT = 32, GK = 16;
+static_assert(4 + 14 * (kPasses - 1) + 10 == kMixedLaunches, "launch count of the mixed eigensolver");
+
+// Shape codes of the batched complex products: dimension = n_st or kp of the problem.
+enum Dim { DN = 0, DKP = 1 };
+
+__device__ __forceinline__ int dim_of(int code, int n, int kp) { return code == DN ? n : kp; }
+
+__device__ __forceinline__ double2 ld_c(const double2* p, size_t i) { return p[i]; }
+__device__ __forceinline__ double2 ld_c(const float2* p, size_t i) {
+  const float2 v = p[i];
+  return make_double2(v.x, v.y);
+}
+
+// out[i, j] = sum_k op(A)[i, k] B[k, j]  (FP64 accumulate), op = identity or
+// conjugate transpose; all operands column-major with per-problem strides.
+template <typename TA, bool CONJ_T>
+__global__ void k_zgemm(const int* nst, const int* kp, int mc, int nc, int kc, const TA* A, size_t sa, int lda,
+                        const double2* B, size_t sb, int ldb, double2* out, size_t so, int ldo,
+                        const int* status) {
+  const int t = blockIdx.z;
+  if (status[t]) return;
+  const int n = nst[t], k_p = kp[t];
+  const int M = dim_of(mc, n, k_p), NN = dim_of(nc, n, k_p), K = dim_of(kc, n, k_p);
+  const int i0 = blockIdx.x * GT, j0 = blockIdx.y * GT;
+  if (i0 >= M || j0 >= NN) return;
+  A += (size_t)t * sa;
+  B += (size_t)t * sb;
+  out += (size_t)t * so;
+  __shared__ double2 sA[GK][GT + 1];
+  __shared__ double2 sB[GK][GT + 1];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  double2 acc[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) acc[u] = make_double2(0.0, 0.0);
+  for (int k0 = 0; k0 < K; k0 += GK) {
+    for (int e = threadIdx.x; e < GK * GT; e += blockDim.x) {
+      const int kk = e / GT, ii = e % GT, k = k0 + kk;
+      const int i = i0 + ii, j = j0 + ii;
+      double2 a = make_double2(0.0, 0.0), bv = make_double2(0.0, 0.0);
+      if (k < K && i < M) {
+        if (CONJ_T) {
+          a = ld_c(A, (size_t)k + (size_t)i * lda);  // op(A)[i,k] = conj(A[k,i])
+          a.y = -a.y;
+        } else {
+          a = ld_c(A, (size_t)i + (size_t)k * lda);
+        }
+      }
+      if (k < K && j < NN) bv = B[(size_t)k + (size_t)j * ldb];
+      sA[kk][ii] = a;
+      sB[kk][ii] = bv;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      const double2 a = sA[kk][tx];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const double2 bv = sB[kk][ty + 8 * u];
+        acc[u].x = fma(a.x, bv.x, fma(-a.y, bv.y, acc[u].x));
+        acc[u].y = fma(a.x, bv.y, fma(a.y, bv.x, acc[u].y));
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = i0 + tx, j = j0 + ty + 8 * u;
+    if (i < M && j < NN) out[(size_t)i + (size_t)j * ldo] = acc[u];
+  }
+}
+
+// C32 = fp32(C): written into the first half of the problem's X buffer.
+__global__ void k_mx_tof32(Batch b) {
+  const int t = blockIdx.y;
+  if (b.status[t]) return;
+  const int n = b.nst[t], N = b.n_max;
+  const double2* C = b.C + (size_t)t * N * N;
+  float2* C32 = reinterpret_cast<float2*>(b.X + (size_t)t * N * N);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
+    const int i = e % n, j = e / n;
+    const double2 v = C[(size_t)i + (size_t)j * N];
+    C32[(size_t)i + (size_t)j * N] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+// Rank the FP32 eigenvalues, mark the kp leading ones (sel[m] = rank or -1),
+// copy their FP32 eigenvectors into X (FP64), record ||C||_F.
+__global__ void k_mx_pick(Batch b, MixedWs w) {
+  const int t = blockIdx.x;
+  if (b.status[t]) return;
+  const int n = b.nst[t], N = b.n_max;
+  const int kp = min(n, b.neig[t] + kPad);
+  const double* mu = b.mu + (size_t)t * N;
+  int* sel = w.sel + (size_t)t * N;
+  const float2* Q32 = reinterpret_cast<const float2*>(b.X + (size_t)t * N * N) + (size_t)N * N;
+  double2* X = b.Q + (size_t)t * N * N;
+  __shared__ double red[256];
+  double s2 = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double mi = mu[i];
+    s2 += mi * mi;
+    int rank = 0;
+    for (int j = 0; j < n; ++j) {
+      const double mj = mu[j];
+      rank += (mj > mi) || (mj == mi && j < i);
+    }
+    sel[i] = rank < kp ? rank : -1;
+  }
+  red[threadIdx.x] = s2;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    w.kp[t] = kp;
+    w.cnorm[t] = sqrt(red[0]);
+  }
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e % n, m = e / n;  // row i of FP32 eigenvector m
+    const int r = sel[m];
+    if (r >= 0) {
+      const float2 v = Q32[(size_t)i + (size_t)m * N];
+      X[(size_t)i + (size_t)r * N] = make_double2(v.x, v.y);
+    }
+  }
+}
+
+// S = R^H R (Cholesky, upper R) of the kp x kp Gram matrix of X, then
+// W = R^{-1} (upper), so that X W has orthonormal columns. One CTA per step.
+__global__ void k_mx_cholinv(Batch b, MixedWs w, const double2* S0, double2* W0, size_t stride, int ld) {
+  const int t = blockIdx.x;
+  if (b.status[t]) return;
+  const int kp = w.kp[t];
+  double2* S = const_cast<double2*>(S0) + (size_t)t * stride;
+  double2* W = W0 + (size_t)t * stride;
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  // in-place upper Cholesky S = R^H R (R stored in the upper triangle of S)
+  for (int j = 0; j < kp; ++j) {
+    if (threadIdx.x == 0) {
+      double d = S[j + (size_t)j * ld].x;
+      for (int k = 0; k < j; ++k) {
+        const double2 r = S[k + (size_t)j * ld];
+        d -= r.x * r.x + r.y * r.y;
+      }
+      if (!(d > 0.0)) bad = 1;
+      S[j + (size_t)j * ld] = make_double2(sqrt(fmax(d, 1e-300)), 0.0);
+    }
+    __syncthreads();
+    const double rjj = S[j + (size_t)j * ld].x;
+    for (int c = j + 1 + threadIdx.x; c < kp; c += blockDim.x) {
+      // R[j, c] = (S[j, c] - sum_k conj(R[k, j]) R[k, c]) / R[j, j]
+      double2 s = S[j + (size_t)c * ld];
+      for (int k = 0; k < j; ++k) {
+        const double2 a = S[k + (size_t)j * ld], bb = S[k + (size_t)c * ld];
+        s.x -= a.x * bb.x + a.y * bb.y;
+        s.y -= a.x * bb.y - a.y * bb.x;
+      }
+      S[j + (size_t)c * ld] = make_double2(s.x / rjj, s.y / rjj);
+    }
+    __syncthreads();
+  }
+  // W = R^{-1}: column c solves R w = e_c (back substitution), one thread per column
+  for (int c = threadIdx.x; c < kp; c += blockDim.x) {
+    for (int i = kp - 1; i >= 0; --i) {
+      double2 s = make_double2(i == c ? 1.0 : 0.0, 0.0);
+      if (i < c || i == c) {
+        for (int k = i + 1; k <= c; ++k) {
+          const double2 r = S[i + (size_t)k * ld], x = W[k + (size_t)c * ld];
+          s.x -= r.x * x.x - r.y * x.y;
+          s.y -= r.x * x.y + r.y * x.x;
+        }
+        const double rii = S[i + (size_t)i * ld].x;
+        W[i + (size_t)c * ld] = (i <= c) ? make_double2(s.x / rii, s.y / rii) : make_double2(0.0, 0.0);
+      } else {
+        W[i + (size_t)c * ld] = make_double2(0.0, 0.0);
+      }
+    }
+  }
+  if (threadIdx.x == 0 && bad) b.status[t] |= kStatusNotConverged;
+}
+
+// H <- (H + H^H)/2 on the kp x kp block.
+__global__ void k_mx_herm(Batch b, MixedWs w, double2* H0, size_t stride, int ld) {
+  const int t = blockIdx.x;
+  if (b.status[t]) return;
+  const int kp = w.kp[t];
+  double2* H = H0 + (size_t)t * stride;
+  for (int e = threadIdx.x; e < kp * kp; e += blockDim.x) {
+    const int i = e % kp, j = e / kp;
+    if (i > j) continue;
+    const double2 a = H[i + (size_t)j * ld], c = H[j + (size_t)i * ld];
+    double2 h = make_double2(0.5 * (a.x + c.x), 0.5 * (a.y - c.y));
+    if (i == j) h.y = 0.0;
+    H[i + (size_t)j * ld] = h;
+    H[j + (size_t)i * ld] = make_double2(h.x, -h.y);
+  }
+}
+
+// R = Y - X diag(theta) in place of Y; rnorm[j] = ||R[:, j]||.
+__global__ void k_mx_resid(Batch b, MixedWs w, const double2* X0, double2* Y0, size_t stride) {
+  const int t = blockIdx.y, j = blockIdx.x;
+  if (b.status[t]) return;
+  const int n = b.nst[t], N = b.n_max, kp = w.kp[t];
+  if (j >= kp) return;
+  const double th = w.theta[(size_t)t * w.KP + j];
+  const double2* X = X0 + (size_t)t * stride + (size_t)j * N;
+  double2* Y = Y0 + (size_t)t * stride + (size_t)j * N;
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double2 x = X[i], y = Y[i];
+    const double2 r = make_double2(y.x - th * x.x, y.y - th * x.y);
+    Y[i] = r;
+    s += r.x * r.x + r.y * r.y;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) w.rnorm[(size_t)t * w.KP + j] = sqrt(red[0]);
+}
+
+// T[m, j] /= (mu32[m] - theta[j]) for directions outside the kept set, 0 inside.
+__global__ void k_mx_scale(Batch b, MixedWs w, double2* T0, size_t stride) {
+  const int t = blockIdx.y;
+  if (b.status[t]) return;
+  const int n = b.nst[t], N = b.n_max, kp = w.kp[t];
+  const double* mu = b.mu + (size_t)t * N;
+  const int* sel = w.sel + (size_t)t * N;
+  double2* T = T0 + (size_t)t * stride;
+  const double eps = 1e-13 * w.cnorm[t];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * kp; e += gridDim.x * blockDim.x) {
+    const int m = e % n, j = e / n;
+    double2 v = T[(size_t)m + (size_t)j * N];
+    const double den = mu[m] - w.theta[(size_t)t * w.KP + j];
+    if (sel[m] >= 0 || fabs(den) <= eps) v = make_double2(0.0, 0.0);
+    else v = make_double2(v.x / den, v.y / den);
+    T[(size_t)m + (size_t)j * N] = v;
+  }
+}
+
+// X <- X - D on the n x kp block.
+__global__ void k_mx_sub(Batch b, MixedWs w, double2* X0, const double2* D0, size_t stride) {
+  const int t = blockIdx.y;
+  if (b.status[t]) return;
+  const int n = b.nst[t], N = b.n_max, kp = w.kp[t];
+  double2* X = X0 + (size_t)t * stride;
+  const double2* D = D0 + (size_t)t * stride;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * kp; e += gridDim.x * blockDim.x) {
+    const int i = e % n, j = e / n;
+    const double2 x = X[(size_t)i + (size_t)j * N], d = D[(size_t)i + (size_t)j * N];
+    X[(size_t)i + (size_t)j * N] = make_double2(x.x - d.x, x.y - d.y);
+  }
+}
+
+// Hand theta / X to the selection stage (which ranks b.mu and reads the
+// columns of b.Q): mu[j] = theta[j] for j < kp, -inf beyond; check the last
+// residuals of the n_eig leading pairs.
+__global__ void k_mx_final(Batch b, MixedWs w, double rtol) {
+  const int t = blockIdx.x;
+  if (b.status[t]) return;
+  const int n = b.nst[t], N = b.n_max, kp = w.kp[t];
+  double* mu = b.mu + (size_t)t * N;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) mu[j] = (j < kp) ? w.theta[(size_t)t * w.KP + j] : -INFINITY;
+  if (threadIdx.x == 0) {
+    // residual of the pairs that can be kept: rank by theta, check the top n_eig
+    const int K = b.neig[t];
+    double worst = 0.0;
+    for (int j = 0; j < kp; ++j) {
+      int rank = 0;
+      const double tj = w.theta[(size_t)t * w.KP + j];
+      for (int i = 0; i < kp; ++i) {
+        const double ti = w.theta[(size_t)t * w.KP + i];
+        rank += (ti > tj) || (ti == tj && i < j);
+      }
+      if (rank < K) worst = fmax(worst, w.rnorm[(size_t)t * w.KP + j]);
+    }
+    if (!(worst <= rtol * w.cnorm[t]) || w.st2[t]) b.status[t] |= kStatusNotConverged;
+  }
+}
+
+template <typename TA, bool CT>
+void zgemm(const Batch& b, const MixedWs& w, int mc, int nc, int kc, int mmax, int nmax, const TA* A, size_t sa,
+           int lda, const double2* B, size_t sb, int ldb, double2* out, size_t so, int ldo, cudaStream_t s) {
+  dim3 grd((mmax + GT - 1) / GT, (nmax + GT - 1) / GT, b.T);
+  k_zgemm<TA, CT><<<grd, 256, 0, s>>>(b.nst, w.kp, mc, nc, kc, A, sa, lda, B, sb, ldb, out, so, ldo, b.status);
+}
+
+}  // namespace
+
+bool eig_mixed_fits(int N, int KP) { return 4LL * N * KP + 3LL * KP * KP <= (long long)N * N; }
+
+void launch_eig_mixed(const Batch& b, const MixedWs& w, double tol, int max_sweeps, cudaStream_t s) {
+  const int N = b.n_max, KP = w.KP, T = b.T;
+  const size_t NN = (size_t)N * N;
+  // 1. FP32 Jacobi on all pairs (C32, Q32 in the two halves of the X buffer)
+  k_mx_tof32<<<dim3(std::max(1, std::min(64, (N * N + 255) / 256)), T), 256, 0, s>>>(b);
+  JacobiArgs a;
+  a.C = reinterpret_cast<float2*>(b.X);
+  a.Q = reinterpret_cast<float2*>(b.X) + NN;
+  a.mu = b.mu;
+  a.status = b.status;
+  a.sweeps = b.sweeps;
+  a.n = b.nst;
+  a.ld = N;
+  a.stride = 2 * NN;
+  a.report_nonconv = 0;
+  launch_jacobi_args(a, T, true, 1e-6, std::min(max_sweeps, 15), s);
+  const float2* Q32 = reinterpret_cast<const float2*>(b.X) + NN;
+  // 2. FP64 refinement of the kp leading pairs; buffers inside the Q buffer
+  double2* P0 = b.Q;                       // X (final eigenvectors), n x kp, ld N
+  double2* P1 = b.Q + (size_t)N * KP;      // orthonormalised X / T
+  double2* P2 = b.Q + (size_t)2 * N * KP;  // Y = C X / D
+  double2* P3 = b.Q + (size_t)3 * N * KP;  // Y U / R
+  double2* Hs = b.Q + (size_t)4 * N * KP;  // S, then H (kp x kp, ld KP)
+  double2* Us = Hs + (size_t)KP * KP;      // rotations of H
+  double2* Ws = Us + (size_t)KP * KP;      // R^{-1}
+  k_mx_pick<<<T, 256, 0, s>>>(b, w);
+  JacobiArgs h;
+  h.C = Hs;
+  h.Q = Us;
+  h.mu = w.theta;
+  h.status = w.st2;
+  h.sweeps = w.sw2;
+  h.n = w.kp;
+  h.ld = KP;
+  h.stride = NN;
+  h.report_nonconv = 1;
+  cudaMemsetAsync(w.st2, 0, sizeof(int) * T, s);
+  for (int pass = 0; pass < kPasses; ++pass) {
+    zgemm<double2, true>(b, w, DKP, DKP, DN, KP, KP, P0, NN, N, P0, NN, N, Hs, NN, KP, s);    // S = X^H X
+    k_mx_cholinv<<<T, 128, 0, s>>>(b, w, Hs, Ws, NN, KP);                                      // W = R^{-1}
+    zgemm<double2, false>(b, w, DN, DKP, DKP, N, KP, P0, NN, N, Ws, NN, KP, P1, NN, N, s);   // X1 = X W
+    zgemm<double2, false>(b, w, DN, DKP, DN, N, KP, b.C, NN, N, P1, NN, N, P2, NN, N, s);    // Y = C X1
+    zgemm<double2, true>(b, w, DKP, DKP, DN, KP, KP, P1, NN, N, P2, NN, N, Hs, NN, KP, s);   // H = X1^H Y
+    k_mx_herm<<<T, 256, 0, s>>>(b, w, Hs, NN, KP);
+    launch_jacobi_args(h, T, false, 1e-15, 60, s);                                            // H = U th U^H
+    zgemm<double2, false>(b, w, DN, DKP, DKP, N, KP, P1, NN, N, Us, NN, KP, P0, NN, N, s);   // X = X1 U
+    zgemm<double2, false>(b, w, DN, DKP, DKP, N, KP, P2, NN, N, Us, NN, KP, P3, NN, N, s);   // Y U
+    k_mx_resid<<<dim3(KP, T), 256, 0, s>>>(b, w, P0, P3, NN);                                // R = YU - X th
+    if (pass == kPasses - 1) break;
+    zgemm<float2, true>(b, w, DN, DKP, DN, N, KP, Q32, 2 * NN, N, P3, NN, N, P1, NN, N, s);  // T = Q32^H R
+    k_mx_scale<<<dim3(std::max(1, (N * KP + 255) / 256 / 8), T), 256, 0, s>>>(b, w, P1, NN);
+    zgemm<float2, false>(b, w, DN, DKP, DN, N, KP, Q32, 2 * NN, N, P1, NN, N, P2, NN, N, s); // D = Q32 T
+    k_mx_sub<<<dim3(std::max(1, (N * KP + 255) / 256 / 8), T), 256, 0, s>>>(b, w, P0, P2, NN);
+  }
+  k_mx_final<<<T, 256, 0, s>>>(b, w, 1e3 * tol);
+}
+
+}  // namespace bipp
