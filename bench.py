@@ -44,6 +44,26 @@ SMS = 148
 SM_MAX_GHZ = 2.032
 FP64_PEAK_FLOPS = SMS * 2 * 2 * SM_MAX_GHZ * 1e9
 FP32_PEAK_FLOPS = SMS * 128 * 2 * SM_MAX_GHZ * 1e9
+# __sincosf pairs per second measured on a B300 of this machine (148 SMs at 2032 MHz:
+# 4.45e12 MUFU results/s, i.e. 14.8 per SM per clock).
+MUFU_SINCOS_PER_S = 2.23e12
+
+
+DTYPES = {"fp64": "f64", "fp32": "f64 eig + f32 synth",
+          "split_bf16": "f64 eig + bf16x3 tensor synth (f32 acc)", "split_fp16": "f64 eig + f16x3 tensor synth (f32 acc)"}
+
+
+EIG_DESC = {"jacobi64": "fp64 parallel-order Jacobi (off(C) <= 1e-13 ||C||_F)",
+            "mixed": ("fp32 block Jacobi (32-index blocks, off(C) <= 1e-5 ||C||_F), then fp64 Rayleigh-Ritz "
+                      "refinement of the n_eig+16 leading pairs (residual <= 1e-10 ||C||_F)")}
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {"bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0, "hbm_gbs": 6400.0}
 
 
 def parse():
@@ -52,12 +72,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--precision", default="split_fp16", choices=["fp64", "fp32", "split_bf16", "split_fp16"])
     ap.add_argument("--n-t", type=int, default=100, help="time steps per imaging job")
     ap.add_argument("--side", type=int, default=1024, help="image side in pixels")
     ap.add_argument("--n-st", type=int, default=0, help="keep only the first n stations (small profiling cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--eig", default="mixed", choices=["jacobi64", "mixed"],
+                    help="eigensolver: FP64 Jacobi, or FP32 Jacobi + FP64 refinement of the kept pairs")
     return ap.parse_args()
 
 
@@ -78,7 +100,8 @@ def config_dict(args, inp, precision):
                      f"{inp.n_t} time steps per job, wl 2 m"),
         "n_st": int(inp.st_xyz[0].shape[0]), "n_pix": int(inp.n_pix), "n_eig": int(inp.n_eig),
         "n_level": int(inp.n_level), "n_t": int(inp.n_t), "synthesis": precision,
-        "eigensolve": "fp64 parallel-order Jacobi",
+        "eigensolve": EIG_DESC.get(getattr(args, "eig", "jacobi64"), "fp64 parallel-order Jacobi")
+        if precision != "fp64 (oracle)" else "fp64 cyclic Jacobi (oracle)",
         "l2": "inputs larger than L2 (visibilities 400 MB per job)",
     }
 
@@ -209,13 +232,14 @@ def ours_main(args, ws, rank, local):
     inp = workload(args)
     n_st = inp.st_xyz[0].shape[0]
     # level bounds: the library's own parameter-estimation pre-pass on every 10th step
-    bounds, _ = bipp_ss.estimate_level_bounds(inp.st_xyz[::10], inp.vis[::10], inp.wl, inp.n_eig, inp.n_level)
+    bounds, _ = bipp_ss.estimate_level_bounds(inp.st_xyz[::10], inp.vis[::10], inp.wl, inp.n_eig, inp.n_level,
+                                              eig_mode=args.eig)
     nst, N, st, V = bipp_ss.pack_batch(inp.st_xyz, inp.vis)
     d_st = torch.from_numpy(st).to(f"cuda:{local}")
     d_V = torch.from_numpy(V).to(f"cuda:{local}")
     stream = torch.cuda.Stream()
     ss = bipp_ss.StandardSynthesis(inp.pix, inp.wl, bounds, n_eig=inp.n_eig, precision=args.precision,
-                                   device=local)
+                                   device=local, eig_mode=args.eig)
 
     def one_step():
         bipp_ss.bipp_ss_collect_device(ss.h, nst, d_st, d_V, stream=stream)
@@ -257,15 +281,50 @@ def ours_main(args, ws, rank, local):
     eig_ms, syn_ms = stage[1] / K, stage[3] / K
     jac_flops = 20.0 * n_st ** 2 * (n_st - 1) * (sweeps / K)  # Hermitian two-sided rotations + Q, per launch
     syn_flops = 8.0 * prods  # one complex multiply-add per product
-    roof_jacobi = {"kernel": "k_jacobi", "bound": "alu", "achieved": jac_flops / (eig_ms / 1e3) / 1e12,
-                   "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s", "traffic": None,
-                   "peak_note": "FP64 pipe, 148 SM x 2 DFMA/clk x 2 flop x 2.032 GHz"}
-    roof_jacobi["frac"] = roof_jacobi["achieved"] / roof_jacobi["peak"]
-    roof_synth = {"kernel": "k_synth_f32" if args.precision == "fp32" else "synth_tc", "bound": "alu",
-                  "achieved": syn_flops / (syn_ms / 1e3) / 1e12, "peak": FP32_PEAK_FLOPS / 1e12,
-                  "unit": "TFLOP/s", "traffic": None,
-                  "peak_note": "FP32 pipe, 148 SM x 128 FFMA/clk x 2 flop x 2.032 GHz"}
-    roof_synth["frac"] = roof_synth["achieved"] / roof_synth["peak"]
+    if args.eig == "jacobi64":
+        roof_jacobi = {"kernel": "k_jacobi_t<double>", "bound": "alu",
+                       "achieved": jac_flops / (eig_ms / 1e3) / 1e12, "peak": FP64_PEAK_FLOPS / 1e12,
+                       "unit": "TFLOP/s", "traffic": None,
+                       "peak_note": "FP64 pipe, 148 SM x 2 DFMA/clk x 2 flop x 2.032 GHz"}
+        roof_jacobi["frac"] = roof_jacobi["achieved"] / roof_jacobi["peak"]
+    else:
+        # FP32 sweeps on the FP32 pipe + FP64 refinement products on the FP64 pipe
+        kp = min(n_st, inp.n_eig + 16)
+        f64 = 8.0 * (10 * n_st ** 2 * kp + 20 * n_st * kp ** 2) * inp.n_t
+        # block sweep: (nb - 1) nb / 2 pivot steps, each R = U^H C[P, :] and Q[:, P] U (64 x 64 x n complex)
+        nb = -(-n_st // 32)
+        nb += nb & 1
+        jac_flops = (sweeps / K) * (nb - 1) * (nb // 2) * 2 * 8.0 * 64 * 64 * n_st
+        t_roof = jac_flops / FP32_PEAK_FLOPS + f64 / FP64_PEAK_FLOPS
+        roof_jacobi = {"kernel": "k_bjacobi32 + FP64 refinement", "bound": "alu",
+                       "achieved": (jac_flops + f64) / (eig_ms / 1e3) / 1e12, "peak": None, "unit": "TFLOP/s",
+                       "traffic": None, "frac": t_roof / (eig_ms / 1e3),
+                       "t_roof_ms": {"fp32_sweeps": jac_flops / FP32_PEAK_FLOPS * 1e3,
+                                     "fp64_refinement": f64 / FP64_PEAK_FLOPS * 1e3},
+                       "peak_note": ("frac = (FP32 sweep flops / FP32 peak + FP64 refinement flops / FP64 peak) / "
+                                     "measured time; peaks from unit counts x 2.032 GHz")}
+    if args.precision in ("fp32", "fp64"):
+        peak = FP32_PEAK_FLOPS if args.precision == "fp32" else FP64_PEAK_FLOPS
+        roof_synth = {"kernel": f"k_synth_{args.precision[-2:]}", "bound": "alu",
+                      "achieved": syn_flops / (syn_ms / 1e3) / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                      "traffic": None, "peak_note": "CUDA-core FMA pipe, unit count x 2 flop x 2.032 GHz"}
+        roof_synth["frac"] = roof_synth["achieved"] / roof_synth["peak"]
+    else:
+        # split GEMM: 3 tensor products per real multiply-add; T_roof = max(T_tensor, T_sfu)
+        peaks = measured_peaks()
+        r_tc = peaks.get("bf16_tflops_sustained", 1411.3) * 1e12
+        pairs = inp.n_pix * n_st * inp.n_t
+        t_tc = 3 * syn_flops / r_tc
+        t_sfu = pairs / MUFU_SINCOS_PER_S
+        roof_synth = {"kernel": "k_synth_tc", "bound": "tensor", "achieved": 3 * syn_flops / (syn_ms / 1e3) / 1e12,
+                      "peak": r_tc / 1e12, "unit": "TFLOP/s", "traffic": None,
+                      "frac": max(t_tc, t_sfu) / (syn_ms / 1e3),
+                      "frac_algorithmic_s1": (syn_flops / r_tc) / (syn_ms / 1e3),
+                      "t_roof_ms": {"tensor_split": t_tc * 1e3, "sfu_sincos": t_sfu * 1e3},
+                      "peak_note": ("of measured: cuBLAS bf16 sustained (FP16 dense rate is the same nominal); "
+                                    "frac = max(T_tensor(s=3), T_sfu) / measured time; "
+                                    f"SFU rate {MUFU_SINCOS_PER_S:.3g} sincos/s measured by a sin/cos "
+                                    "microbenchmark on this B300 pool")}
     dominant = roof_jacobi if eig_ms >= syn_ms else roof_synth
 
     # ---- end to end through the host-buffer C ABI (pinned host inputs, images read back)
@@ -303,7 +362,7 @@ def ours_main(args, ws, rank, local):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+                "vs_baseline": None, "dtype": DTYPES[args.precision].replace("f64 eig", "f32+f64 eig") if args.eig == "mixed" else DTYPES[args.precision], "data": "synthetic",
                 "config": config_dict(args, inp, args.precision),
                 "stage_ms_per_step": {"gram_chol_reduce": stage[0] / K, "jacobi": eig_ms,
                                       "select_pack": stage[2] / K, "synthesis": syn_ms},

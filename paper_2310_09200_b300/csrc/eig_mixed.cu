@@ -25,6 +25,7 @@
 #include <algorithm>
 
 #include "bipp_internal.cuh"
+#include "bjacobi.cuh"
 #include "jacobi.cuh"
 
 namespace bipp {
@@ -333,9 +334,10 @@ bool eig_mixed_fits(int N, int KP) { return 4LL * N * KP + 3LL * KP * KP <= (lon
 void launch_eig_mixed(const Batch& b, const MixedWs& w, double tol, int max_sweeps, cudaStream_t s) {
   const int N = b.n_max, KP = w.KP, T = b.T;
   const size_t NN = (size_t)N * N;
-  // 1. FP32 Jacobi on all pairs (C32, Q32 in the two halves of the X buffer)
+  // 1. FP32 block Jacobi on all pairs (C32, Q32 in the two halves of the X buffer);
+  //    one inner sweep per pivot block converges in as many block sweeps as two
   k_mx_tof32<<<dim3(std::max(1, std::min(64, (N * N + 255) / 256)), T), 256, 0, s>>>(b);
-  JacobiArgs a;
+  BJacobiArgs a;
   a.C = reinterpret_cast<float2*>(b.X);
   a.Q = reinterpret_cast<float2*>(b.X) + NN;
   a.mu = b.mu;
@@ -344,8 +346,9 @@ void launch_eig_mixed(const Batch& b, const MixedWs& w, double tol, int max_swee
   a.n = b.nst;
   a.ld = N;
   a.stride = 2 * NN;
-  a.report_nonconv = 0;
-  launch_jacobi_args(a, T, true, 1e-6, std::min(max_sweeps, 15), s);
+  const size_t smem = bjacobi_smem();
+  cudaFuncSetAttribute(k_bjacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_bjacobi32<<<T, kBJThreads, smem, s>>>(a, 1e-5, std::min(max_sweeps, 12), 1);
   const float2* Q32 = reinterpret_cast<const float2*>(b.X) + NN;
   // 2. FP64 refinement of the kp leading pairs; buffers inside the Q buffer
   double2* P0 = b.Q;                       // X (final eigenvectors), n x kp, ld N
