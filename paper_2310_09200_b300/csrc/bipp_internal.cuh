@@ -81,7 +81,7 @@ void launch_jacobi(const Batch& b, double tol, int max_sweeps, cudaStream_t s);
 // pairs); needs the X and Q buffers of the batch as scratch, which fits when
 // eig_mixed_fits(n_max, KP).
 bool eig_mixed_fits(int n_max, int KP);
-constexpr int kMixedLaunches = 56;  // kernels launched by launch_eig_mixed
+constexpr int kMixedLaunches = 59;  // kernels launched by launch_eig_mixed
 void launch_eig_mixed(const Batch& b, const MixedWs& w, double tol, int max_sweeps, cudaStream_t s);
 // d_bounds: per channel, n_level x 2 column-major blocks.
 void launch_select(const Batch& b, int n_level, const double* d_bounds, int filter, cudaStream_t s);

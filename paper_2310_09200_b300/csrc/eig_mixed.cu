@@ -4,8 +4,8 @@
 // that are kept, at a fraction of the FP64 work, which matters on B300 where
 // the FP64 pipe runs at 1/58 of the FP32 rate:
 //   1. the reduced matrix C = L^{-1} V L^{-T} (formed in FP64) is rounded to
-//      FP32 and diagonalised by the same parallel-order Jacobi in FP32:
-//      C ~ Q32 diag(mu32) Q32^H, accurate to ~1e-6;
+//      FP32 and diagonalised by a block Jacobi in FP32 (bjacobi.cuh):
+//      C ~ Q32 diag(mu32) Q32^H, off-diagonal mass <= 1e-5 ||C||_F;
 //   2. the kp = min(n, n_eig + 16) leading approximate eigenvectors X are
 //      refined in FP64 with the operator C itself:
 //        orthonormalise X (Cholesky QR), Y = C X, H = X^H Y,
@@ -13,12 +13,16 @@
 //        R = Y - X diag(theta) (residuals),
 //        X <- X - Q32 T,  T[m, j] = (Q32^H R)[m, j] / (mu32[m] - theta[j]) for
 //        the directions m outside the kept set (the FP32 decomposition acts as
-//        an approximate inverse of C - theta I on the complement),
-//      repeated a fixed number of times; each pass contracts the error by the
-//      FP32 preconditioner's relative accuracy over the spectral gap.
+//        an approximate inverse of C - theta I on the complement); the two
+//        products with Q32 run in FP32, as they carry no more accuracy than
+//        Q32 itself, while the residual they correct is formed in FP64;
+//      each pass contracts the error by the FP32 preconditioner's relative
+//      accuracy over the spectral gap (about 3e-5 per pass here); a problem
+//      whose kept residuals fall below 10 * jacobi_tol * ||C||_F stops early,
+//      the rest run at most kPasses passes.
 //   3. theta and X replace the Jacobi eigenvalues and eigenvectors; the
 //      residual of the last pass is checked against 1e3 * jacobi_tol * ||C||_F.
-// FP64 cost per pass is O(n^2 kp) (two n x n by n x kp products) instead of
+// FP64 cost per pass is O(n^2 kp) (one n x n by n x kp product) instead of
 // the O(n^3) of every FP64 Jacobi sweep.
 #include <math.h>
 
@@ -32,29 +36,40 @@ namespace bipp {
 namespace {
 
 constexpr int kPad = 16;       // extra leading pairs refined beyond n_eig
-constexpr int kPasses = 4;     // refinement passes
+constexpr int kPasses = 4;     // refinement passes at most
+constexpr int kMxDone = 8;     // st2 bit: residual met the early-exit bound, later passes skip the step
 constexpr int GT = 32, GK = 16;
-static_assert(4 + 14 * (kPasses - 1) + 10 == kMixedLaunches, "launch count of the mixed eigensolver");
+static_assert(4 + 15 * (kPasses - 1) + 10 == kMixedLaunches, "launch count of the mixed eigensolver");
 
 // Shape codes of the batched complex products: dimension = n_st or kp of the problem.
 enum Dim { DN = 0, DKP = 1 };
 
 __device__ __forceinline__ int dim_of(int code, int n, int kp) { return code == DN ? n : kp; }
 
-__device__ __forceinline__ double2 ld_c(const double2* p, size_t i) { return p[i]; }
-__device__ __forceinline__ double2 ld_c(const float2* p, size_t i) {
-  const float2 v = p[i];
-  return make_double2(v.x, v.y);
+__device__ __forceinline__ void ld_c(const double2* p, size_t i, double2* v) { *v = p[i]; }
+__device__ __forceinline__ void ld_c(const float2* p, size_t i, double2* v) {
+  const float2 f = p[i];
+  *v = make_double2(f.x, f.y);
+}
+__device__ __forceinline__ void ld_c(const float2* p, size_t i, float2* v) { *v = p[i]; }
+
+// Problem t takes no further part in the refinement: an error status, or its
+// residual already met the early-exit bound.
+__device__ __forceinline__ bool mx_skip(const int* status, const int* st2, int t) {
+  return status[t] || (st2[t] & kMxDone);
 }
 
-// out[i, j] = sum_k op(A)[i, k] B[k, j]  (FP64 accumulate), op = identity or
-// conjugate transpose; all operands column-major with per-problem strides.
-template <typename TA, bool CONJ_T>
+// out[i, j] = sum_k op(A)[i, k] B[k, j], op = identity or conjugate transpose;
+// all operands column-major with per-problem strides. R is the arithmetic
+// (FP64 for the Rayleigh-Ritz products, FP32 for the preconditioner products),
+// A may be stored in FP32 either way.
+template <typename R, typename TA, bool CONJ_T>
 __global__ void k_zgemm(const int* nst, const int* kp, int mc, int nc, int kc, const TA* A, size_t sa, int lda,
-                        const double2* B, size_t sb, int ldb, double2* out, size_t so, int ldo,
-                        const int* status) {
+                        const typename CplxOf<R>::T* B, size_t sb, int ldb, typename CplxOf<R>::T* out, size_t so,
+                        int ldo, const int* status, const int* st2) {
+  using C2 = typename CplxOf<R>::T;
   const int t = blockIdx.z;
-  if (status[t]) return;
+  if (mx_skip(status, st2, t)) return;
   const int n = nst[t], k_p = kp[t];
   const int M = dim_of(mc, n, k_p), NN = dim_of(nc, n, k_p), K = dim_of(kc, n, k_p);
   const int i0 = blockIdx.x * GT, j0 = blockIdx.y * GT;
@@ -62,23 +77,23 @@ __global__ void k_zgemm(const int* nst, const int* kp, int mc, int nc, int kc, c
   A += (size_t)t * sa;
   B += (size_t)t * sb;
   out += (size_t)t * so;
-  __shared__ double2 sA[GK][GT + 1];
-  __shared__ double2 sB[GK][GT + 1];
+  __shared__ C2 sA[GK][GT + 1];
+  __shared__ C2 sB[GK][GT + 1];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  double2 acc[4];
+  C2 acc[4];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) acc[u] = make_double2(0.0, 0.0);
+  for (int u = 0; u < 4; ++u) acc[u] = CplxOf<R>::make(R(0), R(0));
   for (int k0 = 0; k0 < K; k0 += GK) {
     for (int e = threadIdx.x; e < GK * GT; e += blockDim.x) {
       const int kk = e / GT, ii = e % GT, k = k0 + kk;
       const int i = i0 + ii, j = j0 + ii;
-      double2 a = make_double2(0.0, 0.0), bv = make_double2(0.0, 0.0);
+      C2 a = CplxOf<R>::make(R(0), R(0)), bv = CplxOf<R>::make(R(0), R(0));
       if (k < K && i < M) {
         if (CONJ_T) {
-          a = ld_c(A, (size_t)k + (size_t)i * lda);  // op(A)[i,k] = conj(A[k,i])
+          ld_c(A, (size_t)k + (size_t)i * lda, &a);  // op(A)[i,k] = conj(A[k,i])
           a.y = -a.y;
         } else {
-          a = ld_c(A, (size_t)i + (size_t)k * lda);
+          ld_c(A, (size_t)i + (size_t)k * lda, &a);
         }
       }
       if (k < K && j < NN) bv = B[(size_t)k + (size_t)j * ldb];
@@ -88,10 +103,10 @@ __global__ void k_zgemm(const int* nst, const int* kp, int mc, int nc, int kc, c
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < GK; ++kk) {
-      const double2 a = sA[kk][tx];
+      const C2 a = sA[kk][tx];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const double2 bv = sB[kk][ty + 8 * u];
+        const C2 bv = sB[kk][ty + 8 * u];
         acc[u].x = fma(a.x, bv.x, fma(-a.y, bv.y, acc[u].x));
         acc[u].y = fma(a.x, bv.y, fma(a.y, bv.x, acc[u].y));
       }
@@ -166,7 +181,7 @@ __global__ void k_mx_pick(Batch b, MixedWs w) {
 // W = R^{-1} (upper), so that X W has orthonormal columns. One CTA per step.
 __global__ void k_mx_cholinv(Batch b, MixedWs w, const double2* S0, double2* W0, size_t stride, int ld) {
   const int t = blockIdx.x;
-  if (b.status[t]) return;
+  if (mx_skip(b.status, w.st2, t)) return;
   const int kp = w.kp[t];
   double2* S = const_cast<double2*>(S0) + (size_t)t * stride;
   double2* W = W0 + (size_t)t * stride;
@@ -221,7 +236,7 @@ __global__ void k_mx_cholinv(Batch b, MixedWs w, const double2* S0, double2* W0,
 // H <- (H + H^H)/2 on the kp x kp block.
 __global__ void k_mx_herm(Batch b, MixedWs w, double2* H0, size_t stride, int ld) {
   const int t = blockIdx.x;
-  if (b.status[t]) return;
+  if (mx_skip(b.status, w.st2, t)) return;
   const int kp = w.kp[t];
   double2* H = H0 + (size_t)t * stride;
   for (int e = threadIdx.x; e < kp * kp; e += blockDim.x) {
@@ -236,20 +251,22 @@ __global__ void k_mx_herm(Batch b, MixedWs w, double2* H0, size_t stride, int ld
 }
 
 // R = Y - X diag(theta) in place of Y; rnorm[j] = ||R[:, j]||.
-__global__ void k_mx_resid(Batch b, MixedWs w, const double2* X0, double2* Y0, size_t stride) {
+__global__ void k_mx_resid(Batch b, MixedWs w, const double2* X0, double2* Y0, float2* R32, size_t stride) {
   const int t = blockIdx.y, j = blockIdx.x;
-  if (b.status[t]) return;
+  if (mx_skip(b.status, w.st2, t)) return;
   const int n = b.nst[t], N = b.n_max, kp = w.kp[t];
   if (j >= kp) return;
   const double th = w.theta[(size_t)t * w.KP + j];
   const double2* X = X0 + (size_t)t * stride + (size_t)j * N;
   double2* Y = Y0 + (size_t)t * stride + (size_t)j * N;
+  float2* Rf = R32 + (size_t)t * stride * 2 + (size_t)j * N;  // stride counts double2 elements
   __shared__ double red[256];
   double s = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const double2 x = X[i], y = Y[i];
     const double2 r = make_double2(y.x - th * x.x, y.y - th * x.y);
     Y[i] = r;
+    Rf[i] = make_float2((float)r.x, (float)r.y);
     s += r.x * r.x + r.y * r.y;
   }
   red[threadIdx.x] = s;
@@ -262,34 +279,38 @@ __global__ void k_mx_resid(Batch b, MixedWs w, const double2* X0, double2* Y0, s
 }
 
 // T[m, j] /= (mu32[m] - theta[j]) for directions outside the kept set, 0 inside.
-__global__ void k_mx_scale(Batch b, MixedWs w, double2* T0, size_t stride) {
+__global__ void k_mx_scale(Batch b, MixedWs w, float2* T0, size_t stride) {
   const int t = blockIdx.y;
-  if (b.status[t]) return;
+  if (mx_skip(b.status, w.st2, t)) return;
   const int n = b.nst[t], N = b.n_max, kp = w.kp[t];
   const double* mu = b.mu + (size_t)t * N;
   const int* sel = w.sel + (size_t)t * N;
-  double2* T = T0 + (size_t)t * stride;
+  float2* T = T0 + (size_t)t * stride;
   const double eps = 1e-13 * w.cnorm[t];
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * kp; e += gridDim.x * blockDim.x) {
     const int m = e % n, j = e / n;
-    double2 v = T[(size_t)m + (size_t)j * N];
+    const float2 v = T[(size_t)m + (size_t)j * N];
     const double den = mu[m] - w.theta[(size_t)t * w.KP + j];
-    if (sel[m] >= 0 || fabs(den) <= eps) v = make_double2(0.0, 0.0);
-    else v = make_double2(v.x / den, v.y / den);
-    T[(size_t)m + (size_t)j * N] = v;
+    float2 o = make_float2(0.f, 0.f);
+    if (sel[m] < 0 && fabs(den) > eps) {
+      const float inv = (float)(1.0 / den);
+      o = make_float2(v.x * inv, v.y * inv);
+    }
+    T[(size_t)m + (size_t)j * N] = o;
   }
 }
 
 // X <- X - D on the n x kp block.
-__global__ void k_mx_sub(Batch b, MixedWs w, double2* X0, const double2* D0, size_t stride) {
+__global__ void k_mx_sub(Batch b, MixedWs w, double2* X0, const float2* D0, size_t stride_x, size_t stride_d) {
   const int t = blockIdx.y;
-  if (b.status[t]) return;
+  if (mx_skip(b.status, w.st2, t)) return;
   const int n = b.nst[t], N = b.n_max, kp = w.kp[t];
-  double2* X = X0 + (size_t)t * stride;
-  const double2* D = D0 + (size_t)t * stride;
+  double2* X = X0 + (size_t)t * stride_x;
+  const float2* D = D0 + (size_t)t * stride_d;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * kp; e += gridDim.x * blockDim.x) {
     const int i = e % n, j = e / n;
-    const double2 x = X[(size_t)i + (size_t)j * N], d = D[(size_t)i + (size_t)j * N];
+    const double2 x = X[(size_t)i + (size_t)j * N];
+    const float2 d = D[(size_t)i + (size_t)j * N];
     X[(size_t)i + (size_t)j * N] = make_double2(x.x - d.x, x.y - d.y);
   }
 }
@@ -297,6 +318,29 @@ __global__ void k_mx_sub(Batch b, MixedWs w, double2* X0, const double2* D0, siz
 // Hand theta / X to the selection stage (which ranks b.mu and reads the
 // columns of b.Q): mu[j] = theta[j] for j < kp, -inf beyond; check the last
 // residuals of the n_eig leading pairs.
+// Largest residual norm among the pairs that can be kept (the n_eig largest
+// theta of problem t).
+__device__ double mx_worst_kept(const Batch& b, const MixedWs& w, int t) {
+  const int kp = w.kp[t], K = b.neig[t];
+  double worst = 0.0;
+  for (int j = 0; j < kp; ++j) {
+    int rank = 0;
+    const double tj = w.theta[(size_t)t * w.KP + j];
+    for (int i = 0; i < kp; ++i) {
+      const double ti = w.theta[(size_t)t * w.KP + i];
+      rank += (ti > tj) || (ti == tj && i < j);
+    }
+    if (rank < K) worst = fmax(worst, w.rnorm[(size_t)t * w.KP + j]);
+  }
+  return worst;
+}
+// Early exit: a problem whose kept residuals are already below rtol ||C||_F
+// skips the remaining passes (its X, theta and residuals stay as they are).
+__global__ void k_mx_check(Batch b, MixedWs w, double rtol) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= b.T || mx_skip(b.status, w.st2, t)) return;
+  if (mx_worst_kept(b, w, t) <= rtol * w.cnorm[t]) w.st2[t] |= kMxDone;
+}
 __global__ void k_mx_final(Batch b, MixedWs w, double rtol) {
   const int t = blockIdx.x;
   if (b.status[t]) return;
@@ -304,27 +348,18 @@ __global__ void k_mx_final(Batch b, MixedWs w, double rtol) {
   double* mu = b.mu + (size_t)t * N;
   for (int j = threadIdx.x; j < n; j += blockDim.x) mu[j] = (j < kp) ? w.theta[(size_t)t * w.KP + j] : -INFINITY;
   if (threadIdx.x == 0) {
-    // residual of the pairs that can be kept: rank by theta, check the top n_eig
-    const int K = b.neig[t];
-    double worst = 0.0;
-    for (int j = 0; j < kp; ++j) {
-      int rank = 0;
-      const double tj = w.theta[(size_t)t * w.KP + j];
-      for (int i = 0; i < kp; ++i) {
-        const double ti = w.theta[(size_t)t * w.KP + i];
-        rank += (ti > tj) || (ti == tj && i < j);
-      }
-      if (rank < K) worst = fmax(worst, w.rnorm[(size_t)t * w.KP + j]);
-    }
-    if (!(worst <= rtol * w.cnorm[t]) || w.st2[t]) b.status[t] |= kStatusNotConverged;
+    const double worst = mx_worst_kept(b, w, t);
+    if (!(worst <= rtol * w.cnorm[t]) || (w.st2[t] & ~kMxDone)) b.status[t] |= kStatusNotConverged;
   }
 }
 
-template <typename TA, bool CT>
+template <typename R, typename TA, bool CT>
 void zgemm(const Batch& b, const MixedWs& w, int mc, int nc, int kc, int mmax, int nmax, const TA* A, size_t sa,
-           int lda, const double2* B, size_t sb, int ldb, double2* out, size_t so, int ldo, cudaStream_t s) {
+           int lda, const typename CplxOf<R>::T* B, size_t sb, int ldb, typename CplxOf<R>::T* out, size_t so,
+           int ldo, cudaStream_t s) {
   dim3 grd((mmax + GT - 1) / GT, (nmax + GT - 1) / GT, b.T);
-  k_zgemm<TA, CT><<<grd, 256, 0, s>>>(b.nst, w.kp, mc, nc, kc, A, sa, lda, B, sb, ldb, out, so, ldo, b.status);
+  k_zgemm<R, TA, CT><<<grd, 256, 0, s>>>(b.nst, w.kp, mc, nc, kc, A, sa, lda, B, sb, ldb, out, so, ldo, b.status,
+                                         w.st2);
 }
 
 }  // namespace
@@ -352,9 +387,13 @@ void launch_eig_mixed(const Batch& b, const MixedWs& w, double tol, int max_swee
   const float2* Q32 = reinterpret_cast<const float2*>(b.X) + NN;
   // 2. FP64 refinement of the kp leading pairs; buffers inside the Q buffer
   double2* P0 = b.Q;                       // X (final eigenvectors), n x kp, ld N
-  double2* P1 = b.Q + (size_t)N * KP;      // orthonormalised X / T
-  double2* P2 = b.Q + (size_t)2 * N * KP;  // Y = C X / D
+  double2* P1 = b.Q + (size_t)N * KP;      // orthonormalised X / FP32 R and T
+  double2* P2 = b.Q + (size_t)2 * N * KP;  // Y = C X / FP32 D
   double2* P3 = b.Q + (size_t)3 * N * KP;  // Y U / R
+  float2* R32 = reinterpret_cast<float2*>(P1);
+  float2* T32 = R32 + (size_t)N * KP;
+  float2* D32 = reinterpret_cast<float2*>(P2);
+  const size_t NN2 = 2 * NN;  // per-problem stride of the FP32 views
   double2* Hs = b.Q + (size_t)4 * N * KP;  // S, then H (kp x kp, ld KP)
   double2* Us = Hs + (size_t)KP * KP;      // rotations of H
   double2* Ws = Us + (size_t)KP * KP;      // R^{-1}
@@ -370,22 +409,25 @@ void launch_eig_mixed(const Batch& b, const MixedWs& w, double tol, int max_swee
   h.stride = NN;
   h.report_nonconv = 1;
   cudaMemsetAsync(w.st2, 0, sizeof(int) * T, s);
+  const int ew = std::max(1, (N * KP + 255) / 256 / 8);  // blocks per problem of the elementwise kernels
   for (int pass = 0; pass < kPasses; ++pass) {
-    zgemm<double2, true>(b, w, DKP, DKP, DN, KP, KP, P0, NN, N, P0, NN, N, Hs, NN, KP, s);    // S = X^H X
-    k_mx_cholinv<<<T, 128, 0, s>>>(b, w, Hs, Ws, NN, KP);                                      // W = R^{-1}
-    zgemm<double2, false>(b, w, DN, DKP, DKP, N, KP, P0, NN, N, Ws, NN, KP, P1, NN, N, s);   // X1 = X W
-    zgemm<double2, false>(b, w, DN, DKP, DN, N, KP, b.C, NN, N, P1, NN, N, P2, NN, N, s);    // Y = C X1
-    zgemm<double2, true>(b, w, DKP, DKP, DN, KP, KP, P1, NN, N, P2, NN, N, Hs, NN, KP, s);   // H = X1^H Y
+    zgemm<double, double2, true>(b, w, DKP, DKP, DN, KP, KP, P0, NN, N, P0, NN, N, Hs, NN, KP, s);   // S = X^H X
+    k_mx_cholinv<<<T, 128, 0, s>>>(b, w, Hs, Ws, NN, KP);                                          // W = R^{-1}
+    zgemm<double, double2, false>(b, w, DN, DKP, DKP, N, KP, P0, NN, N, Ws, NN, KP, P1, NN, N, s);  // X1 = X W
+    zgemm<double, double2, false>(b, w, DN, DKP, DN, N, KP, b.C, NN, N, P1, NN, N, P2, NN, N, s);   // Y = C X1
+    zgemm<double, double2, true>(b, w, DKP, DKP, DN, KP, KP, P1, NN, N, P2, NN, N, Hs, NN, KP, s);  // H = X1^H Y
     k_mx_herm<<<T, 256, 0, s>>>(b, w, Hs, NN, KP);
-    launch_jacobi_args(h, T, false, 1e-15, 60, s);                                            // H = U th U^H
-    zgemm<double2, false>(b, w, DN, DKP, DKP, N, KP, P1, NN, N, Us, NN, KP, P0, NN, N, s);   // X = X1 U
-    zgemm<double2, false>(b, w, DN, DKP, DKP, N, KP, P2, NN, N, Us, NN, KP, P3, NN, N, s);   // Y U
-    k_mx_resid<<<dim3(KP, T), 256, 0, s>>>(b, w, P0, P3, NN);                                // R = YU - X th
+    launch_jacobi_args(h, T, false, 1e-15, 60, s);                                                // H = U th U^H
+    zgemm<double, double2, false>(b, w, DN, DKP, DKP, N, KP, P1, NN, N, Us, NN, KP, P0, NN, N, s);  // X = X1 U
+    zgemm<double, double2, false>(b, w, DN, DKP, DKP, N, KP, P2, NN, N, Us, NN, KP, P3, NN, N, s);  // Y U
+    k_mx_resid<<<dim3(KP, T), 256, 0, s>>>(b, w, P0, P3, R32, NN);                                // R = YU - X th
     if (pass == kPasses - 1) break;
-    zgemm<float2, true>(b, w, DN, DKP, DN, N, KP, Q32, 2 * NN, N, P3, NN, N, P1, NN, N, s);  // T = Q32^H R
-    k_mx_scale<<<dim3(std::max(1, (N * KP + 255) / 256 / 8), T), 256, 0, s>>>(b, w, P1, NN);
-    zgemm<float2, false>(b, w, DN, DKP, DN, N, KP, Q32, 2 * NN, N, P1, NN, N, P2, NN, N, s); // D = Q32 T
-    k_mx_sub<<<dim3(std::max(1, (N * KP + 255) / 256 / 8), T), 256, 0, s>>>(b, w, P0, P2, NN);
+    k_mx_check<<<(T + 127) / 128, 128, 0, s>>>(b, w, 10.0 * tol);
+    // preconditioner products in FP32: they only need the accuracy of Q32 itself
+    zgemm<float, float2, true>(b, w, DN, DKP, DN, N, KP, Q32, NN2, N, R32, NN2, N, T32, NN2, N, s);   // T = Q32^H R
+    k_mx_scale<<<dim3(ew, T), 256, 0, s>>>(b, w, T32, NN2);
+    zgemm<float, float2, false>(b, w, DN, DKP, DN, N, KP, Q32, NN2, N, T32, NN2, N, D32, NN2, N, s);  // D = Q32 T
+    k_mx_sub<<<dim3(ew, T), 256, 0, s>>>(b, w, P0, D32, NN, NN2);                                   // X -= D
   }
   k_mx_final<<<T, 256, 0, s>>>(b, w, 1e3 * tol);
 }
