@@ -35,7 +35,7 @@ struct Batch {
   double2* Q;     // [T][n_max][n_max] Jacobi rotations (column-major)
   double* mu;     // [T][n_max] Jacobi eigenvalues (unsorted)
   int* status;    // [T] status bits
-  int* sweeps;    // [T] Jacobi sweeps used
+  int* sweeps;    // [T] Jacobi sweeps used (QR steps of the FP32 stage of the mixed eigensolve)
   // selection / packing outputs
   int* nkept;     // [T] eigenpairs kept (== neig[t] on success, 0 on failure)
   double* sel_mu; // [T][k_max] kept eigenvalues, descending
@@ -81,7 +81,7 @@ void launch_jacobi(const Batch& b, double tol, int max_sweeps, cudaStream_t s);
 // pairs); needs the X and Q buffers of the batch as scratch, which fits when
 // eig_mixed_fits(n_max, KP).
 bool eig_mixed_fits(int n_max, int KP);
-constexpr int kMixedLaunches = 59;  // kernels launched by launch_eig_mixed
+constexpr int kMixedLaunches = 61;  // kernels launched by launch_eig_mixed
 void launch_eig_mixed(const Batch& b, const MixedWs& w, double tol, int max_sweeps, cudaStream_t s);
 // d_bounds: per channel, n_level x 2 column-major blocks.
 void launch_select(const Batch& b, int n_level, const double* d_bounds, int filter, cudaStream_t s);

@@ -4,8 +4,8 @@
 // that are kept, at a fraction of the FP64 work, which matters on B300 where
 // the FP64 pipe runs at 1/58 of the FP32 rate:
 //   1. the reduced matrix C = L^{-1} V L^{-T} (formed in FP64) is rounded to
-//      FP32 and diagonalised by a block Jacobi in FP32 (bjacobi.cuh):
-//      C ~ Q32 diag(mu32) Q32^H, off-diagonal mass <= 1e-5 ||C||_F;
+//      FP32 and diagonalised in FP32 through its real tridiagonal form
+//      (tridiag32.cuh): C ~ Q32 diag(mu32) Q32^H to a few FP32 ulps of ||C||;
 //   2. the kp = min(n, n_eig + 16) leading approximate eigenvectors X are
 //      refined in FP64 with the operator C itself:
 //        orthonormalise X (Cholesky QR), Y = C X, H = X^H Y,
@@ -29,8 +29,8 @@
 #include <algorithm>
 
 #include "bipp_internal.cuh"
-#include "bjacobi.cuh"
 #include "jacobi.cuh"
+#include "tridiag32.cuh"
 
 namespace bipp {
 namespace {
@@ -39,7 +39,7 @@ constexpr int kPad = 16;       // extra leading pairs refined beyond n_eig
 constexpr int kPasses = 4;     // refinement passes at most
 constexpr int kMxDone = 8;     // st2 bit: residual met the early-exit bound, later passes skip the step
 constexpr int GT = 32, GK = 16;
-static_assert(4 + 15 * (kPasses - 1) + 10 == kMixedLaunches, "launch count of the mixed eigensolver");
+static_assert(6 + 15 * (kPasses - 1) + 10 == kMixedLaunches, "launch count of the mixed eigensolver");
 
 // Shape codes of the batched complex products: dimension = n_st or kp of the problem.
 enum Dim { DN = 0, DKP = 1 };
@@ -369,21 +369,22 @@ bool eig_mixed_fits(int N, int KP) { return 4LL * N * KP + 3LL * KP * KP <= (lon
 void launch_eig_mixed(const Batch& b, const MixedWs& w, double tol, int max_sweeps, cudaStream_t s) {
   const int N = b.n_max, KP = w.KP, T = b.T;
   const size_t NN = (size_t)N * N;
-  // 1. FP32 block Jacobi on all pairs (C32, Q32 in the two halves of the X buffer);
-  //    one inner sweep per pivot block converges in as many block sweeps as two
+  // 1. FP32 eigendecomposition of all pairs through the real tridiagonal form
+  //    (C32, Q32 in the two halves of the X buffer; its scratch in the Q buffer,
+  //    which the refinement takes over afterwards)
   k_mx_tof32<<<dim3(std::max(1, std::min(64, (N * N + 255) / 256)), T), 256, 0, s>>>(b);
-  BJacobiArgs a;
+  TridiagArgs a;
   a.C = reinterpret_cast<float2*>(b.X);
   a.Q = reinterpret_cast<float2*>(b.X) + NN;
+  a.scratch = reinterpret_cast<float*>(b.Q);
+  a.sstride = 4 * NN;
   a.mu = b.mu;
   a.status = b.status;
-  a.sweeps = b.sweeps;
+  a.steps = b.sweeps;
   a.n = b.nst;
   a.ld = N;
   a.stride = 2 * NN;
-  const size_t smem = bjacobi_smem();
-  cudaFuncSetAttribute(k_bjacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_bjacobi32<<<T, kBJThreads, smem, s>>>(a, 1e-5, std::min(max_sweeps, 12), 1);
+  launch_tridiag32(a, T, s);
   const float2* Q32 = reinterpret_cast<const float2*>(b.X) + NN;
   // 2. FP64 refinement of the kp leading pairs; buffers inside the Q buffer
   double2* P0 = b.Q;                       // X (final eigenvectors), n x kp, ld N

@@ -1,0 +1,506 @@
+// tridiag32.cuh — FP32 Hermitian eigendecomposition through a real tridiagonal
+// form (the preconditioning stage of the mixed-precision eigensolver).
+//
+// For each problem (one CTA per problem; n x n Hermitian C, column-major):
+//   1. k_tridiag32: Householder reduction T = H^H C H, H = H_0 H_1 ... H_{n-2},
+//      H_k = I - tau_k v_k v_k^H acting on indices k+1..n-1 with v_k[k+1] = 1
+//      and beta_k = (H_k^H C[k+1:, k])[0] real, so that T is real symmetric
+//      tridiagonal (diagonal d, off-diagonal e = beta). The rank-2 update of
+//      step k is fused with the matrix-vector product of step k+1: the
+//      trailing matrix is read and written once per step.
+//   2. k_tridiag_qr32: implicit symmetric QR with the Wilkinson shift on (d, e);
+//      one thread chases the bulge and records the Givens rotations of each
+//      QR step while the other warps apply those of the previous step to
+//      their rows of Z (Z starts as I), so that T = Z diag(d) Z^T at
+//      convergence.
+//   3. k_tridiag_back32: Q = H Z, applying H_{n-2} first, one warp per column.
+// Result: C ~ Q diag(d) Q^H with Q unitary to FP32 rounding; the eigenvalues
+// are left unsorted in mu.
+#pragma once
+
+#include <math.h>
+
+#include "bipp_internal.cuh"
+
+namespace bipp {
+
+constexpr int kTdThreads = 512;
+
+struct TridiagArgs {
+  float2* C;          // [T] n x n Hermitian (ld, stride): overwritten by the reflectors v_k[k+2:]
+  float2* Q;          // [T] eigenvectors (ld, stride)
+  float* scratch;     // [T] per problem: Z (ld x ld floats), d, e (ld floats each), tau (ld float2)
+  size_t sstride;     // floats between the scratch regions of consecutive problems
+  double* mu;         // [T][ld] eigenvalues (unsorted)
+  int* status;        // [T] problems with a status bit are skipped; QR failure sets kStatusNotConverged
+  int* steps;         // [T] QR steps used
+  const int* n;       // [T]
+  int ld;
+  size_t stride;      // float2 elements between consecutive problems of C and Q
+};
+
+// Per-problem scratch layout (in floats): Z at 0, d at ld^2, e at ld^2 + ld,
+// tau (float2, 8-byte aligned) after them.
+__host__ __device__ __forceinline__ size_t td_off_d(int ld) { return (size_t)ld * ld; }
+__host__ __device__ __forceinline__ size_t td_off_e(int ld) { return (size_t)ld * ld + ld; }
+__host__ __device__ __forceinline__ size_t td_off_tau(int ld) { return ((size_t)ld * ld + 2 * (size_t)ld + 1) & ~(size_t)1; }
+__host__ __device__ __forceinline__ size_t td_scratch_floats(int ld) { return td_off_tau(ld) + 2 * (size_t)ld; }
+
+namespace td {
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+
+// Sum over the block of kTdThreads threads (all threads get the result).
+template <typename V>
+__device__ __forceinline__ float2 block_sum2(float2 v, V* red) {
+  const int tid = threadIdx.x;
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  if ((tid & 31) == 0) red[tid >> 5] = v;
+  __syncthreads();
+  float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int w = 0; w < kTdThreads / 32; ++w) {
+    s.x += red[w].x;
+    s.y += red[w].y;
+  }
+  __syncthreads();
+  return s;
+}
+
+}  // namespace td
+
+// ---- 1. Householder reduction to real tridiagonal form
+// Dynamic shared memory: 5 * ld float2 (v_prev, w_prev, v, w, p).
+__global__ void __launch_bounds__(kTdThreads, 1) k_tridiag32(TridiagArgs a) {
+  using namespace td;
+  const int t = blockIdx.x;
+  if (a.status[t]) return;
+  const int n = a.n[t], N = a.ld, tid = threadIdx.x;
+  float2* A = a.C + (size_t)t * a.stride;
+  float* S = a.scratch + (size_t)t * a.sstride;
+  float* d = S + td_off_d(N);
+  float* e = S + td_off_e(N);
+  float2* tau = reinterpret_cast<float2*>(S + td_off_tau(N));
+  extern __shared__ __align__(16) unsigned char tdsm[];
+  float2* vp = reinterpret_cast<float2*>(tdsm);  // v_{k-1} (global row index)
+  float2* wp = vp + N;                            // w_{k-1}
+  float2* v = wp + N;                             // v_k
+  float2* w = v + N;                              // w_k
+  float2* p = w + N;                              // p_k = A v_k
+  __shared__ float2 red[kTdThreads / 32];
+  __shared__ float2 s_tau, s_scale;
+  __shared__ float s_beta;
+  __shared__ int s_trivial;
+  for (int i = tid; i < N; i += kTdThreads) {
+    vp[i] = make_float2(0.f, 0.f);
+    wp[i] = make_float2(0.f, 0.f);
+  }
+  if (n == 1 && tid == 0) d[0] = A[0].x;
+  __syncthreads();
+  for (int k = 0; k + 1 < n; ++k) {
+    const int m = n - k - 1;  // rows k+1..n-1
+    // (a) reflector from column k (already up to date)
+    float2 sg = make_float2(0.f, 0.f);
+    for (int r = tid; r < m; r += kTdThreads) {
+      const float2 x = A[(size_t)(k + 1 + r) + (size_t)k * N];
+      if (r > 0) sg.x += x.x * x.x + x.y * x.y;
+    }
+    const float sigma = block_sum2(sg, red).x;
+    if (tid == 0) {
+      const float2 al = A[(size_t)(k + 1) + (size_t)k * N];
+      d[k] = A[(size_t)k + (size_t)k * N].x;
+      if (sigma == 0.f && al.y == 0.f) {
+        s_trivial = 1;
+        s_tau = make_float2(0.f, 0.f);
+        s_beta = al.x;
+        s_scale = make_float2(0.f, 0.f);
+      } else {
+        const float beta = -copysignf(sqrtf(al.x * al.x + al.y * al.y + sigma), al.x);
+        s_trivial = 0;
+        s_tau = make_float2((beta - al.x) / beta, -al.y / beta);
+        s_beta = beta;
+        const float2 dn = make_float2(al.x - beta, al.y);  // 1 / (alpha - beta)
+        const float inv = 1.f / (dn.x * dn.x + dn.y * dn.y);
+        s_scale = make_float2(dn.x * inv, -dn.y * inv);
+      }
+      e[k] = s_beta;
+      tau[k] = s_tau;
+    }
+    __syncthreads();
+    const float2 tk = s_tau, sc = s_scale;
+    const bool triv = s_trivial != 0;
+    for (int r = tid; r < m; r += kTdThreads) {
+      float2 vv;
+      if (r == 0) {
+        vv = make_float2(1.f, 0.f);
+      } else if (triv) {
+        vv = make_float2(0.f, 0.f);
+      } else {
+        vv = cmul(A[(size_t)(k + 1 + r) + (size_t)k * N], sc);
+        A[(size_t)(k + 1 + r) + (size_t)k * N] = vv;  // reflector storage
+      }
+      v[k + 1 + r] = vv;
+    }
+    __syncthreads();
+    // (b) fused pass over A[k+1:, k+1:]: pending rank-2 update of step k-1, then p = A v_k
+    for (int r = tid; r < m; r += kTdThreads) {
+      const int i = k + 1 + r;
+      const float2 vpi = vp[i], wpi = wp[i];
+      float2 acc = make_float2(0.f, 0.f);
+      float2* Ai = A + i;
+      // 8 columns per group, the next group's loads issued before this group is stored
+      constexpr int G = 8;
+      int j = k + 1;
+      float2 cur[G], nxt[G];
+      if (j + G <= n) {
+#pragma unroll
+        for (int u = 0; u < G; ++u) cur[u] = Ai[(size_t)(j + u) * N];
+      }
+      for (; j + G <= n; j += G) {
+        const bool more = j + 2 * G <= n;
+        if (more) {
+#pragma unroll
+          for (int u = 0; u < G; ++u) nxt[u] = Ai[(size_t)(j + G + u) * N];
+        }
+#pragma unroll
+        for (int u = 0; u < G; ++u) {
+          // a -= w_i conj(v_j) + v_i conj(w_j)
+          float2 x = cur[u];
+          const float2 t1 = cmulc(wpi, vp[j + u]), t2 = cmulc(vpi, wp[j + u]);
+          x.x -= t1.x + t2.x;
+          x.y -= t1.y + t2.y;
+          Ai[(size_t)(j + u) * N] = x;
+          const float2 pv = cmul(x, v[j + u]);
+          acc.x += pv.x;
+          acc.y += pv.y;
+        }
+        if (more) {
+#pragma unroll
+          for (int u = 0; u < G; ++u) cur[u] = nxt[u];
+        }
+      }
+      for (; j < n; ++j) {
+        float2 x = Ai[(size_t)j * N];
+        const float2 t1 = cmulc(wpi, vp[j]), t2 = cmulc(vpi, wp[j]);
+        x.x -= t1.x + t2.x;
+        x.y -= t1.y + t2.y;
+        Ai[(size_t)j * N] = x;
+        const float2 pv = cmul(x, v[j]);
+        acc.x += pv.x;
+        acc.y += pv.y;
+      }
+      p[i] = acc;
+    }
+    __syncthreads();
+    // (c) gamma = v^H p (real), w = tau p - |tau|^2 gamma / 2 v
+    float2 gp = make_float2(0.f, 0.f);
+    for (int r = tid; r < m; r += kTdThreads) {
+      const int i = k + 1 + r;
+      const float2 vi = v[i], pi = p[i];
+      gp.x += vi.x * pi.x + vi.y * pi.y;
+    }
+    const float gamma = block_sum2(gp, red).x;
+    const float hg = 0.5f * (tk.x * tk.x + tk.y * tk.y) * gamma;
+    for (int r = tid; r < m; r += kTdThreads) {
+      const int i = k + 1 + r;
+      const float2 tp = cmul(tk, p[i]), vi = v[i];
+      w[i] = make_float2(tp.x - hg * vi.x, tp.y - hg * vi.y);
+    }
+    __syncthreads();
+    // (d) column k+1 gets the update of step k now (v_k[k+1] = 1); the rest is pending
+    const float2 wk1 = w[k + 1];
+    for (int r = tid; r < m; r += kTdThreads) {
+      const int i = k + 1 + r;
+      float2 x = A[(size_t)i + (size_t)(k + 1) * N];
+      const float2 t2 = cmulc(v[i], wk1);
+      x.x -= w[i].x + t2.x;
+      x.y -= w[i].y + t2.y;
+      A[(size_t)i + (size_t)(k + 1) * N] = x;
+      vp[i] = v[i];
+      wp[i] = w[i];
+    }
+    if (tid == 0) vp[k] = wp[k] = make_float2(0.f, 0.f);
+    __syncthreads();
+    if (k + 2 == n && tid == 0) d[n - 1] = A[(size_t)(n - 1) + (size_t)(n - 1) * N].x;
+  }
+}
+
+// ---- 2. implicit symmetric QR on (d, e) with the Wilkinson shift, rotations applied to Z
+// One driver thread (lane 0 of warp 0) runs the QR iteration on the
+// tridiagonal (scaled to unit Frobenius norm) and records the Givens rotations
+// of step s+1 while the applier warps apply those of step s to their rows of Z
+// (double-buffered rotation lists, one barrier per step). The driver's chain
+// of dependent operations is the critical path, so the warps that share its
+// SM sub-partition (warp index = 0 mod 4) stay idle and the appliers are the
+// other 18 of 24 warps (one row of Z each up to n = 576).
+// Dynamic shared memory: 6 * ld floats (d, e, two (c, s) lists).
+constexpr int kQrThreads = 768;
+constexpr int kQrApply = kQrThreads / 4 * 3;
+
+__global__ void __launch_bounds__(kQrThreads, 1) k_tridiag_qr32(TridiagArgs a, int max_steps) {
+  const int t = blockIdx.x;
+  if (a.status[t]) return;
+  const int n = a.n[t], N = a.ld, tid = threadIdx.x;
+  float* Z = a.scratch + (size_t)t * a.sstride;
+  const float* dg = Z + td_off_d(N);
+  const float* eg = Z + td_off_e(N);
+  extern __shared__ __align__(16) unsigned char qrsm[];
+  float* d = reinterpret_cast<float*>(qrsm);
+  float* e = d + N;
+  float* rc0 = e + N;  // [2][N] cosines
+  float* rs0 = rc0 + 2 * N;  // [2][N] sines
+  __shared__ int s_p[2], s_q[2], s_state[2];  // state: 0 apply, 1 done, 2 step cap hit
+  __shared__ float s_norm;
+  for (int i = tid; i < n; i += kQrThreads) {
+    d[i] = dg[i];
+    e[i] = (i + 1 < n) ? eg[i] : 0.f;
+  }
+  for (int e0 = tid; e0 < n * n; e0 += kQrThreads) {
+    const int r = e0 % n, c = e0 / n;
+    Z[(size_t)r + (size_t)c * N] = (r == c) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  const int wid = tid >> 5;
+  const bool driver = tid == 0;
+  const int ai = (wid & 3) ? (wid - 1 - (wid >> 2)) * 32 + (tid & 31) : -1;  // applier index
+  const float eps = 5.96e-8f, tiny = 1e-8f;  // deflation: relative to the neighbours, or to ||T||_F = 1
+  int q = n - 1, plo = n, steps = 0, fin = 0;  // driver state (plo >= q: find the block start again)
+  auto small = [&](float ev, float d0, float d1) { return ev <= eps * (fabsf(d0) + fabsf(d1)) || ev <= tiny; };
+  auto drive = [&](int slot) {
+    float* rc = rc0 + slot * N;
+    float* rs = rs0 + slot * N;
+    int state = 1;
+    while (q > 0) {
+      if (small(fabsf(e[q - 1]), d[q - 1], d[q])) {
+        e[q - 1] = 0.f;
+        --q;
+        continue;
+      }
+      if (steps >= max_steps) {
+        state = 2;
+        break;
+      }
+      if (plo >= q) {  // start of the unreduced block ending at q
+        plo = q - 1;
+        while (plo > 0 && !small(fabsf(e[plo - 1]), d[plo - 1], d[plo])) --plo;
+        if (plo > 0) e[plo - 1] = 0.f;
+      }
+      const int p = plo;
+      // Wilkinson shift from the trailing 2 x 2 block
+      const float dl = 0.5f * (d[q - 1] - d[q]), ee = e[q - 1];
+      const float den = dl + copysignf(sqrtf(dl * dl + ee * ee), dl);
+      const float mu = d[q] - ((den != 0.f) ? ee * ee / den : 0.f);
+      float ak = d[p], bk = e[p];
+      float x = ak - mu, z = bk;
+      float dn = d[p + 1], en = (p + 1 < q) ? e[p + 1] : 0.f;
+      float dprev = 0.f;
+      int split = p;
+      for (int k = p; k < q; ++k) {
+        const float dk1 = dn, ek1 = en;
+        if (k + 2 <= q) {
+          dn = d[k + 2];
+          en = (k + 2 < q) ? e[k + 2] : 0.f;
+        }
+        const float r2 = x * x + z * z;
+        float c = 1.f, s = 0.f, r = 0.f;
+        if (r2 > 0.f) {
+          // rsqrtf's error is biased, and a bias in c^2 + s^2 would build up
+          // linearly over the ~n^2 rotations applied to Z. One Newton-Raphson
+          // step on c^2 + s^2 = 1 with the residual h = 1 - c^2 - s^2 formed
+          // by FMAs (exact to far below an ulp) leaves only the unbiased
+          // round-to-nearest of the final FMA.
+          const float ri = rsqrtf(r2);
+          c = x * ri;
+          s = z * ri;
+          const float hh = 0.5f * fmaf(-c, c, fmaf(-s, s, 1.f));
+          c = fmaf(hh, c, c);
+          s = fmaf(hh, s, s);
+          r = fmaf(x, c, z * s);
+        }
+        const float cc = c * c, ss = s * s, cs = c * s;
+        const float ndk = cc * ak + 2.f * cs * bk + ss * dk1;
+        const float ndk1 = ss * ak - 2.f * cs * bk + cc * dk1;
+        const float nek = cs * (dk1 - ak) + (cc - ss) * bk;
+        d[k] = ndk;
+        if (k > p) {
+          if (small(fabsf(r), dprev, ndk)) {
+            r = 0.f;
+            split = k;
+          }
+          e[k - 1] = r;
+        }
+        dprev = ndk;
+        if (k + 1 < q) {
+          x = nek;
+          z = s * ek1;
+          bk = c * ek1;
+        } else {
+          e[k] = nek;
+        }
+        ak = ndk1;
+        rc[k - p] = c;
+        rs[k - p] = s;
+      }
+      d[q] = ak;
+      plo = split;
+      ++steps;
+      s_p[slot] = p;
+      s_q[slot] = q;
+      state = 0;
+      break;
+    }
+    s_state[slot] = state;
+    fin = state;
+  };
+  if (driver) {
+    float tn2 = 0.f;
+    for (int i = 0; i < n; ++i) tn2 += d[i] * d[i] + 2.f * e[i] * e[i];
+    const float tn = sqrtf(tn2), sc = tn > 0.f ? 1.f / tn : 1.f;
+    for (int i = 0; i < n; ++i) {
+      d[i] *= sc;
+      e[i] *= sc;
+    }
+    s_norm = tn > 0.f ? tn : 1.f;
+    drive(0);
+  }
+  __syncthreads();
+  for (int it = 0;; ++it) {
+    const int cur = it & 1;
+    if (s_state[cur] != 0) break;
+    if (driver) {
+      drive(cur ^ 1);
+    } else if (ai >= 0) {
+      const int p = s_p[cur], qq = s_q[cur];
+      const float* rc = rc0 + cur * N;
+      const float* rs = rs0 + cur * N;
+      const size_t sN = (size_t)N;
+      for (int r = ai; r < n; r += kQrApply) {
+        float* wr = Z + r + (size_t)p * N;  // column k of row r
+        const float* rd = wr + sN;         // next column to load
+        float zc = *wr;
+        // groups of 8 columns; the next group's loads are issued before this group is rotated
+        constexpr int G = 8;
+        int k = p;
+        float cur[G], nxt[G];
+        if (k + G <= qq) {
+#pragma unroll
+          for (int u = 0; u < G; ++u) {
+            cur[u] = *rd;
+            rd += sN;
+          }
+        }
+        for (; k + G <= qq; k += G) {
+          const bool more = k + 2 * G <= qq;
+          if (more) {
+#pragma unroll
+            for (int u = 0; u < G; ++u) {
+              nxt[u] = *rd;
+              rd += sN;
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < G; ++u) {
+            const float c = rc[k + u - p], s = rs[k + u - p];
+            *wr = fmaf(c, zc, s * cur[u]);
+            wr += sN;
+            zc = fmaf(c, cur[u], -s * zc);
+          }
+          if (more) {
+#pragma unroll
+            for (int u = 0; u < G; ++u) cur[u] = nxt[u];
+          }
+        }
+        for (; k < qq; ++k) {
+          const float zn = wr[sN];
+          const float c = rc[k - p], s = rs[k - p];
+          *wr = fmaf(c, zc, s * zn);
+          wr += sN;
+          zc = fmaf(c, zn, -s * zc);
+        }
+        *wr = zc;
+      }
+    }
+    __syncthreads();
+  }
+  const float tn = s_norm;
+  for (int i = tid; i < n; i += kQrThreads) a.mu[(size_t)t * N + i] = (double)(d[i] * tn);
+  if (driver) {
+    a.steps[t] = steps;
+    if (fin == 2) a.status[t] |= kStatusNotConverged;
+  }
+}
+
+// ---- 3. back-transformation Q = H_0 ... H_{n-2} Z, one warp per column
+// Grid (column groups, T); dynamic shared memory: ld float2 (the current v_k).
+__global__ void __launch_bounds__(kTdThreads) k_tridiag_back32(TridiagArgs a, int cols_per_cta) {
+  using namespace td;
+  const int t = blockIdx.y;
+  if (a.status[t]) return;
+  const int n = a.n[t], N = a.ld, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int c0 = blockIdx.x * cols_per_cta;
+  if (c0 >= n) return;
+  const int c1 = min(n, c0 + cols_per_cta);
+  const float2* A = a.C + (size_t)t * a.stride;
+  float2* Q = a.Q + (size_t)t * a.stride;
+  const float* Z = a.scratch + (size_t)t * a.sstride;
+  const float2* tau = reinterpret_cast<const float2*>(Z + td_off_tau(N));
+  extern __shared__ __align__(16) unsigned char bksm[];
+  float2* v = reinterpret_cast<float2*>(bksm);
+  for (int e0 = tid; e0 < n * (c1 - c0); e0 += kTdThreads) {
+    const int r = e0 % n, c = c0 + e0 / n;
+    Q[(size_t)r + (size_t)c * N] = make_float2(Z[(size_t)r + (size_t)c * N], 0.f);
+  }
+  for (int k = n - 2; k >= 0; --k) {
+    const int m = n - k - 1;
+    __syncthreads();
+    for (int r = tid; r < m; r += kTdThreads)
+      v[r] = (r == 0) ? make_float2(1.f, 0.f) : A[(size_t)(k + 1 + r) + (size_t)k * N];
+    __syncthreads();
+    const float2 tk = tau[k];
+    if (tk.x == 0.f && tk.y == 0.f) continue;
+    for (int c = c0 + wid; c < c1; c += kTdThreads / 32) {
+      float2* Qc = Q + (size_t)(k + 1) + (size_t)c * N;
+      float2 u = make_float2(0.f, 0.f);  // v^H Q[k+1:, c]
+      for (int r = lane; r < m; r += 32) {
+        const float2 x = Qc[r], vr = v[r];
+        u.x += vr.x * x.x + vr.y * x.y;
+        u.y += vr.x * x.y - vr.y * x.x;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        u.x += __shfl_xor_sync(0xffffffffu, u.x, o);
+        u.y += __shfl_xor_sync(0xffffffffu, u.y, o);
+      }
+      const float2 tu = cmul(tk, u);
+      for (int r = lane; r < m; r += 32) {
+        const float2 vr = v[r], y = cmul(vr, tu);
+        float2 x = Qc[r];
+        x.x -= y.x;
+        x.y -= y.y;
+        Qc[r] = x;
+      }
+    }
+  }
+}
+
+// Launches the three stages on stream s; 3 kernel launches.
+inline void launch_tridiag32(const TridiagArgs& a, int T, cudaStream_t s) {
+  const int N = a.ld;
+  const int smem1 = 5 * N * (int)sizeof(float2), smem2 = 6 * N * (int)sizeof(float), smem3 = N * (int)sizeof(float2);
+  cudaFuncSetAttribute(k_tridiag32, cudaFuncAttributeMaxDynamicSharedMemorySize, smem1);
+  cudaFuncSetAttribute(k_tridiag_qr32, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2);
+  cudaFuncSetAttribute(k_tridiag_back32, cudaFuncAttributeMaxDynamicSharedMemorySize, smem3);
+  k_tridiag32<<<T, kTdThreads, smem1, s>>>(a);
+  k_tridiag_qr32<<<T, kQrThreads, smem2, s>>>(a, 30 * N + 30);
+  constexpr int kCols = 64;
+  k_tridiag_back32<<<dim3((N + kCols - 1) / kCols, T), kTdThreads, smem3, s>>>(a, kCols);
+}
+
+}  // namespace bipp
