@@ -11,10 +11,10 @@
 // Kernel structure (one persistent CTA per SM, 18 warps):
 //   warps 0-15 (4 warpgroups) generate A for a 128-pixel tile on the fly:
 //              thread = pixel row, warpgroup g = stations 8g..8g+7 of the
-//              stage; exact phase reduction, SFU sincos, split into hi + lo
-//              (BF16 or FP16), written into shared memory in the UMMA K-major
-//              128-byte swizzled layout (one 128-byte row per pixel, 32
-//              stations per stage). They also run the epilogue: tcgen05.ld of
+//              stage; phase reduction in 64-bit fixed point (below), SFU
+//              sincos, split into hi + lo (BF16 or FP16), written into shared
+//              memory in the UMMA K-major 128-byte swizzled layout (one
+//              128-byte row per pixel, 32 stations per stage). They also run the epilogue: tcgen05.ld of
 //              the FP32 accumulator (pixel row = TMEM lane, warpgroup g takes
 //              column blocks g, g+4, ...), |z|^2, weights and levels in
 //              registers, accumulated over all steps and added to the FP64
@@ -27,6 +27,15 @@
 // Stage handoff uses mbarriers; every wait is bounded (clock64 budget) and on
 // expiry sets a device error word, drains its own in-flight work, frees TMEM
 // and returns.
+//
+// Phase. Only frac(<r, q_i>) matters (q_i = p_i/wl in cycles, |<r, q_i>| up to
+// ~4e4 at 65 km). With R = round(r 2^40) and Q = round(q 2^24) as 64-bit
+// integers, sum_c R_c Q_c = <r, q> 2^64 up to the rounding of R and Q, and
+// its value mod 2^64 is frac(<r, q>) 2^64: the wrapped low 64 bits of the
+// integer products are exact. Only their upper 32 bits are needed, which for
+// each component are hi32(Rlo Qlo) + Rhi Qlo + Rlo Qhi (mod 2^32); dropping
+// the carries out of the three low words costs < 3 2^-32 cycles. Error:
+// 2^-41 |q| + 2^-25 per component (~1e-7 cycles at |q| = 4e4).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <math.h>
@@ -123,20 +132,38 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// hi/lo split of two values into packed 16-bit pairs (element 0 in the low half).
+// hi/lo split of two values in [-1, 1] into packed 16-bit pairs (element 0
+// in the low half). hi is x rounded to a multiple of 2^-11 (FP16) or 2^-8
+// (BF16), by adding and subtracting 1.5 * 2^12 (2^15), whose FP32 ulp is that
+// step; such multiples in [-1, 1] are exact in the 16-bit type. lo = x - hi is
+// exact in FP32 and |lo| <= 2^-12 (2^-9), so its 16-bit rounding costs at most
+// 2^-24 (2^-17) absolute.
 template <bool FP16>
 __device__ __forceinline__ void split2(float x0, float x1, uint32_t* hi, uint32_t* lo) {
+  constexpr float M = FP16 ? 6144.0f : 49152.0f;
+  const float h0 = __fsub_rn(__fadd_rn(x0, M), M), h1 = __fsub_rn(__fadd_rn(x1, M), M);
+  const float l0 = __fsub_rn(x0, h0), l1 = __fsub_rn(x1, h1);
   if constexpr (FP16) {
-    __half2 h = __floats2half2_rn(x0, x1);
-    __half2 l = __floats2half2_rn(x0 - __low2float(h), x1 - __high2float(h));
+    __half2 h = __floats2half2_rn(h0, h1);
+    __half2 l = __floats2half2_rn(l0, l1);
     *hi = *reinterpret_cast<uint32_t*>(&h);
     *lo = *reinterpret_cast<uint32_t*>(&l);
   } else {
-    __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
-    __nv_bfloat162 l = __floats2bfloat162_rn(x0 - __low2float(h), x1 - __high2float(h));
+    __nv_bfloat162 h = __floats2bfloat162_rn(h0, h1);
+    __nv_bfloat162 l = __floats2bfloat162_rn(l0, l1);
     *hi = *reinterpret_cast<uint32_t*>(&h);
     *lo = *reinterpret_cast<uint32_t*>(&l);
   }
+}
+
+// frac(<r, q>) in cycles, in [-1/2, 1/2), from the 32-bit words of the
+// fixed-point R (per pixel) and Q (per station); see the header comment.
+__device__ __forceinline__ float phase_frac_fixed(const uint32_t (&rl)[3], const uint32_t (&rh)[3], uint4 qa,
+                                                  uint2 qb) {
+  uint32_t acc = __umulhi(rl[0], qa.x) + rh[0] * qa.x + rl[0] * qa.y;
+  acc += __umulhi(rl[1], qa.z) + rh[1] * qa.z + rl[1] * qa.w;
+  acc += __umulhi(rl[2], qb.x) + rh[2] * qb.x + rl[2] * qb.y;
+  return (float)(int32_t)acc * 2.3283064365386963e-10f;  // 2^-32
 }
 
 __device__ __forceinline__ void st_shared_v4(uint32_t a, const uint32_t (&w)[4]) {
@@ -155,8 +182,9 @@ __device__ __forceinline__ void level_add(float (&acc)[MAXL], int lev, float v) 
 template <int MAXL, bool FP16>
 __global__ void __launch_bounds__(kThreads, 1)
     k_synth_tc(Batch b, Pixels px, int n_level, double* img, const TcStep* __restrict__ steps,
-               const unsigned char* __restrict__ Bpack, const float* __restrict__ scales, int n_stages,
-               int stage_bytes, int ncols_buf, int* status) {
+               const unsigned char* __restrict__ Bpack, const float* __restrict__ scales,
+               const uint32_t* __restrict__ qfix, int qfix_stride, int n_stages, int stage_bytes, int ncols_buf,
+               int* status) {
   if (*b.flag) return;  // a step of the batch failed: commit nothing
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -246,13 +274,16 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
       const int64_t r = (int64_t)tile * kRows + row;
-      float rr[6];
+      uint32_t rl[3], rh[3];  // R = round(r 2^40)
 #pragma unroll
-      for (int c = 0; c < 6; ++c) rr[c] = (r < px.n) ? px.hl[(size_t)c * px.n + r] : 0.0f;
+      for (int c = 0; c < 3; ++c) {
+        const long long R = (r < px.n) ? __double2ll_rn(px.xyz[(size_t)c * px.n + r] * 1099511627776.0) : 0ll;
+        rl[c] = (uint32_t)(unsigned long long)R;
+        rh[c] = (uint32_t)((unsigned long long)R >> 32);
+      }
       for (int t = 0; t < T && ok; ++t) {
         const int nch = steps[t].n_chunks;
-        const int n = b.nst[t];
-        const float* qv = b.q + (size_t)t * 6 * N;
+        const uint4* qv = reinterpret_cast<const uint4*>(qfix + (size_t)t * qfix_stride * 8);
         for (int c = 0; c < nch; ++c, ++ctr) {
           const uint32_t s = ctr % (uint32_t)n_stages, rnd = ctr / (uint32_t)n_stages;
           if (!mbar_wait(smem_u32(&bar_empty[s]), (rnd & 1) ^ 1, &s_abort)) {
@@ -266,14 +297,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t hw[4], lw[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
+              // padded stations have Q = 0 and zero B rows
               const int i = c * kStations + qp * 4 + j;
-              float cs = 0.0f, sn = 0.0f;
-              if (i < n) {
-                float qq[6];
-#pragma unroll
-                for (int k = 0; k < 6; ++k) qq[k] = __ldg(qv + (size_t)k * N + i);
-                sincos_cycles(phase_frac_f32(rr, qq), &sn, &cs);
-              }
+              const uint4 qa = __ldg(qv + 2 * (size_t)i);
+              const uint2 qb = __ldg(reinterpret_cast<const uint2*>(qv + 2 * (size_t)i + 1));
+              float cs, sn;
+              sincos_cycles(phase_frac_fixed(rl, rh, qa, qb), &sn, &cs);
               split2<FP16>(cs, sn, &hw[j], &lw[j]);
             }
             const uint32_t phys = (uint32_t)((qp ^ (row & 7)) << 4);
@@ -424,12 +453,32 @@ __global__ void k_tc_scale(Batch b, float* scales) {
 
 // B chunk c of step t: rows n < ncols (K-major, 128 bytes = 64 K-elements),
 // hi image then lo image, 16-byte pieces XOR-swizzled by (row & 7).
+// Also the chunk's station words for the phase: Q = round(p/wl 2^24) per
+// component as (low, high) 32-bit words, 8 words per station, zero for the
+// padded stations i >= n.
 template <bool FP16>
-__global__ void k_tc_pack(Batch b, const TcStep* steps, unsigned char* Bpack, const float* scales) {
+__global__ void k_tc_pack(Batch b, const TcStep* steps, unsigned char* Bpack, const float* scales, uint32_t* qfix,
+                          int qfix_stride) {
   const int t = blockIdx.y, c = blockIdx.x;
   const TcStep st = steps[t];
   if (c >= st.n_chunks) return;
   const int n = b.nst[t], K = b.nkept[t], KM = b.k_max, N = b.n_max;
+  if (threadIdx.x < kStations) {
+    const int i = c * kStations + threadIdx.x;
+    uint32_t wv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (i < n) {
+      const double inv_wl = 1.0 / b.wl[t];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const long long Q = __double2ll_rn(b.st[((size_t)t * 3 + k) * N + i] * inv_wl * 16777216.0);
+        wv[2 * k] = (uint32_t)(unsigned long long)Q;
+        wv[2 * k + 1] = (uint32_t)((unsigned long long)Q >> 32);
+      }
+    }
+    uint4* dst = reinterpret_cast<uint4*>(qfix + ((size_t)t * qfix_stride + i) * 8);
+    dst[0] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+    dst[1] = make_uint4(wv[4], wv[5], wv[6], wv[7]);
+  }
   const double scale = FP16 ? (double)scales[t] : 1.0;
   unsigned char* base = Bpack + st.b_off + (size_t)c * st.ncols * 256;
   for (int w = threadIdx.x; w < st.ncols * 8; w += blockDim.x) {
@@ -495,6 +544,8 @@ int tc_alloc(TcWorkspace* w, int T, int N, int K) {
   if (cudaMalloc(&w->steps, sizeof(TcStep) * T) != cudaSuccess) return -1;
   if (cudaMallocHost(&w->h_steps, sizeof(TcStep) * T) != cudaSuccess) return -1;
   if (cudaMalloc(&w->scale, sizeof(float) * T) != cudaSuccess) return -1;
+  w->qfix_stride = n_chunks_for(N) * kStations;
+  if (cudaMalloc(&w->qfix, sizeof(uint32_t) * 8 * (size_t)T * w->qfix_stride) != cudaSuccess) return -1;
   if (cudaMalloc(&w->status, sizeof(int)) != cudaSuccess) return -1;
   w->cap_T = T;
   return 0;
@@ -505,6 +556,7 @@ void tc_free(TcWorkspace* w) {
   if (w->steps) cudaFree(w->steps);
   if (w->h_steps) cudaFreeHost(w->h_steps);
   if (w->scale) cudaFree(w->scale);
+  if (w->qfix) cudaFree(w->qfix);
   if (w->status) cudaFree(w->status);
   *w = TcWorkspace{};
 }
@@ -543,7 +595,8 @@ int launch_kernel(const Batch& b, const Pixels& px, int n_level, double* img, co
       rc = -7;
       return;
     }
-    k_synth_tc<ML, F16><<<grid, kThreads, smem, s>>>(b, px, n_level, img, w->steps, w->B, w->scale, n_stages,
+    k_synth_tc<ML, F16><<<grid, kThreads, smem, s>>>(b, px, n_level, img, w->steps, w->B, w->scale, w->qfix,
+                                                      w->qfix_stride, n_stages,
                                                      stage_bytes, p.ncols_buf, w->status);
   });
   return rc;
@@ -588,8 +641,10 @@ int tc_enqueue_pack(const Batch& b, const TcPlan& p, TcWorkspace* w, cudaStream_
   if (cudaMemcpyAsync(w->steps, w->h_steps, sizeof(TcStep) * T, cudaMemcpyHostToDevice, s) != cudaSuccess) return -5;
   if (cudaMemsetAsync(w->status, 0, sizeof(int), s) != cudaSuccess) return -5;
   if (p.fp16) k_tc_scale<<<T, 256, 0, s>>>(b, w->scale);
-  if (p.fp16) k_tc_pack<true><<<dim3(p.max_chunks, T), 256, 0, s>>>(b, w->steps, w->B, w->scale);
-  else k_tc_pack<false><<<dim3(p.max_chunks, T), 256, 0, s>>>(b, w->steps, w->B, w->scale);
+  if (p.fp16)
+    k_tc_pack<true><<<dim3(p.max_chunks, T), 256, 0, s>>>(b, w->steps, w->B, w->scale, w->qfix, w->qfix_stride);
+  else
+    k_tc_pack<false><<<dim3(p.max_chunks, T), 256, 0, s>>>(b, w->steps, w->B, w->scale, w->qfix, w->qfix_stride);
   return cudaGetLastError() == cudaSuccess ? 0 : -5;
 }
 

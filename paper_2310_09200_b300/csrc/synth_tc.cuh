@@ -30,6 +30,8 @@ struct TcWorkspace {
   TcStep* steps = nullptr;     // [cap_T] device copy of the step table
   TcStep* h_steps = nullptr;   // [cap_T] pinned host step table (source of the copy, graph-safe)
   float* scale = nullptr;      // [cap_T] operand scale of the FP16 variant (W * scale)
+  uint32_t* qfix = nullptr;    // [cap_T][chunks * 32][8] station p/wl in 40.24 fixed point (see k_tc_pack)
+  int qfix_stride = 0;         // stations per step in qfix (32 * chunks of n_max)
   int* status = nullptr;       // [1] device error word (0 = ok)
   int cap_T = 0;
 };
