@@ -80,29 +80,173 @@ __global__ void k_cholesky(Batch b) {
   if (threadIdx.x == 0 && bad) b.status[t] |= kStatusNotPD;
 }
 
-// L^{-1} by forward substitution, one thread per column j; stored row-major
-// (Linv[i*N + j]) so that a warp's stores and loads are coalesced.
-__global__ void k_trinv(Batch b, int gram_identity) {
+// Blocked right-looking Cholesky G = L L^T in place (lower triangle), one CTA
+// per step: for each 32-column panel, factor its diagonal block (one warp),
+// solve the rows below against it (one thread per row) and subtract the
+// panel's outer product from the trailing lower triangle (one warp per 32 x 32
+// tile, K = 32 from shared memory). Global traffic is one read and write of
+// the trailing triangle per panel instead of per column.
+// Dynamic shared memory: (n_max + 32) x (kChB + 1) doubles: the panel,
+// row-major, plus 32 rows that the last partial tile reads and never stores.
+constexpr int kChB = 32;
+constexpr int kChThreads = 512;
+constexpr int kChLd = kChB + 1;
+
+__global__ void __launch_bounds__(kChThreads, 1) k_cholesky_blk(Batch b) {
   const int t = blockIdx.x;
   const int n = b.nst[t];
   const int N = b.n_max;
+  double* A = b.G + mat_off(t, N);
+  extern __shared__ double sP[];
+  __shared__ int bad;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int k0 = 0; k0 < n; k0 += kChB) {
+    const int bw = min(kChB, n - k0), m = n - k0;
+    for (int e = tid; e < m * bw; e += kChThreads) {
+      const int r = e % m, c = e / m;
+      sP[r * kChLd + c] = A[(size_t)(k0 + r) + (size_t)(k0 + c) * N];
+    }
+    __syncthreads();
+    if (warp == 0) {  // diagonal block, lane = row
+      for (int j = 0; j < bw; ++j) {
+        double d = 1.0;
+        if (lane == j) {
+          const double sjj = sP[j * kChLd + j];
+          if (!(sjj > 0.0)) bad = 1;
+          d = sqrt(fmax(sjj, 1e-300));
+          sP[j * kChLd + j] = d;
+        }
+        d = __shfl_sync(0xffffffffu, d, j);
+        if (lane > j && lane < bw) sP[lane * kChLd + j] /= d;
+        __syncwarp();
+        if (lane > j && lane < bw) {
+          const double lij = sP[lane * kChLd + j];
+          for (int c = j + 1; c <= lane; ++c) sP[lane * kChLd + c] -= lij * sP[c * kChLd + j];
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    if (bad) break;
+    for (int r = bw + tid; r < m; r += kChThreads) {  // x L_dd^T = p, forward substitution
+      double* x = sP + r * kChLd;
+      for (int j = 0; j < bw; ++j) {
+        double sj = x[j];
+        for (int k = 0; k < j; ++k) sj -= x[k] * sP[j * kChLd + k];
+        x[j] = sj / sP[j * kChLd + j];
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < m * bw; e += kChThreads) {
+      const int r = e % m, c = e / m;
+      if (r >= c) A[(size_t)(k0 + r) + (size_t)(k0 + c) * N] = sP[r * kChLd + c];
+    }
+    // trailing lower triangle: A(i, j) -= sum_k P(i, k) P(j, k) for k0 + bw <= j <= i < n
+    const int m2 = m - bw, nt = (m2 + 31) / 32;
+    int tile = 0;
+    for (int ti = 0; ti < nt; ++ti) {
+      for (int tj = 0; tj <= ti; ++tj, ++tile) {
+        if (tile % (kChThreads / 32) != warp) continue;
+        const int i = ti * 32 + lane;
+        if (i >= m2) continue;
+        double acc[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) acc[c] = 0.0;
+        const double* pi = sP + (bw + i) * kChLd;
+        const double* pj = sP + (bw + tj * 32) * kChLd;
+        for (int k = 0; k < bw; ++k) {
+          const double pik = pi[k];
+#pragma unroll
+          for (int c = 0; c < 32; ++c) acc[c] = fma(pik, pj[c * kChLd + k], acc[c]);
+        }
+        double* Ai = A + (size_t)(k0 + bw + i);
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          const int j = tj * 32 + c;
+          if (j <= i && j < m2) Ai[(size_t)(k0 + bw + j) * N] -= acc[c];
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && bad) b.status[t] |= kStatusNotPD;
+}
+
+// L^{-1} column block by column block: one CTA per (32-column block cb, step)
+// solves L Y = E[:, cb] by block forward substitution, Y_i = L_ii^{-1}
+// (E_i - sum_{cb <= j < i} L_ij Y_j) over 32-row blocks i >= cb (Y_i = 0 for
+// i < cb). The products are 32 x 32 x 32 tiles staged in shared memory; the
+// diagonal solves run one thread per column. Stored row-major (Linv[i*N + j]).
+constexpr int kTiThreads = 256;
+
+__global__ void __launch_bounds__(kTiThreads) k_trinv_blk(Batch b, int gram_identity) {
+  const int t = blockIdx.y, cb = blockIdx.x;
+  const int n = b.nst[t];
+  const int N = b.n_max;
+  const int c0 = cb * 32;
+  if (c0 >= n || b.status[t]) return;
   const double* L = b.G + mat_off(t, N);
   double* R = b.Linv + mat_off(t, N);
-  if (b.status[t]) return;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    for (int i = 0; i < n; ++i) {
-      double x;
-      if (gram_identity) {
-        x = (i == j) ? 1.0 : 0.0;
-      } else if (i < j) {
-        x = 0.0;
-      } else {
-        double s = (i == j) ? 1.0 : 0.0;
-        for (int k = j; k < i; ++k) s -= L[i + (size_t)k * N] * R[(size_t)k * N + j];
-        x = s / L[i + (size_t)i * N];
+  const int cw = min(32, n - c0);
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;  // 8 rows of 4 outputs per thread
+  __shared__ double sL[32][33], sY[32][33], sAcc[32][33];
+  // rows above the block are zero
+  for (int e = tid; e < c0 * cw; e += kTiThreads) {
+    const int i = e / cw, j = e % cw;
+    R[(size_t)i * N + c0 + j] = 0.0;
+  }
+  for (int i0 = c0; i0 < n; i0 += 32) {
+    const int rh = min(32, n - i0);
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};  // rows ty + 8u, column tx
+    if (!gram_identity) {
+      for (int j0 = c0; j0 < i0; j0 += 32) {
+        __syncthreads();
+        for (int e = tid; e < 32 * 32; e += kTiThreads) {
+          const int r = e % 32, k = e / 32;  // L tile: column-major reads
+          sL[r][k] = (i0 + r < n) ? L[(size_t)(i0 + r) + (size_t)(j0 + k) * N] : 0.0;
+          const int kr = e / 32, c = e % 32;  // Y tile: row-major reads
+          sY[kr][c] = (c < cw && j0 + kr < n) ? R[(size_t)(j0 + kr) * N + c0 + c] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+          const double y = sY[k][tx];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) acc[u] = fma(sL[ty + 8 * u][k], y, acc[u]);
+        }
       }
-      R[(size_t)i * N + j] = x;
     }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int r = ty + 8 * u;
+      sAcc[r][tx] = ((i0 + r == c0 + tx) ? 1.0 : 0.0) - acc[u];  // E_i - sum
+    }
+    for (int e = tid; e < 32 * 32; e += kTiThreads) {  // diagonal block of L
+      const int r = e % 32, k = e / 32;
+      sL[r][k] = (r < rh && k < rh) ? L[(size_t)(i0 + r) + (size_t)(i0 + k) * N] : (r == k ? 1.0 : 0.0);
+    }
+    __syncthreads();
+    if (tid < 32) {  // column tid: forward substitution with L_ii
+      for (int r = 0; r < rh; ++r) {
+        double sr = sAcc[r][tid];
+        if (gram_identity) {
+          sAcc[r][tid] = sr;
+          continue;
+        }
+        for (int k = 0; k < r; ++k) sr -= sL[r][k] * sAcc[k][tid];
+        sAcc[r][tid] = sr / sL[r][r];
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < rh * cw; e += kTiThreads) {
+      const int r = e / cw, c = e % cw;
+      R[(size_t)(i0 + r) * N + c0 + c] = sAcc[r][c];
+    }
+    // the next block row reads these rows of Y back through global memory
+    __threadfence_block();
   }
 }
 
@@ -112,7 +256,8 @@ constexpr int GT = 32;  // output tile
 constexpr int GK = 16;  // k tile
 
 // mode 0: X = Linv V           X(i,j) = sum_{k <= i} Linv(i,k) V(k,j)
-// mode 1: C = X Linv^T         C(i,j) = sum_{k <= j} X(i,k) Linv(j,k)
+// mode 1: C = X Linv^T         C(i,j) = sum_{k <= j} X(i,k) Linv(j,k); C is
+//         Hermitian, so only tiles with i0 <= j0 are formed and mirrored.
 template <int MODE>
 __global__ void k_reduce_gemm(Batch b) {
   const int t = blockIdx.z;
@@ -121,6 +266,7 @@ __global__ void k_reduce_gemm(Batch b) {
   if (b.status[t]) return;
   const int i0 = blockIdx.x * GT, j0 = blockIdx.y * GT;
   if (i0 >= n || j0 >= n) return;
+  if (MODE == 1 && i0 > j0) return;
   const double* Linv = b.Linv + mat_off(t, N);
   const double2* Z = (MODE == 0) ? (b.vis + mat_off(t, N)) : (b.X + mat_off(t, N));
   double2* out = (MODE == 0) ? (b.X + mat_off(t, N)) : (b.C + mat_off(t, N));
@@ -172,7 +318,10 @@ __global__ void k_reduce_gemm(Batch b) {
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     int i = i0 + tx, j = j0 + ty + 8 * u;
-    if (i < n && j < n) out[(size_t)i + (size_t)j * N] = acc[u];
+    if (i < n && j < n) {
+      out[(size_t)i + (size_t)j * N] = acc[u];
+      if (MODE == 1 && i0 != j0) out[(size_t)j + (size_t)i * N] = make_double2(acc[u].x, -acc[u].y);
+    }
   }
 }
 
@@ -296,8 +445,16 @@ void launch_gram(const Batch& b, int gram_identity, cudaStream_t s) {
 }
 
 void launch_cholesky(const Batch& b, int gram_identity, cudaStream_t s) {
-  if (!gram_identity) k_cholesky<<<b.T, 256, 0, s>>>(b);
-  k_trinv<<<b.T, 256, 0, s>>>(b, gram_identity);
+  const size_t smem = sizeof(double) * (size_t)(b.n_max + 32) * kChLd;
+  if (!gram_identity) {
+    if (smem <= 200 * 1024) {
+      cudaFuncSetAttribute(k_cholesky_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_cholesky_blk<<<b.T, kChThreads, smem, s>>>(b);
+    } else {
+      k_cholesky<<<b.T, 256, 0, s>>>(b);
+    }
+  }
+  k_trinv_blk<<<dim3((b.n_max + 31) / 32, b.T), kTiThreads, 0, s>>>(b, gram_identity);
 }
 
 void launch_reduce(const Batch& b, int gram_identity, cudaStream_t s) {
