@@ -1,0 +1,51 @@
+// dfloat.cuh — double-float ("float-float") arithmetic: a value is carried as
+// an unevaluated sum hi + lo of two floats (~48 significant bits), so that
+// FP64-class dense products run on the FP32 pipe, which on B300 issues 64
+// FMAs for every FP64 one.
+//
+// Multiply-accumulate (hi, lo) += a * b follows the classic error-free
+// transformations: the high product's rounding error is recovered exactly by
+// an FMA (Dekker / Kahan product), the high parts are added with Knuth's
+// TwoSum, and the small terms (cross products, both rounding errors) go to the
+// low accumulator; a_lo * b_lo (~2^-48 relative) is dropped. Accumulating K
+// terms gives a relative error of order K 2^-48 in the worst case and
+// sqrt(K) 2^-48 typically (about 1e-13 at K = 512), with the low word
+// renormalised into the high word after every block of terms. Inputs must lie
+// in the FP32 range; the low word of values below ~1e-31 is subnormal and
+// carries fewer bits.
+#pragma once
+
+namespace bipp {
+namespace df {
+
+// x = hi + lo with hi = fl32(x), lo = fl32(x - hi).
+__device__ __forceinline__ void split(double x, float& hi, float& lo) {
+  hi = __double2float_rn(x);
+  lo = __double2float_rn(x - (double)hi);
+}
+
+// (sh, sl) += (ah + al) * (bh + bl).
+__device__ __forceinline__ void mac(float& sh, float& sl, float ah, float al, float bh, float bl) {
+  const float ph = __fmul_rn(ah, bh);
+  float pl = fmaf(ah, bh, -ph);
+  pl = fmaf(ah, bl, pl);
+  pl = fmaf(al, bh, pl);
+  const float t = __fadd_rn(sh, ph);
+  const float z = __fsub_rn(t, sh);
+  const float e = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, z)), __fsub_rn(ph, z));
+  sh = t;
+  sl = __fadd_rn(sl, __fadd_rn(e, pl));
+}
+
+// Fold the low word into the high one (Fast2Sum, |sl| <= |sh| up to the
+// accumulated small terms).
+__device__ __forceinline__ void renorm(float& sh, float& sl) {
+  const float t = __fadd_rn(sh, sl);
+  sl = __fsub_rn(sl, __fsub_rn(t, sh));
+  sh = t;
+}
+
+__device__ __forceinline__ double to_double(float hi, float lo) { return (double)hi + (double)lo; }
+
+}  // namespace df
+}  // namespace bipp

@@ -29,6 +29,7 @@
 #include <algorithm>
 
 #include "bipp_internal.cuh"
+#include "dfloat.cuh"
 #include "jacobi.cuh"
 #include "tridiag32.cuh"
 
@@ -117,6 +118,82 @@ __global__ void k_zgemm(const int* nst, const int* kp, int mc, int nc, int kc, c
   for (int u = 0; u < 4; ++u) {
     const int i = i0 + tx, j = j0 + ty + 8 * u;
     if (i < M && j < NN) out[(size_t)i + (size_t)j * ldo] = acc[u];
+  }
+}
+
+// The FP64 products of the refinement in double-float arithmetic (dfloat.cuh):
+// same operands, layout and result as k_zgemm<double, double2, CONJ_T>, with
+// ~2^-48 relative rounding per operation instead of 2^-53, at several times
+// the FP64 pipe's rate. Operands are split into hi/lo floats once per tile.
+template <bool CONJ_T>
+__global__ void k_zgemm_df(const int* nst, const int* kp, int mc, int nc, int kc, const double2* A, size_t sa,
+                           int lda, const double2* B, size_t sb, int ldb, double2* out, size_t so, int ldo,
+                           const int* status, const int* st2) {
+  const int t = blockIdx.z;
+  if (mx_skip(status, st2, t)) return;
+  const int n = nst[t], k_p = kp[t];
+  const int M = dim_of(mc, n, k_p), NN = dim_of(nc, n, k_p), K = dim_of(kc, n, k_p);
+  const int i0 = blockIdx.x * GT, j0 = blockIdx.y * GT;
+  if (i0 >= M || j0 >= NN) return;
+  A += (size_t)t * sa;
+  B += (size_t)t * sb;
+  out += (size_t)t * so;
+  __shared__ float4 sA[GK][GT + 1];  // (re hi, re lo, im hi, im lo)
+  __shared__ float4 sB[GK][GT + 1];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  float acc[4][4];  // [u][re hi, re lo, im hi, im lo]
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[u][c] = 0.f;
+  for (int k0 = 0; k0 < K; k0 += GK) {
+    for (int e = threadIdx.x; e < GK * GT; e += blockDim.x) {
+      const int kk = e / GT, ii = e % GT, k = k0 + kk;
+      const int i = i0 + ii, j = j0 + ii;
+      double2 a = make_double2(0.0, 0.0), bv = make_double2(0.0, 0.0);
+      if (k < K && i < M) {
+        if (CONJ_T) {
+          a = A[(size_t)k + (size_t)i * lda];
+          a.y = -a.y;
+        } else {
+          a = A[(size_t)i + (size_t)k * lda];
+        }
+      }
+      if (k < K && j < NN) bv = B[(size_t)k + (size_t)j * ldb];
+      float4 fa, fb;
+      df::split(a.x, fa.x, fa.y);
+      df::split(a.y, fa.z, fa.w);
+      df::split(bv.x, fb.x, fb.y);
+      df::split(bv.y, fb.z, fb.w);
+      sA[kk][ii] = fa;
+      sB[kk][ii] = fb;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < GK; ++kk) {
+      const float4 a = sA[kk][tx];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float4 bv = sB[kk][ty + 8 * u];
+        df::mac(acc[u][0], acc[u][1], a.x, a.y, bv.x, bv.y);    // re += ar br
+        df::mac(acc[u][0], acc[u][1], -a.z, -a.w, bv.z, bv.w);  //     - ai bi
+        df::mac(acc[u][2], acc[u][3], a.x, a.y, bv.z, bv.w);    // im += ar bi
+        df::mac(acc[u][2], acc[u][3], a.z, a.w, bv.x, bv.y);    //     + ai br
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      df::renorm(acc[u][0], acc[u][1]);
+      df::renorm(acc[u][2], acc[u][3]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = i0 + tx, j = j0 + ty + 8 * u;
+    if (i < M && j < NN)
+      out[(size_t)i + (size_t)j * ldo] = make_double2(df::to_double(acc[u][0], acc[u][1]),
+                                                      df::to_double(acc[u][2], acc[u][3]));
   }
 }
 
@@ -353,6 +430,14 @@ __global__ void k_mx_final(Batch b, MixedWs w, double rtol) {
   }
 }
 
+template <bool CT>
+void zgemm_df(const Batch& b, const MixedWs& w, int mc, int nc, int kc, int mmax, int nmax, const double2* A,
+              size_t sa, int lda, const double2* B, size_t sb, int ldb, double2* out, size_t so, int ldo,
+              cudaStream_t s) {
+  dim3 grd((mmax + GT - 1) / GT, (nmax + GT - 1) / GT, b.T);
+  k_zgemm_df<CT><<<grd, 256, 0, s>>>(b.nst, w.kp, mc, nc, kc, A, sa, lda, B, sb, ldb, out, so, ldo, b.status, w.st2);
+}
+
 template <typename R, typename TA, bool CT>
 void zgemm(const Batch& b, const MixedWs& w, int mc, int nc, int kc, int mmax, int nmax, const TA* A, size_t sa,
            int lda, const typename CplxOf<R>::T* B, size_t sb, int ldb, typename CplxOf<R>::T* out, size_t so,
@@ -412,15 +497,15 @@ void launch_eig_mixed(const Batch& b, const MixedWs& w, double tol, int max_swee
   cudaMemsetAsync(w.st2, 0, sizeof(int) * T, s);
   const int ew = std::max(1, (N * KP + 255) / 256 / 8);  // blocks per problem of the elementwise kernels
   for (int pass = 0; pass < kPasses; ++pass) {
-    zgemm<double, double2, true>(b, w, DKP, DKP, DN, KP, KP, P0, NN, N, P0, NN, N, Hs, NN, KP, s);   // S = X^H X
+    zgemm_df<true>(b, w, DKP, DKP, DN, KP, KP, P0, NN, N, P0, NN, N, Hs, NN, KP, s);   // S = X^H X
     k_mx_cholinv<<<T, 128, 0, s>>>(b, w, Hs, Ws, NN, KP);                                          // W = R^{-1}
-    zgemm<double, double2, false>(b, w, DN, DKP, DKP, N, KP, P0, NN, N, Ws, NN, KP, P1, NN, N, s);  // X1 = X W
-    zgemm<double, double2, false>(b, w, DN, DKP, DN, N, KP, b.C, NN, N, P1, NN, N, P2, NN, N, s);   // Y = C X1
-    zgemm<double, double2, true>(b, w, DKP, DKP, DN, KP, KP, P1, NN, N, P2, NN, N, Hs, NN, KP, s);  // H = X1^H Y
+    zgemm_df<false>(b, w, DN, DKP, DKP, N, KP, P0, NN, N, Ws, NN, KP, P1, NN, N, s);  // X1 = X W
+    zgemm_df<false>(b, w, DN, DKP, DN, N, KP, b.C, NN, N, P1, NN, N, P2, NN, N, s);   // Y = C X1
+    zgemm_df<true>(b, w, DKP, DKP, DN, KP, KP, P1, NN, N, P2, NN, N, Hs, NN, KP, s);  // H = X1^H Y
     k_mx_herm<<<T, 256, 0, s>>>(b, w, Hs, NN, KP);
     launch_jacobi_args(h, T, false, 1e-15, 60, s);                                                // H = U th U^H
-    zgemm<double, double2, false>(b, w, DN, DKP, DKP, N, KP, P1, NN, N, Us, NN, KP, P0, NN, N, s);  // X = X1 U
-    zgemm<double, double2, false>(b, w, DN, DKP, DKP, N, KP, P2, NN, N, Us, NN, KP, P3, NN, N, s);  // Y U
+    zgemm_df<false>(b, w, DN, DKP, DKP, N, KP, P1, NN, N, Us, NN, KP, P0, NN, N, s);  // X = X1 U
+    zgemm_df<false>(b, w, DN, DKP, DKP, N, KP, P2, NN, N, Us, NN, KP, P3, NN, N, s);  // Y U
     k_mx_resid<<<dim3(KP, T), 256, 0, s>>>(b, w, P0, P3, R32, NN);                                // R = YU - X th
     if (pass == kPasses - 1) break;
     k_mx_check<<<(T + 127) / 128, 128, 0, s>>>(b, w, 10.0 * tol);
