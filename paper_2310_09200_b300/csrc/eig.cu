@@ -11,6 +11,7 @@
 #include <math.h>
 
 #include "bipp_internal.cuh"
+#include "dfloat.cuh"
 #include "jacobi.cuh"
 
 namespace bipp {
@@ -258,8 +259,11 @@ constexpr int GK = 16;  // k tile
 // mode 0: X = Linv V           X(i,j) = sum_{k <= i} Linv(i,k) V(k,j)
 // mode 1: C = X Linv^T         C(i,j) = sum_{k <= j} X(i,k) Linv(j,k); C is
 //         Hermitian, so only tiles with i0 <= j0 are formed and mirrored.
+// Both products in double-float arithmetic (dfloat.cuh): FP64-class results
+// (~1e-13 relative at N = 512) on the FP32 pipe, which issues 64 FMAs per
+// FP64 one on B300. Operands are split into hi/lo floats once per tile.
 template <int MODE>
-__global__ void k_reduce_gemm(Batch b) {
+__global__ void k_reduce_gemm_df(Batch b) {
   const int t = blockIdx.z;
   const int n = b.nst[t];
   const int N = b.n_max;
@@ -270,57 +274,63 @@ __global__ void k_reduce_gemm(Batch b) {
   const double* Linv = b.Linv + mat_off(t, N);
   const double2* Z = (MODE == 0) ? (b.vis + mat_off(t, N)) : (b.X + mat_off(t, N));
   double2* out = (MODE == 0) ? (b.X + mat_off(t, N)) : (b.C + mat_off(t, N));
-  __shared__ double sR[GK][GT + 1];
-  __shared__ double2 sZ[GK][GT + 1];
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 256 threads: 32 x 8
-  double2 acc[4];
+  __shared__ float2 sR[GK][GT + 1];  // (hi, lo)
+  __shared__ float4 sZ[GK][GT + 1];  // (re hi, re lo, im hi, im lo)
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  float acc[4][4];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) acc[u] = make_double2(0.0, 0.0);
-  // triangular structure: Linv(i,k) = 0 for k > i (mode 0), Linv(j,k) = 0 for k > j (mode 1)
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[u][c] = 0.f;
   const int kend = min(n, (MODE == 0 ? i0 : j0) + GT);
   for (int k0 = 0; k0 < kend; k0 += GK) {
     for (int e = threadIdx.x; e < GK * GT; e += blockDim.x) {
-      int kk = e / GT, ii = e % GT;
-      int k = k0 + kk;
+      const int kk = e / GT, ii = e % GT, k = k0 + kk;
+      double r;
+      double2 z;
       if (MODE == 0) {
-        int i = i0 + ii;
-        sR[kk][ii] = (k < n && i < n) ? Linv[(size_t)i * N + k] : 0.0;
-        int j = j0 + ii;
-        sZ[kk][ii] = (k < n && j < n) ? Z[(size_t)k + (size_t)j * N] : make_double2(0.0, 0.0);
+        const int i = i0 + ii, j = j0 + ii;
+        r = (k < n && i < n) ? Linv[(size_t)i * N + k] : 0.0;
+        z = (k < n && j < n) ? Z[(size_t)k + (size_t)j * N] : make_double2(0.0, 0.0);
       } else {
-        int i = i0 + ii;
-        sZ[kk][ii] = (k < n && i < n) ? Z[(size_t)i + (size_t)k * N] : make_double2(0.0, 0.0);
-        int j = j0 + ii;
-        sR[kk][ii] = (k < n && j < n) ? Linv[(size_t)j * N + k] : 0.0;
+        const int i = i0 + ii, j = j0 + ii;
+        z = (k < n && i < n) ? Z[(size_t)i + (size_t)k * N] : make_double2(0.0, 0.0);
+        r = (k < n && j < n) ? Linv[(size_t)j * N + k] : 0.0;
       }
+      float2 fr;
+      float4 fz;
+      df::split(r, fr.x, fr.y);
+      df::split(z.x, fz.x, fz.y);
+      df::split(z.y, fz.z, fz.w);
+      sR[kk][ii] = fr;
+      sZ[kk][ii] = fz;
     }
     __syncthreads();
-#pragma unroll
+#pragma unroll 4
     for (int kk = 0; kk < GK; ++kk) {
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        int ii = tx, jj = ty + 8 * u;
-        if (MODE == 0) {
-          double r = sR[kk][ii];
-          double2 z = sZ[kk][jj];
-          acc[u].x = fma(r, z.x, acc[u].x);
-          acc[u].y = fma(r, z.y, acc[u].y);
-        } else {
-          double2 z = sZ[kk][ii];
-          double r = sR[kk][jj];
-          acc[u].x = fma(z.x, r, acc[u].x);
-          acc[u].y = fma(z.y, r, acc[u].y);
-        }
+        const int ii = tx, jj = ty + 8 * u;
+        const float2 r = (MODE == 0) ? sR[kk][ii] : sR[kk][jj];
+        const float4 z = (MODE == 0) ? sZ[kk][jj] : sZ[kk][ii];
+        df::mac(acc[u][0], acc[u][1], r.x, r.y, z.x, z.y);
+        df::mac(acc[u][2], acc[u][3], r.x, r.y, z.z, z.w);
       }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      df::renorm(acc[u][0], acc[u][1]);
+      df::renorm(acc[u][2], acc[u][3]);
     }
     __syncthreads();
   }
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
-    int i = i0 + tx, j = j0 + ty + 8 * u;
+    const int i = i0 + tx, j = j0 + ty + 8 * u;
     if (i < n && j < n) {
-      out[(size_t)i + (size_t)j * N] = acc[u];
-      if (MODE == 1 && i0 != j0) out[(size_t)j + (size_t)i * N] = make_double2(acc[u].x, -acc[u].y);
+      const double2 v = make_double2(df::to_double(acc[u][0], acc[u][1]), df::to_double(acc[u][2], acc[u][3]));
+      out[(size_t)i + (size_t)j * N] = v;
+      if (MODE == 1 && i0 != j0) out[(size_t)j + (size_t)i * N] = make_double2(v.x, -v.y);
     }
   }
 }
@@ -464,8 +474,8 @@ void launch_reduce(const Batch& b, int gram_identity, cudaStream_t s) {
     return;
   }
   dim3 grd((b.n_max + GT - 1) / GT, (b.n_max + GT - 1) / GT, b.T);
-  k_reduce_gemm<0><<<grd, 256, 0, s>>>(b);
-  k_reduce_gemm<1><<<grd, 256, 0, s>>>(b);
+  k_reduce_gemm_df<0><<<grd, 256, 0, s>>>(b);
+  k_reduce_gemm_df<1><<<grd, 256, 0, s>>>(b);
   k_hermitize<<<hg, hb, 0, s>>>(b, 0);
 }
 
