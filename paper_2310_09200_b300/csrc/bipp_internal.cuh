@@ -77,9 +77,9 @@ void launch_gram(const Batch& b, int gram_identity, cudaStream_t s);
 void launch_cholesky(const Batch& b, int gram_identity, cudaStream_t s);
 void launch_reduce(const Batch& b, int gram_identity, cudaStream_t s);
 void launch_jacobi(const Batch& b, double tol, int max_sweeps, cudaStream_t s);
-// Mixed-precision eigensolve (FP32 Jacobi + FP64 refinement of the leading
-// pairs); needs the X and Q buffers of the batch as scratch, which fits when
-// eig_mixed_fits(n_max, KP).
+// Mixed-precision eigensolve (FP32 tridiagonal eigendecomposition + FP64-class
+// refinement of the leading pairs); needs the X and Q buffers of the batch as
+// scratch, which fits when eig_mixed_fits(n_max, KP).
 bool eig_mixed_fits(int n_max, int KP);
 constexpr int kMixedLaunches = 61;  // kernels launched by launch_eig_mixed
 void launch_eig_mixed(const Batch& b, const MixedWs& w, double tol, int max_sweeps, cudaStream_t s);

@@ -256,61 +256,79 @@ __global__ void k_mx_pick(Batch b, MixedWs w) {
 
 // S = R^H R (Cholesky, upper R) of the kp x kp Gram matrix of X, then
 // W = R^{-1} (upper), so that X W has orthonormal columns. One CTA per step.
+// S = R^H R (upper Cholesky) and W = R^{-1}, one CTA per step, in one
+// kp x kp shared-memory buffer: R in the upper triangle, W transposed into
+// the strict lower triangle (W(i, c) at (c, i)) with its diagonal beside it.
+// The factorisation is right-looking (row j of R, then the trailing update in
+// parallel); W is solved one thread per column.
+// Dynamic shared memory: (kp_max^2 + kp_max) complex doubles.
 __global__ void k_mx_cholinv(Batch b, MixedWs w, const double2* S0, double2* W0, size_t stride, int ld) {
   const int t = blockIdx.x;
   if (mx_skip(b.status, w.st2, t)) return;
   const int kp = w.kp[t];
-  double2* S = const_cast<double2*>(S0) + (size_t)t * stride;
+  const double2* S = S0 + (size_t)t * stride;
   double2* W = W0 + (size_t)t * stride;
+  extern __shared__ __align__(16) unsigned char cism[];
+  double2* B = reinterpret_cast<double2*>(cism);  // column-major, leading dimension kp
+  double2* wd = B + (size_t)kp * kp;              // diagonal of W
   __shared__ int bad;
+  __shared__ double s_inv;
   if (threadIdx.x == 0) bad = 0;
+  for (int e = threadIdx.x; e < kp * kp; e += blockDim.x) {
+    const int i = e % kp, c = e / kp;
+    if (i <= c) B[e] = S[(size_t)i + (size_t)c * ld];
+  }
   __syncthreads();
-  // in-place upper Cholesky S = R^H R (R stored in the upper triangle of S)
   for (int j = 0; j < kp; ++j) {
     if (threadIdx.x == 0) {
-      double d = S[j + (size_t)j * ld].x;
-      for (int k = 0; k < j; ++k) {
-        const double2 r = S[k + (size_t)j * ld];
-        d -= r.x * r.x + r.y * r.y;
-      }
+      const double d = B[j + (size_t)j * kp].x;
       if (!(d > 0.0)) bad = 1;
-      S[j + (size_t)j * ld] = make_double2(sqrt(fmax(d, 1e-300)), 0.0);
+      const double r = sqrt(fmax(d, 1e-300));
+      B[j + (size_t)j * kp] = make_double2(r, 0.0);
+      s_inv = 1.0 / r;
     }
     __syncthreads();
-    const double rjj = S[j + (size_t)j * ld].x;
+    const double inv = s_inv;
     for (int c = j + 1 + threadIdx.x; c < kp; c += blockDim.x) {
-      // R[j, c] = (S[j, c] - sum_k conj(R[k, j]) R[k, c]) / R[j, j]
-      double2 s = S[j + (size_t)c * ld];
-      for (int k = 0; k < j; ++k) {
-        const double2 a = S[k + (size_t)j * ld], bb = S[k + (size_t)c * ld];
-        s.x -= a.x * bb.x + a.y * bb.y;
-        s.y -= a.x * bb.y - a.y * bb.x;
-      }
-      S[j + (size_t)c * ld] = make_double2(s.x / rjj, s.y / rjj);
+      const double2 v = B[j + (size_t)c * kp];
+      B[j + (size_t)c * kp] = make_double2(v.x * inv, v.y * inv);
+    }
+    __syncthreads();
+    const int m = kp - j - 1;  // S(c1, c2) -= conj(R(j, c1)) R(j, c2), j < c1 <= c2
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int c1 = j + 1 + e % m, c2 = j + 1 + e / m;
+      if (c1 > c2) continue;
+      const double2 a1 = B[j + (size_t)c1 * kp], a2 = B[j + (size_t)c2 * kp];
+      double2 v = B[c1 + (size_t)c2 * kp];
+      v.x -= a1.x * a2.x + a1.y * a2.y;
+      v.y -= a1.x * a2.y - a1.y * a2.x;
+      B[c1 + (size_t)c2 * kp] = v;
     }
     __syncthreads();
   }
-  // W = R^{-1}: column c solves R w = e_c (back substitution), one thread per column
+  // W = R^{-1}: column c solves R w = e_c from the bottom up
   for (int c = threadIdx.x; c < kp; c += blockDim.x) {
-    for (int i = kp - 1; i >= 0; --i) {
-      double2 s = make_double2(i == c ? 1.0 : 0.0, 0.0);
-      if (i < c || i == c) {
-        for (int k = i + 1; k <= c; ++k) {
-          const double2 r = S[i + (size_t)k * ld], x = W[k + (size_t)c * ld];
-          s.x -= r.x * x.x - r.y * x.y;
-          s.y -= r.x * x.y + r.y * x.x;
-        }
-        const double rii = S[i + (size_t)i * ld].x;
-        W[i + (size_t)c * ld] = (i <= c) ? make_double2(s.x / rii, s.y / rii) : make_double2(0.0, 0.0);
-      } else {
-        W[i + (size_t)c * ld] = make_double2(0.0, 0.0);
+    for (int i = c; i >= 0; --i) {
+      double2 sm = make_double2(i == c ? 1.0 : 0.0, 0.0);
+      for (int k = i + 1; k <= c; ++k) {
+        const double2 r = B[i + (size_t)k * kp];
+        const double2 x = (k == c) ? wd[c] : B[c + (size_t)k * kp];
+        sm.x -= r.x * x.x - r.y * x.y;
+        sm.y -= r.x * x.y + r.y * x.x;
       }
+      const double rii = B[i + (size_t)i * kp].x;
+      const double2 v = make_double2(sm.x / rii, sm.y / rii);
+      if (i == c) wd[c] = v;
+      else B[c + (size_t)i * kp] = v;
     }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kp * kp; e += blockDim.x) {
+    const int i = e % kp, c = e / kp;
+    W[(size_t)i + (size_t)c * ld] = (i < c) ? B[c + (size_t)i * kp] : (i == c ? wd[c] : make_double2(0.0, 0.0));
   }
   if (threadIdx.x == 0 && bad) b.status[t] |= kStatusNotConverged;
 }
-
-// H <- (H + H^H)/2 on the kp x kp block.
 __global__ void k_mx_herm(Batch b, MixedWs w, double2* H0, size_t stride, int ld) {
   const int t = blockIdx.x;
   if (mx_skip(b.status, w.st2, t)) return;
@@ -449,7 +467,9 @@ void zgemm(const Batch& b, const MixedWs& w, int mc, int nc, int kc, int mmax, i
 
 }  // namespace
 
-bool eig_mixed_fits(int N, int KP) { return 4LL * N * KP + 3LL * KP * KP <= (long long)N * N; }
+// The refinement's blocks must fit the Q buffer, and the kp x kp Cholesky of
+// k_mx_cholinv its shared memory (kp <= 110: 195 KB).
+bool eig_mixed_fits(int N, int KP) { return KP <= 110 && 4LL * N * KP + 3LL * KP * KP <= (long long)N * N; }
 
 void launch_eig_mixed(const Batch& b, const MixedWs& w, double tol, int max_sweeps, cudaStream_t s) {
   const int N = b.n_max, KP = w.KP, T = b.T;
@@ -496,14 +516,16 @@ void launch_eig_mixed(const Batch& b, const MixedWs& w, double tol, int max_swee
   h.report_nonconv = 1;
   cudaMemsetAsync(w.st2, 0, sizeof(int) * T, s);
   const int ew = std::max(1, (N * KP + 255) / 256 / 8);  // blocks per problem of the elementwise kernels
+  const int ci_smem = (int)(sizeof(double2) * ((size_t)KP * KP + KP));
+  cudaFuncSetAttribute(k_mx_cholinv, cudaFuncAttributeMaxDynamicSharedMemorySize, ci_smem);
   for (int pass = 0; pass < kPasses; ++pass) {
     zgemm_df<true>(b, w, DKP, DKP, DN, KP, KP, P0, NN, N, P0, NN, N, Hs, NN, KP, s);   // S = X^H X
-    k_mx_cholinv<<<T, 128, 0, s>>>(b, w, Hs, Ws, NN, KP);                                          // W = R^{-1}
+    k_mx_cholinv<<<T, 256, ci_smem, s>>>(b, w, Hs, Ws, NN, KP);                                    // W = R^{-1}
     zgemm_df<false>(b, w, DN, DKP, DKP, N, KP, P0, NN, N, Ws, NN, KP, P1, NN, N, s);  // X1 = X W
     zgemm_df<false>(b, w, DN, DKP, DN, N, KP, b.C, NN, N, P1, NN, N, P2, NN, N, s);   // Y = C X1
     zgemm_df<true>(b, w, DKP, DKP, DN, KP, KP, P1, NN, N, P2, NN, N, Hs, NN, KP, s);  // H = X1^H Y
     k_mx_herm<<<T, 256, 0, s>>>(b, w, Hs, NN, KP);
-    launch_jacobi_args(h, T, false, 1e-15, 60, s);                                                // H = U th U^H
+    launch_jacobi_small(h, T, KP, 1e-14, 60, s);                                                  // H = U th U^H
     zgemm_df<false>(b, w, DN, DKP, DKP, N, KP, P1, NN, N, Us, NN, KP, P0, NN, N, s);  // X = X1 U
     zgemm_df<false>(b, w, DN, DKP, DKP, N, KP, P2, NN, N, Us, NN, KP, P3, NN, N, s);  // Y U
     k_mx_resid<<<dim3(KP, T), 256, 0, s>>>(b, w, P0, P3, R32, NN);                                // R = YU - X th

@@ -83,16 +83,28 @@ constexpr int kJacobiThreads = 512;
 // only the blocks on or above the diagonal computed and the ones below
 // written as their conjugate transposes, and Q <- Q J. For odd n a phantom
 // index n pairs with one real index per round (identity rotation).
-template <typename R>
+// CSM: C is staged in dynamic shared memory (leading dimension n) for the
+// sweeps, for small matrices whose scattered 2x2 accesses would otherwise
+// wait on L2 every round; only its diagonal goes back (mu), Q stays in place.
+template <typename R, bool CSM = false>
 __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_t(JacobiArgs a, double tol, int max_sweeps) {
   using C2 = typename CplxOf<R>::T;
   using namespace jac;
   const int t = blockIdx.x;
   const int n = a.n[t];
-  const int N = a.ld;
   if (a.status[t]) return;
-  C2* C = static_cast<C2*>(a.C) + (size_t)t * a.stride;
   C2* Q = static_cast<C2*>(a.Q) + (size_t)t * a.stride;
+  const int NQ = a.ld;  // leading dimension of Q (and of C in global memory)
+  C2* C = static_cast<C2*>(a.C) + (size_t)t * a.stride;
+  int N = a.ld;         // leading dimension of C where the sweeps run
+  if constexpr (CSM) {
+    extern __shared__ __align__(16) unsigned char jsm[];
+    C2* Cs = reinterpret_cast<C2*>(jsm);
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) Cs[e] = C[(size_t)(e % n) + (size_t)(e / n) * a.ld];
+    C = Cs;
+    N = n;
+    __syncthreads();
+  }
   const int m = n + (n & 1);
   const int np = m / 2;
 
@@ -106,7 +118,7 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_t(JacobiArgs a, doubl
   double fro = 0.0;
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     const int i = e % n, j = e / n;
-    Q[(size_t)i + (size_t)j * N] = CplxOf<R>::make(i == j ? R(1) : R(0), R(0));
+    Q[(size_t)i + (size_t)j * NQ] = CplxOf<R>::make(i == j ? R(1) : R(0), R(0));
     const C2 v = C[(size_t)i + (size_t)j * N];
     fro += (double)v.x * v.x + (double)v.y * v.y;
   }
@@ -240,15 +252,15 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_t(JacobiArgs a, doubl
         if (q >= n) continue;
         const R c = sc[k];
         const C2 g = ssig[k];
-        const C2 aq = Q[(size_t)i + (size_t)p * N];
-        const C2 bq = Q[(size_t)i + (size_t)q * N];
-        Q[(size_t)i + (size_t)p * N] = sub<C2, R>(scale<C2, R>(aq, c), mulc<C2, R>(bq, g));
-        Q[(size_t)i + (size_t)q * N] = add<C2, R>(mul<C2, R>(aq, g), scale<C2, R>(bq, c));
+        const C2 aq = Q[(size_t)i + (size_t)p * NQ];
+        const C2 bq = Q[(size_t)i + (size_t)q * NQ];
+        Q[(size_t)i + (size_t)p * NQ] = sub<C2, R>(scale<C2, R>(aq, c), mulc<C2, R>(bq, g));
+        Q[(size_t)i + (size_t)q * NQ] = add<C2, R>(mul<C2, R>(aq, g), scale<C2, R>(bq, c));
       }
       __syncthreads();
     }
   }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) a.mu[(size_t)t * N + i] = (double)C[(size_t)i + (size_t)i * N].x;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a.mu[(size_t)t * NQ + i] = (double)C[(size_t)i + (size_t)i * N].x;
   if (threadIdx.x == 0) {
     a.sweeps[t] = sweep;
     if (!converged && a.report_nonconv) a.status[t] |= kStatusNotConverged;
@@ -258,6 +270,18 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_t(JacobiArgs a, doubl
 inline void launch_jacobi_args(const JacobiArgs& a, int T, bool fp32, double tol, int max_sweeps, cudaStream_t s) {
   if (fp32) k_jacobi_t<float><<<T, kJacobiThreads, 0, s>>>(a, tol, max_sweeps);
   else k_jacobi_t<double><<<T, kJacobiThreads, 0, s>>>(a, tol, max_sweeps);
+}
+
+// FP64 Jacobi of matrices of at most n_max rows with C staged in shared
+// memory when it fits (n_max^2 complex doubles beside the static arrays).
+inline void launch_jacobi_small(const JacobiArgs& a, int T, int n_max, double tol, int max_sweeps, cudaStream_t s) {
+  const size_t smem = sizeof(double2) * (size_t)n_max * n_max;
+  if (smem <= 160 * 1024) {
+    cudaFuncSetAttribute(k_jacobi_t<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_jacobi_t<double, true><<<T, kJacobiThreads, smem, s>>>(a, tol, max_sweeps);
+  } else {
+    k_jacobi_t<double><<<T, kJacobiThreads, 0, s>>>(a, tol, max_sweeps);
+  }
 }
 
 }  // namespace bipp
