@@ -13,7 +13,9 @@
 //      QR step while the other warps apply those of the previous step to
 //      their rows of Z (Z starts as I), so that T = Z diag(d) Z^T at
 //      convergence.
-//   3. k_tridiag_back32: Q = H Z, applying H_{n-2} first, one warp per column.
+//   3. k_tridiag_back32_blk: Q = H Z, applying H_{n-2} first, in blocks of
+//      reflectors with each column of Q in a warp's registers (the one-reflector
+//      -at-a-time k_tridiag_back32 serves n_max > 1024).
 // Result: C ~ Q diag(d) Q^H with Q unitary to FP32 rounding; the eigenvalues
 // are left unsorted in mu.
 #pragma once
@@ -490,6 +492,90 @@ __global__ void __launch_bounds__(kTdThreads) k_tridiag_back32(TridiagArgs a, in
   }
 }
 
+// ---- 3'. the same back-transformation, reflectors applied in blocks of RB
+// with each column of Q held in a warp's registers for a whole block (lane l
+// holds rows l, l + 32, ...): per block the reflectors' vectors are staged in
+// shared memory, every column is read and written once, and the dot product
+// of each reflector is a warp reduction. Columns of up to 32 * RPL rows.
+// Grid (column groups, T); dynamic shared memory: ld x (RB + 1) float2.
+template <int RB, int RPL>
+__global__ void __launch_bounds__(kTdThreads) k_tridiag_back32_blk(TridiagArgs a, int cols_per_cta) {
+  using namespace td;
+  const int t = blockIdx.y;
+  if (a.status[t]) return;
+  const int n = a.n[t], N = a.ld, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int c0 = blockIdx.x * cols_per_cta;
+  if (c0 >= n) return;
+  const int c1 = min(n, c0 + cols_per_cta);
+  const float2* A = a.C + (size_t)t * a.stride;
+  float2* Q = a.Q + (size_t)t * a.stride;
+  const float* Z = a.scratch + (size_t)t * a.sstride;
+  const float2* tau = reinterpret_cast<const float2*>(Z + td_off_tau(N));
+  extern __shared__ __align__(16) unsigned char bbsm[];
+  float2* V = reinterpret_cast<float2*>(bbsm);  // [row - (k0 + 1)][j], leading dimension RB + 1
+  __shared__ float2 stau[RB];
+  for (int e0 = tid; e0 < n * (c1 - c0); e0 += kTdThreads) {
+    const int r = e0 % n, c = c0 + e0 / n;
+    Q[(size_t)r + (size_t)c * N] = make_float2(Z[(size_t)r + (size_t)c * N], 0.f);
+  }
+  const int nref = n - 1;  // reflectors 0 .. n-2
+  for (int k0 = ((nref - 1) / RB) * RB; k0 >= 0 && nref > 0; k0 -= RB) {
+    const int nb = min(RB, nref - k0), mb = n - k0 - 1;  // reflectors k0..k0+nb-1 act on rows k0+1..n-1
+    __syncthreads();
+    for (int e0 = tid; e0 < mb * nb; e0 += kTdThreads) {
+      const int r = e0 % mb, j = e0 / mb;  // v_{k0+j}: 1 at local row j, stored below it
+      float2 v = make_float2(0.f, 0.f);
+      if (r == j) v = make_float2(1.f, 0.f);
+      else if (r > j) v = A[(size_t)(k0 + 1 + r) + (size_t)(k0 + j) * N];
+      V[(size_t)r * (RB + 1) + j] = v;
+    }
+    if (tid < nb) stau[tid] = tau[k0 + tid];
+    __syncthreads();
+    for (int c = c0 + wid; c < c1; c += kTdThreads / 32) {
+      float2* Qc = Q + (size_t)(k0 + 1) + (size_t)c * N;
+      float2 q[RPL];
+#pragma unroll
+      for (int i = 0; i < RPL; ++i) {
+        const int r = lane + 32 * i;
+        q[i] = (r < mb) ? Qc[r] : make_float2(0.f, 0.f);
+      }
+      for (int j = nb - 1; j >= 0; --j) {
+        const float2 tj = stau[j];
+        float2 u = make_float2(0.f, 0.f);  // v^H q
+#pragma unroll
+        for (int i = 0; i < RPL; ++i) {
+          const int r = lane + 32 * i;
+          if (r < mb) {
+            const float2 vr = V[(size_t)r * (RB + 1) + j];
+            u.x += vr.x * q[i].x + vr.y * q[i].y;
+            u.y += vr.x * q[i].y - vr.y * q[i].x;
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          u.x += __shfl_xor_sync(0xffffffffu, u.x, o);
+          u.y += __shfl_xor_sync(0xffffffffu, u.y, o);
+        }
+        const float2 tu = cmul(tj, u);
+#pragma unroll
+        for (int i = 0; i < RPL; ++i) {
+          const int r = lane + 32 * i;
+          if (r < mb) {
+            const float2 y = cmul(V[(size_t)r * (RB + 1) + j], tu);
+            q[i].x -= y.x;
+            q[i].y -= y.y;
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < RPL; ++i) {
+        const int r = lane + 32 * i;
+        if (r < mb) Qc[r] = q[i];
+      }
+    }
+  }
+}
+
 // Launches the three stages on stream s; 3 kernel launches.
 inline void launch_tridiag32(const TridiagArgs& a, int T, cudaStream_t s) {
   const int N = a.ld;
@@ -500,7 +586,17 @@ inline void launch_tridiag32(const TridiagArgs& a, int T, cudaStream_t s) {
   k_tridiag32<<<T, kTdThreads, smem1, s>>>(a);
   k_tridiag_qr32<<<T, kQrThreads, smem2, s>>>(a, 30 * N + 30);
   constexpr int kCols = 64;
-  k_tridiag_back32<<<dim3((N + kCols - 1) / kCols, T), kTdThreads, smem3, s>>>(a, kCols);
+  if (N <= 512) {
+    const int smb = N * (32 + 1) * (int)sizeof(float2);
+    cudaFuncSetAttribute(k_tridiag_back32_blk<32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
+    k_tridiag_back32_blk<32, 16><<<dim3((N + kCols - 1) / kCols, T), kTdThreads, smb, s>>>(a, kCols);
+  } else if (N <= 1024) {
+    const int smb = N * (16 + 1) * (int)sizeof(float2);
+    cudaFuncSetAttribute(k_tridiag_back32_blk<16, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
+    k_tridiag_back32_blk<16, 32><<<dim3((N + kCols - 1) / kCols, T), kTdThreads, smb, s>>>(a, kCols);
+  } else {
+    k_tridiag_back32<<<dim3((N + kCols - 1) / kCols, T), kTdThreads, smem3, s>>>(a, kCols);
+  }
 }
 
 }  // namespace bipp
