@@ -45,7 +45,6 @@
 #include <mutex>
 #include <type_traits>
 
-#include "phase.cuh"
 #include "synth_tc.cuh"
 
 namespace bipp {
@@ -74,12 +73,15 @@ __device__ __forceinline__ void mbar_arrive(uint32_t a) {
 __device__ __forceinline__ void mbar_arrive_tx(uint32_t a, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
 }
+// try_wait with a suspend-time hint (ns): a waiting warp sleeps in hardware
+// until the phase completes or the hint expires instead of spinning on issue
+// slots that the other producer warps need.
 __device__ __forceinline__ bool mbar_test(uint32_t a, uint32_t parity) {
   uint32_t done;
   asm volatile(
-      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(done)
-      : "r"(a), "r"(parity)
+      : "r"(a), "r"(parity), "r"(1000000u)
       : "memory");
   return done != 0;
 }
@@ -156,14 +158,14 @@ __device__ __forceinline__ void split2(float x0, float x1, uint32_t* hi, uint32_
   }
 }
 
-// frac(<r, q>) in cycles, in [-1/2, 1/2), from the 32-bit words of the
+// 2 pi frac(<r, q>) in radians, in [-pi, pi), from the 32-bit words of the
 // fixed-point R (per pixel) and Q (per station); see the header comment.
-__device__ __forceinline__ float phase_frac_fixed(const uint32_t (&rl)[3], const uint32_t (&rh)[3], uint4 qa,
-                                                  uint2 qb) {
+__device__ __forceinline__ float phase_rad_fixed(const uint32_t (&rl)[3], const uint32_t (&rh)[3], uint4 qa,
+                                                 uint2 qb) {
   uint32_t acc = __umulhi(rl[0], qa.x) + rh[0] * qa.x + rl[0] * qa.y;
   acc += __umulhi(rl[1], qa.z) + rh[1] * qa.z + rl[1] * qa.w;
   acc += __umulhi(rl[2], qb.x) + rh[2] * qb.x + rl[2] * qb.y;
-  return (float)(int32_t)acc * 2.3283064365386963e-10f;  // 2^-32
+  return (float)(int32_t)acc * 1.4629180792671596e-09f;  // 2 pi 2^-32
 }
 
 __device__ __forceinline__ void st_shared_v4(uint32_t a, const uint32_t (&w)[4]) {
@@ -183,8 +185,8 @@ template <int MAXL, bool FP16>
 __global__ void __launch_bounds__(kThreads, 1)
     k_synth_tc(Batch b, Pixels px, int n_level, double* img, const TcStep* __restrict__ steps,
                const unsigned char* __restrict__ Bpack, const float* __restrict__ scales,
-               const uint32_t* __restrict__ qfix, int qfix_stride, int n_stages, int stage_bytes, int ncols_buf,
-               int* status) {
+               const uint32_t* __restrict__ qfix, int qfix_stride, const int2* __restrict__ lwt, int n_stages,
+               int stage_bytes, int ncols_buf, int* status) {
   if (*b.flag) return;  // a step of the batch failed: commit nothing
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -220,7 +222,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t taddr = s_taddr;
   const uint32_t smem0 = smem_u32(smem);
   const int n_tiles = (int)((px.n + kRows - 1) / kRows);
-  const int T = b.T, KM = b.k_max, N = b.n_max;
+  const int T = b.T;
 
   if (warp < kProdWarps) {
     // ------------------------------------------------ A producer + epilogue
@@ -240,7 +242,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_after();
       const TcStep st = steps[t];
       const int K = b.nkept[t];
-      const float inv2 = FP16 ? 1.0f / (scales[t] * scales[t]) : 1.0f;
+      const int2* lw = lwt + (size_t)t * kTcMaxEig;
       const uint32_t tbase = taddr + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(bb * ncols_buf);
       for (int cb = wg; cb < st.ncols / 16; cb += 4) {
         float v[16];
@@ -249,11 +251,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int p = 0; p < 8; ++p) {
           const int e = cb * 8 + p;
           if (e < K) {
-            const int lev = b.level[(size_t)t * KM + e];
-            if (lev >= 0) {
-              const float w = (float)b.wt[(size_t)t * KM + e] * inv2;
-              level_add<MAXL>(lacc, lev, w * fmaf(v[2 * p], v[2 * p], v[2 * p + 1] * v[2 * p + 1]));
-            }
+            const int2 lv = lw[e];
+            if (lv.x >= 0)
+              level_add<MAXL>(lacc, lv.x, __int_as_float(lv.y) * fmaf(v[2 * p], v[2 * p], v[2 * p + 1] * v[2 * p + 1]));
           }
         }
       }
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               const uint4 qa = __ldg(qv + 2 * (size_t)i);
               const uint2 qb = __ldg(reinterpret_cast<const uint2*>(qv + 2 * (size_t)i + 1));
               float cs, sn;
-              sincos_cycles(phase_frac_fixed(rl, rh, qa, qb), &sn, &cs);
+              __sincosf(phase_rad_fixed(rl, rh, qa, qb), &sn, &cs);
               split2<FP16>(cs, sn, &hw[j], &lw[j]);
             }
             const uint32_t phys = (uint32_t)((qp ^ (row & 7)) << 4);
@@ -458,11 +458,20 @@ __global__ void k_tc_scale(Batch b, float* scales) {
 // padded stations i >= n.
 template <bool FP16>
 __global__ void k_tc_pack(Batch b, const TcStep* steps, unsigned char* Bpack, const float* scales, uint32_t* qfix,
-                          int qfix_stride) {
+                          int qfix_stride, int2* lwt) {
   const int t = blockIdx.y, c = blockIdx.x;
   const TcStep st = steps[t];
   if (c >= st.n_chunks) return;
   const int n = b.nst[t], K = b.nkept[t], KM = b.k_max, N = b.n_max;
+  if (c == 0) {  // (level, FP32 weight / scale^2) of each accumulator column pair; level -1 = not imaged
+    const double inv2 = FP16 ? 1.0 / ((double)scales[t] * (double)scales[t]) : 1.0;
+    for (int e = threadIdx.x; e < kTcMaxEig; e += blockDim.x) {
+      int2 v = make_int2(-1, 0);
+      if (e < K && b.level[(size_t)t * KM + e] >= 0)
+        v = make_int2(b.level[(size_t)t * KM + e], __float_as_int((float)(b.wt[(size_t)t * KM + e] * inv2)));
+      lwt[(size_t)t * kTcMaxEig + e] = v;
+    }
+  }
   if (threadIdx.x < kStations) {
     const int i = c * kStations + threadIdx.x;
     uint32_t wv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -546,6 +555,7 @@ int tc_alloc(TcWorkspace* w, int T, int N, int K) {
   if (cudaMalloc(&w->scale, sizeof(float) * T) != cudaSuccess) return -1;
   w->qfix_stride = n_chunks_for(N) * kStations;
   if (cudaMalloc(&w->qfix, sizeof(uint32_t) * 8 * (size_t)T * w->qfix_stride) != cudaSuccess) return -1;
+  if (cudaMalloc(&w->lwt, sizeof(int2) * (size_t)T * kTcMaxEig) != cudaSuccess) return -1;
   if (cudaMalloc(&w->status, sizeof(int)) != cudaSuccess) return -1;
   w->cap_T = T;
   return 0;
@@ -557,6 +567,7 @@ void tc_free(TcWorkspace* w) {
   if (w->h_steps) cudaFreeHost(w->h_steps);
   if (w->scale) cudaFree(w->scale);
   if (w->qfix) cudaFree(w->qfix);
+  if (w->lwt) cudaFree(w->lwt);
   if (w->status) cudaFree(w->status);
   *w = TcWorkspace{};
 }
@@ -596,7 +607,7 @@ int launch_kernel(const Batch& b, const Pixels& px, int n_level, double* img, co
       return;
     }
     k_synth_tc<ML, F16><<<grid, kThreads, smem, s>>>(b, px, n_level, img, w->steps, w->B, w->scale, w->qfix,
-                                                      w->qfix_stride, n_stages,
+                                                      w->qfix_stride, w->lwt, n_stages,
                                                      stage_bytes, p.ncols_buf, w->status);
   });
   return rc;
@@ -642,9 +653,11 @@ int tc_enqueue_pack(const Batch& b, const TcPlan& p, TcWorkspace* w, cudaStream_
   if (cudaMemsetAsync(w->status, 0, sizeof(int), s) != cudaSuccess) return -5;
   if (p.fp16) k_tc_scale<<<T, 256, 0, s>>>(b, w->scale);
   if (p.fp16)
-    k_tc_pack<true><<<dim3(p.max_chunks, T), 256, 0, s>>>(b, w->steps, w->B, w->scale, w->qfix, w->qfix_stride);
+    k_tc_pack<true><<<dim3(p.max_chunks, T), 256, 0, s>>>(b, w->steps, w->B, w->scale, w->qfix, w->qfix_stride,
+                                                          w->lwt);
   else
-    k_tc_pack<false><<<dim3(p.max_chunks, T), 256, 0, s>>>(b, w->steps, w->B, w->scale, w->qfix, w->qfix_stride);
+    k_tc_pack<false><<<dim3(p.max_chunks, T), 256, 0, s>>>(b, w->steps, w->B, w->scale, w->qfix, w->qfix_stride,
+                                                           w->lwt);
   return cudaGetLastError() == cudaSuccess ? 0 : -5;
 }
 

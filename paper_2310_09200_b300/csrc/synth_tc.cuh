@@ -32,6 +32,7 @@ struct TcWorkspace {
   float* scale = nullptr;      // [cap_T] operand scale of the FP16 variant (W * scale)
   uint32_t* qfix = nullptr;    // [cap_T][chunks * 32][8] station p/wl in 40.24 fixed point (see k_tc_pack)
   int qfix_stride = 0;         // stations per step in qfix (32 * chunks of n_max)
+  int2* lwt = nullptr;         // [cap_T][kTcMaxEig] (level, FP32 weight / scale^2) per accumulator column pair
   int* status = nullptr;       // [1] device error word (0 = ok)
   int cap_T = 0;
 };

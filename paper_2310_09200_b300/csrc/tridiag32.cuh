@@ -235,6 +235,185 @@ __global__ void __launch_bounds__(kTdThreads, 1) k_tridiag32(TridiagArgs a) {
   }
 }
 
+// ---- 1'. the same reduction on the lower triangle only (ld <= 512): the
+// fused pass runs over 32 x 32 tiles of the trailing lower triangle, one warp
+// per tile with lane = row and 16 of the tile's columns at a time in registers
+// (16 loads in flight per lane); an element a_ij (i >= j) contributes a_ij v_j to p_i and,
+// off the diagonal, conj(a_ij) v_i to p_j. Each tile writes its row sums and
+// its column sums into fixed slots (rowp[tile column][i], colp[tile row][j]),
+// summed in a fixed order afterwards, so the result is deterministic.
+// Dynamic shared memory: 5 * ld + 2 * 16 * ld float2.
+constexpr int kTdLoMax = 512;
+
+__global__ void __launch_bounds__(kTdThreads, 1) k_tridiag32_lo(TridiagArgs a) {
+  using namespace td;
+  const int t = blockIdx.x;
+  if (a.status[t]) return;
+  const int n = a.n[t], N = a.ld, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  float2* A = a.C + (size_t)t * a.stride;
+  float* S = a.scratch + (size_t)t * a.sstride;
+  float* d = S + td_off_d(N);
+  float* e = S + td_off_e(N);
+  float2* tau = reinterpret_cast<float2*>(S + td_off_tau(N));
+  extern __shared__ __align__(16) unsigned char tdlsm[];
+  float2* vp = reinterpret_cast<float2*>(tdlsm);
+  float2* wp = vp + N;
+  float2* v = wp + N;
+  float2* w = v + N;
+  float2* p = w + N;
+  float2* rowp = p + N;                       // [16][N]
+  float2* colp = rowp + (size_t)(kTdLoMax / 32) * N;  // [16][N]
+  __shared__ float2 red[kTdThreads / 32];
+  __shared__ float2 s_tau, s_scale;
+  __shared__ float s_beta;
+  __shared__ int s_trivial;
+  for (int i = tid; i < N; i += kTdThreads) {
+    vp[i] = make_float2(0.f, 0.f);
+    wp[i] = make_float2(0.f, 0.f);
+  }
+  if (n == 1 && tid == 0) d[0] = A[0].x;
+  __syncthreads();
+  for (int k = 0; k + 1 < n; ++k) {
+    const int m = n - k - 1;
+    // (a) reflector from column k
+    float2 sg = make_float2(0.f, 0.f);
+    for (int r = tid; r < m; r += kTdThreads) {
+      const float2 x = A[(size_t)(k + 1 + r) + (size_t)k * N];
+      if (r > 0) sg.x += x.x * x.x + x.y * x.y;
+    }
+    const float sigma = block_sum2(sg, red).x;
+    if (tid == 0) {
+      const float2 al = A[(size_t)(k + 1) + (size_t)k * N];
+      d[k] = A[(size_t)k + (size_t)k * N].x;
+      if (sigma == 0.f && al.y == 0.f) {
+        s_trivial = 1;
+        s_tau = make_float2(0.f, 0.f);
+        s_beta = al.x;
+        s_scale = make_float2(0.f, 0.f);
+      } else {
+        const float beta = -copysignf(sqrtf(al.x * al.x + al.y * al.y + sigma), al.x);
+        s_trivial = 0;
+        s_tau = make_float2((beta - al.x) / beta, -al.y / beta);
+        s_beta = beta;
+        const float2 dn = make_float2(al.x - beta, al.y);
+        const float inv = 1.f / (dn.x * dn.x + dn.y * dn.y);
+        s_scale = make_float2(dn.x * inv, -dn.y * inv);
+      }
+      e[k] = s_beta;
+      tau[k] = s_tau;
+    }
+    __syncthreads();
+    const float2 tk = s_tau, sc = s_scale;
+    const bool triv = s_trivial != 0;
+    const int nt = (m + 31) / 32;  // tile rows = tile columns of the trailing block
+    for (int r = tid; r < m; r += kTdThreads) {
+      float2 vv;
+      if (r == 0) {
+        vv = make_float2(1.f, 0.f);
+      } else if (triv) {
+        vv = make_float2(0.f, 0.f);
+      } else {
+        vv = cmul(A[(size_t)(k + 1 + r) + (size_t)k * N], sc);
+        A[(size_t)(k + 1 + r) + (size_t)k * N] = vv;
+      }
+      v[k + 1 + r] = vv;
+    }
+    for (int e0 = tid; e0 < nt * N; e0 += kTdThreads) {
+      rowp[e0] = make_float2(0.f, 0.f);
+      colp[e0] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    // (b) tiles (ti >= tj) of the lower triangle of A[k+1:, k+1:]
+    {
+      int tile = 0;
+      for (int ti = 0; ti < nt; ++ti) {
+        for (int tj = 0; tj <= ti; ++tj, ++tile) {
+          if (tile % (kTdThreads / 32) != wid) continue;
+          const int i = k + 1 + ti * 32 + lane, j0 = k + 1 + tj * 32;
+          const bool rv = i < n;
+          const float2 zero = make_float2(0.f, 0.f);
+          const float2 vpi = rv ? vp[i] : zero, wpi = rv ? wp[i] : zero, vi = rv ? v[i] : zero;
+          float2* Ai = A + (rv ? i : k + 1);
+          float2 acc = zero;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {  // two halves of 16 columns
+            float2 x[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+              const int j = j0 + 16 * h + u;
+              x[u] = (rv && j <= i) ? Ai[(size_t)j * N] : zero;
+            }
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+              const int j = j0 + 16 * h + u;
+              const bool ok = rv && j <= i;
+              float2 col = zero;
+              if (ok) {
+                const float2 t1 = cmulc(wpi, vp[j]), t2 = cmulc(vpi, wp[j]);
+                x[u].x -= t1.x + t2.x;
+                x[u].y -= t1.y + t2.y;
+                Ai[(size_t)j * N] = x[u];
+                const float2 pv = cmul(x[u], v[j]);
+                acc.x += pv.x;
+                acc.y += pv.y;
+                if (j < i) col = cmulc(vi, x[u]);  // conj(a_ij) v_i
+              }
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) {
+                col.x += __shfl_xor_sync(0xffffffffu, col.x, o);
+                col.y += __shfl_xor_sync(0xffffffffu, col.y, o);
+              }
+              if (lane == 16 * h + u && j < n) colp[(size_t)ti * N + j] = col;
+            }
+          }
+          if (rv) rowp[(size_t)tj * N + i] = acc;
+        }
+      }
+    }
+    __syncthreads();
+    for (int r = tid; r < m; r += kTdThreads) {
+      const int i = k + 1 + r;
+      float2 sum = make_float2(0.f, 0.f);
+      for (int q = 0; q < nt; ++q) {
+        sum.x += rowp[(size_t)q * N + i].x + colp[(size_t)q * N + i].x;
+        sum.y += rowp[(size_t)q * N + i].y + colp[(size_t)q * N + i].y;
+      }
+      p[i] = sum;
+    }
+    __syncthreads();
+    // (c) gamma = v^H p, w = tau p - |tau|^2 gamma / 2 v
+    float2 gp = make_float2(0.f, 0.f);
+    for (int r = tid; r < m; r += kTdThreads) {
+      const int i = k + 1 + r;
+      const float2 vi = v[i], pi = p[i];
+      gp.x += vi.x * pi.x + vi.y * pi.y;
+    }
+    const float gamma = block_sum2(gp, red).x;
+    const float hg = 0.5f * (tk.x * tk.x + tk.y * tk.y) * gamma;
+    for (int r = tid; r < m; r += kTdThreads) {
+      const int i = k + 1 + r;
+      const float2 tp = cmul(tk, p[i]), vi = v[i];
+      w[i] = make_float2(tp.x - hg * vi.x, tp.y - hg * vi.y);
+    }
+    __syncthreads();
+    // (d) column k+1 (rows k+1..n-1) gets the update of step k now
+    const float2 wk1 = w[k + 1];
+    for (int r = tid; r < m; r += kTdThreads) {
+      const int i = k + 1 + r;
+      float2 x = A[(size_t)i + (size_t)(k + 1) * N];
+      const float2 t2 = cmulc(v[i], wk1);
+      x.x -= w[i].x + t2.x;
+      x.y -= w[i].y + t2.y;
+      A[(size_t)i + (size_t)(k + 1) * N] = x;
+      vp[i] = v[i];
+      wp[i] = w[i];
+    }
+    if (tid == 0) vp[k] = wp[k] = make_float2(0.f, 0.f);
+    __syncthreads();
+    if (k + 2 == n && tid == 0) d[n - 1] = A[(size_t)(n - 1) + (size_t)(n - 1) * N].x;
+  }
+}
+
 // ---- 2. implicit symmetric QR on (d, e) with the Wilkinson shift, rotations applied to Z
 // One driver thread (lane 0 of warp 0) runs the QR iteration on the
 // tridiagonal (scaled to unit Frobenius norm) and records the Givens rotations
@@ -581,9 +760,15 @@ inline void launch_tridiag32(const TridiagArgs& a, int T, cudaStream_t s) {
   const int N = a.ld;
   const int smem1 = 5 * N * (int)sizeof(float2), smem2 = 6 * N * (int)sizeof(float), smem3 = N * (int)sizeof(float2);
   cudaFuncSetAttribute(k_tridiag32, cudaFuncAttributeMaxDynamicSharedMemorySize, smem1);
+  const int smem1l = (5 + 2 * (kTdLoMax / 32)) * N * (int)sizeof(float2);
   cudaFuncSetAttribute(k_tridiag_qr32, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2);
   cudaFuncSetAttribute(k_tridiag_back32, cudaFuncAttributeMaxDynamicSharedMemorySize, smem3);
-  k_tridiag32<<<T, kTdThreads, smem1, s>>>(a);
+  if (N <= kTdLoMax) {
+    cudaFuncSetAttribute(k_tridiag32_lo, cudaFuncAttributeMaxDynamicSharedMemorySize, smem1l);
+    k_tridiag32_lo<<<T, kTdThreads, smem1l, s>>>(a);
+  } else {
+    k_tridiag32<<<T, kTdThreads, smem1, s>>>(a);
+  }
   k_tridiag_qr32<<<T, kQrThreads, smem2, s>>>(a, 30 * N + 30);
   constexpr int kCols = 64;
   if (N <= 512) {
