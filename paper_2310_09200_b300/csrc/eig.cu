@@ -10,6 +10,8 @@
 // whole GPU. Matrices live in global memory (L2-resident at N <= 1024).
 #include <math.h>
 
+#include <algorithm>
+
 #include "bipp_internal.cuh"
 #include "dfloat.cuh"
 #include "jacobi.cuh"
@@ -360,8 +362,13 @@ __global__ void k_hermitize(Batch b, int from_vis) {
 // Keep the n_eig algebraically largest eigenvalues (descending, ties by lower
 // Jacobi index), assign filter weights and levels, back-transform the kept
 // eigenvectors a = L^{-T} q, and pack them for the synthesis kernels.
+// Grid (T, eigenvector groups of kSelE): every CTA ranks the step's
+// eigenvalues; group 0 also writes levels, weights and station coordinates;
+// each group back-transforms its kSelE kept eigenvectors (double-float).
+constexpr int kSelE = 8;
+
 __global__ void k_select(Batch b, int n_level, const double* all_bounds, int filter) {
-  const int t = blockIdx.x;
+  const int t = blockIdx.x, eg = blockIdx.y;
   const int n = b.nst[t];
   const int N = b.n_max;
   const int K = b.neig[t];
@@ -371,6 +378,7 @@ __global__ void k_select(Batch b, int n_level, const double* all_bounds, int fil
   __shared__ int idx[kMaxEig];
   const int st = b.status[t];
   if (st) {
+    if (eg != 0) return;
     for (int e = threadIdx.x; e < KM; e += blockDim.x) b.level[(size_t)t * KM + e] = -1;
     if (threadIdx.x == 0) {
       b.nkept[t] = 0;
@@ -389,7 +397,7 @@ __global__ void k_select(Batch b, int n_level, const double* all_bounds, int fil
     if (rank < K) idx[rank] = i;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < KM; e += blockDim.x) {
+  for (int e = threadIdx.x; eg == 0 && e < KM; e += blockDim.x) {
     int lev = -1;
     double m = 0.0, w = 0.0;
     if (e < K) {
@@ -406,22 +414,57 @@ __global__ void k_select(Batch b, int n_level, const double* all_bounds, int fil
     b.wt[(size_t)t * KM + e] = w;
     b.level[(size_t)t * KM + e] = lev;
   }
-  // a_e[i] = sum_{k >= i} Linv(k, i) q_{idx[e]}[k]
-  const double* Linv = b.Linv + mat_off(t, N);
-  const double2* Qm = b.Q + mat_off(t, N);
-  for (int w = threadIdx.x; w < K * n; w += blockDim.x) {
-    const int i = w % n, e = w / n;
-    const double2* qc = Qm + (size_t)idx[e] * N;
-    double2 a = make_double2(0.0, 0.0);
-    for (int k = i; k < n; ++k) {
-      const double r = Linv[(size_t)k * N + i];
-      const double2 qk = qc[k];
-      a.x = fma(r, qk.x, a.x);
-      a.y = fma(r, qk.y, a.y);
+  // a_e[i] = sum_{k >= i} Linv(k, i) q_{idx[e]}[k] for this group's eigenvectors, in double-float:
+  // the group's columns of Q staged in shared memory as hi/lo pairs, one row i per thread
+  const int e0 = eg * kSelE, ne = min(kSelE, K - e0);
+  if (ne > 0) {
+    extern __shared__ __align__(16) unsigned char selsm[];
+    float4* sq = reinterpret_cast<float4*>(selsm);  // [kSelE][N]
+    const double* Linv = b.Linv + mat_off(t, N);
+    const double2* Qm = b.Q + mat_off(t, N);
+    for (int w = threadIdx.x; w < ne * n; w += blockDim.x) {
+      const int k = w % n, e = w / n;
+      const double2 qk = Qm[(size_t)idx[e0 + e] * N + k];
+      float4 f;
+      df::split(qk.x, f.x, f.y);
+      df::split(qk.y, f.z, f.w);
+      sq[(size_t)e * N + k] = f;
     }
-    b.W64[((size_t)t * KM + e) * N + i] = a;
-    b.W32[((size_t)t * N + i) * KM + e] = make_float2((float)a.x, (float)a.y);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      float acc[kSelE][4];
+#pragma unroll
+      for (int e = 0; e < kSelE; ++e) acc[e][0] = acc[e][1] = acc[e][2] = acc[e][3] = 0.f;
+      for (int k = i; k < n; ++k) {
+        float rh, rl;
+        df::split(Linv[(size_t)k * N + i], rh, rl);
+#pragma unroll
+        for (int e = 0; e < kSelE; ++e) {
+          if (e < ne) {
+            const float4 q = sq[(size_t)e * N + k];
+            df::mac(acc[e][0], acc[e][1], rh, rl, q.x, q.y);
+            df::mac(acc[e][2], acc[e][3], rh, rl, q.z, q.w);
+          }
+        }
+        if (((k - i) & 15) == 15) {
+#pragma unroll
+          for (int e = 0; e < kSelE; ++e) {
+            df::renorm(acc[e][0], acc[e][1]);
+            df::renorm(acc[e][2], acc[e][3]);
+          }
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < kSelE; ++e) {
+        if (e < ne) {
+          const double2 a = make_double2(df::to_double(acc[e][0], acc[e][1]), df::to_double(acc[e][2], acc[e][3]));
+          b.W64[((size_t)t * KM + e0 + e) * N + i] = a;
+          b.W32[((size_t)t * N + i) * KM + e0 + e] = make_float2((float)a.x, (float)a.y);
+        }
+      }
+    }
   }
+  if (eg != 0) return;
   // station coordinates in cycles per unit direction cosine, float hi/lo
   const double* p = b.st + (size_t)t * 3 * N;
   float* q = b.q + (size_t)t * 6 * N;
@@ -494,7 +537,9 @@ void launch_jacobi(const Batch& b, double tol, int max_sweeps, cudaStream_t s) {
 }
 
 void launch_select(const Batch& b, int n_level, const double* d_bounds, int filter, cudaStream_t s) {
-  k_select<<<b.T, 256, 0, s>>>(b, n_level, d_bounds, filter);
+  const int smem = (int)(sizeof(float4) * kSelE * (size_t)b.n_max);
+  cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  k_select<<<dim3(b.T, std::max(1, (b.k_max + kSelE - 1) / kSelE)), 256, smem, s>>>(b, n_level, d_bounds, filter);
 }
 
 void launch_pixel_split(const double* d_xyz, float* d_hl, int64_t n, cudaStream_t s) {
