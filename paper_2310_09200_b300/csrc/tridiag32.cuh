@@ -449,15 +449,13 @@ __global__ void __launch_bounds__(kQrThreads, 1) k_tridiag_qr32(TridiagArgs a, i
     Z[(size_t)r + (size_t)c * N] = (r == c) ? 1.f : 0.f;
   }
   __syncthreads();
-  const int wid = tid >> 5;
+  const int wid = tid >> 5, lane = tid & 31;
   const bool driver = tid == 0;
   const int ai = (wid & 3) ? (wid - 1 - (wid >> 2)) * 32 + (tid & 31) : -1;  // applier index
   const float eps = 5.96e-8f, tiny = 1e-8f;  // deflation: relative to the neighbours, or to ||T||_F = 1
   int q = n - 1, plo = n, steps = 0, fin = 0;  // driver state (plo >= q: find the block start again)
   auto small = [&](float ev, float d0, float d1) { return ev <= eps * (fabsf(d0) + fabsf(d1)) || ev <= tiny; };
   auto drive = [&](int slot) {
-    float* rc = rc0 + slot * N;
-    float* rs = rs0 + slot * N;
     int state = 1;
     while (q > 0) {
       if (small(fabsf(e[q - 1]), d[q - 1], d[q])) {
@@ -479,59 +477,65 @@ __global__ void __launch_bounds__(kQrThreads, 1) k_tridiag_qr32(TridiagArgs a, i
       const float dl = 0.5f * (d[q - 1] - d[q]), ee = e[q - 1];
       const float den = dl + copysignf(sqrtf(dl * dl + ee * ee), dl);
       const float mu = d[q] - ((den != 0.f) ? ee * ee / den : 0.f);
+      // Givens rotation zeroing z against x (scaled T: |x|, |z| <= ~1); rsqrtf's error is
+      // biased, and a bias in c^2 + s^2 would build up linearly over the ~n^2 rotations
+      // applied to Z, so one Newton-Raphson step on c^2 + s^2 = 1 with the residual
+      // formed by FMAs (exact far below an ulp) leaves only unbiased rounding.
+      auto givens = [](float x, float z, float& c, float& s, float& r) {
+        const float r2 = fmaf(x, x, z * z);
+        const float ri = rsqrtf(r2);
+        c = x * ri;
+        s = z * ri;
+        const float hh = 0.5f * fmaf(-c, c, fmaf(-s, s, 1.f));
+        c = fmaf(hh, c, c);
+        s = fmaf(hh, s, s);
+        const bool deg = !(r2 > 0.f);  // x = z = 0: identity (replaces the NaNs of 0 * inf)
+        c = deg ? 1.f : c;
+        s = deg ? 0.f : s;
+        r = fmaf(x, c, z * s);
+      };
+      float* rc = rc0 + slot * N;
+      float* rs = rs0 + slot * N;
+      // e[q] = 0 at the bottom of an unreduced block, so the bulge leaves it without a test
       float ak = d[p], bk = e[p];
       float x = ak - mu, z = bk;
-      float dn = d[p + 1], en = (p + 1 < q) ? e[p + 1] : 0.f;
-      float dprev = 0.f;
-      int split = p;
-      for (int k = p; k < q; ++k) {
-        const float dk1 = dn, ek1 = en;
-        if (k + 2 <= q) {
-          dn = d[k + 2];
-          en = (k + 2 < q) ? e[k + 2] : 0.f;
-        }
-        const float r2 = x * x + z * z;
-        float c = 1.f, s = 0.f, r = 0.f;
-        if (r2 > 0.f) {
-          // rsqrtf's error is biased, and a bias in c^2 + s^2 would build up
-          // linearly over the ~n^2 rotations applied to Z. One Newton-Raphson
-          // step on c^2 + s^2 = 1 with the residual h = 1 - c^2 - s^2 formed
-          // by FMAs (exact to far below an ulp) leaves only the unbiased
-          // round-to-nearest of the final FMA.
-          const float ri = rsqrtf(r2);
-          c = x * ri;
-          s = z * ri;
-          const float hh = 0.5f * fmaf(-c, c, fmaf(-s, s, 1.f));
-          c = fmaf(hh, c, c);
-          s = fmaf(hh, s, s);
-          r = fmaf(x, c, z * s);
-        }
+      float dk1 = d[p + 1], ek1 = e[p + 1];
+      int k = p;
+      {  // first rotation: creates the bulge, no off-diagonal to its left
+        float c, s, r;
+        givens(x, z, c, s, r);
         const float cc = c * c, ss = s * s, cs = c * s;
-        const float ndk = cc * ak + 2.f * cs * bk + ss * dk1;
+        d[p] = cc * ak + 2.f * cs * bk + ss * dk1;
         const float ndk1 = ss * ak - 2.f * cs * bk + cc * dk1;
-        const float nek = cs * (dk1 - ak) + (cc - ss) * bk;
-        d[k] = ndk;
-        if (k > p) {
-          if (small(fabsf(r), dprev, ndk)) {
-            r = 0.f;
-            split = k;
-          }
-          e[k - 1] = r;
-        }
-        dprev = ndk;
-        if (k + 1 < q) {
-          x = nek;
-          z = s * ek1;
-          bk = c * ek1;
-        } else {
-          e[k] = nek;
-        }
+        x = cs * (dk1 - ak) + (cc - ss) * bk;
+        z = s * ek1;
+        bk = c * ek1;
+        ak = ndk1;
+        rc[0] = c;
+        rs[0] = s;
+        ++k;
+      }
+      float dn = d[k + 1], en = e[k + 1];
+      for (; k < q; ++k) {  // chase: rotation k removes the bulge at (k + 1, k - 1)
+        dk1 = dn;
+        ek1 = en;
+        dn = d[k + 2];  // one ahead; past the block the values are read but unused
+        en = e[k + 2];
+        float c, s, r;
+        givens(x, z, c, s, r);
+        const float cc = c * c, ss = s * s, cs = c * s;
+        d[k] = cc * ak + 2.f * cs * bk + ss * dk1;
+        const float ndk1 = ss * ak - 2.f * cs * bk + cc * dk1;
+        e[k - 1] = r;
+        x = cs * (dk1 - ak) + (cc - ss) * bk;
+        z = s * ek1;
+        bk = c * ek1;
         ak = ndk1;
         rc[k - p] = c;
         rs[k - p] = s;
       }
+      e[q - 1] = x;
       d[q] = ak;
-      plo = split;
       ++steps;
       s_p[slot] = p;
       s_q[slot] = q;
@@ -540,6 +544,23 @@ __global__ void __launch_bounds__(kQrThreads, 1) k_tridiag_qr32(TridiagArgs a, i
     }
     s_state[slot] = state;
     fin = state;
+  };
+  // After a QR step the driver warp scans the block's off-diagonals for new
+  // negligible ones (a split: the next steps start below the last one).
+  auto scan_splits = [&](int slot) {
+    __syncwarp();
+    if (s_state[slot] != 0) return;
+    const int p = s_p[slot], qq = s_q[slot];
+    int best = -1;
+    for (int k = p + 1 + lane; k < qq; k += 32) {
+      if (small(fabsf(e[k - 1]), d[k - 1], d[k])) {
+        e[k - 1] = 0.f;
+        best = k;
+      }
+    }
+    best = __reduce_max_sync(0xffffffffu, best);
+    if (driver && best > plo) plo = best;
+    __syncwarp();
   };
   if (driver) {
     float tn2 = 0.f;
@@ -552,12 +573,14 @@ __global__ void __launch_bounds__(kQrThreads, 1) k_tridiag_qr32(TridiagArgs a, i
     s_norm = tn > 0.f ? tn : 1.f;
     drive(0);
   }
+  if (wid == 0) scan_splits(0);
   __syncthreads();
   for (int it = 0;; ++it) {
     const int cur = it & 1;
     if (s_state[cur] != 0) break;
-    if (driver) {
-      drive(cur ^ 1);
+    if (wid == 0) {
+      if (driver) drive(cur ^ 1);
+      scan_splits(cur ^ 1);
     } else if (ai >= 0) {
       const int p = s_p[cur], qq = s_q[cur];
       const float* rc = rc0 + cur * N;
