@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ------------------------------------------------ A producer + epilogue
     const int row = threadIdx.x & (kRows - 1);
     const int wg = threadIdx.x >> 7;  // warpgroup: stations 8wg..8wg+7 of a stage, column blocks wg + 4j
-    uint32_t ctr = 0;
+    uint32_t rs_s = 0, rs_rnd = 0;  // ring slot and round, advanced per chunk
     int unit = 0;
     int pend_tile = -1, pend_t = -1;
     float lacc[MAXL];
@@ -284,8 +284,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int t = 0; t < T && ok; ++t) {
         const int nch = steps[t].n_chunks;
         const uint4* qv = reinterpret_cast<const uint4*>(qfix + (size_t)t * qfix_stride * 8);
-        for (int c = 0; c < nch; ++c, ++ctr) {
-          const uint32_t s = ctr % (uint32_t)n_stages, rnd = ctr / (uint32_t)n_stages;
+        for (int c = 0; c < nch; ++c) {
+          const uint32_t s = rs_s, rnd = rs_rnd;
+          if (++rs_s == (uint32_t)n_stages) {
+            rs_s = 0;
+            ++rs_rnd;
+          }
           if (!mbar_wait(smem_u32(&bar_empty[s]), (rnd & 1) ^ 1, &s_abort)) {
             ok = false;
             break;
@@ -328,7 +332,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == kMmaWarp) {
     // ------------------------------------------------ MMA issuer
     if (lane == 0) {
-      uint32_t ctr = 0;
+      uint32_t rs_s = 0, rs_rnd = 0;
       int unit = 0;
       bool ok = true;
       bool issued = false;
@@ -342,8 +346,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc_fence_after();
           const uint32_t d = taddr + (uint32_t)(bb * ncols_buf);
-          for (int c = 0; c < st.n_chunks; ++c, ++ctr) {
-            const uint32_t s = ctr % (uint32_t)n_stages, rnd = ctr / (uint32_t)n_stages;
+          for (int c = 0; c < st.n_chunks; ++c) {
+            const uint32_t s = rs_s, rnd = rs_rnd;
+            if (++rs_s == (uint32_t)n_stages) {
+              rs_s = 0;
+              ++rs_rnd;
+            }
             if (!mbar_wait(smem_u32(&bar_fullA[s]), rnd & 1, &s_abort) ||
                 !mbar_wait(smem_u32(&bar_fullB[s]), rnd & 1, &s_abort)) {
               ok = false;
@@ -382,7 +390,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == kLoadWarp) {
     // ------------------------------------------------ B loader
     if (lane == 0) {
-      uint32_t ctr = 0;
+      uint32_t rs_s = 0, rs_rnd = 0;
       bool ok = true;
       uint32_t last_round[kMaxStages];
       bool used[kMaxStages] = {false, false, false, false};
@@ -390,8 +398,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int t = 0; t < T && ok; ++t) {
           const TcStep st = steps[t];
           const uint32_t bytes = (uint32_t)st.ncols * 256u;
-          for (int c = 0; c < st.n_chunks; ++c, ++ctr) {
-            const uint32_t s = ctr % (uint32_t)n_stages, rnd = ctr / (uint32_t)n_stages;
+          for (int c = 0; c < st.n_chunks; ++c) {
+            const uint32_t s = rs_s, rnd = rs_rnd;
+            if (++rs_s == (uint32_t)n_stages) {
+              rs_s = 0;
+              ++rs_rnd;
+            }
             if (!mbar_wait(smem_u32(&bar_empty[s]), (rnd & 1) ^ 1, &s_abort)) {
               ok = false;
               break;
