@@ -296,22 +296,32 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           const uint32_t a_hi = smem0 + s * stage_bytes + row * 128;
           const uint32_t a_lo = a_hi + kABytes;
+          {
+            // the thread's eight stations side by side (loads, phases, sincos, splits), so
+            // that their independent dependency chains interleave; padded stations have
+            // Q = 0 and zero B rows
+            const uint4* qs = qv + 2 * (size_t)(c * kStations + 8 * wg);
+            uint4 qa[8];
+            uint2 qb[8];
 #pragma unroll
-          for (int qp = 2 * wg; qp < 2 * wg + 2; ++qp) {
-            uint32_t hw[4], lw[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              // padded stations have Q = 0 and zero B rows
-              const int i = c * kStations + qp * 4 + j;
-              const uint4 qa = __ldg(qv + 2 * (size_t)i);
-              const uint2 qb = __ldg(reinterpret_cast<const uint2*>(qv + 2 * (size_t)i + 1));
-              float cs, sn;
-              __sincosf(phase_rad_fixed(rl, rh, qa, qb), &sn, &cs);
-              split2<FP16>(cs, sn, &hw[j], &lw[j]);
+            for (int j = 0; j < 8; ++j) {
+              qa[j] = __ldg(qs + 2 * j);
+              qb[j] = __ldg(reinterpret_cast<const uint2*>(qs + 2 * j + 1));
             }
-            const uint32_t phys = (uint32_t)((qp ^ (row & 7)) << 4);
-            st_shared_v4(a_hi + phys, hw);
-            st_shared_v4(a_lo + phys, lw);
+            float ph[8], cs[8], sn[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) ph[j] = phase_rad_fixed(rl, rh, qa[j], qb[j]);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) __sincosf(ph[j], &sn[j], &cs[j]);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              uint32_t hw[4], lw[4];
+#pragma unroll
+              for (int j = 0; j < 4; ++j) split2<FP16>(cs[4 * h + j], sn[4 * h + j], &hw[j], &lw[j]);
+              const uint32_t phys = (uint32_t)(((2 * wg + h) ^ (row & 7)) << 4);
+              st_shared_v4(a_hi + phys, hw);
+              st_shared_v4(a_lo + phys, lw);
+            }
           }
           fence_async_smem();
           __syncwarp();
