@@ -11,17 +11,37 @@
 // terms gives a relative error of order K 2^-48 in the worst case and
 // sqrt(K) 2^-48 typically (about 1e-13 at K = 512), with the low word
 // renormalised into the high word after every block of terms. Inputs must lie
-// in the FP32 range; the low word of values below ~1e-31 is subnormal and
-// carries fewer bits.
+// in the FP32 range; values below 2^-74 carry fewer than 48 bits.
 #pragma once
 
 namespace bipp {
 namespace df {
 
-// x = hi + lo with hi = fl32(x), lo = fl32(x - hi).
-__device__ __forceinline__ void split(double x, float& hi, float& lo) {
+// x = hi + lo with hi = fl32(x), lo = fl32(x - hi), through the FP64 pipe.
+__device__ __forceinline__ void split_fp64(double x, float& hi, float& lo) {
   hi = __double2float_rn(x);
   lo = __double2float_rn(x - (double)hi);
+}
+
+// x = hi + lo from the bits of x, off the FP64 pipe (which converts at the
+// DFMA rate on B300): hi keeps the sign, the exponent and the leading 23
+// fraction bits (x truncated to 24 significant bits), lo is the remaining 29
+// fraction bits, r 2^(e - 1075) with r < 2^29, converted to FP32 (24 of those
+// bits kept) with the sign of x. hi + lo carries 48 significant bits. Values
+// whose hi or lo would leave the FP32 normal range (|x| < 2^-74 or
+// |x| >= 2^128, zero, inf, NaN) take split_fp64.
+__device__ __forceinline__ void split(double x, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int hw = (unsigned int)(b >> 32), lw = (unsigned int)b;
+  const int e = (int)((hw >> 20) & 0x7FFu);
+  if (e < 1023 - 74 + 1 || e > 1023 + 127) {
+    split_fp64(x, hi, lo);
+    return;
+  }
+  const unsigned int sgn = hw & 0x80000000u;
+  hi = __uint_as_float(sgn | ((unsigned int)(e - 1023 + 127) << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29));
+  const float scale = __uint_as_float((unsigned int)(e - 1075 + 127) << 23);  // 2^(e - 1075), e >= 950
+  lo = __uint_as_float(__float_as_uint(__uint2float_rn(lw & 0x1FFFFFFFu) * scale) | sgn);
 }
 
 // (sh, sl) += (ah + al) * (bh + bl).
