@@ -82,8 +82,14 @@ typedef struct {
   int32_t use_graph;         /* 1: capture each batch geometry once in a CUDA graph and replay it; default 1 */
   int32_t autotune;          /* 1: time the tensor-core kernel's stage count on the first batch of a
                                 geometry and keep the fastest; default 1 */
-  int32_t reserved[4];       /* must be zero */
+  int32_t eigenimages;       /* 1: one image per kept eigenpair instead of energy levels: image e holds
+                                sum over steps of d_e |Phi^H a_e|^2 for the e-th largest kept eigenvalue
+                                (filter weight d_e as for levels); needs 1 <= n_eig <= BIPP_MAX_EIGENIMAGES
+                                and n_level = n_eig at create, level_bounds may be NULL; default 0 */
+  int32_t reserved[3];       /* must be zero */
 } bipp_ss_options;
+
+#define BIPP_MAX_EIGENIMAGES 64
 
 /* Fill *opt with the defaults listed above. */
 void bipp_ss_default_options(bipp_ss_options* opt);
@@ -91,9 +97,11 @@ void bipp_ss_default_options(bipp_ss_options* opt);
 /* Create an imaging handle (the paper's StandardSynthesis object, Sec. 3.1).
  *   pix_xyz      n_pix x 3 unit vectors (host), copied; must be finite.
  *   wl           wavelength [m], finite and > 0.
- *   level_bounds n_level x 2 (host): column 0 = lo, column 1 = hi; copied.
+ *   level_bounds n_level x 2 (host): column 0 = lo, column 1 = hi; copied
+ *                (unused, may be NULL, with opt->eigenimages).
  *   opt          NULL for defaults.
- * n_pix >= 1, 1 <= n_level <= 16. Images start at zero. */
+ * n_pix >= 1, 1 <= n_level <= 16 (n_level = n_eig <= 64 with eigenimages).
+ * Images start at zero. */
 int bipp_ss_create(bipp_ss_t* out, int64_t n_pix, const double* pix_xyz, double wl,
                    int32_t n_level, const double* level_bounds, const bipp_ss_options* opt);
 

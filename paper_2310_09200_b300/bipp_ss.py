@@ -53,6 +53,7 @@ EXPORTED = [
 
 BIPP_NOALLOC_MAX_STATIONS = 128
 BIPP_NOALLOC_MAX_EIG = 128
+BIPP_MAX_EIGENIMAGES = 64
 
 
 class BippError(RuntimeError):
@@ -65,7 +66,8 @@ class bipp_ss_options(C.Structure):
     _fields_ = [
         ("n_eig", C.c_int32), ("precision", C.c_int32), ("filter", C.c_int32), ("gram_identity", C.c_int32),
         ("max_jacobi_sweeps", C.c_int32), ("jacobi_tol", C.c_double), ("device", C.c_int32),
-        ("eig_mode", C.c_int32), ("use_graph", C.c_int32), ("autotune", C.c_int32), ("reserved", C.c_int32 * 4),
+        ("eig_mode", C.c_int32), ("use_graph", C.c_int32), ("autotune", C.c_int32), ("eigenimages", C.c_int32),
+        ("reserved", C.c_int32 * 3),
     ]
 
 
@@ -137,7 +139,7 @@ def bipp_ss_default_options(**kw) -> bipp_ss_options:
     for k, v in kw.items():
         if k in names and isinstance(v, str):
             v = names[k][v]
-        setattr(o, k, v)
+        setattr(o, k, int(v) if isinstance(v, bool) else v)
     return o
 
 
@@ -149,16 +151,21 @@ def _colmajor_xyz(xyz) -> np.ndarray:
 
 
 def bipp_ss_create(pix_xyz, wl: float, level_bounds, **opts) -> C.c_void_p:
-    """Create a handle. level_bounds: (n_level, 2) rows [lo, hi)."""
+    """Create a handle. level_bounds: (n_level, 2) rows [lo, hi); None with
+    eigenimages=1 (one image per kept eigenpair, n_level = n_eig)."""
     L = load()
     pix = _colmajor_xyz(pix_xyz)
-    b = np.asarray(level_bounds, dtype=np.float64)
-    if b.ndim != 2 or b.shape[1] != 2:
-        raise ValueError("level_bounds must be (n_level, 2)")
-    bc = np.ascontiguousarray(b.T)
     o = bipp_ss_default_options(**opts)
+    if level_bounds is None:
+        n_level, bptr = int(o.n_eig), None
+    else:
+        b = np.asarray(level_bounds, dtype=np.float64)
+        if b.ndim != 2 or b.shape[1] != 2:
+            raise ValueError("level_bounds must be (n_level, 2)")
+        bc = np.ascontiguousarray(b.T)
+        n_level, bptr = b.shape[0], _dp(bc)
     h = C.c_void_p()
-    rc = L.bipp_ss_create(C.byref(h), pix.shape[1], _dp(pix), float(wl), b.shape[0], _dp(bc), C.byref(o))
+    rc = L.bipp_ss_create(C.byref(h), pix.shape[1], _dp(pix), float(wl), n_level, bptr, C.byref(o))
     if rc != BIPP_OK:
         raise BippError(rc, bipp_ss_last_error(None))
     return h
@@ -373,7 +380,7 @@ class StandardSynthesis:
 
     def __init__(self, pix_xyz, wl, level_bounds, **opts):
         self.n_pix = int(np.asarray(pix_xyz).shape[0])
-        self.n_level = int(np.asarray(level_bounds).shape[0])
+        self.n_level = int(opts["n_eig"]) if level_bounds is None else int(np.asarray(level_bounds).shape[0])
         self.h = None
         self.h = bipp_ss_create(pix_xyz, wl, level_bounds, **opts)
 

@@ -209,6 +209,7 @@ static Batch make_batch(bipp_ss* h, int T, int N, int K, const double* st, const
   b.status = h->d_status; b.sweeps = h->d_sweeps; b.nkept = h->d_nkept;
   b.sel_mu = h->d_sel_mu; b.level = h->d_level; b.wt = h->d_wt; b.W64 = h->d_W64; b.W32 = h->d_W32;
   b.q = h->d_q; b.flag = h->d_flag;
+  b.eigen = h->opt.eigenimages;
   return b;
 }
 
@@ -252,12 +253,19 @@ extern "C" int bipp_ss_create_channels(bipp_ss_t* out, int64_t n_pix, const doub
   for (int c = 0; c < n_chan; ++c)
     if (!(wl[c] > 0.0) || !isfinite(wl[c]))
       return fail(nullptr, BIPP_ERR_INVALID_ARG, "wavelength of channel %d must be finite and > 0", c);
-  if (n_level < 1 || n_level > kMaxLevels || !level_bounds)
-    return fail(nullptr, BIPP_ERR_INVALID_ARG, "need 1 <= n_level <= %d and level_bounds", kMaxLevels);
   bipp_ss_options o;
   if (opt) o = *opt; else bipp_ss_default_options(&o);
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 3; ++i)
     if (o.reserved[i]) return fail(nullptr, BIPP_ERR_INVALID_ARG, "reserved option fields must be zero");
+  if (o.eigenimages != 0 && o.eigenimages != 1)
+    return fail(nullptr, BIPP_ERR_INVALID_ARG, "eigenimages must be 0 or 1");
+  if (o.eigenimages) {
+    if (o.n_eig < 1 || o.n_eig > kMaxEigenimages || n_level != o.n_eig)
+      return fail(nullptr, BIPP_ERR_INVALID_ARG, "eigenimages need 1 <= n_eig <= %d and n_level == n_eig",
+                  kMaxEigenimages);
+  } else if (n_level < 1 || n_level > kMaxLevels || !level_bounds) {
+    return fail(nullptr, BIPP_ERR_INVALID_ARG, "need 1 <= n_level <= %d and level_bounds", kMaxLevels);
+  }
   if (o.precision < BIPP_PREC_FP64 || o.precision > BIPP_PREC_SPLIT_FP16)
     return fail(nullptr, BIPP_ERR_INVALID_ARG, "unknown precision %d", o.precision);
   if (o.filter != BIPP_FILTER_LSQ && o.filter != BIPP_FILTER_STD)
@@ -266,7 +274,7 @@ extern "C" int bipp_ss_create_channels(bipp_ss_t* out, int64_t n_pix, const doub
     return fail(nullptr, BIPP_ERR_INVALID_ARG, "unknown eig_mode %d", o.eig_mode);
   if (o.n_eig < 0 || o.max_jacobi_sweeps < 1 || !(o.jacobi_tol > 0.0))
     return fail(nullptr, BIPP_ERR_INVALID_ARG, "bad n_eig / max_jacobi_sweeps / jacobi_tol");
-  for (int64_t i = 0; i < (int64_t)2 * n_level * n_chan; ++i)
+  for (int64_t i = 0; !o.eigenimages && i < (int64_t)2 * n_level * n_chan; ++i)
     if (isnan(level_bounds[i])) return fail(nullptr, BIPP_ERR_INVALID_ARG, "level bound %lld is NaN", (long long)i);
   for (int64_t i = 0; i < 3 * n_pix; ++i)
     if (!isfinite(pix_xyz[i]))
@@ -303,9 +311,13 @@ extern "C" int bipp_ss_create_channels(bipp_ss_t* out, int64_t n_pix, const doub
   if ((e = dalloc(&h->d_bounds, (size_t)2 * n_level * n_chan)) != cudaSuccess) return bail(BIPP_ERR_OUT_OF_MEMORY, "bounds", e);
   if ((e = cudaMemcpy(h->d_pix, pix_xyz, sizeof(double) * 3 * n_pix, cudaMemcpyHostToDevice)) != cudaSuccess)
     return bail(BIPP_ERR_CUDA, "pixel upload", e);
-  if ((e = cudaMemcpy(h->d_bounds, level_bounds, sizeof(double) * 2 * n_level * n_chan, cudaMemcpyHostToDevice)) !=
-      cudaSuccess)
+  if (o.eigenimages) {  // levels are ranks; the bounds are unused
+    if ((e = cudaMemset(h->d_bounds, 0, sizeof(double) * 2 * n_level * n_chan)) != cudaSuccess)
+      return bail(BIPP_ERR_CUDA, "bounds", e);
+  } else if ((e = cudaMemcpy(h->d_bounds, level_bounds, sizeof(double) * 2 * n_level * n_chan,
+                             cudaMemcpyHostToDevice)) != cudaSuccess) {
     return bail(BIPP_ERR_CUDA, "bounds upload", e);
+  }
   if ((e = cudaMemset(h->d_img, 0, sizeof(double) * n_img)) != cudaSuccess) return bail(BIPP_ERR_CUDA, "memset", e);
   launch_pixel_split(h->d_pix, h->d_pix_hl, n_pix, h->stream);
   if ((e = cudaGetLastError()) != cudaSuccess) return bail(BIPP_ERR_CUDA, "pixel split launch", e);
@@ -337,6 +349,8 @@ static int check_sizes(bipp_ss* h, int n_t, int n_st_max, const int32_t* chan, c
     const int k = n_eig ? n_eig[t] : (h->opt.n_eig > 0 ? h->opt.n_eig : n);
     if (k < 1) return fail(h, BIPP_ERR_INVALID_ARG, "step %d: n_eig=%d must be >= 1", t, k);
     if (k > n) return fail(h, BIPP_ERR_UNSUPPORTED, "step %d: n_eig=%d exceeds n_st=%d", t, k, n);
+    if (h->opt.eigenimages && k > h->n_level)
+      return fail(h, BIPP_ERR_INVALID_ARG, "step %d: n_eig=%d exceeds the handle's %d eigenimages", t, k, h->n_level);
     const int c = chan ? chan[t] : 0;
     if (c < 0 || c >= h->n_chan) return fail(h, BIPP_ERR_INVALID_ARG, "step %d: channel %d outside [0, %d)", t, c, h->n_chan);
     if (t > 0 && c < chan_v[t - 1])

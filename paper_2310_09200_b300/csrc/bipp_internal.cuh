@@ -45,7 +45,13 @@ struct Batch {
   float2* W32;    // [T][n_max][k_max] FP32 copy, station-major
   float* q;       // [T][6][n_max] station p/wl as float hi/lo: xh,yh,zh,xl,yl,zl
   int* flag;      // [1] OR of all step statuses (synthesis skips the batch if set)
+  int eigen;      // 1: one image per kept eigenpair (level = rank) instead of energy levels
 };
+
+// Eigenimages use the level kernels with kEigSlots register slots per thread:
+// every synthesis thread owns a fixed quarter of the <= 64 eigenvectors.
+constexpr int kMaxEigenimages = 64;
+constexpr int kEigSlots = 16;
 
 // Small per-step arrays of the mixed-precision eigensolver (eig_mixed.cu).
 struct MixedWs {

@@ -403,10 +403,14 @@ __global__ void k_select(Batch b, int n_level, const double* all_bounds, int fil
     if (e < K) {
       m = mu[idx[e]];
       w = (filter == 0) ? m : 1.0;
-      for (int l = 0; l < n_level; ++l) {
-        if (bounds[l] <= m && m < bounds[n_level + l]) {
-          lev = l;
-          break;
+      if (b.eigen) {  // eigenimages: the level is the rank
+        lev = e;
+      } else {
+        for (int l = 0; l < n_level; ++l) {
+          if (bounds[l] <= m && m < bounds[n_level + l]) {
+            lev = l;
+            break;
+          }
         }
       }
     }

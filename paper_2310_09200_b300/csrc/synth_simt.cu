@@ -69,10 +69,14 @@ __global__ void __launch_bounds__(kThreads) k_synth_f32(Batch b, Pixels px, int 
     __syncthreads();
     if (eg == 0 && valid) {
       double* im = img + (size_t)chan * n_level * px.n;
-      for (int l = 0; l < n_level; ++l) {
-        float s = 0.0f;
-        for (int g = 0; g < kThreads / kPix; ++g) s += sh_red[(g * MAXL + l) * kPix + pl];
-        im[(size_t)l * px.n + r] += (double)s;
+      if (b.eigen) {  // slot s of group g is eigenvector 4 s + g
+        for (int l = 0; l < n_level; ++l) im[(size_t)l * px.n + r] += (double)sh_red[((l & 3) * MAXL + (l >> 2)) * kPix + pl];
+      } else {
+        for (int l = 0; l < n_level; ++l) {
+          float s = 0.0f;
+          for (int g = 0; g < kThreads / kPix; ++g) s += sh_red[(g * MAXL + l) * kPix + pl];
+          im[(size_t)l * px.n + r] += (double)s;
+        }
       }
     }
     __syncthreads();
@@ -127,7 +131,8 @@ __global__ void __launch_bounds__(kThreads) k_synth_f32(Batch b, Pixels px, int 
         if (e < K) {
           const int lev = b.level[(size_t)t * KM + e];
           if (lev >= 0)
-            level_add<MAXL, float>(lacc, lev, (float)b.wt[(size_t)t * KM + e] * (zr[u] * zr[u] + zi[u] * zi[u]));
+            // eigenimages: slot (e - eg) / 4 of this thread's eigenvectors e = eg (mod 4)
+            level_add<MAXL, float>(lacc, b.eigen ? e0 / 4 + u : lev, (float)b.wt[(size_t)t * KM + e] * (zr[u] * zr[u] + zi[u] * zi[u]));
         }
       }
     }
@@ -164,10 +169,14 @@ __global__ void __launch_bounds__(kThreads) k_synth_f64(Batch b, Pixels px, int 
     __syncthreads();
     if (eg == 0 && valid) {
       double* im = img + (size_t)chan * n_level * px.n;
-      for (int l = 0; l < n_level; ++l) {
-        double s = 0.0;
-        for (int g = 0; g < kThreads / kPix; ++g) s += sh_red[(g * MAXL + l) * kPix + pl];
-        im[(size_t)l * px.n + r] += s;
+      if (b.eigen) {  // slot s of group g is eigenvector 4 s + g
+        for (int l = 0; l < n_level; ++l) im[(size_t)l * px.n + r] += sh_red[((l & 3) * MAXL + (l >> 2)) * kPix + pl];
+      } else {
+        for (int l = 0; l < n_level; ++l) {
+          double s = 0.0;
+          for (int g = 0; g < kThreads / kPix; ++g) s += sh_red[(g * MAXL + l) * kPix + pl];
+          im[(size_t)l * px.n + r] += s;
+        }
       }
     }
     __syncthreads();
@@ -218,7 +227,8 @@ __global__ void __launch_bounds__(kThreads) k_synth_f64(Batch b, Pixels px, int 
         if (e < K) {
           const int lev = b.level[(size_t)t * KM + e];
           if (lev >= 0)
-            level_add<MAXL, double>(lacc, lev, b.wt[(size_t)t * KM + e] * (zr[u] * zr[u] + zi[u] * zi[u]));
+            // eigenimages: slot (e - eg) / 4 of this thread's eigenvectors e = eg (mod 4)
+            level_add<MAXL, double>(lacc, b.eigen ? e0 / 4 + u : lev, b.wt[(size_t)t * KM + e] * (zr[u] * zr[u] + zi[u] * zi[u]));
         }
       }
     }

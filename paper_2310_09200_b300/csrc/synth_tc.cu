@@ -252,8 +252,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int e = cb * 8 + p;
           if (e < K) {
             const int2 lv = lw[e];
+            // eigenimages: slot (cb / 4) * 8 + p of this warpgroup's eigenvectors e = cb * 8 + p
             if (lv.x >= 0)
-              level_add<MAXL>(lacc, lv.x, __int_as_float(lv.y) * fmaf(v[2 * p], v[2 * p], v[2 * p + 1] * v[2 * p + 1]));
+              level_add<MAXL>(lacc, b.eigen ? (cb >> 2) * 8 + p : lv.x,
+                              __int_as_float(lv.y) * fmaf(v[2 * p], v[2 * p], v[2 * p + 1] * v[2 * p + 1]));
           }
         }
       }
@@ -263,9 +265,19 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (last_of_chan(b, t)) {
         const int64_t r = (int64_t)tile * kRows + row;
         double* im = img + (size_t)step_chan(b, t) * n_level * px.n;
-        if (r < px.n)
-          for (int l = 0; l < n_level; ++l)
-            if (lacc[l] != 0.0f) atomicAdd(im + (size_t)l * px.n + r, (double)lacc[l]);
+        if (r < px.n) {
+          if (b.eigen) {
+#pragma unroll
+            for (int sl = 0; sl < MAXL; ++sl) {
+              const int e = ((sl >> 3) * 4 + wg) * 8 + (sl & 7);
+              if (e < n_level && lacc[sl] != 0.0f) atomicAdd(im + (size_t)e * px.n + r, (double)lacc[sl]);
+            }
+          } else {
+#pragma unroll
+            for (int l = 0; l < MAXL; ++l)
+              if (l < n_level && lacc[l] != 0.0f) atomicAdd(im + (size_t)l * px.n + r, (double)lacc[l]);
+          }
+        }
 #pragma unroll
         for (int l = 0; l < MAXL; ++l) lacc[l] = 0.0f;
       }

@@ -61,3 +61,18 @@ def quad_form_image(pix, st_xyz, wl, M):
     """Phi(r)^H M Phi(r) for every pixel (real part), M (n_st, n_st)."""
     P = phi_matrix(pix, st_xyz, wl)
     return np.real(np.einsum("ri,ij,rj->r", P.conj(), M, P))
+
+
+def oracle_eigenimages(pix, wl, st_list, vis_list, n_eig, filter="lsq", gram_identity=False):
+    """One image per kept eigenpair (rank order), summed over steps, from the
+    oracle's eigensolve and synthesis with level id = rank. n_eig: one count
+    for all steps or one per step; the image count is the largest."""
+    counts = [n_eig] * len(st_list) if np.isscalar(n_eig) else list(n_eig)
+    n_img = max(counts)
+    img = None
+    for p, V, k in zip(st_list, vis_list, counts):
+        G = np.eye(p.shape[0]) if gram_identity else oracle.gram(p, wl)
+        mu, A, _ = oracle.geneig(V, G)
+        d = mu[:k] if filter == "lsq" else np.ones(k)
+        img = oracle.synth_levels(pix, p, wl, A[:, :k], d, np.arange(k, dtype=np.int32), n_img, img=img)
+    return img

@@ -64,7 +64,8 @@ def test_default_options(lib):
     assert o.device == -1 and o.eig_mode == bipp_ss.BIPP_EIG_JACOBI64
 
 
-@pytest.mark.parametrize("case", ["n_pix", "wl", "levels", "precision", "reserved", "nan_bound", "nan_pix"])
+@pytest.mark.parametrize("case", ["n_pix", "wl", "levels", "precision", "reserved", "nan_bound", "nan_pix",
+                                  "eig_levels", "eig_many", "eig_flag"])
 def test_create_rejects_invalid_arguments_before_device_use(lib, case):
     pix = np.array([[0.0, 0.0, 1.0], [0.1, 0.0, 0.99]])
     b = np.array([[-np.inf, np.inf]])
@@ -94,6 +95,14 @@ def test_create_rejects_invalid_arguments_before_device_use(lib, case):
     elif case == "nan_pix":
         pix = pix.copy()
         pix[1, 2] = np.nan
+    elif case == "eig_levels":  # eigenimages need n_level == n_eig
+        kw.update(eigenimages=1, n_eig=4)
+        b = np.zeros((3, 2))
+    elif case == "eig_many":
+        kw.update(eigenimages=1, n_eig=bipp_ss.BIPP_MAX_EIGENIMAGES + 1)
+        b = None
+    elif case == "eig_flag":
+        kw.update(eigenimages=2, n_eig=1)
     with pytest.raises(bipp_ss.BippError) as e:
         bipp_ss.bipp_ss_create(pix, wl, b, **kw)
     assert e.value.code == bipp_ss.BIPP_ERR_INVALID_ARG

@@ -308,3 +308,20 @@ def test_oracle_gradient_matches_central_differences():
             Wm[t, i, e] -= h * unit
             num += unit * (loss(g, Wp) - loss(g, Wm)) / (2 * h)
         assert abs(num - gW[t, i, e]) <= 1e-6 * max(1.0, abs(gW[t, i, e])), (t, i, e, num, gW[t, i, e])
+
+
+def test_eigenimages_partition_and_closed_form():
+    """One image per kept eigenpair: they sum to the single-level image, and
+    image e is d_e |Phi^H a_e|^2 written out from the eigenvectors."""
+    p, wl, pix, V, _, _ = _small_case(seed=12)
+    n_eig = 6
+    eig = helpers.oracle_eigenimages(pix, wl, [p], [V], n_eig)
+    one, mu, _, _ = oracle.ss_step(pix, wl, ALL, n_eig, p, V)
+    np.testing.assert_allclose(eig.sum(axis=1), one[:, 0], rtol=1e-12, atol=1e-12 * np.max(np.abs(one)))
+    mu_all, A, _ = oracle.geneig(V, oracle.gram(p, wl))
+    P = helpers.phi_matrix(pix, p, wl)
+    for e in range(n_eig):
+        want = mu_all[e] * np.abs(P.conj() @ A[:, e]) ** 2
+        np.testing.assert_allclose(eig[:, e], want, rtol=1e-10, atol=1e-12 * np.max(np.abs(want)))
+    std = helpers.oracle_eigenimages(pix, wl, [p], [V], n_eig, filter="std")
+    assert np.all(std >= 0.0)
