@@ -250,6 +250,25 @@ int bipp_ss_destroy(bipp_ss_t h);
  * h is NULL); valid until the next call on h. Never NULL. */
 const char* bipp_ss_last_error(bipp_ss_t h);
 
+/* ---- parameter estimation (Sec. 2.6 "Energy Levels & Partitioning"), host only
+ *
+ * bipp_ss_energy_neig: the least number of leading eigenpairs holding at least
+ * `fraction` (0 < fraction <= 1) of the energy of one step, energy being the
+ * sum of the positive eigenvalues. mu_desc: n eigenvalues in descending order
+ * (host); *n_eig receives the count (>= 1). BIPP_ERR_INVALID_ARG on bad sizes,
+ * non-finite or unordered values. */
+int bipp_ss_energy_neig(int32_t n, const double* mu_desc, double fraction, int32_t* n_eig);
+
+/* bipp_ss_kmeans_bounds: level intervals from k-means clustering of n values
+ * (e.g. eigenvalues pooled over an observation's steps): the exact partition
+ * of the sorted values into n_level contiguous clusters of least
+ * within-cluster sum of squares. Writes level_bounds (host, n_level x 2
+ * column-major, the layout of bipp_ss_create): level 0 is the highest
+ * cluster, inner edges lie halfway between neighbouring clusters, outer edges
+ * are -inf and +inf. 1 <= n_level <= n; BIPP_ERR_INVALID_ARG otherwise or on
+ * non-finite values. Error text via bipp_ss_last_error(NULL). */
+int bipp_ss_kmeans_bounds(int32_t n, const double* values, int32_t n_level, double* level_bounds);
+
 #ifdef __cplusplus
 }
 #endif

@@ -49,6 +49,7 @@ EXPORTED = [
     "bipp_ss_set_images", "bipp_ss_last_eigvals", "bipp_ss_get_timings", "bipp_ss_destroy",
     "bipp_ss_last_error", "bipp_ss_collect_noalloc", "bipp_ss_synth_levels_device",
     "bipp_ss_synth_adjoint_device", "bipp_ss_create_channels", "bipp_ss_collect_channels",
+    "bipp_ss_energy_neig", "bipp_ss_kmeans_bounds",
 ]
 
 BIPP_NOALLOC_MAX_STATIONS = 128
@@ -99,6 +100,8 @@ def load(path: str | None = None):
     L.bipp_ss_last_eigvals.argtypes = [H, i32, i32, ip, ip, dp, ip]
     L.bipp_ss_get_timings.argtypes = [H, dp]
     L.bipp_ss_destroy.argtypes = [H]
+    L.bipp_ss_energy_neig.argtypes = [i32, dp, C.c_double, ip]
+    L.bipp_ss_kmeans_bounds.argtypes = [i32, dp, i32, dp]
     L.bipp_ss_last_error.argtypes = [H]
     L.bipp_ss_last_error.restype = C.c_char_p
     L.bipp_ss_collect_noalloc.argtypes = [i64, vp, C.c_double, i32, dp, i32, i32, i32, i32, vp, vp, vp, vp,
@@ -434,14 +437,55 @@ def quantile_level_bounds(pooled_mu, n_level: int) -> np.ndarray:
     return np.array(list(zip(lo, hi)))[::-1].copy()
 
 
-def estimate_level_bounds(st_xyz, vis, wl, n_eig, n_level, **opts):
-    """Parameter-estimation pre-pass (Table tts): run the GPU Gram + eigensolve
-    on the given steps (synthesis on one pixel only), pool the kept
-    eigenvalues and derive quantile level bounds. Returns (bounds, pooled)."""
+def bipp_ss_energy_neig(mu_desc, fraction: float) -> int:
+    """Least number of leading eigenpairs holding `fraction` of the positive energy."""
+    mu = np.ascontiguousarray(mu_desc, dtype=np.float64)
+    k = C.c_int32(0)
+    rc = load().bipp_ss_energy_neig(mu.shape[0], _dp(mu), float(fraction), C.byref(k))
+    if rc != BIPP_OK:
+        raise BippError(rc, bipp_ss_last_error(None))
+    return int(k.value)
+
+
+def bipp_ss_kmeans_bounds(values, n_level: int) -> np.ndarray:
+    """Level intervals (n_level, 2) rows [lo, hi) from 1-D k-means of the values."""
+    v = np.ascontiguousarray(values, dtype=np.float64).ravel()
+    out = np.zeros(2 * n_level, dtype=np.float64)
+    rc = load().bipp_ss_kmeans_bounds(v.shape[0], _dp(v), int(n_level), _dp(out))
+    if rc != BIPP_OK:
+        raise BippError(rc, bipp_ss_last_error(None))
+    return np.ascontiguousarray(out.reshape(2, n_level).T)
+
+
+def _prepass_eigvals(st_xyz, vis, wl, n_eig, **opts):
+    """GPU Gram + eigensolve of the given steps (synthesis on one pixel only);
+    returns each step's kept eigenvalues, descending. n_eig: one count or one
+    per step."""
     one_px = np.array([[0.0, 0.0, 1.0]])
     opts = {k: v for k, v in opts.items() if k != "n_eig"}
-    with StandardSynthesis(one_px, wl, np.array([[-math.inf, math.inf]]), n_eig=n_eig, **opts) as ss:
-        ss.collect_batch(st_xyz, vis)
-        nt, nk, mu, _ = bipp_ss_last_eigvals(ss.h, len(vis), n_eig)
-    pooled = np.concatenate([mu[t, : nk[t]] for t in range(nt)])
+    per_step = None if np.isscalar(n_eig) else [int(k) for k in n_eig]
+    k_max = int(n_eig) if per_step is None else max(per_step)
+    with StandardSynthesis(one_px, wl, np.array([[-math.inf, math.inf]]), n_eig=k_max, **opts) as ss:
+        ss.collect_batch(st_xyz, vis, per_step)
+        nt, nk, mu, _ = bipp_ss_last_eigvals(ss.h, len(vis), k_max)
+    return [mu[t, : nk[t]] for t in range(nt)]
+
+
+def estimate_level_bounds(st_xyz, vis, wl, n_eig, n_level, method: str = "quantile", **opts):
+    """Parameter-estimation pre-pass (Table tts): run the GPU Gram + eigensolve
+    on the given steps, pool the kept eigenvalues and derive level bounds by
+    quantiles or by k-means clustering (Sec. 2.6). Returns (bounds, pooled)."""
+    pooled = np.concatenate(_prepass_eigvals(st_xyz, vis, wl, n_eig, **opts))
+    if method == "kmeans":
+        return bipp_ss_kmeans_bounds(pooled, n_level), pooled
+    if method != "quantile":
+        raise ValueError(f"unknown method {method!r}")
     return quantile_level_bounds(pooled, n_level), pooled
+
+
+def estimate_n_eig(st_xyz, vis, wl, fraction: float, **opts) -> int:
+    """Truncation of Sec. 2.6 estimated from an observation: the least number
+    of leading eigenpairs holding `fraction` of each step's energy, maximised
+    over the given steps (all eigenpairs are solved for in the pre-pass)."""
+    steps = _prepass_eigvals(st_xyz, vis, wl, [int(np.asarray(p).shape[0]) for p in st_xyz], **opts)
+    return max(bipp_ss_energy_neig(mu, fraction) for mu in steps)

@@ -101,6 +101,12 @@ struct bipp_ss {
 
 static std::string g_create_err = "no error";
 
+// Error message of calls without a handle (create, the estimation functions).
+int bipp::set_global_error(int code, const char* msg) {
+  g_create_err = msg;
+  return code;
+}
+
 static int fail(bipp_ss* h, int code, const char* fmt, ...) {
   char buf[512];
   va_list ap;

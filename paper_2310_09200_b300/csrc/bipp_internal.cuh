@@ -89,6 +89,8 @@ void launch_jacobi(const Batch& b, double tol, int max_sweeps, cudaStream_t s);
 bool eig_mixed_fits(int n_max, int KP);
 constexpr int kMixedLaunches = 61;  // kernels launched by launch_eig_mixed
 void launch_eig_mixed(const Batch& b, const MixedWs& w, double tol, int max_sweeps, cudaStream_t s);
+// Error message of calls without a handle (returned by bipp_ss_last_error(NULL)).
+int set_global_error(int code, const char* msg);
 // d_bounds: per channel, n_level x 2 column-major blocks.
 void launch_select(const Batch& b, int n_level, const double* d_bounds, int filter, cudaStream_t s);
 void launch_pixel_split(const double* d_xyz, float* d_hl, int64_t n, cudaStream_t s);

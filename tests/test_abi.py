@@ -44,6 +44,12 @@ def test_library_exports_every_declared_symbol(lib):
         getattr(lib, name)
 
 
+def test_library_has_no_unresolved_own_symbols(lib):
+    out = subprocess.run(["nm", "-D", "--undefined-only", bipp_ss.LIB_PATH], capture_output=True, text=True,
+                         check=True).stdout
+    assert "bipp" not in out, out
+
+
 def test_binding_names_match_abi():
     assert set(bipp_ss.EXPORTED) == _declared()
     for name in bipp_ss.EXPORTED:
