@@ -58,6 +58,8 @@ constexpr int kRows = 128;            // pixels per tile = UMMA M
 constexpr int kStations = 32;         // stations per stage (64 K-elements)
 constexpr int kABytes = kRows * 128;  // one A operand image per stage (hi or lo)
 constexpr int kMaxStages = 4;
+constexpr int kQWin = 16;  // chunks of station words staged per window (two windows in shared memory)
+static_assert((kQWin & (kQWin - 1)) == 0, "window of a power-of-two chunk count");
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 // ---------------------------------------------------------------- PTX wrappers
@@ -168,6 +170,22 @@ __device__ __forceinline__ float phase_rad_fixed(const uint32_t (&rl)[3], const 
   return (float)(int32_t)acc * 1.4629180792671596e-09f;  // 2 pi 2^-32
 }
 
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ uint4 ld_shared_v4(uint32_t a) {
+  uint4 v;
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ uint2 ld_shared_v2(uint32_t a) {
+  uint2 v;
+  asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a));
+  return v;
+}
+
 __device__ __forceinline__ void st_shared_v4(uint32_t a, const uint32_t (&w)[4]) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3])
                : "memory");
@@ -191,7 +209,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t bar_fullA[kMaxStages], bar_fullB[kMaxStages], bar_empty[kMaxStages];
-  __shared__ __align__(8) uint64_t bar_accf[2], bar_acce[2], bar_drain;
+  __shared__ __align__(8) uint64_t bar_accf[2], bar_acce[2], bar_drain, bar_q;
   __shared__ uint32_t s_taddr;
   __shared__ volatile int s_abort;
 
@@ -207,6 +225,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(smem_u32(&bar_acce[i]), kProdWarps);
     }
     mbar_init(smem_u32(&bar_drain), 1);
+    mbar_init(smem_u32(&bar_q), kProdWarps);
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     fence_async_smem();
@@ -235,6 +254,22 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
     for (int l = 0; l < MAXL; ++l) lacc[l] = 0.0f;
     bool ok = true;
+    // Station words, staged in shared memory by windows of up to kQWin chunks
+    // in two buffers after the stage ring: the window after the current one
+    // (in tile, step, chunk order) is copied with cp.async while the current
+    // one is produced, so the per-stage reads hit shared memory, not L2.
+    constexpr uint32_t kQWinBytes = kQWin * kStations * 32u;
+    const uint32_t qsm0 = smem0 + (uint32_t)n_stages * (uint32_t)stage_bytes;
+    uint32_t qbuf = 0, qphase = 0;
+    auto q_prefetch = [&](int tn, int c0, uint32_t buf) {
+      const unsigned char* src =
+          reinterpret_cast<const unsigned char*>(qfix + ((size_t)tn * qfix_stride + (size_t)c0 * kStations) * 8);
+      const uint32_t nbytes = (uint32_t)min(kQWin, steps[tn].n_chunks - c0) * kStations * 32u;
+      for (uint32_t o = threadIdx.x * 16u; o < nbytes; o += kProdWarps * 32u * 16u)
+        cp_async16(qsm0 + buf * kQWinBytes + o, src + o);
+      cp_async_commit();
+    };
+    if (blockIdx.x < n_tiles) q_prefetch(0, 0, 0);
 
     auto epilogue = [&](int tile, int t, int u) -> bool {
       const int bb = u & 1;
@@ -295,8 +330,28 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       for (int t = 0; t < T && ok; ++t) {
         const int nch = steps[t].n_chunks;
-        const uint4* qv = reinterpret_cast<const uint4*>(qfix + (size_t)t * qfix_stride * 8);
+        uint32_t qcur = 0;
         for (int c = 0; c < nch; ++c) {
+          if ((c & (kQWin - 1)) == 0) {
+            // the window's words have landed in every producer's share, and every
+            // producer is done with the previous window: refill its buffer
+            cp_async_wait();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&bar_q));
+            if (!mbar_wait(smem_u32(&bar_q), qphase, &s_abort)) {
+              ok = false;
+              break;
+            }
+            qphase ^= 1;
+            if (c + kQWin < nch)
+              q_prefetch(t, c + kQWin, qbuf ^ 1);
+            else if (t + 1 < T)
+              q_prefetch(t + 1, 0, qbuf ^ 1);
+            else if (tile + (int)gridDim.x < n_tiles)
+              q_prefetch(0, 0, qbuf ^ 1);
+            qcur = qsm0 + qbuf * kQWinBytes;
+            qbuf ^= 1;
+          }
           const uint32_t s = rs_s, rnd = rs_rnd;
           if (++rs_s == (uint32_t)n_stages) {
             rs_s = 0;
@@ -312,13 +367,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             // the thread's eight stations side by side (loads, phases, sincos, splits), so
             // that their independent dependency chains interleave; padded stations have
             // Q = 0 and zero B rows
-            const uint4* qs = qv + 2 * (size_t)(c * kStations + 8 * wg);
+            const uint32_t qs = qcur + (uint32_t)((c & (kQWin - 1)) * kStations + 8 * wg) * 32u;
             uint4 qa[8];
             uint2 qb[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-              qa[j] = __ldg(qs + 2 * j);
-              qb[j] = __ldg(reinterpret_cast<const uint2*>(qs + 2 * j + 1));
+              qa[j] = ld_shared_v4(qs + 32u * j);
+              qb[j] = ld_shared_v2(qs + 32u * j + 16u);
             }
             float ph[8], cs[8], sn[8];
 #pragma unroll
@@ -350,6 +405,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
     if (ok && pend_tile >= 0) ok = epilogue(pend_tile, pend_t, unit - 1);
+    cp_async_wait();  // no copy may still be in flight into shared memory at exit
     if (!ok) s_abort = 1;
   } else if (warp == kMmaWarp) {
     // ------------------------------------------------ MMA issuer
@@ -615,7 +671,13 @@ int tc_read_status(TcWorkspace* w) {
 namespace {
 
 int stage_bytes_for(int ncols_max) { return 2 * kABytes + 2 * ncols_max * 128; }
-int max_stages_for(int ncols_max) { return std::min(kMaxStages, (220 * 1024) / stage_bytes_for(ncols_max)); }
+constexpr int kQStageBytes = 2 * kQWin * kStations * 32;  // the two station-word windows
+// Dynamic shared memory: the stage ring, the station-word windows and 1 KB of
+// alignment slack, within 227 KB less room for the static barriers.
+constexpr int kDynSmemMax = 227 * 1024 - 1024 - 512;
+int max_stages_for(int ncols_max) {
+  return std::min(kMaxStages, (kDynSmemMax - kQStageBytes) / stage_bytes_for(ncols_max));
+}
 
 // Autotuned stage counts, keyed by (accumulator width, operand type): the
 // tuned value holds for every batch with the same key in this process.
@@ -625,7 +687,7 @@ std::map<std::pair<int, int>, int> g_tuned_stages;
 int launch_kernel(const Batch& b, const Pixels& px, int n_level, double* img, const TcPlan& p, int n_stages,
                   TcWorkspace* w, cudaStream_t s) {
   const int stage_bytes = stage_bytes_for(p.ncols_max);
-  const size_t smem = (size_t)n_stages * stage_bytes + 1024;
+  const size_t smem = (size_t)n_stages * stage_bytes + kQStageBytes + 1024;
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
