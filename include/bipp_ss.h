@@ -66,7 +66,7 @@ extern "C" {
 #define BIPP_FILTER_STD 1 /* d_e = 1    (Sec. 2.6, standardised image) */
 
 #define BIPP_EIG_JACOBI64 0 /* FP64 parallel-order Jacobi on the reduced matrix */
-#define BIPP_EIG_MIXED 1    /* FP32 Jacobi, then FP64 refinement of the kept pairs */
+#define BIPP_EIG_MIXED 1    /* FP32 tridiagonal eigendecomposition, then FP64-class refinement of the kept pairs */
 
 typedef struct bipp_ss* bipp_ss_t;
 
@@ -86,8 +86,27 @@ typedef struct {
                                 sum over steps of d_e |Phi^H a_e|^2 for the e-th largest kept eigenvalue
                                 (filter weight d_e as for levels); needs 1 <= n_eig <= BIPP_MAX_EIGENIMAGES
                                 and n_level = n_eig at create, level_bounds may be NULL; default 0 */
-  int32_t reserved[3];       /* must be zero */
+  int32_t synthesis;         /* BIPP_SYNTH_*; default BIPP_SYNTH_STANDARD */
+  double nufft_eps;          /* BIPP_SYNTH_NUFFT: type-3 NUFFT tolerance in [1e-7, 0.1]; default 1e-5 */
+  int32_t reserved[4];       /* must be zero */
 } bipp_ss_options;
+
+/* Image synthesis strategy (Sec. 2.5, 3.4).
+ * STANDARD: Phi^H W per pixel and step, then the level reduction (Algorithm 2).
+ * NUFFT:    per level, the Gram-corrected visibilities of the level's eigenpairs,
+ *           V'_l = sum_{e in l} d_e a_e a_e^H, summed over all baselines of the
+ *           batch's steps with one type-3 NUFFT per level and channel
+ *           (Algorithm 3): I_l(r) = sum_t sum_{p,q} V'_l,pq exp(-j 2 pi/wl <p_p - p_q, r>).
+ *           Same images as STANDARD up to the NUFFT tolerance (relative L2 of
+ *           the order of nufft_eps). Grids and sums are FP32 with coordinates
+ *           and phases reduced in FP64; `precision` does not apply. The uniform
+ *           grid spans the batch's baseline extent times the pixels' extent per
+ *           dimension (of the order of 2 max|b|/wl x (pixel extent) points), so
+ *           it suits fields whose pixels resolve the array (small fields of
+ *           view); BIPP_ERR_UNSUPPORTED when it does not fit in device memory.
+ *           Not with eigenimages. */
+#define BIPP_SYNTH_STANDARD 0
+#define BIPP_SYNTH_NUFFT 1
 
 #define BIPP_MAX_EIGENIMAGES 64
 

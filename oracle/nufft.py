@@ -206,6 +206,14 @@ def level_visibilities(W, d, level_id, n_level):
     return Vl
 
 
+def error_scale(W, d, level_id, n_level, n_pix):
+    """Per level, ||V'_l||_F sqrt(n_pix): the l2 size of a type-3 sum over the
+    level's strengths with unrelated phases, the scale of the NUFFT's error
+    (squares add over steps: combine as sqrt(sum of squares))."""
+    Vl = level_visibilities(W, d, level_id, n_level)
+    return np.sqrt(np.sum(np.abs(Vl) ** 2, axis=(1, 2)) * n_pix)
+
+
 def baseline_points(st_xyz, wl, Vl):
     """Input points x_n = -2 pi / wl (p_p - p_q) of all ordered pairs and their
     per-level strengths c_n = V'_l,pq, so that I_l = Re sum_n c_n exp(i <r, x_n>)."""
@@ -232,3 +240,16 @@ def nufft_levels(pix, wl, bounds, n_eig, st_xyz, V, eps=None, filter="lsq", gram
     x, c = baseline_points(st_xyz, wl, Vl)
     f = type3_direct(x, c, pix) if eps is None else type3(x, c, pix, eps)
     return np.asfortranarray(f.real), mu, lev, W
+
+
+def nufft_levels_with_scale(pix, wl, bounds, n_eig, st_list, vis_list, eps=None, **kw):
+    """Level images summed over the steps, and the per-level error scale
+    sqrt(sum_t error_scale_t^2)."""
+    img, sc2 = None, 0.0
+    bounds = np.asarray(bounds, dtype=np.float64)
+    for p, V in zip(st_list, vis_list):
+        f, mu, lev, W = nufft_levels(pix, wl, bounds, n_eig, p, V, eps=eps, **kw)
+        d = mu if kw.get("filter", "lsq") == "lsq" else np.ones_like(mu)
+        sc2 = sc2 + error_scale(W, d, lev, bounds.shape[0], pix.shape[0]) ** 2
+        img = f if img is None else img + f
+    return img, np.sqrt(sc2)

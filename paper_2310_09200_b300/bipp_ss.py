@@ -36,6 +36,8 @@ BIPP_FILTER_LSQ, BIPP_FILTER_STD = 0, 1
 FILTERS = {"lsq": 0, "std": 1}
 BIPP_EIG_JACOBI64, BIPP_EIG_MIXED = 0, 1
 EIG_MODES = {"jacobi64": 0, "mixed": 1}
+BIPP_SYNTH_STANDARD, BIPP_SYNTH_NUFFT = 0, 1
+SYNTHESES = {"standard": 0, "nufft": 1}
 
 ERROR_NAMES = {
     -1: "BIPP_ERR_INVALID_ARG", -2: "BIPP_ERR_CUDA", -3: "BIPP_ERR_OUT_OF_MEMORY",
@@ -68,7 +70,7 @@ class bipp_ss_options(C.Structure):
         ("n_eig", C.c_int32), ("precision", C.c_int32), ("filter", C.c_int32), ("gram_identity", C.c_int32),
         ("max_jacobi_sweeps", C.c_int32), ("jacobi_tol", C.c_double), ("device", C.c_int32),
         ("eig_mode", C.c_int32), ("use_graph", C.c_int32), ("autotune", C.c_int32), ("eigenimages", C.c_int32),
-        ("reserved", C.c_int32 * 3),
+        ("synthesis", C.c_int32), ("nufft_eps", C.c_double), ("reserved", C.c_int32 * 4),
     ]
 
 
@@ -138,7 +140,7 @@ def _check(h, rc):
 def bipp_ss_default_options(**kw) -> bipp_ss_options:
     o = bipp_ss_options()
     load().bipp_ss_default_options(C.byref(o))
-    names = {"precision": PRECISIONS, "filter": FILTERS, "eig_mode": EIG_MODES}
+    names = {"precision": PRECISIONS, "filter": FILTERS, "eig_mode": EIG_MODES, "synthesis": SYNTHESES}
     for k, v in kw.items():
         if k in names and isinstance(v, str):
             v = names[k][v]

@@ -21,6 +21,7 @@
 
 #include "bipp_internal.cuh"
 #include "bipp_ss.h"
+#include "nufft.cuh"
 #include "synth_tc.cuh"
 
 using namespace bipp;
@@ -87,6 +88,15 @@ struct bipp_ss {
   TcWorkspace tc{};
   MixedWs mx{};
   int mixed_kp = 0;  // KP of the current batch when the mixed eigensolver runs, else 0
+  // NUFFT synthesis: pixel box, kernel, and the current batch's per-channel plans
+  NuPixBox nu_px{};
+  int nu_w = 0;
+  float nu_beta = 0.f;
+  NufftWs nu;
+  std::vector<NuPlan> nu_plans;
+  std::vector<int> nu_t0;  // first step of each channel group, plus n_t at the end
+  std::vector<double> nu_st;  // host copy of device station coordinates
+  int nu_launches = 0;
   // graph cache: the last geometry seen, and the captured graph of it
   GraphKey last_key;
   bool have_key = false;
@@ -232,6 +242,8 @@ extern "C" void bipp_ss_default_options(bipp_ss_options* opt) {
   opt->eig_mode = BIPP_EIG_JACOBI64;
   opt->use_graph = 1;
   opt->autotune = 1;
+  opt->synthesis = BIPP_SYNTH_STANDARD;
+  opt->nufft_eps = 1e-5;
 }
 
 extern "C" int bipp_ss_destroy(bipp_ss_t h) {
@@ -239,6 +251,7 @@ extern "C" int bipp_ss_destroy(bipp_ss_t h) {
   cudaSetDevice(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
   free_batch(h);
+  nu_free(&h->nu);
   if (h->d_pix) cudaFree(h->d_pix);
   if (h->d_pix_hl) cudaFree(h->d_pix_hl);
   if (h->d_img) cudaFree(h->d_img);
@@ -261,8 +274,17 @@ extern "C" int bipp_ss_create_channels(bipp_ss_t* out, int64_t n_pix, const doub
       return fail(nullptr, BIPP_ERR_INVALID_ARG, "wavelength of channel %d must be finite and > 0", c);
   bipp_ss_options o;
   if (opt) o = *opt; else bipp_ss_default_options(&o);
-  for (int i = 0; i < 3; ++i)
+  for (int i = 0; i < 4; ++i)
     if (o.reserved[i]) return fail(nullptr, BIPP_ERR_INVALID_ARG, "reserved option fields must be zero");
+  if (o.synthesis != BIPP_SYNTH_STANDARD && o.synthesis != BIPP_SYNTH_NUFFT)
+    return fail(nullptr, BIPP_ERR_INVALID_ARG, "unknown synthesis %d", o.synthesis);
+  int nu_w = 0;
+  float nu_beta = 0.f;
+  if (o.synthesis == BIPP_SYNTH_NUFFT) {
+    if (!nu_kernel_params(o.nufft_eps, &nu_w, &nu_beta))
+      return fail(nullptr, BIPP_ERR_INVALID_ARG, "nufft_eps must be in [1e-7, 0.1]");
+    if (o.eigenimages) return fail(nullptr, BIPP_ERR_UNSUPPORTED, "NUFFT synthesis makes level images, not eigenimages");
+  }
   if (o.eigenimages != 0 && o.eigenimages != 1)
     return fail(nullptr, BIPP_ERR_INVALID_ARG, "eigenimages must be 0 or 1");
   if (o.eigenimages) {
@@ -293,6 +315,9 @@ extern "C" int bipp_ss_create_channels(bipp_ss_t* out, int64_t n_pix, const doub
   h->n_level = n_level;
   h->n_chan = n_chan;
   h->wl.assign(wl, wl + n_chan);
+  h->nu_w = nu_w;
+  h->nu_beta = nu_beta;
+  if (o.synthesis == BIPP_SYNTH_NUFFT) h->nu_px = nu_pixel_box(pix_xyz, n_pix);
   if (o.device >= 0 && cudaSetDevice(o.device) != cudaSuccess) {
     delete h;
     return fail(nullptr, BIPP_ERR_CUDA, "cudaSetDevice(%d) failed", o.device);
@@ -407,10 +432,25 @@ static int enqueue_batch(bipp_ss* h, const Batch& b, const TcPlan& plan, cudaStr
   }
   CUDA_TRY(h, record(h->ev[2], s));
   launch_select(b, h->n_level, h->d_bounds, h->opt.filter, s);
-  const bool tc = h->opt.precision >= BIPP_PREC_SPLIT_BF16;
+  const bool tc = h->opt.synthesis == BIPP_SYNTH_STANDARD && h->opt.precision >= BIPP_PREC_SPLIT_BF16;
   if (tc && tc_enqueue_pack(b, plan, &h->tc, s)) return fail(h, BIPP_ERR_CUDA, "operand packing launch failed");
   CUDA_TRY(h, record(h->ev[3], s));
   Pixels px{h->n_pix, h->d_pix, h->d_pix_hl};
+  if (h->opt.synthesis == BIPP_SYNTH_NUFFT) {
+    h->nu_launches = 0;
+    for (size_t g = 0; g + 1 < h->nu_t0.size(); ++g) {
+      const int t0 = h->nu_t0[g], t1 = h->nu_t0[g + 1];
+      double* img = h->d_img + (size_t)h->h_chan[t0] * h->n_level * h->n_pix;
+      const int rc = nu_enqueue(b, t0, t1, h->nu_plans[g], &h->nu, h->d_pix, h->n_pix, h->n_level, img, s,
+                                &h->nu_launches);
+      if (rc == -1) return fail(h, BIPP_ERR_OUT_OF_MEMORY, "NUFFT grid allocation failed");
+      if (rc == -2) return fail(h, BIPP_ERR_CUDA, "NUFFT: cuFFT plan or execution failed");
+      if (rc) return fail(h, BIPP_ERR_CUDA, "NUFFT kernel launch failed");
+    }
+    CUDA_TRY(h, cudaGetLastError());
+    CUDA_TRY(h, record(h->ev[4], s));
+    return BIPP_OK;
+  }
   switch (h->opt.precision) {
     case BIPP_PREC_FP64: launch_synth_simt_f64(b, px, h->n_level, h->d_img, s); break;
     case BIPP_PREC_FP32: launch_synth_simt_f32(b, px, h->n_level, h->d_img, s); break;
@@ -423,9 +463,49 @@ static int enqueue_batch(bipp_ss* h, const Batch& b, const TcPlan& plan, cudaStr
   return BIPP_OK;
 }
 
+// NUFFT synthesis: one plan per channel group of the batch, from the host
+// station coordinates (copied back when the caller passed device memory).
+static int plan_nufft(bipp_ss* h, int n_t, int N, const std::vector<int>& nst_v, const std::vector<int>& chan_v,
+                      const double* h_st, const double* d_st, cudaStream_t s) {
+  if (!h_st) {
+    h->nu_st.resize((size_t)n_t * 3 * N);
+    CUDA_TRY(h, cudaMemcpyAsync(h->nu_st.data(), d_st, sizeof(double) * h->nu_st.size(), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+    h_st = h->nu_st.data();
+  }
+  h->nu_t0.clear();
+  h->nu_plans.clear();
+  std::vector<double> wl_t(n_t);
+  for (int t = 0; t < n_t; ++t) wl_t[t] = h->wl[chan_v[t]];
+  size_t need = 0;
+  for (int t = 0; t < n_t; ++t)
+    if (t == 0 || chan_v[t] != chan_v[t - 1]) h->nu_t0.push_back(t);
+  h->nu_t0.push_back(n_t);
+  for (size_t g = 0; g + 1 < h->nu_t0.size(); ++g) {
+    const NuPlan p = nu_plan(h->nu_px, h->nu_w, h->nu_beta, h_st, N, nst_v.data(), wl_t.data(), h->nu_t0[g],
+                             h->nu_t0[g + 1]);
+    for (int d = 0; d < 3; ++d)
+      if (p.M[d] > (1 << 28))
+        return fail(h, BIPP_ERR_UNSUPPORTED, "NUFFT grid dimension %d needs %d points", d, p.M[d]);
+    need = std::max(need, nu_grid_bytes(p, h->n_level));
+    h->nu_plans.push_back(p);
+  }
+  size_t free_b = 0, total_b = 0;
+  CUDA_TRY(h, cudaMemGetInfo(&free_b, &total_b));
+  const size_t have = (h->nu.F_cap + h->nu.G_cap) * sizeof(float2);
+  // grids plus the FFT's workspace (of the order of the fine grid) must fit
+  const NuPlan& p0 = h->nu_plans[0];
+  if (need + p0.cells2() * sizeof(float2) > free_b + have)
+    return fail(h, BIPP_ERR_UNSUPPORTED,
+                "NUFFT grids need %.1f GB (spread grid %d x %d x %d, FFT grid x8) but %.1f GB are free; "
+                "image a smaller field or fewer steps per batch",
+                (need + p0.cells2() * sizeof(float2)) / 1e9, p0.M[0], p0.M[1], p0.M[2], (free_b + have) / 1e9);
+  return BIPP_OK;
+}
+
 static int run_batch(bipp_ss* h, int n_t, int N, const std::vector<int>& nst_v, const std::vector<int>& neig_v,
                      const std::vector<int>& chan_v, int K, const double* d_st, const double2* d_vis,
-                     cudaStream_t s) {
+                     cudaStream_t s, const double* h_st) {
   (void)cudaGetLastError();  // errors of earlier, unrelated calls are not ours to report
   for (int t = 0; t < n_t; ++t) {
     h->h_nst[t] = nst_v[t];
@@ -441,7 +521,12 @@ static int run_batch(bipp_ss* h, int n_t, int N, const std::vector<int>& nst_v, 
     for (int t = 0; t < n_t; ++t) kp = std::max(kp, std::min(nst_v[t], neig_v[t] + 16));
     if (eig_mixed_fits(N, kp)) h->mixed_kp = kp;
   }
-  const bool tc = h->opt.precision >= BIPP_PREC_SPLIT_BF16;
+  const bool nufft = h->opt.synthesis == BIPP_SYNTH_NUFFT;
+  const bool tc = !nufft && h->opt.precision >= BIPP_PREC_SPLIT_BF16;
+  if (nufft) {
+    const int rc = plan_nufft(h, n_t, N, nst_v, chan_v, h_st, d_st, s);
+    if (rc) return rc;
+  }
   TcPlan plan;
   if (tc) {
     const int rc = tc_prepare(nst_v, neig_v, h->opt.precision == BIPP_PREC_SPLIT_FP16, &h->tc, &plan);
@@ -452,7 +537,11 @@ static int run_batch(bipp_ss* h, int n_t, int N, const std::vector<int>& nst_v, 
   key.T = n_t; key.N = N; key.K = K; key.st = d_st; key.vis = d_vis; key.stream = s;
   key.nst = nst_v; key.neig = neig_v; key.chan = chan_v; key.n_stages = tc ? plan.n_stages : 0;
 
-  if (tc && h->opt.autotune && !plan.tuned) {
+  if (nufft) {
+    // host-planned grids and cuFFT: enqueued directly, not captured
+    const int rc = enqueue_batch(h, b, plan, s);
+    if (rc) return rc;
+  } else if (tc && h->opt.autotune && !plan.tuned) {
     // first batch of this accumulator width: run up to the packing, tune, then synthesise
     Batch bb = b;
     int rc = enqueue_batch(h, bb, plan, s);  // ... runs the synthesis with the default plan too
@@ -512,7 +601,7 @@ static int run_batch(bipp_ss* h, int n_t, int N, const std::vector<int>& nst_v, 
   for (int t = 0; t < n_t; ++t) h->timings[4] += sweeps[t];
   // gram, [cholesky], trinv, [2 reduction GEMMs], hermitize, jacobi, select, [scale], [pack], synthesis
   h->timings[5] = (h->opt.gram_identity ? 6 : 9) + (tc ? 1 + (h->opt.precision == BIPP_PREC_SPLIT_FP16) : 0) +
-                  (h->mixed_kp > 0 ? kMixedLaunches - 1 : 0);
+                  (h->mixed_kp > 0 ? kMixedLaunches - 1 : 0) + (nufft ? h->nu_launches - 1 : 0);
   for (int t = 0; t < n_t; ++t) {
     if (status[t] & kStatusNotPD)
       return fail(h, BIPP_ERR_GRAM_NOT_PD, "step %d: Gram matrix is not positive definite (Cholesky pivot <= 0 or NaN)", t);
@@ -552,12 +641,13 @@ static int collect_common(bipp_ss_t h, int32_t n_t, int32_t n_st_max, const int3
   if (rc) return rc;
   if (on_device) {
     cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
-    return run_batch(h, n_t, n_st_max, nst_v, neig_v, chan_v, K, st_xyz, reinterpret_cast<const double2*>(vis), s);
+    return run_batch(h, n_t, n_st_max, nst_v, neig_v, chan_v, K, st_xyz, reinterpret_cast<const double2*>(vis), s,
+                     nullptr);
   }
   const size_t N = (size_t)n_st_max;
   CUDA_TRY(h, cudaMemcpyAsync(h->d_st, st_xyz, sizeof(double) * 3 * N * n_t, cudaMemcpyHostToDevice, h->stream));
   CUDA_TRY(h, cudaMemcpyAsync(h->d_vis, vis, sizeof(double2) * N * N * n_t, cudaMemcpyHostToDevice, h->stream));
-  return run_batch(h, n_t, n_st_max, nst_v, neig_v, chan_v, K, h->d_st, h->d_vis, h->stream);
+  return run_batch(h, n_t, n_st_max, nst_v, neig_v, chan_v, K, h->d_st, h->d_vis, h->stream, st_xyz);
 }
 
 extern "C" int bipp_ss_collect_batch(bipp_ss_t h, int32_t n_t, int32_t n_st_max, const int32_t* n_st,

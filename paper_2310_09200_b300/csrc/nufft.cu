@@ -1,0 +1,596 @@
+// nufft.cu — NUFFT synthesis (Sec. 2.5, Sec. 3.4, Algorithm 3) on B300.
+//
+// Per channel of a batch (steps [t0, t1) with one wavelength), one type-3
+// NUFFT per level maps the baselines of all steps to the pixels:
+//
+//   1. k_nu_spread: one thread per station pair p < q of a step. It forms the
+//      pair's level strengths 2 V'_l,pq = 2 sum_{e in l} d_e a_pe conj(a_qe)
+//      (eigenvectors staged through shared memory), orients the pair so that
+//      the folded coordinate is >= 0 (the (q, p) term is the conjugate one, so
+//      Re of the sum is unchanged), pre-phases the strengths by exp(2 pi i <D, x>)
+//      and spreads them onto the grid y_m = (m - M/2) h with the
+//      exponential-of-semicircle kernel, w^3 cells x all levels, with vector
+//      float atomics. Coordinates and phases are reduced in FP64; kernel
+//      weights, strengths and the grid are FP32.
+//   2. k_nu_const: the p = q terms (zero baseline): sum_t sum_{e in l} d_e |a_e|^2,
+//      a constant per level.
+//   3. per level: k_nu_pad divides each grid mode by the second kernel's
+//      transform and places it into the twice finer grid (zeros elsewhere);
+//      cuFFT's backward C2C transform evaluates the Fourier series there;
+//      k_nu_interp interpolates it at t = (s - D) h with the kernel, applies
+//      the trapezoid factor, the diagonal correction 1 / psi_hat(s - D) and
+//      the post-phase exp(2 pi i <s - D, C>), and adds Re + the constant to
+//      the level image.
+//
+// The kernel and grid rules are those of the exponential-of-semicircle NUFFT
+// (Barnett, Magland and af Klinteberg, SIAM J. Sci. Comput. 41, 2019):
+// w = ceil(log10(1/eps)) + 1, beta = 2.30 w, upsampling 2; spacing
+// h = pi / (2 S) so the spread function's spectrum aliases only beyond the
+// kernel's pass band, and M = 8 X S + w + 2 points (X, S half-widths in cycles
+// and direction units) rounded up to an even 2^a 3^b 5^c.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "nufft.cuh"
+
+namespace bipp {
+
+namespace {
+
+constexpr double kSigma = 2.0;
+
+__device__ __forceinline__ float es_w(float z, float beta) {
+  const float q = 1.0f - z * z;
+  return q >= 0.0f ? expf(beta * (sqrtf(q) - 1.0f)) : 0.0f;
+}
+
+// Least even integer >= n with prime factors 2, 3, 5 only.
+long long next_smooth(long long n) {
+  for (long long m = std::max(2LL, n);; ++m) {
+    if (m & 1) continue;
+    long long r = m;
+    for (int p : {2, 3, 5})
+      while (r % p == 0) r /= p;
+    if (r == 1) return m;
+  }
+}
+
+// Gauss-Legendre rule of 2 kNuGL points on [-1, 1] (Newton's method on the
+// Legendre recurrence); the kNuGL positive nodes and their weights.
+void gauss_legendre_half(double* z, double* wq) {
+  const int n = 2 * kNuGL;
+  for (int i = 0; i < kNuGL; ++i) {
+    double x = cos(M_PI * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = x;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (x * p1 - p0) / (x * x - 1.0);
+      const double dx = p1 / dp;
+      x -= dx;
+      if (fabs(dx) < 1e-16) break;
+    }
+    z[i] = x;
+    wq[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+  }
+}
+
+double phi_host(double z, double beta) {
+  const double q = 1.0 - z * z;
+  return q >= 0.0 ? exp(beta * (sqrt(q) - 1.0)) : 0.0;
+}
+
+// psi_hat(xi) = alpha * int_{-1}^{1} phi(z) cos(alpha xi z) dz for the kernel psi(y) = phi(y / alpha).
+double es_ft_host(double xi, double alpha, double beta, const double* z, const double* wq) {
+  double s = 0.0;
+  for (int q = 0; q < kNuGL; ++q) s += wq[q] * phi_host(z[q], beta) * cos(alpha * xi * z[q]);
+  return 2.0 * alpha * s;
+}
+
+struct SpreadArgs {
+  int M[3];
+  double C[3], invH[3], D[3];
+  int fold, w, L, Lp;
+  float beta;
+};
+
+// Upper-triangle tile (pb <= qb) of linear index r, tiles ordered by qb.
+__device__ __forceinline__ void tri_tile(int r, int* pb, int* qb) {
+  int q = (int)((sqrt(8.0 * r + 1.0) - 1.0) * 0.5);
+  while (q * (q + 1) / 2 > r) --q;
+  while ((q + 1) * (q + 2) / 2 <= r) ++q;
+  *qb = q;
+  *pb = r - q * (q + 1) / 2;
+}
+
+constexpr int kTile = 16;
+constexpr int kEChunk = 64;
+
+template <int MAXL>
+__global__ void __launch_bounds__(kTile* kTile) k_nu_spread(Batch b, int t0, SpreadArgs a, float2* __restrict__ F) {
+  const int t = t0 + blockIdx.z;
+  const int n = b.nst[t];
+  const int K = b.nkept[t];
+  if (K <= 0) return;  // failed step: nothing kept (the batch flag stops the image update)
+  int pb, qb;
+  tri_tile(blockIdx.x, &pb, &qb);
+  if (qb * kTile >= n) return;
+  const int tx = threadIdx.x & (kTile - 1), ty = threadIdx.x / kTile;
+  const int p = pb * kTile + ty, q = qb * kTile + tx;
+  const int N = b.n_max, KM = b.k_max;
+  __shared__ float2 sWp[kEChunk][kTile], sWq[kEChunk][kTile];
+  __shared__ float sD[kEChunk];
+  __shared__ int sL[kEChunk];
+  float2 acc[MAXL];
+#pragma unroll
+  for (int l = 0; l < MAXL; ++l) acc[l] = make_float2(0.f, 0.f);
+  for (int e0 = 0; e0 < K; e0 += kEChunk) {
+    for (int i = threadIdx.x; i < kEChunk * kTile; i += kTile * kTile) {
+      const int e = e0 + i / kTile, j = i % kTile;
+      const int ip = pb * kTile + j, iq = qb * kTile + j;
+      double2 vp = make_double2(0.0, 0.0), vq = vp;
+      if (e < K && ip < n) vp = b.W64[((size_t)t * KM + e) * N + ip];
+      if (e < K && iq < n) vq = b.W64[((size_t)t * KM + e) * N + iq];
+      sWp[i / kTile][j] = make_float2((float)vp.x, (float)vp.y);
+      sWq[i / kTile][j] = make_float2((float)vq.x, (float)vq.y);
+    }
+    if (threadIdx.x < kEChunk) {
+      const int e = e0 + threadIdx.x;
+      sD[threadIdx.x] = e < K ? (float)b.wt[(size_t)t * KM + e] : 0.f;
+      sL[threadIdx.x] = e < K ? b.level[(size_t)t * KM + e] : -1;
+    }
+    __syncthreads();
+    const int ne = min(kEChunk, K - e0);
+    for (int e = 0; e < ne; ++e) {
+      const float2 wp = sWp[e][ty], wq = sWq[e][tx];
+      const float pr = fmaf(wp.x, wq.x, wp.y * wq.y), pi = fmaf(wp.y, wq.x, -wp.x * wq.y);
+      const int lv = sL[e];
+      const float dd = sD[e];
+#pragma unroll
+      for (int l = 0; l < MAXL; ++l) {
+        const float m = (lv == l) ? dd : 0.f;
+        acc[l].x = fmaf(m, pr, acc[l].x);
+        acc[l].y = fmaf(m, pi, acc[l].y);
+      }
+    }
+    __syncthreads();
+  }
+  if (!(p < q && q < n)) return;
+
+  const double* st = b.st + (size_t)t * 3 * N;
+  const double iwl = 1.0 / b.wl[t];
+  double x[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) x[d] = -(st[(size_t)d * N + p] - st[(size_t)d * N + q]) * iwl;
+  float cs = 1.f;
+  const double xf = a.fold == 0 ? x[0] : (a.fold == 1 ? x[1] : x[2]);
+  if (xf < 0.0) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) x[d] = -x[d];
+    cs = -1.f;  // conjugate strengths
+  }
+  // pre-phase exp(2 pi i <D, x>), reduced to [-1/2, 1/2] cycles in FP64
+  const double ph = a.D[0] * x[0] + a.D[1] * x[1] + a.D[2] * x[2];
+  float sn, cn;
+  sincospif(2.0f * (float)(ph - rint(ph)), &sn, &cn);
+  float2 c[MAXL];
+#pragma unroll
+  for (int l = 0; l < MAXL; ++l) {
+    const float ar = 2.f * acc[l].x, ai = 2.f * cs * acc[l].y;
+    c[l] = make_float2(ar * cn - ai * sn, ar * sn + ai * cn);
+  }
+  int m0[3];
+  float fr[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double g = (x[d] - a.C[d]) * a.invH[d] + 0.5 * a.M[d];
+    int m = (int)ceil(g - 0.5 * a.w);
+    m = min(max(m, 0), a.M[d] - a.w);  // never outside the grid (the plan's margin makes this a no-op)
+    m0[d] = m;
+    fr[d] = (float)((double)m - g);
+  }
+  const float tw = 2.0f / (float)a.w;
+  float k0[kNuMaxW];
+#pragma unroll
+  for (int j = 0; j < kNuMaxW; ++j) k0[j] = (j < a.w) ? es_w((fr[0] + j) * tw, a.beta) : 0.f;
+  for (int j2 = 0; j2 < a.w; ++j2) {
+    const float k2 = es_w((fr[2] + j2) * tw, a.beta);
+    for (int j1 = 0; j1 < a.w; ++j1) {
+      const float k12 = k2 * es_w((fr[1] + j1) * tw, a.beta);
+      const size_t row = ((size_t)(m0[2] + j2) * a.M[1] + (m0[1] + j1)) * a.M[0] + m0[0];
+#pragma unroll
+      for (int j0 = 0; j0 < kNuMaxW; ++j0) {
+        if (j0 < a.w) {
+          const float wt = k12 * k0[j0];
+          float2* cell = F + (row + j0) * a.Lp;
+          if (MAXL == 1) {
+            atomicAdd(cell, make_float2(wt * c[0].x, wt * c[0].y));
+          } else {
+#pragma unroll
+            for (int lp = 0; lp < (MAXL + 1) / 2; ++lp)
+              if (2 * lp < a.L)
+                atomicAdd(reinterpret_cast<float4*>(cell) + lp,
+                          make_float4(wt * c[2 * lp].x, wt * c[2 * lp].y, wt * c[min(2 * lp + 1, MAXL - 1)].x,
+                                      wt * c[min(2 * lp + 1, MAXL - 1)].y));
+          }
+        }
+      }
+    }
+  }
+}
+
+// Zero-baseline terms: cst[l] += sum_{e in l} d_e sum_p |a_pe|^2 for each step.
+__global__ void k_nu_const(Batch b, int t0, double* cst) {
+  const int t = t0 + blockIdx.x;
+  const int n = b.nst[t], K = b.nkept[t], N = b.n_max, KM = b.k_max;
+  __shared__ double red[256];
+  for (int e = 0; e < K; ++e) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double2 v = b.W64[((size_t)t * KM + e) * N + i];
+      s += v.x * v.x + v.y * v.y;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      const int l = b.level[(size_t)t * KM + e];
+      if (l >= 0 && l < kMaxLevels) atomicAdd(cst + l, b.wt[(size_t)t * KM + e] * red[0]);
+    }
+    __syncthreads();
+  }
+}
+
+// Per pixel 1 / prod_d psi_hat_d(s_d - D_d), psi_hat_d(xi) = alpha_d phi_hat(alpha_d xi), alpha_d = pi w Hc_d.
+__global__ void k_nu_corr(const double* __restrict__ pix, int64_t n, double D0, double D1, double D2, float al0,
+                          float al1, float al2, const float* __restrict__ gl, float* __restrict__ corr) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double D[3] = {D0, D1, D2};
+  const float al[3] = {al0, al1, al2};
+  float prod = 1.f;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float k = al[d] * (float)(pix[(size_t)d * n + j] - D[d]);
+    float s = 0.f;
+#pragma unroll 8
+    for (int q = 0; q < kNuGL; ++q) s = fmaf(gl[kNuGL + q], cosf(k * gl[q]), s);
+    prod *= 2.f * al[d] * s;
+  }
+  corr[j] = 1.f / prod;
+}
+
+struct GridArgs {
+  int M[3], N2[3], Lp, l;
+};
+
+// Fine grid G[j] = F[m(k)] / prod_d psi2_hat_d(k_d) for modes |k_d| < M_d / 2 (k = j or j - N2), else 0.
+__global__ void k_nu_pad(const float2* __restrict__ F, GridArgs a, const float* __restrict__ inv,
+                         float2* __restrict__ G) {
+  const size_t total = (size_t)a.N2[0] * a.N2[1] * a.N2[2];
+  const float* inv0 = inv;
+  const float* inv1 = inv + a.M[0];
+  const float* inv2 = inv1 + a.M[1];
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int j0 = (int)(idx % a.N2[0]);
+    const size_t r = idx / a.N2[0];
+    const int j1 = (int)(r % a.N2[1]);
+    const int j2 = (int)(r / a.N2[1]);
+    const int k0 = j0 < a.N2[0] / 2 ? j0 : j0 - a.N2[0];
+    const int k1 = j1 < a.N2[1] / 2 ? j1 : j1 - a.N2[1];
+    const int k2 = j2 < a.N2[2] / 2 ? j2 : j2 - a.N2[2];
+    float2 v = make_float2(0.f, 0.f);
+    const int h0 = a.M[0] / 2, h1 = a.M[1] / 2, h2 = a.M[2] / 2;
+    if (k0 >= -h0 && k0 < h0 && k1 >= -h1 && k1 < h1 && k2 >= -h2 && k2 < h2) {
+      const int m0 = k0 + h0, m1 = k1 + h1, m2 = k2 + h2;
+      const float2 f = F[(((size_t)m2 * a.M[1] + m1) * a.M[0] + m0) * a.Lp + a.l];
+      const float sc = inv0[m0] * inv1[m1] * inv2[m2];
+      v = make_float2(f.x * sc, f.y * sc);
+    }
+    G[idx] = v;
+  }
+}
+
+struct InterpArgs {
+  int N2[3], w;
+  float beta;
+  double D[3], C[3], HN[3];  // HN = Hc * N2: target offset -> fine-grid coordinate
+  double scale;              // trapezoid factor prod_d (2 pi Hc_d)(2 pi / N2_d)
+};
+
+__global__ void k_nu_interp(const double* __restrict__ pix, int64_t n, InterpArgs a, const float2* __restrict__ G,
+                            const float* __restrict__ corr, const double* __restrict__ cst, int l,
+                            const int* __restrict__ flag, double* __restrict__ img) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n || *flag) return;
+  double sp[3];
+  int m0[3];
+  float fr[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    sp[d] = pix[(size_t)d * n + j] - a.D[d];
+    const double tg = sp[d] * a.HN[d];
+    const int m = (int)ceil(tg - 0.5 * a.w);
+    fr[d] = (float)((double)m - tg);
+    int mm = m % a.N2[d];
+    if (mm < 0) mm += a.N2[d];
+    m0[d] = mm;
+  }
+  const float tw = 2.0f / (float)a.w;
+  float k0[kNuMaxW];
+  int i0[kNuMaxW];
+#pragma unroll
+  for (int q = 0; q < kNuMaxW; ++q) {
+    k0[q] = (q < a.w) ? es_w((fr[0] + q) * tw, a.beta) : 0.f;
+    int ii = m0[0] + q;
+    if (ii >= a.N2[0]) ii -= a.N2[0];
+    i0[q] = ii;
+  }
+  float sr = 0.f, si = 0.f;
+  for (int j2 = 0; j2 < a.w; ++j2) {
+    const float k2 = es_w((fr[2] + j2) * tw, a.beta);
+    int i2 = m0[2] + j2;
+    if (i2 >= a.N2[2]) i2 -= a.N2[2];
+    for (int j1 = 0; j1 < a.w; ++j1) {
+      const float k12 = k2 * es_w((fr[1] + j1) * tw, a.beta);
+      int i1 = m0[1] + j1;
+      if (i1 >= a.N2[1]) i1 -= a.N2[1];
+      const float2* row = G + ((size_t)i2 * a.N2[1] + i1) * a.N2[0];
+      float rr = 0.f, ri = 0.f;
+#pragma unroll
+      for (int q = 0; q < kNuMaxW; ++q) {
+        if (q < a.w) {
+          const float2 g = __ldg(row + i0[q]);
+          rr = fmaf(k0[q], g.x, rr);
+          ri = fmaf(k0[q], g.y, ri);
+        }
+      }
+      sr = fmaf(k12, rr, sr);
+      si = fmaf(k12, ri, si);
+    }
+  }
+  // post-phase exp(2 pi i <s - D, C>), reduced in FP64
+  const double ph = sp[0] * a.C[0] + sp[1] * a.C[1] + sp[2] * a.C[2];
+  float sn, cn;
+  sincospif(2.0f * (float)(ph - rint(ph)), &sn, &cn);
+  const double re = (double)(sr * cn - si * sn) * (double)corr[j] * a.scale;
+  img[(size_t)l * n + j] += re + cst[l];
+}
+
+template <typename F>
+void dispatch_levels(int L, F&& f) {
+  if (L <= 1) f(std::integral_constant<int, 1>{});
+  else if (L <= 2) f(std::integral_constant<int, 2>{});
+  else if (L <= 4) f(std::integral_constant<int, 4>{});
+  else if (L <= 8) f(std::integral_constant<int, 8>{});
+  else f(std::integral_constant<int, 16>{});
+}
+
+template <typename T>
+bool grow(T** p, size_t* cap, size_t need) {
+  if (need <= *cap && *p) return true;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  if (cudaMalloc((void**)p, sizeof(T) * std::max<size_t>(need, 1)) != cudaSuccess) {
+    *p = nullptr;
+    return false;
+  }
+  *cap = need;
+  return true;
+}
+
+}  // namespace
+
+bool nu_kernel_params(double eps, int* w, float* beta) {
+  if (!(eps >= 1e-7 && eps <= 0.1)) return false;
+  int ww = (int)ceil(log10(1.0 / eps) - 1e-12) + 1;
+  ww = std::min(std::max(ww, 2), kNuMaxW);
+  *w = ww;
+  *beta = 2.30f * (float)ww;
+  return true;
+}
+
+NuPixBox nu_pixel_box(const double* pix, int64_t n) {
+  NuPixBox b;
+  for (int d = 0; d < 3; ++d) {
+    double lo = pix[(size_t)d * n], hi = lo;
+    for (int64_t j = 1; j < n; ++j) {
+      lo = std::min(lo, pix[(size_t)d * n + j]);
+      hi = std::max(hi, pix[(size_t)d * n + j]);
+    }
+    b.D[d] = 0.5 * (lo + hi);
+    b.S[d] = 0.5 * (hi - lo);
+  }
+  return b;
+}
+
+NuPlan nu_plan(const NuPixBox& px, int w, float beta, const double* h_st, int N, const int* nst, const double* wl,
+               int t0, int t1) {
+  NuPlan p;
+  p.w = w;
+  p.beta = beta;
+  double R[3] = {0, 0, 0};  // largest baseline component per dimension [cycles]
+  for (int t = t0; t < t1; ++t)
+    for (int d = 0; d < 3; ++d) {
+      const double* c = h_st + ((size_t)t * 3 + d) * N;
+      double lo = c[0], hi = c[0];
+      for (int i = 1; i < nst[t]; ++i) {
+        lo = std::min(lo, c[i]);
+        hi = std::max(hi, c[i]);
+      }
+      R[d] = std::max(R[d], (hi - lo) / wl[t]);
+    }
+  int fold = 0;
+  for (int d = 1; d < 3; ++d)
+    if (R[d] * px.S[d] > R[fold] * px.S[fold]) fold = d;
+  p.fold = fold;
+  for (int d = 0; d < 3; ++d) {
+    const double lo = (d == fold) ? 0.0 : -R[d], hi = R[d];
+    const double X = 0.5 * (hi - lo), S = px.S[d];
+    p.C[d] = 0.5 * (hi + lo);
+    p.D[d] = px.D[d];
+    const long long need = (long long)ceil(4.0 * kSigma * X * S * (1.0 + 1e-12)) + w + 2;
+    p.M[d] = (int)next_smooth(std::max<long long>(2 * w, need));
+    if (S > 0.0)
+      p.Hc[d] = 1.0 / (2.0 * kSigma * S);
+    else if (X > 0.0)
+      p.Hc[d] = 2.0 * X / (p.M[d] - w - 2);
+    else
+      p.Hc[d] = 1.0 / (2.0 * M_PI);
+    p.N2[d] = 2 * p.M[d];
+  }
+  return p;
+}
+
+size_t nu_grid_bytes(const NuPlan& p, int n_level) {
+  const int Lp = n_level == 1 ? 1 : n_level + (n_level & 1);
+  return p.cells() * Lp * sizeof(float2) + p.cells2() * sizeof(float2);
+}
+
+int nu_enqueue(const Batch& b, int t0, int t1, const NuPlan& p, NufftWs* w, const double* d_pix, int64_t n_pix,
+               int n_level, double* img, cudaStream_t s, int* launches) {
+  const int Lp = n_level == 1 ? 1 : n_level + (n_level & 1);
+  int nl = 0;
+  if (!grow(&w->F, &w->F_cap, p.cells() * Lp)) return -1;
+  if (!grow(&w->G, &w->G_cap, p.cells2())) return -1;
+  if (!grow(&w->inv, &w->inv_cap, (size_t)p.M[0] + p.M[1] + p.M[2])) return -1;
+  size_t corr_cap = (size_t)w->corr_cap;
+  if (!grow(&w->corr, &corr_cap, (size_t)n_pix)) return -1;
+  if ((int64_t)corr_cap != w->corr_cap) w->corr_valid = false;
+  w->corr_cap = (int64_t)corr_cap;
+  if (!w->cst && cudaMalloc(&w->cst, sizeof(double) * kMaxLevels) != cudaSuccess) return -1;
+
+  double z[kNuGL], wq[kNuGL];
+  gauss_legendre_half(z, wq);
+  if (!w->gl || w->gl_w != p.w || w->gl_beta != p.beta) {
+    if (!w->gl && cudaMalloc(&w->gl, sizeof(float) * 2 * kNuGL) != cudaSuccess) return -1;
+    float hg[2 * kNuGL];
+    for (int q = 0; q < kNuGL; ++q) {
+      hg[q] = (float)z[q];
+      hg[kNuGL + q] = (float)(wq[q] * phi_host(z[q], p.beta));
+    }
+    if (cudaMemcpy(w->gl, hg, sizeof(hg), cudaMemcpyHostToDevice) != cudaSuccess) return -1;
+    w->gl_w = p.w;
+    w->gl_beta = p.beta;
+    w->corr_valid = false;
+  }
+  // per-pixel correction: depends on the pixels, the kernel and the spacing only
+  bool same = w->corr_valid && w->corr_w == p.w;
+  for (int d = 0; d < 3; ++d) same = same && w->corr_Hc[d] == p.Hc[d] && w->corr_D[d] == p.D[d];
+  if (!same) {
+    const float al[3] = {(float)(M_PI * p.w * p.Hc[0]), (float)(M_PI * p.w * p.Hc[1]), (float)(M_PI * p.w * p.Hc[2])};
+    k_nu_corr<<<(unsigned)((n_pix + 255) / 256), 256, 0, s>>>(d_pix, n_pix, p.D[0], p.D[1], p.D[2], al[0], al[1], al[2],
+                                                               w->gl, w->corr);
+    ++nl;
+    w->corr_valid = true;
+    w->corr_w = p.w;
+    for (int d = 0; d < 3; ++d) {
+      w->corr_Hc[d] = p.Hc[d];
+      w->corr_D[d] = p.D[d];
+    }
+  }
+  // 1 / psi2_hat per mode, alpha2 = pi w / N2
+  w->h_inv.resize((size_t)p.M[0] + p.M[1] + p.M[2]);
+  size_t o = 0;
+  for (int d = 0; d < 3; ++d) {
+    const double al2 = M_PI * p.w / p.N2[d];
+    for (int m = 0; m < p.M[d]; ++m) w->h_inv[o++] = (float)(1.0 / es_ft_host(m - p.M[d] / 2, al2, p.beta, z, wq));
+  }
+  if (cudaMemcpyAsync(w->inv, w->h_inv.data(), sizeof(float) * o, cudaMemcpyHostToDevice, s) != cudaSuccess) return -1;
+  if (cudaMemsetAsync(w->F, 0, sizeof(float2) * p.cells() * Lp, s) != cudaSuccess) return -1;
+  if (cudaMemsetAsync(w->cst, 0, sizeof(double) * kMaxLevels, s) != cudaSuccess) return -1;
+
+  const int T = t1 - t0;
+  k_nu_const<<<T, 256, 0, s>>>(b, t0, w->cst);
+  ++nl;
+  SpreadArgs sa;
+  for (int d = 0; d < 3; ++d) {
+    sa.M[d] = p.M[d];
+    sa.C[d] = p.C[d];
+    sa.invH[d] = 1.0 / p.Hc[d];
+    sa.D[d] = p.D[d];
+  }
+  sa.fold = p.fold;
+  sa.w = p.w;
+  sa.L = n_level;
+  sa.Lp = Lp;
+  sa.beta = p.beta;
+  const int nb = (b.n_max + kTile - 1) / kTile;
+  const dim3 grid(nb * (nb + 1) / 2, 1, T);
+  dispatch_levels(n_level, [&](auto ML) {
+    constexpr int L = decltype(ML)::value;
+    k_nu_spread<L><<<grid, kTile * kTile, 0, s>>>(b, t0, sa, w->F);
+  });
+  ++nl;
+  if (cudaGetLastError() != cudaSuccess) return -3;
+
+  if (!w->have_fft || w->fft_n[0] != p.N2[0] || w->fft_n[1] != p.N2[1] || w->fft_n[2] != p.N2[2]) {
+    if (w->have_fft) {
+      if (cudaStreamSynchronize(s) != cudaSuccess) return -2;  // the old plan may still be executing
+      cufftDestroy(w->fft);
+    }
+    w->have_fft = false;
+    if (cufftCreate(&w->fft) != CUFFT_SUCCESS) return -2;
+    long long dims[3] = {p.N2[2], p.N2[1], p.N2[0]};
+    size_t ws = 0;
+    if (cufftMakePlanMany64(w->fft, 3, dims, nullptr, 1, 0, nullptr, 1, 0, CUFFT_C2C, 1, &ws) != CUFFT_SUCCESS) {
+      cufftDestroy(w->fft);
+      return -2;
+    }
+    w->have_fft = true;
+    for (int d = 0; d < 3; ++d) w->fft_n[d] = p.N2[d];
+  }
+  if (cufftSetStream(w->fft, s) != CUFFT_SUCCESS) return -2;
+
+  GridArgs ga;
+  InterpArgs ia;
+  double scale = 1.0;
+  for (int d = 0; d < 3; ++d) {
+    ga.M[d] = p.M[d];
+    ga.N2[d] = p.N2[d];
+    ia.N2[d] = p.N2[d];
+    ia.D[d] = p.D[d];
+    ia.C[d] = p.C[d];
+    ia.HN[d] = p.Hc[d] * p.N2[d];
+    scale *= (2.0 * M_PI * p.Hc[d]) * (2.0 * M_PI / p.N2[d]);
+  }
+  ia.w = p.w;
+  ia.beta = p.beta;
+  ia.scale = scale;
+  ga.Lp = Lp;
+  int sms = 148, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const unsigned pad_grid = (unsigned)std::min<size_t>((p.cells2() + 255) / 256, (size_t)sms * 16);
+  const unsigned pix_grid = (unsigned)((n_pix + 255) / 256);
+  for (int l = 0; l < n_level; ++l) {
+    ga.l = l;
+    k_nu_pad<<<pad_grid, 256, 0, s>>>(w->F, ga, w->inv, w->G);
+    if (cufftExecC2C(w->fft, (cufftComplex*)w->G, (cufftComplex*)w->G, CUFFT_INVERSE) != CUFFT_SUCCESS) return -2;
+    k_nu_interp<<<pix_grid, 256, 0, s>>>(d_pix, n_pix, ia, w->G, w->corr, w->cst, l, b.flag, img);
+    nl += 2;
+  }
+  if (cudaGetLastError() != cudaSuccess) return -3;
+  if (launches) *launches += nl;
+  return 0;
+}
+
+void nu_free(NufftWs* w) {
+  if (w->have_fft) cufftDestroy(w->fft);
+  void* ptrs[] = {w->F, w->G, w->inv, w->corr, w->cst, w->gl};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  *w = NufftWs{};
+}
+
+}  // namespace bipp

@@ -1,0 +1,88 @@
+// nufft.cuh — NUFFT synthesis (Sec. 2.5 "NUFFT Image Synthesis", Sec. 3.4
+// "NUFFT Synthesis", Algorithm 3): internal interface of nufft.cu.
+//
+// Per channel and level, the level's Gram-corrected visibilities
+// V'_l = sum_{e in l} d_e a_e a_e^H of every step of the batch are summed over
+// all baselines with one type-3 NUFFT:
+//   I_l(r) += sum_t sum_{p,q} V'_l,pq(t) exp(2 pi i <r, x_pq(t)>),  x_pq = -(p_p - p_q) / wl  [cycles]
+// Coordinates are in cycles: the phase of input point x and target s is 2 pi <s, x>.
+#pragma once
+
+#include <cufft.h>
+
+#include <vector>
+
+#include "bipp_internal.cuh"
+
+namespace bipp {
+
+constexpr int kNuMaxW = 8;  // kernel width cap: tolerances down to 1e-7
+constexpr int kNuGL = 32;   // Gauss-Legendre nodes on (0, 1) for the kernel's Fourier transform
+
+// Target (pixel) box of a handle: centre D and half-width S per dimension.
+struct NuPixBox {
+  double D[3], S[3];
+};
+
+// Geometry of one type-3 transform.
+struct NuPlan {
+  int w = 0;        // kernel width (grid points)
+  float beta = 0;   // kernel shape, 2.30 w
+  int fold = 0;     // dimension on which every point is oriented to x >= 0 (Hermitian symmetry)
+  int M[3] = {};    // spread-grid points per dimension (dimension 0 fastest in memory)
+  int N2[3] = {};   // type-2 fine grid, 2 M
+  double C[3] = {}; // centre of the input points [cycles]
+  double Hc[3] = {};// spread-grid spacing [cycles]
+  double D[3] = {}; // centre of the targets
+  size_t cells() const { return (size_t)M[0] * M[1] * M[2]; }
+  size_t cells2() const { return (size_t)N2[0] * N2[1] * N2[2]; }
+};
+
+struct NufftWs {
+  float2* F = nullptr;   // spread grid [M2][M1][M0][Lp] (Lp levels, even unless 1)
+  size_t F_cap = 0;      // float2 elements
+  float2* G = nullptr;   // fine grid [N2_2][N2_1][N2_0]
+  size_t G_cap = 0;
+  float* inv = nullptr;  // 1 / (second kernel's transform) per mode, M0 + M1 + M2
+  size_t inv_cap = 0;
+  float* corr = nullptr; // per pixel 1 / prod_d psi_hat_d(s_d - D_d)
+  int64_t corr_cap = 0;
+  double* cst = nullptr; // [kMaxLevels] zero-baseline (p = q) terms of the current channel
+  float* gl = nullptr;   // [2][kNuGL]: Gauss-Legendre nodes z_q and weights w_q phi(z_q) on (0, 1)
+  int gl_w = 0;          // kernel width gl was made for
+  float gl_beta = 0;
+  // the per-pixel correction in corr is valid for this kernel and spacing
+  int corr_w = 0;
+  double corr_Hc[3] = {};
+  double corr_D[3] = {};
+  bool corr_valid = false;
+  cufftHandle fft = 0;
+  bool have_fft = false;
+  int fft_n[3] = {};
+  std::vector<float> h_inv;
+};
+
+// Kernel parameters for tolerance eps in [1e-7, 0.1]; false outside.
+bool nu_kernel_params(double eps, int* w, float* beta);
+
+// Target box of n pixels (host, [3][n] column-major).
+NuPixBox nu_pixel_box(const double* pix, int64_t n);
+
+// Plan of the steps [t0, t1) of a batch: host station coordinates h_st
+// ([T][3][N] column-major per step), per-step station counts and wavelengths.
+NuPlan nu_plan(const NuPixBox& px, int w, float beta, const double* h_st, int N, const int* nst, const double* wl,
+               int t0, int t1);
+
+// Device bytes the plan needs beyond those already allocated (grids only; the
+// FFT's own workspace comes on top).
+size_t nu_grid_bytes(const NuPlan& p, int n_level);
+
+// Enqueue the NUFFT synthesis of steps [t0, t1) (one channel) into img
+// (n_level x n_pix FP64, accumulated; skipped when *b.flag is set).
+// Returns 0, or -1 (allocation failed), -2 (FFT plan or launch failed), -3 (kernel launch failed).
+int nu_enqueue(const Batch& b, int t0, int t1, const NuPlan& p, NufftWs* w, const double* d_pix, int64_t n_pix,
+               int n_level, double* img, cudaStream_t s, int* launches);
+
+void nu_free(NufftWs* w);
+
+}  // namespace bipp

@@ -212,6 +212,27 @@ def make_config(i: int, *, n_t: int | None = None, n_side: int | None = None, se
                    extra={"cap_deg": cap, "n_side": side, "p0": p0})
 
 
+def make_nufft_config(*, n_t: int = 50, n_side: int = 1024, pix_arcsec: float = 4.0, hours: float = 6.0,
+                      n_st: int = 512, seed: int = 1005) -> SSInput:
+    """Workload of the NUFFT-synthesis comparison (Sec. 5: 512 SKA-Low-like
+    stations, 50 steps spread over 6 hours, pixels of 4 arcsec, so that the
+    field of view grows with the image size): the 512-station layout of
+    configuration 1 (its first n_st stations), wl 2 m, 500 power-law sources
+    within the field, SNR 20, N_eig 64, 4 levels; n_side^2 pixels spaced
+    pix_arcsec apart in l and m around +z; visibilities rounded to complex64."""
+    rng1 = np.random.default_rng(1001)
+    p0 = layout_lognormal(512, 1000.0, 1.0, 20.0, 65000.0, 5.0, 35.0, rng1)[:n_st]
+    rng = np.random.default_rng(seed)
+    half = 0.5 * (n_side - 1) * math.radians(pix_arcsec / 3600.0)  # half-width in l, m
+    cap = math.degrees(math.asin(half))
+    src = sources_in_cap(500, cap, rng)
+    flux = flux_powerlaw(500, rng)
+    st, vis = make_steps(p0, n_t, hours * 3600.0 / n_t, 2.0, src, flux, 20.0, rng, np.complex64)
+    return SSInput(name="nufft", wl=2.0, pix=pixel_grid(n_side, cap), st_xyz=st, vis=vis, n_eig=64, n_level=4,
+                   src_dir=src, src_flux=flux,
+                   extra={"cap_deg": cap, "n_side": n_side, "p0": p0, "pix_arcsec": pix_arcsec})
+
+
 def make_batch_config(n_chan: int = 64, n_t: int = 20, n_side: int = 512, seed: int = 1003,
                       wl_lo: float = 1.5, wl_hi: float = 3.0, n_st_lo: int = 48, n_st_hi: int = 512,
                       n_eig_lo: int = 8, n_eig_hi: int = 64):

@@ -127,3 +127,17 @@ def test_level_visibilities_rank_one():
     assert np.all(Vl[0] == 0)
     np.testing.assert_allclose(Vl[1], 3.0 * np.outer(a, a.conj()))
     np.testing.assert_allclose(Vl[1], Vl[1].conj().T)
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-5])
+def test_nufft_level_error_within_its_scale(eps):
+    """On the NUFFT workload's geometry (48 stations, 40^2 pixels of 4 arcsec),
+    every level's error stays within 5 eps of max(||I_l||, ||V'_l||_F sqrt(n_pix)):
+    weak levels, whose images cancel, are judged against the size of their
+    strengths rather than of their image (the bound the GPU tests use, doubled)."""
+    inp = inputs.make_nufft_config(n_t=3, n_side=40, n_st=48)
+    b = np.array([[1217.0, np.inf], [514.0, 1217.0], [255.0, 514.0], [-np.inf, 255.0]])
+    want, scale = nu.nufft_levels_with_scale(inp.pix, inp.wl, b, 16, inp.st_xyz, inp.vis)
+    got, _ = nu.nufft_levels_with_scale(inp.pix, inp.wl, b, 16, inp.st_xyz, inp.vis, eps=eps)
+    err = np.linalg.norm(got - want, axis=0)
+    assert np.all(err <= 5 * eps * np.maximum(np.linalg.norm(want, axis=0), scale)), err
