@@ -2,6 +2,7 @@
 """Benchmark of the standard-synthesis hot path on B300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--synthesis standard|nufft]
 
 One bench step = one whole imaging job of the SKA-Low-like workload: 100 time
 steps of (Gram matrix, generalised eigensolve, selection + levels, synthesis
@@ -11,6 +12,11 @@ whole path. Inputs (positions, 400 MB of visibilities) are resident in HBM
 for `value` and are larger than L2, so every step streams them from DRAM;
 `e2e` repeats the measurement through the host-buffer C ABI with the
 host->device copies and the image read-back inside the timed region.
+
+`--synthesis nufft` measures NUFFT synthesis (Sec. 3.4) on its own workload,
+the one of the paper's NUFFT comparison: 512 stations, 50 steps over 6 hours,
+1024^2 pixels of 4 arcsec, N_eig 64, 4 levels, tolerance 1e-5; the metric
+counts the same products (the images are the same up to the tolerance).
 
 `--impl reference` times the FP64 CPU oracle (the only other place this
 script runs it) on a bounded sample of the same workload on the host cores.
@@ -97,7 +103,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", default="split_fp16", choices=["fp64", "fp32", "split_bf16", "split_fp16"])
-    ap.add_argument("--n-t", type=int, default=100, help="time steps per imaging job")
+    ap.add_argument("--n-t", type=int, default=0, help="time steps per imaging job (default 100; 50 for nufft)")
+    ap.add_argument("--synthesis", default="standard", choices=["standard", "nufft"])
+    ap.add_argument("--nufft-eps", type=float, default=1e-5)
     ap.add_argument("--side", type=int, default=1024, help="image side in pixels")
     ap.add_argument("--n-st", type=int, default=0, help="keep only the first n stations (small profiling cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -109,7 +117,9 @@ def parse():
 
 def workload(args):
     from paper_2310_09200_b300 import inputs
-    inp = inputs.make_config(1, n_t=args.n_t, n_side=args.side)
+    if args.synthesis == "nufft":
+        return inputs.make_nufft_config(n_t=args.n_t or 50, n_side=args.side, n_st=args.n_st or 512)
+    inp = inputs.make_config(1, n_t=args.n_t or 100, n_side=args.side)
     if args.n_st:
         n = args.n_st
         inp.st_xyz = [p[:n] for p in inp.st_xyz]
@@ -118,6 +128,18 @@ def workload(args):
 
 
 def config_dict(args, inp, precision):
+    if args.synthesis == "nufft":
+        return {
+            "workload": (f"SKA-Low-like NUFFT synthesis: {inp.st_xyz[0].shape[0]} stations (lognormal to 65 km), "
+                         f"{args.side}^2 px of 4 arcsec, N_eig {inp.n_eig}, {inp.n_level} levels, {inp.n_t} time "
+                         f"steps over 6 h per job, wl 2 m, type-3 NUFFT tolerance {args.nufft_eps:g}"),
+            "n_st": int(inp.st_xyz[0].shape[0]), "n_pix": int(inp.n_pix), "n_eig": int(inp.n_eig),
+            "n_level": int(inp.n_level), "n_t": int(inp.n_t), "synthesis": "nufft",
+            "nufft_eps": args.nufft_eps,
+            "eigensolve": EIG_DESC.get(getattr(args, "eig", "jacobi64"), "fp64 parallel-order Jacobi")
+            if precision != "fp64 (oracle)" else "fp64 cyclic Jacobi (oracle)",
+            "l2": "inputs larger than L2 (visibilities 200 MB per job)",
+        }
     return {
         "workload": (f"SKA-Low-like standard synthesis: {inp.st_xyz[0].shape[0]} stations (lognormal to 65 km), "
                      f"{args.side}^2 px in a 20 deg cap, N_eig {inp.n_eig}, {inp.n_level} levels, "
@@ -168,6 +190,14 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def dtype_label(args):
+    if args.synthesis == "nufft":
+        base = "f64 eig + f32 NUFFT grids (f64 coordinates and phase reduction)"
+    else:
+        base = DTYPES[args.precision]
+    return base.replace("f64 eig", "f32+f64 eig") if args.eig == "mixed" else base
+
+
 def dist_setup(args):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -200,6 +230,48 @@ def cpu_sample(inp, bounds, n_sub_side=64):
             "value": prods / full_step}
 
 
+def cpu_sample_nufft(inp, bounds, eps, patch=128):
+    """Oracle NUFFT synthesis on a bounded sample: one time step (FP64 Gram +
+    Jacobi eigensolve, then the type-3 NUFFT of its level visibilities) onto
+    the central patch^2 pixels of the image; products/s of that sample."""
+    import oracle
+    from oracle import nufft as onu
+    side = int(round(math.sqrt(inp.n_pix)))
+    c0 = side // 2 - patch // 2
+    rows = np.arange(c0, c0 + patch)
+    sel = (rows[:, None] * side + rows[None, :]).ravel()
+    t0 = time.perf_counter()
+    onu.nufft_levels(inp.pix[sel], inp.wl, bounds, inp.n_eig, inp.st_xyz[0], inp.vis[0], eps=eps)
+    dt = time.perf_counter() - t0
+    n_st = inp.st_xyz[0].shape[0]
+    return {"t_s": dt, "n_sub": int(len(sel)), "value": len(sel) * inp.n_eig * n_st / dt}
+
+
+def nufft_roofline(nt, n_level, n_pix, n_t, n_st, n_eig, hbm_gbs):
+    """The dominant kernel of NUFFT synthesis (largest total time per job) and its
+    HBM roofline: algorithmic bytes per launch / measured launch time."""
+    M = nt["grid"]
+    cells = M[0] * M[1] * M[2]
+    cells2 = 8 * cells
+    Lp = 1 if n_level == 1 else n_level + (n_level & 1)
+    kern = {  # name: (launches per job, ms per launch, algorithmic bytes per launch)
+        "k_nu_spread": (1, nt["spread_ms"], cells * Lp * 8 + n_t * n_eig * n_st * 16 + n_t * n_st * 24),
+        "k_nu_pad": (n_level, nt["pad_ms"], cells * 8 + cells2 * 8),
+        "cuFFT C2C (library)": (n_level, nt["fft_ms"], 2 * cells2 * 8),
+        "k_nu_interp": (n_level, nt["interp_ms"], n_pix * (24 + 16 + 4)),
+    }
+    name = max(kern, key=lambda k: kern[k][0] * kern[k][1])
+    nl, ms, by = kern[name]
+    ach = by / (ms / 1e3) / 1e9
+    return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm_gbs, "unit": "GB/s", "traffic": None,
+            "frac": ach / hbm_gbs,
+            "kernels_ms_per_job": {k: v[0] * v[1] for k, v in kern.items()},
+            "grid": list(M), "fine_grid_points": cells2,
+            "peak_note": ("of measured: STREAM-style copy; algorithmic bytes = grid written once (spread), "
+                          "one level read + fine grid written (pad), fine grid read + written once (FFT), "
+                          "pixel coordinates + correction + image read/write (interp)")}
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
@@ -220,6 +292,22 @@ def reference_main(args, ws, rank):
         pooled.extend(mu[: inp.n_eig])
     from paper_2310_09200_b300.bipp_ss import quantile_level_bounds
     bounds = quantile_level_bounds(pooled, inp.n_level)
+    if args.synthesis == "nufft":
+        samples = [cpu_sample_nufft(inp, bounds, args.nufft_eps) for _ in range(args.steps)]
+        value = statistics.median(s["value"] for s in samples)
+        job_ms = inp.n_pix * inp.n_eig * inp.st_xyz[0].shape[0] * inp.n_t / value * 1e3
+        sample = (f"1 of {inp.n_t} time steps per bench step: FP64 Gram + Jacobi eigensolve of 512 stations and "
+                  f"the FP64 numpy type-3 NUFFT of its 4 level visibilities onto the central {samples[0]['n_sub']} "
+                  f"pixels; products/s of that sample (no warm-up: each sample is a whole oracle run)")
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+                "warmup": 0, "ms_per_step": job_ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+                "config": config_dict(args, inp, "fp64 (oracle)"),
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                 "sample": sample},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
     samples = []
     for i in range(args.warmup + args.steps):
         s = cpu_sample(inp, bounds)
@@ -262,8 +350,10 @@ def ours_main(args, ws, rank, local):
     d_st = torch.from_numpy(st).to(f"cuda:{local}")
     d_V = torch.from_numpy(V).to(f"cuda:{local}")
     stream = torch.cuda.Stream()
+    nufft = args.synthesis == "nufft"
+    extra = {"synthesis": "nufft", "nufft_eps": args.nufft_eps} if nufft else {}
     ss = bipp_ss.StandardSynthesis(inp.pix, inp.wl, bounds, n_eig=inp.n_eig, precision=args.precision,
-                                   device=local, eig_mode=args.eig)
+                                   device=local, eig_mode=args.eig, **extra)
 
     def one_step():
         bipp_ss.bipp_ss_collect_device(ss.h, nst, d_st, d_V, stream=stream)
@@ -278,6 +368,8 @@ def ours_main(args, ws, rank, local):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     stage = np.zeros(4)
+    nu_ms = np.zeros(5)
+    nu_last = None
     sweeps = 0
     launches = 0
     e0.record(stream)
@@ -286,6 +378,10 @@ def ours_main(args, ws, rank, local):
         stage += [t["gram_reduce_ms"], t["eig_ms"], t["select_ms"], t["synth_ms"]]
         sweeps += t["sweeps_total"]
         launches += t["launches"]
+        if nufft:
+            nu_last = ss.nufft_timings()
+            nu_ms += [nu_last["spread_ms"], nu_last["pad_ms"], nu_last["fft_ms"], nu_last["interp_ms"],
+                      nu_last["levels_ms"]]
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = clk.stop()
@@ -329,7 +425,13 @@ def ours_main(args, ws, rank, local):
                        "peak_note": ("frac = (FP32 reduction + back-transformation flops / FP32 peak + "
                                      "double-float refinement operations / FP32 instruction rate) / measured "
                                      "stage time; the QR chase is latency-bound and not in the bound")}
-    if args.precision in ("fp32", "fp64"):
+    if nufft:
+        nt = dict(nu_last)
+        for i, k in enumerate(["spread_ms", "pad_ms", "fft_ms", "interp_ms", "levels_ms"]):
+            nt[k] = nu_ms[i] / K
+        roof_synth = nufft_roofline(nt, inp.n_level, inp.n_pix, inp.n_t, n_st, inp.n_eig,
+                                    measured_peaks().get("hbm_gbs", 6400.0))
+    elif args.precision in ("fp32", "fp64"):
         peak = FP32_PEAK_FLOPS if args.precision == "fp32" else FP64_PEAK_FLOPS
         roof_synth = {"kernel": f"k_synth_{args.precision[-2:]}", "bound": "alu",
                       "achieved": syn_flops / (syn_ms / 1e3) / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
@@ -383,7 +485,13 @@ def ours_main(args, ws, rank, local):
     ss.close()
 
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and nufft:
+        s = cpu_sample_nufft(inp, bounds, args.nufft_eps)
+        cpu = {"value": s["value"], "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": (f"one time step: FP64 Gram + Jacobi of {n_st} stations and the FP64 numpy type-3 NUFFT "
+                          f"of its level visibilities onto the central {s['n_sub']} pixels ({s['t_s']:.1f} s); "
+                          f"products/s of that sample")}
+    elif rank == 0 and ws == 1 and not args.no_cpu_baseline:
         s = cpu_sample(inp, bounds)
         cpu = {"value": s["value"], "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": (f"one time step: FP64 Gram + Jacobi of {n_st} stations (single thread, "
@@ -392,10 +500,13 @@ def ours_main(args, ws, rank, local):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": DTYPES[args.precision].replace("f64 eig", "f32+f64 eig") if args.eig == "mixed" else DTYPES[args.precision], "data": "synthetic",
+                "vs_baseline": None, "dtype": dtype_label(args), "data": "synthetic",
                 "config": config_dict(args, inp, args.precision),
                 "stage_ms_per_step": {"gram_chol_reduce": stage[0] / K, "jacobi": eig_ms,
                                       "select_pack": stage[2] / K, "synthesis": syn_ms},
+                **({"nufft_ms_per_step": {"spread": nu_ms[0] / K, "pad_per_level": nu_ms[1] / K,
+                                          "fft_per_level": nu_ms[2] / K, "interp_per_level": nu_ms[3] / K,
+                                          "levels": nu_ms[4] / K}} if nufft else {}),
                 "synthesis_only_value": prods / (syn_ms / 1e3),
                 "roofline": dominant, "roofline_synthesis": roof_synth, "roofline_jacobi": roof_jacobi,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}

@@ -200,6 +200,16 @@ int bipp_ss_last_eigvals(bipp_ss_t h, int32_t n_t_cap, int32_t n_eig_cap, int32_
  * out[4] Jacobi sweeps summed over the steps, out[5] kernels launched. */
 int bipp_ss_get_timings(bipp_ss_t h, double* out6);
 
+/* Kernel times of the last collect's NUFFT synthesis (BIPP_SYNTH_NUFFT; CUDA
+ * events on the collect's stream, first channel of the batch):
+ * out[0] level strengths + spreading (k_nu_const + k_nu_spread) [ms],
+ * out[1] one level's deconvolve/pad (k_nu_pad) [ms], out[2] one level's FFT
+ * (cuFFT) [ms], out[3] one level's interpolation (k_nu_interp) [ms],
+ * out[4] all levels' pad + FFT + interpolation [ms], out[5..7] the spread
+ * grid's points per dimension (M), out[8] the kernel width w. Zeros for
+ * STANDARD. */
+int bipp_ss_get_nufft_timings(bipp_ss_t h, double* out9);
+
 /* Differentiable synthesis with complex station gains (device pointers,
  * e.g. PyTorch memory; stream-ordered on `stream`, NULL = default stream;
  * returns after the work has finished).

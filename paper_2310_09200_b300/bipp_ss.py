@@ -51,7 +51,7 @@ EXPORTED = [
     "bipp_ss_set_images", "bipp_ss_last_eigvals", "bipp_ss_get_timings", "bipp_ss_destroy",
     "bipp_ss_last_error", "bipp_ss_collect_noalloc", "bipp_ss_synth_levels_device",
     "bipp_ss_synth_adjoint_device", "bipp_ss_create_channels", "bipp_ss_collect_channels",
-    "bipp_ss_energy_neig", "bipp_ss_kmeans_bounds",
+    "bipp_ss_energy_neig", "bipp_ss_kmeans_bounds", "bipp_ss_get_nufft_timings",
 ]
 
 BIPP_NOALLOC_MAX_STATIONS = 128
@@ -101,6 +101,7 @@ def load(path: str | None = None):
     L.bipp_ss_set_images.argtypes = [H, dp]
     L.bipp_ss_last_eigvals.argtypes = [H, i32, i32, ip, ip, dp, ip]
     L.bipp_ss_get_timings.argtypes = [H, dp]
+    L.bipp_ss_get_nufft_timings.argtypes = [H, dp]
     L.bipp_ss_destroy.argtypes = [H]
     L.bipp_ss_energy_neig.argtypes = [i32, dp, C.c_double, ip]
     L.bipp_ss_kmeans_bounds.argtypes = [i32, dp, i32, dp]
@@ -317,6 +318,13 @@ def bipp_ss_get_timings(h) -> dict:
             "launches": int(a[5])}
 
 
+def bipp_ss_get_nufft_timings(h) -> dict:
+    a = np.zeros(9, dtype=np.float64)
+    _check(h, load().bipp_ss_get_nufft_timings(h, _dp(a)))
+    return {"spread_ms": a[0], "pad_ms": a[1], "fft_ms": a[2], "interp_ms": a[3], "levels_ms": a[4],
+            "grid": (int(a[5]), int(a[6]), int(a[7])), "w": int(a[8])}
+
+
 def bipp_ss_destroy(h) -> None:
     if h:
         load().bipp_ss_destroy(h)
@@ -405,6 +413,9 @@ class StandardSynthesis:
 
     def timings(self):
         return bipp_ss_get_timings(self.h)
+
+    def nufft_timings(self):
+        return bipp_ss_get_nufft_timings(self.h)
 
     def close(self):
         if self.h:

@@ -97,6 +97,8 @@ struct bipp_ss {
   std::vector<int> nu_t0;  // first step of each channel group, plus n_t at the end
   std::vector<double> nu_st;  // host copy of device station coordinates
   int nu_launches = 0;
+  cudaEvent_t nu_ev[7] = {};
+  double nu_timings[9] = {};
   // graph cache: the last geometry seen, and the captured graph of it
   GraphKey last_key;
   bool have_key = false;
@@ -257,6 +259,7 @@ extern "C" int bipp_ss_destroy(bipp_ss_t h) {
   if (h->d_img) cudaFree(h->d_img);
   if (h->d_bounds) cudaFree(h->d_bounds);
   for (auto& e : h->ev) if (e) cudaEventDestroy(e);
+  for (auto& e : h->nu_ev) if (e) cudaEventDestroy(e);
   if (h->stream) cudaStreamDestroy(h->stream);
   delete h;
   return BIPP_OK;
@@ -335,6 +338,8 @@ extern "C" int bipp_ss_create_channels(bipp_ss_t* out, int64_t n_pix, const doub
   cudaError_t e;
   if ((e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)) != cudaSuccess) return bail(BIPP_ERR_CUDA, "stream", e);
   for (auto& ev : h->ev)
+    if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(BIPP_ERR_CUDA, "event", e);
+  for (auto& ev : h->nu_ev)
     if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(BIPP_ERR_CUDA, "event", e);
   if ((e = dalloc(&h->d_pix, (size_t)3 * n_pix)) != cudaSuccess) return bail(BIPP_ERR_OUT_OF_MEMORY, "pixels", e);
   if ((e = dalloc(&h->d_pix_hl, (size_t)6 * n_pix)) != cudaSuccess) return bail(BIPP_ERR_OUT_OF_MEMORY, "pixels", e);
@@ -442,7 +447,7 @@ static int enqueue_batch(bipp_ss* h, const Batch& b, const TcPlan& plan, cudaStr
       const int t0 = h->nu_t0[g], t1 = h->nu_t0[g + 1];
       double* img = h->d_img + (size_t)h->h_chan[t0] * h->n_level * h->n_pix;
       const int rc = nu_enqueue(b, t0, t1, h->nu_plans[g], &h->nu, h->d_pix, h->n_pix, h->n_level, img, s,
-                                &h->nu_launches);
+                                &h->nu_launches, g == 0 ? h->nu_ev : nullptr);
       if (rc == -1) return fail(h, BIPP_ERR_OUT_OF_MEMORY, "NUFFT grid allocation failed");
       if (rc == -2) return fail(h, BIPP_ERR_CUDA, "NUFFT: cuFFT plan or execution failed");
       if (rc) return fail(h, BIPP_ERR_CUDA, "NUFFT kernel launch failed");
@@ -597,6 +602,20 @@ static int run_batch(bipp_ss* h, int n_t, int N, const std::vector<int>& nst_v, 
   CUDA_TRY(h, cudaMemcpy(sweeps.data(), h->d_sweeps, sizeof(int) * n_t, cudaMemcpyDeviceToHost));
   const int tc_status = tc ? tc_read_status(&h->tc) : 0;
   for (int i = 0; i < 4; ++i) h->timings[i] = ms[i];
+  for (double& v : h->nu_timings) v = 0.0;
+  if (nufft) {
+    const int pairs[5][2] = {{0, 1}, {2, 3}, {3, 4}, {4, 5}, {2, 6}};
+    for (int i = 0; i < 5; ++i) {
+      float v = 0.f;
+      if (cudaEventElapsedTime(&v, h->nu_ev[pairs[i][0]], h->nu_ev[pairs[i][1]]) != cudaSuccess) {
+        v = NAN;
+        (void)cudaGetLastError();
+      }
+      h->nu_timings[i] = v;
+    }
+    for (int d = 0; d < 3; ++d) h->nu_timings[5 + d] = h->nu_plans[0].M[d];
+    h->nu_timings[8] = h->nu_plans[0].w;
+  }
   h->timings[4] = 0;
   for (int t = 0; t < n_t; ++t) h->timings[4] += sweeps[t];
   // gram, [cholesky], trinv, [2 reduction GEMMs], hermitize, jacobi, select, [scale], [pack], synthesis
@@ -749,6 +768,13 @@ extern "C" int bipp_ss_get_timings(bipp_ss_t h, double* out6) {
   if (!h) return fail(nullptr, BIPP_ERR_INVALID_ARG, "handle is NULL");
   if (!out6) return fail(h, BIPP_ERR_INVALID_ARG, "out6 is NULL");
   for (int i = 0; i < 6; ++i) out6[i] = h->timings[i];
+  return BIPP_OK;
+}
+
+extern "C" int bipp_ss_get_nufft_timings(bipp_ss_t h, double* out9) {
+  if (!h) return fail(nullptr, BIPP_ERR_INVALID_ARG, "handle is NULL");
+  if (!out9) return fail(h, BIPP_ERR_INVALID_ARG, "out9 is NULL");
+  for (int i = 0; i < 9; ++i) out9[i] = h->nu_timings[i];
   return BIPP_OK;
 }
 

@@ -458,7 +458,7 @@ size_t nu_grid_bytes(const NuPlan& p, int n_level) {
 }
 
 int nu_enqueue(const Batch& b, int t0, int t1, const NuPlan& p, NufftWs* w, const double* d_pix, int64_t n_pix,
-               int n_level, double* img, cudaStream_t s, int* launches) {
+               int n_level, double* img, cudaStream_t s, int* launches, const cudaEvent_t* ev) {
   const int Lp = n_level == 1 ? 1 : n_level + (n_level & 1);
   int nl = 0;
   if (!grow(&w->F, &w->F_cap, p.cells() * Lp)) return -1;
@@ -511,6 +511,7 @@ int nu_enqueue(const Batch& b, int t0, int t1, const NuPlan& p, NufftWs* w, cons
   if (cudaMemsetAsync(w->cst, 0, sizeof(double) * kMaxLevels, s) != cudaSuccess) return -1;
 
   const int T = t1 - t0;
+  if (ev) cudaEventRecord(ev[0], s);
   k_nu_const<<<T, 256, 0, s>>>(b, t0, w->cst);
   ++nl;
   SpreadArgs sa;
@@ -533,6 +534,7 @@ int nu_enqueue(const Batch& b, int t0, int t1, const NuPlan& p, NufftWs* w, cons
   });
   ++nl;
   if (cudaGetLastError() != cudaSuccess) return -3;
+  if (ev) cudaEventRecord(ev[1], s);
 
   if (!w->have_fft || w->fft_n[0] != p.N2[0] || w->fft_n[1] != p.N2[1] || w->fft_n[2] != p.N2[2]) {
     if (w->have_fft) {
@@ -575,11 +577,16 @@ int nu_enqueue(const Batch& b, int t0, int t1, const NuPlan& p, NufftWs* w, cons
   const unsigned pix_grid = (unsigned)((n_pix + 255) / 256);
   for (int l = 0; l < n_level; ++l) {
     ga.l = l;
+    if (ev && l == 0) cudaEventRecord(ev[2], s);
     k_nu_pad<<<pad_grid, 256, 0, s>>>(w->F, ga, w->inv, w->G);
+    if (ev && l == 0) cudaEventRecord(ev[3], s);
     if (cufftExecC2C(w->fft, (cufftComplex*)w->G, (cufftComplex*)w->G, CUFFT_INVERSE) != CUFFT_SUCCESS) return -2;
+    if (ev && l == 0) cudaEventRecord(ev[4], s);
     k_nu_interp<<<pix_grid, 256, 0, s>>>(d_pix, n_pix, ia, w->G, w->corr, w->cst, l, b.flag, img);
+    if (ev && l == 0) cudaEventRecord(ev[5], s);
     nl += 2;
   }
+  if (ev) cudaEventRecord(ev[6], s);
   if (cudaGetLastError() != cudaSuccess) return -3;
   if (launches) *launches += nl;
   return 0;

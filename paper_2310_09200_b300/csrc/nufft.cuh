@@ -80,8 +80,10 @@ size_t nu_grid_bytes(const NuPlan& p, int n_level);
 // Enqueue the NUFFT synthesis of steps [t0, t1) (one channel) into img
 // (n_level x n_pix FP64, accumulated; skipped when *b.flag is set).
 // Returns 0, or -1 (allocation failed), -2 (FFT plan or launch failed), -3 (kernel launch failed).
+// ev (optional, 7 events): recorded before the spreading, after it, around the
+// first level's pad, FFT and interpolation, and after the last level.
 int nu_enqueue(const Batch& b, int t0, int t1, const NuPlan& p, NufftWs* w, const double* d_pix, int64_t n_pix,
-               int n_level, double* img, cudaStream_t s, int* launches);
+               int n_level, double* img, cudaStream_t s, int* launches, const cudaEvent_t* ev);
 
 void nu_free(NufftWs* w);
 

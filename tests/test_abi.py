@@ -68,10 +68,13 @@ def test_default_options(lib):
     assert o.precision == bipp_ss.BIPP_PREC_FP32 and o.filter == bipp_ss.BIPP_FILTER_LSQ
     assert o.max_jacobi_sweeps == 40 and abs(o.jacobi_tol - 1e-13) < 1e-30 and o.gram_identity == 0
     assert o.device == -1 and o.eig_mode == bipp_ss.BIPP_EIG_JACOBI64
+    assert o.synthesis == bipp_ss.BIPP_SYNTH_STANDARD and abs(o.nufft_eps - 1e-5) < 1e-20
+    assert C.sizeof(bipp_ss.bipp_ss_options) == 80  # the C struct's size on x86-64
 
 
 @pytest.mark.parametrize("case", ["n_pix", "wl", "levels", "precision", "reserved", "nan_bound", "nan_pix",
-                                  "eig_levels", "eig_many", "eig_flag"])
+                                  "eig_levels", "eig_many", "eig_flag", "synthesis", "nufft_eps_small",
+                                  "nufft_eps_large", "nufft_eigenimages"])
 def test_create_rejects_invalid_arguments_before_device_use(lib, case):
     pix = np.array([[0.0, 0.0, 1.0], [0.1, 0.0, 0.99]])
     b = np.array([[-np.inf, np.inf]])
@@ -109,9 +112,18 @@ def test_create_rejects_invalid_arguments_before_device_use(lib, case):
         b = None
     elif case == "eig_flag":
         kw.update(eigenimages=2, n_eig=1)
+    elif case == "synthesis":
+        kw["synthesis"] = 2
+    elif case == "nufft_eps_small":
+        kw.update(synthesis="nufft", nufft_eps=1e-8)  # beyond FP32 grids
+    elif case == "nufft_eps_large":
+        kw.update(synthesis="nufft", nufft_eps=0.5)
+    elif case == "nufft_eigenimages":  # NUFFT synthesis makes level images only
+        kw.update(synthesis="nufft", eigenimages=1, n_eig=1)
     with pytest.raises(bipp_ss.BippError) as e:
         bipp_ss.bipp_ss_create(pix, wl, b, **kw)
-    assert e.value.code == bipp_ss.BIPP_ERR_INVALID_ARG
+    want = bipp_ss.BIPP_ERR_UNSUPPORTED if case == "nufft_eigenimages" else bipp_ss.BIPP_ERR_INVALID_ARG
+    assert e.value.code == want
 
 
 def test_null_handle_calls_fail_cleanly(lib):
