@@ -492,12 +492,14 @@ static int plan_nufft(bipp_ss* h, int n_t, int N, const std::vector<int>& nst_v,
     for (int d = 0; d < 3; ++d)
       if (p.M[d] > (1 << 28))
         return fail(h, BIPP_ERR_UNSUPPORTED, "NUFFT grid dimension %d needs %d points", d, p.M[d]);
-    need = std::max(need, nu_grid_bytes(p, h->n_level));
+    const size_t slots = (size_t)(h->nu_t0[g + 1] - h->nu_t0[g]) * N * (N - 1) / 2;
+    need = std::max(need, nu_grid_bytes(p, h->n_level, slots));
     h->nu_plans.push_back(p);
   }
   size_t free_b = 0, total_b = 0;
   CUDA_TRY(h, cudaMemGetInfo(&free_b, &total_b));
-  const size_t have = (h->nu.F_cap + h->nu.G_cap) * sizeof(float2);
+  const size_t have = (h->nu.F_cap + h->nu.G_cap + h->nu.rc_cap) * sizeof(float2) +
+                      (h->nu.rm_cap + h->nu.rf_cap) * sizeof(int4);
   // grids plus the FFT's workspace (of the order of the fine grid) must fit
   const NuPlan& p0 = h->nu_plans[0];
   if (need + p0.cells2() * sizeof(float2) > free_b + have)

@@ -3,15 +3,23 @@
 // Per channel of a batch (steps [t0, t1) with one wavelength), one type-3
 // NUFFT per level maps the baselines of all steps to the pixels:
 //
-//   1. k_nu_spread: one thread per station pair p < q of a step. It forms the
-//      pair's level strengths 2 V'_l,pq = 2 sum_{e in l} d_e a_pe conj(a_qe)
-//      (eigenvectors staged through shared memory), orients the pair so that
-//      the folded coordinate is >= 0 (the (q, p) term is the conjugate one, so
-//      Re of the sum is unchanged), pre-phases the strengths by exp(2 pi i <D, x>)
-//      and spreads them onto the grid y_m = (m - M/2) h with the
-//      exponential-of-semicircle kernel, w^3 cells x all levels, with vector
-//      float atomics. Coordinates and phases are reduced in FP64; kernel
-//      weights, strengths and the grid are FP32.
+//   1. Spreading onto the grid y_m = (m - M/2) h with the exponential-of-
+//      semicircle kernel, sorted by bins of the grid so that the w^3-cell
+//      footprints are summed in shared memory:
+//      k_nu_count   one thread per station pair p < q of a step: orientation
+//                   (the folded coordinate >= 0; the (q, p) term is the
+//                   conjugate one, so Re of the sum is unchanged), spread start,
+//                   bin; warp-aggregated count per bin;
+//      k_nu_scan    exclusive offsets of the bins' points and of their chunks;
+//      k_nu_scatter per pair, the level strengths 2 V'_l,pq = 2 sum_{e in l}
+//                   d_e a_pe conj(a_qe) (eigenvectors staged through shared
+//                   memory), pre-phased by exp(2 pi i <D, x>), written with the
+//                   start and fractions at the pair's place in bin order;
+//      k_nu_spread  one block per chunk of <= 2048 points of a bin: footprints
+//                   summed into a shared-memory tile (bin + w - 1 halo), then the
+//                   tile added to the grid with vector float atomics.
+//      Coordinates and phases are reduced in FP64; kernel weights, strengths and
+//      the grid are FP32.
 //   2. k_nu_const: the p = q terms (zero baseline): sum_t sum_{e in l} d_e |a_e|^2,
 //      a constant per level.
 //   3. per level: k_nu_pad divides each grid mode by the second kernel's
@@ -100,6 +108,53 @@ struct SpreadArgs {
   float beta;
 };
 
+// Oriented coordinates, spread start m0 (inside the grid) and fraction m0 - g of
+// the pair (p, q) of step t.
+struct PairGeo {
+  double x[3];
+  int m0[3];
+  float fr[3];
+  bool flip;
+};
+
+__device__ __forceinline__ PairGeo pair_geo(const Batch& b, int t, int p, int q, const SpreadArgs& a) {
+  PairGeo g;
+  const int N = b.n_max;
+  const double* st = b.st + (size_t)t * 3 * N;
+  const double iwl = 1.0 / b.wl[t];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) g.x[d] = -(st[(size_t)d * N + p] - st[(size_t)d * N + q]) * iwl;
+  const double xf = a.fold == 0 ? g.x[0] : (a.fold == 1 ? g.x[1] : g.x[2]);
+  g.flip = xf < 0.0;
+  if (g.flip) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) g.x[d] = -g.x[d];
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double gg = (g.x[d] - a.C[d]) * a.invH[d] + 0.5 * a.M[d];
+    int m = (int)ceil(gg - 0.5 * a.w);
+    m = min(max(m, 0), a.M[d] - a.w);  // never outside the grid (the plan's margin makes this a no-op)
+    g.m0[d] = m;
+    g.fr[d] = (float)((double)m - gg);
+  }
+  return g;
+}
+
+// Sort key of a point: the grid cell of its spread start.
+__device__ __forceinline__ int cell_of(const PairGeo& g, const SpreadArgs& a) {
+  return (g.m0[2] * a.M[1] + g.m0[1]) * a.M[0] + g.m0[0];
+}
+
+// Pair index r -> (p, q), p < q, r = q (q - 1) / 2 + p.
+__device__ __forceinline__ void tri_pair(long long r, int* p, int* q) {
+  long long qq = (long long)((1.0 + sqrt(8.0 * (double)r + 1.0)) * 0.5);
+  while (qq * (qq - 1) / 2 > r) --qq;
+  while ((qq + 1) * qq / 2 <= r) ++qq;
+  *q = (int)qq;
+  *p = (int)(r - qq * (qq - 1) / 2);
+}
+
 // Upper-triangle tile (pb <= qb) of linear index r, tiles ordered by qb.
 __device__ __forceinline__ void tri_tile(int r, int* pb, int* qb) {
   int q = (int)((sqrt(8.0 * r + 1.0) - 1.0) * 0.5);
@@ -109,11 +164,132 @@ __device__ __forceinline__ void tri_tile(int r, int* pb, int* qb) {
   *pb = r - q * (q + 1) / 2;
 }
 
+// Warp-aggregated counter increment: the lanes of `active` add 1 each to ctr[key];
+// returns the counter's value before this lane's increment.
+__device__ __forceinline__ int agg_add(int* ctr, int key, unsigned active) {
+  const unsigned grp = __match_any_sync(active, key);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(grp) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(ctr + key, __popc(grp));
+  base = __shfl_sync(grp, base, leader);
+  return base + __popc(grp & ((1u << lane) - 1u));
+}
+
+// 1. Points per start cell: one thread per pair slot (t, p < q) of the steps [t0, t0 + T).
+__global__ void k_nu_count(Batch b, int t0, int T, SpreadArgs a, int* __restrict__ count) {
+  const long long NP = (long long)b.n_max * (b.n_max - 1) / 2;
+  const long long total = NP * T;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < total; base += (long long)gridDim.x * blockDim.x) {
+    const long long sl = base + threadIdx.x;
+    bool active = false;
+    int t = 0, p = 0, q = 0;
+    if (sl < total) {
+      t = t0 + (int)(sl / NP);
+      tri_pair(sl % NP, &p, &q);
+      active = q < b.nst[t] && b.nkept[t] > 0;
+    }
+    const unsigned am = __ballot_sync(0xffffffffu, active);
+    if (active) {
+      const PairGeo g = pair_geo(b, t, p, q, a);
+      agg_add(count, cell_of(g, a), am);
+    }
+  }
+}
+
+// Exclusive scan out[0..n] of v(in[i]) (out[n] = total) in one block of 1024
+// threads; MODE 0: v = x, MODE 1: v = ceil(x / P) (chunks of P points).
+template <int MODE>
+__global__ void __launch_bounds__(1024) k_nu_scan(const int* __restrict__ in, int n, int P, int* __restrict__ out) {
+  __shared__ int part[1024];
+  const int per = (n + 1023) / 1024;
+  const int i0 = min(n, threadIdx.x * per), i1 = min(n, i0 + per);
+  int sum = 0;
+  for (int i = i0; i < i1; ++i) sum += MODE == 0 ? in[i] : (in[i] + P - 1) / P;
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {  // inclusive Hillis-Steele scan of the partial sums
+    const int v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int run = part[threadIdx.x] - sum;
+  for (int i = i0; i < i1; ++i) {
+    out[i] = run;
+    run += MODE == 0 ? in[i] : (in[i] + P - 1) / P;
+  }
+  if (threadIdx.x == 1023) out[n] = part[1023];
+}
+
+// Exclusive scan of n ints over many blocks: segments of kSeg elements per
+// block; k_nu_seg_sum totals each segment, k_nu_scan<0> scans the totals,
+// k_nu_seg_scan writes out[i] (and out[n] = total).
+constexpr int kSeg = 8192;
+
+__global__ void __launch_bounds__(1024) k_nu_seg_sum(const int* __restrict__ in, long long n, int* __restrict__ sums) {
+  __shared__ int red[32];
+  const long long i0 = (long long)blockIdx.x * kSeg + threadIdx.x * 8;
+  int v = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if (i0 + k < n) v += in[i0 + k];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int u = red[threadIdx.x];
+    for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+    if (threadIdx.x == 0) sums[blockIdx.x] = u;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_nu_seg_scan(const int* __restrict__ in, long long n,
+                                                      const int* __restrict__ seg_off, int* __restrict__ out) {
+  __shared__ int wsum[32];
+  const long long i0 = (long long)blockIdx.x * kSeg + threadIdx.x * 8;
+  int v[8], tot = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    v[k] = i0 + k < n ? in[i0 + k] : 0;
+    tot += v[k];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int inc = tot;  // inclusive warp scan of the thread totals
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += u;
+  }
+  if (lane == 31) wsum[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    int x = wsum[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += u;
+    }
+    wsum[lane] = x;  // inclusive over warps
+  }
+  __syncthreads();
+  int run = seg_off[blockIdx.x] + (warp > 0 ? wsum[warp - 1] : 0) + inc - tot;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if (i0 + k < n) out[i0 + k] = run;
+    run += v[k];
+  }
+  if (i0 <= n - 1 && n - 1 < i0 + 8) out[n] = run;  // the thread holding the last element writes the total
+}
+
 constexpr int kTile = 16;
 constexpr int kEChunk = 64;
+constexpr int kNuRun = 256;  // sorted points per spreading warp
 
+// 2. Level strengths, orientation and pre-phase of every pair, written in start-cell
+// order: rm = (m0, cell), rf = (fractions), rc = Lp strengths (pair-major).
 template <int MAXL>
-__global__ void __launch_bounds__(kTile* kTile) k_nu_spread(Batch b, int t0, SpreadArgs a, float2* __restrict__ F) {
+__global__ void __launch_bounds__(kTile* kTile)
+    k_nu_scatter(Batch b, int t0, SpreadArgs a, const int* __restrict__ cell_off, int* __restrict__ cursor,
+                 int4* __restrict__ rm, float4* __restrict__ rf, float2* __restrict__ rc) {
   const int t = t0 + blockIdx.z;
   const int n = b.nst[t];
   const int K = b.nkept[t];
@@ -161,68 +337,102 @@ __global__ void __launch_bounds__(kTile* kTile) k_nu_spread(Batch b, int t0, Spr
     }
     __syncthreads();
   }
-  if (!(p < q && q < n)) return;
-
-  const double* st = b.st + (size_t)t * 3 * N;
-  const double iwl = 1.0 / b.wl[t];
-  double x[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) x[d] = -(st[(size_t)d * N + p] - st[(size_t)d * N + q]) * iwl;
-  float cs = 1.f;
-  const double xf = a.fold == 0 ? x[0] : (a.fold == 1 ? x[1] : x[2]);
-  if (xf < 0.0) {
-#pragma unroll
-    for (int d = 0; d < 3; ++d) x[d] = -x[d];
-    cs = -1.f;  // conjugate strengths
-  }
+  const bool active = p < q && q < n;
+  const unsigned am = __ballot_sync(0xffffffffu, active);
+  if (!active) return;
+  const PairGeo g = pair_geo(b, t, p, q, a);
+  const int key = cell_of(g, a);
+  const int pos = cell_off[key] + agg_add(cursor, key, am);
   // pre-phase exp(2 pi i <D, x>), reduced to [-1/2, 1/2] cycles in FP64
-  const double ph = a.D[0] * x[0] + a.D[1] * x[1] + a.D[2] * x[2];
+  const double ph = a.D[0] * g.x[0] + a.D[1] * g.x[1] + a.D[2] * g.x[2];
   float sn, cn;
   sincospif(2.0f * (float)(ph - rint(ph)), &sn, &cn);
-  float2 c[MAXL];
+  const float cs = g.flip ? -1.f : 1.f;  // the (q, p) orientation carries the conjugate strength
+  rm[pos] = make_int4(g.m0[0], g.m0[1], g.m0[2], key);
+  rf[pos] = make_float4(g.fr[0], g.fr[1], g.fr[2], 0.f);
 #pragma unroll
   for (int l = 0; l < MAXL; ++l) {
-    const float ar = 2.f * acc[l].x, ai = 2.f * cs * acc[l].y;
-    c[l] = make_float2(ar * cn - ai * sn, ar * sn + ai * cn);
+    if (l < a.Lp) {
+      const float ar = 2.f * acc[l].x, ai = 2.f * cs * acc[l].y;
+      rc[(size_t)pos * a.Lp + l] = make_float2(ar * cn - ai * sn, ar * sn + ai * cn);
+    }
   }
-  int m0[3];
-  float fr[3];
+}
+
+// 3. Spread the sorted points: warp j takes points [j kNuRun, (j + 1) kNuRun).
+// Lane i owns the footprint cells i, i + 32, ... (R rounds cover w^3 cells) and
+// sums weight x strength of consecutive points with the same start cell in
+// registers; at a change of start cell (and at the end) it adds its cells to
+// the grid with vector float atomics. LG levels from level lg0 per pass.
+template <int R, int LG>
+__global__ void __launch_bounds__(256) k_nu_spread(SpreadArgs a, const int* __restrict__ total_pts,
+                                                   const int4* __restrict__ rm, const float4* __restrict__ rf,
+                                                   const float2* __restrict__ rc, int lg0, float2* __restrict__ F) {
+  const int lane = threadIdx.x & 31;
+  const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int total = *total_pts;
+  const long long i_begin = wid * kNuRun;
+  if (i_begin >= total) return;
+  const int i_end = (int)min((long long)total, i_begin + kNuRun);
+  const int w = a.w, w3 = w * w * w;
+  int ix[R];  // lane's footprint cells: i0 | i1 << 4 | i2 << 8, or -1
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const double g = (x[d] - a.C[d]) * a.invH[d] + 0.5 * a.M[d];
-    int m = (int)ceil(g - 0.5 * a.w);
-    m = min(max(m, 0), a.M[d] - a.w);  // never outside the grid (the plan's margin makes this a no-op)
-    m0[d] = m;
-    fr[d] = (float)((double)m - g);
+  for (int r = 0; r < R; ++r) {
+    const int c = r * 32 + lane;
+    ix[r] = c < w3 ? ((c % w) | (((c / w) % w) << 4) | ((c / (w * w)) << 8)) : -1;
   }
-  const float tw = 2.0f / (float)a.w;
-  float k0[kNuMaxW];
+  float2 acc[R][LG];
 #pragma unroll
-  for (int j = 0; j < kNuMaxW; ++j) k0[j] = (j < a.w) ? es_w((fr[0] + j) * tw, a.beta) : 0.f;
-  for (int j2 = 0; j2 < a.w; ++j2) {
-    const float k2 = es_w((fr[2] + j2) * tw, a.beta);
-    for (int j1 = 0; j1 < a.w; ++j1) {
-      const float k12 = k2 * es_w((fr[1] + j1) * tw, a.beta);
-      const size_t row = ((size_t)(m0[2] + j2) * a.M[1] + (m0[1] + j1)) * a.M[0] + m0[0];
+  for (int r = 0; r < R; ++r)
 #pragma unroll
-      for (int j0 = 0; j0 < kNuMaxW; ++j0) {
-        if (j0 < a.w) {
-          const float wt = k12 * k0[j0];
-          float2* cell = F + (row + j0) * a.Lp;
-          if (MAXL == 1) {
-            atomicAdd(cell, make_float2(wt * c[0].x, wt * c[0].y));
-          } else {
+    for (int l = 0; l < LG; ++l) acc[r][l] = make_float2(0.f, 0.f);
+  const float tw = 2.0f / (float)w;
+  const int kd = lane >> 3, kj = lane & 7;  // lane's kernel value: dimension kd, offset kj
+  auto flush = [&](int4 m) {
 #pragma unroll
-            for (int lp = 0; lp < (MAXL + 1) / 2; ++lp)
-              if (2 * lp < a.L)
-                atomicAdd(reinterpret_cast<float4*>(cell) + lp,
-                          make_float4(wt * c[2 * lp].x, wt * c[2 * lp].y, wt * c[min(2 * lp + 1, MAXL - 1)].x,
-                                      wt * c[min(2 * lp + 1, MAXL - 1)].y));
-          }
+    for (int r = 0; r < R; ++r) {
+      if (ix[r] >= 0) {
+        const int g0 = m.x + (ix[r] & 15), g1 = m.y + ((ix[r] >> 4) & 15), g2 = m.z + (ix[r] >> 8);
+        float2* dst = F + (((size_t)g2 * a.M[1] + g1) * a.M[0] + g0) * a.Lp + lg0;
+        if (LG == 1) {
+          atomicAdd(dst, acc[r][0]);
+        } else {
+#pragma unroll
+          for (int l = 0; l < LG; l += 2)
+            atomicAdd(reinterpret_cast<float4*>(dst + l),
+                      make_float4(acc[r][l].x, acc[r][l].y, acc[r][l + 1].x, acc[r][l + 1].y));
         }
+      }
+#pragma unroll
+      for (int l = 0; l < LG; ++l) acc[r][l] = make_float2(0.f, 0.f);
+    }
+  };
+  int4 cur = rm[i_begin];
+  for (int i = (int)i_begin; i < i_end; ++i) {
+    const int4 m = rm[i];
+    if (m.w != cur.w) {
+      flush(cur);
+      cur = m;
+    }
+    const float4 f = rf[i];
+    float2 c[LG];
+#pragma unroll
+    for (int l = 0; l < LG; ++l) c[l] = rc[(size_t)i * a.Lp + lg0 + l];
+    const float fd = kd == 0 ? f.x : (kd == 1 ? f.y : f.z);
+    const float kv = (kd < 3 && kj < w) ? es_w((fd + kj) * tw, a.beta) : 0.f;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int x = ix[r] < 0 ? 0 : ix[r];
+      const float wt = __shfl_sync(0xffffffffu, kv, x & 15) * __shfl_sync(0xffffffffu, kv, 8 + ((x >> 4) & 15)) *
+                       __shfl_sync(0xffffffffu, kv, 16 + (x >> 8));
+#pragma unroll
+      for (int l = 0; l < LG; ++l) {
+        acc[r][l].x = fmaf(wt, c[l].x, acc[r][l].x);
+        acc[r][l].y = fmaf(wt, c[l].y, acc[r][l].y);
       }
     }
   }
+  flush(cur);
 }
 
 // Zero-baseline terms: cst[l] += sum_{e in l} d_e sum_p |a_pe|^2 for each step.
@@ -452,9 +662,10 @@ NuPlan nu_plan(const NuPixBox& px, int w, float beta, const double* h_st, int N,
   return p;
 }
 
-size_t nu_grid_bytes(const NuPlan& p, int n_level) {
+size_t nu_grid_bytes(const NuPlan& p, int n_level, size_t pair_slots) {
   const int Lp = n_level == 1 ? 1 : n_level + (n_level & 1);
-  return p.cells() * Lp * sizeof(float2) + p.cells2() * sizeof(float2);
+  return p.cells() * (Lp * sizeof(float2) + 3 * sizeof(int)) + p.cells2() * sizeof(float2) +
+         pair_slots * (sizeof(int4) + sizeof(float4) + Lp * sizeof(float2));
 }
 
 int nu_enqueue(const Batch& b, int t0, int t1, const NuPlan& p, NufftWs* w, const double* d_pix, int64_t n_pix,
@@ -511,9 +722,6 @@ int nu_enqueue(const Batch& b, int t0, int t1, const NuPlan& p, NufftWs* w, cons
   if (cudaMemsetAsync(w->cst, 0, sizeof(double) * kMaxLevels, s) != cudaSuccess) return -1;
 
   const int T = t1 - t0;
-  if (ev) cudaEventRecord(ev[0], s);
-  k_nu_const<<<T, 256, 0, s>>>(b, t0, w->cst);
-  ++nl;
   SpreadArgs sa;
   for (int d = 0; d < 3; ++d) {
     sa.M[d] = p.M[d];
@@ -526,13 +734,63 @@ int nu_enqueue(const Batch& b, int t0, int t1, const NuPlan& p, NufftWs* w, cons
   sa.L = n_level;
   sa.Lp = Lp;
   sa.beta = p.beta;
+  // points sorted by the grid cell of their spread start (a counting sort)
+  const int LG = Lp == 1 ? 1 : (Lp % 4 == 0 ? 4 : 2);
+  const size_t ncells = p.cells();
+  if (ncells >= (size_t)1 << 31) return -1;
+  const long long nseg = ((long long)ncells + kSeg - 1) / kSeg;
+  const long long NP = (long long)b.n_max * (b.n_max - 1) / 2;
+  const size_t slots = (size_t)NP * T;
+  if (!grow(&w->count, &w->count_cap, ncells) || !grow(&w->cursor, &w->cursor_cap, ncells) ||
+      !grow(&w->cell_off, &w->cell_off_cap, ncells + 1) || !grow(&w->seg_sum, &w->seg_sum_cap, (size_t)nseg) ||
+      !grow(&w->seg_off, &w->seg_off_cap, (size_t)nseg + 1) || !grow(&w->rm, &w->rm_cap, slots) ||
+      !grow(&w->rf, &w->rf_cap, slots) || !grow(&w->rc, &w->rc_cap, slots * Lp))
+    return -1;
+  if (cudaMemsetAsync(w->count, 0, sizeof(int) * ncells, s) != cudaSuccess) return -1;
+  if (cudaMemsetAsync(w->cursor, 0, sizeof(int) * ncells, s) != cudaSuccess) return -1;
+  int sms = 148, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+
+  if (ev) cudaEventRecord(ev[0], s);
+  k_nu_const<<<T, 256, 0, s>>>(b, t0, w->cst);
+  if (slots > 0) {
+    const unsigned cgrid = (unsigned)std::min<size_t>((slots + 255) / 256, (size_t)sms * 32);
+    k_nu_count<<<cgrid, 256, 0, s>>>(b, t0, T, sa, w->count);
+  }
+  k_nu_seg_sum<<<(unsigned)nseg, 1024, 0, s>>>(w->count, (long long)ncells, w->seg_sum);
+  k_nu_scan<0><<<1, 1024, 0, s>>>(w->seg_sum, (int)nseg, 0, w->seg_off);
+  k_nu_seg_scan<<<(unsigned)nseg, 1024, 0, s>>>(w->count, (long long)ncells, w->seg_off, w->cell_off);
   const int nb = (b.n_max + kTile - 1) / kTile;
   const dim3 grid(nb * (nb + 1) / 2, 1, T);
   dispatch_levels(n_level, [&](auto ML) {
     constexpr int L = decltype(ML)::value;
-    k_nu_spread<L><<<grid, kTile * kTile, 0, s>>>(b, t0, sa, w->F);
+    k_nu_scatter<L><<<grid, kTile * kTile, 0, s>>>(b, t0, sa, w->cell_off, w->cursor, w->rm, w->rf, w->rc);
   });
-  ++nl;
+  nl += 6;
+  if (slots > 0) {
+    const unsigned sgrid = (unsigned)((slots + (size_t)kNuRun * 8 - 1) / ((size_t)kNuRun * 8));
+    const int* total = w->cell_off + ncells;
+    auto spread = [&](auto kern) {
+      for (int g = 0; g < Lp / LG; ++g) {
+        kern<<<sgrid, 256, 0, s>>>(sa, total, w->rm, w->rf, w->rc, g * LG, w->F);
+        ++nl;
+      }
+    };
+    const int w3 = p.w * p.w * p.w;
+    auto by_lg = [&](auto RR) {
+      constexpr int R = decltype(RR)::value;
+      if (LG == 1) spread(k_nu_spread<R, 1>);
+      else if (LG == 2) spread(k_nu_spread<R, 2>);
+      else spread(k_nu_spread<R, 4>);
+    };
+    if (w3 <= 32) by_lg(std::integral_constant<int, 1>{});
+    else if (w3 <= 64) by_lg(std::integral_constant<int, 2>{});
+    else if (w3 <= 128) by_lg(std::integral_constant<int, 4>{});
+    else if (w3 <= 224) by_lg(std::integral_constant<int, 7>{});
+    else if (w3 <= 352) by_lg(std::integral_constant<int, 11>{});
+    else by_lg(std::integral_constant<int, 16>{});
+  }
   if (cudaGetLastError() != cudaSuccess) return -3;
   if (ev) cudaEventRecord(ev[1], s);
 
@@ -570,9 +828,6 @@ int nu_enqueue(const Batch& b, int t0, int t1, const NuPlan& p, NufftWs* w, cons
   ia.beta = p.beta;
   ia.scale = scale;
   ga.Lp = Lp;
-  int sms = 148, dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const unsigned pad_grid = (unsigned)std::min<size_t>((p.cells2() + 255) / 256, (size_t)sms * 16);
   const unsigned pix_grid = (unsigned)((n_pix + 255) / 256);
   for (int l = 0; l < n_level; ++l) {
@@ -594,7 +849,8 @@ int nu_enqueue(const Batch& b, int t0, int t1, const NuPlan& p, NufftWs* w, cons
 
 void nu_free(NufftWs* w) {
   if (w->have_fft) cufftDestroy(w->fft);
-  void* ptrs[] = {w->F, w->G, w->inv, w->corr, w->cst, w->gl};
+  void* ptrs[] = {w->F, w->G, w->inv, w->corr, w->cst, w->gl, w->count, w->cursor, w->cell_off, w->seg_sum,
+                  w->seg_off, w->rm, w->rf, w->rc};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   *w = NufftWs{};

@@ -48,6 +48,23 @@ struct NufftWs {
   float* corr = nullptr; // per pixel 1 / prod_d psi_hat_d(s_d - D_d)
   int64_t corr_cap = 0;
   double* cst = nullptr; // [kMaxLevels] zero-baseline (p = q) terms of the current channel
+  // points sorted by the grid cell of their spread start: counts, cursors, offsets
+  int* count = nullptr;
+  size_t count_cap = 0;
+  int* cursor = nullptr;
+  size_t cursor_cap = 0;
+  int* cell_off = nullptr;  // [cells + 1] exclusive offsets, total at the end
+  size_t cell_off_cap = 0;
+  int* seg_sum = nullptr;   // scan segments' totals and offsets
+  size_t seg_sum_cap = 0;
+  int* seg_off = nullptr;
+  size_t seg_off_cap = 0;
+  int4* rm = nullptr;    // per point: spread start m0 and its cell
+  size_t rm_cap = 0;
+  float4* rf = nullptr;  // per point: fractions m0 - g
+  size_t rf_cap = 0;
+  float2* rc = nullptr;  // per point: Lp pre-phased level strengths
+  size_t rc_cap = 0;
   float* gl = nullptr;   // [2][kNuGL]: Gauss-Legendre nodes z_q and weights w_q phi(z_q) on (0, 1)
   int gl_w = 0;          // kernel width gl was made for
   float gl_beta = 0;
@@ -73,9 +90,9 @@ NuPixBox nu_pixel_box(const double* pix, int64_t n);
 NuPlan nu_plan(const NuPixBox& px, int w, float beta, const double* h_st, int N, const int* nst, const double* wl,
                int t0, int t1);
 
-// Device bytes the plan needs beyond those already allocated (grids only; the
-// FFT's own workspace comes on top).
-size_t nu_grid_bytes(const NuPlan& p, int n_level);
+// Device bytes of the plan's grids and of the sorted point records for
+// pair_slots = steps x n_max (n_max - 1) / 2 (the FFT's own workspace comes on top).
+size_t nu_grid_bytes(const NuPlan& p, int n_level, size_t pair_slots);
 
 // Enqueue the NUFFT synthesis of steps [t0, t1) (one channel) into img
 // (n_level x n_pix FP64, accumulated; skipped when *b.flag is set).
