@@ -106,6 +106,8 @@ def parse():
     ap.add_argument("--n-t", type=int, default=0, help="time steps per imaging job (default 100; 50 for nufft)")
     ap.add_argument("--synthesis", default="standard", choices=["standard", "nufft"])
     ap.add_argument("--nufft-eps", type=float, default=1e-5)
+    ap.add_argument("--nufft-partition", type=int, nargs=6, default=[1, 1, 1, 1, 1, 1],
+                    help="NUFFT domain partitioning: input cells (x y z) then image cells (x y z)")
     ap.add_argument("--side", type=int, default=1024, help="image side in pixels")
     ap.add_argument("--n-st", type=int, default=0, help="keep only the first n stations (small profiling cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -135,7 +137,7 @@ def config_dict(args, inp, precision):
                          f"steps over 6 h per job, wl 2 m, type-3 NUFFT tolerance {args.nufft_eps:g}"),
             "n_st": int(inp.st_xyz[0].shape[0]), "n_pix": int(inp.n_pix), "n_eig": int(inp.n_eig),
             "n_level": int(inp.n_level), "n_t": int(inp.n_t), "synthesis": "nufft",
-            "nufft_eps": args.nufft_eps,
+            "nufft_eps": args.nufft_eps, "nufft_partition": list(args.nufft_partition),
             "eigensolve": EIG_DESC.get(getattr(args, "eig", "jacobi64"), "fp64 parallel-order Jacobi")
             if precision != "fp64 (oracle)" else "fp64 cyclic Jacobi (oracle)",
             "l2": "inputs larger than L2 (visibilities 200 MB per job)",
@@ -254,8 +256,11 @@ def nufft_roofline(nt, n_level, n_pix, n_t, n_st, n_eig, hbm_gbs):
     cells = M[0] * M[1] * M[2]
     cells2 = 8 * cells
     Lp = 1 if n_level == 1 else n_level + (n_level & 1)
+    pts = nt["points"]
     kern = {  # name: (launches per job, ms per launch, algorithmic bytes per launch)
-        "k_nu_spread": (1, nt["spread_ms"], cells * Lp * 8 + n_t * n_eig * n_st * 16 + n_t * n_st * 24),
+        "sort + strengths (k_nu_count, scans, k_nu_scatter)":
+            (1, nt["sort_ms"], n_t * n_eig * n_st * 16 + n_t * n_st * 24 + pts * (32 + 8 * Lp) + cells * 12),
+        "k_nu_spread": (1, nt["spread_ms"], pts * (32 + 8 * Lp) + cells * Lp * 8),
         "k_nu_pad": (n_level, nt["pad_ms"], cells * 8 + cells2 * 8),
         "cuFFT C2C (library)": (n_level, nt["fft_ms"], 2 * cells2 * 8),
         "k_nu_interp": (n_level, nt["interp_ms"], n_pix * (24 + 16 + 4)),
@@ -267,9 +272,10 @@ def nufft_roofline(nt, n_level, n_pix, n_t, n_st, n_eig, hbm_gbs):
             "frac": ach / hbm_gbs,
             "kernels_ms_per_job": {k: v[0] * v[1] for k, v in kern.items()},
             "grid": list(M), "fine_grid_points": cells2,
-            "peak_note": ("of measured: STREAM-style copy; algorithmic bytes = grid written once (spread), "
-                          "one level read + fine grid written (pad), fine grid read + written once (FFT), "
-                          "pixel coordinates + correction + image read/write (interp)")}
+            "peak_note": ("of measured: STREAM-style copy; algorithmic bytes = eigenvectors and stations read, "
+                          "sorted records and cell counts written (sort), sorted records read and the grid "
+                          "written once (spread), one level read + fine grid written (pad), fine grid read + "
+                          "written once (FFT), pixel coordinates + correction + image read/write (interp)")}
 
 
 def main():
@@ -351,7 +357,8 @@ def ours_main(args, ws, rank, local):
     d_V = torch.from_numpy(V).to(f"cuda:{local}")
     stream = torch.cuda.Stream()
     nufft = args.synthesis == "nufft"
-    extra = {"synthesis": "nufft", "nufft_eps": args.nufft_eps} if nufft else {}
+    extra = ({"synthesis": "nufft", "nufft_eps": args.nufft_eps, "nufft_partition": args.nufft_partition}
+             if nufft else {})
     ss = bipp_ss.StandardSynthesis(inp.pix, inp.wl, bounds, n_eig=inp.n_eig, precision=args.precision,
                                    device=local, eig_mode=args.eig, **extra)
 
@@ -368,7 +375,7 @@ def ours_main(args, ws, rank, local):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     stage = np.zeros(4)
-    nu_ms = np.zeros(5)
+    nu_ms = np.zeros(6)
     nu_last = None
     sweeps = 0
     launches = 0
@@ -380,8 +387,8 @@ def ours_main(args, ws, rank, local):
         launches += t["launches"]
         if nufft:
             nu_last = ss.nufft_timings()
-            nu_ms += [nu_last["spread_ms"], nu_last["pad_ms"], nu_last["fft_ms"], nu_last["interp_ms"],
-                      nu_last["levels_ms"]]
+            nu_ms += [nu_last["sort_ms"], nu_last["spread_ms"], nu_last["pad_ms"], nu_last["fft_ms"],
+                      nu_last["interp_ms"], nu_last["levels_ms"]]
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = clk.stop()
@@ -427,7 +434,7 @@ def ours_main(args, ws, rank, local):
                                      "stage time; the QR chase is latency-bound and not in the bound")}
     if nufft:
         nt = dict(nu_last)
-        for i, k in enumerate(["spread_ms", "pad_ms", "fft_ms", "interp_ms", "levels_ms"]):
+        for i, k in enumerate(["sort_ms", "spread_ms", "pad_ms", "fft_ms", "interp_ms", "levels_ms"]):
             nt[k] = nu_ms[i] / K
         roof_synth = nufft_roofline(nt, inp.n_level, inp.n_pix, inp.n_t, n_st, inp.n_eig,
                                     measured_peaks().get("hbm_gbs", 6400.0))
@@ -504,9 +511,10 @@ def ours_main(args, ws, rank, local):
                 "config": config_dict(args, inp, args.precision),
                 "stage_ms_per_step": {"gram_chol_reduce": stage[0] / K, "jacobi": eig_ms,
                                       "select_pack": stage[2] / K, "synthesis": syn_ms},
-                **({"nufft_ms_per_step": {"spread": nu_ms[0] / K, "pad_per_level": nu_ms[1] / K,
-                                          "fft_per_level": nu_ms[2] / K, "interp_per_level": nu_ms[3] / K,
-                                          "levels": nu_ms[4] / K}} if nufft else {}),
+                **({"nufft_ms_per_step": {"sort": nu_ms[0] / K, "spread": nu_ms[1] / K,
+                                          "pad_per_level": nu_ms[2] / K, "fft_per_level": nu_ms[3] / K,
+                                          "interp_per_level": nu_ms[4] / K, "levels": nu_ms[5] / K}}
+                   if nufft else {}),
                 "synthesis_only_value": prods / (syn_ms / 1e3),
                 "roofline": dominant, "roofline_synthesis": roof_synth, "roofline_jacobi": roof_jacobi,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}

@@ -88,7 +88,12 @@ typedef struct {
                                 and n_level = n_eig at create, level_bounds may be NULL; default 0 */
   int32_t synthesis;         /* BIPP_SYNTH_*; default BIPP_SYNTH_STANDARD */
   double nufft_eps;          /* BIPP_SYNTH_NUFFT: type-3 NUFFT tolerance in [1e-7, 0.1]; default 1e-5 */
-  int32_t reserved[4];       /* must be zero */
+  int32_t nufft_partition[6]; /* BIPP_SYNTH_NUFFT domain partitioning (Sec. 3.4.1), each in [1, 64]:
+                                 [0..2] input cells of the baseline box per dimension (x, y, z),
+                                 [3..5] image cells of the pixels' box per dimension; each non-empty
+                                 (input, image) cell pair is one type-3 transform whose grid spans
+                                 that cell only. Default all 1 (one transform per level) */
+  int32_t reserved[2];       /* must be zero */
 } bipp_ss_options;
 
 /* Image synthesis strategy (Sec. 2.5, 3.4).
@@ -202,13 +207,14 @@ int bipp_ss_get_timings(bipp_ss_t h, double* out6);
 
 /* Kernel times of the last collect's NUFFT synthesis (BIPP_SYNTH_NUFFT; CUDA
  * events on the collect's stream, first channel of the batch):
- * out[0] level strengths + spreading (k_nu_const + k_nu_spread) [ms],
- * out[1] one level's deconvolve/pad (k_nu_pad) [ms], out[2] one level's FFT
- * (cuFFT) [ms], out[3] one level's interpolation (k_nu_interp) [ms],
- * out[4] all levels' pad + FFT + interpolation [ms], out[5..7] the spread
- * grid's points per dimension (M), out[8] the kernel width w. Zeros for
- * STANDARD. */
-int bipp_ss_get_nufft_timings(bipp_ss_t h, double* out9);
+ * out[0] sorting the baselines and forming their level strengths (k_nu_const,
+ * k_nu_count, the scans, k_nu_scatter) [ms], out[1] spreading (k_nu_spread,
+ * all level groups) [ms], out[2] one level's deconvolve/pad (k_nu_pad) [ms],
+ * out[3] one level's FFT (cuFFT) [ms], out[4] one level's interpolation
+ * (k_nu_interp) [ms], out[5] all levels' pad + FFT + interpolation [ms],
+ * out[6..8] the spread grid's points per dimension (M), out[9] the kernel
+ * width w, out[10] the number of baselines spread. Zeros for STANDARD. */
+int bipp_ss_get_nufft_timings(bipp_ss_t h, double* out11);
 
 /* Differentiable synthesis with complex station gains (device pointers,
  * e.g. PyTorch memory; stream-ordered on `stream`, NULL = default stream;

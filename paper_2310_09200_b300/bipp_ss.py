@@ -70,7 +70,8 @@ class bipp_ss_options(C.Structure):
         ("n_eig", C.c_int32), ("precision", C.c_int32), ("filter", C.c_int32), ("gram_identity", C.c_int32),
         ("max_jacobi_sweeps", C.c_int32), ("jacobi_tol", C.c_double), ("device", C.c_int32),
         ("eig_mode", C.c_int32), ("use_graph", C.c_int32), ("autotune", C.c_int32), ("eigenimages", C.c_int32),
-        ("synthesis", C.c_int32), ("nufft_eps", C.c_double), ("reserved", C.c_int32 * 4),
+        ("synthesis", C.c_int32), ("nufft_eps", C.c_double), ("nufft_partition", C.c_int32 * 6),
+        ("reserved", C.c_int32 * 2),
     ]
 
 
@@ -145,6 +146,8 @@ def bipp_ss_default_options(**kw) -> bipp_ss_options:
     for k, v in kw.items():
         if k in names and isinstance(v, str):
             v = names[k][v]
+        if k == "nufft_partition":  # (uvw cells, image cells), each a triple
+            v = (C.c_int32 * 6)(*[int(x) for x in np.ravel(v)])
         setattr(o, k, int(v) if isinstance(v, bool) else v)
     return o
 
@@ -319,10 +322,10 @@ def bipp_ss_get_timings(h) -> dict:
 
 
 def bipp_ss_get_nufft_timings(h) -> dict:
-    a = np.zeros(9, dtype=np.float64)
+    a = np.zeros(11, dtype=np.float64)
     _check(h, load().bipp_ss_get_nufft_timings(h, _dp(a)))
-    return {"spread_ms": a[0], "pad_ms": a[1], "fft_ms": a[2], "interp_ms": a[3], "levels_ms": a[4],
-            "grid": (int(a[5]), int(a[6]), int(a[7])), "w": int(a[8])}
+    return {"sort_ms": a[0], "spread_ms": a[1], "pad_ms": a[2], "fft_ms": a[3], "interp_ms": a[4],
+            "levels_ms": a[5], "grid": (int(a[6]), int(a[7]), int(a[8])), "w": int(a[9]), "points": int(a[10])}
 
 
 def bipp_ss_destroy(h) -> None:

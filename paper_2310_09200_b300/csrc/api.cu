@@ -89,7 +89,8 @@ struct bipp_ss {
   MixedWs mx{};
   int mixed_kp = 0;  // KP of the current batch when the mixed eigensolver runs, else 0
   // NUFFT synthesis: pixel box, kernel, and the current batch's per-channel plans
-  NuPixBox nu_px{};
+  NuPixCells nu_cells;     // image cells (pixels sorted by cell, ranges, boxes)
+  int* d_nu_order = nullptr;  // the sorted pixel order on the device
   int nu_w = 0;
   float nu_beta = 0.f;
   NufftWs nu;
@@ -97,8 +98,8 @@ struct bipp_ss {
   std::vector<int> nu_t0;  // first step of each channel group, plus n_t at the end
   std::vector<double> nu_st;  // host copy of device station coordinates
   int nu_launches = 0;
-  cudaEvent_t nu_ev[7] = {};
-  double nu_timings[9] = {};
+  cudaEvent_t nu_ev[8] = {};
+  double nu_timings[11] = {};
   // graph cache: the last geometry seen, and the captured graph of it
   GraphKey last_key;
   bool have_key = false;
@@ -246,6 +247,7 @@ extern "C" void bipp_ss_default_options(bipp_ss_options* opt) {
   opt->autotune = 1;
   opt->synthesis = BIPP_SYNTH_STANDARD;
   opt->nufft_eps = 1e-5;
+  for (int i = 0; i < 6; ++i) opt->nufft_partition[i] = 1;
 }
 
 extern "C" int bipp_ss_destroy(bipp_ss_t h) {
@@ -254,6 +256,7 @@ extern "C" int bipp_ss_destroy(bipp_ss_t h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   free_batch(h);
   nu_free(&h->nu);
+  if (h->d_nu_order) cudaFree(h->d_nu_order);
   if (h->d_pix) cudaFree(h->d_pix);
   if (h->d_pix_hl) cudaFree(h->d_pix_hl);
   if (h->d_img) cudaFree(h->d_img);
@@ -277,8 +280,11 @@ extern "C" int bipp_ss_create_channels(bipp_ss_t* out, int64_t n_pix, const doub
       return fail(nullptr, BIPP_ERR_INVALID_ARG, "wavelength of channel %d must be finite and > 0", c);
   bipp_ss_options o;
   if (opt) o = *opt; else bipp_ss_default_options(&o);
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 2; ++i)
     if (o.reserved[i]) return fail(nullptr, BIPP_ERR_INVALID_ARG, "reserved option fields must be zero");
+  for (int i = 0; i < 6; ++i)
+    if (o.nufft_partition[i] < 1 || o.nufft_partition[i] > 64)
+      return fail(nullptr, BIPP_ERR_INVALID_ARG, "nufft_partition[%d] must be in [1, 64]", i);
   if (o.synthesis != BIPP_SYNTH_STANDARD && o.synthesis != BIPP_SYNTH_NUFFT)
     return fail(nullptr, BIPP_ERR_INVALID_ARG, "unknown synthesis %d", o.synthesis);
   int nu_w = 0;
@@ -287,6 +293,7 @@ extern "C" int bipp_ss_create_channels(bipp_ss_t* out, int64_t n_pix, const doub
     if (!nu_kernel_params(o.nufft_eps, &nu_w, &nu_beta))
       return fail(nullptr, BIPP_ERR_INVALID_ARG, "nufft_eps must be in [1e-7, 0.1]");
     if (o.eigenimages) return fail(nullptr, BIPP_ERR_UNSUPPORTED, "NUFFT synthesis makes level images, not eigenimages");
+    if (n_pix >= ((int64_t)1 << 31)) return fail(nullptr, BIPP_ERR_UNSUPPORTED, "NUFFT synthesis needs n_pix < 2^31");
   }
   if (o.eigenimages != 0 && o.eigenimages != 1)
     return fail(nullptr, BIPP_ERR_INVALID_ARG, "eigenimages must be 0 or 1");
@@ -320,7 +327,7 @@ extern "C" int bipp_ss_create_channels(bipp_ss_t* out, int64_t n_pix, const doub
   h->wl.assign(wl, wl + n_chan);
   h->nu_w = nu_w;
   h->nu_beta = nu_beta;
-  if (o.synthesis == BIPP_SYNTH_NUFFT) h->nu_px = nu_pixel_box(pix_xyz, n_pix);
+  if (o.synthesis == BIPP_SYNTH_NUFFT) h->nu_cells = nu_pixel_cells(pix_xyz, n_pix, o.nufft_partition + 3);
   if (o.device >= 0 && cudaSetDevice(o.device) != cudaSuccess) {
     delete h;
     return fail(nullptr, BIPP_ERR_CUDA, "cudaSetDevice(%d) failed", o.device);
@@ -347,6 +354,12 @@ extern "C" int bipp_ss_create_channels(bipp_ss_t* out, int64_t n_pix, const doub
   if ((e = dalloc(&h->d_bounds, (size_t)2 * n_level * n_chan)) != cudaSuccess) return bail(BIPP_ERR_OUT_OF_MEMORY, "bounds", e);
   if ((e = cudaMemcpy(h->d_pix, pix_xyz, sizeof(double) * 3 * n_pix, cudaMemcpyHostToDevice)) != cudaSuccess)
     return bail(BIPP_ERR_CUDA, "pixel upload", e);
+  if (o.synthesis == BIPP_SYNTH_NUFFT) {
+    if ((e = dalloc(&h->d_nu_order, (size_t)n_pix)) != cudaSuccess) return bail(BIPP_ERR_OUT_OF_MEMORY, "pixel order", e);
+    if ((e = cudaMemcpy(h->d_nu_order, h->nu_cells.order.data(), sizeof(int) * n_pix, cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+      return bail(BIPP_ERR_CUDA, "pixel order upload", e);
+  }
   if (o.eigenimages) {  // levels are ranks; the bounds are unused
     if ((e = cudaMemset(h->d_bounds, 0, sizeof(double) * 2 * n_level * n_chan)) != cudaSuccess)
       return bail(BIPP_ERR_CUDA, "bounds", e);
@@ -443,14 +456,21 @@ static int enqueue_batch(bipp_ss* h, const Batch& b, const TcPlan& plan, cudaStr
   Pixels px{h->n_pix, h->d_pix, h->d_pix_hl};
   if (h->opt.synthesis == BIPP_SYNTH_NUFFT) {
     h->nu_launches = 0;
+    const int nc = (int)h->nu_cells.box.size();
+    bool first = true;
     for (size_t g = 0; g + 1 < h->nu_t0.size(); ++g) {
       const int t0 = h->nu_t0[g], t1 = h->nu_t0[g + 1];
       double* img = h->d_img + (size_t)h->h_chan[t0] * h->n_level * h->n_pix;
-      const int rc = nu_enqueue(b, t0, t1, h->nu_plans[g], &h->nu, h->d_pix, h->n_pix, h->n_level, img, s,
-                                &h->nu_launches, g == 0 ? h->nu_ev : nullptr);
-      if (rc == -1) return fail(h, BIPP_ERR_OUT_OF_MEMORY, "NUFFT grid allocation failed");
-      if (rc == -2) return fail(h, BIPP_ERR_CUDA, "NUFFT: cuFFT plan or execution failed");
-      if (rc) return fail(h, BIPP_ERR_CUDA, "NUFFT kernel launch failed");
+      for (int c = 0; c < nc; ++c) {
+        const int64_t off = h->nu_cells.off[c], cnt = h->nu_cells.off[c + 1] - off;
+        if (cnt == 0) continue;
+        const int rc = nu_enqueue(b, t0, t1, h->nu_plans[g * nc + c], &h->nu, h->d_pix, h->n_pix, h->d_nu_order,
+                                  off, cnt, c, nc, h->n_level, img, s, &h->nu_launches, first ? h->nu_ev : nullptr);
+        first = false;
+        if (rc == -1) return fail(h, BIPP_ERR_OUT_OF_MEMORY, "NUFFT grid allocation failed");
+        if (rc == -2) return fail(h, BIPP_ERR_CUDA, "NUFFT: cuFFT plan or execution failed");
+        if (rc) return fail(h, BIPP_ERR_CUDA, "NUFFT kernel launch failed");
+      }
     }
     CUDA_TRY(h, cudaGetLastError());
     CUDA_TRY(h, record(h->ev[4], s));
@@ -486,27 +506,34 @@ static int plan_nufft(bipp_ss* h, int n_t, int N, const std::vector<int>& nst_v,
   for (int t = 0; t < n_t; ++t)
     if (t == 0 || chan_v[t] != chan_v[t - 1]) h->nu_t0.push_back(t);
   h->nu_t0.push_back(n_t);
-  for (size_t g = 0; g + 1 < h->nu_t0.size(); ++g) {
-    const NuPlan p = nu_plan(h->nu_px, h->nu_w, h->nu_beta, h_st, N, nst_v.data(), wl_t.data(), h->nu_t0[g],
-                             h->nu_t0[g + 1]);
-    for (int d = 0; d < 3; ++d)
-      if (p.M[d] > (1 << 28))
-        return fail(h, BIPP_ERR_UNSUPPORTED, "NUFFT grid dimension %d needs %d points", d, p.M[d]);
-    const size_t slots = (size_t)(h->nu_t0[g + 1] - h->nu_t0[g]) * N * (N - 1) / 2;
-    need = std::max(need, nu_grid_bytes(p, h->n_level, slots));
-    h->nu_plans.push_back(p);
-  }
+  const int nc = (int)h->nu_cells.box.size();
+  size_t fine = 0;
+  for (size_t g = 0; g + 1 < h->nu_t0.size(); ++g)
+    for (int c = 0; c < nc; ++c) {
+      const NuPlan p = nu_plan(h->nu_cells.box[c], h->nu_w, h->nu_beta, h->opt.nufft_partition, h_st, N,
+                               nst_v.data(), wl_t.data(), h->nu_t0[g], h->nu_t0[g + 1]);
+      h->nu_plans.push_back(p);
+      if (h->nu_cells.off[c + 1] == h->nu_cells.off[c]) continue;  // empty image cell: no transform
+      for (int d = 0; d < 3; ++d)
+        if (p.M[d] > (1 << 28))
+          return fail(h, BIPP_ERR_UNSUPPORTED, "NUFFT grid dimension %d needs %d points", d, p.M[d]);
+      if ((size_t)p.parts() * p.cells() >= ((size_t)1 << 31))
+        return fail(h, BIPP_ERR_UNSUPPORTED, "NUFFT grids of %d input cells x %zu points exceed 2^31 points",
+                    p.parts(), p.cells());
+      const size_t slots = (size_t)(h->nu_t0[g + 1] - h->nu_t0[g]) * N * (N - 1) / 2;
+      need = std::max(need, nu_grid_bytes(p, h->n_level, slots));
+      fine = std::max(fine, p.cells2() * sizeof(float2));
+    }
   size_t free_b = 0, total_b = 0;
   CUDA_TRY(h, cudaMemGetInfo(&free_b, &total_b));
   const size_t have = (h->nu.F_cap + h->nu.G_cap + h->nu.rc_cap) * sizeof(float2) +
                       (h->nu.rm_cap + h->nu.rf_cap) * sizeof(int4);
   // grids plus the FFT's workspace (of the order of the fine grid) must fit
-  const NuPlan& p0 = h->nu_plans[0];
-  if (need + p0.cells2() * sizeof(float2) > free_b + have)
+  if (need + fine > free_b + have)
     return fail(h, BIPP_ERR_UNSUPPORTED,
-                "NUFFT grids need %.1f GB (spread grid %d x %d x %d, FFT grid x8) but %.1f GB are free; "
-                "image a smaller field or fewer steps per batch",
-                (need + p0.cells2() * sizeof(float2)) / 1e9, p0.M[0], p0.M[1], p0.M[2], (free_b + have) / 1e9);
+                "NUFFT grids need %.1f GB but %.1f GB are free; partition the domain (nufft_partition), "
+                "image a smaller field or collect fewer steps per batch",
+                (need + fine) / 1e9, (free_b + have) / 1e9);
   return BIPP_OK;
 }
 
@@ -606,8 +633,8 @@ static int run_batch(bipp_ss* h, int n_t, int N, const std::vector<int>& nst_v, 
   for (int i = 0; i < 4; ++i) h->timings[i] = ms[i];
   for (double& v : h->nu_timings) v = 0.0;
   if (nufft) {
-    const int pairs[5][2] = {{0, 1}, {2, 3}, {3, 4}, {4, 5}, {2, 6}};
-    for (int i = 0; i < 5; ++i) {
+    const int pairs[6][2] = {{0, 7}, {7, 1}, {2, 3}, {3, 4}, {4, 5}, {2, 6}};
+    for (int i = 0; i < 6; ++i) {
       float v = 0.f;
       if (cudaEventElapsedTime(&v, h->nu_ev[pairs[i][0]], h->nu_ev[pairs[i][1]]) != cudaSuccess) {
         v = NAN;
@@ -615,8 +642,11 @@ static int run_batch(bipp_ss* h, int n_t, int N, const std::vector<int>& nst_v, 
       }
       h->nu_timings[i] = v;
     }
-    for (int d = 0; d < 3; ++d) h->nu_timings[5 + d] = h->nu_plans[0].M[d];
-    h->nu_timings[8] = h->nu_plans[0].w;
+    for (int d = 0; d < 3; ++d) h->nu_timings[6 + d] = h->nu_plans[0].M[d];
+    h->nu_timings[9] = h->nu_plans[0].w;
+    double pairs_spread = 0;
+    for (int t = h->nu_t0[0]; t < h->nu_t0[1]; ++t) pairs_spread += 0.5 * (double)nst_v[t] * (nst_v[t] - 1);
+    h->nu_timings[10] = pairs_spread;
   }
   h->timings[4] = 0;
   for (int t = 0; t < n_t; ++t) h->timings[4] += sweeps[t];
@@ -773,10 +803,10 @@ extern "C" int bipp_ss_get_timings(bipp_ss_t h, double* out6) {
   return BIPP_OK;
 }
 
-extern "C" int bipp_ss_get_nufft_timings(bipp_ss_t h, double* out9) {
+extern "C" int bipp_ss_get_nufft_timings(bipp_ss_t h, double* out11) {
   if (!h) return fail(nullptr, BIPP_ERR_INVALID_ARG, "handle is NULL");
-  if (!out9) return fail(h, BIPP_ERR_INVALID_ARG, "out9 is NULL");
-  for (int i = 0; i < 9; ++i) out9[i] = h->nu_timings[i];
+  if (!out11) return fail(h, BIPP_ERR_INVALID_ARG, "out11 is NULL");
+  for (int i = 0; i < 11; ++i) out11[i] = h->nu_timings[i];
   return BIPP_OK;
 }
 

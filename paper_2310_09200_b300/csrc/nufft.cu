@@ -103,17 +103,22 @@ double es_ft_host(double xi, double alpha, double beta, const double* z, const d
 
 struct SpreadArgs {
   int M[3];
-  double C[3], invH[3], D[3];
+  double invH[3], D[3];
+  int P[3];                // input cells per dimension
+  double lo[3], delta[3];  // input box corner and cell size
+  double idelta[3];        // 1 / delta (0 for a single cell)
+  long long cells;         // grid points of one input cell's grid
   int fold, w, L, Lp;
   float beta;
 };
 
-// Oriented coordinates, spread start m0 (inside the grid) and fraction m0 - g of
-// the pair (p, q) of step t.
+// Oriented coordinates, input cell, spread start m0 (inside the cell's grid) and
+// fraction m0 - g of the pair (p, q) of step t.
 struct PairGeo {
   double x[3];
   int m0[3];
   float fr[3];
+  int pid;
   bool flip;
 };
 
@@ -130,20 +135,26 @@ __device__ __forceinline__ PairGeo pair_geo(const Batch& b, int t, int p, int q,
 #pragma unroll
     for (int d = 0; d < 3; ++d) g.x[d] = -g.x[d];
   }
+  int ci[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const double gg = (g.x[d] - a.C[d]) * a.invH[d] + 0.5 * a.M[d];
+    int c = a.P[d] > 1 ? (int)floor((g.x[d] - a.lo[d]) * a.idelta[d]) : 0;
+    c = min(max(c, 0), a.P[d] - 1);
+    ci[d] = c;
+    const double C = a.lo[d] + (c + 0.5) * a.delta[d];
+    const double gg = (g.x[d] - C) * a.invH[d] + 0.5 * a.M[d];
     int m = (int)ceil(gg - 0.5 * a.w);
     m = min(max(m, 0), a.M[d] - a.w);  // never outside the grid (the plan's margin makes this a no-op)
     g.m0[d] = m;
     g.fr[d] = (float)((double)m - gg);
   }
+  g.pid = (ci[2] * a.P[1] + ci[1]) * a.P[0] + ci[0];
   return g;
 }
 
-// Sort key of a point: the grid cell of its spread start.
+// Sort key of a point: its input cell, then the grid cell of its spread start.
 __device__ __forceinline__ int cell_of(const PairGeo& g, const SpreadArgs& a) {
-  return (g.m0[2] * a.M[1] + g.m0[1]) * a.M[0] + g.m0[0];
+  return (int)(g.pid * a.cells + ((long long)g.m0[2] * a.M[1] + g.m0[1]) * a.M[0] + g.m0[0]);
 }
 
 // Pair index r -> (p, q), p < q, r = q (q - 1) / 2 + p.
@@ -393,7 +404,8 @@ __global__ void __launch_bounds__(256) k_nu_spread(SpreadArgs a, const int* __re
     for (int r = 0; r < R; ++r) {
       if (ix[r] >= 0) {
         const int g0 = m.x + (ix[r] & 15), g1 = m.y + ((ix[r] >> 4) & 15), g2 = m.z + (ix[r] >> 8);
-        float2* dst = F + (((size_t)g2 * a.M[1] + g1) * a.M[0] + g0) * a.Lp + lg0;
+        const size_t base = (size_t)(m.w / a.cells) * a.cells;  // the input cell's grid
+        float2* dst = F + (base + ((size_t)g2 * a.M[1] + g1) * a.M[0] + g0) * a.Lp + lg0;
         if (LG == 1) {
           atomicAdd(dst, acc[r][0]);
         } else {
@@ -460,23 +472,31 @@ __global__ void k_nu_const(Batch b, int t0, double* cst) {
   }
 }
 
-// Per pixel 1 / prod_d psi_hat_d(s_d - D_d), psi_hat_d(xi) = alpha_d phi_hat(alpha_d xi), alpha_d = pi w Hc_d.
-__global__ void k_nu_corr(const double* __restrict__ pix, int64_t n, double D0, double D1, double D2, float al0,
-                          float al1, float al2, const float* __restrict__ gl, float* __restrict__ corr) {
+// Per pixel j of a cell (pixel order[j]): 1 / prod_d psi_hat_d(s_d - D_d),
+// psi_hat_d(xi) = alpha_d phi_hat(alpha_d xi), alpha_d = pi w Hc_d.
+__global__ void k_nu_corr(const double* __restrict__ pix, int64_t n, const int* __restrict__ order, int64_t cnt,
+                          double D0, double D1, double D2, float al0, float al1, float al2, const float* __restrict__ gl,
+                          float* __restrict__ corr) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
+  if (j >= cnt) return;
+  const int64_t px = order[j];
   const double D[3] = {D0, D1, D2};
   const float al[3] = {al0, al1, al2};
   float prod = 1.f;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const float k = al[d] * (float)(pix[(size_t)d * n + j] - D[d]);
+    const float k = al[d] * (float)(pix[(size_t)d * n + px] - D[d]);
     float s = 0.f;
 #pragma unroll 8
     for (int q = 0; q < kNuGL; ++q) s = fmaf(gl[kNuGL + q], cosf(k * gl[q]), s);
     prod *= 2.f * al[d] * s;
   }
   corr[j] = 1.f / prod;
+}
+
+// First sorted point of each input cell: bnd[i] = cell_off[i * cells], i <= parts.
+__global__ void k_nu_bounds(const int* __restrict__ cell_off, long long cells, int parts, int* __restrict__ bnd) {
+  for (int i = threadIdx.x; i <= parts; i += blockDim.x) bnd[i] = cell_off[(size_t)i * cells];
 }
 
 struct GridArgs {
@@ -517,17 +537,22 @@ struct InterpArgs {
   double scale;              // trapezoid factor prod_d (2 pi Hc_d)(2 pi / N2_d)
 };
 
-__global__ void k_nu_interp(const double* __restrict__ pix, int64_t n, InterpArgs a, const float2* __restrict__ G,
-                            const float* __restrict__ corr, const double* __restrict__ cst, int l,
-                            const int* __restrict__ flag, double* __restrict__ img) {
+// Pixel j of a cell (pixel order[j]) of level l: the transform of one input
+// cell, interpolated, corrected and post-phased; Re added to the image, plus
+// the level's zero-baseline constant when add_cst.
+__global__ void k_nu_interp(const double* __restrict__ pix, int64_t n, const int* __restrict__ order, int64_t cnt,
+                            InterpArgs a, const float2* __restrict__ G, const float* __restrict__ corr,
+                            const double* __restrict__ cst, int add_cst, int l, const int* __restrict__ flag,
+                            double* __restrict__ img) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n || *flag) return;
+  if (j >= cnt || *flag) return;
+  const int64_t px = order[j];
   double sp[3];
   int m0[3];
   float fr[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    sp[d] = pix[(size_t)d * n + j] - a.D[d];
+    sp[d] = pix[(size_t)d * n + px] - a.D[d];
     const double tg = sp[d] * a.HN[d];
     const int m = (int)ceil(tg - 0.5 * a.w);
     fr[d] = (float)((double)m - tg);
@@ -573,7 +598,7 @@ __global__ void k_nu_interp(const double* __restrict__ pix, int64_t n, InterpArg
   float sn, cn;
   sincospif(2.0f * (float)(ph - rint(ph)), &sn, &cn);
   const double re = (double)(sr * cn - si * sn) * (double)corr[j] * a.scale;
-  img[(size_t)l * n + j] += re + cst[l];
+  img[(size_t)l * n + px] += re + (add_cst ? cst[l] : 0.0);
 }
 
 template <typename F>
@@ -610,22 +635,53 @@ bool nu_kernel_params(double eps, int* w, float* beta) {
   return true;
 }
 
-NuPixBox nu_pixel_box(const double* pix, int64_t n) {
-  NuPixBox b;
+NuPixCells nu_pixel_cells(const double* pix, int64_t n, const int P[3]) {
+  double lo[3], hi[3];
   for (int d = 0; d < 3; ++d) {
-    double lo = pix[(size_t)d * n], hi = lo;
+    lo[d] = hi[d] = pix[(size_t)d * n];
     for (int64_t j = 1; j < n; ++j) {
-      lo = std::min(lo, pix[(size_t)d * n + j]);
-      hi = std::max(hi, pix[(size_t)d * n + j]);
+      lo[d] = std::min(lo[d], pix[(size_t)d * n + j]);
+      hi[d] = std::max(hi[d], pix[(size_t)d * n + j]);
     }
-    b.D[d] = 0.5 * (lo + hi);
-    b.S[d] = 0.5 * (hi - lo);
   }
-  return b;
+  const int nc = P[0] * P[1] * P[2];
+  std::vector<int> cell(n);
+  std::vector<int64_t> cnt(nc, 0);
+  for (int64_t j = 0; j < n; ++j) {
+    int ci[3];
+    for (int d = 0; d < 3; ++d) {
+      const double wd = hi[d] - lo[d];
+      int c = wd > 0.0 ? (int)floor((pix[(size_t)d * n + j] - lo[d]) / wd * P[d]) : 0;
+      ci[d] = std::min(std::max(c, 0), P[d] - 1);
+    }
+    cell[j] = (ci[2] * P[1] + ci[1]) * P[0] + ci[0];
+    ++cnt[cell[j]];
+  }
+  NuPixCells out;
+  out.off.assign(nc + 1, 0);
+  for (int c = 0; c < nc; ++c) out.off[c + 1] = out.off[c] + cnt[c];
+  out.order.resize(n);
+  std::vector<int64_t> cur(out.off.begin(), out.off.end() - 1);
+  for (int64_t j = 0; j < n; ++j) out.order[cur[cell[j]]++] = (int)j;
+  out.box.resize(nc);
+  for (int c = 0; c < nc; ++c) {
+    NuPixBox& b = out.box[c];
+    for (int d = 0; d < 3; ++d) {
+      double l = 0.0, h = 0.0;
+      for (int64_t k = out.off[c]; k < out.off[c + 1]; ++k) {
+        const double v = pix[(size_t)d * n + out.order[k]];
+        if (k == out.off[c] || v < l) l = v;
+        if (k == out.off[c] || v > h) h = v;
+      }
+      b.D[d] = 0.5 * (l + h);
+      b.S[d] = 0.5 * (h - l);
+    }
+  }
+  return out;
 }
 
-NuPlan nu_plan(const NuPixBox& px, int w, float beta, const double* h_st, int N, const int* nst, const double* wl,
-               int t0, int t1) {
+NuPlan nu_plan(const NuPixBox& px, int w, float beta, const int P[3], const double* h_st, int N, const int* nst,
+               const double* wl, int t0, int t1) {
   NuPlan p;
   p.w = w;
   p.beta = beta;
@@ -646,8 +702,10 @@ NuPlan nu_plan(const NuPixBox& px, int w, float beta, const double* h_st, int N,
   p.fold = fold;
   for (int d = 0; d < 3; ++d) {
     const double lo = (d == fold) ? 0.0 : -R[d], hi = R[d];
-    const double X = 0.5 * (hi - lo), S = px.S[d];
-    p.C[d] = 0.5 * (hi + lo);
+    p.P[d] = P[d];
+    p.lo[d] = lo;
+    p.delta[d] = (hi - lo) / P[d];
+    const double X = 0.5 * p.delta[d], S = px.S[d];  // half-widths of one input cell and of the targets
     p.D[d] = px.D[d];
     const long long need = (long long)ceil(4.0 * kSigma * X * S * (1.0 + 1e-12)) + w + 2;
     p.M[d] = (int)next_smooth(std::max<long long>(2 * w, need));
@@ -664,21 +722,27 @@ NuPlan nu_plan(const NuPixBox& px, int w, float beta, const double* h_st, int N,
 
 size_t nu_grid_bytes(const NuPlan& p, int n_level, size_t pair_slots) {
   const int Lp = n_level == 1 ? 1 : n_level + (n_level & 1);
-  return p.cells() * (Lp * sizeof(float2) + 3 * sizeof(int)) + p.cells2() * sizeof(float2) +
+  return (size_t)p.parts() * p.cells() * (Lp * sizeof(float2) + 3 * sizeof(int)) + p.cells2() * sizeof(float2) +
          pair_slots * (sizeof(int4) + sizeof(float4) + Lp * sizeof(float2));
 }
 
 int nu_enqueue(const Batch& b, int t0, int t1, const NuPlan& p, NufftWs* w, const double* d_pix, int64_t n_pix,
-               int n_level, double* img, cudaStream_t s, int* launches, const cudaEvent_t* ev) {
+               const int* d_order, int64_t pix_off, int64_t pix_cnt, int cell, int n_cells, int n_level,
+               double* img, cudaStream_t s, int* launches, const cudaEvent_t* ev) {
   const int Lp = n_level == 1 ? 1 : n_level + (n_level & 1);
+  const int parts = p.parts();
+  const size_t cells = p.cells();
+  const size_t nkeys = (size_t)parts * cells;  // sort keys: input cell, then start cell
+  if (nkeys >= (size_t)1 << 31) return -1;
   int nl = 0;
-  if (!grow(&w->F, &w->F_cap, p.cells() * Lp)) return -1;
+  if (!grow(&w->F, &w->F_cap, nkeys * Lp)) return -1;
   if (!grow(&w->G, &w->G_cap, p.cells2())) return -1;
   if (!grow(&w->inv, &w->inv_cap, (size_t)p.M[0] + p.M[1] + p.M[2])) return -1;
   size_t corr_cap = (size_t)w->corr_cap;
   if (!grow(&w->corr, &corr_cap, (size_t)n_pix)) return -1;
-  if ((int64_t)corr_cap != w->corr_cap) w->corr_valid = false;
+  if ((int64_t)corr_cap != w->corr_cap || (int)w->corr_key.size() != n_cells) w->corr_key.assign(n_cells, {});
   w->corr_cap = (int64_t)corr_cap;
+  if (!grow(&w->bnd, &w->bnd_cap, (size_t)parts + 1)) return -1;
   if (!w->cst && cudaMalloc(&w->cst, sizeof(double) * kMaxLevels) != cudaSuccess) return -1;
 
   double z[kNuGL], wq[kNuGL];
@@ -693,22 +757,17 @@ int nu_enqueue(const Batch& b, int t0, int t1, const NuPlan& p, NufftWs* w, cons
     if (cudaMemcpy(w->gl, hg, sizeof(hg), cudaMemcpyHostToDevice) != cudaSuccess) return -1;
     w->gl_w = p.w;
     w->gl_beta = p.beta;
-    w->corr_valid = false;
+    w->corr_key.assign(n_cells, {});
   }
-  // per-pixel correction: depends on the pixels, the kernel and the spacing only
-  bool same = w->corr_valid && w->corr_w == p.w;
-  for (int d = 0; d < 3; ++d) same = same && w->corr_Hc[d] == p.Hc[d] && w->corr_D[d] == p.D[d];
-  if (!same) {
+  // per-pixel correction of this image cell: depends on its pixels, the kernel and the spacing only
+  const std::vector<double> key = {(double)p.w, p.Hc[0], p.Hc[1], p.Hc[2], p.D[0], p.D[1], p.D[2]};
+  if (w->corr_key[cell] != key && pix_cnt > 0) {
     const float al[3] = {(float)(M_PI * p.w * p.Hc[0]), (float)(M_PI * p.w * p.Hc[1]), (float)(M_PI * p.w * p.Hc[2])};
-    k_nu_corr<<<(unsigned)((n_pix + 255) / 256), 256, 0, s>>>(d_pix, n_pix, p.D[0], p.D[1], p.D[2], al[0], al[1], al[2],
-                                                               w->gl, w->corr);
+    k_nu_corr<<<(unsigned)((pix_cnt + 255) / 256), 256, 0, s>>>(d_pix, n_pix, d_order + pix_off, pix_cnt, p.D[0],
+                                                                p.D[1], p.D[2], al[0], al[1], al[2], w->gl,
+                                                                w->corr + pix_off);
     ++nl;
-    w->corr_valid = true;
-    w->corr_w = p.w;
-    for (int d = 0; d < 3; ++d) {
-      w->corr_Hc[d] = p.Hc[d];
-      w->corr_D[d] = p.D[d];
-    }
+    w->corr_key[cell] = key;
   }
   // 1 / psi2_hat per mode, alpha2 = pi w / N2
   w->h_inv.resize((size_t)p.M[0] + p.M[1] + p.M[2]);
@@ -718,36 +777,38 @@ int nu_enqueue(const Batch& b, int t0, int t1, const NuPlan& p, NufftWs* w, cons
     for (int m = 0; m < p.M[d]; ++m) w->h_inv[o++] = (float)(1.0 / es_ft_host(m - p.M[d] / 2, al2, p.beta, z, wq));
   }
   if (cudaMemcpyAsync(w->inv, w->h_inv.data(), sizeof(float) * o, cudaMemcpyHostToDevice, s) != cudaSuccess) return -1;
-  if (cudaMemsetAsync(w->F, 0, sizeof(float2) * p.cells() * Lp, s) != cudaSuccess) return -1;
+  if (cudaMemsetAsync(w->F, 0, sizeof(float2) * nkeys * Lp, s) != cudaSuccess) return -1;
   if (cudaMemsetAsync(w->cst, 0, sizeof(double) * kMaxLevels, s) != cudaSuccess) return -1;
 
   const int T = t1 - t0;
   SpreadArgs sa;
   for (int d = 0; d < 3; ++d) {
     sa.M[d] = p.M[d];
-    sa.C[d] = p.C[d];
     sa.invH[d] = 1.0 / p.Hc[d];
     sa.D[d] = p.D[d];
+    sa.P[d] = p.P[d];
+    sa.lo[d] = p.lo[d];
+    sa.delta[d] = p.delta[d];
+    sa.idelta[d] = (p.P[d] > 1 && p.delta[d] > 0.0) ? 1.0 / p.delta[d] : 0.0;
   }
+  sa.cells = (long long)cells;
   sa.fold = p.fold;
   sa.w = p.w;
   sa.L = n_level;
   sa.Lp = Lp;
   sa.beta = p.beta;
-  // points sorted by the grid cell of their spread start (a counting sort)
+  // points sorted by input cell and the grid cell of their spread start (a counting sort)
   const int LG = Lp == 1 ? 1 : (Lp % 4 == 0 ? 4 : 2);
-  const size_t ncells = p.cells();
-  if (ncells >= (size_t)1 << 31) return -1;
-  const long long nseg = ((long long)ncells + kSeg - 1) / kSeg;
+  const long long nseg = ((long long)nkeys + kSeg - 1) / kSeg;
   const long long NP = (long long)b.n_max * (b.n_max - 1) / 2;
   const size_t slots = (size_t)NP * T;
-  if (!grow(&w->count, &w->count_cap, ncells) || !grow(&w->cursor, &w->cursor_cap, ncells) ||
-      !grow(&w->cell_off, &w->cell_off_cap, ncells + 1) || !grow(&w->seg_sum, &w->seg_sum_cap, (size_t)nseg) ||
+  if (!grow(&w->count, &w->count_cap, nkeys) || !grow(&w->cursor, &w->cursor_cap, nkeys) ||
+      !grow(&w->cell_off, &w->cell_off_cap, nkeys + 1) || !grow(&w->seg_sum, &w->seg_sum_cap, (size_t)nseg) ||
       !grow(&w->seg_off, &w->seg_off_cap, (size_t)nseg + 1) || !grow(&w->rm, &w->rm_cap, slots) ||
       !grow(&w->rf, &w->rf_cap, slots) || !grow(&w->rc, &w->rc_cap, slots * Lp))
     return -1;
-  if (cudaMemsetAsync(w->count, 0, sizeof(int) * ncells, s) != cudaSuccess) return -1;
-  if (cudaMemsetAsync(w->cursor, 0, sizeof(int) * ncells, s) != cudaSuccess) return -1;
+  if (cudaMemsetAsync(w->count, 0, sizeof(int) * nkeys, s) != cudaSuccess) return -1;
+  if (cudaMemsetAsync(w->cursor, 0, sizeof(int) * nkeys, s) != cudaSuccess) return -1;
   int sms = 148, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -758,9 +819,9 @@ int nu_enqueue(const Batch& b, int t0, int t1, const NuPlan& p, NufftWs* w, cons
     const unsigned cgrid = (unsigned)std::min<size_t>((slots + 255) / 256, (size_t)sms * 32);
     k_nu_count<<<cgrid, 256, 0, s>>>(b, t0, T, sa, w->count);
   }
-  k_nu_seg_sum<<<(unsigned)nseg, 1024, 0, s>>>(w->count, (long long)ncells, w->seg_sum);
+  k_nu_seg_sum<<<(unsigned)nseg, 1024, 0, s>>>(w->count, (long long)nkeys, w->seg_sum);
   k_nu_scan<0><<<1, 1024, 0, s>>>(w->seg_sum, (int)nseg, 0, w->seg_off);
-  k_nu_seg_scan<<<(unsigned)nseg, 1024, 0, s>>>(w->count, (long long)ncells, w->seg_off, w->cell_off);
+  k_nu_seg_scan<<<(unsigned)nseg, 1024, 0, s>>>(w->count, (long long)nkeys, w->seg_off, w->cell_off);
   const int nb = (b.n_max + kTile - 1) / kTile;
   const dim3 grid(nb * (nb + 1) / 2, 1, T);
   dispatch_levels(n_level, [&](auto ML) {
@@ -768,9 +829,10 @@ int nu_enqueue(const Batch& b, int t0, int t1, const NuPlan& p, NufftWs* w, cons
     k_nu_scatter<L><<<grid, kTile * kTile, 0, s>>>(b, t0, sa, w->cell_off, w->cursor, w->rm, w->rf, w->rc);
   });
   nl += 6;
+  if (ev) cudaEventRecord(ev[7], s);
   if (slots > 0) {
     const unsigned sgrid = (unsigned)((slots + (size_t)kNuRun * 8 - 1) / ((size_t)kNuRun * 8));
-    const int* total = w->cell_off + ncells;
+    const int* total = w->cell_off + nkeys;
     auto spread = [&](auto kern) {
       for (int g = 0; g < Lp / LG; ++g) {
         kern<<<sgrid, 256, 0, s>>>(sa, total, w->rm, w->rf, w->rc, g * LG, w->F);
@@ -793,6 +855,23 @@ int nu_enqueue(const Batch& b, int t0, int t1, const NuPlan& p, NufftWs* w, cons
   }
   if (cudaGetLastError() != cudaSuccess) return -3;
   if (ev) cudaEventRecord(ev[1], s);
+
+  // the input cells that received points (all of them are transformed when there is one)
+  std::vector<int> todo;
+  if (parts == 1) {
+    todo.push_back(0);
+  } else {
+    k_nu_bounds<<<1, 256, 0, s>>>(w->cell_off, (long long)cells, parts, w->bnd);
+    ++nl;
+    w->h_bnd.resize(parts + 1);
+    if (cudaMemcpyAsync(w->h_bnd.data(), w->bnd, sizeof(int) * (parts + 1), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return -3;
+    for (int q = 0; q < parts; ++q)
+      if (w->h_bnd[q + 1] > w->h_bnd[q]) todo.push_back(q);
+    if (todo.empty()) todo.push_back(0);  // the zero-baseline constants still go into the image
+  }
 
   if (!w->have_fft || w->fft_n[0] != p.N2[0] || w->fft_n[1] != p.N2[1] || w->fft_n[2] != p.N2[2]) {
     if (w->have_fft) {
@@ -820,7 +899,6 @@ int nu_enqueue(const Batch& b, int t0, int t1, const NuPlan& p, NufftWs* w, cons
     ga.N2[d] = p.N2[d];
     ia.N2[d] = p.N2[d];
     ia.D[d] = p.D[d];
-    ia.C[d] = p.C[d];
     ia.HN[d] = p.Hc[d] * p.N2[d];
     scale *= (2.0 * M_PI * p.Hc[d]) * (2.0 * M_PI / p.N2[d]);
   }
@@ -829,17 +907,26 @@ int nu_enqueue(const Batch& b, int t0, int t1, const NuPlan& p, NufftWs* w, cons
   ia.scale = scale;
   ga.Lp = Lp;
   const unsigned pad_grid = (unsigned)std::min<size_t>((p.cells2() + 255) / 256, (size_t)sms * 16);
-  const unsigned pix_grid = (unsigned)((n_pix + 255) / 256);
-  for (int l = 0; l < n_level; ++l) {
-    ga.l = l;
-    if (ev && l == 0) cudaEventRecord(ev[2], s);
-    k_nu_pad<<<pad_grid, 256, 0, s>>>(w->F, ga, w->inv, w->G);
-    if (ev && l == 0) cudaEventRecord(ev[3], s);
-    if (cufftExecC2C(w->fft, (cufftComplex*)w->G, (cufftComplex*)w->G, CUFFT_INVERSE) != CUFFT_SUCCESS) return -2;
-    if (ev && l == 0) cudaEventRecord(ev[4], s);
-    k_nu_interp<<<pix_grid, 256, 0, s>>>(d_pix, n_pix, ia, w->G, w->corr, w->cst, l, b.flag, img);
-    if (ev && l == 0) cudaEventRecord(ev[5], s);
-    nl += 2;
+  const unsigned pix_grid = (unsigned)((pix_cnt + 255) / 256);
+  bool first = true;
+  for (const int q : todo) {
+    for (int d = 0; d < 3; ++d) ia.C[d] = p.C(q, d);
+    const float2* Fq = w->F + (size_t)q * cells * Lp;
+    for (int l = 0; l < n_level; ++l) {
+      ga.l = l;
+      const bool mark = ev && first && l == 0;
+      if (mark) cudaEventRecord(ev[2], s);
+      k_nu_pad<<<pad_grid, 256, 0, s>>>(Fq, ga, w->inv, w->G);
+      if (mark) cudaEventRecord(ev[3], s);
+      if (cufftExecC2C(w->fft, (cufftComplex*)w->G, (cufftComplex*)w->G, CUFFT_INVERSE) != CUFFT_SUCCESS) return -2;
+      if (mark) cudaEventRecord(ev[4], s);
+      if (pix_cnt > 0)
+        k_nu_interp<<<pix_grid, 256, 0, s>>>(d_pix, n_pix, d_order + pix_off, pix_cnt, ia, w->G, w->corr + pix_off,
+                                             w->cst, first ? 1 : 0, l, b.flag, img);
+      if (mark) cudaEventRecord(ev[5], s);
+      nl += 2;
+    }
+    first = false;
   }
   if (ev) cudaEventRecord(ev[6], s);
   if (cudaGetLastError() != cudaSuccess) return -3;
@@ -850,7 +937,7 @@ int nu_enqueue(const Batch& b, int t0, int t1, const NuPlan& p, NufftWs* w, cons
 void nu_free(NufftWs* w) {
   if (w->have_fft) cufftDestroy(w->fft);
   void* ptrs[] = {w->F, w->G, w->inv, w->corr, w->cst, w->gl, w->count, w->cursor, w->cell_off, w->seg_sum,
-                  w->seg_off, w->rm, w->rf, w->rc};
+                  w->seg_off, w->rm, w->rf, w->rc, w->bnd};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   *w = NufftWs{};

@@ -69,12 +69,13 @@ def test_default_options(lib):
     assert o.max_jacobi_sweeps == 40 and abs(o.jacobi_tol - 1e-13) < 1e-30 and o.gram_identity == 0
     assert o.device == -1 and o.eig_mode == bipp_ss.BIPP_EIG_JACOBI64
     assert o.synthesis == bipp_ss.BIPP_SYNTH_STANDARD and abs(o.nufft_eps - 1e-5) < 1e-20
-    assert C.sizeof(bipp_ss.bipp_ss_options) == 80  # the C struct's size on x86-64
+    assert C.sizeof(bipp_ss.bipp_ss_options) == 96  # the C struct's size on x86-64
+    assert list(o.nufft_partition) == [1] * 6
 
 
 @pytest.mark.parametrize("case", ["n_pix", "wl", "levels", "precision", "reserved", "nan_bound", "nan_pix",
                                   "eig_levels", "eig_many", "eig_flag", "synthesis", "nufft_eps_small",
-                                  "nufft_eps_large", "nufft_eigenimages"])
+                                  "nufft_eps_large", "nufft_eigenimages", "nufft_partition"])
 def test_create_rejects_invalid_arguments_before_device_use(lib, case):
     pix = np.array([[0.0, 0.0, 1.0], [0.1, 0.0, 0.99]])
     b = np.array([[-np.inf, np.inf]])
@@ -90,7 +91,7 @@ def test_create_rejects_invalid_arguments_before_device_use(lib, case):
         kw["precision"] = 9
     elif case == "reserved":
         o = bipp_ss.bipp_ss_default_options()
-        o.reserved[2] = 1
+        o.reserved[1] = 1
         h = C.c_void_p()
         pc = np.ascontiguousarray(pix.T)
         bc = np.ascontiguousarray(b.T)
@@ -120,6 +121,8 @@ def test_create_rejects_invalid_arguments_before_device_use(lib, case):
         kw.update(synthesis="nufft", nufft_eps=0.5)
     elif case == "nufft_eigenimages":  # NUFFT synthesis makes level images only
         kw.update(synthesis="nufft", eigenimages=1, n_eig=1)
+    elif case == "nufft_partition":
+        kw.update(synthesis="nufft", nufft_partition=(1, 1, 1, 1, 0, 1))
     with pytest.raises(bipp_ss.BippError) as e:
         bipp_ss.bipp_ss_create(pix, wl, b, **kw)
     want = bipp_ss.BIPP_ERR_UNSUPPORTED if case == "nufft_eigenimages" else bipp_ss.BIPP_ERR_INVALID_ARG

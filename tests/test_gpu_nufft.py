@@ -162,3 +162,36 @@ def test_nufft_benchmark_workload_sampled_pixels():
         ss.collect_batch(inp.st_xyz, inp.vis)
         got = ss.get()
     _check(got[sample], want, np.sqrt(sc2), 1e-5)
+
+
+@pytest.mark.parametrize("part", [(3, 2, 1, 2, 2, 1), (1, 4, 2, 1, 1, 3), (2, 2, 2, 3, 1, 1)])
+def test_nufft_domain_partitioning(small, part):
+    """Sec. 3.4.1: input (baseline) cells x image cells, one transform per
+    non-empty pair; the images match the unpartitioned sum."""
+    inp = small
+    b, _ = helpers.oracle_prepass_bounds(inp)
+    want, scale = _direct(inp.pix, inp.wl, b, 16, inp.st_xyz, inp.vis)
+    with bipp_ss.StandardSynthesis(inp.pix, inp.wl, b, n_eig=16, synthesis="nufft", nufft_eps=1e-5,
+                                   nufft_partition=part) as ss:
+        ss.collect_batch(inp.st_xyz, inp.vis)
+        got = ss.get()
+    _check(got, want, scale, 1e-5)
+
+
+def test_nufft_partitioned_benchmark_workload_sampled_pixels():
+    """The paper's setting, input and image partitions of (4, 4, 1), on the
+    benchmark workload (4 of its 50 steps), sampled pixels against the oracle."""
+    inp = inputs.make_nufft_config(n_t=4)
+    n_pix = inp.pix.shape[0]
+    rng = np.random.default_rng(11)
+    sample = np.unique(np.concatenate([rng.choice(n_pix, 300, replace=False), np.arange(255 * 1024, 257 * 1024, 3)]))
+    bounds, _ = helpers.oracle_prepass_bounds(inp)
+    want, sc2 = None, 0.0
+    for p, V in zip(inp.st_xyz, inp.vis):
+        want, mu, lev, W = oracle.ss_step(inp.pix[sample], inp.wl, bounds, inp.n_eig, p, V, img=want)
+        sc2 = sc2 + onu.error_scale(W, mu, lev, 4, len(sample)) ** 2
+    with bipp_ss.StandardSynthesis(inp.pix, inp.wl, bounds, n_eig=inp.n_eig, synthesis="nufft", nufft_eps=1e-5,
+                                   eig_mode="mixed", nufft_partition=(4, 4, 1, 4, 4, 1)) as ss:
+        ss.collect_batch(inp.st_xyz, inp.vis)
+        got = ss.get()
+    _check(got[sample], want, np.sqrt(sc2), 1e-5)
