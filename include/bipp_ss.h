@@ -108,8 +108,9 @@ typedef struct {
  *           grid spans the batch's baseline extent times the pixels' extent per
  *           dimension (of the order of 2 max|b|/wl x (pixel extent) points), so
  *           it suits fields whose pixels resolve the array (small fields of
- *           view); BIPP_ERR_UNSUPPORTED when it does not fit in device memory.
- *           Not with eigenimages. */
+ *           view); nufft_partition splits it into smaller transforms, and
+ *           BIPP_ERR_UNSUPPORTED reports grids that do not fit in device
+ *           memory. Not with eigenimages. */
 #define BIPP_SYNTH_STANDARD 0
 #define BIPP_SYNTH_NUFFT 1
 

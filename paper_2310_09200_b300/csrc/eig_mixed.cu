@@ -47,11 +47,6 @@ enum Dim { DN = 0, DKP = 1 };
 
 __device__ __forceinline__ int dim_of(int code, int n, int kp) { return code == DN ? n : kp; }
 
-__device__ __forceinline__ void ld_c(const double2* p, size_t i, double2* v) { *v = p[i]; }
-__device__ __forceinline__ void ld_c(const float2* p, size_t i, double2* v) {
-  const float2 f = p[i];
-  *v = make_double2(f.x, f.y);
-}
 __device__ __forceinline__ void ld_c(const float2* p, size_t i, float2* v) { *v = p[i]; }
 
 // Problem t takes no further part in the refinement: an error status, or its
