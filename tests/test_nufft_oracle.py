@@ -141,3 +141,28 @@ def test_nufft_level_error_within_its_scale(eps):
     got, _ = nu.nufft_levels_with_scale(inp.pix, inp.wl, b, 16, inp.st_xyz, inp.vis, eps=eps)
     err = np.linalg.norm(got - want, axis=0)
     assert np.all(err <= 5 * eps * np.maximum(np.linalg.norm(want, axis=0), scale)), err
+
+
+def test_gram_corrected_visibilities_appendix_a():
+    """App. A: with all eigenpairs, the visibilities are the Gram-corrected ones
+    V' = A diag(mu) A^H mixed by the Gram matrix, V = G V' G for G-orthonormal
+    eigenvectors (V A = G A Lambda and A^-1 = A^H G; App. A prints V = G V', which
+    drops one factor G, harmless when G ~ I); the back-projected image (G = I) is
+    the type-3 sum of G V' G, the least-squares image that of V'."""
+    rng = np.random.default_rng(21)
+    p = inputs.layout_disk(20, 300.0, 1.0, 6.0, rng)
+    wl = 5.656  # 53 MHz
+    V = inputs.visibilities(p, wl, inputs.sources_in_cap(3, 2.0, rng), np.array([1000.0, 5.0, 2.0]), 20.0, rng)
+    G = oracle.gram(p, wl)
+    mu, A, _ = oracle.geneig(V, G)
+    Vp = nu.level_visibilities(A, mu, np.zeros(len(mu), dtype=np.int32), 1)[0]
+    np.testing.assert_allclose(G @ Vp @ G, V, atol=1e-10 * np.abs(V).max())
+    assert np.abs(G @ Vp - V).max() > 1e-3 * np.abs(V).max()  # the printed form is not exact
+    pix = inputs.pixel_grid(12, 0.6)
+    b = np.array([[-np.inf, np.inf]])
+    x, c = nu.baseline_points(p, wl, np.stack([Vp, G @ Vp @ G]))
+    f = nu.type3_direct(x, c, pix).real
+    lsq, *_ = oracle.ss_step(pix, wl, b, len(p), p, V)
+    back, *_ = oracle.ss_step(pix, wl, b, len(p), p, V, gram_identity=True)
+    np.testing.assert_allclose(f[:, 0], lsq[:, 0], rtol=1e-10, atol=1e-10 * np.abs(lsq).max())
+    np.testing.assert_allclose(f[:, 1], back[:, 0], rtol=1e-10, atol=1e-10 * np.abs(back).max())
