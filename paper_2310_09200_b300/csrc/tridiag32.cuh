@@ -343,11 +343,12 @@ __global__ void __launch_bounds__(kTdThreads, 1) k_tridiag32_lo(TridiagArgs a) {
               const int j = j0 + 16 * h + u;
               x[u] = (rv && j <= i) ? Ai[(size_t)j * N] : zero;
             }
+            float2 cv[16];  // this row's contributions conj(a_ij) v_i to the 16 column sums
 #pragma unroll
             for (int u = 0; u < 16; ++u) {
               const int j = j0 + 16 * h + u;
               const bool ok = rv && j <= i;
-              float2 col = zero;
+              cv[u] = zero;
               if (ok) {
                 const float2 t1 = cmulc(wpi, vp[j]), t2 = cmulc(vpi, wp[j]);
                 x[u].x -= t1.x + t2.x;
@@ -356,14 +357,31 @@ __global__ void __launch_bounds__(kTdThreads, 1) k_tridiag32_lo(TridiagArgs a) {
                 const float2 pv = cmul(x[u], v[j]);
                 acc.x += pv.x;
                 acc.y += pv.y;
-                if (j < i) col = cmulc(vi, x[u]);  // conj(a_ij) v_i
+                if (j < i) cv[u] = cmulc(vi, x[u]);
               }
+            }
+            // column sums over the 32 rows by a reduce-scatter butterfly: at each level a
+            // lane keeps half of its partial sums and adds its partner's other half, so
+            // the 16 sums take 16 shuffles per component instead of 80; lane l ends with
+            // the sum of column 8 b4 + 4 b3 + 2 b2 + b1 (bits of l), as does lane l ^ 1
 #pragma unroll
-              for (int o = 16; o > 0; o >>= 1) {
-                col.x += __shfl_xor_sync(0xffffffffu, col.x, o);
-                col.y += __shfl_xor_sync(0xffffffffu, col.y, o);
+            for (int lv = 0; lv < 4; ++lv) {
+              const int half = 8 >> lv, bit = 16 >> lv;
+              const bool up = (lane & bit) != 0;
+#pragma unroll
+              for (int k = 0; k < half; ++k) {
+                const float2 send = up ? cv[k] : cv[k + half];
+                const float2 keep = up ? cv[k + half] : cv[k];
+                cv[k].x = keep.x + __shfl_xor_sync(0xffffffffu, send.x, bit);
+                cv[k].y = keep.y + __shfl_xor_sync(0xffffffffu, send.y, bit);
               }
-              if (lane == 16 * h + u && j < n) colp[(size_t)ti * N + j] = col;
+            }
+            cv[0].x += __shfl_xor_sync(0xffffffffu, cv[0].x, 1);
+            cv[0].y += __shfl_xor_sync(0xffffffffu, cv[0].y, 1);
+            {
+              const int cu = 8 * ((lane >> 4) & 1) + 4 * ((lane >> 3) & 1) + 2 * ((lane >> 2) & 1) + ((lane >> 1) & 1);
+              const int j = j0 + 16 * h + cu;
+              if ((lane & 1) == 0 && j < n) colp[(size_t)ti * N + j] = cv[0];
             }
           }
           if (rv) rowp[(size_t)tj * N + i] = acc;
