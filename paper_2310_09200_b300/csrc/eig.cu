@@ -146,29 +146,49 @@ __global__ void __launch_bounds__(kChThreads, 1) k_cholesky_blk(Batch b) {
       const int r = e % m, c = e / m;
       if (r >= c) A[(size_t)(k0 + r) + (size_t)(k0 + c) * N] = sP[r * kChLd + c];
     }
+    __syncthreads();
+    // the panel's trailing rows become double-float pairs (hi, lo) in place, so the
+    // trailing update runs on the FP32 pipe (dfloat.cuh)
+    for (int e = tid; e < (m - bw) * bw; e += kChThreads) {
+      double* slot = sP + (bw + e / bw) * kChLd + e % bw;
+      float hi, lo;
+      df::split(*slot, hi, lo);
+      *reinterpret_cast<float2*>(slot) = make_float2(hi, lo);
+    }
+    __syncthreads();
     // trailing lower triangle: A(i, j) -= sum_k P(i, k) P(j, k) for k0 + bw <= j <= i < n
     const int m2 = m - bw, nt = (m2 + 31) / 32;
+    const float2* P2 = reinterpret_cast<const float2*>(sP);
     int tile = 0;
     for (int ti = 0; ti < nt; ++ti) {
       for (int tj = 0; tj <= ti; ++tj, ++tile) {
         if (tile % (kChThreads / 32) != warp) continue;
         const int i = ti * 32 + lane;
         if (i >= m2) continue;
-        double acc[32];
-#pragma unroll
-        for (int c = 0; c < 32; ++c) acc[c] = 0.0;
-        const double* pi = sP + (bw + i) * kChLd;
-        const double* pj = sP + (bw + tj * 32) * kChLd;
-        for (int k = 0; k < bw; ++k) {
-          const double pik = pi[k];
-#pragma unroll
-          for (int c = 0; c < 32; ++c) acc[c] = fma(pik, pj[c * kChLd + k], acc[c]);
-        }
+        const float2* pi = P2 + (bw + i) * kChLd;
         double* Ai = A + (size_t)(k0 + bw + i);
+        for (int h = 0; h < 2; ++h) {  // 16 columns at a time
+          float ah[16], al[16];
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          const int j = tj * 32 + c;
-          if (j <= i && j < m2) Ai[(size_t)(k0 + bw + j) * N] -= acc[c];
+          for (int c = 0; c < 16; ++c) ah[c] = al[c] = 0.f;
+          const float2* pj = P2 + (bw + tj * 32 + 16 * h) * kChLd;  // rows past the panel hold stale values, unused
+          for (int k = 0; k < bw; ++k) {
+            const float2 a = pi[k];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+              const float2 q = pj[c * kChLd + k];
+              df::mac(ah[c], al[c], a.x, a.y, q.x, q.y);
+            }
+            if ((k & 15) == 15) {
+#pragma unroll
+              for (int c = 0; c < 16; ++c) df::renorm(ah[c], al[c]);
+            }
+          }
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const int j = tj * 32 + 16 * h + c;
+            if (j <= i && j < m2) Ai[(size_t)(k0 + bw + j) * N] -= df::to_double(ah[c], al[c]);
+          }
         }
       }
     }
