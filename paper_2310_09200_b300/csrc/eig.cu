@@ -214,7 +214,8 @@ __global__ void __launch_bounds__(kTiThreads) k_trinv_blk(Batch b, int gram_iden
   double* R = b.Linv + mat_off(t, N);
   const int cw = min(32, n - c0);
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;  // 8 rows of 4 outputs per thread
-  __shared__ double sL[32][33], sY[32][33], sAcc[32][33];
+  __shared__ double sL[32][33], sAcc[32][33];
+  __shared__ float2 fL[32][33], fY[32][33];  // tiles of the products as double-float pairs (dfloat.cuh)
   // rows above the block are zero
   for (int e = tid; e < c0 * cw; e += kTiThreads) {
     const int i = e / cw, j = e % cw;
@@ -222,25 +223,38 @@ __global__ void __launch_bounds__(kTiThreads) k_trinv_blk(Batch b, int gram_iden
   }
   for (int i0 = c0; i0 < n; i0 += 32) {
     const int rh = min(32, n - i0);
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};  // rows ty + 8u, column tx
+    float ah[4] = {0.f, 0.f, 0.f, 0.f}, al[4] = {0.f, 0.f, 0.f, 0.f};  // rows ty + 8u, column tx
     if (!gram_identity) {
       for (int j0 = c0; j0 < i0; j0 += 32) {
         __syncthreads();
         for (int e = tid; e < 32 * 32; e += kTiThreads) {
+          float h, l;
           const int r = e % 32, k = e / 32;  // L tile: column-major reads
-          sL[r][k] = (i0 + r < n) ? L[(size_t)(i0 + r) + (size_t)(j0 + k) * N] : 0.0;
+          df::split((i0 + r < n) ? L[(size_t)(i0 + r) + (size_t)(j0 + k) * N] : 0.0, h, l);
+          fL[r][k] = make_float2(h, l);
           const int kr = e / 32, c = e % 32;  // Y tile: row-major reads
-          sY[kr][c] = (c < cw && j0 + kr < n) ? R[(size_t)(j0 + kr) * N + c0 + c] : 0.0;
+          df::split((c < cw && j0 + kr < n) ? R[(size_t)(j0 + kr) * N + c0 + c] : 0.0, h, l);
+          fY[kr][c] = make_float2(h, l);
         }
         __syncthreads();
-#pragma unroll 8
+#pragma unroll 4
         for (int k = 0; k < 32; ++k) {
-          const double y = sY[k][tx];
+          const float2 y = fY[k][tx];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) acc[u] = fma(sL[ty + 8 * u][k], y, acc[u]);
+          for (int u = 0; u < 4; ++u) {
+            const float2 a = fL[ty + 8 * u][k];
+            df::mac(ah[u], al[u], a.x, a.y, y.x, y.y);
+          }
+          if ((k & 15) == 15) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) df::renorm(ah[u], al[u]);
+          }
         }
       }
     }
+    double acc[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[u] = df::to_double(ah[u], al[u]);
     __syncthreads();
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
