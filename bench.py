@@ -105,6 +105,9 @@ def parse():
     ap.add_argument("--precision", default="split_fp16", choices=["fp64", "fp32", "split_bf16", "split_fp16"])
     ap.add_argument("--n-t", type=int, default=0, help="time steps per imaging job (default 100; 50 for nufft)")
     ap.add_argument("--synthesis", default="standard", choices=["standard", "nufft"])
+    ap.add_argument("--workload", default="", choices=["", "ska_low_20deg", "nufft_4arcsec"],
+                    help="inputs (default: the 20 deg SKA-Low job for standard synthesis, the 4 arcsec field "
+                         "of the paper's NUFFT comparison for nufft)")
     ap.add_argument("--nufft-eps", type=float, default=1e-5)
     ap.add_argument("--nufft-partition", type=int, nargs=6, default=[1, 1, 1, 1, 1, 1],
                     help="NUFFT domain partitioning: input cells (x y z) then image cells (x y z)")
@@ -117,9 +120,13 @@ def parse():
     return ap.parse_args()
 
 
+def workload_name(args):
+    return args.workload or ("nufft_4arcsec" if args.synthesis == "nufft" else "ska_low_20deg")
+
+
 def workload(args):
     from paper_2310_09200_b300 import inputs
-    if args.synthesis == "nufft":
+    if workload_name(args) == "nufft_4arcsec":
         return inputs.make_nufft_config(n_t=args.n_t or 50, n_side=args.side, n_st=args.n_st or 512)
     inp = inputs.make_config(1, n_t=args.n_t or 100, n_side=args.side)
     if args.n_st:
@@ -130,14 +137,18 @@ def workload(args):
 
 
 def config_dict(args, inp, precision):
-    if args.synthesis == "nufft":
+    if workload_name(args) == "nufft_4arcsec":
+        how = (f"NUFFT synthesis, type-3 NUFFT tolerance {args.nufft_eps:g}" if args.synthesis == "nufft"
+               else f"standard synthesis ({precision})")
         return {
-            "workload": (f"SKA-Low-like NUFFT synthesis: {inp.st_xyz[0].shape[0]} stations (lognormal to 65 km), "
-                         f"{args.side}^2 px of 4 arcsec, N_eig {inp.n_eig}, {inp.n_level} levels, {inp.n_t} time "
-                         f"steps over 6 h per job, wl 2 m, type-3 NUFFT tolerance {args.nufft_eps:g}"),
+            "workload": (f"SKA-Low-like field of 4 arcsec pixels, {how}: {inp.st_xyz[0].shape[0]} stations "
+                         f"(lognormal to 65 km), {args.side}^2 px, N_eig {inp.n_eig}, {inp.n_level} levels, "
+                         f"{inp.n_t} time steps over 6 h per job, wl 2 m"),
             "n_st": int(inp.st_xyz[0].shape[0]), "n_pix": int(inp.n_pix), "n_eig": int(inp.n_eig),
-            "n_level": int(inp.n_level), "n_t": int(inp.n_t), "synthesis": "nufft",
-            "nufft_eps": args.nufft_eps, "nufft_partition": list(args.nufft_partition),
+            "n_level": int(inp.n_level), "n_t": int(inp.n_t),
+            "synthesis": "nufft" if args.synthesis == "nufft" else precision,
+            **({"nufft_eps": args.nufft_eps, "nufft_partition": list(args.nufft_partition)}
+               if args.synthesis == "nufft" else {}),
             "eigensolve": EIG_DESC.get(getattr(args, "eig", "jacobi64"), "fp64 parallel-order Jacobi")
             if precision != "fp64 (oracle)" else "fp64 cyclic Jacobi (oracle)",
             "l2": "inputs larger than L2 (visibilities 200 MB per job)",
