@@ -195,3 +195,32 @@ def test_nufft_partitioned_benchmark_workload_sampled_pixels():
         ss.collect_batch(inp.st_xyz, inp.vis)
         got = ss.get()
     _check(got[sample], want, np.sqrt(sc2), 1e-5)
+
+
+@pytest.mark.parametrize("eps", [1e-7, 3e-2])
+def test_nufft_kernel_width_extremes(small, eps):
+    """The widest kernel (eps 1e-7: w = 8, 512-cell footprints) and a narrow one
+    (eps 3e-2: w = 3); below ~1e-6 the FP32 grids set the floor."""
+    inp = small
+    b, _ = helpers.oracle_prepass_bounds(inp)
+    want, scale = _direct(inp.pix, inp.wl, b, 16, inp.st_xyz, inp.vis)
+    with bipp_ss.StandardSynthesis(inp.pix, inp.wl, b, n_eig=16, synthesis="nufft", nufft_eps=eps) as ss:
+        ss.collect_batch(inp.st_xyz, inp.vis)
+        got = ss.get()
+    _check(got, want, scale, max(eps, 1e-6))
+
+
+def test_nufft_sixteen_levels(small):
+    """16 levels (four spreading passes of 4 interleaved levels), one eigenpair
+    or none per level."""
+    inp = small
+    mus = []
+    for p, V in zip(inp.st_xyz, inp.vis):
+        mus.extend(oracle.geneig(V, oracle.gram(p, inp.wl))[0][:16])
+    b = bipp_ss.quantile_level_bounds(mus, 16)
+    want, scale = _direct(inp.pix, inp.wl, b, 16, inp.st_xyz, inp.vis)
+    with bipp_ss.StandardSynthesis(inp.pix, inp.wl, b, n_eig=16, synthesis="nufft", nufft_eps=1e-5) as ss:
+        ss.collect_batch(inp.st_xyz, inp.vis)
+        got = ss.get()
+    assert got.shape == want.shape == (inp.pix.shape[0], 16)
+    _check(got, want, scale, 1e-5)
