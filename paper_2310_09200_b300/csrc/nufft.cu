@@ -4,20 +4,22 @@
 // NUFFT per level maps the baselines of all steps to the pixels:
 //
 //   1. Spreading onto the grid y_m = (m - M/2) h with the exponential-of-
-//      semicircle kernel, sorted by bins of the grid so that the w^3-cell
-//      footprints are summed in shared memory:
+//      semicircle kernel, the baselines sorted by the grid cell where their
+//      w^3-cell footprint starts (a counting sort), so that runs of baselines
+//      with the same start are summed in registers and added to the grid once:
 //      k_nu_count   one thread per station pair p < q of a step: orientation
 //                   (the folded coordinate >= 0; the (q, p) term is the
-//                   conjugate one, so Re of the sum is unchanged), spread start,
-//                   bin; warp-aggregated count per bin;
-//      k_nu_scan    exclusive offsets of the bins' points and of their chunks;
+//                   conjugate one, so Re of the sum is unchanged), input cell
+//                   (domain partitioning), spread start; warp-aggregated count
+//                   per sort key;
+//      k_nu_seg_sum, k_nu_scan, k_nu_seg_scan  exclusive offsets of the keys;
 //      k_nu_scatter per pair, the level strengths 2 V'_l,pq = 2 sum_{e in l}
 //                   d_e a_pe conj(a_qe) (eigenvectors staged through shared
 //                   memory), pre-phased by exp(2 pi i <D, x>), written with the
-//                   start and fractions at the pair's place in bin order;
-//      k_nu_spread  one block per chunk of <= 2048 points of a bin: footprints
-//                   summed into a shared-memory tile (bin + w - 1 halo), then the
-//                   tile added to the grid with vector float atomics.
+//                   start and fractions at the pair's sorted place;
+//      k_nu_spread  one warp per 256 sorted baselines: lane i owns footprint
+//                   cells i, i + 32, ...; runs of equal start cells are summed
+//                   in registers and added with vector float atomics.
 //      Coordinates and phases are reduced in FP64; kernel weights, strengths and
 //      the grid are FP32.
 //   2. k_nu_const: the p = q terms (zero baseline): sum_t sum_{e in l} d_e |a_e|^2,
@@ -208,15 +210,13 @@ __global__ void k_nu_count(Batch b, int t0, int T, SpreadArgs a, int* __restrict
   }
 }
 
-// Exclusive scan out[0..n] of v(in[i]) (out[n] = total) in one block of 1024
-// threads; MODE 0: v = x, MODE 1: v = ceil(x / P) (chunks of P points).
-template <int MODE>
-__global__ void __launch_bounds__(1024) k_nu_scan(const int* __restrict__ in, int n, int P, int* __restrict__ out) {
+// Exclusive scan out[0..n] of in (out[n] = total) in one block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_nu_scan(const int* __restrict__ in, int n, int* __restrict__ out) {
   __shared__ int part[1024];
   const int per = (n + 1023) / 1024;
   const int i0 = min(n, threadIdx.x * per), i1 = min(n, i0 + per);
   int sum = 0;
-  for (int i = i0; i < i1; ++i) sum += MODE == 0 ? in[i] : (in[i] + P - 1) / P;
+  for (int i = i0; i < i1; ++i) sum += in[i];
   part[threadIdx.x] = sum;
   __syncthreads();
   for (int o = 1; o < 1024; o <<= 1) {  // inclusive Hillis-Steele scan of the partial sums
@@ -228,13 +228,13 @@ __global__ void __launch_bounds__(1024) k_nu_scan(const int* __restrict__ in, in
   int run = part[threadIdx.x] - sum;
   for (int i = i0; i < i1; ++i) {
     out[i] = run;
-    run += MODE == 0 ? in[i] : (in[i] + P - 1) / P;
+    run += in[i];
   }
   if (threadIdx.x == 1023) out[n] = part[1023];
 }
 
 // Exclusive scan of n ints over many blocks: segments of kSeg elements per
-// block; k_nu_seg_sum totals each segment, k_nu_scan<0> scans the totals,
+// block; k_nu_seg_sum totals each segment, k_nu_scan scans the totals,
 // k_nu_seg_scan writes out[i] (and out[n] = total).
 constexpr int kSeg = 8192;
 
@@ -820,7 +820,7 @@ int nu_enqueue(const Batch& b, int t0, int t1, const NuPlan& p, NufftWs* w, cons
     k_nu_count<<<cgrid, 256, 0, s>>>(b, t0, T, sa, w->count);
   }
   k_nu_seg_sum<<<(unsigned)nseg, 1024, 0, s>>>(w->count, (long long)nkeys, w->seg_sum);
-  k_nu_scan<0><<<1, 1024, 0, s>>>(w->seg_sum, (int)nseg, 0, w->seg_off);
+  k_nu_scan<<<1, 1024, 0, s>>>(w->seg_sum, (int)nseg, w->seg_off);
   k_nu_seg_scan<<<(unsigned)nseg, 1024, 0, s>>>(w->count, (long long)nkeys, w->seg_off, w->cell_off);
   const int nb = (b.n_max + kTile - 1) / kTile;
   const dim3 grid(nb * (nb + 1) / 2, 1, T);
