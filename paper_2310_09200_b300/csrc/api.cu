@@ -104,7 +104,12 @@ struct bipp_ss {
   GraphKey last_key;
   bool have_key = false;
   GraphKey graph_key;
-  cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // the batch before and from the reduction on
+  // host-buffer collects: the visibilities' upload runs on copy_stream while the
+  // Gram matrix, its Cholesky factor and inverse (which do not read them) run
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t vis_ready = nullptr, ev_order = nullptr;
+  bool vis_pending = false;
   // last batch
   int last_T = 0, last_N = 0, last_K = 0;
   double timings[6] = {0, 0, 0, 0, 0, 0};
@@ -147,8 +152,10 @@ static cudaError_t dalloc(T** p, size_t count) {
 }
 
 static void drop_graph(bipp_ss* h) {
-  if (h->graph) cudaGraphExecDestroy(h->graph);
-  h->graph = nullptr;
+  for (auto& g : h->graph) {
+    if (g) cudaGraphExecDestroy(g);
+    g = nullptr;
+  }
   h->have_key = false;
 }
 
@@ -263,6 +270,9 @@ extern "C" int bipp_ss_destroy(bipp_ss_t h) {
   if (h->d_bounds) cudaFree(h->d_bounds);
   for (auto& e : h->ev) if (e) cudaEventDestroy(e);
   for (auto& e : h->nu_ev) if (e) cudaEventDestroy(e);
+  if (h->vis_ready) cudaEventDestroy(h->vis_ready);
+  if (h->ev_order) cudaEventDestroy(h->ev_order);
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
   if (h->stream) cudaStreamDestroy(h->stream);
   delete h;
   return BIPP_OK;
@@ -348,6 +358,11 @@ extern "C" int bipp_ss_create_channels(bipp_ss_t* out, int64_t n_pix, const doub
     if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(BIPP_ERR_CUDA, "event", e);
   for (auto& ev : h->nu_ev)
     if ((e = cudaEventCreate(&ev)) != cudaSuccess) return bail(BIPP_ERR_CUDA, "event", e);
+  if ((e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return bail(BIPP_ERR_CUDA, "stream", e);
+  if ((e = cudaEventCreateWithFlags(&h->vis_ready, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&h->ev_order, cudaEventDisableTiming)) != cudaSuccess)
+    return bail(BIPP_ERR_CUDA, "event", e);
   if ((e = dalloc(&h->d_pix, (size_t)3 * n_pix)) != cudaSuccess) return bail(BIPP_ERR_OUT_OF_MEMORY, "pixels", e);
   if ((e = dalloc(&h->d_pix_hl, (size_t)6 * n_pix)) != cudaSuccess) return bail(BIPP_ERR_OUT_OF_MEMORY, "pixels", e);
   if ((e = dalloc(&h->d_img, n_img)) != cudaSuccess) return bail(BIPP_ERR_OUT_OF_MEMORY, "images", e);
@@ -425,9 +440,23 @@ static cudaError_t record(cudaEvent_t ev, cudaStream_t s) {
 }
 
 // Everything between the per-step table upload and the synthesis: stream
-// ordered, no host synchronisation, so it can be captured into a graph.
-static int enqueue_batch(bipp_ss* h, const Batch& b, const TcPlan& plan, cudaStream_t s) {
+// ordered, no host synchronisation, so it can be captured into graphs. Part 0
+// (tables, Gram matrix, Cholesky factor and its inverse) does not read the
+// visibilities; part 1 (reduction onwards) does.
+static int enqueue_batch(bipp_ss* h, const Batch& b, const TcPlan& plan, cudaStream_t s, int part);
+
+// Both parts, with the wait for a pending visibility upload between them.
+static int enqueue_all(bipp_ss* h, const Batch& b, const TcPlan& plan, cudaStream_t s) {
+  int rc = enqueue_batch(h, b, plan, s, 0);
+  if (rc) return rc;
+  if (h->vis_pending) CUDA_TRY(h, cudaStreamWaitEvent(s, h->vis_ready, 0));
+  return enqueue_batch(h, b, plan, s, 1);
+}
+
+static int enqueue_batch(bipp_ss* h, const Batch& b, const TcPlan& plan, cudaStream_t s, int part) {
   const int T = b.T;
+  const int gi = h->opt.gram_identity;
+  if (part == 0) {
   CUDA_TRY(h, cudaMemcpyAsync(h->d_nst, h->h_nst, sizeof(int) * T, cudaMemcpyHostToDevice, s));
   CUDA_TRY(h, cudaMemcpyAsync(h->d_neig, h->h_neig, sizeof(int) * T, cudaMemcpyHostToDevice, s));
   CUDA_TRY(h, cudaMemcpyAsync(h->d_chan, h->h_chan, sizeof(int) * T, cudaMemcpyHostToDevice, s));
@@ -435,10 +464,11 @@ static int enqueue_batch(bipp_ss* h, const Batch& b, const TcPlan& plan, cudaStr
   CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int) * T, s));
   CUDA_TRY(h, cudaMemsetAsync(h->d_sweeps, 0, sizeof(int) * T, s));
   CUDA_TRY(h, cudaMemsetAsync(h->d_flag, 0, sizeof(int), s));
-  const int gi = h->opt.gram_identity;
   CUDA_TRY(h, record(h->ev[0], s));
   launch_gram(b, gi, s);
   launch_cholesky(b, gi, s);
+  return cudaGetLastError() == cudaSuccess ? BIPP_OK : fail(h, BIPP_ERR_CUDA, "Gram / Cholesky launch failed");
+  }
   launch_reduce(b, gi, s);
   CUDA_TRY(h, record(h->ev[1], s));
   if (h->mixed_kp > 0) {
@@ -573,12 +603,12 @@ static int run_batch(bipp_ss* h, int n_t, int N, const std::vector<int>& nst_v, 
 
   if (nufft) {
     // host-planned grids and cuFFT: enqueued directly, not captured
-    const int rc = enqueue_batch(h, b, plan, s);
+    const int rc = enqueue_all(h, b, plan, s);
     if (rc) return rc;
   } else if (tc && h->opt.autotune && !plan.tuned) {
     // first batch of this accumulator width: run up to the packing, tune, then synthesise
     Batch bb = b;
-    int rc = enqueue_batch(h, bb, plan, s);  // ... runs the synthesis with the default plan too
+    int rc = enqueue_all(h, bb, plan, s);  // ... runs the synthesis with the default plan too
     if (rc) return rc;
     CUDA_TRY(h, cudaStreamSynchronize(s));
     const int chan_sub = chan_v[std::min(n_t, 4) - 1] + 1;
@@ -587,31 +617,42 @@ static int run_batch(bipp_ss* h, int n_t, int N, const std::vector<int>& nst_v, 
       cudaGetLastError();
       // keep the default stage count; tuning failure is not a collect failure
     }
-  } else if (h->opt.use_graph && h->graph && key == h->graph_key) {
-    CUDA_TRY(h, cudaGraphLaunch(h->graph, s));
+  } else if (h->opt.use_graph && h->graph[0] && h->graph[1] && key == h->graph_key) {
+    CUDA_TRY(h, cudaGraphLaunch(h->graph[0], s));
+    if (h->vis_pending) CUDA_TRY(h, cudaStreamWaitEvent(s, h->vis_ready, 0));
+    CUDA_TRY(h, cudaGraphLaunch(h->graph[1], s));
   } else if (h->opt.use_graph && h->have_key && key == h->last_key) {
-    // second batch of the same geometry: capture once, replay from now on
-    if (h->graph) cudaGraphExecDestroy(h->graph);
-    h->graph = nullptr;
-    cudaGraph_t g = nullptr;
-    CUDA_TRY(h, cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
-    const int rc = enqueue_batch(h, b, plan, s);
-    const cudaError_t ce = cudaStreamEndCapture(s, &g);
-    if (rc) {
-      if (g) cudaGraphDestroy(g);
-      return rc;
-    }
-    if (ce != cudaSuccess) return fail(h, BIPP_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
-    const cudaError_t ie = cudaGraphInstantiate(&h->graph, g, 0);
-    cudaGraphDestroy(g);
-    if (ie != cudaSuccess) {
-      h->graph = nullptr;
-      return fail(h, BIPP_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ie));
+    // second batch of the same geometry: capture once (two graphs, so that a pending
+    // visibility upload can be waited for between them), replay from now on
+    drop_graph(h);
+    for (int part = 0; part < 2; ++part) {
+      cudaGraph_t g = nullptr;
+      CUDA_TRY(h, cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+      const int rc = enqueue_batch(h, b, plan, s, part);
+      const cudaError_t ce = cudaStreamEndCapture(s, &g);
+      if (rc) {
+        if (g) cudaGraphDestroy(g);
+        drop_graph(h);
+        return rc;
+      }
+      if (ce != cudaSuccess) {
+        drop_graph(h);
+        return fail(h, BIPP_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+      }
+      const cudaError_t ie = cudaGraphInstantiate(&h->graph[part], g, 0);
+      cudaGraphDestroy(g);
+      if (ie != cudaSuccess) {
+        h->graph[part] = nullptr;
+        drop_graph(h);
+        return fail(h, BIPP_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ie));
+      }
     }
     h->graph_key = key;
-    CUDA_TRY(h, cudaGraphLaunch(h->graph, s));
+    CUDA_TRY(h, cudaGraphLaunch(h->graph[0], s));
+    if (h->vis_pending) CUDA_TRY(h, cudaStreamWaitEvent(s, h->vis_ready, 0));
+    CUDA_TRY(h, cudaGraphLaunch(h->graph[1], s));
   } else {
-    const int rc = enqueue_batch(h, b, plan, s);
+    const int rc = enqueue_all(h, b, plan, s);
     if (rc) return rc;
   }
   h->last_key = key;
@@ -697,8 +738,16 @@ static int collect_common(bipp_ss_t h, int32_t n_t, int32_t n_st_max, const int3
   }
   const size_t N = (size_t)n_st_max;
   CUDA_TRY(h, cudaMemcpyAsync(h->d_st, st_xyz, sizeof(double) * 3 * N * n_t, cudaMemcpyHostToDevice, h->stream));
-  CUDA_TRY(h, cudaMemcpyAsync(h->d_vis, vis, sizeof(double2) * N * N * n_t, cudaMemcpyHostToDevice, h->stream));
-  return run_batch(h, n_t, n_st_max, nst_v, neig_v, chan_v, K, h->d_st, h->d_vis, h->stream, st_xyz);
+  // the visibilities on the copy stream, after the stream's earlier work (which may read d_vis)
+  CUDA_TRY(h, cudaEventRecord(h->ev_order, h->stream));
+  CUDA_TRY(h, cudaStreamWaitEvent(h->copy_stream, h->ev_order, 0));
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_vis, vis, sizeof(double2) * N * N * n_t, cudaMemcpyHostToDevice, h->copy_stream));
+  CUDA_TRY(h, cudaEventRecord(h->vis_ready, h->copy_stream));
+  h->vis_pending = true;
+  const int rb = run_batch(h, n_t, n_st_max, nst_v, neig_v, chan_v, K, h->d_st, h->d_vis, h->stream, st_xyz);
+  h->vis_pending = false;
+  if (rb) cudaStreamSynchronize(h->copy_stream);  // no upload may outlive a failed collect
+  return rb;
 }
 
 extern "C" int bipp_ss_collect_batch(bipp_ss_t h, int32_t n_t, int32_t n_st_max, const int32_t* n_st,
