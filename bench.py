@@ -492,7 +492,8 @@ def ours_main(args, ws, rank, local):
     if not args.no_e2e:
         st_h = torch.from_numpy(st).pin_memory()
         V_h = torch.from_numpy(V).pin_memory()
-        img_h = np.zeros((inp.n_level, inp.n_pix))
+        img_t = torch.zeros((inp.n_level, inp.n_pix), dtype=torch.float64).pin_memory()  # pinned, like the inputs
+        img_h = img_t.numpy()
         bipp_ss.bipp_ss_collect_batch_packed(ss.h, nst, N, st_h.data_ptr(), V_h.data_ptr())
         if dist:
             dist.barrier()
