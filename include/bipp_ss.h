@@ -110,7 +110,11 @@ typedef struct {
  *           it suits fields whose pixels resolve the array (small fields of
  *           view); nufft_partition splits it into smaller transforms, and
  *           BIPP_ERR_UNSUPPORTED reports grids that do not fit in device
- *           memory. Not with eigenimages. */
+ *           memory. The grids are planned on the host from the batch's station
+ *           coordinates, so a collect with device inputs copies those back
+ *           (one synchronisation), and collects are not captured in CUDA
+ *           graphs. The spreading sums with float atomics, so results are
+ *           reproducible to FP32 rounding, not bitwise. Not with eigenimages. */
 #define BIPP_SYNTH_STANDARD 0
 #define BIPP_SYNTH_NUFFT 1
 
