@@ -556,7 +556,7 @@ static int plan_nufft(bipp_ss* h, int n_t, int N, const std::vector<int>& nst_v,
     }
   size_t free_b = 0, total_b = 0;
   CUDA_TRY(h, cudaMemGetInfo(&free_b, &total_b));
-  const size_t have = (h->nu.F_cap + h->nu.G_cap + h->nu.rc_cap) * sizeof(float2) +
+  const size_t have = (h->nu.F_cap + h->nu.G_cap + h->nu.G2_cap + h->nu.rc_cap) * sizeof(float2) +
                       (h->nu.rm_cap + h->nu.rf_cap) * sizeof(int4);
   // grids plus the FFT's workspace (of the order of the fine grid) must fit
   if (need + fine > free_b + have)

@@ -25,8 +25,11 @@
 //   2. k_nu_const: the p = q terms (zero baseline): sum_t sum_{e in l} d_e |a_e|^2,
 //      a constant per level.
 //   3. per level: k_nu_pad divides each grid mode by the second kernel's
-//      transform and places it into the twice finer grid (zeros elsewhere);
-//      cuFFT's backward C2C transform evaluates the Fourier series there;
+//      transform and places it into the twice finer grid; cuFFT's backward
+//      C2C transforms evaluate the Fourier series there, pruned: 2-D (x, y)
+//      transforms of the M_z planes that hold modes, then the transforms
+//      along z out of place, so the other M_z planes stay zero and are never
+//      rewritten;
 //      k_nu_interp interpolates it at t = (s - D) h with the kernel, applies
 //      the trapezoid factor, the diagonal correction 1 / psi_hat(s - D) and
 //      the post-phase exp(2 pi i <s - D, C>), and adds Re + the constant to
@@ -503,10 +506,12 @@ struct GridArgs {
   int M[3], N2[3], Lp, l;
 };
 
-// Fine grid G[j] = F[m(k)] / prod_d psi2_hat_d(k_d) for modes |k_d| < M_d / 2 (k = j or j - N2), else 0.
+// Fine grid G[j] = F[m(k)] / prod_d psi2_hat_d(k_d) for modes |k_d| < M_d / 2 (k = j or j - N2), else 0,
+// on the M_2 planes j2 that hold modes (j2 < M_2 / 2 or j2 >= N2_2 - M_2 / 2; N2_2 = 2 M_2).
 __global__ void k_nu_pad(const float2* __restrict__ F, GridArgs a, const float* __restrict__ inv,
                          float2* __restrict__ G) {
-  const size_t total = (size_t)a.N2[0] * a.N2[1] * a.N2[2];
+  const size_t plane = (size_t)a.N2[0] * a.N2[1];
+  const size_t total = plane * a.M[2];
   const float* inv0 = inv;
   const float* inv1 = inv + a.M[0];
   const float* inv2 = inv1 + a.M[1];
@@ -514,7 +519,8 @@ __global__ void k_nu_pad(const float2* __restrict__ F, GridArgs a, const float* 
     const int j0 = (int)(idx % a.N2[0]);
     const size_t r = idx / a.N2[0];
     const int j1 = (int)(r % a.N2[1]);
-    const int j2 = (int)(r / a.N2[1]);
+    const int qz = (int)(r / a.N2[1]);
+    const int j2 = qz < a.M[2] / 2 ? qz : qz + a.M[2];
     const int k0 = j0 < a.N2[0] / 2 ? j0 : j0 - a.N2[0];
     const int k1 = j1 < a.N2[1] / 2 ? j1 : j1 - a.N2[1];
     const int k2 = j2 < a.N2[2] / 2 ? j2 : j2 - a.N2[2];
@@ -526,7 +532,7 @@ __global__ void k_nu_pad(const float2* __restrict__ F, GridArgs a, const float* 
       const float sc = inv0[m0] * inv1[m1] * inv2[m2];
       v = make_float2(f.x * sc, f.y * sc);
     }
-    G[idx] = v;
+    G[(size_t)j2 * plane + (size_t)j1 * a.N2[0] + j0] = v;
   }
 }
 
@@ -722,7 +728,7 @@ NuPlan nu_plan(const NuPixBox& px, int w, float beta, const int P[3], const doub
 
 size_t nu_grid_bytes(const NuPlan& p, int n_level, size_t pair_slots) {
   const int Lp = n_level == 1 ? 1 : n_level + (n_level & 1);
-  return (size_t)p.parts() * p.cells() * (Lp * sizeof(float2) + 3 * sizeof(int)) + p.cells2() * sizeof(float2) +
+  return (size_t)p.parts() * p.cells() * (Lp * sizeof(float2) + 3 * sizeof(int)) + 2 * p.cells2() * sizeof(float2) +
          pair_slots * (sizeof(int4) + sizeof(float4) + Lp * sizeof(float2));
 }
 
@@ -736,7 +742,11 @@ int nu_enqueue(const Batch& b, int t0, int t1, const NuPlan& p, NufftWs* w, cons
   if (nkeys >= (size_t)1 << 31) return -1;
   int nl = 0;
   if (!grow(&w->F, &w->F_cap, nkeys * Lp)) return -1;
+  const size_t oldG = w->G_cap;
+  const float2* oldGp = w->G;
   if (!grow(&w->G, &w->G_cap, p.cells2())) return -1;
+  if (!grow(&w->G2, &w->G2_cap, p.cells2())) return -1;
+  if (w->G != oldGp || w->G_cap != oldG) w->have_fft = false;  // new buffer: zero planes to rewrite
   if (!grow(&w->inv, &w->inv_cap, (size_t)p.M[0] + p.M[1] + p.M[2])) return -1;
   size_t corr_cap = (size_t)w->corr_cap;
   if (!grow(&w->corr, &corr_cap, (size_t)n_pix)) return -1;
@@ -873,23 +883,27 @@ int nu_enqueue(const Batch& b, int t0, int t1, const NuPlan& p, NufftWs* w, cons
     if (todo.empty()) todo.push_back(0);  // the zero-baseline constants still go into the image
   }
 
+  const long long plane = (long long)p.N2[0] * p.N2[1];
   if (!w->have_fft || w->fft_n[0] != p.N2[0] || w->fft_n[1] != p.N2[1] || w->fft_n[2] != p.N2[2]) {
-    if (w->have_fft) {
-      if (cudaStreamSynchronize(s) != cudaSuccess) return -2;  // the old plan may still be executing
-      cufftDestroy(w->fft);
-    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return -2;  // old plans may still be executing
+    if (w->fft) cufftDestroy(w->fft);
+    if (w->fftz) cufftDestroy(w->fftz);
+    w->fft = w->fftz = 0;
     w->have_fft = false;
-    if (cufftCreate(&w->fft) != CUFFT_SUCCESS) return -2;
-    long long dims[3] = {p.N2[2], p.N2[1], p.N2[0]};
     size_t ws = 0;
-    if (cufftMakePlanMany64(w->fft, 3, dims, nullptr, 1, 0, nullptr, 1, 0, CUFFT_C2C, 1, &ws) != CUFFT_SUCCESS) {
-      cufftDestroy(w->fft);
+    long long n2[2] = {p.N2[1], p.N2[0]};
+    long long nz[1] = {p.N2[2]}, ez[1] = {p.N2[2]};
+    if (cufftCreate(&w->fft) != CUFFT_SUCCESS || cufftCreate(&w->fftz) != CUFFT_SUCCESS) return -2;
+    if (cufftMakePlanMany64(w->fft, 2, n2, nullptr, 1, plane, nullptr, 1, plane, CUFFT_C2C, p.M[2] / 2, &ws) !=
+            CUFFT_SUCCESS ||
+        cufftMakePlanMany64(w->fftz, 1, nz, ez, plane, 1, ez, plane, 1, CUFFT_C2C, plane, &ws) != CUFFT_SUCCESS)
       return -2;
-    }
+    // the planes without modes are zero once and for all
+    if (cudaMemsetAsync(w->G, 0, sizeof(float2) * p.cells2(), s) != cudaSuccess) return -2;
     w->have_fft = true;
     for (int d = 0; d < 3; ++d) w->fft_n[d] = p.N2[d];
   }
-  if (cufftSetStream(w->fft, s) != CUFFT_SUCCESS) return -2;
+  if (cufftSetStream(w->fft, s) != CUFFT_SUCCESS || cufftSetStream(w->fftz, s) != CUFFT_SUCCESS) return -2;
 
   GridArgs ga;
   InterpArgs ia;
@@ -906,7 +920,7 @@ int nu_enqueue(const Batch& b, int t0, int t1, const NuPlan& p, NufftWs* w, cons
   ia.beta = p.beta;
   ia.scale = scale;
   ga.Lp = Lp;
-  const unsigned pad_grid = (unsigned)std::min<size_t>((p.cells2() + 255) / 256, (size_t)sms * 16);
+  const unsigned pad_grid = (unsigned)std::min<size_t>(((size_t)plane * p.M[2] + 255) / 256, (size_t)sms * 16);
   const unsigned pix_grid = (unsigned)((pix_cnt + 255) / 256);
   bool first = true;
   for (const int q : todo) {
@@ -918,10 +932,15 @@ int nu_enqueue(const Batch& b, int t0, int t1, const NuPlan& p, NufftWs* w, cons
       if (mark) cudaEventRecord(ev[2], s);
       k_nu_pad<<<pad_grid, 256, 0, s>>>(Fq, ga, w->inv, w->G);
       if (mark) cudaEventRecord(ev[3], s);
-      if (cufftExecC2C(w->fft, (cufftComplex*)w->G, (cufftComplex*)w->G, CUFFT_INVERSE) != CUFFT_SUCCESS) return -2;
+      cufftComplex* g = reinterpret_cast<cufftComplex*>(w->G);
+      cufftComplex* g_hi = g + (size_t)(p.N2[2] - p.M[2] / 2) * plane;  // the upper planes with modes
+      if (cufftExecC2C(w->fft, g, g, CUFFT_INVERSE) != CUFFT_SUCCESS ||
+          cufftExecC2C(w->fft, g_hi, g_hi, CUFFT_INVERSE) != CUFFT_SUCCESS ||
+          cufftExecC2C(w->fftz, g, reinterpret_cast<cufftComplex*>(w->G2), CUFFT_INVERSE) != CUFFT_SUCCESS)
+        return -2;
       if (mark) cudaEventRecord(ev[4], s);
       if (pix_cnt > 0)
-        k_nu_interp<<<pix_grid, 256, 0, s>>>(d_pix, n_pix, d_order + pix_off, pix_cnt, ia, w->G, w->corr + pix_off,
+        k_nu_interp<<<pix_grid, 256, 0, s>>>(d_pix, n_pix, d_order + pix_off, pix_cnt, ia, w->G2, w->corr + pix_off,
                                              w->cst, first ? 1 : 0, l, b.flag, img);
       if (mark) cudaEventRecord(ev[5], s);
       nl += 2;
@@ -935,8 +954,9 @@ int nu_enqueue(const Batch& b, int t0, int t1, const NuPlan& p, NufftWs* w, cons
 }
 
 void nu_free(NufftWs* w) {
-  if (w->have_fft) cufftDestroy(w->fft);
-  void* ptrs[] = {w->F, w->G, w->inv, w->corr, w->cst, w->gl, w->count, w->cursor, w->cell_off, w->seg_sum,
+  if (w->fft) cufftDestroy(w->fft);
+  if (w->fftz) cufftDestroy(w->fftz);
+  void* ptrs[] = {w->F, w->G, w->G2, w->inv, w->corr, w->cst, w->gl, w->count, w->cursor, w->cell_off, w->seg_sum,
                   w->seg_off, w->rm, w->rf, w->rc, w->bnd};
   for (void* q : ptrs)
     if (q) cudaFree(q);

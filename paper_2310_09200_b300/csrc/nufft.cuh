@@ -63,8 +63,10 @@ struct NuPlan {
 struct NufftWs {
   float2* F = nullptr;   // spread grid [M2][M1][M0][Lp] (Lp levels, even unless 1)
   size_t F_cap = 0;      // float2 elements
-  float2* G = nullptr;   // fine grid [N2_2][N2_1][N2_0]
+  float2* G = nullptr;   // fine grid [N2_2][N2_1][N2_0]: the modes; planes without modes stay zero
   size_t G_cap = 0;
+  float2* G2 = nullptr;  // its transform (the z-transform writes here, out of place)
+  size_t G2_cap = 0;
   float* inv = nullptr;  // 1 / (second kernel's transform) per mode, M0 + M1 + M2
   size_t inv_cap = 0;
   float* corr = nullptr; // per pixel (sorted order) 1 / prod_d psi_hat_d(s_d - D_d)
@@ -95,9 +97,10 @@ struct NufftWs {
   float gl_beta = 0;
   // per image cell: the kernel width, spacing and centre its part of corr was made for
   std::vector<std::vector<double>> corr_key;
-  cufftHandle fft = 0;
+  cufftHandle fft = 0;   // 2-D (x, y) transforms of the planes that hold modes, in place
+  cufftHandle fftz = 0;  // 1-D transforms along z, G -> G2
   bool have_fft = false;
-  int fft_n[3] = {};
+  int fft_n[3] = {};     // the fine grid the plans and G's zero planes were made for
   std::vector<float> h_inv;
 };
 
