@@ -360,6 +360,7 @@ def ours_main(args, ws, rank, local):
     import torch
 
     from paper_2310_09200_b300 import bipp_ss, build
+    from paper_2310_09200_b300.distributed import max_over_ranks
     build.build()
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA device")
@@ -417,9 +418,7 @@ def ours_main(args, ws, rank, local):
         dist.barrier()
     ms_total = e0.elapsed_time(e1)
     if dist:
-        x = torch.tensor([ms_total], device=f"cuda:{local}")
-        dist.all_reduce(x, op=dist.ReduceOp.MAX)
-        ms_total = float(x.item())
+        ms_total = max_over_ranks(ms_total, device=f"cuda:{local}")
     ms_step = ms_total / args.steps
     prods = inp.n_pix * inp.n_eig * n_st * inp.n_t
     value = prods * ws / (ms_step / 1e3)
@@ -506,9 +505,7 @@ def ours_main(args, ws, rank, local):
                 raise RuntimeError(bipp_ss.bipp_ss_last_error(ss.h))
         dt = (time.perf_counter() - t0) / args.steps
         if dist:
-            x = torch.tensor([dt], device=f"cuda:{local}")
-            dist.all_reduce(x, op=dist.ReduceOp.MAX)
-            dt = float(x.item())
+            dt = max_over_ranks(dt, device=f"cuda:{local}")
         e2e = {"value": prods * ws / dt, "unit": UNIT, "h2d_bytes_per_step": int(st.nbytes + V.nbytes),
                "d2h_bytes_per_step": int(img_h.nbytes)}
     ss.close()
