@@ -102,6 +102,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--mode", default="synthesis", choices=["synthesis", "grad"],
+                    help="grad: forward + backward of the differentiable level images (configuration 4)")
     ap.add_argument("--precision", default="split_fp16", choices=["fp64", "fp32", "split_bf16", "split_fp16"])
     ap.add_argument("--n-t", type=int, default=0, help="time steps per imaging job (default 100; 50 for nufft)")
     ap.add_argument("--synthesis", default="standard", choices=["standard", "nufft"])
@@ -302,9 +304,115 @@ def nufft_roofline(nt, n_level, n_pix, n_t, n_st, n_eig, hbm_gbs):
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
+    if args.mode == "grad":
+        return grad_main(args, ws, rank, local)
     if args.impl == "reference":
         return reference_main(args, ws, rank)
     return ours_main(args, ws, rank, local)
+
+
+def grad_main(args, ws, rank, local):
+    """Differentiation (configuration 4): loss = ||I_levels - I_target||^2 over 4
+    levels of 512^2 pixels from 256 stations, 16 steps, N_eig 32; forward through
+    the plain FP32 synthesis (with station gains), backward through the adjoint
+    kernel that recomputes the phases. Eigenvectors, weights and levels are
+    synthetic of the same shapes (their values do not change the work). One JSON
+    line: fwd + bwd ms per step (one step = the whole 16-step loss and its
+    gradients), the forward alone (the plain FP32 path) and their ratio."""
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "the grad mode has no CPU reference arm; "
+                              "the FP64 oracle gradient is checked in tests/test_gpu_adjoint.py"}), flush=True)
+        return 0
+    import torch
+
+    from paper_2310_09200_b300 import build, inputs
+    from paper_2310_09200_b300.autograd import synth_levels
+    from paper_2310_09200_b300.distributed import max_over_ranks
+    build.build()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    inp = inputs.make_config(4)
+    T, n_st, K, L = inp.n_t, inp.st_xyz[0].shape[0], inp.n_eig, inp.n_level
+    rng = np.random.default_rng(1004)
+    st = np.stack(inp.st_xyz)
+    W = (rng.normal(size=(T, n_st, K)) + 1j * rng.normal(size=(T, n_st, K))) / np.sqrt(n_st)
+    d = np.abs(rng.normal(size=(T, K))) * 50.0 + 1.0
+    lev = rng.integers(0, L, size=(T, K)).astype(np.int32)
+    g = inputs.gains(n_st, 0.05, rng)
+    dev = torch.device(f"cuda:{local}")
+    t_pix = torch.tensor(inp.pix, device=dev)
+    t_st = torch.tensor(st, device=dev)
+    t_d = torch.tensor(d, device=dev)
+    t_lev = torch.tensor(lev, device=dev)
+    target = torch.tensor(np.abs(rng.normal(size=(inp.n_pix, L))) * 1e3, device=dev)
+    tW = torch.tensor(W, device=dev, requires_grad=True)
+    tg = torch.tensor(g, device=dev, requires_grad=True)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(marks=None):
+        tW.grad = None
+        tg.grad = None
+        if marks:
+            marks[0].record(stream)
+        img = synth_levels(t_pix, t_st, tW, t_d, t_lev, tg, inp.wl, L)
+        if marks:
+            marks[1].record(stream)
+        loss = ((img - target) ** 2).sum()
+        loss.backward()
+        if marks:
+            marks[2].record(stream)
+        return loss
+
+    for _ in range(args.warmup):
+        step()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    marks = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        step(marks[k])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms_total = e0.elapsed_time(e1)
+    fwd = statistics.mean(m[0].elapsed_time(m[1]) for m in marks)
+    bwd = statistics.mean(m[1].elapsed_time(m[2]) for m in marks)
+    if dist:
+        dist.barrier()
+        ms_total = max_over_ranks(ms_total, device=dev)
+    ms_step = ms_total / args.steps
+    pairs = inp.n_pix * n_st * T
+    flops_bwd = pairs * (16.0 * K)  # recomputed z plus the gradient sums, complex
+    ach = flops_bwd / (bwd / 1e3) / 1e12
+    if rank == 0:
+        line = {"metric": "fwd+bwd ms per step of the differentiable level images (vs the plain FP32 forward)",
+                "value": ms_step, "unit": "ms", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32 (f64 image and gradients)", "data": "synthetic",
+                "config": {"workload": (f"differentiation: {n_st} stations, {int(round(math.sqrt(inp.n_pix)))}^2 px, "
+                                        f"{T} time steps, N_eig {K}, {L} levels, gains 1 + N(0, 0.05)"),
+                           "n_st": n_st, "n_pix": int(inp.n_pix), "n_t": T, "n_eig": K, "n_level": L},
+                "fwd_ms": fwd, "bwd_ms": bwd, "fwd_bwd_over_fp32_forward": (fwd + bwd) / fwd,
+                "roofline": {"kernel": "k_adjoint", "bound": "alu", "achieved": ach,
+                             "peak": FP32_PEAK_FLOPS / 1e12, "unit": "TFLOP/s", "traffic": None,
+                             "frac": ach / (FP32_PEAK_FLOPS / 1e12),
+                             "peak_note": "16 K flops per pixel-station pair and step (recomputed z and the "
+                                          "gradient sums) against the FP32 pipe"},
+                "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
 
 
 def reference_main(args, ws, rank):
