@@ -107,7 +107,8 @@ def parse():
     ap.add_argument("--precision", default="split_fp16", choices=["fp64", "fp32", "split_bf16", "split_fp16"])
     ap.add_argument("--n-t", type=int, default=0, help="time steps per imaging job (default 100; 50 for nufft)")
     ap.add_argument("--synthesis", default="standard", choices=["standard", "nufft"])
-    ap.add_argument("--workload", default="", choices=["", "ska_low_20deg", "nufft_4arcsec"],
+    ap.add_argument("--n-chan", type=int, default=64, help="channels of the batched workload")
+    ap.add_argument("--workload", default="", choices=["", "ska_low_20deg", "nufft_4arcsec", "batch"],
                     help="inputs (default: the 20 deg SKA-Low job for standard synthesis, the 4 arcsec field "
                          "of the paper's NUFFT comparison for nufft)")
     ap.add_argument("--nufft-eps", type=float, default=1e-5)
@@ -306,9 +307,138 @@ def main():
     ws, rank, local = dist_setup(args)
     if args.mode == "grad":
         return grad_main(args, ws, rank, local)
+    if args.workload == "batch":
+        return batch_main(args, ws, rank, local)
     if args.impl == "reference":
         return reference_main(args, ws, rank)
     return ours_main(args, ws, rank, local)
+
+
+def batch_main(args, ws, rank, local):
+    """Batched form (configuration 3): n_chan channels (wl 1.5 to 3 m) x 20 steps,
+    each step a random flagging of the 512-station layout (48 to 512 stations)
+    with 8 to 64 eigenpairs, 512^2 px; the whole batch is one collect (the
+    synthesis one persistent launch, the batch a replayed CUDA graph), level
+    bounds per channel from the library's own pre-pass."""
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "the batched workload has no CPU reference arm; "
+                              "its parity is checked in tests/test_gpu_batch.py"}), flush=True)
+        return 0
+    import torch
+
+    from paper_2310_09200_b300 import bipp_ss, build, inputs
+    from paper_2310_09200_b300.distributed import max_over_ranks
+    build.build()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    cfg = inputs.make_batch_config(n_chan=args.n_chan, n_t=args.n_t or 20, n_side=args.side if args.side != 1024 else 512)
+    pix, chans, L = cfg["pix"], cfg["channels"], cfg["n_level"]
+    wls = np.array([c["wl"] for c in chans])
+    bounds = np.stack([bipp_ss.estimate_level_bounds(c["st_xyz"][::4], c["vis"][::4], c["wl"], c["n_eig"][::4], L,
+                                                     eig_mode=args.eig)[0] for c in chans])
+    chan, st, vis, neig = [], [], [], []
+    for ci, c in enumerate(chans):
+        chan += [ci] * len(c["vis"])
+        st += c["st_xyz"]
+        vis += c["vis"]
+        neig += c["n_eig"]
+    nst, N, st_p, V_p = bipp_ss.pack_batch(st, vis)
+    dev = f"cuda:{local}"
+    d_st = torch.from_numpy(st_p).to(dev)
+    d_V = torch.from_numpy(V_p).to(dev)
+    stream = torch.cuda.Stream()
+    h = bipp_ss.bipp_ss_create_channels(pix, wls, bounds, precision=args.precision, eig_mode=args.eig,
+                                        device=local)
+    n_pix = pix.shape[0]
+    prods = float(sum(float(n_pix) * int(k) * int(n) for k, n in zip(neig, nst)))
+
+    def one_step():
+        bipp_ss.bipp_ss_collect_channels_device(h, chan, nst, d_st, d_V, n_eig=neig, stream=stream)
+        return bipp_ss.bipp_ss_get_timings(h)
+
+    for _ in range(args.warmup):
+        one_step()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    stage = np.zeros(4)
+    launches = 0
+    e0.record(stream)
+    for _ in range(args.steps):
+        t = one_step()
+        stage += [t["gram_reduce_ms"], t["eig_ms"], t["select_ms"], t["synth_ms"]]
+        launches += t["launches"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms_total = e0.elapsed_time(e1)
+    if dist:
+        dist.barrier()
+        ms_total = max_over_ranks(ms_total, device=dev)
+    K = args.steps
+    ms_step = ms_total / K
+    syn_ms = stage[3] / K
+    e2e = None
+    if not args.no_e2e:
+        st_h = torch.from_numpy(st_p).pin_memory()
+        V_h = torch.from_numpy(V_p).pin_memory()
+        img_t = torch.zeros((len(chans), L, n_pix), dtype=torch.float64).pin_memory()
+        lib = bipp_ss.load()
+        img_ptr = img_t.numpy().ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        ch = np.ascontiguousarray(chan, dtype=np.int32)
+        ne = np.ascontiguousarray(neig, dtype=np.int32)
+        nsv = np.ascontiguousarray(nst, dtype=np.int32)
+
+        def host_step():
+            rc = lib.bipp_ss_collect_channels(h, len(nsv), N, bipp_ss._ip(ch), bipp_ss._ip(nsv), bipp_ss._ip(ne),
+                                              ctypes.c_void_p(st_h.data_ptr()), ctypes.c_void_p(V_h.data_ptr()),
+                                              0, None)
+            if rc != 0 or lib.bipp_ss_get_f64(h, img_ptr) != 0:
+                raise RuntimeError(bipp_ss.bipp_ss_last_error(h))
+
+        host_step()
+        t0 = time.perf_counter()
+        for _ in range(K):
+            host_step()
+        dt = (time.perf_counter() - t0) / K
+        if dist:
+            dt = max_over_ranks(dt, device=dev)
+        e2e = {"value": prods * ws / dt, "unit": UNIT, "h2d_bytes_per_step": int(st_p.nbytes + V_p.nbytes),
+               "d2h_bytes_per_step": int(img_t.numpy().nbytes)}
+    bipp_ss.bipp_ss_destroy(h)
+    if rank == 0:
+        peaks = measured_peaks()
+        r_tc = peaks.get("bf16_tflops_sustained", 1411.3) * 1e12
+        pairs = float(sum(float(n_pix) * int(n) for n in nst))
+        t_tc, t_sfu = 3 * 8.0 * prods / r_tc, pairs / MUFU_SINCOS_PER_S
+        roof = {"kernel": "k_synth_tc", "bound": "tensor", "achieved": 3 * 8.0 * prods / (syn_ms / 1e3) / 1e12,
+                "peak": r_tc / 1e12, "unit": "TFLOP/s", "traffic": None, "frac": max(t_tc, t_sfu) / (syn_ms / 1e3),
+                "t_roof_ms": {"tensor_split": t_tc * 1e3, "sfu_sincos": t_sfu * 1e3},
+                "peak_note": "of measured: cuBLAS bf16 sustained; frac = max(T_tensor(s=3), T_sfu) / measured time"}
+        line = {"metric": METRIC, "value": prods * ws / (ms_step / 1e3), "unit": UNIT, "n_gpus": ws,
+                "steps": K, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": dtype_label(args), "data": "synthetic",
+                "config": {"workload": (f"batched: {len(chans)} channels (wl 1.5-3 m) x {len(vis) // len(chans)} "
+                                        f"steps, 48-512 stations and N_eig 8-64 per step, "
+                                        f"{int(round(math.sqrt(n_pix)))}^2 px, {L} levels, one collect"),
+                           "problems": len(vis), "n_pix": int(n_pix), "synthesis": args.precision,
+                           "eigensolve": EIG_DESC.get(args.eig), "l2": "inputs larger than L2"},
+                "stage_ms_per_step": {"gram_chol_reduce": stage[0] / K, "jacobi": stage[1] / K,
+                                      "select_pack": stage[2] / K, "synthesis": syn_ms},
+                "roofline": roof, "cpu_baseline": None, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
 
 
 def grad_main(args, ws, rank, local):
