@@ -6,7 +6,7 @@ directly (and the CPU tests pin it to the standard-synthesis images). The GPU
 path approximates it with a type-3 NUFFT of tolerance eps. Per level, the L2
 error must stay within 10 eps of max(||I_l||, ||V'_l||_F sqrt(n_pix)) plus
 2e-6 ||I_l|| for the FP32 grids: the FP64 oracle NUFFT stays within 5 eps of
-that scale (CPU pin); weak levels, whose images cancel, are judged against the
+that scale (CPU pin); weak levels, whose images cancel, are measured against the
 size of their strengths.
 """
 from __future__ import annotations

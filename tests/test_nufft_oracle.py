@@ -133,7 +133,7 @@ def test_level_visibilities_rank_one():
 def test_nufft_level_error_within_its_scale(eps):
     """On the NUFFT workload's geometry (48 stations, 40^2 pixels of 4 arcsec),
     every level's error stays within 5 eps of max(||I_l||, ||V'_l||_F sqrt(n_pix)):
-    weak levels, whose images cancel, are judged against the size of their
+    weak levels, whose images cancel, are measured against the size of their
     strengths rather than of their image (the bound the GPU tests use, doubled)."""
     inp = inputs.make_nufft_config(n_t=3, n_side=40, n_st=48)
     b = np.array([[1217.0, np.inf], [514.0, 1217.0], [255.0, 514.0], [-np.inf, 255.0]])
