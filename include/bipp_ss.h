@@ -286,8 +286,9 @@ int bipp_ss_collect_noalloc(int64_t n_pix, const double* d_pix_xyz, double wl, i
 /* Release the handle and its device memory. NULL is accepted. */
 int bipp_ss_destroy(bipp_ss_t h);
 
-/* Message of the last failing call on h (or of the last failing create when
- * h is NULL); valid until the next call on h. Never NULL. */
+/* Message of the last failing call on h (or, when h is NULL, of this
+ * thread's last failing call without a handle: create and the estimation
+ * functions); valid until the next such call. Never NULL. */
 const char* bipp_ss_last_error(bipp_ss_t h);
 
 /* ---- parameter estimation (Sec. 2.6 "Energy Levels & Partitioning"), host only

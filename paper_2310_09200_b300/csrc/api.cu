@@ -117,7 +117,8 @@ struct bipp_ss {
   std::string err;
 };
 
-static std::string g_create_err = "no error";
+// per calling thread, so that creates on distinct threads do not share it
+static thread_local std::string g_create_err = "no error";
 
 // Error message of calls without a handle (create, the estimation functions).
 int bipp::set_global_error(int code, const char* msg) {
@@ -457,17 +458,17 @@ static int enqueue_batch(bipp_ss* h, const Batch& b, const TcPlan& plan, cudaStr
   const int T = b.T;
   const int gi = h->opt.gram_identity;
   if (part == 0) {
-  CUDA_TRY(h, cudaMemcpyAsync(h->d_nst, h->h_nst, sizeof(int) * T, cudaMemcpyHostToDevice, s));
-  CUDA_TRY(h, cudaMemcpyAsync(h->d_neig, h->h_neig, sizeof(int) * T, cudaMemcpyHostToDevice, s));
-  CUDA_TRY(h, cudaMemcpyAsync(h->d_chan, h->h_chan, sizeof(int) * T, cudaMemcpyHostToDevice, s));
-  CUDA_TRY(h, cudaMemcpyAsync(h->d_wl, h->h_wl, sizeof(double) * T, cudaMemcpyHostToDevice, s));
-  CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int) * T, s));
-  CUDA_TRY(h, cudaMemsetAsync(h->d_sweeps, 0, sizeof(int) * T, s));
-  CUDA_TRY(h, cudaMemsetAsync(h->d_flag, 0, sizeof(int), s));
-  CUDA_TRY(h, record(h->ev[0], s));
-  launch_gram(b, gi, s);
-  launch_cholesky(b, gi, s);
-  return cudaGetLastError() == cudaSuccess ? BIPP_OK : fail(h, BIPP_ERR_CUDA, "Gram / Cholesky launch failed");
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_nst, h->h_nst, sizeof(int) * T, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_neig, h->h_neig, sizeof(int) * T, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_chan, h->h_chan, sizeof(int) * T, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_wl, h->h_wl, sizeof(double) * T, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int) * T, s));
+    CUDA_TRY(h, cudaMemsetAsync(h->d_sweeps, 0, sizeof(int) * T, s));
+    CUDA_TRY(h, cudaMemsetAsync(h->d_flag, 0, sizeof(int), s));
+    CUDA_TRY(h, record(h->ev[0], s));
+    launch_gram(b, gi, s);
+    launch_cholesky(b, gi, s);
+    return cudaGetLastError() == cudaSuccess ? BIPP_OK : fail(h, BIPP_ERR_CUDA, "Gram / Cholesky launch failed");
   }
   launch_reduce(b, gi, s);
   CUDA_TRY(h, record(h->ev[1], s));
@@ -698,8 +699,13 @@ static int run_batch(bipp_ss* h, int n_t, int N, const std::vector<int>& nst_v, 
     if (status[t] & kStatusNotPD)
       return fail(h, BIPP_ERR_GRAM_NOT_PD, "step %d: Gram matrix is not positive definite (Cholesky pivot <= 0 or NaN)", t);
     if (status[t] & kStatusNotConverged)
-      return fail(h, BIPP_ERR_EIG_NOT_CONVERGED, "step %d: Jacobi did not converge in %d sweeps", t,
-                  h->opt.max_jacobi_sweeps);
+      return h->mixed_kp > 0
+                 ? fail(h, BIPP_ERR_EIG_NOT_CONVERGED,
+                        "step %d: mixed eigensolver did not converge (QR step cap, refinement Jacobi sweep cap %d, "
+                        "or a kept residual above 1e3 * jacobi_tol * ||C||_F)",
+                        t, h->opt.max_jacobi_sweeps)
+                 : fail(h, BIPP_ERR_EIG_NOT_CONVERGED, "step %d: Jacobi did not converge in %d sweeps", t,
+                        h->opt.max_jacobi_sweeps);
   }
   if (tc_status) return fail(h, BIPP_ERR_DEVICE_TIMEOUT, "tensor-core synthesis: bounded wait gave up (code %d)", tc_status);
   return BIPP_OK;
