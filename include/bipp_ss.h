@@ -52,7 +52,7 @@ extern "C" {
 #define BIPP_ERR_CUDA (-2)              /* a CUDA runtime call failed */
 #define BIPP_ERR_OUT_OF_MEMORY (-3)     /* device allocation failed */
 #define BIPP_ERR_GRAM_NOT_PD (-4)       /* Cholesky of G met a non-positive (or NaN) pivot */
-#define BIPP_ERR_EIG_NOT_CONVERGED (-5) /* Jacobi hit max_jacobi_sweeps */
+#define BIPP_ERR_EIG_NOT_CONVERGED (-5) /* an eigensolver iteration cap was hit (or a kept residual too large) */
 #define BIPP_ERR_DEVICE_TIMEOUT (-6)    /* a bounded device-side wait gave up */
 #define BIPP_ERR_UNSUPPORTED (-7)       /* e.g. n_eig > n_st, sizes beyond limits */
 
@@ -175,11 +175,22 @@ int bipp_ss_collect_batch(bipp_ss_t h, int32_t n_t, int32_t n_st_max, const int3
  * on the device (e.g. memory owned by PyTorch), stream-ordered on `stream`
  * (a cudaStream_t; NULL = the handle's stream). n_st / n_eig are host arrays
  * of n_t int32 (n_eig NULL = handle default). Values are not inspected on the
- * host: a non-finite position surfaces as BIPP_ERR_GRAM_NOT_PD. Returns after
- * the batch has run and its per-step status was read (one host sync). */
+ * host: a non-finite position surfaces as BIPP_ERR_GRAM_NOT_PD. d_st_xyz
+ * must be 8-byte and d_vis 16-byte aligned (BIPP_ERR_INVALID_ARG otherwise).
+ * Returns after the batch has run and its per-step status was read (one host
+ * sync). */
 int bipp_ss_collect_device(bipp_ss_t h, int32_t n_t, int32_t n_st_max, const int32_t* n_st,
                            const int32_t* n_eig, const double* d_st_xyz, const double* d_vis,
                            void* stream);
+
+/* As bipp_ss_collect_device with complex64 visibilities: d_vis holds n_t
+ * blocks of n_st_max x n_st_max interleaved (re, im) floats, column-major
+ * (8-byte aligned). They are widened to complex128 on the device, in stream
+ * order, into the handle's batch buffer; the rest of the batch is identical
+ * to bipp_ss_collect_device on the widened values. */
+int bipp_ss_collect_device_c64(bipp_ss_t h, int32_t n_t, int32_t n_st_max, const int32_t* n_st,
+                               const int32_t* n_eig, const double* d_st_xyz, const float* d_vis,
+                               void* stream);
 
 /* Copy the accumulated images (n_pix x n_level column-major per channel,
  * channels consecutive) to host memory. */

@@ -51,7 +51,7 @@ EXPORTED = [
     "bipp_ss_set_images", "bipp_ss_last_eigvals", "bipp_ss_get_timings", "bipp_ss_destroy",
     "bipp_ss_last_error", "bipp_ss_collect_noalloc", "bipp_ss_synth_levels_device",
     "bipp_ss_synth_adjoint_device", "bipp_ss_create_channels", "bipp_ss_collect_channels",
-    "bipp_ss_energy_neig", "bipp_ss_kmeans_bounds", "bipp_ss_get_nufft_timings",
+    "bipp_ss_energy_neig", "bipp_ss_kmeans_bounds", "bipp_ss_get_nufft_timings", "bipp_ss_collect_device_c64",
 ]
 
 BIPP_NOALLOC_MAX_STATIONS = 128
@@ -95,6 +95,7 @@ def load(path: str | None = None):
     L.bipp_ss_collect.argtypes = [H, i32, dp, dp]
     L.bipp_ss_collect_batch.argtypes = [H, i32, i32, ip, ip, dp, dp]
     L.bipp_ss_collect_device.argtypes = [H, i32, i32, ip, ip, vp, vp, vp]
+    L.bipp_ss_collect_device_c64.argtypes = [H, i32, i32, ip, ip, vp, vp, vp]
     L.bipp_ss_get.argtypes = [H, C.POINTER(C.c_float)]
     L.bipp_ss_get_f64.argtypes = [H, dp]
     L.bipp_ss_get_device_f64.argtypes = [H, vp, vp]
@@ -263,16 +264,30 @@ def bipp_ss_collect_batch_packed(h, nst, n_st_max: int, st_addr: int, vis_addr: 
 
 def bipp_ss_collect_device(h, n_st, d_st, d_vis, n_eig=None, stream=None) -> None:
     """Device variant. d_st: torch float64 (T, 3, N) contiguous; d_vis: torch
-    complex128 (T, N, N) holding each block column-major (i.e. V[t].T, as
-    ``pack_batch`` returns); n_st / n_eig host int sequences; stream: a
-    torch.cuda.Stream or None (the handle's stream)."""
+    complex128 or complex64 (T, N, N) contiguous, holding each block
+    column-major (i.e. V[t].T, as ``pack_batch`` returns; complex64 goes
+    through bipp_ss_collect_device_c64); n_st / n_eig host int sequences;
+    stream: a torch.cuda.Stream or None (the handle's stream)."""
     nst = np.ascontiguousarray(n_st, dtype=np.int32)
     ne = None if n_eig is None else np.ascontiguousarray(n_eig, dtype=np.int32)
     N = int(d_st.shape[-1])
     sp = None if stream is None else C.c_void_p(stream.cuda_stream)
-    rc = load().bipp_ss_collect_device(h, len(nst), N, _ip(nst), None if ne is None else _ip(ne),
-                                       C.c_void_p(d_st.data_ptr()), C.c_void_p(d_vis.data_ptr()), sp)
+    dt = str(d_vis.dtype)
+    if (dt not in ("torch.complex128", "torch.complex64") or str(d_st.dtype) != "torch.float64"
+            or not d_vis.is_contiguous() or not d_st.is_contiguous()):
+        raise ValueError("d_st must be contiguous float64 and d_vis contiguous complex128 or complex64")
+    fn = load().bipp_ss_collect_device_c64 if dt == "torch.complex64" else load().bipp_ss_collect_device
+    rc = fn(h, len(nst), N, _ip(nst), None if ne is None else _ip(ne), C.c_void_p(d_st.data_ptr()),
+            C.c_void_p(d_vis.data_ptr()), sp)
     _check(h, rc)
+
+
+def bipp_ss_collect_device_c64(h, n_st, d_st, d_vis, n_eig=None, stream=None) -> None:
+    """bipp_ss_collect_device with complex64 visibilities (d_vis a torch
+    complex64 (T, N, N) tensor, blocks column-major)."""
+    if str(d_vis.dtype) != "torch.complex64":
+        raise ValueError("d_vis must be complex64")
+    bipp_ss_collect_device(h, n_st, d_st, d_vis, n_eig, stream)
 
 
 def bipp_ss_get(h, n_pix: int, n_level: int, n_chan: int = 1) -> np.ndarray:

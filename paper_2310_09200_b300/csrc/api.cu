@@ -711,9 +711,11 @@ static int run_batch(bipp_ss* h, int n_t, int N, const std::vector<int>& nst_v, 
   return BIPP_OK;
 }
 
+// on_device: the inputs are device memory; vis_c64: (device only) the
+// visibilities are complex64 and are widened into the batch buffer first.
 static int collect_common(bipp_ss_t h, int32_t n_t, int32_t n_st_max, const int32_t* chan, const int32_t* n_st,
-                          const int32_t* n_eig, const double* st_xyz, const double* vis, int on_device,
-                          void* stream) {
+                          const int32_t* n_eig, const double* st_xyz, const void* vis, int on_device,
+                          void* stream, int vis_c64 = 0) {
   if (!h) return fail(nullptr, BIPP_ERR_INVALID_ARG, "handle is NULL");
   if (!st_xyz || !vis) return fail(h, BIPP_ERR_INVALID_ARG, "st_xyz / vis is NULL");
   std::vector<int> nst_v, neig_v, chan_v;
@@ -728,6 +730,9 @@ static int collect_common(bipp_ss_t h, int32_t n_t, int32_t n_st_max, const int3
       cudaGetLastError();
       return fail(h, BIPP_ERR_INVALID_ARG, "st_xyz and vis must be device memory on device %d", h->device);
     }
+    // the kernels load doubles and complex pairs
+    if ((reinterpret_cast<uintptr_t>(st_xyz) & 7) || (reinterpret_cast<uintptr_t>(vis) & (vis_c64 ? 7 : 15)))
+      return fail(h, BIPP_ERR_INVALID_ARG, "d_st_xyz must be 8-byte and d_vis %d-byte aligned", vis_c64 ? 8 : 16);
   } else {
     for (int t = 0; t < n_t; ++t)
       for (int c = 0; c < 3; ++c)
@@ -739,8 +744,13 @@ static int collect_common(bipp_ss_t h, int32_t n_t, int32_t n_st_max, const int3
   if (rc) return rc;
   if (on_device) {
     cudaStream_t s = stream ? (cudaStream_t)stream : h->stream;
-    return run_batch(h, n_t, n_st_max, nst_v, neig_v, chan_v, K, st_xyz, reinterpret_cast<const double2*>(vis), s,
-                     nullptr);
+    const double2* d_vis = reinterpret_cast<const double2*>(vis);
+    if (vis_c64) {  // stream-ordered after the caller's writes; the batch then reads the widened copy
+      launch_vis_widen(reinterpret_cast<const float2*>(vis), h->d_vis, (size_t)n_t * n_st_max * n_st_max, s);
+      CUDA_TRY(h, cudaGetLastError());
+      d_vis = h->d_vis;
+    }
+    return run_batch(h, n_t, n_st_max, nst_v, neig_v, chan_v, K, st_xyz, d_vis, s, nullptr);
   }
   const size_t N = (size_t)n_st_max;
   CUDA_TRY(h, cudaMemcpyAsync(h->d_st, st_xyz, sizeof(double) * 3 * N * n_t, cudaMemcpyHostToDevice, h->stream));
@@ -769,6 +779,12 @@ extern "C" int bipp_ss_collect_device(bipp_ss_t h, int32_t n_t, int32_t n_st_max
                                       const int32_t* n_eig, const double* d_st_xyz, const double* d_vis,
                                       void* stream) {
   return collect_common(h, n_t, n_st_max, nullptr, n_st, n_eig, d_st_xyz, d_vis, 1, stream);
+}
+
+extern "C" int bipp_ss_collect_device_c64(bipp_ss_t h, int32_t n_t, int32_t n_st_max, const int32_t* n_st,
+                                          const int32_t* n_eig, const double* d_st_xyz, const float* d_vis,
+                                          void* stream) {
+  return collect_common(h, n_t, n_st_max, nullptr, n_st, n_eig, d_st_xyz, d_vis, 1, stream, 1);
 }
 
 extern "C" int bipp_ss_collect_channels(bipp_ss_t h, int32_t n_t, int32_t n_st_max, const int32_t* chan,

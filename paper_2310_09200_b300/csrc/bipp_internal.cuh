@@ -94,6 +94,8 @@ int set_global_error(int code, const char* msg);
 // d_bounds: per channel, n_level x 2 column-major blocks.
 void launch_select(const Batch& b, int n_level, const double* d_bounds, int filter, cudaStream_t s);
 void launch_pixel_split(const double* d_xyz, float* d_hl, int64_t n, cudaStream_t s);
+// n complex64 values widened into complex128 (the batch visibility buffer).
+void launch_vis_widen(const float2* d_in, double2* d_out, size_t n, cudaStream_t s);
 
 // Synthesis of a whole batch into img (per channel c: n_pix x n_level FP64 at
 // img + c * n_level * n_pix, accumulated).

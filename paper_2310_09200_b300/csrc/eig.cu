@@ -528,6 +528,15 @@ __global__ void k_pixel_split(const double* xyz, float* hl, int64_t n) {
   }
 }
 
+// Complex64 visibilities widened to complex128 (exact), grid-stride.
+__global__ void k_vis_widen(const float2* __restrict__ in, double2* __restrict__ out, size_t n) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const float2 v = in[i];
+    out[i] = make_double2((double)v.x, (double)v.y);
+  }
+}
+
 }  // namespace
 
 void launch_gram(const Batch& b, int gram_identity, cudaStream_t s) {
@@ -582,6 +591,12 @@ void launch_select(const Batch& b, int n_level, const double* d_bounds, int filt
 
 void launch_pixel_split(const double* d_xyz, float* d_hl, int64_t n, cudaStream_t s) {
   k_pixel_split<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_xyz, d_hl, n);
+}
+
+void launch_vis_widen(const float2* d_in, double2* d_out, size_t n, cudaStream_t s) {
+  if (n == 0) return;
+  const size_t blocks = std::min<size_t>((n + 255) / 256, (size_t)148 * 16);
+  k_vis_widen<<<(unsigned)blocks, 256, 0, s>>>(d_in, d_out, n);
 }
 
 }  // namespace bipp

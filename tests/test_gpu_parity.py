@@ -193,6 +193,46 @@ def test_device_pointer_variant_matches_oracle():
     np.testing.assert_array_equal(out.cpu().numpy().T, got)
 
 
+def test_device_complex64_visibilities():
+    """complex64 device visibilities (widened on the device) give the images of
+    the same values passed as complex128, and those of the oracle on them."""
+    import dataclasses
+    import torch
+    inp = inputs.make_config(0, n_t=3, n_side=16)
+    inp = dataclasses.replace(inp, vis=[v.astype(np.complex64).astype(np.complex128) for v in inp.vis])
+    bounds, _ = helpers.oracle_prepass_bounds(inp)
+    want, _, _ = oracle_images(inp, bounds)
+    nst, N, st, V = bipp_ss.pack_batch(inp.st_xyz, inp.vis)
+    d_st = torch.from_numpy(st).cuda()
+    stream = torch.cuda.Stream()
+    got = {}
+    for dt in (np.complex64, np.complex128):
+        with bipp_ss.StandardSynthesis(inp.pix, inp.wl, bounds, n_eig=inp.n_eig, precision="fp32") as ss:
+            bipp_ss.bipp_ss_collect_device(ss.h, nst, d_st, torch.from_numpy(V.astype(dt)).cuda(), stream=stream)
+            got[dt] = ss.get()
+    np.testing.assert_allclose(got[np.complex64], got[np.complex128], rtol=1e-12, atol=0)
+    assert np.all(rel_l2_per_level(got[np.complex64], want) <= TOL["fp32"])
+
+
+def test_device_variant_rejects_misaligned_pointers():
+    """The device variants check pointer alignment on the host, before any
+    launch: d_vis 8 bytes into an allocation is not a complex128 array."""
+    import ctypes
+    import torch
+    inp = inputs.make_config(0, n_t=1, n_side=8)
+    b = np.array([[-np.inf, np.inf]])
+    nst, N, st, V = bipp_ss.pack_batch(inp.st_xyz, inp.vis)
+    d_st = torch.from_numpy(st).cuda()
+    buf = torch.zeros(2 * V.size + 2, dtype=torch.float64, device="cuda")
+    L = bipp_ss.load()
+    with bipp_ss.StandardSynthesis(inp.pix, inp.wl, b, n_eig=4, precision="fp32") as ss:
+        rc = L.bipp_ss_collect_device(ss.h, 1, N, bipp_ss._ip(nst), None, ctypes.c_void_p(d_st.data_ptr()),
+                                      ctypes.c_void_p(buf.data_ptr() + 8), None)
+        assert rc == bipp_ss.BIPP_ERR_INVALID_ARG
+        assert "aligned" in bipp_ss.bipp_ss_last_error(ss.h)
+        assert np.all(ss.get() == 0.0)
+
+
 def test_checkpoint_resume_is_additive():
     inp = inputs.make_config(0, n_t=4, n_side=16)
     b = np.array([[-np.inf, np.inf]])
