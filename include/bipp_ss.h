@@ -232,6 +232,18 @@ int bipp_ss_get_timings(bipp_ss_t h, double* out6);
  * width w, out[10] the number of baselines spread. Zeros for STANDARD. */
 int bipp_ss_get_nufft_timings(bipp_ss_t h, double* out11);
 
+/* Fault injection for tests of failure detection (no GPU fault): while on
+ * (1), the tensor-core synthesis kernel (BIPP_PREC_SPLIT_*) makes its MMA
+ * issuer wait on a shared-memory barrier phase that nothing completes. Its
+ * bounded wait runs out after ~2 s; the kernel then sets its abort flag, the
+ * other warps leave their own bounded waits, copies in flight land, TMEM is
+ * released, and the collect returns BIPP_ERR_DEVICE_TIMEOUT with the images
+ * unchanged (nothing is added before the first accumulator is complete).
+ * Off (0, the default) restores normal operation; the switch is a device
+ * word read at launch, so captured CUDA graphs follow it. Other synthesis
+ * paths have no such waits and ignore it. */
+int bipp_ss_debug_fail_wait(bipp_ss_t h, int32_t on);
+
 /* Differentiable synthesis with complex station gains (device pointers,
  * e.g. PyTorch memory; stream-ordered on `stream`, NULL = default stream;
  * returns after the work has finished).

@@ -52,6 +52,7 @@ EXPORTED = [
     "bipp_ss_last_error", "bipp_ss_collect_noalloc", "bipp_ss_synth_levels_device",
     "bipp_ss_synth_adjoint_device", "bipp_ss_create_channels", "bipp_ss_collect_channels",
     "bipp_ss_energy_neig", "bipp_ss_kmeans_bounds", "bipp_ss_get_nufft_timings", "bipp_ss_collect_device_c64",
+    "bipp_ss_debug_fail_wait",
 ]
 
 BIPP_NOALLOC_MAX_STATIONS = 128
@@ -104,6 +105,7 @@ def load(path: str | None = None):
     L.bipp_ss_last_eigvals.argtypes = [H, i32, i32, ip, ip, dp, ip]
     L.bipp_ss_get_timings.argtypes = [H, dp]
     L.bipp_ss_get_nufft_timings.argtypes = [H, dp]
+    L.bipp_ss_debug_fail_wait.argtypes = [H, i32]
     L.bipp_ss_destroy.argtypes = [H]
     L.bipp_ss_energy_neig.argtypes = [i32, dp, C.c_double, ip]
     L.bipp_ss_kmeans_bounds.argtypes = [i32, dp, i32, dp]
@@ -341,6 +343,13 @@ def bipp_ss_get_nufft_timings(h) -> dict:
     _check(h, load().bipp_ss_get_nufft_timings(h, _dp(a)))
     return {"sort_ms": a[0], "spread_ms": a[1], "pad_ms": a[2], "fft_ms": a[3], "interp_ms": a[4],
             "levels_ms": a[5], "grid": (int(a[6]), int(a[7]), int(a[8])), "w": int(a[9]), "points": int(a[10])}
+
+
+def bipp_ss_debug_fail_wait(h, on: bool) -> None:
+    """Fault injection for failure-detection tests: while on, the tensor-core
+    synthesis kernel's bounded wait runs out and collects raise
+    BIPP_ERR_DEVICE_TIMEOUT (no GPU fault)."""
+    _check(h, load().bipp_ss_debug_fail_wait(h, 1 if on else 0))
 
 
 def bipp_ss_destroy(h) -> None:

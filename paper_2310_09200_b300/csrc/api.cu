@@ -88,6 +88,7 @@ struct bipp_ss {
   TcWorkspace tc{};
   MixedWs mx{};
   int mixed_kp = 0;  // KP of the current batch when the mixed eigensolver runs, else 0
+  int fail_wait = 0; // fault injection into the tensor-core kernel's bounded waits (tests)
   // NUFFT synthesis: pixel box, kernel, and the current batch's per-channel plans
   NuPixCells nu_cells;     // image cells (pixels sorted by cell, ranges, boxes)
   int* d_nu_order = nullptr;  // the sorted pixel order on the device
@@ -221,6 +222,7 @@ static int ensure_batch(bipp_ss* h, int T, int N, int K) {
   CUDA_TRY(h, cudaMallocHost(&h->h_chan, sizeof(int) * T));
   CUDA_TRY(h, cudaMallocHost(&h->h_wl, sizeof(double) * T));
   if (tc_alloc(&h->tc, T, N, K)) return fail(h, BIPP_ERR_OUT_OF_MEMORY, "tensor-core workspace allocation failed");
+  if (h->fail_wait && tc_set_fail_wait(&h->tc, 1)) return fail(h, BIPP_ERR_CUDA, "fault-injection word");
   h->cap_T = T;
   h->cap_N = N;
   h->cap_K = K;
@@ -864,6 +866,16 @@ extern "C" int bipp_ss_last_eigvals(bipp_ss_t h, int32_t n_t_cap, int32_t n_eig_
       if (level) level[(size_t)t * n_eig_cap + e] = lv[(size_t)t * K + e];
     }
   }
+  return BIPP_OK;
+}
+
+extern "C" int bipp_ss_debug_fail_wait(bipp_ss_t h, int32_t on) {
+  if (!h) return fail(nullptr, BIPP_ERR_INVALID_ARG, "handle is NULL");
+  if (on != 0 && on != 1) return fail(h, BIPP_ERR_INVALID_ARG, "on must be 0 or 1");
+  CUDA_TRY(h, cudaSetDevice(h->device));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  if (tc_set_fail_wait(&h->tc, on)) return fail(h, BIPP_ERR_CUDA, "fault-injection word");
+  h->fail_wait = on;
   return BIPP_OK;
 }
 

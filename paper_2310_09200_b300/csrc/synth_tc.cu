@@ -414,6 +414,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       int unit = 0;
       bool ok = true;
       bool issued = false;
+      // fault injection (status[1] set by the host): wait for a phase of bar_drain
+      // that nothing completes, so that the bounded wait runs out and the abort
+      // path below runs
+      if (status[1] != 0) ok = mbar_wait(smem_u32(&bar_drain), 0, &s_abort);
       for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
         for (int t = 0; t < T && ok; ++t, ++unit) {
           const TcStep st = steps[t];
@@ -646,7 +650,8 @@ int tc_alloc(TcWorkspace* w, int T, int N, int K) {
   w->qfix_stride = n_chunks_for(N) * kStations;
   if (cudaMalloc(&w->qfix, sizeof(uint32_t) * 8 * (size_t)T * w->qfix_stride) != cudaSuccess) return -1;
   if (cudaMalloc(&w->lwt, sizeof(int2) * (size_t)T * kTcMaxEig) != cudaSuccess) return -1;
-  if (cudaMalloc(&w->status, sizeof(int)) != cudaSuccess) return -1;
+  if (cudaMalloc(&w->status, 2 * sizeof(int)) != cudaSuccess) return -1;
+  if (cudaMemset(w->status, 0, 2 * sizeof(int)) != cudaSuccess) return -1;
   w->cap_T = T;
   return 0;
 }
@@ -660,6 +665,11 @@ void tc_free(TcWorkspace* w) {
   if (w->lwt) cudaFree(w->lwt);
   if (w->status) cudaFree(w->status);
   *w = TcWorkspace{};
+}
+
+int tc_set_fail_wait(TcWorkspace* w, int on) {
+  if (!w->status) return 0;
+  return cudaMemcpy(w->status + 1, &on, sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess ? 0 : -1;
 }
 
 int tc_read_status(TcWorkspace* w) {

@@ -33,7 +33,7 @@ struct TcWorkspace {
   uint32_t* qfix = nullptr;    // [cap_T][chunks * 32][8] station p/wl in 40.24 fixed point (see k_tc_pack)
   int qfix_stride = 0;         // stations per step in qfix (32 * chunks of n_max)
   int2* lwt = nullptr;         // [cap_T][kTcMaxEig] (level, FP32 weight / scale^2) per accumulator column pair
-  int* status = nullptr;       // [1] device error word (0 = ok)
+  int* status = nullptr;       // [2] device error word (0 = ok), fault-injection word (0 = off)
   int cap_T = 0;
 };
 
@@ -50,6 +50,10 @@ struct TcPlan {
 int tc_alloc(TcWorkspace* w, int T, int N, int K);
 void tc_free(TcWorkspace* w);
 int tc_read_status(TcWorkspace* w);  // 0 or the device error word
+// Fault injection for tests: while on, the synthesis kernel's MMA issuer waits
+// on a barrier phase that nothing completes until its bounded wait runs out.
+// Synchronous; 0, or -1 if the copy failed. No-op before the workspace exists.
+int tc_set_fail_wait(TcWorkspace* w, int on);
 // Host side: step table into pinned memory and the launch plan. Returns 0,
 // -3 if some step has n_eig > kTcMaxEig, other negatives on capacity errors.
 int tc_prepare(const std::vector<int>& nst, const std::vector<int>& neig, bool fp16, TcWorkspace* w, TcPlan* p);
