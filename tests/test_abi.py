@@ -160,3 +160,26 @@ def test_quantile_level_bounds_host_logic():
     assert b[0, 1] == np.inf and b[-1, 0] == -np.inf
     np.testing.assert_allclose(b[:, 0][:3], [9.5, 6.5, 3.5])
     np.testing.assert_allclose(b[1:, 1], [9.5, 6.5, 3.5])
+
+
+def test_device_collect_checks_tensor_types_before_the_library():
+    """The device collect's binding accepts float64 positions and complex128 or
+    complex64 visibilities, contiguous; anything else is refused on the host
+    before the library is called (the handle is never dereferenced here)."""
+    import torch
+    st = torch.zeros((1, 3, 4), dtype=torch.float64)
+    bad = [
+        (st, torch.zeros((1, 4, 4), dtype=torch.float64)),            # real visibilities
+        (st.float(), torch.zeros((1, 4, 4), dtype=torch.complex128)),  # float32 positions
+        (st, torch.zeros((1, 4, 8), dtype=torch.complex128)[:, :, ::2]),  # non-contiguous
+    ]
+    for d_st, d_vis in bad:
+        with pytest.raises(ValueError):
+            bipp_ss.bipp_ss_collect_device(None, [4], d_st, d_vis)
+    with pytest.raises(ValueError):
+        bipp_ss.bipp_ss_collect_device_c64(None, [4], st, torch.zeros((1, 4, 4), dtype=torch.complex128))
+
+
+def test_fault_injection_switch_rejects_null_handle(lib):
+    assert lib.bipp_ss_debug_fail_wait(None, 1) == bipp_ss.BIPP_ERR_INVALID_ARG
+    assert b"NULL" in lib.bipp_ss_last_error(None)
