@@ -325,3 +325,19 @@ def test_eigenimages_partition_and_closed_form():
         np.testing.assert_allclose(eig[:, e], want, rtol=1e-10, atol=1e-12 * np.max(np.abs(want)))
     std = helpers.oracle_eigenimages(pix, wl, [p], [V], n_eig, filter="std")
     assert np.all(std >= 0.0)
+
+
+def test_single_station_degenerate_case():
+    """One station: G = [1], V = [v] with v > 0, so mu = v and a = [1] (A^H G A = 1),
+    and |Phi(r) a|^2 = 1 at every pixel: the LSQ image is v everywhere, the STD
+    image 1, each in the level holding v; the other levels stay zero."""
+    pix = inputs.pixel_grid(5, 10.0)
+    p = np.array([[1234.5, -321.0, 2.5]])
+    v = 37.25
+    bounds = np.array([[100.0, np.inf], [10.0, 100.0], [-np.inf, 10.0]])
+    for filt, want_val in (("lsq", v), ("std", 1.0)):
+        img, mu, lev, W = oracle.ss_step(pix, 2.0, bounds, 1, p, np.array([[v + 0j]]), filter=filt)
+        assert mu[0] == pytest.approx(v, rel=1e-15) and lev[0] == 1
+        assert abs(abs(W[0, 0]) - 1.0) < 1e-15
+        np.testing.assert_allclose(img[:, 1], want_val, rtol=1e-13)
+        assert np.all(img[:, [0, 2]] == 0.0)
