@@ -305,12 +305,15 @@ def nufft_roofline(nt, n_level, n_pix, n_t, n_st, n_eig, hbm_gbs):
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        if args.mode == "grad" or args.workload == "batch":
+            raise SystemExit("--impl reference times the oracle on the synthesis workloads only "
+                             "(not --mode grad or --workload batch)")
+        return reference_main(args, ws, rank)
     if args.mode == "grad":
         return grad_main(args, ws, rank, local)
     if args.workload == "batch":
         return batch_main(args, ws, rank, local)
-    if args.impl == "reference":
-        return reference_main(args, ws, rank)
     return ours_main(args, ws, rank, local)
 
 
@@ -564,7 +567,7 @@ def reference_main(args, ws, rank):
         sample = (f"1 of {inp.n_t} time steps per bench step: FP64 Gram + Jacobi eigensolve of 512 stations and "
                   f"the FP64 numpy type-3 NUFFT of its 4 level visibilities onto the central {samples[0]['n_sub']} "
                   f"pixels; products/s of that sample (no warm-up: each sample is a whole oracle run)")
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "gpu_used": False, "steps": args.steps,
                 "warmup": 0, "ms_per_step": job_ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
                 "config": config_dict(args, inp, "fp64 (oracle)"),
@@ -584,7 +587,7 @@ def reference_main(args, ws, rank):
     sample = (f"1 of {inp.n_t} time steps per bench step: FP64 Gram + Jacobi eigensolve (single thread) of 512 "
               f"stations, then synthesis of a strided {samples[0]['n_sub']}-pixel subset (OpenMP over pixels); "
               f"per-step time extrapolated linearly to {inp.n_pix} pixels and to {inp.n_t} steps")
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "gpu_used": False, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": full_job_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": config_dict(args, inp, "fp64 (oracle)"),
