@@ -175,7 +175,9 @@ int bipp_ss_collect_batch(bipp_ss_t h, int32_t n_t, int32_t n_st_max, const int3
  * on the device (e.g. memory owned by PyTorch), stream-ordered on `stream`
  * (a cudaStream_t; NULL = the handle's stream). n_st / n_eig are host arrays
  * of n_t int32 (n_eig NULL = handle default). Values are not inspected on the
- * host: a non-finite position surfaces as BIPP_ERR_GRAM_NOT_PD. d_st_xyz
+ * host: a non-finite position surfaces as BIPP_ERR_GRAM_NOT_PD (as
+ * BIPP_ERR_INVALID_ARG with BIPP_SYNTH_NUFFT, which plans its grids from a
+ * host copy of the positions). d_st_xyz
  * must be 8-byte and d_vis 16-byte aligned (BIPP_ERR_INVALID_ARG otherwise).
  * Returns after the batch has run and its per-step status was read (one host
  * sync). */

@@ -530,6 +530,12 @@ static int plan_nufft(bipp_ss* h, int n_t, int N, const std::vector<int>& nst_v,
     CUDA_TRY(h, cudaMemcpyAsync(h->nu_st.data(), d_st, sizeof(double) * h->nu_st.size(), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(h, cudaStreamSynchronize(s));
     h_st = h->nu_st.data();
+    // the grids are planned from these values: device positions are checked here
+    for (int t = 0; t < n_t; ++t)
+      for (int c = 0; c < 3; ++c)
+        for (int i = 0; i < nst_v[t]; ++i)
+          if (!isfinite(h_st[((size_t)t * 3 + c) * N + i]))
+            return fail(h, BIPP_ERR_INVALID_ARG, "step %d: station %d coordinate %d is not finite", t, i, c);
   }
   h->nu_t0.clear();
   h->nu_plans.clear();

@@ -713,8 +713,12 @@ NuPlan nu_plan(const NuPixBox& px, int w, float beta, const int P[3], const doub
     p.delta[d] = (hi - lo) / P[d];
     const double X = 0.5 * p.delta[d], S = px.S[d];  // half-widths of one input cell and of the targets
     p.D[d] = px.D[d];
-    const long long need = (long long)ceil(4.0 * kSigma * X * S * (1.0 + 1e-12)) + w + 2;
-    p.M[d] = (int)next_smooth(std::max<long long>(2 * w, need));
+    // grids beyond 2^28 points per dimension are reported as such (the caller
+    // rejects them) rather than searched for and cast to int
+    const double need = ceil(4.0 * kSigma * X * S * (1.0 + 1e-12)) + w + 2;
+    constexpr long long kMaxM = 1LL << 28;
+    p.M[d] = !(need <= (double)kMaxM) ? (int)(kMaxM + 2)
+                                      : (int)next_smooth(std::max<long long>(2 * w, (long long)need));
     if (S > 0.0)
       p.Hc[d] = 1.0 / (2.0 * kSigma * S);
     else if (X > 0.0)
