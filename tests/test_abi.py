@@ -183,3 +183,46 @@ def test_device_collect_checks_tensor_types_before_the_library():
 def test_fault_injection_switch_rejects_null_handle(lib):
     assert lib.bipp_ss_debug_fail_wait(None, 1) == bipp_ss.BIPP_ERR_INVALID_ARG
     assert b"NULL" in lib.bipp_ss_last_error(None)
+
+
+C_PROGRAM = r"""
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+#include "bipp_ss.h"
+
+int main(void) {
+  bipp_ss_options o;
+  double mu[5] = {9.0, 4.0, 1.0, 0.5, -2.0}, v[6] = {1.0, 1.1, 5.0, 5.2, 9.0, 9.3}, b[6];
+  int32_t k = 0;
+  bipp_ss_default_options(&o);
+  if (sizeof(bipp_ss_options) != 96 || o.precision != BIPP_PREC_FP32 || o.max_jacobi_sweeps != 40) return 1;
+  /* 90% of the positive energy 14.5 needs the three leading eigenvalues (13.0 < 13.05 <= 14.0) */
+  if (bipp_ss_energy_neig(5, mu, 0.9, &k) != BIPP_OK || k != 3) return 2;
+  if (bipp_ss_kmeans_bounds(6, v, 3, b) != BIPP_OK) return 3;
+  /* n_level x 2 column-major, level 0 = highest cluster {9, 9.3}: lo = b[0..2] = (7.1, 3.05, -inf),
+     hi = b[3..5] = (inf, 7.1, 3.05) */
+  if (fabs(b[0] - 7.1) > 1e-12 || fabs(b[1] - 3.05) > 1e-12 || !(isinf(b[2]) && b[2] < 0)) return 4;
+  if (!(isinf(b[3]) && b[3] > 0) || fabs(b[4] - 7.1) > 1e-12 || fabs(b[5] - 3.05) > 1e-12) return 8;
+  if (bipp_ss_energy_neig(0, mu, 0.9, &k) != BIPP_ERR_INVALID_ARG) return 5;
+  if (strlen(bipp_ss_last_error(NULL)) == 0) return 6;
+  if (bipp_ss_collect(NULL, 1, mu, mu) != BIPP_ERR_INVALID_ARG) return 7;
+  puts("ok");
+  return 0;
+}
+"""
+
+
+def test_header_compiles_and_links_as_c(lib, tmp_path):
+    """The ABI is usable from plain C99 (warnings as errors): defaults, the
+    host-only estimation calls and the NULL-handle error path."""
+    src = tmp_path / "abi.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "abi"
+    libdir = os.path.dirname(bipp_ss.LIB_PATH)
+    cc = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I",
+                         os.path.join(ROOT, "include"), str(src), "-o", str(exe), "-L", libdir, "-lbipp_ss",
+                         f"-Wl,-rpath,{libdir}", "-lm"], capture_output=True, text=True)
+    assert cc.returncode == 0, cc.stderr
+    run = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert run.returncode == 0 and run.stdout.strip() == "ok", (run.returncode, run.stdout, run.stderr)
