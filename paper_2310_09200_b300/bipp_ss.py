@@ -146,11 +146,19 @@ def bipp_ss_default_options(**kw) -> bipp_ss_options:
     o = bipp_ss_options()
     load().bipp_ss_default_options(C.byref(o))
     names = {"precision": PRECISIONS, "filter": FILTERS, "eig_mode": EIG_MODES, "synthesis": SYNTHESES}
+    fields = {f[0] for f in bipp_ss_options._fields_}
     for k, v in kw.items():
+        if k not in fields:  # a ctypes Structure would silently take an unknown attribute
+            raise TypeError(f"unknown option {k!r}; options are {sorted(fields)}")
         if k in names and isinstance(v, str):
+            if v not in names[k]:
+                raise ValueError(f"{k}={v!r}; choose from {sorted(names[k])}")
             v = names[k][v]
         if k == "nufft_partition":  # (uvw cells, image cells), each a triple
-            v = (C.c_int32 * 6)(*[int(x) for x in np.ravel(v)])
+            flat = [int(x) for x in np.ravel(v)]
+            if len(flat) != 6:
+                raise ValueError("nufft_partition needs 6 values: 3 input cells, then 3 image cells")
+            v = (C.c_int32 * 6)(*flat)
         setattr(o, k, int(v) if isinstance(v, bool) else v)
     return o
 

@@ -226,3 +226,14 @@ def test_header_compiles_and_links_as_c(lib, tmp_path):
     assert cc.returncode == 0, cc.stderr
     run = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert run.returncode == 0 and run.stdout.strip() == "ok", (run.returncode, run.stdout, run.stderr)
+
+
+def test_binding_rejects_unknown_options(lib):
+    with pytest.raises(TypeError):
+        bipp_ss.bipp_ss_default_options(autotun=0)
+    with pytest.raises(ValueError):
+        bipp_ss.bipp_ss_default_options(precision="bf16")
+    with pytest.raises(ValueError):
+        bipp_ss.bipp_ss_default_options(nufft_partition=(2, 2, 1))
+    o = bipp_ss.bipp_ss_default_options(precision="split_fp16", nufft_partition=((2, 2, 1), (1, 1, 1)), autotune=False)
+    assert o.precision == 3 and list(o.nufft_partition) == [2, 2, 1, 1, 1, 1] and o.autotune == 0
