@@ -53,6 +53,11 @@ FP32_PEAK_FLOPS = SMS * 128 * 2 * SM_MAX_GHZ * 1e9
 # __sincosf pairs per second measured on a B300 of this machine (148 SMs at 2032 MHz:
 # 4.45e12 MUFU results/s, i.e. 14.8 per SM per clock).
 MUFU_SINCOS_PER_S = 2.23e12
+# Issue slots: 4 warp instructions per SM per clock. k_synth_tc issues 41 thread
+# instructions per pixel-station pair (ncu, profiles/k_synth_tc_ska_low_512st_1024px_10steps.md:
+# phase, sincos, hi/lo split and stores of A in the producers, plus the epilogue).
+ISSUE_THREAD_INSTR_PER_S = SMS * 4 * 32 * SM_MAX_GHZ * 1e9
+SYNTH_TC_INSTR_PER_PAIR = 41
 
 
 DTYPES = {"fp64": "f64", "fp32": "f64 eig + f32 synth",
@@ -86,6 +91,30 @@ def synth_tc_traffic(workload: dict):
         except OSError:
             return None
     return SYNTH_TC_TRAFFIC["bytes"] if workload == SYNTH_TC_TRAFFIC["workload"] else None
+
+
+def tc_roofline(syn_flops: float, syn_ms: float, pairs: float, peaks: dict, traffic) -> dict:
+    """Roofline of the split tensor-core synthesis: 3 tensor products per real
+    multiply-add, T_roof = max(T_tensor, T_sfu) for `frac`; beside it the
+    issue-slot time of the kernel's measured instruction count per pair and
+    the name of the largest of the three."""
+    r_tc = peaks.get("bf16_tflops_sustained", 1411.3) * 1e12
+    t_tc = 3 * syn_flops / r_tc
+    t_sfu = pairs / MUFU_SINCOS_PER_S
+    t_issue = SYNTH_TC_INSTR_PER_PAIR * pairs / ISSUE_THREAD_INSTR_PER_S
+    t = {"tensor_split": t_tc * 1e3, "sfu_sincos": t_sfu * 1e3, "issue_slots": t_issue * 1e3}
+    return {"kernel": "k_synth_tc", "bound": "tensor", "achieved": 3 * syn_flops / (syn_ms / 1e3) / 1e12,
+            "peak": r_tc / 1e12, "unit": "TFLOP/s", "traffic": traffic,
+            "frac": max(t_tc, t_sfu) / (syn_ms / 1e3),
+            "frac_algorithmic_s1": (syn_flops / r_tc) / (syn_ms / 1e3),
+            "frac_issue": t_issue / (syn_ms / 1e3),
+            "t_roof_ms": t, "largest_bound": max(t, key=t.get),
+            "peak_note": ("of measured: cuBLAS bf16 sustained (FP16 dense rate is the same nominal); "
+                          "frac = max(T_tensor(s=3), T_sfu) / measured time; "
+                          f"SFU rate {MUFU_SINCOS_PER_S:.3g} sincos/s measured by a sin/cos "
+                          "microbenchmark on this B300 pool; issue_slots = "
+                          f"{SYNTH_TC_INSTR_PER_PAIR} thread instructions per pair (ncu) at 4 warp "
+                          "instructions per SM per clock, 148 SMs, 2.032 GHz")}
 
 
 def measured_peaks() -> dict:
@@ -706,23 +735,9 @@ def ours_main(args, ws, rank, local):
                       "traffic": None, "peak_note": "CUDA-core FMA pipe, unit count x 2 flop x 2.032 GHz"}
         roof_synth["frac"] = roof_synth["achieved"] / roof_synth["peak"]
     else:
-        # split GEMM: 3 tensor products per real multiply-add; T_roof = max(T_tensor, T_sfu)
-        peaks = measured_peaks()
-        r_tc = peaks.get("bf16_tflops_sustained", 1411.3) * 1e12
-        pairs = inp.n_pix * n_st * inp.n_t
-        t_tc = 3 * syn_flops / r_tc
-        t_sfu = pairs / MUFU_SINCOS_PER_S
         traffic = synth_tc_traffic({"n_st": int(n_st), "n_pix": int(inp.n_pix), "n_eig": int(inp.n_eig),
                                     "n_level": int(inp.n_level), "n_t": int(inp.n_t), "precision": args.precision})
-        roof_synth = {"kernel": "k_synth_tc", "bound": "tensor", "achieved": 3 * syn_flops / (syn_ms / 1e3) / 1e12,
-                      "peak": r_tc / 1e12, "unit": "TFLOP/s", "traffic": traffic,
-                      "frac": max(t_tc, t_sfu) / (syn_ms / 1e3),
-                      "frac_algorithmic_s1": (syn_flops / r_tc) / (syn_ms / 1e3),
-                      "t_roof_ms": {"tensor_split": t_tc * 1e3, "sfu_sincos": t_sfu * 1e3},
-                      "peak_note": ("of measured: cuBLAS bf16 sustained (FP16 dense rate is the same nominal); "
-                                    "frac = max(T_tensor(s=3), T_sfu) / measured time; "
-                                    f"SFU rate {MUFU_SINCOS_PER_S:.3g} sincos/s measured by a sin/cos "
-                                    "microbenchmark on this B300 pool")}
+        roof_synth = tc_roofline(syn_flops, syn_ms, inp.n_pix * n_st * inp.n_t, measured_peaks(), traffic)
     # the dominant single kernel: the FP64 Jacobi when it runs, else the synthesis (the mixed
     # eigensolve is a stage of ~60 launches, the largest of which is well below the synthesis)
     dominant = roof_jacobi if (args.eig == "jacobi64" and eig_ms >= syn_ms) else roof_synth

@@ -1,0 +1,32 @@
+"""Host-side arithmetic of bench.py (no GPU): the tensor-core synthesis
+roofline and the guard on the recorded DRAM traffic."""
+from __future__ import annotations
+
+import pytest
+
+import bench
+
+
+def test_tc_roofline_of_the_default_job():
+    """1024^2 pixels x 512 stations x 64 eigenvectors x 100 steps in 96.8 ms against
+    a 1385.2 TFLOP/s tensor peak: the split GEMM's 3 x 8 P flops take 59.5 ms at
+    peak, the 5.4e10 sincos pairs 24.1 ms at the SFU rate, and 41 instructions per
+    pair 57.2 ms of issue slots; frac is the larger of the first two over 96.8 ms."""
+    P = 1048576 * 512 * 64 * 100
+    pairs = 1048576 * 512 * 100
+    r = bench.tc_roofline(8.0 * P, 96.8, pairs, {"bf16_tflops_sustained": 1385.2}, None)
+    t = r["t_roof_ms"]
+    assert t["tensor_split"] == pytest.approx(3 * 8.0 * P / 1385.2e12 * 1e3)
+    assert t["sfu_sincos"] == pytest.approx(pairs / 2.23e12 * 1e3)
+    assert t["issue_slots"] == pytest.approx(41 * pairs / (148 * 4 * 32 * 2.032e9) * 1e3)
+    assert r["frac"] == pytest.approx(t["tensor_split"] / 96.8)
+    assert r["achieved"] == pytest.approx(3 * 8.0 * P / 96.8e-3 / 1e12)
+    assert r["largest_bound"] == "tensor_split" and r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
+    assert 0.6 < r["frac"] < 0.63 and 0.58 < r["frac_issue"] < 0.6
+
+
+def test_traffic_only_for_the_captured_workload():
+    w = dict(bench.SYNTH_TC_TRAFFIC["workload"])
+    assert bench.synth_tc_traffic(w) == bench.SYNTH_TC_TRAFFIC["bytes"]
+    w["n_t"] = 10
+    assert bench.synth_tc_traffic(w) is None
