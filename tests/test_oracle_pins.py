@@ -341,3 +341,34 @@ def test_single_station_degenerate_case():
         assert abs(abs(W[0, 0]) - 1.0) < 1e-15
         np.testing.assert_allclose(img[:, 1], want_val, rtol=1e-13)
         assert np.all(img[:, [0, 2]] == 0.0)
+
+
+def test_station_permutation_invariance():
+    """Relabelling the stations (rows of the positions, rows and columns of V
+    together) changes neither the eigenvalues nor the images: a position and
+    its visibilities must travel together through every index of the path."""
+    inp = inputs.make_config(0, n_t=1, n_side=10)
+    p, V = inp.st_xyz[0], inp.vis[0]
+    perm = np.random.default_rng(9).permutation(p.shape[0])
+    bounds = np.array([[200.0, np.inf], [50.0, 200.0], [-np.inf, 50.0]])
+    a, mu_a, lev_a, _ = oracle.ss_step(inp.pix, inp.wl, bounds, inp.n_eig, p, V)
+    b, mu_b, lev_b, _ = oracle.ss_step(inp.pix, inp.wl, bounds, inp.n_eig, p[perm], V[np.ix_(perm, perm)])
+    np.testing.assert_allclose(mu_b, mu_a, rtol=1e-11)
+    assert list(lev_a) == list(lev_b)
+    np.testing.assert_allclose(b, a, rtol=1e-10, atol=1e-12 * np.abs(a).max())
+
+
+def test_visibility_scaling():
+    """V -> c V (c > 0) with the level edges scaled by c: the eigenvalues scale
+    by c and the G-orthonormal eigenvectors do not change, so the LSQ images
+    (weights mu) scale by c and the STD images (weights 1) stay the same."""
+    inp = inputs.make_config(0, n_t=1, n_side=10)
+    p, V = inp.st_xyz[0], inp.vis[0]
+    c = 7.5
+    bounds = np.array([[200.0, np.inf], [50.0, 200.0], [-np.inf, 50.0]])
+    for filt, factor in (("lsq", c), ("std", 1.0)):
+        a, mu_a, lev_a, _ = oracle.ss_step(inp.pix, inp.wl, bounds, inp.n_eig, p, V, filter=filt)
+        b, mu_b, lev_b, _ = oracle.ss_step(inp.pix, inp.wl, c * bounds, inp.n_eig, p, c * V, filter=filt)
+        np.testing.assert_allclose(mu_b, c * mu_a, rtol=1e-11)
+        assert list(lev_a) == list(lev_b)
+        np.testing.assert_allclose(b, factor * a, rtol=1e-10, atol=1e-12 * factor * np.abs(a).max())
