@@ -60,7 +60,11 @@ extern "C" {
 #define BIPP_PREC_FP64 0       /* FP64 phases, sincos and sums (CUDA cores) */
 #define BIPP_PREC_FP32 1       /* exact phase reduction, SFU sincos, FP32 CUDA-core sums */
 #define BIPP_PREC_SPLIT_BF16 2 /* exact phase reduction, SFU sincos, tcgen05 hi/lo BF16 x3, FP32 accumulate */
-#define BIPP_PREC_SPLIT_FP16 3 /* as SPLIT_BF16 with FP16 hi/lo operands (scaled W) */
+#define BIPP_PREC_SPLIT_FP16 3 /* as SPLIT_BF16 with FP16 hi/lo operands (scaled W): finer
+                                  operands, so it meets the FP32 path's 1e-5 relative L2 per level
+                                  up to ~512 stations (6.5e-6 measured at 512); the error grows with
+                                  K = 2 n_st (1.27e-5 measured at 1024), bounded by FP32 summation
+                                  over K terms, 2 n_st 2^-24 */
 
 #define BIPP_FILTER_LSQ 0 /* d_e = mu_e (Sec. 2.6, least-squares image) */
 #define BIPP_FILTER_STD 1 /* d_e = 1    (Sec. 2.6, standardised image) */
@@ -291,6 +295,11 @@ int bipp_ss_synth_adjoint_device(int64_t n_pix, const double* d_pix, double wl, 
  *                ADDED to it (the caller zeroes it before the first step).
  *   stream       cudaStream_t or NULL; work runs on the current device.
  *   err_msg      optional buffer of err_len bytes for a message (may be NULL).
+ * The eigensolve is the FP64 Jacobi with the handle defaults (stop at
+ * off(C) <= 1e-13 ||C||_F, at most 40 sweeps). Every device buffer must be
+ * device memory on the current device (d_vis 16-byte, the others 8-byte
+ * aligned) and level bounds must not be NaN (BIPP_ERR_INVALID_ARG otherwise).
+ * A step that fails (e.g. BIPP_ERR_GRAM_NOT_PD) adds nothing to d_img.
  * Limits: 1 <= n_eig <= n_st <= BIPP_NOALLOC_MAX_STATIONS,
  * n_eig <= BIPP_NOALLOC_MAX_EIG, 1 <= n_level <= 16; larger sizes return
  * BIPP_ERR_UNSUPPORTED with a message naming the limit. The first call on a
@@ -334,6 +343,18 @@ int bipp_ss_energy_neig(int32_t n, const double* mu_desc, double fraction, int32
  * are -inf and +inf. 1 <= n_level <= n; BIPP_ERR_INVALID_ARG otherwise or on
  * non-finite values. Error text via bipp_ss_last_error(NULL). */
 int bipp_ss_kmeans_bounds(int32_t n, const double* values, int32_t n_level, double* level_bounds);
+
+/* bipp_ss_quantile_bounds: level intervals at the quantiles of n values
+ * (eigenvalues pooled over an observation's steps; Sec. 2.6 "Partitioning"
+ * leaves the partition rule to the user, this is the equal-count one). The
+ * values are sorted; inner edge q (1 <= q < n_level) lies halfway between the
+ * sorted values k-1 and k, k = q n / n_level rounded half to even and clamped
+ * to [1, n-1], so no value sits on an edge unless two values are equal.
+ * Writes level_bounds (host, n_level x 2 column-major, the layout of
+ * bipp_ss_create): level 0 holds the largest values, outer edges are -inf and
+ * +inf. 1 <= n_level <= n; BIPP_ERR_INVALID_ARG otherwise or on non-finite
+ * values. Error text via bipp_ss_last_error(NULL). */
+int bipp_ss_quantile_bounds(int32_t n, const double* values, int32_t n_level, double* level_bounds);
 
 #ifdef __cplusplus
 }

@@ -5,6 +5,9 @@ may use it; the library never does).
 - energy_n_eig: truncation to the least number of leading eigenvectors whose
   eigenvalues hold a given share of the energy (energy = sum of the positive
   eigenvalues).
+- quantile_bounds: the equal-count partition used by the benchmark's
+  pre-pass (levels split at the eigenvalue quantiles, each inner edge halfway
+  between the two pooled values it separates).
 - kmeans_1d / kmeans_bounds: k-means clustering of eigenvalues into level
   partitions. In one dimension the optimal clusters of sorted values are
   contiguous runs; the least within-cluster sum of squares is found by the
@@ -68,3 +71,19 @@ def kmeans_bounds(values, k):
         hi = math.inf if c == k - 1 else 0.5 * (x[starts[c + 1] - 1] + x[starts[c + 1]])
         out.append((lo, hi))
     return out
+
+
+def quantile_bounds(values, k):
+    """Inner edge q (1 <= q < k) halfway between sorted values m-1 and m,
+    m = round(q n / k) (half to even) clamped to [1, n-1]; outer edges -inf and
+    +inf; returns k (lo, hi) pairs, level 0 holding the largest values."""
+    x = sorted(float(v) for v in values)
+    n = len(x)
+    edges = []
+    for q in range(1, k):
+        m = min(max(int(round(q * n / k)), 1), n - 1)
+        edges.append(0.5 * (x[m - 1] + x[m]))
+    edges.sort()
+    lows = [-math.inf] + edges
+    highs = edges + [math.inf]
+    return [(lows[c], highs[c]) for c in range(k - 1, -1, -1)]

@@ -52,7 +52,7 @@ EXPORTED = [
     "bipp_ss_last_error", "bipp_ss_collect_noalloc", "bipp_ss_synth_levels_device",
     "bipp_ss_synth_adjoint_device", "bipp_ss_create_channels", "bipp_ss_collect_channels",
     "bipp_ss_energy_neig", "bipp_ss_kmeans_bounds", "bipp_ss_get_nufft_timings", "bipp_ss_collect_device_c64",
-    "bipp_ss_debug_fail_wait",
+    "bipp_ss_debug_fail_wait", "bipp_ss_quantile_bounds",
 ]
 
 BIPP_NOALLOC_MAX_STATIONS = 128
@@ -109,6 +109,7 @@ def load(path: str | None = None):
     L.bipp_ss_destroy.argtypes = [H]
     L.bipp_ss_energy_neig.argtypes = [i32, dp, C.c_double, ip]
     L.bipp_ss_kmeans_bounds.argtypes = [i32, dp, i32, dp]
+    L.bipp_ss_quantile_bounds.argtypes = [i32, dp, i32, dp]
     L.bipp_ss_last_error.argtypes = [H]
     L.bipp_ss_last_error.restype = C.c_char_p
     L.bipp_ss_collect_noalloc.argtypes = [i64, vp, C.c_double, i32, dp, i32, i32, i32, i32, vp, vp, vp, vp,
@@ -365,6 +366,18 @@ def bipp_ss_destroy(h) -> None:
         load().bipp_ss_destroy(h)
 
 
+def _noalloc_tensor(name, t, dtype, shape):
+    """Host-side check of one tensor handed to bipp_ss_collect_noalloc: the
+    kernels read or write exactly `shape` elements of `dtype` at its address,
+    on the device."""
+    if not hasattr(t, "data_ptr") or str(t.dtype) != f"torch.{dtype}":
+        raise ValueError(f"{name} must be a torch {dtype} tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
 def bipp_ss_collect_noalloc(d_pix, wl, level_bounds, n_eig, d_st, d_vis, d_img, filter="lsq",
                             gram_identity=False, stream=None) -> None:
     """One collect() step that allocates no device memory, for callers that
@@ -376,14 +389,34 @@ def bipp_ss_collect_noalloc(d_pix, wl, level_bounds, n_eig, d_st, d_vis, d_img, 
     d_pix: torch float64 (3, n_pix) contiguous (column-major n_pix x 3);
     d_st: torch float64 (3, n_st); d_vis: torch complex128 (n_st, n_st)
     holding vis.T (column-major); d_img: torch float64 (n_level, n_pix),
-    to which the step's level images are added."""
+    to which the step's level images are added; level_bounds (n_level, 2).
+    Every tensor must be contiguous on the current CUDA device; anything else
+    raises ValueError before the library is called."""
     b = np.asarray(level_bounds, dtype=np.float64)
+    if b.ndim != 2 or b.shape[1] != 2 or b.shape[0] < 1:
+        raise ValueError("level_bounds must be (n_level, 2)")
+    if getattr(d_pix, "ndim", 0) != 2 or getattr(d_st, "ndim", 0) != 2:
+        raise ValueError("d_pix must be (3, n_pix) and d_st (3, n_st)")
+    n_pix, n_st, n_level = int(d_pix.shape[1]), int(d_st.shape[1]), int(b.shape[0])
+    _noalloc_tensor("d_pix", d_pix, "float64", (3, n_pix))
+    _noalloc_tensor("d_st", d_st, "float64", (3, n_st))
+    _noalloc_tensor("d_vis", d_vis, "complex128", (n_st, n_st))
+    _noalloc_tensor("d_img", d_img, "float64", (n_level, n_pix))
+    named = (("d_pix", d_pix), ("d_st", d_st), ("d_vis", d_vis), ("d_img", d_img))
+    for name, t in named:
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be on a CUDA device, got {t.device}")
+    import torch
+    cur = torch.cuda.current_device()
+    for name, t in named:
+        if t.device.index != cur:
+            raise ValueError(f"{name} is on {t.device}; the step runs on the current device cuda:{cur}")
     bc = np.ascontiguousarray(b.T)
     msg = C.create_string_buffer(512)
     sp = None if stream is None else C.c_void_p(stream.cuda_stream)
-    rc = load().bipp_ss_collect_noalloc(int(d_pix.shape[1]), C.c_void_p(d_pix.data_ptr()), float(wl), b.shape[0],
+    rc = load().bipp_ss_collect_noalloc(n_pix, C.c_void_p(d_pix.data_ptr()), float(wl), n_level,
                                         _dp(bc), int(n_eig), FILTERS[filter] if isinstance(filter, str) else int(filter),
-                                        int(bool(gram_identity)), int(d_st.shape[1]), C.c_void_p(d_st.data_ptr()),
+                                        int(bool(gram_identity)), n_st, C.c_void_p(d_st.data_ptr()),
                                         C.c_void_p(d_vis.data_ptr()), C.c_void_p(d_img.data_ptr()), sp, msg, 512)
     if rc != BIPP_OK:
         raise BippError(rc, msg.value.decode())
@@ -470,19 +503,20 @@ class StandardSynthesis:
             pass
 
 
-def quantile_level_bounds(pooled_mu, n_level: int) -> np.ndarray:
-    """Level intervals from pooled eigenvalues: inner edges at the 1/n_level
-    quantiles, each moved to the midpoint between the two nearest pooled
-    values; outer edges +-inf; level 0 holds the largest eigenvalues."""
-    v = np.sort(np.asarray(pooled_mu, dtype=np.float64))
-    edges = []
-    for q in range(1, n_level):
-        k = min(max(int(round(q * len(v) / n_level)), 1), len(v) - 1)
-        edges.append(0.5 * (v[k - 1] + v[k]))
-    edges = sorted(edges)
-    lo = [-math.inf] + edges
-    hi = edges + [math.inf]
-    return np.array(list(zip(lo, hi)))[::-1].copy()
+def bipp_ss_quantile_bounds(pooled_mu, n_level: int) -> np.ndarray:
+    """Level intervals (n_level, 2) rows [lo, hi) at the quantiles of the
+    pooled eigenvalues (bipp_ss_quantile_bounds): inner edges halfway between
+    neighbouring values at the 1/n_level quantiles, outer edges +-inf, level 0
+    holding the largest eigenvalues."""
+    v = np.ascontiguousarray(pooled_mu, dtype=np.float64).ravel()
+    out = np.zeros(2 * n_level, dtype=np.float64)
+    rc = load().bipp_ss_quantile_bounds(v.shape[0], _dp(v), int(n_level), _dp(out))
+    if rc != BIPP_OK:
+        raise BippError(rc, bipp_ss_last_error(None))
+    return np.ascontiguousarray(out.reshape(2, n_level).T)
+
+
+quantile_level_bounds = bipp_ss_quantile_bounds
 
 
 def bipp_ss_energy_neig(mu_desc, fraction: float) -> int:

@@ -1,7 +1,8 @@
 // estimate.cu — the parameter estimation of Sec. 2.6 ("Energy Levels &
 // Partitioning") on eigenvalues pooled from an observation: truncation to the
 // leading eigenvectors that hold a given share of the energy, and level
-// partitions by k-means clustering of the eigenvalues. Host code.
+// partitions by quantiles or by k-means clustering of the eigenvalues. Host
+// code.
 //
 // k-means in one dimension has an exact optimum: the clusters of sorted values
 // are contiguous runs, so dynamic programming over (cluster count, last index)
@@ -98,6 +99,32 @@ extern "C" int bipp_ss_kmeans_bounds(int32_t n, const double* values, int32_t n_
     const double hi = (c == K - 1) ? INFINITY : 0.5 * (x[start[c + 1] - 1] + x[start[c + 1]]);
     level_bounds[l] = lo;
     level_bounds[K + l] = hi;
+  }
+  return BIPP_OK;
+}
+
+extern "C" int bipp_ss_quantile_bounds(int32_t n, const double* values, int32_t n_level, double* level_bounds) {
+  if (n < 1 || !values || !level_bounds || n_level < 1 || n_level > n)
+    return set_global_error(BIPP_ERR_INVALID_ARG, "need 1 <= n_level <= n, values and level_bounds");
+  std::vector<double> x(values, values + n);
+  for (double v : x)
+    if (!isfinite(v)) return set_global_error(BIPP_ERR_INVALID_ARG, "values must be finite");
+  std::sort(x.begin(), x.end());
+  // inner edge q (1 <= q < n_level) sits between the sorted values k-1 and k,
+  // k = q n / n_level rounded half to even and clamped to [1, n-1]
+  std::vector<double> edge;
+  for (int q = 1; q < n_level; ++q) {
+    int k = (int)nearbyint((double)q * (double)n / (double)n_level);
+    k = std::min(std::max(k, 1), n - 1);
+    edge.push_back(0.5 * (x[k - 1] + x[k]));
+  }
+  std::sort(edge.begin(), edge.end());
+  // level 0 holds the largest values: its interval is [edge_last, +inf)
+  const int K = n_level;
+  for (int l = 0; l < K; ++l) {
+    const int c = K - 1 - l;  // interval index in ascending order
+    level_bounds[l] = (c == 0) ? -INFINITY : edge[c - 1];
+    level_bounds[K + l] = (c == K - 1) ? INFINITY : edge[c];
   }
   return BIPP_OK;
 }

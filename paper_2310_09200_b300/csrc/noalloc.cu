@@ -12,6 +12,7 @@
 // The array is a module global: every GPU that loads the library holds it
 // until the process exits, every call shares it and it keeps the contents
 // of the last call, so calls that overlap on a GPU race with each other.
+#include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -28,6 +29,10 @@ using namespace bipp;
 constexpr int kN = BIPP_NOALLOC_MAX_STATIONS;
 constexpr int kK = BIPP_NOALLOC_MAX_EIG;
 constexpr size_t kAlign = 256;
+// The eigensolve of the step: FP64 Jacobi with the handle's default stopping
+// rule (off(C) <= 1e-13 ||C||_F) and sweep cap.
+constexpr double kJacobiTol = 1e-13;
+constexpr int kJacobiSweeps = 40;
 
 constexpr size_t up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -86,13 +91,36 @@ extern "C" int bipp_ss_collect_noalloc(int64_t n_pix, const double* d_pix_xyz, d
     return report(err_msg, err_len, BIPP_ERR_UNSUPPORTED, "n_level=%d outside [1, %d]", n_level, kMaxLevels);
   if (n_pix < 1 || !d_pix_xyz || !level_bounds || !d_st_xyz || !d_vis || !d_img)
     return report(err_msg, err_len, BIPP_ERR_INVALID_ARG, "need n_pix >= 1 and non-NULL buffers");
-  if (!(wl > 0.0) || filter < 0 || filter > 1)
-    return report(err_msg, err_len, BIPP_ERR_INVALID_ARG, "need wl > 0 and filter LSQ (0) or STD (1)");
+  if (!(wl > 0.0) || !isfinite(wl) || filter < 0 || filter > 1)
+    return report(err_msg, err_len, BIPP_ERR_INVALID_ARG, "need a finite wl > 0 and filter LSQ (0) or STD (1)");
+  for (int l = 0; l < 2 * n_level; ++l)
+    if (isnan(level_bounds[l]))
+      return report(err_msg, err_len, BIPP_ERR_INVALID_ARG, "level bound %d of %d is NaN", l, 2 * n_level);
 
+  (void)cudaGetLastError();  // an error left by an earlier, unrelated call is not this call's
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return report(err_msg, err_len, BIPP_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return report(err_msg, err_len, BIPP_ERR_UNSUPPORTED, "device %d", dev);
+  // Every buffer is read or written by kernels on the current device: it must
+  // be device memory there, and aligned for the kernels' double and complex
+  // loads (a host pointer or a misaligned view would fault on the device).
+  {
+    const void* ptrs[4] = {d_pix_xyz, d_st_xyz, d_vis, d_img};
+    const char* names[4] = {"d_pix_xyz", "d_st_xyz", "d_vis", "d_img"};
+    const uintptr_t align[4] = {8, 8, 16, 8};
+    for (int i = 0; i < 4; ++i) {
+      cudaPointerAttributes a{};
+      if (cudaPointerGetAttributes(&a, ptrs[i]) != cudaSuccess || a.type != cudaMemoryTypeDevice || a.device != dev) {
+        (void)cudaGetLastError();
+        return report(err_msg, err_len, BIPP_ERR_INVALID_ARG, "%s must be device memory on the current device %d",
+                      names[i], dev);
+      }
+      if (reinterpret_cast<uintptr_t>(ptrs[i]) % align[i])
+        return report(err_msg, err_len, BIPP_ERR_INVALID_ARG, "%s must be %d-byte aligned", names[i],
+                      (int)align[i]);
+    }
+  }
   unsigned char* base;
   {
     std::lock_guard<std::mutex> lock(g_mu);
@@ -151,7 +179,7 @@ extern "C" int bipp_ss_collect_noalloc(int64_t n_pix, const double* d_pix_xyz, d
   launch_gram(b, gram_identity, s);
   launch_cholesky(b, gram_identity, s);
   launch_reduce(b, gram_identity, s);
-  launch_jacobi(b, 1e-13, 40, s);
+  launch_jacobi(b, kJacobiTol, kJacobiSweeps, s);
   launch_select(b, n_level, d_bounds, filter, s);
   Pixels px{n_pix, d_pix_xyz, nullptr};
   launch_synth_simt_f64(b, px, n_level, d_img, s);
@@ -164,6 +192,6 @@ extern "C" int bipp_ss_collect_noalloc(int64_t n_pix, const double* d_pix_xyz, d
   if (status & kStatusNotPD)
     return report(err_msg, err_len, BIPP_ERR_GRAM_NOT_PD, "Gram matrix is not positive definite");
   if (status & kStatusNotConverged)
-    return report(err_msg, err_len, BIPP_ERR_EIG_NOT_CONVERGED, "Jacobi did not converge in 40 sweeps");
+    return report(err_msg, err_len, BIPP_ERR_EIG_NOT_CONVERGED, "Jacobi did not converge in %d sweeps", kJacobiSweeps);
   return BIPP_OK;
 }

@@ -10,24 +10,16 @@ import math
 import numpy as np
 
 import oracle
+from oracle import estimate as oest
 
 
 def quantile_bounds(pooled_mu, n_level: int) -> np.ndarray:
     """Level intervals from pooled eigenvalues (the "parameter estimation"
-    pre-pass of Table tts): inner edges at the 1/n_level quantiles, each moved
-    to the midpoint between the two nearest pooled values; outer edges +-inf.
-    Level 0 holds the largest eigenvalues. Returns (n_level, 2) [lo, hi)."""
-    v = np.sort(np.asarray(pooled_mu, dtype=np.float64))
-    edges = []
-    for q in range(1, n_level):
-        k = int(round(q * len(v) / n_level))
-        k = min(max(k, 1), len(v) - 1)
-        edges.append(0.5 * (v[k - 1] + v[k]))
-    edges = sorted(edges)
-    lo = [-np.inf] + edges
-    hi = edges + [np.inf]
-    b = np.array(list(zip(lo, hi)))[::-1].copy()  # level 0 = highest energy
-    return b
+    pre-pass of Table tts), by the oracle's equal-count rule: inner edges at
+    the 1/n_level quantiles, each halfway between the two nearest pooled
+    values; outer edges +-inf; level 0 holds the largest eigenvalues.
+    Returns (n_level, 2) rows [lo, hi)."""
+    return np.array(oest.quantile_bounds(pooled_mu, n_level), dtype=np.float64)
 
 
 def min_edge_margin(pooled_mu, bounds) -> float:

@@ -237,3 +237,59 @@ def test_binding_rejects_unknown_options(lib):
         bipp_ss.bipp_ss_default_options(nufft_partition=(2, 2, 1))
     o = bipp_ss.bipp_ss_default_options(precision="split_fp16", nufft_partition=((2, 2, 1), (1, 1, 1)), autotune=False)
     assert o.precision == 3 and list(o.nufft_partition) == [2, 2, 1, 1, 1, 1] and o.autotune == 0
+
+
+def test_noalloc_binding_checks_tensors_before_the_library():
+    """bipp_ss_collect_noalloc's binding refuses, on the host and before the
+    library is called, every tensor whose type, shape, layout or device would
+    make the kernels read or write outside it."""
+    import torch
+    n_pix, n_st = 6, 5
+    good = dict(d_pix=torch.zeros((3, n_pix), dtype=torch.float64), d_st=torch.zeros((3, n_st), dtype=torch.float64),
+                d_vis=torch.zeros((n_st, n_st), dtype=torch.complex128),
+                d_img=torch.zeros((2, n_pix), dtype=torch.float64))
+    bounds = np.array([[1.0, np.inf], [-np.inf, 1.0]])
+    bad = [
+        ("d_pix", torch.zeros((3, n_pix), dtype=torch.float32)),
+        ("d_pix", torch.zeros((n_pix, 3), dtype=torch.float64)[:, :3].T),          # a transposed view
+        ("d_st", torch.zeros((3, n_st), dtype=torch.float32)),
+        ("d_vis", torch.zeros((n_st, n_st), dtype=torch.complex64)),
+        ("d_vis", torch.zeros((n_st, n_st + 1), dtype=torch.complex128)),
+        ("d_vis", torch.zeros((n_st, 2 * n_st), dtype=torch.complex128)[:, ::2]),  # non-contiguous
+        ("d_img", torch.zeros((2, n_pix), dtype=torch.float32)),
+        ("d_img", torch.zeros((3, n_pix), dtype=torch.float64)),                    # level count != bounds
+        ("d_img", torch.zeros((2, n_pix + 1), dtype=torch.float64)),
+    ]
+    for name, t in bad:
+        kw = dict(good, **{name: t})
+        with pytest.raises(ValueError, match=name):
+            bipp_ss.bipp_ss_collect_noalloc(kw["d_pix"], 2.0, bounds, 2, kw["d_st"], kw["d_vis"], kw["d_img"])
+    with pytest.raises(ValueError, match="level_bounds"):
+        bipp_ss.bipp_ss_collect_noalloc(good["d_pix"], 2.0, np.zeros(4), 2, good["d_st"], good["d_vis"],
+                                        good["d_img"])
+    # well-formed tensors on the CPU are still refused: the kernels need device memory
+    with pytest.raises(ValueError, match="CUDA"):
+        bipp_ss.bipp_ss_collect_noalloc(good["d_pix"], 2.0, bounds, 2, good["d_st"], good["d_vis"], good["d_img"])
+
+
+def test_noalloc_c_entry_rejects_bad_scalars_before_any_cuda_call(lib):
+    """The C entry point checks sizes, the wavelength and the level bounds
+    before it touches CUDA (so these checks also hold without a GPU)."""
+    msg = C.create_string_buffer(256)
+    buf = (C.c_double * 64)()
+    p = C.cast(buf, C.c_void_p)
+
+    def call(n_st, n_eig, n_level, bounds, wl=2.0):
+        b = np.ascontiguousarray(bounds, dtype=np.float64)
+        return lib.bipp_ss_collect_noalloc(4, p, wl, n_level, b.ctypes.data_as(C.POINTER(C.c_double)),
+                                           n_eig, 0, 0, n_st, p, p, p, None, msg, 256)
+
+    inf = np.inf
+    assert call(bipp_ss.BIPP_NOALLOC_MAX_STATIONS + 1, 4, 1, [-inf, inf]) == bipp_ss.BIPP_ERR_UNSUPPORTED
+    assert b"stations" in msg.value
+    assert call(8, 9, 1, [-inf, inf]) == bipp_ss.BIPP_ERR_UNSUPPORTED
+    assert call(8, 4, 17, np.zeros(34)) == bipp_ss.BIPP_ERR_UNSUPPORTED
+    assert call(8, 4, 2, [np.nan, -inf, inf, 1.0]) == bipp_ss.BIPP_ERR_INVALID_ARG
+    assert b"NaN" in msg.value
+    assert call(8, 4, 1, [-inf, inf], wl=np.inf) == bipp_ss.BIPP_ERR_INVALID_ARG
+    assert call(8, 4, 1, [-inf, inf], wl=-1.0) == bipp_ss.BIPP_ERR_INVALID_ARG

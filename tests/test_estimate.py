@@ -48,7 +48,39 @@ def test_kmeans_separated_clusters():
     assert b[2] == (-math.inf, 3.05)
 
 
+def test_quantile_bounds_closed_forms():
+    # 12 values 1..12 in 4 levels: edges between the 3rd/4th, 6th/7th and 9th/10th values
+    b = oest.quantile_bounds(np.arange(1.0, 13.0), 4)
+    assert b == [(9.5, math.inf), (6.5, 9.5), (3.5, 6.5), (-math.inf, 3.5)]
+    # q n / k = 2.5 rounds half to even (to 2): the edge falls between the 2nd and 3rd values
+    assert oest.quantile_bounds([10.0, 0.0, 20.0, 30.0, 40.0], 2) == [(15.0, math.inf), (-math.inf, 15.0)]
+    # one level: the whole real line; a level count equal to n puts an edge between every pair
+    assert oest.quantile_bounds([3.0], 1) == [(-math.inf, math.inf)]
+    assert oest.quantile_bounds([1.0, 2.0, 4.0], 3) == [(3.0, math.inf), (1.5, 3.0), (-math.inf, 1.5)]
+
+
+def test_quantile_bounds_split_into_equal_counts():
+    rng = np.random.default_rng(8)
+    for _ in range(20):
+        n, k = int(rng.integers(8, 200)), int(rng.integers(1, 8))
+        vals = rng.normal(size=n) * 10 ** rng.uniform(-2, 2)
+        b = oest.quantile_bounds(vals, k)
+        counts = [int(np.sum((vals >= lo) & (vals < hi))) for lo, hi in b]
+        assert sum(counts) == n  # distinct values: every one in exactly one half-open level
+        assert max(counts) - min(counts) <= 2, counts
+
+
 # ---------------------------------------------------------------- library vs oracle
+
+@pytest.mark.parametrize("k", [1, 2, 4, 7])
+def test_library_quantile_bounds_match_oracle(k):
+    rng = np.random.default_rng(20 + k)
+    for n in (k, k + 1, 13, 257):
+        vals = rng.lognormal(size=n) * rng.choice([-1.0, 1.0], size=n)
+        got = bipp_ss.quantile_level_bounds(vals, k)
+        want = np.array(oest.quantile_bounds(vals, k))
+        np.testing.assert_array_equal(got, want)  # same sorted values, same halving: bit for bit
+
 
 def test_library_energy_matches_oracle():
     rng = np.random.default_rng(5)
@@ -78,7 +110,7 @@ def test_library_kmeans_on_pooled_oracle_eigenvalues():
                                rtol=1e-13)
 
 
-@pytest.mark.parametrize("case", ["n_level0", "too_many", "nan", "fraction", "unordered"])
+@pytest.mark.parametrize("case", ["n_level0", "too_many", "nan", "fraction", "unordered", "q_too_many", "q_nan"])
 def test_library_estimation_rejects_invalid_arguments(case):
     with pytest.raises(bipp_ss.BippError) as e:
         if case == "n_level0":
@@ -87,6 +119,10 @@ def test_library_estimation_rejects_invalid_arguments(case):
             bipp_ss.bipp_ss_kmeans_bounds([1.0, 2.0], 3)
         elif case == "nan":
             bipp_ss.bipp_ss_kmeans_bounds([1.0, np.nan], 1)
+        elif case == "q_too_many":
+            bipp_ss.quantile_level_bounds([1.0, 2.0], 3)
+        elif case == "q_nan":
+            bipp_ss.quantile_level_bounds([1.0, np.inf, 3.0], 2)
         elif case == "fraction":
             bipp_ss.bipp_ss_energy_neig([2.0, 1.0], 1.5)
         else:
