@@ -50,9 +50,6 @@ SMS = 148
 SM_MAX_GHZ = 2.032
 FP64_PEAK_FLOPS = SMS * 2 * 2 * SM_MAX_GHZ * 1e9
 FP32_PEAK_FLOPS = SMS * 128 * 2 * SM_MAX_GHZ * 1e9
-# __sincosf pairs per second measured on a B300 of this machine (148 SMs at 2032 MHz:
-# 4.45e12 MUFU results/s, i.e. 14.8 per SM per clock).
-MUFU_SINCOS_PER_S = 2.23e12
 # Issue slots: 4 warp instructions per SM per clock. k_synth_tc issues 41 thread
 # instructions per pixel-station pair (ncu, profiles/k_synth_tc_ska_low_512st_1024px_10steps.md:
 # phase, sincos, hi/lo split and stores of A in the producers, plus the epilogue).
@@ -93,14 +90,15 @@ def synth_tc_traffic(workload: dict):
     return SYNTH_TC_TRAFFIC["bytes"] if workload == SYNTH_TC_TRAFFIC["workload"] else None
 
 
-def tc_roofline(syn_flops: float, syn_ms: float, pairs: float, peaks: dict, traffic) -> dict:
+def tc_roofline(syn_flops: float, syn_ms: float, pairs: float, peaks: dict, traffic, sfu_rate: float) -> dict:
     """Roofline of the split tensor-core synthesis: 3 tensor products per real
-    multiply-add, T_roof = max(T_tensor, T_sfu) for `frac`; beside it the
-    issue-slot time of the kernel's measured instruction count per pair and
+    multiply-add, T_roof = max(T_tensor, T_sfu) for `frac` (sfu_rate: sincos
+    pairs/s measured by bipp_ss_measure_sincos_rate in the same run); beside it
+    the issue-slot time of the kernel's measured instruction count per pair and
     the name of the largest of the three."""
     r_tc = peaks.get("bf16_tflops_sustained", 1411.3) * 1e12
     t_tc = 3 * syn_flops / r_tc
-    t_sfu = pairs / MUFU_SINCOS_PER_S
+    t_sfu = pairs / sfu_rate
     t_issue = SYNTH_TC_INSTR_PER_PAIR * pairs / ISSUE_THREAD_INSTR_PER_S
     t = {"tensor_split": t_tc * 1e3, "sfu_sincos": t_sfu * 1e3, "issue_slots": t_issue * 1e3}
     return {"kernel": "k_synth_tc", "bound": "tensor", "achieved": 3 * syn_flops / (syn_ms / 1e3) / 1e12,
@@ -111,8 +109,8 @@ def tc_roofline(syn_flops: float, syn_ms: float, pairs: float, peaks: dict, traf
             "t_roof_ms": t, "largest_bound": max(t, key=t.get),
             "peak_note": ("of measured: cuBLAS bf16 sustained (FP16 dense rate is the same nominal); "
                           "frac = max(T_tensor(s=3), T_sfu) / measured time; "
-                          f"SFU rate {MUFU_SINCOS_PER_S:.3g} sincos/s measured by a sin/cos "
-                          "microbenchmark on this B300 pool; issue_slots = "
+                          f"SFU rate {sfu_rate:.3g} sincos pairs/s measured in this run by "
+                          "bipp_ss_measure_sincos_rate (__sincosf chains on every SM); issue_slots = "
                           f"{SYNTH_TC_INSTR_PER_PAIR} thread instructions per pair (ncu) at 4 warp "
                           "instructions per SM per clock, 148 SMs, 2.032 GHz")}
 
@@ -147,6 +145,8 @@ def parse():
     ap.add_argument("--n-st", type=int, default=0, help="keep only the first n stations (small profiling cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the side-by-side precision forms (FP32, split BF16, split FP16) after the timed region")
     ap.add_argument("--eig", default="mixed", choices=["jacobi64", "mixed"],
                     help="eigensolver: FP64 Jacobi, or FP32 Jacobi + FP64 refinement of the kept pairs")
     return ap.parse_args()
@@ -250,46 +250,61 @@ def dist_setup(args):
     return ws, rank, local
 
 
-def cpu_sample(inp, bounds, n_sub_side=64):
-    """Oracle on a bounded sample: Gram + eigensolve of one time step plus the
-    synthesis of a strided n_sub_side^2 pixel subset; returns timings and the
-    products/s of one full time step extrapolated linearly in pixels."""
-    import oracle
-    side = int(round(math.sqrt(inp.n_pix)))
+def strided_subset(n_pix: int, n_sub_side: int = 64) -> np.ndarray:
+    """Indices of a strided n_sub_side^2 subset of a square image (l fastest)."""
+    side = int(round(math.sqrt(n_pix)))
     stride = max(1, side // n_sub_side)
-    sel = (np.arange(0, side, stride)[:, None] * side + np.arange(0, side, stride)[None, :]).ravel()
+    return (np.arange(0, side, stride)[:, None] * side + np.arange(0, side, stride)[None, :]).ravel()
+
+
+def cpu_sample(inp, bounds, t: int = 0, n_sub_side: int = 64, eig: bool = True):
+    """The oracle on a bounded sample of the job: Gram + eigensolve of time
+    step t (single thread, as the oracle stands) and the synthesis of a
+    strided n_sub_side^2 pixel subset with that step's kept eigenpairs (OpenMP
+    over pixels). Returns the measured times, the products of exactly that
+    synthesis and their rate over the whole sample, the subset's image, and,
+    separately, the linear extrapolation of the step to all pixels and of the
+    job to all steps. eig=False skips the eigensolve (random G-free
+    eigenvectors of the same shape: a warm-up of the synthesis only)."""
+    import oracle
+    sel = strided_subset(inp.n_pix, n_sub_side)
     pix = inp.pix[sel]
-    p, V = inp.st_xyz[0], inp.vis[0]
+    p, V = inp.st_xyz[t], inp.vis[t]
     t0 = time.perf_counter()
-    G = oracle.gram(p, inp.wl)
-    mu, A, _ = oracle.geneig(V, G)
+    if eig:
+        G = oracle.gram(p, inp.wl)
+        mu, A, _ = oracle.geneig(V, G)
+    else:
+        rng = np.random.default_rng(t)
+        mu = np.sort(rng.normal(size=p.shape[0]))[::-1]
+        A = rng.normal(size=(p.shape[0], p.shape[0])) + 0j
     t1 = time.perf_counter()
     d = mu[: inp.n_eig]
     lev = oracle.select_levels(d, bounds)
-    oracle.synth_levels(pix, p, inp.wl, A[:, : inp.n_eig], d, lev, bounds.shape[0])
+    img = oracle.synth_levels(pix, p, inp.wl, A[:, : inp.n_eig], d, lev, bounds.shape[0])
     t2 = time.perf_counter()
     t_eig, t_syn = t1 - t0, t2 - t1
-    full_step = t_eig + t_syn * (inp.n_pix / len(sel))
-    prods = inp.n_pix * inp.n_eig * p.shape[0]
-    return {"t_eig_s": t_eig, "t_synth_sub_s": t_syn, "n_sub": int(len(sel)), "full_step_s": full_step,
-            "value": prods / full_step}
+    prods = float(len(sel)) * inp.n_eig * p.shape[0]
+    return {"t_eig_s": t_eig, "t_synth_sub_s": t_syn, "wall_s": t2 - t0, "n_sub": int(len(sel)), "sel": sel,
+            "img": img, "products": prods, "value": prods / (t2 - t0),
+            "extrapolated_job_ms": inp.n_t * (t_eig + t_syn * inp.n_pix / len(sel)) * 1e3}
 
 
-def cpu_sample_nufft(inp, bounds, eps, patch=128):
-    """Oracle NUFFT synthesis on a bounded sample: one time step (FP64 Gram +
+def cpu_sample_nufft(inp, bounds, eps, patch=128, t=0):
+    """Oracle NUFFT synthesis on a bounded sample: time step t (FP64 Gram +
     Jacobi eigensolve, then the type-3 NUFFT of its level visibilities) onto
-    the central patch^2 pixels of the image; products/s of that sample."""
-    import oracle
+    the central patch^2 pixels of the image; measured time and products."""
     from oracle import nufft as onu
     side = int(round(math.sqrt(inp.n_pix)))
     c0 = side // 2 - patch // 2
     rows = np.arange(c0, c0 + patch)
     sel = (rows[:, None] * side + rows[None, :]).ravel()
     t0 = time.perf_counter()
-    onu.nufft_levels(inp.pix[sel], inp.wl, bounds, inp.n_eig, inp.st_xyz[0], inp.vis[0], eps=eps)
+    onu.nufft_levels(inp.pix[sel], inp.wl, bounds, inp.n_eig, inp.st_xyz[t], inp.vis[t], eps=eps)
     dt = time.perf_counter() - t0
-    n_st = inp.st_xyz[0].shape[0]
-    return {"t_s": dt, "n_sub": int(len(sel)), "value": len(sel) * inp.n_eig * n_st / dt}
+    n_st = inp.st_xyz[t].shape[0]
+    prods = float(len(sel)) * inp.n_eig * n_st
+    return {"t_s": dt, "n_sub": int(len(sel)), "products": prods, "value": prods / dt}
 
 
 def nufft_roofline(nt, n_level, n_pix, n_t, n_st, n_eig, hbm_gbs):
@@ -396,6 +411,7 @@ def batch_main(args, ws, rank, local):
 
     for _ in range(args.warmup):
         one_step()
+    sfu_rate = bipp_ss.bipp_ss_measure_sincos_rate(local, 5)  # the SFU bound's rate, on this GPU now
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -451,11 +467,13 @@ def batch_main(args, ws, rank, local):
         peaks = measured_peaks()
         r_tc = peaks.get("bf16_tflops_sustained", 1411.3) * 1e12
         pairs = float(sum(float(n_pix) * int(n) for n in nst))
-        t_tc, t_sfu = 3 * 8.0 * prods / r_tc, pairs / MUFU_SINCOS_PER_S
+        t_tc, t_sfu = 3 * 8.0 * prods / r_tc, pairs / sfu_rate
         roof = {"kernel": "k_synth_tc", "bound": "tensor", "achieved": 3 * 8.0 * prods / (syn_ms / 1e3) / 1e12,
                 "peak": r_tc / 1e12, "unit": "TFLOP/s", "traffic": None, "frac": max(t_tc, t_sfu) / (syn_ms / 1e3),
                 "t_roof_ms": {"tensor_split": t_tc * 1e3, "sfu_sincos": t_sfu * 1e3},
-                "peak_note": "of measured: cuBLAS bf16 sustained; frac = max(T_tensor(s=3), T_sfu) / measured time"}
+                "sfu_sincos_pairs_per_s": sfu_rate,
+                "peak_note": ("of measured: cuBLAS bf16 sustained; frac = max(T_tensor(s=3), T_sfu) / measured "
+                              "time; SFU rate measured in this run by bipp_ss_measure_sincos_rate")}
         line = {"metric": METRIC, "value": prods * ws / (ms_step / 1e3), "unit": UNIT, "n_gpus": ws,
                 "steps": K, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": dtype_label(args), "data": "synthetic",
@@ -578,50 +596,57 @@ def grad_main(args, ws, rank, local):
 
 
 def reference_main(args, ws, rank):
+    """The reference arm: the FP64 CPU oracle, as it stands, on bounded samples
+    of the same workload (one time step's Gram + eigensolve and the synthesis
+    of a strided pixel subset per bench step). value = the products of the
+    timed samples / their measured wall time; ms_per_step = the measured wall
+    time of one sample; the linear extrapolation to the whole job is reported
+    apart (extrapolated_job_ms), never as the value."""
     if rank != 0:
         return 0
     import oracle
+    from oracle import estimate as oest
     inp = workload(args)
-    # level bounds from the oracle's own pre-pass over a few steps (no GPU input)
+    # level bounds from the oracle's own pre-pass over a few steps (no GPU, no library)
     pooled = []
-    for t in range(0, inp.n_t, max(1, inp.n_t // 4))[:4]:
+    for t in range(0, inp.n_t, max(1, inp.n_t // 2))[:2]:
         mu, _, _ = oracle.geneig(inp.vis[t], oracle.gram(inp.st_xyz[t], inp.wl))
         pooled.extend(mu[: inp.n_eig])
-    from paper_2310_09200_b300.bipp_ss import quantile_level_bounds
-    bounds = quantile_level_bounds(pooled, inp.n_level)
-    if args.synthesis == "nufft":
-        samples = [cpu_sample_nufft(inp, bounds, args.nufft_eps) for _ in range(args.steps)]
-        value = statistics.median(s["value"] for s in samples)
-        job_ms = inp.n_pix * inp.n_eig * inp.st_xyz[0].shape[0] * inp.n_t / value * 1e3
-        sample = (f"1 of {inp.n_t} time steps per bench step: FP64 Gram + Jacobi eigensolve of 512 stations and "
-                  f"the FP64 numpy type-3 NUFFT of its 4 level visibilities onto the central {samples[0]['n_sub']} "
-                  f"pixels; products/s of that sample (no warm-up: each sample is a whole oracle run)")
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "gpu_used": False, "steps": args.steps,
-                "warmup": 0, "ms_per_step": job_ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-                "config": config_dict(args, inp, "fp64 (oracle)"),
-                "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                                 "sample": sample},
-                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-        print(json.dumps(line), flush=True)
-        return 0
-    samples = []
-    for i in range(args.warmup + args.steps):
-        s = cpu_sample(inp, bounds)
-        if i >= args.warmup:
-            samples.append(s)
-    value = statistics.median(s["value"] for s in samples)
-    full_job_ms = inp.n_t * statistics.median(s["full_step_s"] for s in samples) * 1e3
+    bounds = np.array(oest.quantile_bounds(pooled, inp.n_level))
     cores = os.cpu_count()
-    sample = (f"1 of {inp.n_t} time steps per bench step: FP64 Gram + Jacobi eigensolve (single thread) of 512 "
-              f"stations, then synthesis of a strided {samples[0]['n_sub']}-pixel subset (OpenMP over pixels); "
-              f"per-step time extrapolated linearly to {inp.n_pix} pixels and to {inp.n_t} steps")
+    n_st = inp.st_xyz[0].shape[0]
+    if args.synthesis == "nufft":
+        for _ in range(args.warmup):
+            cpu_sample_nufft(inp, bounds, args.nufft_eps, patch=32)  # warm-up: a small patch
+        samples = [cpu_sample_nufft(inp, bounds, args.nufft_eps, t=k % inp.n_t) for k in range(args.steps)]
+        wall = sum(x["t_s"] for x in samples)
+        value = sum(x["products"] for x in samples) / wall
+        sample = (f"per bench step one time step of the job (steps 0..{args.steps - 1}): FP64 Gram + Jacobi "
+                  f"eigensolve of {n_st} stations and the FP64 numpy type-3 NUFFT of its {inp.n_level} level "
+                  f"visibilities onto the central {samples[0]['n_sub']} pixels; value = products of those pixels / "
+                  f"measured wall time; warm-up: the same on 32^2 pixels")
+        extra = {}
+    else:
+        for k in range(args.warmup):
+            cpu_sample(inp, bounds, t=k % inp.n_t, eig=False)  # warm-up: synthesis of the subset only
+        samples = [cpu_sample(inp, bounds, t=k % inp.n_t) for k in range(args.steps)]
+        wall = sum(x["wall_s"] for x in samples)
+        value = sum(x["products"] for x in samples) / wall
+        sample = (f"per bench step one time step of the job (steps 0..{args.steps - 1}): FP64 Gram + Jacobi "
+                  f"eigensolve of {n_st} stations (single thread, mean {statistics.mean(x['t_eig_s'] for x in samples):.1f} s) "
+                  f"and the synthesis of a strided {samples[0]['n_sub']}-pixel subset with its {inp.n_eig} kept "
+                  f"eigenpairs (OpenMP over pixels, mean {statistics.mean(x['t_synth_sub_s'] for x in samples):.2f} s); "
+                  f"value = products of that subset / measured wall time of the sample; warm-up steps run the "
+                  f"subset synthesis only")
+        extra = {"extrapolated_job_ms": statistics.median(x["extrapolated_job_ms"] for x in samples),
+                 "extrapolation_note": ("the whole job (all pixels, all steps) scaled linearly from the samples: "
+                                        "context only, not the value")}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "gpu_used": False, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": full_job_ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": config_dict(args, inp, "fp64 (oracle)"),
+            "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": config_dict(args, inp, args.precision),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}, **extra}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -660,6 +685,7 @@ def ours_main(args, ws, rank, local):
 
     for _ in range(args.warmup):
         one_step()
+    sfu_rate = bipp_ss.bipp_ss_measure_sincos_rate(local, 5)  # the SFU bound's rate, on this GPU now
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -737,7 +763,8 @@ def ours_main(args, ws, rank, local):
     else:
         traffic = synth_tc_traffic({"n_st": int(n_st), "n_pix": int(inp.n_pix), "n_eig": int(inp.n_eig),
                                     "n_level": int(inp.n_level), "n_t": int(inp.n_t), "precision": args.precision})
-        roof_synth = tc_roofline(syn_flops, syn_ms, inp.n_pix * n_st * inp.n_t, measured_peaks(), traffic)
+        roof_synth = tc_roofline(syn_flops, syn_ms, inp.n_pix * n_st * inp.n_t, measured_peaks(), traffic,
+                                 sfu_rate)
     # the dominant single kernel: the FP64 Jacobi when it runs, else the synthesis (the mixed
     # eigensolve is a stage of ~60 launches, the largest of which is well below the synthesis)
     dominant = roof_jacobi if (args.eig == "jacobi64" and eig_ms >= syn_ms) else roof_synth
@@ -767,18 +794,24 @@ def ours_main(args, ws, rank, local):
     ss.close()
 
     cpu = None
+    ref = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and nufft:
         s = cpu_sample_nufft(inp, bounds, args.nufft_eps)
         cpu = {"value": s["value"], "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": (f"one time step: FP64 Gram + Jacobi of {n_st} stations and the FP64 numpy type-3 NUFFT "
                           f"of its level visibilities onto the central {s['n_sub']} pixels ({s['t_s']:.1f} s); "
-                          f"products/s of that sample")}
+                          f"products of those pixels / measured time")}
     elif rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        s = cpu_sample(inp, bounds)
-        cpu = {"value": s["value"], "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-               "sample": (f"one time step: FP64 Gram + Jacobi of {n_st} stations (single thread, "
-                          f"{s['t_eig_s']:.1f} s) + synthesis of a strided {s['n_sub']}-pixel subset "
-                          f"(OpenMP, {s['t_synth_sub_s']:.2f} s), extrapolated linearly to {inp.n_pix} pixels")}
+        ref = cpu_sample(inp, bounds)
+        cpu = {"value": ref["value"], "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": (f"time step 0: FP64 Gram + Jacobi of {n_st} stations (single thread, "
+                          f"{ref['t_eig_s']:.1f} s) + synthesis of a strided {ref['n_sub']}-pixel subset "
+                          f"(OpenMP, {ref['t_synth_sub_s']:.2f} s); products of that subset / measured wall time "
+                          f"of the sample"),
+               "extrapolated_job_ms": ref["extrapolated_job_ms"]}
+    forms = None
+    if rank == 0 and not nufft and not args.no_forms:
+        forms = precision_forms(args, inp, bounds, d_st, d_V, nst, local, ref)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -792,11 +825,48 @@ def ours_main(args, ws, rank, local):
                    if nufft else {}),
                 "synthesis_only_value": prods / (syn_ms / 1e3),
                 "roofline": dominant, "roofline_synthesis": roof_synth, "roofline_jacobi": roof_jacobi,
-                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+                **({"precision_forms": forms} if forms else {})}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def precision_forms(args, inp, bounds, d_st, d_V, nst, local, ref):
+    """The precision forms side by side on the same job (outside the timed
+    region): the synthesis stage of its first 10 steps on all pixels in the
+    plain FP32 CUDA-core path and the two split tensor-core forms (best of two
+    collects after one that autotunes and captures the graph), and, when the
+    oracle sample `ref` of step 0 is at hand, each form's per-level relative L2
+    error on that sample's pixels against the FP64 oracle."""
+    from paper_2310_09200_b300 import bipp_ss
+    n10 = min(10, inp.n_t)
+    n_st = inp.st_xyz[0].shape[0]
+    prods = float(inp.n_pix) * inp.n_eig * n_st * n10
+    out = {"note": (f"synthesis stage of steps 0..{n10 - 1} on all {inp.n_pix} pixels (CUDA events in the library, "
+                    "best of 2 after a warm-up collect); level_rel_l2_vs_oracle: step 0 on the strided "
+                    "pixel subset of the CPU sample, GPU eigensolve and synthesis against the FP64 oracle's")}
+    for prec in ("fp32", "split_bf16", "split_fp16"):
+        with bipp_ss.StandardSynthesis(inp.pix, inp.wl, bounds, n_eig=inp.n_eig, precision=prec, device=local,
+                                       eig_mode=args.eig) as ss:
+            ms = []
+            for k in range(3):
+                bipp_ss.bipp_ss_collect_device(ss.h, nst[:n10], d_st[:n10], d_V[:n10])
+                if k:
+                    ms.append(ss.timings()["synth_ms"])
+        entry = {"synth_ms": min(ms), "synth_products_per_s": prods / (min(ms) / 1e3)}
+        if ref is not None:
+            with bipp_ss.StandardSynthesis(inp.pix[ref["sel"]], inp.wl, bounds, n_eig=inp.n_eig, precision=prec,
+                                           device=local, eig_mode=args.eig) as ss:
+                ss.collect(inp.st_xyz[0], inp.vis[0])
+                got = ss.get()
+            want = ref["img"]
+            entry["level_rel_l2_vs_oracle"] = [
+                float(np.linalg.norm(got[:, l] - want[:, l]) / max(np.linalg.norm(want[:, l]), 1e-300))
+                for l in range(want.shape[1])]
+        out[prec] = entry
+    return out
 
 
 if __name__ == "__main__":

@@ -317,6 +317,16 @@ int bipp_ss_collect_noalloc(int64_t n_pix, const double* d_pix_xyz, double wl, i
                             int32_t n_st, const double* d_st_xyz, const double* d_vis, double* d_img,
                             void* stream, char* err_msg, int32_t err_len);
 
+/* Measurement of the special-function-unit rate that bounds the phase
+ * generation of the synthesis (Algorithm 2 evaluates exp(j theta) for every
+ * pixel-station pair, Sec. 2.9): a kernel of independent __sincosf chains
+ * (the intrinsic the synthesis kernels use) over 4 CTAs of 256 threads per SM
+ * of `device` (-1 = current), timed with CUDA events after one warm-up launch;
+ * *pairs_per_s receives the best of `repeats` (1..100) launches, in sine +
+ * cosine pairs per second. Allocates and frees a small output buffer; takes a
+ * few milliseconds per launch. */
+int bipp_ss_measure_sincos_rate(int32_t device, int32_t repeats, double* pairs_per_s);
+
 /* Release the handle and its device memory. NULL is accepted. */
 int bipp_ss_destroy(bipp_ss_t h);
 

@@ -52,7 +52,7 @@ EXPORTED = [
     "bipp_ss_last_error", "bipp_ss_collect_noalloc", "bipp_ss_synth_levels_device",
     "bipp_ss_synth_adjoint_device", "bipp_ss_create_channels", "bipp_ss_collect_channels",
     "bipp_ss_energy_neig", "bipp_ss_kmeans_bounds", "bipp_ss_get_nufft_timings", "bipp_ss_collect_device_c64",
-    "bipp_ss_debug_fail_wait", "bipp_ss_quantile_bounds",
+    "bipp_ss_debug_fail_wait", "bipp_ss_quantile_bounds", "bipp_ss_measure_sincos_rate",
 ]
 
 BIPP_NOALLOC_MAX_STATIONS = 128
@@ -110,6 +110,7 @@ def load(path: str | None = None):
     L.bipp_ss_energy_neig.argtypes = [i32, dp, C.c_double, ip]
     L.bipp_ss_kmeans_bounds.argtypes = [i32, dp, i32, dp]
     L.bipp_ss_quantile_bounds.argtypes = [i32, dp, i32, dp]
+    L.bipp_ss_measure_sincos_rate.argtypes = [i32, i32, dp]
     L.bipp_ss_last_error.argtypes = [H]
     L.bipp_ss_last_error.restype = C.c_char_p
     L.bipp_ss_collect_noalloc.argtypes = [i64, vp, C.c_double, i32, dp, i32, i32, i32, i32, vp, vp, vp, vp,
@@ -359,6 +360,16 @@ def bipp_ss_debug_fail_wait(h, on: bool) -> None:
     synthesis kernel's bounded wait runs out and collects raise
     BIPP_ERR_DEVICE_TIMEOUT (no GPU fault)."""
     _check(h, load().bipp_ss_debug_fail_wait(h, 1 if on else 0))
+
+
+def bipp_ss_measure_sincos_rate(device: int = -1, repeats: int = 5) -> float:
+    """Measured sine + cosine pairs per second of __sincosf on the device (the
+    SFU bound of the synthesis' phase generation)."""
+    r = C.c_double(0.0)
+    rc = load().bipp_ss_measure_sincos_rate(int(device), int(repeats), C.byref(r))
+    if rc != BIPP_OK:
+        raise BippError(rc, bipp_ss_last_error(None))
+    return float(r.value)
 
 
 def bipp_ss_destroy(h) -> None:

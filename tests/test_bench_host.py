@@ -10,11 +10,11 @@ import bench
 def test_tc_roofline_of_the_default_job():
     """1024^2 pixels x 512 stations x 64 eigenvectors x 100 steps in 96.8 ms against
     a 1385.2 TFLOP/s tensor peak: the split GEMM's 3 x 8 P flops take 59.5 ms at
-    peak, the 5.4e10 sincos pairs 24.1 ms at the SFU rate, and 41 instructions per
+    peak, the 5.4e10 sincos pairs 24.1 ms at an SFU rate of 2.23e12 pairs/s, and 41 instructions per
     pair 57.2 ms of issue slots; frac is the larger of the first two over 96.8 ms."""
     P = 1048576 * 512 * 64 * 100
     pairs = 1048576 * 512 * 100
-    r = bench.tc_roofline(8.0 * P, 96.8, pairs, {"bf16_tflops_sustained": 1385.2}, None)
+    r = bench.tc_roofline(8.0 * P, 96.8, pairs, {"bf16_tflops_sustained": 1385.2}, None, 2.23e12)
     t = r["t_roof_ms"]
     assert t["tensor_split"] == pytest.approx(3 * 8.0 * P / 1385.2e12 * 1e3)
     assert t["sfu_sincos"] == pytest.approx(pairs / 2.23e12 * 1e3)
