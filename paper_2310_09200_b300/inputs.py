@@ -235,12 +235,14 @@ def make_nufft_config(*, n_t: int = 50, n_side: int = 1024, pix_arcsec: float = 
 
 def make_batch_config(n_chan: int = 64, n_t: int = 20, n_side: int = 512, seed: int = 1003,
                       wl_lo: float = 1.5, wl_hi: float = 3.0, n_st_lo: int = 48, n_st_hi: int = 512,
-                      n_eig_lo: int = 8, n_eig_hi: int = 64):
+                      n_eig_lo: int = 8, n_eig_hi: int = 64, sizes=None):
     """Batched multi-channel workload: n_chan channels (wl linear on
     [wl_lo, wl_hi]) x n_t steps; per problem a random flagging of the
     512-station layout keeps n_st ~ U{n_st_lo..n_st_hi} stations and asks for
-    n_eig ~ U{n_eig_lo..min(n_eig_hi, n_st)} eigenpairs. Returns a list of
-    per-channel dicts with keys wl, st_xyz (list), vis (list), n_eig (list)."""
+    n_eig ~ U{n_eig_lo..min(n_eig_hi, n_st)} eigenpairs. sizes: optional
+    [n_chan][n_t] list of (n_st, n_eig) that replaces those draws (the
+    flagging itself stays random). Returns a list of per-channel dicts with
+    keys wl, st_xyz (list), vis (list), n_eig (list)."""
     rng = np.random.default_rng(seed)
     rng1 = np.random.default_rng(1001)
     full = layout_lognormal(512, 1000.0, 1.0, 20.0, 65000.0, 5.0, 35.0, rng1)
@@ -253,10 +255,13 @@ def make_batch_config(n_chan: int = 64, n_t: int = 20, n_side: int = 512, seed: 
         sts, viss, neigs = [], [], []
         for t in range(n_t):
             n_st = int(rng.integers(n_st_lo, n_st_hi + 1))
+            if sizes is not None:
+                n_st = int(sizes[c][t][0])
             keep = np.sort(rng.choice(512, n_st, replace=False))
             p = earth_rotate(full[keep], t * 60.0)
             sts.append(p)
             viss.append(visibilities(p, wl, src, flux, 20.0, rng).astype(np.complex64).astype(np.complex128))
-            neigs.append(int(rng.integers(n_eig_lo, min(n_eig_hi, n_st) + 1)))
+            k = int(rng.integers(n_eig_lo, min(n_eig_hi, n_st) + 1))
+            neigs.append(int(sizes[c][t][1]) if sizes is not None else k)
         chans.append({"wl": wl, "st_xyz": sts, "vis": viss, "n_eig": neigs})
     return {"pix": pixel_grid(n_side, cap), "channels": chans, "n_level": 4, "cap_deg": cap}
