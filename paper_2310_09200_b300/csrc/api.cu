@@ -165,7 +165,7 @@ static void free_batch(bipp_ss* h) {
   drop_graph(h);
   void* ptrs[] = {h->d_st, h->d_vis, h->d_G, h->d_Linv, h->d_X, h->d_C, h->d_Q, h->d_mu, h->d_status,
                   h->d_sweeps, h->d_nkept, h->d_sel_mu, h->d_level, h->d_wt, h->d_W64, h->d_W32, h->d_q,
-                  h->d_nst, h->d_neig, h->d_chan, h->d_wl, h->d_flag, h->mx.kp, h->mx.sel, h->mx.theta,
+                  h->d_nst, h->d_neig, h->d_chan, h->d_wl, h->d_flag, h->mx.kp, h->mx.lam, h->mx.tnorm, h->mx.theta,
                   h->mx.rnorm, h->mx.cnorm, h->mx.st2, h->mx.sw2};
   for (void* p : ptrs) if (p) cudaFree(p);
   h->mx = MixedWs{};
@@ -211,7 +211,8 @@ static int ensure_batch(bipp_ss* h, int T, int N, int K) {
   CUDA_TRY(h, dalloc(&h->d_wl, (size_t)T));
   CUDA_TRY(h, dalloc(&h->d_flag, 1));
   CUDA_TRY(h, dalloc(&h->mx.kp, (size_t)T));
-  CUDA_TRY(h, dalloc(&h->mx.sel, (size_t)T * N));
+  CUDA_TRY(h, dalloc(&h->mx.lam, (size_t)T * N));
+  CUDA_TRY(h, dalloc(&h->mx.tnorm, (size_t)T));
   CUDA_TRY(h, dalloc(&h->mx.theta, (size_t)T * N));
   CUDA_TRY(h, dalloc(&h->mx.rnorm, (size_t)T * N));
   CUDA_TRY(h, dalloc(&h->mx.cnorm, (size_t)T));

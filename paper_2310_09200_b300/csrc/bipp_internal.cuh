@@ -57,7 +57,8 @@ constexpr int kEigSlots = 16;
 struct MixedWs {
   int KP;          // leading dimension of the per-step kp-sized arrays (max kp of the batch)
   int* kp;         // [T] pairs refined per step: min(n, n_eig + 16)
-  int* sel;        // [T][n_max] rank of each FP32 eigenpair among the kept ones, -1 if not kept
+  float* lam;      // [T][n_max] the kp leading eigenvalues of the FP32 tridiagonal form / tnorm, descending
+  float* tnorm;    // [T] ||T||_F of the FP32 tridiagonal form (= ||C||_F to FP32 rounding)
   double* theta;   // [T][KP] refined eigenvalues
   double* rnorm;   // [T][KP] residual norms of the last pass
   double* cnorm;   // [T] ||C||_F
@@ -83,11 +84,11 @@ void launch_gram(const Batch& b, int gram_identity, cudaStream_t s);
 void launch_cholesky(const Batch& b, int gram_identity, cudaStream_t s);
 void launch_reduce(const Batch& b, int gram_identity, cudaStream_t s);
 void launch_jacobi(const Batch& b, double tol, int max_sweeps, cudaStream_t s);
-// Mixed-precision eigensolve (FP32 tridiagonal eigendecomposition + FP64-class
-// refinement of the leading pairs); needs the X and Q buffers of the batch as
-// scratch, which fits when eig_mixed_fits(n_max, KP).
+// Mixed-precision eigensolve (the leading pairs of the FP32 tridiagonal form +
+// FP64-class refinement); needs the X and Q buffers of the batch as scratch,
+// which fits when eig_mixed_fits(n_max, KP).
 bool eig_mixed_fits(int n_max, int KP);
-constexpr int kMixedLaunches = 61;  // kernels launched by launch_eig_mixed
+constexpr int kMixedLaunches = 68;  // kernels launched by launch_eig_mixed
 void launch_eig_mixed(const Batch& b, const MixedWs& w, double tol, int max_sweeps, cudaStream_t s);
 // Error message of calls without a handle (returned by bipp_ss_last_error(NULL)).
 int set_global_error(int code, const char* msg);

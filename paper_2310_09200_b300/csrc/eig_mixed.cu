@@ -2,28 +2,32 @@
 //
 // Same result as the FP64 Jacobi of Sec. 2.3 (Eq. eigenvaleq) for the pairs
 // that are kept, at a fraction of the FP64 work, which matters on B300 where
-// the FP64 pipe runs at 1/58 of the FP32 rate:
+// the FP64 pipe runs at 1/58 of the FP32 rate. Only the kp = min(n, n_eig + 16)
+// leading pairs are computed (Sec. 2.6 keeps the n_eig largest):
 //   1. the reduced matrix C = L^{-1} V L^{-T} (formed in FP64) is rounded to
-//      FP32 and diagonalised in FP32 through its real tridiagonal form
-//      (tridiag32.cuh): C ~ Q32 diag(mu32) Q32^H to a few FP32 ulps of ||C||;
-//   2. the kp = min(n, n_eig + 16) leading approximate eigenvectors X are
-//      refined in FP64 with the operator C itself:
+//      FP32 and reduced to real tridiagonal form, C32 = H T H^H (tridiag32.cuh);
+//      the kp largest eigenvalues of T come from multisection, their
+//      eigenvectors from inverse iteration, and only those kp columns are
+//      back-transformed, X = H Z_k (tridiag_sel.cuh);
+//   2. X is refined in FP64-class arithmetic with the operator C itself:
 //        orthonormalise X (Cholesky QR), Y = C X, H = X^H Y,
 //        H = U diag(theta) U^H (FP64 Jacobi on kp x kp), X <- X U, Y <- Y U,
 //        R = Y - X diag(theta) (residuals),
-//        X <- X - Q32 T,  T[m, j] = (Q32^H R)[m, j] / (mu32[m] - theta[j]) for
-//        the directions m outside the kept set (the FP32 decomposition acts as
-//        an approximate inverse of C - theta I on the complement); the two
-//        products with Q32 run in FP32, as they carry no more accuracy than
-//        Q32 itself, while the residual they correct is formed in FP64;
-//      each pass contracts the error by the FP32 preconditioner's relative
-//      accuracy over the spectral gap (about 3e-5 per pass here); a problem
-//      whose kept residuals fall below 10 * jacobi_tol * ||C||_F stops early,
-//      the rest run at most kPasses passes.
+//        X <- X - H P (T - theta_j I)^{-1} P H^H R, P = I - Z_k Z_k^T,
+//      i.e. the FP32 shift-and-invert of C on the complement of the kept
+//      directions (the same correction as Q32 (M32 - theta)^{-1} Q32^H over the
+//      complement of a full FP32 eigendecomposition, without computing it);
+//      the correction runs in FP32, as it carries no more accuracy than the
+//      FP32 decomposition, while the residual it corrects is formed in FP64;
+//      each pass contracts the error by the FP32 stage's relative accuracy over
+//      the spectral gap (about 3e-5 per pass here); a problem whose kept
+//      residuals fall below 10 * jacobi_tol * ||C||_F stops early, the rest run
+//      at most kPasses passes.
 //   3. theta and X replace the Jacobi eigenvalues and eigenvectors; the
 //      residual of the last pass is checked against 1e3 * jacobi_tol * ||C||_F.
-// FP64 cost per pass is O(n^2 kp) (one n x n by n x kp product) instead of
-// the O(n^3) of every FP64 Jacobi sweep.
+// FP64-class cost per pass is O(n^2 kp) (one n x n by n x kp product) instead
+// of the O(n^3) of every FP64 Jacobi sweep, and the FP32 stage is O(n^3) for
+// the reduction plus O(n^2 kp) for the kp vectors.
 #include <math.h>
 
 #include <algorithm>
@@ -32,6 +36,7 @@
 #include "dfloat.cuh"
 #include "jacobi.cuh"
 #include "tridiag32.cuh"
+#include "tridiag_sel.cuh"
 
 namespace bipp {
 namespace {
@@ -40,14 +45,13 @@ constexpr int kPad = 16;       // extra leading pairs refined beyond n_eig
 constexpr int kPasses = 4;     // refinement passes at most
 constexpr int kMxDone = 8;     // st2 bit: residual met the early-exit bound, later passes skip the step
 constexpr int GT = 32, GK = 16;
-static_assert(6 + 15 * (kPasses - 1) + 10 == kMixedLaunches, "launch count of the mixed eigensolver");
+static_assert(7 + 17 * (kPasses - 1) + 10 == kMixedLaunches, "launch count of the mixed eigensolver");
 
 // Shape codes of the batched complex products: dimension = n_st or kp of the problem.
 enum Dim { DN = 0, DKP = 1 };
 
 __device__ __forceinline__ int dim_of(int code, int n, int kp) { return code == DN ? n : kp; }
 
-__device__ __forceinline__ void ld_c(const float2* p, size_t i, float2* v) { *v = p[i]; }
 
 // Problem t takes no further part in the refinement: an error status, or its
 // residual already met the early-exit bound.
@@ -55,71 +59,12 @@ __device__ __forceinline__ bool mx_skip(const int* status, const int* st2, int t
   return status[t] || (st2[t] & kMxDone);
 }
 
-// out[i, j] = sum_k op(A)[i, k] B[k, j], op = identity or conjugate transpose;
-// all operands column-major with per-problem strides. R is the arithmetic
-// (FP64 for the Rayleigh-Ritz products, FP32 for the preconditioner products),
-// A may be stored in FP32 either way.
-template <typename R, typename TA, bool CONJ_T>
-__global__ void k_zgemm(const int* nst, const int* kp, int mc, int nc, int kc, const TA* A, size_t sa, int lda,
-                        const typename CplxOf<R>::T* B, size_t sb, int ldb, typename CplxOf<R>::T* out, size_t so,
-                        int ldo, const int* status, const int* st2) {
-  using C2 = typename CplxOf<R>::T;
-  const int t = blockIdx.z;
-  if (mx_skip(status, st2, t)) return;
-  const int n = nst[t], k_p = kp[t];
-  const int M = dim_of(mc, n, k_p), NN = dim_of(nc, n, k_p), K = dim_of(kc, n, k_p);
-  const int i0 = blockIdx.x * GT, j0 = blockIdx.y * GT;
-  if (i0 >= M || j0 >= NN) return;
-  A += (size_t)t * sa;
-  B += (size_t)t * sb;
-  out += (size_t)t * so;
-  __shared__ C2 sA[GK][GT + 1];
-  __shared__ C2 sB[GK][GT + 1];
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  C2 acc[4];
-#pragma unroll
-  for (int u = 0; u < 4; ++u) acc[u] = CplxOf<R>::make(R(0), R(0));
-  for (int k0 = 0; k0 < K; k0 += GK) {
-    for (int e = threadIdx.x; e < GK * GT; e += blockDim.x) {
-      const int kk = e / GT, ii = e % GT, k = k0 + kk;
-      const int i = i0 + ii, j = j0 + ii;
-      C2 a = CplxOf<R>::make(R(0), R(0)), bv = CplxOf<R>::make(R(0), R(0));
-      if (k < K && i < M) {
-        if (CONJ_T) {
-          ld_c(A, (size_t)k + (size_t)i * lda, &a);  // op(A)[i,k] = conj(A[k,i])
-          a.y = -a.y;
-        } else {
-          ld_c(A, (size_t)i + (size_t)k * lda, &a);
-        }
-      }
-      if (k < K && j < NN) bv = B[(size_t)k + (size_t)j * ldb];
-      sA[kk][ii] = a;
-      sB[kk][ii] = bv;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < GK; ++kk) {
-      const C2 a = sA[kk][tx];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const C2 bv = sB[kk][ty + 8 * u];
-        acc[u].x = fma(a.x, bv.x, fma(-a.y, bv.y, acc[u].x));
-        acc[u].y = fma(a.x, bv.y, fma(a.y, bv.x, acc[u].y));
-      }
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int i = i0 + tx, j = j0 + ty + 8 * u;
-    if (i < M && j < NN) out[(size_t)i + (size_t)j * ldo] = acc[u];
-  }
-}
-
-// The FP64 products of the refinement in double-float arithmetic (dfloat.cuh):
-// same operands, layout and result as k_zgemm<double, double2, CONJ_T>, with
-// ~2^-48 relative rounding per operation instead of 2^-53, at several times
-// the FP64 pipe's rate. Operands are split into hi/lo floats once per tile.
+// The FP64-class products of the refinement in double-float arithmetic
+// (dfloat.cuh): out[i, j] = sum_k op(A)[i, k] B[k, j], op = identity or
+// conjugate transpose, all operands column-major with per-problem strides,
+// with ~2^-48 relative rounding per operation instead of FP64's 2^-53, at
+// several times the FP64 pipe's rate. Operands are split into hi/lo floats
+// once per tile.
 template <bool CONJ_T>
 __global__ void k_zgemm_df(const int* nst, const int* kp, int mc, int nc, int kc, const double2* A, size_t sa,
                            int lda, const double2* B, size_t sb, int ldb, double2* out, size_t so, int ldo,
@@ -206,46 +151,22 @@ __global__ void k_mx_tof32(Batch b) {
   }
 }
 
-// Rank the FP32 eigenvalues, mark the kp leading ones (sel[m] = rank or -1),
-// copy their FP32 eigenvectors into X (FP64), record ||C||_F.
-__global__ void k_mx_pick(Batch b, MixedWs w) {
+// The kp back-transformed FP32 eigenvectors (rank order) become the FP64
+// start X of the refinement; ||C||_F = ||T||_F.
+__global__ void k_mx_pick(Batch b, MixedWs w, const float2* Q32, size_t qstride) {
   const int t = blockIdx.x;
   if (b.status[t]) return;
-  const int n = b.nst[t], N = b.n_max;
-  const int kp = min(n, b.neig[t] + kPad);
-  const double* mu = b.mu + (size_t)t * N;
-  int* sel = w.sel + (size_t)t * N;
-  const float2* Q32 = reinterpret_cast<const float2*>(b.X + (size_t)t * N * N) + (size_t)N * N;
+  const int n = b.nst[t], N = b.n_max, kp = w.kp[t];
+  const float2* Qt = Q32 + (size_t)t * qstride;
   double2* X = b.Q + (size_t)t * N * N;
-  __shared__ double red[256];
-  double s2 = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double mi = mu[i];
-    s2 += mi * mi;
-    int rank = 0;
-    for (int j = 0; j < n; ++j) {
-      const double mj = mu[j];
-      rank += (mj > mi) || (mj == mi && j < i);
-    }
-    sel[i] = rank < kp ? rank : -1;
-  }
-  red[threadIdx.x] = s2;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
   if (threadIdx.x == 0) {
-    w.kp[t] = kp;
-    w.cnorm[t] = sqrt(red[0]);
+    w.cnorm[t] = (double)w.tnorm[t];
+    b.sweeps[t] = 0;
   }
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    const int i = e % n, m = e / n;  // row i of FP32 eigenvector m
-    const int r = sel[m];
-    if (r >= 0) {
-      const float2 v = Q32[(size_t)i + (size_t)m * N];
-      X[(size_t)i + (size_t)r * N] = make_double2(v.x, v.y);
-    }
+  for (int e = threadIdx.x; e < n * kp; e += blockDim.x) {
+    const int i = e % n, j = e / n;
+    const float2 v = Qt[(size_t)i + (size_t)j * N];
+    X[(size_t)i + (size_t)j * N] = make_double2(v.x, v.y);
   }
 }
 
@@ -368,28 +289,6 @@ __global__ void k_mx_resid(Batch b, MixedWs w, const double2* X0, double2* Y0, f
   if (threadIdx.x == 0) w.rnorm[(size_t)t * w.KP + j] = sqrt(red[0]);
 }
 
-// T[m, j] /= (mu32[m] - theta[j]) for directions outside the kept set, 0 inside.
-__global__ void k_mx_scale(Batch b, MixedWs w, float2* T0, size_t stride) {
-  const int t = blockIdx.y;
-  if (mx_skip(b.status, w.st2, t)) return;
-  const int n = b.nst[t], N = b.n_max, kp = w.kp[t];
-  const double* mu = b.mu + (size_t)t * N;
-  const int* sel = w.sel + (size_t)t * N;
-  float2* T = T0 + (size_t)t * stride;
-  const double eps = 1e-13 * w.cnorm[t];
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * kp; e += gridDim.x * blockDim.x) {
-    const int m = e % n, j = e / n;
-    const float2 v = T[(size_t)m + (size_t)j * N];
-    const double den = mu[m] - w.theta[(size_t)t * w.KP + j];
-    float2 o = make_float2(0.f, 0.f);
-    if (sel[m] < 0 && fabs(den) > eps) {
-      const float inv = (float)(1.0 / den);
-      o = make_float2(v.x * inv, v.y * inv);
-    }
-    T[(size_t)m + (size_t)j * N] = o;
-  }
-}
-
 // X <- X - D on the n x kp block.
 __global__ void k_mx_sub(Batch b, MixedWs w, double2* X0, const float2* D0, size_t stride_x, size_t stride_d) {
   const int t = blockIdx.y;
@@ -451,54 +350,68 @@ void zgemm_df(const Batch& b, const MixedWs& w, int mc, int nc, int kc, int mmax
   k_zgemm_df<CT><<<grd, 256, 0, s>>>(b.nst, w.kp, mc, nc, kc, A, sa, lda, B, sb, ldb, out, so, ldo, b.status, w.st2);
 }
 
-template <typename R, typename TA, bool CT>
-void zgemm(const Batch& b, const MixedWs& w, int mc, int nc, int kc, int mmax, int nmax, const TA* A, size_t sa,
-           int lda, const typename CplxOf<R>::T* B, size_t sb, int ldb, typename CplxOf<R>::T* out, size_t so,
-           int ldo, cudaStream_t s) {
-  dim3 grd((mmax + GT - 1) / GT, (nmax + GT - 1) / GT, b.T);
-  k_zgemm<R, TA, CT><<<grd, 256, 0, s>>>(b.nst, w.kp, mc, nc, kc, A, sa, lda, B, sb, ldb, out, so, ldo, b.status,
-                                         w.st2);
-}
-
 }  // namespace
 
 // The refinement's blocks must fit the Q buffer, and the kp x kp Cholesky of
 // k_mx_cholinv its shared memory (kp <= 110: 195 KB).
-bool eig_mixed_fits(int N, int KP) { return KP <= 110 && 4LL * N * KP + 3LL * KP * KP <= (long long)N * N; }
+// The FP32 stage keeps its reflectors, kp vectors and tridiagonal scratch in
+// the X buffer (2 N^2 + 2 N kp + N^2 + 4 N + 1 floats of 4 N^2).
+bool eig_mixed_fits(int N, int KP) {
+  return KP <= 110 && 4LL * N * KP + 3LL * KP * KP <= (long long)N * N && N >= 2 * KP + 5;
+}
 
 void launch_eig_mixed(const Batch& b, const MixedWs& w, double tol, int max_sweeps, cudaStream_t s) {
   const int N = b.n_max, KP = w.KP, T = b.T;
   const size_t NN = (size_t)N * N;
-  // 1. FP32 eigendecomposition of all pairs through the real tridiagonal form
-  //    (C32, Q32 in the two halves of the X buffer; its scratch in the Q buffer,
-  //    which the refinement takes over afterwards)
+  // 1. FP32 stage, in the X buffer of each problem (4 N^2 floats): C32 and then the
+  //    reflectors in floats [0, 2N^2), the kp back-transformed vectors Q32 (N x KP
+  //    complex) after them, then the tridiagonal scratch (Z_k in its first KP columns,
+  //    d, e, tau). The inverse iteration's factors use the Q buffer, which the
+  //    refinement takes over afterwards.
+  float* Xf = reinterpret_cast<float*>(b.X);
+  const size_t xs = 4 * NN;  // floats per problem in the X and Q buffers
   k_mx_tof32<<<dim3(std::max(1, std::min(64, (N * N + 255) / 256)), T), 256, 0, s>>>(b);
   TridiagArgs a;
-  a.C = reinterpret_cast<float2*>(b.X);
-  a.Q = reinterpret_cast<float2*>(b.X) + NN;
-  a.scratch = reinterpret_cast<float*>(b.Q);
-  a.sstride = 4 * NN;
-  a.mu = b.mu;
+  a.C = reinterpret_cast<float2*>(Xf);
+  a.scratch = Xf + 2 * NN + 2 * (size_t)N * KP;
+  a.sstride = xs;
   a.status = b.status;
-  a.steps = b.sweeps;
   a.n = b.nst;
   a.ld = N;
   a.stride = 2 * NN;
-  launch_tridiag32(a, T, s);
-  const float2* Q32 = reinterpret_cast<const float2*>(b.X) + NN;
+  launch_tridiag32_reduce(a, T, s);
+  float2* Q32 = reinterpret_cast<float2*>(Xf + 2 * NN);  // problem stride 2 N^2 float2, as C32
+  SelArgs sa;
+  sa.refl = a.C;
+  sa.tds = a.scratch;
+  sa.sstride = xs;
+  sa.Z = a.scratch;
+  sa.lam = w.lam;
+  sa.lam_ld = N;
+  sa.tnorm = w.tnorm;
+  sa.n = b.nst;
+  sa.neig = b.neig;
+  sa.kp = w.kp;
+  sa.pad = kPad;
+  sa.status = b.status;
+  sa.ld = N;
+  sa.stride = 2 * NN;
+  const int sm2 = 2 * N * (int)sizeof(float);
+  cudaFuncSetAttribute(k_td_topeig, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
+  k_td_topeig<<<T, kSelThreads, sm2, s>>>(sa);
+  k_td_invit<<<T, kInvitThreads, sm2, s>>>(sa, reinterpret_cast<float*>(b.Q), xs, KP);
+  launch_td_apply<false, true>(sa, Q32, 2 * NN, KP, T, s);  // Q32 = H Z_k
   // 2. FP64 refinement of the kp leading pairs; buffers inside the Q buffer
   double2* P0 = b.Q;                       // X (final eigenvectors), n x kp, ld N
-  double2* P1 = b.Q + (size_t)N * KP;      // orthonormalised X / FP32 R and T
-  double2* P2 = b.Q + (size_t)2 * N * KP;  // Y = C X / FP32 D
-  double2* P3 = b.Q + (size_t)3 * N * KP;  // Y U / R
+  double2* P1 = b.Q + (size_t)N * KP;      // orthonormalised X / FP32 R and its correction
+  double2* P2 = b.Q + (size_t)2 * N * KP;  // Y = C X
+  double2* P3 = b.Q + (size_t)3 * N * KP;  // Y U / R, then the shifted solves' factors
   float2* R32 = reinterpret_cast<float2*>(P1);
-  float2* T32 = R32 + (size_t)N * KP;
-  float2* D32 = reinterpret_cast<float2*>(P2);
   const size_t NN2 = 2 * NN;  // per-problem stride of the FP32 views
   double2* Hs = b.Q + (size_t)4 * N * KP;  // S, then H (kp x kp, ld KP)
   double2* Us = Hs + (size_t)KP * KP;      // rotations of H
   double2* Ws = Us + (size_t)KP * KP;      // R^{-1}
-  k_mx_pick<<<T, 256, 0, s>>>(b, w);
+  k_mx_pick<<<T, 256, 0, s>>>(b, w, Q32, 2 * NN);
   JacobiArgs h;
   h.C = Hs;
   h.Q = Us;
@@ -513,6 +426,7 @@ void launch_eig_mixed(const Batch& b, const MixedWs& w, double tol, int max_swee
   const int ew = std::max(1, (N * KP + 255) / 256 / 8);  // blocks per problem of the elementwise kernels
   const int ci_smem = (int)(sizeof(double2) * ((size_t)KP * KP + KP));
   cudaFuncSetAttribute(k_mx_cholinv, cudaFuncAttributeMaxDynamicSharedMemorySize, ci_smem);
+  float* lu3 = reinterpret_cast<float*>(P3);
   for (int pass = 0; pass < kPasses; ++pass) {
     zgemm_df<true>(b, w, DKP, DKP, DN, KP, KP, P0, NN, N, P0, NN, N, Hs, NN, KP, s);   // S = X^H X
     k_mx_cholinv<<<T, 256, ci_smem, s>>>(b, w, Hs, Ws, NN, KP);                                    // W = R^{-1}
@@ -526,13 +440,16 @@ void launch_eig_mixed(const Batch& b, const MixedWs& w, double tol, int max_swee
     k_mx_resid<<<dim3(KP, T), 256, 0, s>>>(b, w, P0, P3, R32, NN);                                // R = YU - X th
     if (pass == kPasses - 1) break;
     k_mx_check<<<(T + 127) / 128, 128, 0, s>>>(b, w, 10.0 * tol);
-    // preconditioner products in FP32: they only need the accuracy of Q32 itself
-    zgemm<float, float2, true>(b, w, DN, DKP, DN, N, KP, Q32, NN2, N, R32, NN2, N, T32, NN2, N, s);   // T = Q32^H R
-    k_mx_scale<<<dim3(ew, T), 256, 0, s>>>(b, w, T32, NN2);
-    zgemm<float, float2, false>(b, w, DN, DKP, DN, N, KP, Q32, NN2, N, T32, NN2, N, D32, NN2, N, s);  // D = Q32 T
-    k_mx_sub<<<dim3(ew, T), 256, 0, s>>>(b, w, P0, D32, NN, NN2);                                   // X -= D
+    // correction in FP32: H P (T - theta_j)^{-1} P H^H r_j, P = I - Z_k Z_k^T
+    launch_td_apply<true, false>(sa, R32, NN2, KP, T, s);                                   // S = H^H R
+    k_td_deflate<<<dim3(KP, T), 256, KP * sizeof(float2), s>>>(sa, R32, NN2);
+    k_td_shiftsolve<<<dim3((KP + 31) / 32, T), 32, sm2, s>>>(sa, R32, NN2, w.theta, w.KP, lu3, xs, KP);
+    k_td_deflate<<<dim3(KP, T), 256, KP * sizeof(float2), s>>>(sa, R32, NN2);
+    launch_td_apply<false, false>(sa, R32, NN2, KP, T, s);                                  // D = H U
+    k_mx_sub<<<dim3(ew, T), 256, 0, s>>>(b, w, P0, R32, NN, NN2);                                 // X -= D
   }
   k_mx_final<<<T, 256, 0, s>>>(b, w, 1e3 * tol);
+  (void)max_sweeps;
 }
 
 }  // namespace bipp

@@ -25,8 +25,20 @@ def test_tc_roofline_of_the_default_job():
     assert 0.6 < r["frac"] < 0.63 and 0.58 < r["frac_issue"] < 0.6
 
 
-def test_traffic_only_for_the_captured_workload():
-    w = dict(bench.SYNTH_TC_TRAFFIC["workload"])
-    assert bench.synth_tc_traffic(w) == bench.SYNTH_TC_TRAFFIC["bytes"]
+def test_traffic_only_for_the_captured_workload(monkeypatch):
+    """The recorded DRAM traffic is reported only while the kernel sources hash
+    to those of the capture and the workload is the captured one."""
+    import hashlib
+    import os
+    csrc = os.path.join(os.path.dirname(bench.__file__), "paper_2310_09200_b300", "csrc")
+    now = {name: hashlib.sha256(open(os.path.join(csrc, name), "rb").read()).hexdigest()
+           for name in bench.SYNTH_TC_TRAFFIC["sha256"]}
+    rec = dict(bench.SYNTH_TC_TRAFFIC, sha256=now)
+    monkeypatch.setattr(bench, "SYNTH_TC_TRAFFIC", rec)
+    w = dict(rec["workload"])
+    assert bench.synth_tc_traffic(w) == rec["bytes"]
     w["n_t"] = 10
     assert bench.synth_tc_traffic(w) is None
+    stale = dict(rec, sha256={k: "0" * 64 for k in now})
+    monkeypatch.setattr(bench, "SYNTH_TC_TRAFFIC", stale)
+    assert bench.synth_tc_traffic(dict(rec["workload"])) is None
