@@ -493,12 +493,13 @@ def batch_main(args, ws, rank, local):
 
 def grad_main(args, ws, rank, local):
     """Differentiation (configuration 4): loss = ||I_levels - I_target||^2 over 4
-    levels of 512^2 pixels from 256 stations, 16 steps, N_eig 32; forward through
-    the plain FP32 synthesis (with station gains), backward through the adjoint
-    kernel that recomputes the phases. Eigenvectors, weights and levels are
-    synthetic of the same shapes (their values do not change the work). One JSON
-    line: fwd + bwd ms per step (one step = the whole 16-step loss and its
-    gradients), the forward alone (the plain FP32 path) and their ratio."""
+    levels of 512^2 pixels from 256 stations, 16 steps, N_eig 32. One bench step
+    = the forward and backward of the whole 16-step loss in --precision (split
+    FP16 by default: the tensor-core forward and adjoint; "fp32": the CUDA-core
+    kernels). Eigenvectors, weights and levels are synthetic of the same
+    shapes (their values do not change the work). Beside the timed region the
+    plain FP32 path is timed the same way (forward alone, forward + backward),
+    the comparison the metric names."""
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps({"impl": "reference", "unavailable": "the grad mode has no CPU reference arm; "
@@ -517,6 +518,7 @@ def grad_main(args, ws, rank, local):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
+    prec = args.precision if args.precision in ("fp32", "split_fp16", "split_bf16") else "split_fp16"
     inp = inputs.make_config(4)
     T, n_st, K, L = inp.n_t, inp.st_xyz[0].shape[0], inp.n_eig, inp.n_level
     rng = np.random.default_rng(1004)
@@ -535,22 +537,31 @@ def grad_main(args, ws, rank, local):
     tg = torch.tensor(g, device=dev, requires_grad=True)
     stream = torch.cuda.current_stream(dev)
 
-    def step(marks=None):
+    def step(precision, marks=None, backward=True):
         tW.grad = None
         tg.grad = None
         if marks:
             marks[0].record(stream)
-        img = synth_levels(t_pix, t_st, tW, t_d, t_lev, tg, inp.wl, L)
+        img = synth_levels(t_pix, t_st, tW, t_d, t_lev, tg, inp.wl, L, precision)
         if marks:
             marks[1].record(stream)
         loss = ((img - target) ** 2).sum()
-        loss.backward()
+        if backward:
+            loss.backward()
         if marks:
             marks[2].record(stream)
         return loss
 
+    def timed(precision, n, backward=True):
+        marks = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(n)]
+        for k in range(n):
+            step(precision, marks[k], backward)
+        torch.cuda.synchronize()
+        return (statistics.mean(m[0].elapsed_time(m[1]) for m in marks),
+                statistics.mean(m[1].elapsed_time(m[2]) for m in marks))
+
     for _ in range(args.warmup):
-        step()
+        step(prec)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -560,7 +571,7 @@ def grad_main(args, ws, rank, local):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for k in range(args.steps):
-        step(marks[k])
+        step(prec, marks[k])
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = clk.stop()
@@ -571,28 +582,61 @@ def grad_main(args, ws, rank, local):
         dist.barrier()
         ms_total = max_over_ranks(ms_total, device=dev)
     ms_step = ms_total / args.steps
-    pairs = inp.n_pix * n_st * T
-    flops_bwd = pairs * (16.0 * K)  # recomputed z plus the gradient sums, complex
-    ach = flops_bwd / (bwd / 1e3) / 1e12
+    # the plain FP32 path beside it (outside the timed region)
+    for _ in range(2):
+        step("fp32")
+    f32_fwd, _ = timed("fp32", 3, backward=False)
+    f32_fwd_b, f32_bwd = timed("fp32", 3)
+    pairs = float(inp.n_pix) * n_st * T
+    prods = pairs * K
+    if prec == "fp32":
+        flops_bwd = pairs * (16.0 * K)  # recomputed z plus the gradient sums, complex
+        ach = flops_bwd / (bwd / 1e3) / 1e12
+        roof = {"kernel": "k_adjoint", "bound": "alu", "achieved": ach, "peak": FP32_PEAK_FLOPS / 1e12,
+                "unit": "TFLOP/s", "traffic": None, "frac": ach / (FP32_PEAK_FLOPS / 1e12),
+                "peak_note": "16 K flops per pixel-station pair and step (recomputed z and the gradient sums) "
+                             "against the FP32 pipe"}
+    else:
+        # backward: z recomputed (8 P real flops, x3 split) and grad_W' = 2 sum_r Phi Y as the real GEMM
+        # [cos; sin] (2 n_st rows) x [Re Y, Im Y] (2 K columns) over pixels (x3 split); two Phi generations
+        sfu = bipp_ss_rate(local)
+        peaks = measured_peaks()
+        r_tc = peaks.get("bf16_tflops_sustained", 1411.3) * 1e12
+        flops = 3 * (8.0 * prods + 2.0 * (2 * n_st) * (2 * K) * inp.n_pix * T)
+        t_tc, t_sfu = flops / r_tc, 2 * pairs / sfu
+        roof = {"kernel": "adjoint on the tensor cores (k_synth_tc Y stage + k_adjoint_tc)", "bound": "tensor",
+                "achieved": flops / (bwd / 1e3) / 1e12, "peak": r_tc / 1e12, "unit": "TFLOP/s", "traffic": None,
+                "frac": max(t_tc, t_sfu) / (bwd / 1e3),
+                "t_roof_ms": {"tensor_split": t_tc * 1e3, "sfu_sincos": t_sfu * 1e3},
+                "peak_note": ("of measured: cuBLAS bf16 sustained; the backward's split tensor flops (z recomputed, "
+                              "then Phi^T Y over pixels) and its two sincos passes against the SFU rate measured "
+                              "in this run; frac = max(T_tensor, T_sfu) / measured backward time")}
     if rank == 0:
         line = {"metric": "fwd+bwd ms per step of the differentiable level images (vs the plain FP32 forward)",
                 "value": ms_step, "unit": "ms", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32 (f64 image and gradients)", "data": "synthetic",
+                "dtype": {"fp32": "f32 (f64 image and gradients)",
+                          "split_fp16": "f16x3 tensor forward, bf16x3 tensor adjoint (f32 acc; f64 image, gradients)",
+                          "split_bf16": "bf16x3 tensor forward and adjoint (f32 acc; f64 image, gradients)"}[prec],
+                "data": "synthetic",
                 "config": {"workload": (f"differentiation: {n_st} stations, {int(round(math.sqrt(inp.n_pix)))}^2 px, "
                                         f"{T} time steps, N_eig {K}, {L} levels, gains 1 + N(0, 0.05)"),
-                           "n_st": n_st, "n_pix": int(inp.n_pix), "n_t": T, "n_eig": K, "n_level": L},
-                "fwd_ms": fwd, "bwd_ms": bwd, "fwd_bwd_over_fp32_forward": (fwd + bwd) / fwd,
-                "roofline": {"kernel": "k_adjoint", "bound": "alu", "achieved": ach,
-                             "peak": FP32_PEAK_FLOPS / 1e12, "unit": "TFLOP/s", "traffic": None,
-                             "frac": ach / (FP32_PEAK_FLOPS / 1e12),
-                             "peak_note": "16 K flops per pixel-station pair and step (recomputed z and the "
-                                          "gradient sums) against the FP32 pipe"},
-                "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clocks}
+                           "n_st": n_st, "n_pix": int(inp.n_pix), "n_t": T, "n_eig": K, "n_level": L,
+                           "precision": prec},
+                "fwd_ms": fwd, "bwd_ms": bwd,
+                "fp32_path": {"fwd_ms": f32_fwd, "fwd_bwd_ms": f32_fwd_b + f32_bwd, "bwd_ms": f32_bwd},
+                "fwd_bwd_over_fp32_forward": (fwd + bwd) / f32_fwd,
+                "speedup_vs_fp32_fwd_bwd": (f32_fwd_b + f32_bwd) / (fwd + bwd),
+                "roofline": roof, "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clocks}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def bipp_ss_rate(local):
+    from paper_2310_09200_b300 import bipp_ss
+    return bipp_ss.bipp_ss_measure_sincos_rate(local, 5)
 
 
 def reference_main(args, ws, rank):

@@ -260,23 +260,36 @@ int bipp_ss_debug_fail_wait(bipp_ss_t h, int32_t on);
  *   d_st_xyz  n_t blocks of n_st x 3 FP64 [m];  d_W: n_t blocks of n_st x n_eig complex128
  *             (column-major);  d_d: n_t x n_eig FP64 weights (row t contiguous);
  *   d_level   n_t x n_eig int32 level ids (-1 = dropped);  d_gains: n_st complex128.
+ *   precision BIPP_PREC_FP32: exact phase reduction, SFU sincos, FP32 sums on
+ *             the CUDA cores; BIPP_PREC_SPLIT_FP16 / _BF16: the tensor-core
+ *             synthesis kernel of collect() on W' = diag(conj g) W (n_eig <=
+ *             128), to the same accuracy as collect() in that precision.
  * bipp_ss_synth_levels_device writes d_img (n_pix x n_level FP64, overwritten).
- * Arithmetic: exact phase reduction, SFU sincos, FP32 sums.
- * 1 <= n_eig <= n_st <= 1024, 1 <= n_level <= 16. */
+ * 1 <= n_eig <= n_st <= 1024, 1 <= n_level <= 16; another precision returns
+ * BIPP_ERR_INVALID_ARG. */
 int bipp_ss_synth_levels_device(int64_t n_pix, const double* d_pix, double wl, int32_t n_t, int32_t n_st,
                                 int32_t n_eig, int32_t n_level, const double* d_st_xyz, const double* d_W,
                                 const double* d_d, const int32_t* d_level, const double* d_gains, double* d_img,
-                                void* stream);
+                                int32_t precision, void* stream);
 
 /* Adjoint of bipp_ss_synth_levels_device: given d_grad_img = dL/dI (n_pix x
  * n_level FP64) of a real loss L, writes the complex gradients (convention
  * dL/dRe + j dL/dIm) d_grad_W (n_t blocks of n_st x n_eig complex128) and
  * d_grad_g (n_st complex128). The phase matrix is recomputed, not stored;
- * the pixel reduction is deterministic (fixed-order two-stage sum). */
+ * the pixel reduction is deterministic (fixed-order two-stage sum).
+ *   precision BIPP_PREC_FP32: CUDA-core kernels; BIPP_PREC_SPLIT_FP16 / _BF16
+ *             (n_eig <= 64 and n_level <= 4, else BIPP_ERR_UNSUPPORTED): z
+ *             recomputed by the tensor-core synthesis kernel (hi/lo products
+ *             in that type), Y = d R z written in BF16 hi/lo, and the pixel
+ *             contraction grad_W' = 2 sum_r Phi Y as split BF16 products on the
+ *             tensor cores with FP32 accumulation; BIPP_ERR_DEVICE_TIMEOUT if
+ *             a bounded device wait gave up. Calls on one device serialise on
+ *             the library's tensor-core workspace for that device. */
 int bipp_ss_synth_adjoint_device(int64_t n_pix, const double* d_pix, double wl, int32_t n_t, int32_t n_st,
                                  int32_t n_eig, int32_t n_level, const double* d_st_xyz, const double* d_W,
                                  const double* d_d, const int32_t* d_level, const double* d_gains,
-                                 const double* d_grad_img, double* d_grad_W, double* d_grad_g, void* stream);
+                                 const double* d_grad_img, double* d_grad_W, double* d_grad_g, int32_t precision,
+                                 void* stream);
 
 /* No-allocation variant of one collect() step. The paper has no counterpart:
  * this entry point exists for callers that may not allocate device memory,

@@ -115,11 +115,12 @@ def load(path: str | None = None):
     L.bipp_ss_last_error.restype = C.c_char_p
     L.bipp_ss_collect_noalloc.argtypes = [i64, vp, C.c_double, i32, dp, i32, i32, i32, i32, vp, vp, vp, vp,
                                           C.c_char_p, i32]
-    L.bipp_ss_synth_levels_device.argtypes = [i64, vp, C.c_double, i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]
+    L.bipp_ss_synth_levels_device.argtypes = [i64, vp, C.c_double, i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, i32,
+                                              vp]
     L.bipp_ss_create_channels.argtypes = [C.POINTER(H), i64, dp, i32, dp, i32, dp, C.POINTER(bipp_ss_options)]
     L.bipp_ss_collect_channels.argtypes = [H, i32, i32, ip, ip, ip, vp, vp, i32, vp]
     L.bipp_ss_synth_adjoint_device.argtypes = [i64, vp, C.c_double, i32, i32, i32, i32, vp, vp, vp, vp, vp, vp,
-                                               vp, vp, vp]
+                                               vp, vp, i32, vp]
     for name in EXPORTED:
         if name not in ("bipp_ss_default_options", "bipp_ss_last_error"):
             getattr(L, name).restype = C.c_int
@@ -441,28 +442,39 @@ def _stream_ptr(stream):
     return None if stream is None else C.c_void_p(stream.cuda_stream)
 
 
-def bipp_ss_synth_levels_device(pix_cm, wl, st_cm, W_cm, d, level, gains, img, stream=None) -> None:
+def _precision_code(precision) -> int:
+    if isinstance(precision, str):
+        if precision not in ("fp32", "split_bf16", "split_fp16"):
+            raise ValueError(f"precision={precision!r}; choose from fp32, split_bf16, split_fp16")
+        return PRECISIONS[precision]
+    return int(precision)
+
+
+def bipp_ss_synth_levels_device(pix_cm, wl, st_cm, W_cm, d, level, gains, img, precision="fp32",
+                                stream=None) -> None:
     """Forward of the differentiable synthesis on torch CUDA tensors in the ABI
     layout: pix_cm (3, n_pix) f64, st_cm (T, 3, n_st) f64, W_cm (T, n_eig, n_st)
     c128 (column-major blocks), d (T, n_eig) f64, level (T, n_eig) int32,
-    gains (n_st,) c128, img (n_level, n_pix) f64 output."""
+    gains (n_st,) c128, img (n_level, n_pix) f64 output; precision "fp32"
+    (CUDA cores) or "split_fp16" / "split_bf16" (tensor cores)."""
     T, K, N = W_cm.shape
     rc = load().bipp_ss_synth_levels_device(int(pix_cm.shape[1]), _ptr(pix_cm), float(wl), T, N, K,
                                             int(img.shape[0]), _ptr(st_cm), _ptr(W_cm), _ptr(d), _ptr(level),
-                                            _ptr(gains), _ptr(img), _stream_ptr(stream))
+                                            _ptr(gains), _ptr(img), _precision_code(precision),
+                                            _stream_ptr(stream))
     if rc != BIPP_OK:
         raise BippError(rc, "synth_levels_device failed")
 
 
 def bipp_ss_synth_adjoint_device(pix_cm, wl, st_cm, W_cm, d, level, gains, grad_img, grad_W_cm, grad_g,
-                                 stream=None) -> None:
+                                 precision="fp32", stream=None) -> None:
     """Adjoint of bipp_ss_synth_levels_device; grad_img (n_level, n_pix) f64,
     outputs grad_W_cm (T, n_eig, n_st) c128 and grad_g (n_st,) c128."""
     T, K, N = W_cm.shape
     rc = load().bipp_ss_synth_adjoint_device(int(pix_cm.shape[1]), _ptr(pix_cm), float(wl), T, N, K,
                                              int(grad_img.shape[0]), _ptr(st_cm), _ptr(W_cm), _ptr(d),
                                              _ptr(level), _ptr(gains), _ptr(grad_img), _ptr(grad_W_cm),
-                                             _ptr(grad_g), _stream_ptr(stream))
+                                             _ptr(grad_g), _precision_code(precision), _stream_ptr(stream))
     if rc != BIPP_OK:
         raise BippError(rc, "synth_adjoint_device failed")
 

@@ -11,18 +11,25 @@
 //   grad_W'_t[i,e] = 2 sum_r Phi_t(r,i) Y_te(r)        (Phi, not its conjugate)
 //   grad_W_t[i,e]  = g_i grad_W'_t[i,e]
 //   grad_g[i]      = sum_t sum_e conj(grad_W'_t[i,e]) W_t[i,e]
-// The adjoint kernel recomputes Phi (twice: once for z, once for the pixel
-// contraction) instead of storing it, and reduces over pixels in two
-// deterministic stages (per-CTA partial sums in shared memory, then a fixed-
-// order sum over CTAs).
+// Both paths recompute Phi (once for z, once for the pixel contraction)
+// instead of storing it, and reduce over pixels in two deterministic stages
+// (per-CTA partial sums, then a fixed-order sum over CTAs):
+//   - precision BIPP_PREC_SPLIT_FP16 / _BF16 (n_eig <= 64, n_level <= 4 for
+//     the adjoint): the forward is the tensor-core synthesis kernel on W'
+//     (packed like the eigenvectors of a collect); the adjoint recomputes z
+//     with the same kernel, whose epilogue writes Y instead of |z|^2, and runs
+//     the pixel contraction Phi^T Y on the tensor cores (adjoint_tc.cu);
+//   - BIPP_PREC_FP32: the CUDA-core kernels below (FP32 sums).
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "bipp_internal.cuh"
 #include "bipp_ss.h"
 #include "phase.cuh"
+#include "synth_tc.cuh"
 
 namespace bipp {
 namespace {
@@ -284,6 +291,164 @@ int check(int64_t n_pix, int T, int N, int K, int n_level, const void* a, const 
   return BIPP_OK;
 }
 
+// ---- tensor-core path: W' = diag(conj g) W in the e-major FP64 layout of a
+// batch's kept eigenvectors, with its weights, levels, counts and wavelength,
+// so that the packing and synthesis kernels of a collect run on it unchanged.
+__global__ void k_adj_prep_tc(Batch b, const double2* W, const double* d, const int* level, const double2* g,
+                              double wl, int* nst, int* nkept, double* wls) {
+  const int t = blockIdx.x;
+  const int N = b.n_max, K = b.k_max;
+  for (int w = threadIdx.x; w < N * K; w += blockDim.x) {
+    const int i = w % N, e = w / N;
+    const size_t o = ((size_t)t * K + e) * N + i;
+    const double2 a = W[o], gi = g[i];
+    b.W64[o] = make_double2(gi.x * a.x + gi.y * a.y, gi.x * a.y - gi.y * a.x);  // conj(g) a
+  }
+  for (int e = threadIdx.x; e < K; e += blockDim.x) {
+    b.wt[(size_t)t * K + e] = d[(size_t)t * K + e];
+    b.level[(size_t)t * K + e] = level[(size_t)t * K + e];
+  }
+  if (threadIdx.x == 0) {
+    nst[t] = N;
+    nkept[t] = K;
+    wls[t] = wl;
+  }
+}
+
+// One tensor-core workspace per device, grown on demand; a call holds the
+// device's lock from packing to its final synchronisation.
+constexpr int kTcDevs = 64;
+std::mutex g_tc_mu[kTcDevs];
+TcWorkspace g_tc_ws[kTcDevs];
+int g_tc_cap[kTcDevs][3];
+
+struct TcScratch {
+  Batch b{};
+  void* base = nullptr;
+};
+
+cudaError_t prep_tc(TcScratch* s, int T, int N, int K, const double* d_st, const double* d_W, const double* d_d,
+                    const int32_t* d_level, const double* d_g, double wl, cudaStream_t st) {
+  auto rnd = [](size_t n) { return (n + 255) & ~size_t(255); };
+  const size_t bytes = rnd(sizeof(double2) * (size_t)T * N * K) + rnd(sizeof(double) * (size_t)T * K) +
+                       rnd(sizeof(int) * (size_t)T * K) + 2 * rnd(sizeof(int) * (size_t)T) +
+                       rnd(sizeof(double) * (size_t)T) + rnd(sizeof(int));
+  cudaError_t e = cudaMallocAsync(&s->base, bytes, st);
+  if (e != cudaSuccess) return e;
+  unsigned char* p = static_cast<unsigned char*>(s->base);
+  auto take = [&](size_t n) {
+    unsigned char* r = p;
+    p += rnd(n);
+    return r;
+  };
+  Batch& b = s->b;
+  b.T = T;
+  b.n_max = N;
+  b.k_max = K;
+  b.st = d_st;
+  b.chan = nullptr;
+  b.eigen = 0;
+  b.W64 = reinterpret_cast<double2*>(take(sizeof(double2) * (size_t)T * N * K));
+  b.wt = reinterpret_cast<double*>(take(sizeof(double) * (size_t)T * K));
+  b.level = reinterpret_cast<int*>(take(sizeof(int) * (size_t)T * K));
+  int* nst = reinterpret_cast<int*>(take(sizeof(int) * T));
+  int* nkept = reinterpret_cast<int*>(take(sizeof(int) * T));
+  double* wls = reinterpret_cast<double*>(take(sizeof(double) * T));
+  int* flag = reinterpret_cast<int*>(take(sizeof(int)));
+  b.nst = nst;
+  b.neig = nkept;
+  b.nkept = nkept;
+  b.wl = wls;
+  b.flag = flag;
+  if ((e = cudaMemsetAsync(flag, 0, sizeof(int), st)) != cudaSuccess) return e;
+  k_adj_prep_tc<<<T, 256, 0, st>>>(b, reinterpret_cast<const double2*>(d_W), d_d, d_level,
+                                   reinterpret_cast<const double2*>(d_g), wl, nst, nkept, wls);
+  return cudaGetLastError();
+}
+
+// The device's workspace, sized for (T, N, K); the caller holds g_tc_mu[dev].
+TcWorkspace* tc_ws(int dev, int T, int N, int K) {
+  int* c = g_tc_cap[dev];
+  if (g_tc_ws[dev].B && T <= c[0] && N <= c[1] && K <= c[2]) return &g_tc_ws[dev];
+  T = std::max(T, c[0]);
+  N = std::max(N, c[1]);
+  K = std::max(K, c[2]);
+  if (tc_alloc(&g_tc_ws[dev], T, N, K)) {
+    tc_free(&g_tc_ws[dev]);
+    c[0] = c[1] = c[2] = 0;
+    return nullptr;
+  }
+  c[0] = T;
+  c[1] = N;
+  c[2] = K;
+  return &g_tc_ws[dev];
+}
+
+int err_of(cudaError_t e) {
+  return e == cudaSuccess ? BIPP_OK : (e == cudaErrorMemoryAllocation ? BIPP_ERR_OUT_OF_MEMORY : BIPP_ERR_CUDA);
+}
+
+// Forward or adjoint on the tensor cores; R == nullptr: forward into img.
+int run_tc(int64_t n_pix, const double* d_pix, double wl, int T, int N, int K, int n_level, const double* d_st,
+           const double* d_W, const double* d_d, const int32_t* d_level, const double* d_g, bool fp16, double* img,
+           const double* R, double* gW, double* gg, cudaStream_t s) {
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kTcDevs) return BIPP_ERR_CUDA;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  std::lock_guard<std::mutex> lock(g_tc_mu[dev]);
+  TcWorkspace* w = tc_ws(dev, T, N, K);
+  if (!w) return BIPP_ERR_OUT_OF_MEMORY;
+  TcScratch sc;
+  unsigned char* Y = nullptr;
+  float* part = nullptr;
+  int rc = BIPP_OK;
+  cudaError_t e = prep_tc(&sc, T, N, K, d_st, d_W, d_d, d_level, d_g, wl, s);
+  TcPlan plan;
+  if (e == cudaSuccess) {
+    const std::vector<int> nst(T, N), neig(T, K);
+    if (tc_prepare(nst, neig, fp16, w, &plan)) rc = BIPP_ERR_UNSUPPORTED;
+  }
+  if (e == cudaSuccess && rc == BIPP_OK && tc_enqueue_pack(sc.b, plan, w, s)) e = cudaErrorLaunchFailure;
+  if (e == cudaSuccess && rc == BIPP_OK) {
+    Pixels px{n_pix, d_pix, nullptr};  // the tensor-core kernels form their fixed-point phases from FP64
+    if (!R) {
+      e = cudaMemsetAsync(img, 0, sizeof(double) * n_pix * n_level, s);
+      if (e == cudaSuccess && tc_enqueue_synth(sc.b, px, n_level, img, plan, w, s)) e = cudaErrorLaunchFailure;
+    } else {
+      const int nc64 = (int)((n_pix + 63) / 64);
+      const int ncols = plan.ncols_max;
+      const int grid = std::max(1, std::min(nc64, sms));
+      e = cudaMallocAsync(&Y, (size_t)T * nc64 * 2 * ncols * 128, s);
+      if (e == cudaSuccess) e = cudaMallocAsync(&part, sizeof(float) * (size_t)T * grid * 2 * N * ncols, s);
+      if (e == cudaSuccess) {
+        TcYOut yo;
+        yo.R = R;
+        yo.Y = Y;
+        yo.nc64 = nc64;
+        if (tc_enqueue_yout(sc.b, px, n_level, plan, w, yo, s)) rc = BIPP_ERR_UNSUPPORTED;
+      }
+      if (e == cudaSuccess && rc == BIPP_OK &&
+          launch_adjoint_tc(px, T, N, K, ncols, w->qfix, w->qfix_stride, Y, nc64, part, grid,
+                            reinterpret_cast<double2*>(gW), w->status, s))
+        e = cudaErrorLaunchFailure;
+      if (e == cudaSuccess && rc == BIPP_OK) {
+        k_adj_finish<<<(N + 127) / 128, 128, 0, s>>>(T, N, K, reinterpret_cast<const double2*>(d_W),
+                                                     reinterpret_cast<const double2*>(d_g),
+                                                     reinterpret_cast<double2*>(gW), reinterpret_cast<double2*>(gg));
+        e = cudaGetLastError();
+      }
+    }
+  }
+  if (part) cudaFreeAsync(part, s);
+  if (Y) cudaFreeAsync(Y, s);
+  if (sc.base) cudaFreeAsync(sc.base, s);
+  const cudaError_t es = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = es;
+  if (rc == BIPP_OK) rc = err_of(e);
+  if (rc == BIPP_OK && tc_read_status(w) != 0) rc = BIPP_ERR_DEVICE_TIMEOUT;
+  return rc;
+}
+
 }  // namespace
 }  // namespace bipp
 
@@ -292,10 +457,18 @@ using namespace bipp;
 extern "C" int bipp_ss_synth_levels_device(int64_t n_pix, const double* d_pix, double wl, int32_t n_t,
                                            int32_t n_st, int32_t n_eig, int32_t n_level, const double* d_st_xyz,
                                            const double* d_W, const double* d_d, const int32_t* d_level,
-                                           const double* d_gains, double* d_img, void* stream) {
+                                           const double* d_gains, double* d_img, int32_t precision, void* stream) {
   int rc = check(n_pix, n_t, n_st, n_eig, n_level, d_pix, d_st_xyz, d_W, d_d, d_level, d_gains, d_img);
   if (rc || !(wl > 0.0)) return BIPP_ERR_INVALID_ARG;
+  if (precision != BIPP_PREC_FP32 && precision != BIPP_PREC_SPLIT_BF16 && precision != BIPP_PREC_SPLIT_FP16)
+    return BIPP_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (precision != BIPP_PREC_FP32) {
+    (void)cudaGetLastError();
+    if (n_eig > kTcMaxEig) return BIPP_ERR_UNSUPPORTED;
+    return run_tc(n_pix, d_pix, wl, n_t, n_st, n_eig, n_level, d_st_xyz, d_W, d_d, d_level, d_gains,
+                  precision == BIPP_PREC_SPLIT_FP16, d_img, nullptr, nullptr, nullptr, s);
+  }
   Scratch sc;
   cudaError_t e = prep(&sc, n_pix, d_pix, wl, n_t, n_st, n_eig, d_st_xyz, d_W, d_d, d_level, d_gains, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_img, 0, sizeof(double) * n_pix * n_level, s);
@@ -313,10 +486,18 @@ extern "C" int bipp_ss_synth_adjoint_device(int64_t n_pix, const double* d_pix, 
                                             int32_t n_st, int32_t n_eig, int32_t n_level, const double* d_st_xyz,
                                             const double* d_W, const double* d_d, const int32_t* d_level,
                                             const double* d_gains, const double* d_grad_img, double* d_grad_W,
-                                            double* d_grad_g, void* stream) {
+                                            double* d_grad_g, int32_t precision, void* stream) {
   int rc = check(n_pix, n_t, n_st, n_eig, n_level, d_pix, d_st_xyz, d_W, d_d, d_level, d_gains, d_grad_img);
   if (rc || !d_grad_W || !d_grad_g || !(wl > 0.0)) return BIPP_ERR_INVALID_ARG;
+  if (precision != BIPP_PREC_FP32 && precision != BIPP_PREC_SPLIT_BF16 && precision != BIPP_PREC_SPLIT_FP16)
+    return BIPP_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (precision != BIPP_PREC_FP32) {
+    (void)cudaGetLastError();
+    if (n_eig > 64 || n_level > 4) return BIPP_ERR_UNSUPPORTED;
+    return run_tc(n_pix, d_pix, wl, n_t, n_st, n_eig, n_level, d_st_xyz, d_W, d_d, d_level, d_gains,
+                  precision == BIPP_PREC_SPLIT_FP16, nullptr, d_grad_img, d_grad_W, d_grad_g, s);
+  }
   Scratch sc;
   cudaError_t e = prep(&sc, n_pix, d_pix, wl, n_t, n_st, n_eig, d_st_xyz, d_W, d_d, d_level, d_gains, s);
   int dev = 0, sms = 148;

@@ -20,8 +20,12 @@
 //              registers, accumulated over all steps and added to the FP64
 //              image once per tile.
 //   warp 16    allocates TMEM (two accumulator buffers) and issues, per
-//              16-wide K slice, three tcgen05.mma: A_hi*B_hi + A_hi*B_lo +
-//              A_lo*B_hi into the FP32 accumulator.
+//              16-wide K slice, the split products A_hi*B_hi + A_hi*B_lo +
+//              A_lo*B_hi into FP32 accumulators: with FUSE (2 K <= 128
+//              columns) as two tcgen05.mma, A_hi*[B_hi | B_lo] (N = 2 ncols:
+//              the hi and lo images of B lie side by side) and A_lo*B_hi into
+//              the first half, the halves summed in the epilogue; otherwise as
+//              three MMAs of N = ncols into one accumulator.
 //   warp 17    streams the pre-packed, pre-swizzled B chunks of the step with
 //              cp.async.bulk into the stage ring.
 // Stage handoff uses mbarriers; every wait is bounded (clock64 budget) and on
@@ -46,6 +50,7 @@
 #include <type_traits>
 
 #include "synth_tc.cuh"
+#include "tc_ptx.cuh"
 
 namespace bipp {
 
@@ -60,136 +65,8 @@ constexpr int kABytes = kRows * 128;  // one A operand image per stage (hi or lo
 constexpr int kMaxStages = 4;
 constexpr int kQWin = 16;  // chunks of station words staged per window (two windows in shared memory)
 static_assert((kQWin & (kQWin - 1)) == 0, "window of a power-of-two chunk count");
-constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
-// ---------------------------------------------------------------- PTX wrappers
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count));
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t a) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_tx(uint32_t a, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
-}
-// try_wait with a suspend-time hint (ns): a waiting warp sleeps in hardware
-// until the phase completes or the hint expires instead of spinning on issue
-// slots that the other producer warps need.
-__device__ __forceinline__ bool mbar_test(uint32_t a, uint32_t parity) {
-  uint32_t done;
-  asm volatile(
-      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\nselp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(done)
-      : "r"(a), "r"(parity), "r"(1000000u)
-      : "memory");
-  return done != 0;
-}
-// Bounded wait for the phase of the given parity; false on expiry or abort.
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag) {
-  if (mbar_test(a, parity)) return true;
-  const long long t0 = clock64();
-  for (;;) {
-    if (mbar_test(a, parity)) return true;
-    if (*abort_flag) return false;
-    if (clock64() - t0 > kWaitCycles) {
-      *abort_flag = 1;
-      return false;
-    }
-  }
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(bar)
-               : "memory");
-}
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// UMMA shared-memory descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (SBO), version 1, leading offset unused for this layout.
-__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
-  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
-__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-          d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-__device__ __forceinline__ void umma_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// hi/lo split of two values in [-1, 1] into packed 16-bit pairs (element 0
-// in the low half). hi is x rounded to a multiple of 2^-11 (FP16) or 2^-8
-// (BF16), by adding and subtracting 1.5 * 2^12 (2^15), whose FP32 ulp is that
-// step; such multiples in [-1, 1] are exact in the 16-bit type. lo = x - hi is
-// exact in FP32 and |lo| <= 2^-12 (2^-9), so its 16-bit rounding costs at most
-// 2^-24 (2^-17) absolute.
-template <bool FP16>
-__device__ __forceinline__ void split2(float x0, float x1, uint32_t* hi, uint32_t* lo) {
-  constexpr float M = FP16 ? 6144.0f : 49152.0f;
-  const float h0 = __fsub_rn(__fadd_rn(x0, M), M), h1 = __fsub_rn(__fadd_rn(x1, M), M);
-  const float l0 = __fsub_rn(x0, h0), l1 = __fsub_rn(x1, h1);
-  if constexpr (FP16) {
-    __half2 h = __floats2half2_rn(h0, h1);
-    __half2 l = __floats2half2_rn(l0, l1);
-    *hi = *reinterpret_cast<uint32_t*>(&h);
-    *lo = *reinterpret_cast<uint32_t*>(&l);
-  } else {
-    __nv_bfloat162 h = __floats2bfloat162_rn(h0, h1);
-    __nv_bfloat162 l = __floats2bfloat162_rn(l0, l1);
-    *hi = *reinterpret_cast<uint32_t*>(&h);
-    *lo = *reinterpret_cast<uint32_t*>(&l);
-  }
-}
-
-// 2 pi frac(<r, q>) in radians, in [-pi, pi), from the 32-bit words of the
-// fixed-point R (per pixel) and Q (per station); see the header comment.
-__device__ __forceinline__ float phase_rad_fixed(const uint32_t (&rl)[3], const uint32_t (&rh)[3], uint4 qa,
-                                                 uint2 qb) {
-  uint32_t acc = __umulhi(rl[0], qa.x) + rh[0] * qa.x + rl[0] * qa.y;
-  acc += __umulhi(rl[1], qa.z) + rh[1] * qa.z + rl[1] * qa.w;
-  acc += __umulhi(rl[2], qb.x) + rh[2] * qb.x + rl[2] * qb.y;
-  return (float)(int32_t)acc * 1.4629180792671596e-09f;  // 2 pi 2^-32
-}
-
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-__device__ __forceinline__ uint4 ld_shared_v4(uint32_t a) {
-  uint4 v;
-  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
-  return v;
-}
-__device__ __forceinline__ uint2 ld_shared_v2(uint32_t a) {
-  uint2 v;
-  asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a));
-  return v;
-}
-
-__device__ __forceinline__ void st_shared_v4(uint32_t a, const uint32_t (&w)[4]) {
-  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3])
-               : "memory");
-}
+using namespace tcx;
 
 template <int MAXL>
 __device__ __forceinline__ void level_add(float (&acc)[MAXL], int lev, float v) {
@@ -199,9 +76,14 @@ __device__ __forceinline__ void level_add(float (&acc)[MAXL], int lev, float v) 
 
 // ---------------------------------------------------------------- the fused kernel
 
-template <int MAXL, bool FP16>
+// EPI = 0: level images (above). EPI = 1: the adjoint's first stage: instead
+// of |z|^2, write Y_e(r) = d_e R_{l(e)}(r) z_e(r) (R = dL/dI, yo.R) for every
+// pixel, step and accumulator column into yo.Y as BF16 hi/lo images in the
+// K-major, 128-byte-swizzled layout of a UMMA B operand whose K runs over 64
+// pixels (see TcYOut); img is not touched.
+template <int MAXL, bool FP16, bool FUSE, int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_synth_tc(Batch b, Pixels px, int n_level, double* img, const TcStep* __restrict__ steps,
+    k_synth_tc(Batch b, Pixels px, int n_level, double* img, TcYOut yo, const TcStep* __restrict__ steps,
                const unsigned char* __restrict__ Bpack, const float* __restrict__ scales,
                const uint32_t* __restrict__ qfix, int qfix_stride, const int2* __restrict__ lwt, int n_stages,
                int stage_bytes, int ncols_buf, int* status) {
@@ -279,9 +161,66 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int K = b.nkept[t];
       const int2* lw = lwt + (size_t)t * kTcMaxEig;
       const uint32_t tbase = taddr + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(bb * ncols_buf);
+      if constexpr (EPI == 1) {
+        // Y = d R z: R of this pixel per level, z = accumulator / scale (the weights hold d / scale^2)
+        const int64_t r = (int64_t)tile * kRows + row;
+        const bool in = r < px.n;
+        float Rl[MAXL];
+#pragma unroll
+        for (int l = 0; l < MAXL; ++l) Rl[l] = (in && l < n_level) ? (float)yo.R[(size_t)l * px.n + r] : 0.0f;
+        const float sc = FP16 ? scales[t] : 1.0f;
+        const int64_t chunk = r >> 6;  // the tile's second chunk lies past the image when n_pix % 128 <= 64
+        const bool store = chunk < yo.nc64;
+        const int p64 = (int)(r & 63);
+        unsigned char* yb = yo.Y + ((size_t)t * yo.nc64 + (size_t)chunk) * (size_t)(2 * st.ncols * 128);
+        for (int cb = wg; cb < st.ncols / 16; cb += 4) {
+          float v[16];
+          tmem_ld16(tbase + cb * 16, v);  // every lane of the warp takes part (tcgen05.ld is warp-wide)
+          if constexpr (FUSE) {
+            float v2[16];
+            tmem_ld16(tbase + st.ncols + cb * 16, v2);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] += v2[i];
+          }
+#pragma unroll
+          for (int p = 0; p < 8; ++p) {
+            const int e = cb * 8 + p;
+            float f = 0.0f;
+            if (e < K) {
+              const int2 lv = lw[e];
+              float rv = 0.0f;
+#pragma unroll
+              for (int l = 0; l < MAXL; ++l) rv = (lv.x == l) ? Rl[l] : rv;
+              f = __int_as_float(lv.y) * sc * rv;
+            }
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+              const int n = cb * 16 + 2 * p + q;
+              const float y = f * v[2 * p + q];
+              const __nv_bfloat16 yh = __float2bfloat16_rn(y);
+              const __nv_bfloat16 yl = __float2bfloat16_rn(y - __bfloat162float(yh));
+              const size_t off = (size_t)n * 128 + (size_t)((((p64 >> 3) ^ (n & 7)) << 4) + (p64 & 7) * 2);
+              if (store) {
+                *reinterpret_cast<__nv_bfloat16*>(yb + off) = yh;
+                *reinterpret_cast<__nv_bfloat16*>(yb + (size_t)st.ncols * 128 + off) = yl;
+              }
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&bar_acce[bb]));
+        return true;
+      }
       for (int cb = wg; cb < st.ncols / 16; cb += 4) {
         float v[16];
         tmem_ld16(tbase + cb * 16, v);
+        if constexpr (FUSE) {  // the A_hi B_lo half of the accumulator
+          float v2[16];
+          tmem_ld16(tbase + st.ncols + cb * 16, v2);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[i] += v2[i];
+        }
 #pragma unroll
         for (int p = 0; p < 8; ++p) {
           const int e = cb * 8 + p;
@@ -447,9 +386,14 @@ __global__ void __launch_bounds__(kThreads, 1)
               const uint32_t ko = kk * 32;
               const uint64_t dah = umma_desc(a_hi + ko), dal = umma_desc(a_lo + ko);
               const uint64_t dbh = umma_desc(b_hi + ko), dbl = umma_desc(b_lo + ko);
-              umma_f16(d, dah, dbh, st.idesc, (c | kk) != 0);
-              umma_f16(d, dah, dbl, st.idesc, 1);
-              umma_f16(d, dal, dbh, st.idesc, 1);
+              if constexpr (FUSE) {
+                umma_f16(d, dah, dbh, st.idesc2, (c | kk) != 0);  // [A_hi B_hi | A_hi B_lo]
+                umma_f16(d, dal, dbh, st.idesc, 1);               // + A_lo B_hi in the first half
+              } else {
+                umma_f16(d, dah, dbh, st.idesc, (c | kk) != 0);
+                umma_f16(d, dah, dbl, st.idesc, 1);
+                umma_f16(d, dal, dbh, st.idesc, 1);
+              }
             }
             issued = true;
             umma_commit(smem_u32(&bar_empty[s]));
@@ -626,14 +570,18 @@ uint32_t make_idesc(int ncols, bool fp16) {
 }
 
 template <typename F>
-void dispatch(int n_level, bool fp16, F&& f) {
-  auto lv = [&](auto FPV) {
-    if (n_level <= 4) f(std::integral_constant<int, 4>{}, FPV);
-    else if (n_level <= 8) f(std::integral_constant<int, 8>{}, FPV);
-    else f(std::integral_constant<int, 16>{}, FPV);
+void dispatch(int n_level, bool fp16, bool fuse, F&& f) {
+  auto lv = [&](auto FPV, auto FU) {
+    if (n_level <= 4) f(std::integral_constant<int, 4>{}, FPV, FU);
+    else if (n_level <= 8) f(std::integral_constant<int, 8>{}, FPV, FU);
+    else f(std::integral_constant<int, 16>{}, FPV, FU);
   };
-  if (fp16) lv(std::true_type{});
-  else lv(std::false_type{});
+  auto fu = [&](auto FPV) {
+    if (fuse) lv(FPV, std::true_type{});
+    else lv(FPV, std::false_type{});
+  };
+  if (fp16) fu(std::true_type{});
+  else fu(std::false_type{});
 }
 
 }  // namespace
@@ -704,15 +652,16 @@ int launch_kernel(const Batch& b, const Pixels& px, int n_level, double* img, co
   const int n_tiles = (int)((px.n + kRows - 1) / kRows);
   const int grid = std::min(n_tiles, sms);
   int rc = 0;
-  dispatch(n_level, p.fp16, [&](auto L, auto FPV) {
+  dispatch(n_level, p.fp16, p.fused, [&](auto L, auto FPV, auto FU) {
     constexpr int ML = decltype(L)::value;
     constexpr bool F16 = decltype(FPV)::value;
-    if (cudaFuncSetAttribute(k_synth_tc<ML, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    constexpr bool FS = decltype(FU)::value;
+    if (cudaFuncSetAttribute(k_synth_tc<ML, F16, FS, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess) {
       rc = -7;
       return;
     }
-    k_synth_tc<ML, F16><<<grid, kThreads, smem, s>>>(b, px, n_level, img, w->steps, w->B, w->scale, w->qfix,
+    k_synth_tc<ML, F16, FS, 0><<<grid, kThreads, smem, s>>>(b, px, n_level, img, TcYOut{}, w->steps, w->B, w->scale, w->qfix,
                                                       w->qfix_stride, w->lwt, n_stages,
                                                      stage_bytes, p.ncols_buf, w->status);
   });
@@ -733,7 +682,7 @@ int tc_prepare(const std::vector<int>& nst, const std::vector<int>& neig, bool f
     st.n_chunks = n_chunks_for(nst[t]);
     st.ncols = ncols_for(neig[t]);
     st.idesc = make_idesc(st.ncols, fp16);
-    st.pad = 0;
+    st.idesc2 = make_idesc(std::min(2 * st.ncols, 256), fp16);
     off += (long long)st.n_chunks * st.ncols * 256;
     ncols_max = std::max(ncols_max, st.ncols);
     max_chunks = std::max(max_chunks, st.n_chunks);
@@ -742,8 +691,9 @@ int tc_prepare(const std::vector<int>& nst, const std::vector<int>& neig, bool f
   p->fp16 = fp16;
   p->ncols_max = ncols_max;
   p->max_chunks = max_chunks;
+  p->fused = 2 * ncols_max <= 256;  // N = 2 ncols <= 256 per MMA, two buffers of 2 ncols in 512 TMEM columns
   p->ncols_buf = 32;
-  while (p->ncols_buf < ncols_max) p->ncols_buf <<= 1;  // 2 * ncols_buf TMEM columns, a power of two <= 512
+  while (p->ncols_buf < (p->fused ? 2 * ncols_max : ncols_max)) p->ncols_buf <<= 1;  // a power of two <= 256
   const int smax = max_stages_for(ncols_max);
   if (smax < 2) return -6;
   std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -770,6 +720,36 @@ int tc_enqueue_pack(const Batch& b, const TcPlan& p, TcWorkspace* w, cudaStream_
 int tc_enqueue_synth(const Batch& b, const Pixels& px, int n_level, double* img, const TcPlan& p, TcWorkspace* w,
                      cudaStream_t s) {
   return launch_kernel(b, px, n_level, img, p, p.n_stages, w, s);
+}
+
+int tc_enqueue_yout(const Batch& b, const Pixels& px, int n_level, const TcPlan& p, TcWorkspace* w, TcYOut yo,
+                    cudaStream_t s) {
+  const int stage_bytes = stage_bytes_for(p.ncols_max);
+  const size_t smem = (size_t)p.n_stages * stage_bytes + kQStageBytes + 1024;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int n_tiles = (int)((px.n + kRows - 1) / kRows);
+  const int grid = std::min(n_tiles, sms);
+  int rc = 0;
+  dispatch(n_level, p.fp16, p.fused, [&](auto L, auto FPV, auto FU) {
+    constexpr int ML = decltype(L)::value;
+    constexpr bool F16 = decltype(FPV)::value;
+    constexpr bool FS = decltype(FU)::value;
+    if constexpr (ML != 4 || !FS) {  // the adjoint's Y stage is built for <= 4 levels and 2 n_eig <= 128 columns
+      rc = -10;
+    } else {
+      if (cudaFuncSetAttribute(k_synth_tc<ML, F16, FS, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess) {
+        rc = -7;
+        return;
+      }
+      k_synth_tc<ML, F16, FS, 1><<<grid, kThreads, smem, s>>>(b, px, n_level, nullptr, yo, w->steps, w->B, w->scale,
+                                                              w->qfix, w->qfix_stride, w->lwt, p.n_stages,
+                                                              stage_bytes, p.ncols_buf, w->status);
+    }
+  });
+  return rc;
 }
 
 int tc_autotune(const Batch& b, const Pixels& px, int n_level, int n_chan_sub, TcPlan* p, TcWorkspace* w,

@@ -14,13 +14,14 @@ constexpr int kTcMaxEig = 128;  // eigenvectors per step on the tensor-core path
 
 // Per-step geometry of the tensor-core GEMM: B operand chunks of 64 K-rows
 // (32 stations) packed at b_off, n_chunks of them, ncols = 2*K rounded up to
-// a multiple of 16, and the tcgen05 instruction descriptor.
+// a multiple of 16, and the tcgen05 instruction descriptors for N = ncols and
+// N = 2 ncols (the hi and lo images of B side by side).
 struct TcStep {
   long long b_off;
   int n_chunks;
   int ncols;
   uint32_t idesc;
-  int pad;
+  uint32_t idesc2;
 };
 
 // Device workspace of the tensor-core path.
@@ -37,12 +38,24 @@ struct TcWorkspace {
   int cap_T = 0;
 };
 
+// Output of the adjoint's first stage (k_synth_tc with EPI = 1): R = dL/dI
+// (n_level x n_pix FP64) in, Y out. Y holds, per step t and 64-pixel chunk c,
+// at ((t * nc64 + c) * 2 ncols) * 128 bytes, a BF16 hi image and then a lo
+// image of ncols rows of 128 bytes (64 pixels, 16-byte pieces XOR-swizzled by
+// row & 7): row n = accumulator column n (Re / Im of Y_e for n = 2e / 2e+1).
+struct TcYOut {
+  const double* R = nullptr;
+  unsigned char* Y = nullptr;
+  int nc64 = 0;  // 64-pixel chunks of the image, ceil(n_pix / 64)
+};
+
 // Launch geometry of one batch.
 struct TcPlan {
   bool fp16 = false;
   int ncols_max = 16;   // widest accumulator (2 * n_eig rounded to 16)
   int max_chunks = 1;   // most 32-station chunks of a step
   int ncols_buf = 32;   // TMEM columns per accumulator buffer (power of two)
+  bool fused = false;   // A_hi [B_hi | B_lo] as one MMA of N = 2 ncols (ncols_max <= 128)
   int n_stages = 2;     // shared-memory ring depth
   bool tuned = false;   // n_stages comes from the autotuner
 };
@@ -62,6 +75,19 @@ int tc_enqueue_pack(const Batch& b, const TcPlan& p, TcWorkspace* w, cudaStream_
 // Stream-ordered (graph-capturable): the fused synthesis kernel.
 int tc_enqueue_synth(const Batch& b, const Pixels& px, int n_level, double* img, const TcPlan& p, TcWorkspace* w,
                      cudaStream_t s);
+// Stream-ordered: the adjoint's first stage (z recomputed on the tensor
+// cores, Y = d R z written to yo.Y instead of level images); n_level <= 4 and
+// a fused plan (2 n_eig <= 128 accumulator columns) only, else nonzero.
+int tc_enqueue_yout(const Batch& b, const Pixels& px, int n_level, const TcPlan& p, TcWorkspace* w, TcYOut yo,
+                    cudaStream_t s);
+// The adjoint's pixel contraction on the tensor cores (adjoint_tc.cu):
+// grad_W' (n_t blocks of n_eig x n_st complex128, e-major) from Y and the
+// station words of the packed batch; part is scratch of
+// n_t * grid * 2 * n_st * ncols floats. n_eig <= 64. Stream-ordered.
+int launch_adjoint_tc(const Pixels& px, int T, int n_st, int K, int ncols, const uint32_t* qfix, int qfix_stride,
+                      const unsigned char* Y, int nc64, float* part, int grid, double2* gWp, int* status,
+                      cudaStream_t s);
+int adj_tc_smem_bytes(int ncols);
 // Not capturable (synchronises): time each feasible stage count on a subset
 // of the packed batch into a scratch image, keep the fastest in p and in a
 // process-wide cache keyed by (ncols_max, operand type).
