@@ -88,7 +88,7 @@ void launch_jacobi(const Batch& b, double tol, int max_sweeps, cudaStream_t s);
 // FP64-class refinement); needs the X and Q buffers of the batch as scratch,
 // which fits when eig_mixed_fits(n_max, KP).
 bool eig_mixed_fits(int n_max, int KP);
-constexpr int kMixedLaunches = 68;  // kernels launched by launch_eig_mixed
+constexpr int kMixedLaunches = 70;  // kernels launched by launch_eig_mixed
 void launch_eig_mixed(const Batch& b, const MixedWs& w, double tol, int max_sweeps, cudaStream_t s);
 // Error message of calls without a handle (returned by bipp_ss_last_error(NULL)).
 int set_global_error(int code, const char* msg);

@@ -20,9 +20,9 @@
 //      the correction runs in FP32, as it carries no more accuracy than the
 //      FP32 decomposition, while the residual it corrects is formed in FP64;
 //      each pass contracts the error by the FP32 stage's relative accuracy over
-//      the spectral gap (about 3e-5 per pass here); a problem whose kept
-//      residuals fall below 10 * jacobi_tol * ||C||_F stops early, the rest run
-//      at most kPasses passes.
+//      the spectral gap (about 5e-6 per pass here); a problem whose kept
+//      residuals fall below 100 * jacobi_tol * ||C||_F stops early (after one
+//      correction, typically), the rest run at most kPasses passes.
 //   3. theta and X replace the Jacobi eigenvalues and eigenvectors; the
 //      residual of the last pass is checked against 1e3 * jacobi_tol * ||C||_F.
 // FP64-class cost per pass is O(n^2 kp) (one n x n by n x kp product) instead
@@ -43,9 +43,9 @@ namespace {
 
 constexpr int kPad = 16;       // extra leading pairs refined beyond n_eig
 constexpr int kPasses = 4;     // refinement passes at most
-constexpr int kMxDone = 8;     // st2 bit: residual met the early-exit bound, later passes skip the step
+constexpr int kMxDone = kMxDoneBit;  // st2 bit: residual met the early-exit bound, later passes skip the step
 constexpr int GT = 32, GK = 16;
-static_assert(7 + 17 * (kPasses - 1) + 10 == kMixedLaunches, "launch count of the mixed eigensolver");
+static_assert(7 + 2 + 17 * (kPasses - 1) + 10 == kMixedLaunches, "launch count of the mixed eigensolver");
 
 // Shape codes of the batched complex products: dimension = n_st or kp of the problem.
 enum Dim { DN = 0, DKP = 1 };
@@ -261,6 +261,22 @@ __global__ void k_mx_herm(Batch b, MixedWs w, double2* H0, size_t stride, int ld
   }
 }
 
+// TO32: H32 = fp32(H) (kp x kp, ld KP); else U = fp64(U32). The FP32 views
+// lie 2 N^2 float2 apart per problem, the FP64 blocks N^2 double2 apart.
+template <bool TO32>
+__global__ void k_mx_cvt(Batch b, MixedWs w, double2* D0, float2* F0, size_t stride, int ld) {
+  const int t = blockIdx.x;
+  if (mx_skip(b.status, w.st2, t)) return;
+  const int kp = w.kp[t];
+  double2* D = D0 + (size_t)t * stride;
+  float2* F = F0 + (size_t)t * 2 * stride;
+  for (int e = threadIdx.x; e < kp * kp; e += blockDim.x) {
+    const size_t o = (size_t)(e % kp) + (size_t)(e / kp) * ld;
+    if (TO32) F[o] = make_float2((float)D[o].x, (float)D[o].y);
+    else D[o] = make_double2((double)F[o].x, (double)F[o].y);
+  }
+}
+
 // R = Y - X diag(theta) in place of Y; rnorm[j] = ||R[:, j]||.
 __global__ void k_mx_resid(Batch b, MixedWs w, const double2* X0, double2* Y0, float2* R32, size_t stride) {
   const int t = blockIdx.y, j = blockIdx.x;
@@ -304,42 +320,50 @@ __global__ void k_mx_sub(Batch b, MixedWs w, double2* X0, const float2* D0, size
   }
 }
 
-// Hand theta / X to the selection stage (which ranks b.mu and reads the
-// columns of b.Q): mu[j] = theta[j] for j < kp, -inf beyond; check the last
-// residuals of the n_eig leading pairs.
 // Largest residual norm among the pairs that can be kept (the n_eig largest
-// theta of problem t).
-__device__ double mx_worst_kept(const Batch& b, const MixedWs& w, int t) {
+// theta of problem t), over the whole block (every thread gets it).
+__device__ double mx_worst_kept(const Batch& b, const MixedWs& w, int t, double* red) {
   const int kp = w.kp[t], K = b.neig[t];
+  const double* th = w.theta + (size_t)t * w.KP;
   double worst = 0.0;
-  for (int j = 0; j < kp; ++j) {
+  for (int j = threadIdx.x; j < kp; j += blockDim.x) {
+    const double tj = th[j];
     int rank = 0;
-    const double tj = w.theta[(size_t)t * w.KP + j];
-    for (int i = 0; i < kp; ++i) {
-      const double ti = w.theta[(size_t)t * w.KP + i];
-      rank += (ti > tj) || (ti == tj && i < j);
-    }
+    for (int i = 0; i < kp; ++i) rank += (th[i] > tj) || (th[i] == tj && i < j);
     if (rank < K) worst = fmax(worst, w.rnorm[(size_t)t * w.KP + j]);
   }
-  return worst;
+  red[threadIdx.x] = worst;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
 }
 // Early exit: a problem whose kept residuals are already below rtol ||C||_F
 // skips the remaining passes (its X, theta and residuals stay as they are).
+// One block of 128 threads per problem.
 __global__ void k_mx_check(Batch b, MixedWs w, double rtol) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= b.T || mx_skip(b.status, w.st2, t)) return;
-  if (mx_worst_kept(b, w, t) <= rtol * w.cnorm[t]) w.st2[t] |= kMxDone;
+  const int t = blockIdx.x;
+  if (mx_skip(b.status, w.st2, t)) return;
+  __shared__ double red[128];
+  const double worst = mx_worst_kept(b, w, t, red);
+  if (threadIdx.x == 0 && worst <= rtol * w.cnorm[t]) w.st2[t] |= kMxDone;
 }
+// Hand theta / X to the selection stage (which ranks b.mu and reads the
+// columns of b.Q): mu[j] = theta[j] for j < kp, -inf beyond; check the last
+// residuals of the n_eig leading pairs. One block of 128 threads per problem.
 __global__ void k_mx_final(Batch b, MixedWs w, double rtol) {
   const int t = blockIdx.x;
   if (b.status[t]) return;
   const int n = b.nst[t], N = b.n_max, kp = w.kp[t];
   double* mu = b.mu + (size_t)t * N;
   for (int j = threadIdx.x; j < n; j += blockDim.x) mu[j] = (j < kp) ? w.theta[(size_t)t * w.KP + j] : -INFINITY;
-  if (threadIdx.x == 0) {
-    const double worst = mx_worst_kept(b, w, t);
-    if (!(worst <= rtol * w.cnorm[t]) || (w.st2[t] & ~kMxDone)) b.status[t] |= kStatusNotConverged;
-  }
+  __shared__ double red[128];
+  const double worst = mx_worst_kept(b, w, t, red);
+  if (threadIdx.x == 0 && (!(worst <= rtol * w.cnorm[t]) || (w.st2[t] & ~kMxDone))) b.status[t] |= kStatusNotConverged;
 }
 
 template <bool CT>
@@ -370,6 +394,7 @@ void launch_eig_mixed(const Batch& b, const MixedWs& w, double tol, int max_swee
   //    refinement takes over afterwards.
   float* Xf = reinterpret_cast<float*>(b.X);
   const size_t xs = 4 * NN;  // floats per problem in the X and Q buffers
+  cudaMemsetAsync(w.st2, 0, sizeof(int) * T, s);
   k_mx_tof32<<<dim3(std::max(1, std::min(64, (N * N + 255) / 256)), T), 256, 0, s>>>(b);
   TridiagArgs a;
   a.C = reinterpret_cast<float2*>(Xf);
@@ -394,6 +419,7 @@ void launch_eig_mixed(const Batch& b, const MixedWs& w, double tol, int max_swee
   sa.kp = w.kp;
   sa.pad = kPad;
   sa.status = b.status;
+  sa.done = nullptr;
   sa.ld = N;
   sa.stride = 2 * NN;
   const int sm2 = 2 * N * (int)sizeof(float);
@@ -422,7 +448,15 @@ void launch_eig_mixed(const Batch& b, const MixedWs& w, double tol, int max_swee
   h.ld = KP;
   h.stride = NN;
   h.report_nonconv = 1;
-  cudaMemsetAsync(w.st2, 0, sizeof(int) * T, s);
+  // pass 0 diagonalises H in FP32: its eigenvectors need only the FP32 stage's accuracy
+  // (the correction that follows is FP32); H and U in FP32 in the R^{-1} block, free by then
+  JacobiArgs h32 = h;
+  h32.C = reinterpret_cast<float2*>(Ws);
+  h32.Q = reinterpret_cast<float2*>(Ws) + (size_t)KP * KP;
+  h32.stride = 2 * NN;
+  h32.report_nonconv = 0;
+  SelArgs sr = sa;  // the refinement's corrections skip converged problems
+  sr.done = w.st2;
   const int ew = std::max(1, (N * KP + 255) / 256 / 8);  // blocks per problem of the elementwise kernels
   const int ci_smem = (int)(sizeof(double2) * ((size_t)KP * KP + KP));
   cudaFuncSetAttribute(k_mx_cholinv, cudaFuncAttributeMaxDynamicSharedMemorySize, ci_smem);
@@ -434,21 +468,27 @@ void launch_eig_mixed(const Batch& b, const MixedWs& w, double tol, int max_swee
     zgemm_df<false>(b, w, DN, DKP, DN, N, KP, b.C, NN, N, P1, NN, N, P2, NN, N, s);   // Y = C X1
     zgemm_df<true>(b, w, DKP, DKP, DN, KP, KP, P1, NN, N, P2, NN, N, Hs, NN, KP, s);  // H = X1^H Y
     k_mx_herm<<<T, 256, 0, s>>>(b, w, Hs, NN, KP);
-    launch_jacobi_small(h, T, KP, 1e-14, 60, s);                                                  // H = U th U^H
+    if (pass == 0) {                                                                              // H = U th U^H
+      k_mx_cvt<true><<<T, 256, 0, s>>>(b, w, Hs, reinterpret_cast<float2*>(Ws), NN, KP);
+      launch_jacobi_small_f32(h32, T, KP, 1e-6, 30, s);
+      k_mx_cvt<false><<<T, 256, 0, s>>>(b, w, Us, reinterpret_cast<float2*>(Ws) + (size_t)KP * KP, NN, KP);
+    } else {
+      launch_jacobi_small(h, T, KP, 1e-14, 60, s);
+    }
     zgemm_df<false>(b, w, DN, DKP, DKP, N, KP, P1, NN, N, Us, NN, KP, P0, NN, N, s);  // X = X1 U
     zgemm_df<false>(b, w, DN, DKP, DKP, N, KP, P2, NN, N, Us, NN, KP, P3, NN, N, s);  // Y U
     k_mx_resid<<<dim3(KP, T), 256, 0, s>>>(b, w, P0, P3, R32, NN);                                // R = YU - X th
     if (pass == kPasses - 1) break;
-    k_mx_check<<<(T + 127) / 128, 128, 0, s>>>(b, w, 10.0 * tol);
+    k_mx_check<<<T, 128, 0, s>>>(b, w, 1e2 * tol);
     // correction in FP32: H P (T - theta_j)^{-1} P H^H r_j, P = I - Z_k Z_k^T
-    launch_td_apply<true, false>(sa, R32, NN2, KP, T, s);                                   // S = H^H R
-    k_td_deflate<<<dim3(KP, T), 256, KP * sizeof(float2), s>>>(sa, R32, NN2);
-    k_td_shiftsolve<<<dim3((KP + 31) / 32, T), 32, sm2, s>>>(sa, R32, NN2, w.theta, w.KP, lu3, xs, KP);
-    k_td_deflate<<<dim3(KP, T), 256, KP * sizeof(float2), s>>>(sa, R32, NN2);
-    launch_td_apply<false, false>(sa, R32, NN2, KP, T, s);                                  // D = H U
+    launch_td_apply<true, false>(sr, R32, NN2, KP, T, s);                                   // S = H^H R
+    k_td_deflate<<<dim3(KP, T), 256, KP * sizeof(float2), s>>>(sr, R32, NN2);
+    k_td_shiftsolve<<<dim3((KP + 31) / 32, T), 32, sm2, s>>>(sr, R32, NN2, w.theta, w.KP, lu3, xs, KP);
+    k_td_deflate<<<dim3(KP, T), 256, KP * sizeof(float2), s>>>(sr, R32, NN2);
+    launch_td_apply<false, false>(sr, R32, NN2, KP, T, s);                                  // D = H U
     k_mx_sub<<<dim3(ew, T), 256, 0, s>>>(b, w, P0, R32, NN, NN2);                                 // X -= D
   }
-  k_mx_final<<<T, 256, 0, s>>>(b, w, 1e3 * tol);
+  k_mx_final<<<T, 128, 0, s>>>(b, w, 1e3 * tol);
   (void)max_sweeps;
 }
 

@@ -284,4 +284,16 @@ inline void launch_jacobi_small(const JacobiArgs& a, int T, int n_max, double to
   }
 }
 
+// The same in FP32 (float2 C and Q, FP64 eigenvalues out).
+inline void launch_jacobi_small_f32(const JacobiArgs& a, int T, int n_max, double tol, int max_sweeps,
+                                    cudaStream_t s) {
+  const size_t smem = sizeof(float2) * (size_t)n_max * n_max;
+  if (smem <= 160 * 1024) {
+    cudaFuncSetAttribute(k_jacobi_t<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_jacobi_t<float, true><<<T, kJacobiThreads, smem, s>>>(a, tol, max_sweeps);
+  } else {
+    k_jacobi_t<float><<<T, kJacobiThreads, 0, s>>>(a, tol, max_sweeps);
+  }
+}
+
 }  // namespace bipp

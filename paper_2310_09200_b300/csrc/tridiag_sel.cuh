@@ -51,11 +51,18 @@ struct SelArgs {
   int* kp;             // [T] min(n, neig + pad), written by k_td_topeig
   int pad;
   const int* status;   // [T] problems with a status bit are skipped
+  const int* done;     // [T] or nullptr: refinement status (the refinement kernels also skip problems with the
+                       //     early-exit bit kMxDoneBit or any error bit set)
   int ld;              // leading dimension N
   size_t stride;       // float2 elements between the problems' reflector blocks
 };
 
+constexpr int kMxDoneBit = 8;  // refinement status bit: kept residuals met the early-exit bound
+
 namespace sel {
+
+// The problem takes no part: an error status, or (in the refinement) done.
+__device__ __forceinline__ bool skip(const SelArgs& a, int t) { return a.status[t] || (a.done && a.done[t]); }
 
 // Eigenvalues of T below x (Sturm count of the LDL^T factorisation of T - x I).
 __device__ __forceinline__ int sturm_count(int n, const float* d, const float* e2, float x, float pivmin) {
@@ -288,15 +295,16 @@ __global__ void __launch_bounds__(kInvitThreads) k_td_invit(SelArgs a, float* lu
 // ---- apply H (ADJ = false: Q <- H Q, reflectors n-2 .. 0) or H^H (ADJ = true:
 // Q <- H^H Q, reflectors 0 .. n-2 with conj(tau)) to the first ncol[t]
 // columns of a complex n x ncol block in place, reflectors staged RB at a time
-// in shared memory, each column in a warp's registers (lane l holds rows l,
-// l + 32, ...). FROM_Z: the block starts as the real columns of Z (k_td_apply
-// then is the back-transformation q_j = H z_j). Grid (column groups, T);
-// dynamic shared memory: ld x (RB + 1) float2.
-template <int RB, int RPL, bool ADJ, bool FROM_Z>
+// in shared memory, CPW columns in each warp's registers (lane l holds rows
+// l, l + 32, ... of each), so that the CPW dot products of a reflector and
+// their shuffle reductions overlap. FROM_Z: the block starts as the real
+// columns of Z (k_td_apply then is the back-transformation q_j = H z_j).
+// Grid (column groups of 16 CPW, T); dynamic shared memory: ld x (RB + 1) float2.
+template <int RB, int RPL, bool ADJ, bool FROM_Z, int CPW>
 __global__ void __launch_bounds__(kTdThreads, 1) k_td_apply(SelArgs a, float2* Q0, size_t qstride, int cols_per_cta) {
   using namespace td;
   const int t = blockIdx.y;
-  if (a.status[t]) return;
+  if (sel::skip(a, t)) return;
   const int n = a.n[t], N = a.ld, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int c0 = blockIdx.x * cols_per_cta;
   const int ncol = a.kp[t];
@@ -317,6 +325,7 @@ __global__ void __launch_bounds__(kTdThreads, 1) k_td_apply(SelArgs a, float2* Q
   }
   const int nref = n - 1;  // reflectors 0 .. n-2
   const int nblk = (nref + RB - 1) / RB;
+  const int cw = c0 + wid * CPW;  // this warp's first column
   for (int bi = 0; bi < nblk; ++bi) {
     const int k0 = ADJ ? bi * RB : (nblk - 1 - bi) * RB;
     const int nb = min(RB, nref - k0), mb = n - k0 - 1;  // reflectors k0..k0+nb-1 act on rows k0+1..n-1
@@ -333,47 +342,69 @@ __global__ void __launch_bounds__(kTdThreads, 1) k_td_apply(SelArgs a, float2* Q
       stau[tid] = ADJ ? make_float2(tk.x, -tk.y) : tk;
     }
     __syncthreads();
-    for (int c = c0 + wid; c < c1; c += kTdThreads / 32) {
-      float2* Qc = Q + (size_t)(k0 + 1) + (size_t)c * N;
-      float2 q[RPL];
+    if (cw >= c1) continue;
+    float2 q[CPW][RPL];
+#pragma unroll
+    for (int k = 0; k < CPW; ++k) {
+      const int c = min(cw + k, c1 - 1);  // a missing column repeats the last one, not stored
+      const float2* Qc = Q + (size_t)(k0 + 1) + (size_t)c * N;
 #pragma unroll
       for (int i = 0; i < RPL; ++i) {
         const int r = lane + 32 * i;
-        q[i] = (r < mb) ? Qc[r] : make_float2(0.f, 0.f);
+        q[k][i] = (r < mb) ? Qc[r] : make_float2(0.f, 0.f);
       }
-      for (int jj = 0; jj < nb; ++jj) {
-        const int j = ADJ ? jj : nb - 1 - jj;
-        const float2 tj = stau[j];
-        float2 u = make_float2(0.f, 0.f);  // v^H q
+    }
+    for (int jj = 0; jj < nb; ++jj) {
+      const int j = ADJ ? jj : nb - 1 - jj;
+      const float2 tj = stau[j];
+      float2 u[CPW];  // v^H q per column
 #pragma unroll
-        for (int i = 0; i < RPL; ++i) {
-          const int r = lane + 32 * i;
-          if (r < mb) {
-            const float2 vr = V[(size_t)r * (RB + 1) + j];
-            u.x += vr.x * q[i].x + vr.y * q[i].y;
-            u.y += vr.x * q[i].y - vr.y * q[i].x;
-          }
-        }
+      for (int k = 0; k < CPW; ++k) u[k] = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          u.x += __shfl_xor_sync(0xffffffffu, u.x, o);
-          u.y += __shfl_xor_sync(0xffffffffu, u.y, o);
-        }
-        const float2 tu = cmul(tj, u);
+      for (int i = 0; i < RPL; ++i) {
+        const int r = lane + 32 * i;
+        if (r < mb) {
+          const float2 vr = V[(size_t)r * (RB + 1) + j];
 #pragma unroll
-        for (int i = 0; i < RPL; ++i) {
-          const int r = lane + 32 * i;
-          if (r < mb) {
-            const float2 y = cmul(V[(size_t)r * (RB + 1) + j], tu);
-            q[i].x -= y.x;
-            q[i].y -= y.y;
+          for (int k = 0; k < CPW; ++k) {
+            u[k].x += vr.x * q[k][i].x + vr.y * q[k][i].y;
+            u[k].y += vr.x * q[k][i].y - vr.y * q[k][i].x;
           }
         }
       }
 #pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < CPW; ++k) {
+          u[k].x += __shfl_xor_sync(0xffffffffu, u[k].x, o);
+          u[k].y += __shfl_xor_sync(0xffffffffu, u[k].y, o);
+        }
+      }
+      float2 tu[CPW];
+#pragma unroll
+      for (int k = 0; k < CPW; ++k) tu[k] = cmul(tj, u[k]);
+#pragma unroll
       for (int i = 0; i < RPL; ++i) {
         const int r = lane + 32 * i;
-        if (r < mb) Qc[r] = q[i];
+        if (r < mb) {
+          const float2 vr = V[(size_t)r * (RB + 1) + j];
+#pragma unroll
+          for (int k = 0; k < CPW; ++k) {
+            const float2 y = cmul(vr, tu[k]);
+            q[k][i].x -= y.x;
+            q[k][i].y -= y.y;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < CPW; ++k) {
+      if (cw + k >= c1) continue;
+      float2* Qc = Q + (size_t)(k0 + 1) + (size_t)(cw + k) * N;
+#pragma unroll
+      for (int i = 0; i < RPL; ++i) {
+        const int r = lane + 32 * i;
+        if (r < mb) Qc[r] = q[k][i];
       }
     }
   }
@@ -384,7 +415,7 @@ __global__ void __launch_bounds__(kTdThreads, 1) k_td_apply(SelArgs a, float2* Q
 // dynamic shared memory: kp_max float2.
 __global__ void __launch_bounds__(256) k_td_deflate(SelArgs a, float2* S0, size_t qstride) {
   const int t = blockIdx.y, j = blockIdx.x;
-  if (a.status[t]) return;
+  if (sel::skip(a, t)) return;
   const int n = a.n[t], N = a.ld, kp = a.kp[t];
   if (j >= kp) return;
   const float* Z = a.Z + (size_t)t * a.sstride;
@@ -427,7 +458,7 @@ __global__ void __launch_bounds__(256) k_td_deflate(SelArgs a, float2* S0, size_
 __global__ void __launch_bounds__(32) k_td_shiftsolve(SelArgs a, float2* S0, size_t qstride, const double* theta,
                                                     int theta_ld, float* lu0, size_t lu_stride, int lu_ld) {
   const int t = blockIdx.y;
-  if (a.status[t]) return;
+  if (sel::skip(a, t)) return;
   const int n = a.n[t], N = a.ld, kp = a.kp[t];
   const int j = blockIdx.x * 32 + threadIdx.x;
   const float* dg = a.tds + (size_t)t * a.sstride + td_off_d(N);
@@ -491,17 +522,19 @@ __global__ void __launch_bounds__(32) k_td_shiftsolve(SelArgs a, float2* S0, siz
 
 template <bool ADJ, bool FROM_Z>
 inline void launch_td_apply(const SelArgs& a, float2* Q, size_t qstride, int KP, int T, cudaStream_t s) {
-  constexpr int kCols = kTdThreads / 32;  // one column per warp
   const int N = a.ld;
-  const dim3 grd((KP + kCols - 1) / kCols, T);
   if (N <= 512) {
+    constexpr int kCpw = 2, kCols = kTdThreads / 32 * kCpw;
+    const dim3 grd((KP + kCols - 1) / kCols, T);
     const int smb = N * (32 + 1) * (int)sizeof(float2);
-    cudaFuncSetAttribute(k_td_apply<32, 16, ADJ, FROM_Z>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
-    k_td_apply<32, 16, ADJ, FROM_Z><<<grd, kTdThreads, smb, s>>>(a, Q, qstride, kCols);
+    cudaFuncSetAttribute(k_td_apply<32, 16, ADJ, FROM_Z, kCpw>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
+    k_td_apply<32, 16, ADJ, FROM_Z, kCpw><<<grd, kTdThreads, smb, s>>>(a, Q, qstride, kCols);
   } else {
+    constexpr int kCols = kTdThreads / 32;
+    const dim3 grd((KP + kCols - 1) / kCols, T);
     const int smb = N * (16 + 1) * (int)sizeof(float2);
-    cudaFuncSetAttribute(k_td_apply<16, 32, ADJ, FROM_Z>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
-    k_td_apply<16, 32, ADJ, FROM_Z><<<grd, kTdThreads, smb, s>>>(a, Q, qstride, kCols);
+    cudaFuncSetAttribute(k_td_apply<16, 32, ADJ, FROM_Z, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
+    k_td_apply<16, 32, ADJ, FROM_Z, 1><<<grd, kTdThreads, smb, s>>>(a, Q, qstride, kCols);
   }
 }
 
