@@ -219,20 +219,34 @@ __global__ void k_adj_reduce(const float2* part, int T, int n_cta, int N, int K,
 }
 
 // grad_W = g * grad_W' (in place), grad_g[i] = sum_t sum_e conj(grad_W'_t[i,e]) W_t[i,e].
-__global__ void k_adj_finish(int T, int N, int K, const double2* W, const double2* g, double2* gW, double2* gg) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const double2 gi = g[i];
+// Block of 256 threads = 32 stations x 8 slices of the (t, e) pairs; the 8
+// partial sums of a station are added in a fixed order (deterministic).
+__global__ void __launch_bounds__(256) k_adj_finish(int T, int N, int K, const double2* W, const double2* g,
+                                                    double2* gW, double2* gg) {
+  const int li = threadIdx.x & 31, sl = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + li;
+  __shared__ double2 part[8][32];
   double sr = 0.0, si = 0.0;
-  for (int t = 0; t < T; ++t)
-    for (int e = 0; e < K; ++e) {
-      const size_t o = ((size_t)t * K + e) * N + i;
+  if (i < N) {
+    const double2 gi = g[i];
+    for (int te = sl; te < T * K; te += 8) {
+      const size_t o = (size_t)te * N + i;
       const double2 p = gW[o], w = W[o];
       sr += p.x * w.x + p.y * w.y;  // conj(p) * w
       si += p.x * w.y - p.y * w.x;
       gW[o] = make_double2(gi.x * p.x - gi.y * p.y, gi.x * p.y + gi.y * p.x);
     }
-  gg[i] = make_double2(sr, si);
+  }
+  part[sl][li] = make_double2(sr, si);
+  __syncthreads();
+  if (sl == 0 && i < N) {
+    double2 a = part[0][li];
+    for (int k = 1; k < 8; ++k) {
+      a.x += part[k][li].x;
+      a.y += part[k][li].y;
+    }
+    gg[i] = a;
+  }
 }
 
 struct Scratch {
@@ -315,27 +329,55 @@ __global__ void k_adj_prep_tc(Batch b, const double2* W, const double* d, const 
   }
 }
 
-// One tensor-core workspace per device, grown on demand; a call holds the
-// device's lock from packing to its final synchronisation.
+// One tensor-core workspace per device, and its scratch buffers (the batch
+// view of W', the adjoint's Y images and per-CTA partials), grown on demand and
+// kept: a call holds the device's lock from packing to its final
+// synchronisation.
 constexpr int kTcDevs = 64;
 std::mutex g_tc_mu[kTcDevs];
 TcWorkspace g_tc_ws[kTcDevs];
 int g_tc_cap[kTcDevs][3];
+struct DevBuf {
+  void* p = nullptr;
+  size_t n = 0;
+};
+DevBuf g_tc_buf[kTcDevs][3];
+
+// Buffer `slot` of the device, at least `bytes` long; the caller holds g_tc_mu[dev].
+void* tc_buf(int dev, int slot, size_t bytes) {
+  DevBuf& b = g_tc_buf[dev][slot];
+  if (b.p && b.n >= bytes) return b.p;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.n = 0;
+  if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+    (void)cudaGetLastError();
+    b.p = nullptr;
+    return nullptr;
+  }
+  b.n = bytes;
+  return b.p;
+}
 
 struct TcScratch {
   Batch b{};
   void* base = nullptr;
 };
 
-cudaError_t prep_tc(TcScratch* s, int T, int N, int K, const double* d_st, const double* d_W, const double* d_d,
-                    const int32_t* d_level, const double* d_g, double wl, cudaStream_t st) {
-  auto rnd = [](size_t n) { return (n + 255) & ~size_t(255); };
-  const size_t bytes = rnd(sizeof(double2) * (size_t)T * N * K) + rnd(sizeof(double) * (size_t)T * K) +
-                       rnd(sizeof(int) * (size_t)T * K) + 2 * rnd(sizeof(int) * (size_t)T) +
-                       rnd(sizeof(double) * (size_t)T) + rnd(sizeof(int));
-  cudaError_t e = cudaMallocAsync(&s->base, bytes, st);
-  if (e != cudaSuccess) return e;
-  unsigned char* p = static_cast<unsigned char*>(s->base);
+size_t rnd256(size_t n) { return (n + 255) & ~size_t(255); }
+size_t prep_tc_bytes(int T, int N, int K) {
+  return rnd256(sizeof(double2) * (size_t)T * N * K) + rnd256(sizeof(double) * (size_t)T * K) +
+         rnd256(sizeof(int) * (size_t)T * K) + 2 * rnd256(sizeof(int) * (size_t)T) + rnd256(sizeof(double) * (size_t)T) +
+         rnd256(sizeof(int));
+}
+
+// base: prep_tc_bytes(T, N, K) bytes of device scratch.
+cudaError_t prep_tc(TcScratch* s, void* base, int T, int N, int K, const double* d_st, const double* d_W,
+                    const double* d_d, const int32_t* d_level, const double* d_g, double wl, cudaStream_t st) {
+  auto rnd = rnd256;
+  cudaError_t e = cudaSuccess;
+  s->base = base;
+  unsigned char* p = static_cast<unsigned char*>(base);
   auto take = [&](size_t n) {
     unsigned char* r = p;
     p += rnd(n);
@@ -402,7 +444,9 @@ int run_tc(int64_t n_pix, const double* d_pix, double wl, int T, int N, int K, i
   unsigned char* Y = nullptr;
   float* part = nullptr;
   int rc = BIPP_OK;
-  cudaError_t e = prep_tc(&sc, T, N, K, d_st, d_W, d_d, d_level, d_g, wl, s);
+  void* pbase = tc_buf(dev, 0, prep_tc_bytes(T, N, K));
+  if (!pbase) return BIPP_ERR_OUT_OF_MEMORY;
+  cudaError_t e = prep_tc(&sc, pbase, T, N, K, d_st, d_W, d_d, d_level, d_g, wl, s);
   TcPlan plan;
   if (e == cudaSuccess) {
     const std::vector<int> nst(T, N), neig(T, K);
@@ -418,8 +462,9 @@ int run_tc(int64_t n_pix, const double* d_pix, double wl, int T, int N, int K, i
       const int nc64 = (int)((n_pix + 63) / 64);
       const int ncols = plan.ncols_max;
       const int grid = std::max(1, std::min(nc64, sms));
-      e = cudaMallocAsync(&Y, (size_t)T * nc64 * 2 * ncols * 128, s);
-      if (e == cudaSuccess) e = cudaMallocAsync(&part, sizeof(float) * (size_t)T * grid * 2 * N * ncols, s);
+      Y = static_cast<unsigned char*>(tc_buf(dev, 1, (size_t)T * nc64 * 2 * ncols * 128));
+      part = static_cast<float*>(tc_buf(dev, 2, sizeof(float) * (size_t)T * grid * 2 * N * ncols));
+      if (!Y || !part) e = cudaErrorMemoryAllocation;
       if (e == cudaSuccess) {
         TcYOut yo;
         yo.R = R;
@@ -432,16 +477,13 @@ int run_tc(int64_t n_pix, const double* d_pix, double wl, int T, int N, int K, i
                             reinterpret_cast<double2*>(gW), w->status, s))
         e = cudaErrorLaunchFailure;
       if (e == cudaSuccess && rc == BIPP_OK) {
-        k_adj_finish<<<(N + 127) / 128, 128, 0, s>>>(T, N, K, reinterpret_cast<const double2*>(d_W),
+        k_adj_finish<<<(N + 31) / 32, 256, 0, s>>>(T, N, K, reinterpret_cast<const double2*>(d_W),
                                                      reinterpret_cast<const double2*>(d_g),
                                                      reinterpret_cast<double2*>(gW), reinterpret_cast<double2*>(gg));
         e = cudaGetLastError();
       }
     }
   }
-  if (part) cudaFreeAsync(part, s);
-  if (Y) cudaFreeAsync(Y, s);
-  if (sc.base) cudaFreeAsync(sc.base, s);
   const cudaError_t es = cudaStreamSynchronize(s);
   if (e == cudaSuccess) e = es;
   if (rc == BIPP_OK) rc = err_of(e);
@@ -521,7 +563,7 @@ extern "C" int bipp_ss_synth_adjoint_device(int64_t n_pix, const double* d_pix, 
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) {
-    k_adj_finish<<<(n_st + 127) / 128, 128, 0, s>>>(n_t, n_st, n_eig, reinterpret_cast<const double2*>(d_W),
+    k_adj_finish<<<(n_st + 31) / 32, 256, 0, s>>>(n_t, n_st, n_eig, reinterpret_cast<const double2*>(d_W),
                                                      reinterpret_cast<const double2*>(d_gains),
                                                      reinterpret_cast<double2*>(d_grad_W),
                                                      reinterpret_cast<double2*>(d_grad_g));

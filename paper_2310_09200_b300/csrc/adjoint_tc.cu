@@ -11,18 +11,18 @@
 //     P_c[i, n] = sum_r cos th_ri Y_n(r),  P_s[i, n] = sum_r sin th_ri Y_n(r),
 //     grad_W'[i, e] = 2 ((P_c[i, 2e] - P_s[i, 2e+1]) + j (P_c[i, 2e+1] + P_s[i, 2e])).
 //
-// k_adjoint_tc: one persistent CTA per SM, 10 warps. Per (step t, pass over
+// k_adjoint_tc: one persistent CTA per SM, 18 warps. Per (step t, pass over
 // 128 stations) every CTA accumulates P over its 64-pixel chunks:
-//   warps 0-7  generate A for the chunk: thread = (station, half of the 64
+//   warps 0-15 generate A for the chunk: thread = (station, quarter of the 64
 //              pixels); the same 64-bit fixed-point phase and SFU sincos as the
 //              forward kernel, split into BF16 hi + lo, written into two M-tiles
 //              of 128 rows (64 stations' cos rows, then their sin rows) x 64
 //              pixels in the UMMA K-major 128-byte swizzled layout. At the end
 //              of each (t, pass) they read the accumulators (tcgen05.ld) and
 //              write the CTA's partial P to global memory.
-//   warp 8     issues per chunk and M-tile, per 16-pixel K slice,
+//   warp 16    issues per chunk and M-tile, per 16-pixel K slice,
 //              A_hi [Y_hi | Y_lo] (N = 2 ncols) and A_lo Y_hi into TMEM.
-//   warp 9     streams the chunk's Y images (hi, lo) with cp.async.bulk.
+//   warp 17    streams the chunk's Y images (hi, lo) with cp.async.bulk.
 // The partials are summed over CTAs in a fixed order by k_adj_tc_reduce
 // (deterministic), which also forms grad_W'. Every mbarrier wait is bounded
 // and sets the abort word on expiry, as in the forward kernel.
@@ -39,7 +39,7 @@ namespace {
 
 using namespace tcx;
 
-constexpr int kAProdWarps = 8;
+constexpr int kAProdWarps = 16;
 constexpr int kAThreads = (kAProdWarps + 2) * 32;
 constexpr int kAMmaWarp = kAProdWarps, kALoadWarp = kAProdWarps + 1;
 constexpr int kAPix = 64;                // pixels per stage (K of the MMA: one 128-byte row)
@@ -94,8 +94,8 @@ __global__ void __launch_bounds__(kAThreads, 1)
 
   if (warp < kAProdWarps) {
     // ------------------------------------------------ A producer + epilogue
-    const int tid = threadIdx.x;  // 0..255
-    const int sl = tid >> 1, half = tid & 1;
+    const int tid = threadIdx.x;  // 0..511
+    const int sl = tid >> 2, quarter = tid & 3;
     const int m = sl >> 6, rc = sl & 63, rs = 64 + (sl & 63);  // M-tile, cos row, sin row
     uint32_t rs_s = 0, rs_rnd = 0;
     bool ok = true;
@@ -133,8 +133,8 @@ __global__ void __launch_bounds__(kAThreads, 1)
         }
         asm volatile("bar.sync 1, %0;" ::"r"(kAProdWarps * 32) : "memory");
         const uint32_t a_hi = smem0 + s * stage_bytes + m * kATile, a_lo = a_hi + kAImg;
-        for (int q = 0; q < 4; ++q) {  // 8 pixels per 16-byte piece
-          const int pp0 = half * 32 + q * 8;
+        for (int q = 0; q < 2; ++q) {  // 8 pixels per 16-byte piece
+          const int pp0 = quarter * 16 + q * 8;
           float cs[8], sn[8];
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
@@ -161,18 +161,19 @@ __global__ void __launch_bounds__(kAThreads, 1)
         if (lane == 0) mbar_arrive(smem_u32(&bar_fullA[s]));
       }
       if (!ok) break;
-      // epilogue of unit u: warp w reads TMEM lanes 32 (w % 4) .. of M-tile w / 4
+      // epilogue of unit u: warp w reads TMEM lanes 32 (w % 4) .. of M-tile (w / 4) % 2,
+      // the even (w < 8) or odd (w >= 8) 16-column blocks
       if (!mbar_wait(smem_u32(&bar_accf), (uint32_t)(u & 1), &s_abort)) {
         ok = false;
         break;
       }
       tc_fence_after();
       {
-        const int mt = warp >> 2, row = (warp & 3) * 32 + lane;
+        const int mt = (warp >> 2) & 1, row = (warp & 3) * 32 + lane;
         const int kind = row >> 6, st = s0 + mt * 64 + (row & 63);
         const uint32_t tb = taddr + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(mt * 2 * ncols);
         float* dst = part + ((((size_t)t * gridDim.x + blockIdx.x) * 2 + kind) * n_st + st) * ncols;
-        for (int cb = 0; cb < ncols / 16; ++cb) {
+        for (int cb = warp >> 3; cb < ncols / 16; cb += 2) {
           float v[16], v2[16];
           tmem_ld16(tb + cb * 16, v);
           tmem_ld16(tb + ncols + cb * 16, v2);

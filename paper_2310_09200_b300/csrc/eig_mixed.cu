@@ -473,7 +473,7 @@ void launch_eig_mixed(const Batch& b, const MixedWs& w, double tol, int max_swee
       launch_jacobi_small_f32(h32, T, KP, 1e-6, 30, s);
       k_mx_cvt<false><<<T, 256, 0, s>>>(b, w, Us, reinterpret_cast<float2*>(Ws) + (size_t)KP * KP, NN, KP);
     } else {
-      launch_jacobi_small(h, T, KP, 1e-14, 60, s);
+      launch_jacobi_small(h, T, KP, 1e-13, 60, s);
     }
     zgemm_df<false>(b, w, DN, DKP, DKP, N, KP, P1, NN, N, Us, NN, KP, P0, NN, N, s);  // X = X1 U
     zgemm_df<false>(b, w, DN, DKP, DKP, N, KP, P2, NN, N, Us, NN, KP, P3, NN, N, s);  // Y U
