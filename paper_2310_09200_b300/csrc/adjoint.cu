@@ -451,6 +451,7 @@ int run_tc(int64_t n_pix, const double* d_pix, double wl, int T, int N, int K, i
   if (e == cudaSuccess) {
     const std::vector<int> nst(T, N), neig(T, K);
     if (tc_prepare(nst, neig, fp16, w, &plan)) rc = BIPP_ERR_UNSUPPORTED;
+    else if (R) tc_plan_force_fused(&plan);  // the Y stage is built for the fused shape
   }
   if (e == cudaSuccess && rc == BIPP_OK && tc_enqueue_pack(sc.b, plan, w, s)) e = cudaErrorLaunchFailure;
   if (e == cudaSuccess && rc == BIPP_OK) {

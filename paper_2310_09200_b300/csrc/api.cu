@@ -609,7 +609,7 @@ static int run_batch(bipp_ss* h, int n_t, int N, const std::vector<int>& nst_v, 
   }
   GraphKey key;
   key.T = n_t; key.N = N; key.K = K; key.st = d_st; key.vis = d_vis; key.stream = s;
-  key.nst = nst_v; key.neig = neig_v; key.chan = chan_v; key.n_stages = tc ? plan.n_stages : 0;
+  key.nst = nst_v; key.neig = neig_v; key.chan = chan_v; key.n_stages = tc ? plan.n_stages + (plan.fused ? 16 : 0) : 0;
 
   if (nufft) {
     // host-planned grids and cuFFT: enqueued directly, not captured

@@ -637,10 +637,36 @@ int max_stages_for(int ncols_max) {
   return std::min(kMaxStages, (kDynSmemMax - kQStageBytes) / stage_bytes_for(ncols_max));
 }
 
-// Autotuned stage counts, keyed by (accumulator width, operand type): the
-// tuned value holds for every batch with the same key in this process.
+// Autotuned launch shapes: the stage-ring depth and the MMA shape (fused
+// N = 2 ncols, or three MMAs of N = ncols), keyed by (accumulator width,
+// station-chunk count rounded up to a power of two, operand type): the tuned
+// shape holds for every batch with the same key in this process.
+struct TuneKey {
+  int ncols, chunks, fp16;
+  bool operator<(const TuneKey& o) const {
+    return ncols != o.ncols ? ncols < o.ncols : (chunks != o.chunks ? chunks < o.chunks : fp16 < o.fp16);
+  }
+};
+struct TuneVal {
+  int n_stages;
+  bool fused;
+};
 std::mutex g_tune_mu;
-std::map<std::pair<int, int>, int> g_tuned_stages;
+std::map<TuneKey, TuneVal> g_tuned;
+
+TuneKey tune_key(const TcPlan& p) {
+  int c = 1;
+  while (c < p.max_chunks) c <<= 1;
+  return TuneKey{p.ncols_max, c, (int)p.fp16};
+}
+
+// TMEM columns per accumulator buffer: a power of two holding the accumulator
+// (2 ncols when fused).
+void set_shape(TcPlan* p, bool fused) {
+  p->fused = fused && 2 * p->ncols_max <= 256;
+  p->ncols_buf = 32;
+  while (p->ncols_buf < (p->fused ? 2 * p->ncols_max : p->ncols_max)) p->ncols_buf <<= 1;
+}
 
 int launch_kernel(const Batch& b, const Pixels& px, int n_level, double* img, const TcPlan& p, int n_stages,
                   TcWorkspace* w, cudaStream_t s) {
@@ -691,17 +717,17 @@ int tc_prepare(const std::vector<int>& nst, const std::vector<int>& neig, bool f
   p->fp16 = fp16;
   p->ncols_max = ncols_max;
   p->max_chunks = max_chunks;
-  p->fused = 2 * ncols_max <= 256;  // N = 2 ncols <= 256 per MMA, two buffers of 2 ncols in 512 TMEM columns
-  p->ncols_buf = 32;
-  while (p->ncols_buf < (p->fused ? 2 * ncols_max : ncols_max)) p->ncols_buf <<= 1;  // a power of two <= 256
   const int smax = max_stages_for(ncols_max);
   if (smax < 2) return -6;
   std::lock_guard<std::mutex> lock(g_tune_mu);
-  auto it = g_tuned_stages.find({ncols_max, (int)fp16});
-  p->tuned = it != g_tuned_stages.end();
-  p->n_stages = p->tuned ? it->second : smax;
+  auto it = g_tuned.find(tune_key(*p));
+  p->tuned = it != g_tuned.end();
+  p->n_stages = p->tuned ? it->second.n_stages : smax;
+  set_shape(p, p->tuned ? it->second.fused : true);  // untuned: fused where N = 2 ncols <= 256
   return 0;
 }
+
+void tc_plan_force_fused(TcPlan* p) { set_shape(p, true); }
 
 int tc_enqueue_pack(const Batch& b, const TcPlan& p, TcWorkspace* w, cudaStream_t s) {
   const int T = b.T;
@@ -754,8 +780,9 @@ int tc_enqueue_yout(const Batch& b, const Pixels& px, int n_level, const TcPlan&
 
 int tc_autotune(const Batch& b, const Pixels& px, int n_level, int n_chan_sub, TcPlan* p, TcWorkspace* w,
                 cudaStream_t s) {
-  // Time each feasible stage count on the first steps of the batch and a
-  // pixel subset, into a scratch image (the real images are not touched).
+  // Time each feasible (MMA shape, stage count) on the first steps of the
+  // batch and a pixel subset, into a scratch image (the real images are not
+  // touched).
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -769,20 +796,26 @@ int tc_autotune(const Batch& b, const Pixels& px, int n_level, int n_chan_sub, T
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  int best = p->n_stages;
+  TcPlan best = *p;
   float best_ms = 1e30f;
   int rc = 0;
-  for (int ns = 2; ns <= max_stages_for(p->ncols_max) && rc == 0; ++ns) {
-    rc = launch_kernel(bs, ps, n_level, scratch, *p, ns, w, s);  // warm-up
-    cudaEventRecord(e0, s);
-    if (rc == 0) rc = launch_kernel(bs, ps, n_level, scratch, *p, ns, w, s);
-    cudaEventRecord(e1, s);
-    cudaEventSynchronize(e1);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (rc == 0 && ms < best_ms) {
-      best_ms = ms;
-      best = ns;
+  const int n_shapes = (2 * p->ncols_max <= 256) ? 2 : 1;
+  for (int f = 0; f < n_shapes && rc == 0; ++f) {
+    TcPlan q = *p;
+    set_shape(&q, f == 0 && n_shapes == 2);
+    for (int ns = 2; ns <= max_stages_for(q.ncols_max) && rc == 0; ++ns) {
+      rc = launch_kernel(bs, ps, n_level, scratch, q, ns, w, s);  // warm-up
+      cudaEventRecord(e0, s);
+      if (rc == 0) rc = launch_kernel(bs, ps, n_level, scratch, q, ns, w, s);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rc == 0 && ms < best_ms) {
+        best_ms = ms;
+        best = q;
+        best.n_stages = ns;
+      }
     }
   }
   cudaEventDestroy(e0);
@@ -790,10 +823,10 @@ int tc_autotune(const Batch& b, const Pixels& px, int n_level, int n_chan_sub, T
   cudaFreeAsync(scratch, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return -9;
   if (rc) return rc;
-  p->n_stages = best;
+  *p = best;
   p->tuned = true;
   std::lock_guard<std::mutex> lock(g_tune_mu);
-  g_tuned_stages[{p->ncols_max, (int)p->fp16}] = best;
+  g_tuned[tune_key(*p)] = TuneVal{p->n_stages, p->fused};
   return 0;
 }
 

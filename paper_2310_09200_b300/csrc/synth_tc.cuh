@@ -55,9 +55,9 @@ struct TcPlan {
   int ncols_max = 16;   // widest accumulator (2 * n_eig rounded to 16)
   int max_chunks = 1;   // most 32-station chunks of a step
   int ncols_buf = 32;   // TMEM columns per accumulator buffer (power of two)
-  bool fused = false;   // A_hi [B_hi | B_lo] as one MMA of N = 2 ncols (ncols_max <= 128)
+  bool fused = false;   // A_hi [B_hi | B_lo] as one MMA of N = 2 ncols (ncols_max <= 128); autotuned
   int n_stages = 2;     // shared-memory ring depth
-  bool tuned = false;   // n_stages comes from the autotuner
+  bool tuned = false;   // n_stages and fused come from the autotuner
 };
 
 int tc_alloc(TcWorkspace* w, int T, int N, int K);
@@ -88,9 +88,14 @@ int launch_adjoint_tc(const Pixels& px, int T, int n_st, int K, int ncols, const
                       const unsigned char* Y, int nc64, float* part, int grid, double2* gWp, int* status,
                       cudaStream_t s);
 int adj_tc_smem_bytes(int ncols);
-// Not capturable (synchronises): time each feasible stage count on a subset
-// of the packed batch into a scratch image, keep the fastest in p and in a
-// process-wide cache keyed by (ncols_max, operand type).
+// The fused MMA shape (N = 2 ncols) whatever the tuner chose; needs
+// 2 ncols_max <= 256 (else p stays unfused).
+void tc_plan_force_fused(TcPlan* p);
+// Not capturable (synchronises): time each feasible launch shape (MMA shape:
+// fused N = 2 ncols or three N = ncols MMAs; stage-ring depth) on a subset of
+// the packed batch into a scratch image, keep the fastest in p and in a
+// process-wide cache keyed by (ncols_max, chunk count rounded up to a power of
+// two, operand type).
 int tc_autotune(const Batch& b, const Pixels& px, int n_level, int n_chan_sub, TcPlan* p, TcWorkspace* w,
                 cudaStream_t s);
 

@@ -293,3 +293,11 @@ def test_noalloc_c_entry_rejects_bad_scalars_before_any_cuda_call(lib):
     assert b"NaN" in msg.value
     assert call(8, 4, 1, [-inf, inf], wl=np.inf) == bipp_ss.BIPP_ERR_INVALID_ARG
     assert call(8, 4, 1, [-inf, inf], wl=-1.0) == bipp_ss.BIPP_ERR_INVALID_ARG
+
+
+def test_sincos_rate_probe_rejects_bad_arguments(lib):
+    """The SFU-rate probe checks its arguments before any CUDA call."""
+    r = C.c_double(1.0)
+    assert lib.bipp_ss_measure_sincos_rate(-1, 0, C.byref(r)) == bipp_ss.BIPP_ERR_INVALID_ARG
+    assert lib.bipp_ss_measure_sincos_rate(-1, 101, C.byref(r)) == bipp_ss.BIPP_ERR_INVALID_ARG
+    assert lib.bipp_ss_measure_sincos_rate(-1, 3, None) == bipp_ss.BIPP_ERR_INVALID_ARG
