@@ -31,7 +31,7 @@ __global__ void k_gram(Batch b, int gram_identity) {
   const double wl = b.wl[t];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= n || j >= n) return;
+  if (i >= n || j >= n || i > j) return;  // G is symmetric: the upper triangle, mirrored
   double g;
   if (gram_identity) {
     g = (i == j) ? 1.0 : 0.0;
@@ -44,6 +44,7 @@ __global__ void k_gram(Batch b, int gram_identity) {
     g = (x == 0.0) ? 1.0 : sinpi(x) / (M_PI * x);  // NaN positions propagate to G
   }
   b.G[mat_off(t, b.n_max) + (size_t)i + (size_t)j * b.n_max] = g;
+  if (i != j) b.G[mat_off(t, b.n_max) + (size_t)j + (size_t)i * b.n_max] = g;
 }
 
 // ---------------------------------------------------------------- Cholesky
