@@ -473,7 +473,8 @@ static int enqueue_batch(bipp_ss* h, const Batch& b, const TcPlan& plan, cudaStr
     launch_cholesky(b, gi, s);
     return cudaGetLastError() == cudaSuccess ? BIPP_OK : fail(h, BIPP_ERR_CUDA, "Gram / Cholesky launch failed");
   }
-  launch_reduce(b, gi, s);
+  if (h->mixed_kp > 0) launch_reduce32(b, gi, s);  // FP32 C for the FP32 stage; the refinement factors C
+  else launch_reduce(b, gi, s);
   CUDA_TRY(h, record(h->ev[1], s));
   if (h->mixed_kp > 0) {
     MixedWs w = h->mx;
@@ -701,16 +702,20 @@ static int run_batch(bipp_ss* h, int n_t, int N, const std::vector<int>& nst_v, 
   }
   h->timings[4] = 0;
   for (int t = 0; t < n_t; ++t) h->timings[4] += sweeps[t];
-  // gram, [cholesky], trinv, [2 reduction GEMMs], hermitize, jacobi, select, [scale], [pack], synthesis
-  h->timings[5] = (h->opt.gram_identity ? 6 : 9) + (tc ? 1 + (h->opt.precision == BIPP_PREC_SPLIT_FP16) : 0) +
-                  (h->mixed_kp > 0 ? kMixedLaunches - 1 : 0) + (nufft ? h->nu_launches - 1 : 0);
+  // gram, [cholesky], trinv, reduction (G = I: 1; mixed: 2 FP32 GEMMs; else 2 GEMMs + hermitize),
+  // eigensolve (Jacobi: 1; mixed: kMixedLaunches), select, [scale], [pack], synthesis
+  {
+    const bool gi = h->opt.gram_identity != 0, mixed = h->mixed_kp > 0;
+    h->timings[5] = 1 + (gi ? 0 : 1) + 1 + (gi ? 1 : (mixed ? 2 : 3)) + (mixed ? kMixedLaunches : 1) + 2 +
+                    (tc ? 1 + (h->opt.precision == BIPP_PREC_SPLIT_FP16) : 0) + (nufft ? h->nu_launches - 1 : 0);
+  }
   for (int t = 0; t < n_t; ++t) {
     if (status[t] & kStatusNotPD)
       return fail(h, BIPP_ERR_GRAM_NOT_PD, "step %d: Gram matrix is not positive definite (Cholesky pivot <= 0 or NaN)", t);
     if (status[t] & kStatusNotConverged)
       return h->mixed_kp > 0
                  ? fail(h, BIPP_ERR_EIG_NOT_CONVERGED,
-                        "step %d: mixed eigensolver did not converge (QR step cap, refinement Jacobi sweep cap %d, "
+                        "step %d: mixed eigensolver did not converge (refinement Jacobi sweep cap %d, "
                         "or a kept residual above 1e3 * jacobi_tol * ||C||_F)",
                         t, h->opt.max_jacobi_sweeps)
                  : fail(h, BIPP_ERR_EIG_NOT_CONVERGED, "step %d: Jacobi did not converge in %d sweeps", t,

@@ -83,12 +83,17 @@ __device__ __forceinline__ bool last_of_chan(const Batch& b, int t) {
 void launch_gram(const Batch& b, int gram_identity, cudaStream_t s);
 void launch_cholesky(const Batch& b, int gram_identity, cudaStream_t s);
 void launch_reduce(const Batch& b, int gram_identity, cudaStream_t s);
+// The mixed eigensolver's reduction: C32 = L^{-1} V L^{-T} (or the Hermitian
+// part of V when G = I) in FP32 into the first half of each step's X buffer;
+// the FP64 C is not formed (the refinement applies L^{-1} V L^{-T} in factored
+// form). 2 launches (1 with G = I).
+void launch_reduce32(const Batch& b, int gram_identity, cudaStream_t s);
 void launch_jacobi(const Batch& b, double tol, int max_sweeps, cudaStream_t s);
 // Mixed-precision eigensolve (the leading pairs of the FP32 tridiagonal form +
 // FP64-class refinement); needs the X and Q buffers of the batch as scratch,
 // which fits when eig_mixed_fits(n_max, KP).
 bool eig_mixed_fits(int n_max, int KP);
-constexpr int kMixedLaunches = 70;  // kernels launched by launch_eig_mixed
+constexpr int kMixedLaunches = 77;  // kernels launched by launch_eig_mixed
 void launch_eig_mixed(const Batch& b, const MixedWs& w, double tol, int max_sweeps, cudaStream_t s);
 // Error message of calls without a handle (returned by bipp_ss_last_error(NULL)).
 int set_global_error(int code, const char* msg);

@@ -372,6 +372,86 @@ __global__ void k_reduce_gemm_df(Batch b) {
   }
 }
 
+// The same reduction in FP32 for the mixed-precision eigensolver, whose FP32
+// stage needs C only to FP32 accuracy and whose refinement applies
+// L^{-1} V L^{-T} in factored form (eig_mixed.cu):
+// mode 0: X32 = Linv V into the C buffer (float2, 2 N^2 per problem);
+// mode 1: C32 = X32 Linv^T (upper tiles, mirrored) into the first half of the X buffer.
+template <int MODE>
+__global__ void k_reduce32(Batch b) {
+  const int t = blockIdx.z;
+  const int n = b.nst[t];
+  const int N = b.n_max;
+  if (b.status[t]) return;
+  const int i0 = blockIdx.x * GT, j0 = blockIdx.y * GT;
+  if (i0 >= n || j0 >= n) return;
+  if (MODE == 1 && i0 > j0) return;
+  const double* Linv = b.Linv + mat_off(t, N);
+  const size_t NN = (size_t)N * N;
+  const float2* Z32 = reinterpret_cast<const float2*>(b.C) + (size_t)t * 2 * NN;
+  const double2* V = b.vis + mat_off(t, N);
+  float2* out = (MODE == 0) ? reinterpret_cast<float2*>(b.C) + (size_t)t * 2 * NN
+                            : reinterpret_cast<float2*>(b.X) + (size_t)t * 2 * NN;
+  __shared__ float sR[GK][GT + 1];
+  __shared__ float2 sZ[GK][GT + 1];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  float2 acc[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) acc[u] = make_float2(0.f, 0.f);
+  const int kend = min(n, (MODE == 0 ? i0 : j0) + GT);
+  for (int k0 = 0; k0 < kend; k0 += GK) {
+    for (int e = threadIdx.x; e < GK * GT; e += blockDim.x) {
+      const int kk = e / GT, ii = e % GT, k = k0 + kk;
+      const int i = i0 + ii, j = j0 + ii;
+      if (MODE == 0) {
+        sR[kk][ii] = (k < n && i < n) ? (float)Linv[(size_t)i * N + k] : 0.f;
+        const double2 z = (k < n && j < n) ? V[(size_t)k + (size_t)j * N] : make_double2(0.0, 0.0);
+        sZ[kk][ii] = make_float2((float)z.x, (float)z.y);
+      } else {
+        sZ[kk][ii] = (k < n && i < n) ? Z32[(size_t)i + (size_t)k * N] : make_float2(0.f, 0.f);
+        sR[kk][ii] = (k < n && j < n) ? (float)Linv[(size_t)j * N + k] : 0.f;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int ii = tx, jj = ty + 8 * u;
+        const float r = (MODE == 0) ? sR[kk][ii] : sR[kk][jj];
+        const float2 z = (MODE == 0) ? sZ[kk][jj] : sZ[kk][ii];
+        acc[u].x = fmaf(r, z.x, acc[u].x);
+        acc[u].y = fmaf(r, z.y, acc[u].y);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = i0 + tx, j = j0 + ty + 8 * u;
+    if (i < n && j < n) {
+      out[(size_t)i + (size_t)j * N] = acc[u];
+      if (MODE == 1 && i0 != j0) out[(size_t)j + (size_t)i * N] = make_float2(acc[u].x, -acc[u].y);
+    }
+  }
+}
+
+// G = I in the mixed eigensolver: C32 = the Hermitian part of V, in FP32,
+// into the first half of the X buffer.
+__global__ void k_herm32(Batch b) {
+  const int t = blockIdx.z;
+  const int n = b.nst[t];
+  const int N = b.n_max;
+  if (b.status[t]) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= n || j >= n) return;
+  const double2* V = b.vis + mat_off(t, N);
+  const double2 a = V[(size_t)i + (size_t)j * N], c = V[(size_t)j + (size_t)i * N];
+  float2* C32 = reinterpret_cast<float2*>(b.X) + (size_t)t * 2 * (size_t)N * N;
+  C32[(size_t)i + (size_t)j * N] = make_float2((float)(0.5 * (a.x + c.x)), i == j ? 0.f : (float)(0.5 * (a.y - c.y)));
+}
+
 // C <- (C + C^H)/2 (or C <- Hermitian part of V when G = I): removes
 // rounding-level asymmetry before the Jacobi sweeps.
 __global__ void k_hermitize(Batch b, int from_vis) {
@@ -568,6 +648,17 @@ void launch_reduce(const Batch& b, int gram_identity, cudaStream_t s) {
   k_reduce_gemm_df<0><<<grd, 256, 0, s>>>(b);
   k_reduce_gemm_df<1><<<grd, 256, 0, s>>>(b);
   k_hermitize<<<hg, hb, 0, s>>>(b, 0);
+}
+
+void launch_reduce32(const Batch& b, int gram_identity, cudaStream_t s) {
+  if (gram_identity) {
+    dim3 hb(16, 16), hg((b.n_max + 15) / 16, (b.n_max + 15) / 16, b.T);
+    k_herm32<<<hg, hb, 0, s>>>(b);
+    return;
+  }
+  dim3 grd((b.n_max + GT - 1) / GT, (b.n_max + GT - 1) / GT, b.T);
+  k_reduce32<0><<<grd, 256, 0, s>>>(b);
+  k_reduce32<1><<<grd, 256, 0, s>>>(b);
 }
 
 void launch_jacobi(const Batch& b, double tol, int max_sweeps, cudaStream_t s) {

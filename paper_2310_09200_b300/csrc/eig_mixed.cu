@@ -45,7 +45,7 @@ constexpr int kPad = 16;       // extra leading pairs refined beyond n_eig
 constexpr int kPasses = 4;     // refinement passes at most
 constexpr int kMxDone = kMxDoneBit;  // st2 bit: residual met the early-exit bound, later passes skip the step
 constexpr int GT = 32, GK = 16;
-static_assert(7 + 2 + 17 * (kPasses - 1) + 10 == kMixedLaunches, "launch count of the mixed eigensolver");
+static_assert(6 + 2 + 19 * (kPasses - 1) + 12 == kMixedLaunches, "launch count of the mixed eigensolver");
 
 // Shape codes of the batched complex products: dimension = n_st or kp of the problem.
 enum Dim { DN = 0, DKP = 1 };
@@ -137,19 +137,74 @@ __global__ void k_zgemm_df(const int* nst, const int* kp, int mc, int nc, int kc
   }
 }
 
-// C32 = fp32(C): written into the first half of the problem's X buffer.
-__global__ void k_mx_tof32(Batch b) {
-  const int t = blockIdx.y;
-  if (b.status[t]) return;
-  const int n = b.nst[t], N = b.n_max;
-  const double2* C = b.C + (size_t)t * N * N;
-  float2* C32 = reinterpret_cast<float2*>(b.X + (size_t)t * N * N);
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
-    const int i = e % n, j = e / n;
-    const double2 v = C[(size_t)i + (size_t)j * N];
-    C32[(size_t)i + (size_t)j * N] = make_float2((float)v.x, (float)v.y);
+// The factored operator of the refinement, C = L^{-1} V L^{-T}, applied as
+// three products: out = op(Linv) B with Linv the row-major FP64 inverse
+// Cholesky factor (real), B an n x kp complex block (column-major, ld N,
+// NN apart), op = transpose (UPPER: (L^{-T})_ik = Linv[k][i], k >= i) or
+// identity (L^{-1}, k <= i); double-float arithmetic as k_zgemm_df, the zero
+// triangle skipped.
+template <bool UPPER>
+__global__ void k_rgemm_df(const Batch b, const MixedWs w, const double2* B0, double2* out0) {
+  const int t = blockIdx.z;
+  if (mx_skip(b.status, w.st2, t)) return;
+  const int n = b.nst[t], k_p = w.kp[t], N = b.n_max;
+  const size_t NN = (size_t)N * N;
+  const int i0 = blockIdx.x * GT, j0 = blockIdx.y * GT;
+  if (i0 >= n || j0 >= k_p) return;
+  const double* Linv = b.Linv + (size_t)t * NN;
+  const double2* B = B0 + (size_t)t * NN;
+  double2* out = out0 + (size_t)t * NN;
+  __shared__ float2 sA[GK][GT + 1];  // (hi, lo)
+  __shared__ float4 sB[GK][GT + 1];  // (re hi, re lo, im hi, im lo)
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  float acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[u][c] = 0.f;
+  const int kbeg = UPPER ? (i0 / GK) * GK : 0, kend = UPPER ? n : min(n, i0 + GT);
+  for (int k0 = kbeg; k0 < kend; k0 += GK) {
+    for (int e = threadIdx.x; e < GK * GT; e += blockDim.x) {
+      const int kk = e / GT, ii = e % GT, k = k0 + kk;
+      const int i = i0 + ii, j = j0 + ii;
+      double a = 0.0;
+      if (k < n && i < n) a = UPPER ? (k >= i ? Linv[(size_t)k * N + i] : 0.0) : (k <= i ? Linv[(size_t)i * N + k] : 0.0);
+      const double2 bv = (k < n && j < k_p) ? B[(size_t)k + (size_t)j * N] : make_double2(0.0, 0.0);
+      float2 fa;
+      float4 fb;
+      df::split(a, fa.x, fa.y);
+      df::split(bv.x, fb.x, fb.y);
+      df::split(bv.y, fb.z, fb.w);
+      sA[kk][ii] = fa;
+      sB[kk][ii] = fb;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < GK; ++kk) {
+      const float2 a = sA[kk][tx];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float4 bv = sB[kk][ty + 8 * u];
+        df::mac(acc[u][0], acc[u][1], a.x, a.y, bv.x, bv.y);
+        df::mac(acc[u][2], acc[u][3], a.x, a.y, bv.z, bv.w);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      df::renorm(acc[u][0], acc[u][1]);
+      df::renorm(acc[u][2], acc[u][3]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = i0 + tx, j = j0 + ty + 8 * u;
+    if (i < n && j < k_p)
+      out[(size_t)i + (size_t)j * N] = make_double2(df::to_double(acc[u][0], acc[u][1]),
+                                                    df::to_double(acc[u][2], acc[u][3]));
   }
 }
+
 
 // The kp back-transformed FP32 eigenvectors (rank order) become the FP64
 // start X of the refinement; ||C||_F = ||T||_F.
@@ -395,7 +450,6 @@ void launch_eig_mixed(const Batch& b, const MixedWs& w, double tol, int max_swee
   float* Xf = reinterpret_cast<float*>(b.X);
   const size_t xs = 4 * NN;  // floats per problem in the X and Q buffers
   cudaMemsetAsync(w.st2, 0, sizeof(int) * T, s);
-  k_mx_tof32<<<dim3(std::max(1, std::min(64, (N * N + 255) / 256)), T), 256, 0, s>>>(b);
   TridiagArgs a;
   a.C = reinterpret_cast<float2*>(Xf);
   a.scratch = Xf + 2 * NN + 2 * (size_t)N * KP;
@@ -430,8 +484,8 @@ void launch_eig_mixed(const Batch& b, const MixedWs& w, double tol, int max_swee
   // 2. FP64 refinement of the kp leading pairs; buffers inside the Q buffer
   double2* P0 = b.Q;                       // X (final eigenvectors), n x kp, ld N
   double2* P1 = b.Q + (size_t)N * KP;      // orthonormalised X / FP32 R and its correction
-  double2* P2 = b.Q + (size_t)2 * N * KP;  // Y = C X
-  double2* P3 = b.Q + (size_t)3 * N * KP;  // Y U / R, then the shifted solves' factors
+  double2* P2 = b.Q + (size_t)2 * N * KP;  // V L^{-T} X1, then Y U / R
+  double2* P3 = b.Q + (size_t)3 * N * KP;  // L^{-T} X1, then Y = C X1, then the shifted solves' factors
   float2* R32 = reinterpret_cast<float2*>(P1);
   const size_t NN2 = 2 * NN;  // per-problem stride of the FP32 views
   double2* Hs = b.Q + (size_t)4 * N * KP;  // S, then H (kp x kp, ld KP)
@@ -460,13 +514,17 @@ void launch_eig_mixed(const Batch& b, const MixedWs& w, double tol, int max_swee
   const int ew = std::max(1, (N * KP + 255) / 256 / 8);  // blocks per problem of the elementwise kernels
   const int ci_smem = (int)(sizeof(double2) * ((size_t)KP * KP + KP));
   cudaFuncSetAttribute(k_mx_cholinv, cudaFuncAttributeMaxDynamicSharedMemorySize, ci_smem);
-  float* lu3 = reinterpret_cast<float*>(P3);
+  float* lu3 = reinterpret_cast<float*>(P3);  // the shifted solves' factors: Y (P3) is dead once Y U is formed
+  const dim3 rgrd((N + GT - 1) / GT, (KP + GT - 1) / GT, T);
   for (int pass = 0; pass < kPasses; ++pass) {
     zgemm_df<true>(b, w, DKP, DKP, DN, KP, KP, P0, NN, N, P0, NN, N, Hs, NN, KP, s);   // S = X^H X
     k_mx_cholinv<<<T, 256, ci_smem, s>>>(b, w, Hs, Ws, NN, KP);                                    // W = R^{-1}
     zgemm_df<false>(b, w, DN, DKP, DKP, N, KP, P0, NN, N, Ws, NN, KP, P1, NN, N, s);  // X1 = X W
-    zgemm_df<false>(b, w, DN, DKP, DN, N, KP, b.C, NN, N, P1, NN, N, P2, NN, N, s);   // Y = C X1
-    zgemm_df<true>(b, w, DKP, DKP, DN, KP, KP, P1, NN, N, P2, NN, N, Hs, NN, KP, s);  // H = X1^H Y
+    // Y = C X1 = L^{-1} (V (L^{-T} X1)); Y lands in P3 and Y U in P2
+    k_rgemm_df<true><<<rgrd, 256, 0, s>>>(b, w, P1, P3);                                          // L^{-T} X1
+    zgemm_df<false>(b, w, DN, DKP, DN, N, KP, b.vis, NN, N, P3, NN, N, P2, NN, N, s);  // V (.)
+    k_rgemm_df<false><<<rgrd, 256, 0, s>>>(b, w, P2, P3);                                         // Y
+    zgemm_df<true>(b, w, DKP, DKP, DN, KP, KP, P1, NN, N, P3, NN, N, Hs, NN, KP, s);  // H = X1^H Y
     k_mx_herm<<<T, 256, 0, s>>>(b, w, Hs, NN, KP);
     if (pass == 0) {                                                                              // H = U th U^H
       k_mx_cvt<true><<<T, 256, 0, s>>>(b, w, Hs, reinterpret_cast<float2*>(Ws), NN, KP);
@@ -476,8 +534,8 @@ void launch_eig_mixed(const Batch& b, const MixedWs& w, double tol, int max_swee
       launch_jacobi_small(h, T, KP, 1e-13, 60, s);
     }
     zgemm_df<false>(b, w, DN, DKP, DKP, N, KP, P1, NN, N, Us, NN, KP, P0, NN, N, s);  // X = X1 U
-    zgemm_df<false>(b, w, DN, DKP, DKP, N, KP, P2, NN, N, Us, NN, KP, P3, NN, N, s);  // Y U
-    k_mx_resid<<<dim3(KP, T), 256, 0, s>>>(b, w, P0, P3, R32, NN);                                // R = YU - X th
+    zgemm_df<false>(b, w, DN, DKP, DKP, N, KP, P3, NN, N, Us, NN, KP, P2, NN, N, s);  // Y U
+    k_mx_resid<<<dim3(KP, T), 256, 0, s>>>(b, w, P0, P2, R32, NN);                                // R = YU - X th
     if (pass == kPasses - 1) break;
     k_mx_check<<<T, 128, 0, s>>>(b, w, 1e2 * tol);
     // correction in FP32: H P (T - theta_j)^{-1} P H^H r_j, P = I - Z_k Z_k^T
