@@ -44,17 +44,18 @@ if ROOT not in sys.path:
 METRIC = "synthesized pixel*eigvec*station products/s"
 UNIT = "products/s"
 
-# FP64 pipe of a B300: 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz (unit count and
-# maximum SM clock); FP32 pipe: 148 x 128 FFMA/clk x 2 x 2.032 GHz.
+# Nominal FP64 and FP32 pipes of a B300 (148 SMs x 2 DFMA / 128 FFMA per clock x 2
+# flop x 2.032 GHz): defaults only; the reported rooflines use the rates measured in
+# the run by bipp_ss_measure_fma_rates.
 SMS = 148
 SM_MAX_GHZ = 2.032
 FP64_PEAK_FLOPS = SMS * 2 * 2 * SM_MAX_GHZ * 1e9
 FP32_PEAK_FLOPS = SMS * 128 * 2 * SM_MAX_GHZ * 1e9
-# Issue slots: 4 warp instructions per SM per clock. k_synth_tc issues 41 thread
+# Issue slots: 4 warp instructions per SM per clock. k_synth_tc issues 40 thread
 # instructions per pixel-station pair (ncu, profiles/k_synth_tc_ska_low_512st_1024px_10steps.md:
 # phase, sincos, hi/lo split and stores of A in the producers, plus the epilogue).
 ISSUE_THREAD_INSTR_PER_S = SMS * 4 * 32 * SM_MAX_GHZ * 1e9
-SYNTH_TC_INSTR_PER_PAIR = 41
+SYNTH_TC_INSTR_PER_PAIR = 40
 
 
 DTYPES = {"fp64": "f64", "fp32": "f64 eig + f32 synth",
@@ -113,6 +114,26 @@ def tc_roofline(syn_flops: float, syn_ms: float, pairs: float, peaks: dict, traf
                           "bipp_ss_measure_sincos_rate (__sincosf chains on every SM); issue_slots = "
                           f"{SYNTH_TC_INSTR_PER_PAIR} thread instructions per pair (ncu) at 4 warp "
                           "instructions per SM per clock, 148 SMs, 2.032 GHz")}
+
+
+def eig_roofline(n: int, kp: int, n_t: int, eig_ms: float, fp32_rate: float, passes: int = 2) -> dict:
+    """Roofline of the mixed eigensolve stage on the CUDA cores: the FP32
+    Householder reduction (16/3 n^3 flops per step) and the three applications
+    of the reflectors to kp columns (4 n^2 kp flops each) at the measured FP32
+    FMA rate, plus `passes` refinement passes of double-float products at half
+    that rate in instructions (12 FP32 instructions per real multiply-add): per
+    pass C X1 = L^{-1} (V (L^{-T} X1)) (6 n^2 kp real multiply-adds) and the
+    five n x kp x kp products (20 n kp^2). frac = bound / measured stage time
+    (the Sturm counts, solves and small Jacobi are latency chains, not in it)."""
+    fp32_flops = (16.0 / 3.0 * n ** 3 + 3 * 4.0 * n ** 2 * kp) * n_t
+    df_instr = passes * 12.0 * (6.0 * n ** 2 * kp + 20.0 * n * kp ** 2) * n_t
+    t32, tdf = fp32_flops / fp32_rate, df_instr / (fp32_rate / 2)
+    return {"kernel": "mixed eigensolve stage (FP32 tridiagonal form, kp leading pairs, double-float refinement)",
+            "bound": "alu", "achieved": None, "peak": fp32_rate / 1e12, "unit": "TFLOP/s", "traffic": None,
+            "frac": (t32 + tdf) / (eig_ms / 1e3),
+            "t_roof_ms": {"fp32_stage": t32 * 1e3, "df_refinement": tdf * 1e3},
+            "peak_note": ("of measured: FP32 FMA rate of this GPU (bipp_ss_measure_fma_rates, this run); "
+                          "frac = (FP32 flops / rate + double-float instructions / instruction rate) / stage time")}
 
 
 def measured_peaks() -> dict:
@@ -307,7 +328,7 @@ def cpu_sample_nufft(inp, bounds, eps, patch=128, t=0):
     return {"t_s": dt, "n_sub": int(len(sel)), "products": prods, "value": prods / dt}
 
 
-def nufft_roofline(nt, n_level, n_pix, n_t, n_st, n_eig, hbm_gbs):
+def nufft_roofline(nt, n_level, n_pix, n_t, n_st, n_eig, hbm_gbs, fp32_rate=FP32_PEAK_FLOPS):
     """The dominant kernel of NUFFT synthesis (largest total time per job) and its
     HBM roofline: algorithmic bytes per launch / measured launch time."""
     M = nt["grid"]
@@ -328,8 +349,8 @@ def nufft_roofline(nt, n_level, n_pix, n_t, n_st, n_eig, hbm_gbs):
         if k == "k_nu_spread":  # arithmetic: w^3 cells x levels x (weight x complex strength, accumulated)
             flops = pts * nt["w"] ** 3 * n_level * 4.0
             ach = flops / (ms / 1e3) / 1e12
-            return {"kernel": k, "bound": "alu", "achieved": ach, "peak": FP32_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
-                    "frac": ach / (FP32_PEAK_FLOPS / 1e12)}
+            return {"kernel": k, "bound": "alu", "achieved": ach, "peak": fp32_rate / 1e12, "unit": "TFLOP/s",
+                    "frac": ach / (fp32_rate / 1e12)}
         ach = by / (ms / 1e3) / 1e9
         return {"kernel": k, "bound": "hbm", "achieved": ach, "peak": hbm_gbs, "unit": "GB/s", "frac": ach / hbm_gbs}
 
@@ -343,7 +364,7 @@ def nufft_roofline(nt, n_level, n_pix, n_t, n_st, n_eig, hbm_gbs):
                           "sorted records and cell counts written (sort), one level read + fine grid written (pad), "
                           "fine grid read + written once (FFT), pixel coordinates + correction + image read/write "
                           "(interp); alu (spread): 4 flops per footprint cell and level of each baseline against "
-                          "the FP32 pipe (148 SMs x 128 FMA/clk x 2 x 2.032 GHz)")}
+                          "the FP32 FMA rate measured in this run")}
 
 
 def main():
@@ -590,12 +611,13 @@ def grad_main(args, ws, rank, local):
     pairs = float(inp.n_pix) * n_st * T
     prods = pairs * K
     if prec == "fp32":
+        fp32_rate, _ = bipp_ss_fma(local)
         flops_bwd = pairs * (16.0 * K)  # recomputed z plus the gradient sums, complex
         ach = flops_bwd / (bwd / 1e3) / 1e12
-        roof = {"kernel": "k_adjoint", "bound": "alu", "achieved": ach, "peak": FP32_PEAK_FLOPS / 1e12,
-                "unit": "TFLOP/s", "traffic": None, "frac": ach / (FP32_PEAK_FLOPS / 1e12),
+        roof = {"kernel": "k_adjoint", "bound": "alu", "achieved": ach, "peak": fp32_rate / 1e12,
+                "unit": "TFLOP/s", "traffic": None, "frac": ach / (fp32_rate / 1e12),
                 "peak_note": "16 K flops per pixel-station pair and step (recomputed z and the gradient sums) "
-                             "against the FP32 pipe"}
+                             "against the FP32 FMA rate measured in this run"}
     else:
         # backward: z recomputed (8 P real flops, x3 split) and grad_W' = 2 sum_r Phi Y as the real GEMM
         # [cos; sin] (2 n_st rows) x [Re Y, Im Y] (2 K columns) over pixels (x3 split); two Phi generations
@@ -632,6 +654,11 @@ def grad_main(args, ws, rank, local):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def bipp_ss_fma(local):
+    from paper_2310_09200_b300 import bipp_ss
+    return bipp_ss.bipp_ss_measure_fma_rates(local, 5)
 
 
 def bipp_ss_rate(local):
@@ -730,6 +757,7 @@ def ours_main(args, ws, rank, local):
     for _ in range(args.warmup):
         one_step()
     sfu_rate = bipp_ss.bipp_ss_measure_sincos_rate(local, 5)  # the SFU bound's rate, on this GPU now
+    fp32_rate, fp64_rate = bipp_ss.bipp_ss_measure_fma_rates(local, 5)  # CUDA-core FMA rates (flop/s)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -770,39 +798,24 @@ def ours_main(args, ws, rank, local):
     syn_flops = 8.0 * prods  # one complex multiply-add per product
     if args.eig == "jacobi64":
         roof_jacobi = {"kernel": "k_jacobi_t<double>", "bound": "alu",
-                       "achieved": jac_flops / (eig_ms / 1e3) / 1e12, "peak": FP64_PEAK_FLOPS / 1e12,
+                       "achieved": jac_flops / (eig_ms / 1e3) / 1e12, "peak": fp64_rate / 1e12,
                        "unit": "TFLOP/s", "traffic": None,
-                       "peak_note": "FP64 pipe, 148 SM x 2 DFMA/clk x 2 flop x 2.032 GHz"}
+                       "peak_note": "of measured: FP64 FMA rate of this GPU (bipp_ss_measure_fma_rates, this run)"}
         roof_jacobi["frac"] = roof_jacobi["achieved"] / roof_jacobi["peak"]
     else:
-        # FP32 stage: Householder reduction (8 n^3) + back-transformation (8 n^3) flops per step
-        # (the tridiagonal QR's rotations, a sequential chain, are not counted). Refinement:
-        # per pass n^2 kp + 5 n kp^2 complex multiply-adds in double-float, ~48 FP32
-        # operations each, two passes (the early exit stops most steps there).
-        kp = min(n_st, inp.n_eig + 16)
-        jac_flops = 16.0 * n_st ** 3 * inp.n_t
-        df_ops = 2 * 48.0 * (n_st ** 2 * kp + 5 * n_st * kp ** 2) * inp.n_t
-        fp32_ops_per_s = FP32_PEAK_FLOPS / 2  # FP32 instructions per second
-        t_roof = jac_flops / FP32_PEAK_FLOPS + df_ops / fp32_ops_per_s
-        roof_jacobi = {"kernel": "FP32 tridiagonal eigensolve + double-float refinement (61 launches)",
-                       "bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s",
-                       "traffic": None, "frac": t_roof / (eig_ms / 1e3),
-                       "t_roof_ms": {"fp32_eigensolve": jac_flops / FP32_PEAK_FLOPS * 1e3,
-                                     "df_refinement": df_ops / fp32_ops_per_s * 1e3},
-                       "peak_note": ("frac = (FP32 reduction + back-transformation flops / FP32 peak + "
-                                     "double-float refinement operations / FP32 instruction rate) / measured "
-                                     "stage time; the QR chase is latency-bound and not in the bound")}
+        roof_jacobi = eig_roofline(n_st, min(n_st, inp.n_eig + 16), inp.n_t, eig_ms, fp32_rate)
     if nufft:
         nt = dict(nu_last)
         for i, k in enumerate(["sort_ms", "spread_ms", "pad_ms", "fft_ms", "interp_ms", "levels_ms"]):
             nt[k] = nu_ms[i] / K
         roof_synth = nufft_roofline(nt, inp.n_level, inp.n_pix, inp.n_t, n_st, inp.n_eig,
-                                    measured_peaks().get("hbm_gbs", 6400.0))
+                                    measured_peaks().get("hbm_gbs", 6400.0), fp32_rate)
     elif args.precision in ("fp32", "fp64"):
-        peak = FP32_PEAK_FLOPS if args.precision == "fp32" else FP64_PEAK_FLOPS
+        peak = fp32_rate if args.precision == "fp32" else fp64_rate
         roof_synth = {"kernel": f"k_synth_{args.precision[-2:]}", "bound": "alu",
                       "achieved": syn_flops / (syn_ms / 1e3) / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-                      "traffic": None, "peak_note": "CUDA-core FMA pipe, unit count x 2 flop x 2.032 GHz"}
+                      "traffic": None,
+                      "peak_note": "of measured: CUDA-core FMA rate of this GPU (bipp_ss_measure_fma_rates, this run)"}
         roof_synth["frac"] = roof_synth["achieved"] / roof_synth["peak"]
     else:
         traffic = synth_tc_traffic({"n_st": int(n_st), "n_pix": int(inp.n_pix), "n_eig": int(inp.n_eig),

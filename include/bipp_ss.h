@@ -340,6 +340,13 @@ int bipp_ss_collect_noalloc(int64_t n_pix, const double* d_pix_xyz, double wl, i
  * few milliseconds per launch. */
 int bipp_ss_measure_sincos_rate(int32_t device, int32_t repeats, double* pairs_per_s);
 
+/* The FP32 and FP64 FMA rates of `device` (-1 = current) in flop/s (2 per
+ * FMA): kernels of 8 independent FMA chains per thread over 4 CTAs of 256
+ * threads per SM, best of `repeats` (1..100) launches after a warm-up, for the
+ * rooflines of the CUDA-core stages (the eigensolve of Sec. 2.3). Allocates
+ * and frees a small output buffer. */
+int bipp_ss_measure_fma_rates(int32_t device, int32_t repeats, double* fp32_flops, double* fp64_flops);
+
 /* Release the handle and its device memory. NULL is accepted. */
 int bipp_ss_destroy(bipp_ss_t h);
 

@@ -53,6 +53,7 @@ EXPORTED = [
     "bipp_ss_synth_adjoint_device", "bipp_ss_create_channels", "bipp_ss_collect_channels",
     "bipp_ss_energy_neig", "bipp_ss_kmeans_bounds", "bipp_ss_get_nufft_timings", "bipp_ss_collect_device_c64",
     "bipp_ss_debug_fail_wait", "bipp_ss_quantile_bounds", "bipp_ss_measure_sincos_rate",
+    "bipp_ss_measure_fma_rates",
 ]
 
 BIPP_NOALLOC_MAX_STATIONS = 128
@@ -111,6 +112,7 @@ def load(path: str | None = None):
     L.bipp_ss_kmeans_bounds.argtypes = [i32, dp, i32, dp]
     L.bipp_ss_quantile_bounds.argtypes = [i32, dp, i32, dp]
     L.bipp_ss_measure_sincos_rate.argtypes = [i32, i32, dp]
+    L.bipp_ss_measure_fma_rates.argtypes = [i32, i32, dp, dp]
     L.bipp_ss_last_error.argtypes = [H]
     L.bipp_ss_last_error.restype = C.c_char_p
     L.bipp_ss_collect_noalloc.argtypes = [i64, vp, C.c_double, i32, dp, i32, i32, i32, i32, vp, vp, vp, vp,
@@ -371,6 +373,15 @@ def bipp_ss_measure_sincos_rate(device: int = -1, repeats: int = 5) -> float:
     if rc != BIPP_OK:
         raise BippError(rc, bipp_ss_last_error(None))
     return float(r.value)
+
+
+def bipp_ss_measure_fma_rates(device: int = -1, repeats: int = 5) -> tuple:
+    """Measured (FP32, FP64) FMA rates of the device in flop/s."""
+    a, b = C.c_double(0.0), C.c_double(0.0)
+    rc = load().bipp_ss_measure_fma_rates(int(device), int(repeats), C.byref(a), C.byref(b))
+    if rc != BIPP_OK:
+        raise BippError(rc, bipp_ss_last_error(None))
+    return float(a.value), float(b.value)
 
 
 def bipp_ss_destroy(h) -> None:

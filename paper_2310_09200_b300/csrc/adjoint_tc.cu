@@ -47,6 +47,10 @@ constexpr int kASt = 128;                // stations per pass (2 M-tiles of 64 s
 constexpr int kATile = 128 * 128;        // bytes of one M-tile image (128 rows x 128 B)
 constexpr int kAImg = 2 * kATile;        // both M-tiles of one image (hi or lo)
 constexpr int kAStages = 2;
+// Pixel words per stage: word c (0..5) of pixel p at c * kAPw + p + 8 (p / 32): the four
+// quarters of a warp (pixels 16 q + j) then read four different banks.
+constexpr int kAPw = kAPix + 16;
+__device__ __forceinline__ int pw_idx(int c, int p) { return c * kAPw + p + 8 * (p >> 5); }
 
 // Dynamic shared memory: kAStages x (A hi, A lo, Y hi, Y lo), 1 KB aligned,
 // then the stages' pixel words.
@@ -63,7 +67,7 @@ __global__ void __launch_bounds__(kAThreads, 1)
   __shared__ uint32_t s_taddr;
   __shared__ volatile int s_abort;
   const int stage_bytes = adj_stage_bytes(ncols);
-  uint32_t* spix = reinterpret_cast<uint32_t*>(smem + kAStages * stage_bytes);  // [stage][64 pixels][6 words]
+  uint32_t* spix = reinterpret_cast<uint32_t*>(smem + kAStages * stage_bytes);  // [stage][6 words][kAPw]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t tcols = (uint32_t)max(32, 1 << (32 - __clz(4 * ncols - 1)));  // 2 M-tiles x 2 ncols, power of two
   if (threadIdx.x == 0) {
@@ -99,6 +103,17 @@ __global__ void __launch_bounds__(kAThreads, 1)
     const int m = sl >> 6, rc = sl & 63, rs = 64 + (sl & 63);  // M-tile, cos row, sin row
     uint32_t rs_s = 0, rs_rnd = 0;
     bool ok = true;
+    // threads 0..63 load their pixel's coordinates one chunk ahead, so that the global
+    // loads' latency hides behind the previous chunk's phases
+    double pxn[3] = {0.0, 0.0, 0.0};
+    auto fetch = [&](int ch) {
+      if (tid < kAPix) {
+        const int64_t r = (int64_t)ch * kAPix + tid;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) pxn[c] = (r < px.n) ? px.xyz[(size_t)c * px.n + r] : 0.0;
+      }
+    };
+    if (blockIdx.x < nc64) fetch(blockIdx.x);
     for (int u = 0; u < n_units && ok; ++u) {
       const int t = u / npass, s0 = (u % npass) * kASt;
       const int i = s0 + sl;
@@ -121,15 +136,19 @@ __global__ void __launch_bounds__(kAThreads, 1)
           break;
         }
         // the chunk's pixel words: R = round(r 2^40) as (low, high) per component
-        uint32_t* pw = spix + s * kAPix * 6;
+        uint32_t* pw = spix + s * 6 * kAPw;
         if (tid < kAPix) {
-          const int64_t r = (int64_t)chunk * kAPix + tid;
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            const long long R = (r < px.n) ? __double2ll_rn(px.xyz[(size_t)c * px.n + r] * 1099511627776.0) : 0ll;
-            pw[tid * 6 + 2 * c] = (uint32_t)(unsigned long long)R;
-            pw[tid * 6 + 2 * c + 1] = (uint32_t)((unsigned long long)R >> 32);
+            const long long R = __double2ll_rn(pxn[c] * 1099511627776.0);
+            pw[pw_idx(2 * c, tid)] = (uint32_t)(unsigned long long)R;
+            pw[pw_idx(2 * c + 1, tid)] = (uint32_t)((unsigned long long)R >> 32);
           }
+        }
+        {
+          int nch = chunk + gridDim.x;
+          if (nch >= nc64) nch = (u + 1 < n_units) ? (int)blockIdx.x : -1;
+          if (nch >= 0) fetch(nch);
         }
         asm volatile("bar.sync 1, %0;" ::"r"(kAProdWarps * 32) : "memory");
         const uint32_t a_hi = smem0 + s * stage_bytes + m * kATile, a_lo = a_hi + kAImg;
@@ -138,8 +157,9 @@ __global__ void __launch_bounds__(kAThreads, 1)
           float cs[8], sn[8];
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
-            const uint32_t* w = pw + (pp0 + j) * 6;
-            const uint32_t rl[3] = {w[0], w[2], w[4]}, rh[3] = {w[1], w[3], w[5]};
+            const int p = pp0 + j;
+            const uint32_t rl[3] = {pw[pw_idx(0, p)], pw[pw_idx(2, p)], pw[pw_idx(4, p)]};
+            const uint32_t rh[3] = {pw[pw_idx(1, p)], pw[pw_idx(3, p)], pw[pw_idx(5, p)]};
             __sincosf(phase_rad_fixed(rl, rh, qa, qb), &sn[j], &cs[j]);
           }
           uint32_t ch[4], cl[4], sh[4], sl4[4];
@@ -311,7 +331,7 @@ __global__ void k_adj_tc_reduce(const float* part, int T, int n_cta, int n_st, i
 
 }  // namespace
 
-int adj_tc_smem_bytes(int ncols) { return kAStages * adj_stage_bytes(ncols) + kAStages * kAPix * 6 * 4 + 1024; }
+int adj_tc_smem_bytes(int ncols) { return kAStages * adj_stage_bytes(ncols) + kAStages * 6 * kAPw * 4 + 1024; }
 
 int launch_adjoint_tc(const Pixels& px, int T, int n_st, int K, int ncols, const uint32_t* qfix, int qfix_stride,
                       const unsigned char* Y, int nc64, float* part, int grid, double2* gWp, int* status,

@@ -137,6 +137,66 @@ __global__ void k_zgemm_df(const int* nst, const int* kp, int mc, int nc, int kc
   }
 }
 
+// The same products in plain FP32 arithmetic (FP64 operands and results): for
+// the first pass, whose orthonormalisation and Rayleigh-Ritz matrix only need
+// the FP32 stage's accuracy (the products that form the residual stay in
+// double-float).
+template <bool CONJ_T>
+__global__ void k_zgemm_f32(const int* nst, const int* kp, int mc, int nc, int kc, const double2* A, size_t sa,
+                            int lda, const double2* B, size_t sb, int ldb, double2* out, size_t so, int ldo,
+                            const int* status, const int* st2) {
+  const int t = blockIdx.z;
+  if (mx_skip(status, st2, t)) return;
+  const int n = nst[t], k_p = kp[t];
+  const int M = dim_of(mc, n, k_p), NN = dim_of(nc, n, k_p), K = dim_of(kc, n, k_p);
+  const int i0 = blockIdx.x * GT, j0 = blockIdx.y * GT;
+  if (i0 >= M || j0 >= NN) return;
+  A += (size_t)t * sa;
+  B += (size_t)t * sb;
+  out += (size_t)t * so;
+  __shared__ float2 sA[GK][GT + 1];
+  __shared__ float2 sB[GK][GT + 1];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  float2 acc[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) acc[u] = make_float2(0.f, 0.f);
+  for (int k0 = 0; k0 < K; k0 += GK) {
+    for (int e = threadIdx.x; e < GK * GT; e += blockDim.x) {
+      const int kk = e / GT, ii = e % GT, k = k0 + kk;
+      const int i = i0 + ii, j = j0 + ii;
+      double2 a = make_double2(0.0, 0.0), bv = make_double2(0.0, 0.0);
+      if (k < K && i < M) {
+        if (CONJ_T) {
+          a = A[(size_t)k + (size_t)i * lda];
+          a.y = -a.y;
+        } else {
+          a = A[(size_t)i + (size_t)k * lda];
+        }
+      }
+      if (k < K && j < NN) bv = B[(size_t)k + (size_t)j * ldb];
+      sA[kk][ii] = make_float2((float)a.x, (float)a.y);
+      sB[kk][ii] = make_float2((float)bv.x, (float)bv.y);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      const float2 a = sA[kk][tx];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float2 bv = sB[kk][ty + 8 * u];
+        acc[u].x = fmaf(a.x, bv.x, fmaf(-a.y, bv.y, acc[u].x));
+        acc[u].y = fmaf(a.x, bv.y, fmaf(a.y, bv.x, acc[u].y));
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = i0 + tx, j = j0 + ty + 8 * u;
+    if (i < M && j < NN) out[(size_t)i + (size_t)j * ldo] = make_double2(acc[u].x, acc[u].y);
+  }
+}
+
 // The factored operator of the refinement, C = L^{-1} V L^{-T}, applied as
 // three products: out = op(Linv) B with Linv the row-major FP64 inverse
 // Cholesky factor (real), B an n x kp complex block (column-major, ld N,
@@ -225,9 +285,9 @@ __global__ void k_mx_pick(Batch b, MixedWs w, const float2* Q32, size_t qstride)
   }
 }
 
-// S = R^H R (Cholesky, upper R) of the kp x kp Gram matrix of X, then
-// W = R^{-1} (upper), so that X W has orthonormal columns. One CTA per step.
-// S = R^H R (upper Cholesky) and W = R^{-1}, one CTA per step, in one
+// W such that X W has orthonormal columns, from the kp x kp Gram matrix S of
+// X. One CTA (256 threads) per step. Usually S^{-1/2} by its series (below);
+// otherwise S = R^H R (upper Cholesky) and W = R^{-1}, in one
 // kp x kp shared-memory buffer: R in the upper triangle, W transposed into
 // the strict lower triangle (W(i, c) at (c, i)) with its diagonal beside it.
 // The factorisation is right-looking (row j of R, then the trailing update in
@@ -244,7 +304,60 @@ __global__ void k_mx_cholinv(Batch b, MixedWs w, const double2* S0, double2* W0,
   double2* wd = B + (size_t)kp * kp;              // diagonal of W
   __shared__ int bad;
   __shared__ double s_inv;
+  __shared__ double red[256];
   if (threadIdx.x == 0) bad = 0;
+  // Nearly orthonormal columns (max |S - I| < 0.05, the usual case): W = S^{-1/2} by its series
+  // I - E/2 + 3/8 E^2 - 5/16 E^3 (E = S - I; truncation 35/128 |E|^4 <= 2e-6, and 1e-28 once the
+  // columns are orthonormal to FP32 accuracy), the linear term in FP64 and the small E^2, E^3
+  // terms in FP32, instead of the FP64 Cholesky below (FP64 runs at 1/64 of FP32 here).
+  double emax = 0.0;
+  for (int e = threadIdx.x; e < kp * kp; e += blockDim.x) {
+    const int i = e % kp, c = e / kp;
+    const double2 v = S[(size_t)i + (size_t)c * ld];
+    emax = fmax(emax, fmax(fabs(v.x - (i == c ? 1.0 : 0.0)), fabs(v.y)));
+  }
+  red[threadIdx.x] = emax;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (red[0] < 0.05) {
+    float2* E = reinterpret_cast<float2*>(cism);  // E, then E^2, kp x kp each
+    float2* E2 = E + (size_t)kp * kp;
+    for (int e = threadIdx.x; e < kp * kp; e += blockDim.x) {
+      const int i = e % kp, c = e / kp;
+      const double2 v = S[(size_t)i + (size_t)c * ld];
+      E[e] = make_float2((float)(v.x - (i == c ? 1.0 : 0.0)), (float)v.y);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kp * kp; e += blockDim.x) {
+      const int i = e % kp, c = e / kp;
+      float2 a = make_float2(0.f, 0.f);
+      for (int k = 0; k < kp; ++k) {
+        const float2 x = E[i + (size_t)k * kp], y = E[k + (size_t)c * kp];
+        a.x = fmaf(x.x, y.x, fmaf(-x.y, y.y, a.x));
+        a.y = fmaf(x.x, y.y, fmaf(x.y, y.x, a.y));
+      }
+      E2[e] = a;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kp * kp; e += blockDim.x) {
+      const int i = e % kp, c = e / kp;
+      float2 a = make_float2(0.f, 0.f);  // (E E^2)(i, c)
+      for (int k = 0; k < kp; ++k) {
+        const float2 x = E[i + (size_t)k * kp], y = E2[k + (size_t)c * kp];
+        a.x = fmaf(x.x, y.x, fmaf(-x.y, y.y, a.x));
+        a.y = fmaf(x.x, y.y, fmaf(x.y, y.x, a.y));
+      }
+      const double2 sv = S[(size_t)i + (size_t)c * ld];
+      const float2 e2 = E2[e];
+      W[(size_t)i + (size_t)c * ld] =
+          make_double2((i == c ? 1.5 : 0.0) - 0.5 * sv.x + (double)(0.375f * e2.x - 0.3125f * a.x),
+                       -0.5 * sv.y + (double)(0.375f * e2.y - 0.3125f * a.y));
+    }
+    return;
+  }
   for (int e = threadIdx.x; e < kp * kp; e += blockDim.x) {
     const int i = e % kp, c = e / kp;
     if (i <= c) B[e] = S[(size_t)i + (size_t)c * ld];
@@ -424,9 +537,14 @@ __global__ void k_mx_final(Batch b, MixedWs w, double rtol) {
 template <bool CT>
 void zgemm_df(const Batch& b, const MixedWs& w, int mc, int nc, int kc, int mmax, int nmax, const double2* A,
               size_t sa, int lda, const double2* B, size_t sb, int ldb, double2* out, size_t so, int ldo,
-              cudaStream_t s) {
+              cudaStream_t s, bool fp32 = false) {
   dim3 grd((mmax + GT - 1) / GT, (nmax + GT - 1) / GT, b.T);
-  k_zgemm_df<CT><<<grd, 256, 0, s>>>(b.nst, w.kp, mc, nc, kc, A, sa, lda, B, sb, ldb, out, so, ldo, b.status, w.st2);
+  if (fp32)
+    k_zgemm_f32<CT><<<grd, 256, 0, s>>>(b.nst, w.kp, mc, nc, kc, A, sa, lda, B, sb, ldb, out, so, ldo, b.status,
+                                        w.st2);
+  else
+    k_zgemm_df<CT><<<grd, 256, 0, s>>>(b.nst, w.kp, mc, nc, kc, A, sa, lda, B, sb, ldb, out, so, ldo, b.status,
+                                       w.st2);
 }
 
 }  // namespace
@@ -517,14 +635,17 @@ void launch_eig_mixed(const Batch& b, const MixedWs& w, double tol, int max_swee
   float* lu3 = reinterpret_cast<float*>(P3);  // the shifted solves' factors: Y (P3) is dead once Y U is formed
   const dim3 rgrd((N + GT - 1) / GT, (KP + GT - 1) / GT, T);
   for (int pass = 0; pass < kPasses; ++pass) {
-    zgemm_df<true>(b, w, DKP, DKP, DN, KP, KP, P0, NN, N, P0, NN, N, Hs, NN, KP, s);   // S = X^H X
-    k_mx_cholinv<<<T, 256, ci_smem, s>>>(b, w, Hs, Ws, NN, KP);                                    // W = R^{-1}
-    zgemm_df<false>(b, w, DN, DKP, DKP, N, KP, P0, NN, N, Ws, NN, KP, P1, NN, N, s);  // X1 = X W
+    // pass 0 orthonormalises X and forms H to the FP32 stage's accuracy (FP32 products); the
+    // residual's products (Y, X U, Y U) are double-float in every pass
+    const bool lo = pass == 0;
+    zgemm_df<true>(b, w, DKP, DKP, DN, KP, KP, P0, NN, N, P0, NN, N, Hs, NN, KP, s, lo);   // S = X^H X
+    k_mx_cholinv<<<T, 256, ci_smem, s>>>(b, w, Hs, Ws, NN, KP);                                        // W = R^{-1}
+    zgemm_df<false>(b, w, DN, DKP, DKP, N, KP, P0, NN, N, Ws, NN, KP, P1, NN, N, s, lo);  // X1 = X W
     // Y = C X1 = L^{-1} (V (L^{-T} X1)); Y lands in P3 and Y U in P2
     k_rgemm_df<true><<<rgrd, 256, 0, s>>>(b, w, P1, P3);                                          // L^{-T} X1
     zgemm_df<false>(b, w, DN, DKP, DN, N, KP, b.vis, NN, N, P3, NN, N, P2, NN, N, s);  // V (.)
     k_rgemm_df<false><<<rgrd, 256, 0, s>>>(b, w, P2, P3);                                         // Y
-    zgemm_df<true>(b, w, DKP, DKP, DN, KP, KP, P1, NN, N, P3, NN, N, Hs, NN, KP, s);  // H = X1^H Y
+    zgemm_df<true>(b, w, DKP, DKP, DN, KP, KP, P1, NN, N, P3, NN, N, Hs, NN, KP, s, lo);  // H = X1^H Y
     k_mx_herm<<<T, 256, 0, s>>>(b, w, Hs, NN, KP);
     if (pass == 0) {                                                                              // H = U th U^H
       k_mx_cvt<true><<<T, 256, 0, s>>>(b, w, Hs, reinterpret_cast<float2*>(Ws), NN, KP);

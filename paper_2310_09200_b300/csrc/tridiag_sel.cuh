@@ -343,6 +343,7 @@ __global__ void __launch_bounds__(kTdThreads, 1) k_td_apply(SelArgs a, float2* Q
     }
     __syncthreads();
     if (cw >= c1) continue;
+    const int nr = (mb + 31) >> 5;  // row slots in use (uniform): later blocks act on fewer rows
     float2 q[CPW][RPL];
 #pragma unroll
     for (int k = 0; k < CPW; ++k) {
@@ -362,6 +363,7 @@ __global__ void __launch_bounds__(kTdThreads, 1) k_td_apply(SelArgs a, float2* Q
       for (int k = 0; k < CPW; ++k) u[k] = make_float2(0.f, 0.f);
 #pragma unroll
       for (int i = 0; i < RPL; ++i) {
+        if (i >= nr) break;
         const int r = lane + 32 * i;
         if (r < mb) {
           const float2 vr = V[(size_t)r * (RB + 1) + j];
@@ -385,6 +387,7 @@ __global__ void __launch_bounds__(kTdThreads, 1) k_td_apply(SelArgs a, float2* Q
       for (int k = 0; k < CPW; ++k) tu[k] = cmul(tj, u[k]);
 #pragma unroll
       for (int i = 0; i < RPL; ++i) {
+        if (i >= nr) break;
         const int r = lane + 32 * i;
         if (r < mb) {
           const float2 vr = V[(size_t)r * (RB + 1) + j];

@@ -301,3 +301,9 @@ def test_sincos_rate_probe_rejects_bad_arguments(lib):
     assert lib.bipp_ss_measure_sincos_rate(-1, 0, C.byref(r)) == bipp_ss.BIPP_ERR_INVALID_ARG
     assert lib.bipp_ss_measure_sincos_rate(-1, 101, C.byref(r)) == bipp_ss.BIPP_ERR_INVALID_ARG
     assert lib.bipp_ss_measure_sincos_rate(-1, 3, None) == bipp_ss.BIPP_ERR_INVALID_ARG
+
+
+def test_fma_rate_probe_rejects_bad_arguments(lib):
+    a, b = C.c_double(1.0), C.c_double(1.0)
+    assert lib.bipp_ss_measure_fma_rates(-1, 0, C.byref(a), C.byref(b)) == bipp_ss.BIPP_ERR_INVALID_ARG
+    assert lib.bipp_ss_measure_fma_rates(-1, 3, None, C.byref(b)) == bipp_ss.BIPP_ERR_INVALID_ARG
