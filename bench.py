@@ -63,8 +63,9 @@ DTYPES = {"fp64": "f64", "fp32": "f64 eig + f32 synth",
 
 
 EIG_DESC = {"jacobi64": "fp64 parallel-order Jacobi (off(C) <= 1e-13 ||C||_F)",
-            "mixed": ("fp32 Householder tridiagonalisation + implicit QR + back-transformation, then fp64 "
-                      "Rayleigh-Ritz refinement of the n_eig+16 leading pairs (residual <= 1e-10 ||C||_F)")}
+            "mixed": ("fp32 Householder tridiagonalisation, the n_eig+16 leading pairs of the tridiagonal form "
+                      "(multisection, inverse iteration) back-transformed, then double-float Rayleigh-Ritz "
+                      "refinement of those pairs (residual <= 1e-10 ||C||_F)")}
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_synth_tc launch of the

@@ -64,7 +64,12 @@ __device__ __forceinline__ bool mx_skip(const int* status, const int* st2, int t
 // conjugate transpose, all operands column-major with per-problem strides,
 // with ~2^-48 relative rounding per operation instead of FP64's 2^-53, at
 // several times the FP64 pipe's rate. Operands are split into hi/lo floats
-// once per tile.
+// once per tile. Column blocks of 8 that lie wholly past the problem's
+// width are skipped (a warp-uniform test), so kp = 80 columns cost 80, not
+// the 96 of three 32-wide tiles. With CONJ_T the product is one of the
+// refinement's Hermitian kp x kp matrices (X^H X, X1^H C X1): only the tiles
+// on and above the diagonal are computed, and each tile above it is also
+// written, conjugated, to its mirror below.
 template <bool CONJ_T>
 __global__ void k_zgemm_df(const int* nst, const int* kp, int mc, int nc, int kc, const double2* A, size_t sa,
                            int lda, const double2* B, size_t sb, int ldb, double2* out, size_t so, int ldo,
@@ -74,13 +79,14 @@ __global__ void k_zgemm_df(const int* nst, const int* kp, int mc, int nc, int kc
   const int n = nst[t], k_p = kp[t];
   const int M = dim_of(mc, n, k_p), NN = dim_of(nc, n, k_p), K = dim_of(kc, n, k_p);
   const int i0 = blockIdx.x * GT, j0 = blockIdx.y * GT;
-  if (i0 >= M || j0 >= NN) return;
+  if (i0 >= M || j0 >= NN || (CONJ_T && blockIdx.x > blockIdx.y)) return;
   A += (size_t)t * sa;
   B += (size_t)t * sb;
   out += (size_t)t * so;
   __shared__ float4 sA[GK][GT + 1];  // (re hi, re lo, im hi, im lo)
   __shared__ float4 sB[GK][GT + 1];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int nu = min(4, max(0, (NN - j0 - ty + 7) >> 3));  // column blocks u < nu hold columns < NN
   float acc[4][4];  // [u][re hi, re lo, im hi, im lo]
 #pragma unroll
   for (int u = 0; u < 4; ++u)
@@ -114,6 +120,7 @@ __global__ void k_zgemm_df(const int* nst, const int* kp, int mc, int nc, int kc
       const float4 a = sA[kk][tx];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
+        if (u >= nu) break;
         const float4 bv = sB[kk][ty + 8 * u];
         df::mac(acc[u][0], acc[u][1], a.x, a.y, bv.x, bv.y);    // re += ar br
         df::mac(acc[u][0], acc[u][1], -a.z, -a.w, bv.z, bv.w);  //     - ai bi
@@ -131,9 +138,11 @@ __global__ void k_zgemm_df(const int* nst, const int* kp, int mc, int nc, int kc
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int i = i0 + tx, j = j0 + ty + 8 * u;
-    if (i < M && j < NN)
-      out[(size_t)i + (size_t)j * ldo] = make_double2(df::to_double(acc[u][0], acc[u][1]),
-                                                      df::to_double(acc[u][2], acc[u][3]));
+    if (i < M && j < NN) {
+      const double2 v = make_double2(df::to_double(acc[u][0], acc[u][1]), df::to_double(acc[u][2], acc[u][3]));
+      out[(size_t)i + (size_t)j * ldo] = v;
+      if (CONJ_T && blockIdx.x < blockIdx.y) out[(size_t)j + (size_t)i * ldo] = make_double2(v.x, -v.y);
+    }
   }
 }
 
@@ -150,13 +159,14 @@ __global__ void k_zgemm_f32(const int* nst, const int* kp, int mc, int nc, int k
   const int n = nst[t], k_p = kp[t];
   const int M = dim_of(mc, n, k_p), NN = dim_of(nc, n, k_p), K = dim_of(kc, n, k_p);
   const int i0 = blockIdx.x * GT, j0 = blockIdx.y * GT;
-  if (i0 >= M || j0 >= NN) return;
+  if (i0 >= M || j0 >= NN || (CONJ_T && blockIdx.x > blockIdx.y)) return;
   A += (size_t)t * sa;
   B += (size_t)t * sb;
   out += (size_t)t * so;
   __shared__ float2 sA[GK][GT + 1];
   __shared__ float2 sB[GK][GT + 1];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int nu = min(4, max(0, (NN - j0 - ty + 7) >> 3));
   float2 acc[4];
 #pragma unroll
   for (int u = 0; u < 4; ++u) acc[u] = make_float2(0.f, 0.f);
@@ -183,6 +193,7 @@ __global__ void k_zgemm_f32(const int* nst, const int* kp, int mc, int nc, int k
       const float2 a = sA[kk][tx];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
+        if (u >= nu) break;
         const float2 bv = sB[kk][ty + 8 * u];
         acc[u].x = fmaf(a.x, bv.x, fmaf(-a.y, bv.y, acc[u].x));
         acc[u].y = fmaf(a.x, bv.y, fmaf(a.y, bv.x, acc[u].y));
@@ -193,7 +204,10 @@ __global__ void k_zgemm_f32(const int* nst, const int* kp, int mc, int nc, int k
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int i = i0 + tx, j = j0 + ty + 8 * u;
-    if (i < M && j < NN) out[(size_t)i + (size_t)j * ldo] = make_double2(acc[u].x, acc[u].y);
+    if (i < M && j < NN) {
+      out[(size_t)i + (size_t)j * ldo] = make_double2(acc[u].x, acc[u].y);
+      if (CONJ_T && blockIdx.x < blockIdx.y) out[(size_t)j + (size_t)i * ldo] = make_double2(acc[u].x, -acc[u].y);
+    }
   }
 }
 
@@ -217,6 +231,7 @@ __global__ void k_rgemm_df(const Batch b, const MixedWs w, const double2* B0, do
   __shared__ float2 sA[GK][GT + 1];  // (hi, lo)
   __shared__ float4 sB[GK][GT + 1];  // (re hi, re lo, im hi, im lo)
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int nu = min(4, max(0, (k_p - j0 - ty + 7) >> 3));
   float acc[4][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
@@ -244,6 +259,7 @@ __global__ void k_rgemm_df(const Batch b, const MixedWs w, const double2* B0, do
       const float2 a = sA[kk][tx];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
+        if (u >= nu) break;
         const float4 bv = sB[kk][ty + 8 * u];
         df::mac(acc[u][0], acc[u][1], a.x, a.y, bv.x, bv.y);
         df::mac(acc[u][2], acc[u][3], a.x, a.y, bv.z, bv.w);
