@@ -67,5 +67,35 @@ __device__ __forceinline__ void renorm(float& sh, float& sl) {
 
 __device__ __forceinline__ double to_double(float hi, float lo) { return (double)hi + (double)lo; }
 
+// Two independent accumulations at once on the packed FP32 pipe operations of
+// sm_100+ (__fmul2_rn, __fadd2_rn, __ffma2_rn, per component the rounding of
+// the scalar ones): component c of (sh, sl) += (ah + al) * (bh + bl), with the
+// same roundings, term for term, as mac() above, in 12 instructions for the
+// pair instead of 24. The packed operations take no negated operands, so the
+// caller passes nah = -ah and nal = -al (exact) beside ah, and each
+// subtraction x - y is the exact FMA y * (-1) + x.
+__device__ __forceinline__ void mac2(float2& sh, float2& sl, float2 ah, float2 nah, float2 nal, float2 bh,
+                                     float2 bl) {
+  const float2 m1 = make_float2(-1.0f, -1.0f);
+  const float2 ph = __fmul2_rn(ah, bh);
+  float2 npl = __ffma2_rn(nah, bh, ph);  // -(ah bh - ph): the product's rounding error, negated
+  npl = __ffma2_rn(nah, bl, npl);
+  npl = __ffma2_rn(nal, bh, npl);
+  const float2 t = __fadd2_rn(sh, ph);
+  const float2 z = __ffma2_rn(sh, m1, t);                                    // t - sh
+  const float2 e = __fadd2_rn(__ffma2_rn(__ffma2_rn(z, m1, t), m1, sh),     // sh - (t - z)
+                              __ffma2_rn(z, m1, ph));                        // + (ph - z)
+  sh = t;
+  sl = __fadd2_rn(sl, __ffma2_rn(npl, m1, e));  // sl + (e + pl)
+}
+
+// renorm() on both components.
+__device__ __forceinline__ void renorm2(float2& sh, float2& sl) {
+  const float2 m1 = make_float2(-1.0f, -1.0f);
+  const float2 t = __fadd2_rn(sh, sl);
+  sl = __ffma2_rn(__ffma2_rn(sh, m1, t), m1, sl);  // sl - (t - sh)
+  sh = t;
+}
+
 }  // namespace df
 }  // namespace bipp

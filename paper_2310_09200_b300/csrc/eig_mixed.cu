@@ -64,12 +64,24 @@ __device__ __forceinline__ bool mx_skip(const int* status, const int* st2, int t
 // conjugate transpose, all operands column-major with per-problem strides,
 // with ~2^-48 relative rounding per operation instead of FP64's 2^-53, at
 // several times the FP64 pipe's rate. Operands are split into hi/lo floats
-// once per tile. Column blocks of 8 that lie wholly past the problem's
+// once per tile. The real and imaginary accumulations of an output run side
+// by side on the packed FP32 operations (df::mac2): re += ar br, im += ar bi
+// as one packed step and re += (-ai) bi, im += ai br as the next, so the
+// operands are staged in shared memory already paired (and negated where
+// mac2 needs it). Column blocks of 8 that lie wholly past the problem's
 // width are skipped (a warp-uniform test), so kp = 80 columns cost 80, not
 // the 96 of three 32-wide tiles. With CONJ_T the product is one of the
 // refinement's Hermitian kp x kp matrices (X^H X, X1^H C X1): only the tiles
 // on and above the diagonal are computed, and each tile above it is also
 // written, conjugated, to its mirror below.
+struct DfA2 {  // one element a of op(A), paired for the two packed steps
+  float2 h1, nh1, nl1;  // (ar, ar) hi, and -(ar, ar) hi / lo
+  float2 h2, nh2, nl2;  // (-ai, ai) hi, and -(-ai, ai) hi / lo
+};
+struct DfB2 {  // one element b of B
+  float2 h1, l1;  // (br, bi) hi / lo
+  float2 h2, l2;  // (bi, br) hi / lo
+};
 template <bool CONJ_T>
 __global__ void k_zgemm_df(const int* nst, const int* kp, int mc, int nc, int kc, const double2* A, size_t sa,
                            int lda, const double2* B, size_t sb, int ldb, double2* out, size_t so, int ldo,
@@ -83,15 +95,13 @@ __global__ void k_zgemm_df(const int* nst, const int* kp, int mc, int nc, int kc
   A += (size_t)t * sa;
   B += (size_t)t * sb;
   out += (size_t)t * so;
-  __shared__ float4 sA[GK][GT + 1];  // (re hi, re lo, im hi, im lo)
-  __shared__ float4 sB[GK][GT + 1];
+  __shared__ DfA2 sA[GK][GT + 1];
+  __shared__ DfB2 sB[GK][GT + 1];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int nu = min(4, max(0, (NN - j0 - ty + 7) >> 3));  // column blocks u < nu hold columns < NN
-  float acc[4][4];  // [u][re hi, re lo, im hi, im lo]
+  float2 ah[4], al[4];  // [u] (re, im) hi and lo accumulators
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) acc[u][c] = 0.f;
+  for (int u = 0; u < 4; ++u) ah[u] = al[u] = make_float2(0.f, 0.f);
   for (int k0 = 0; k0 < K; k0 += GK) {
     for (int e = threadIdx.x; e < GK * GT; e += blockDim.x) {
       const int kk = e / GT, ii = e % GT, k = k0 + kk;
@@ -106,40 +116,47 @@ __global__ void k_zgemm_df(const int* nst, const int* kp, int mc, int nc, int kc
         }
       }
       if (k < K && j < NN) bv = B[(size_t)k + (size_t)j * ldb];
-      float4 fa, fb;
-      df::split(a.x, fa.x, fa.y);
-      df::split(a.y, fa.z, fa.w);
-      df::split(bv.x, fb.x, fb.y);
-      df::split(bv.y, fb.z, fb.w);
-      sA[kk][ii] = fa;
-      sB[kk][ii] = fb;
+      float arh, arl, aih, ail, brh, brl, bih, bil;
+      df::split(a.x, arh, arl);
+      df::split(a.y, aih, ail);
+      df::split(bv.x, brh, brl);
+      df::split(bv.y, bih, bil);
+      DfA2 pa;
+      pa.h1 = make_float2(arh, arh);
+      pa.nh1 = make_float2(-arh, -arh);
+      pa.nl1 = make_float2(-arl, -arl);
+      pa.h2 = make_float2(-aih, aih);
+      pa.nh2 = make_float2(aih, -aih);
+      pa.nl2 = make_float2(ail, -ail);
+      DfB2 pb;
+      pb.h1 = make_float2(brh, bih);
+      pb.l1 = make_float2(brl, bil);
+      pb.h2 = make_float2(bih, brh);
+      pb.l2 = make_float2(bil, brl);
+      sA[kk][ii] = pa;
+      sB[kk][ii] = pb;
     }
     __syncthreads();
 #pragma unroll 4
     for (int kk = 0; kk < GK; ++kk) {
-      const float4 a = sA[kk][tx];
+      const DfA2 a = sA[kk][tx];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         if (u >= nu) break;
-        const float4 bv = sB[kk][ty + 8 * u];
-        df::mac(acc[u][0], acc[u][1], a.x, a.y, bv.x, bv.y);    // re += ar br
-        df::mac(acc[u][0], acc[u][1], -a.z, -a.w, bv.z, bv.w);  //     - ai bi
-        df::mac(acc[u][2], acc[u][3], a.x, a.y, bv.z, bv.w);    // im += ar bi
-        df::mac(acc[u][2], acc[u][3], a.z, a.w, bv.x, bv.y);    //     + ai br
+        const DfB2 bv = sB[kk][ty + 8 * u];
+        df::mac2(ah[u], al[u], a.h1, a.nh1, a.nl1, bv.h1, bv.l1);  // (re, im) += ar (br, bi)
+        df::mac2(ah[u], al[u], a.h2, a.nh2, a.nl2, bv.h2, bv.l2);  //          + (-ai, ai) (bi, br)
       }
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      df::renorm(acc[u][0], acc[u][1]);
-      df::renorm(acc[u][2], acc[u][3]);
-    }
+    for (int u = 0; u < 4; ++u) df::renorm2(ah[u], al[u]);
     __syncthreads();
   }
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int i = i0 + tx, j = j0 + ty + 8 * u;
     if (i < M && j < NN) {
-      const double2 v = make_double2(df::to_double(acc[u][0], acc[u][1]), df::to_double(acc[u][2], acc[u][3]));
+      const double2 v = make_double2(df::to_double(ah[u].x, al[u].x), df::to_double(ah[u].y, al[u].y));
       out[(size_t)i + (size_t)j * ldo] = v;
       if (CONJ_T && blockIdx.x < blockIdx.y) out[(size_t)j + (size_t)i * ldo] = make_double2(v.x, -v.y);
     }
@@ -228,15 +245,16 @@ __global__ void k_rgemm_df(const Batch b, const MixedWs w, const double2* B0, do
   const double* Linv = b.Linv + (size_t)t * NN;
   const double2* B = B0 + (size_t)t * NN;
   double2* out = out0 + (size_t)t * NN;
-  __shared__ float2 sA[GK][GT + 1];  // (hi, lo)
-  __shared__ float4 sB[GK][GT + 1];  // (re hi, re lo, im hi, im lo)
+  struct RA {
+    float2 h, nh, nl;  // (a, a) hi, -(a, a) hi / lo
+  };
+  __shared__ RA sA[GK][GT + 1];
+  __shared__ float4 sB[GK][GT + 1];  // (re hi, im hi, re lo, im lo)
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int nu = min(4, max(0, (k_p - j0 - ty + 7) >> 3));
-  float acc[4][4];
+  float2 ah[4], al[4];  // [u] (re, im) hi and lo accumulators
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) acc[u][c] = 0.f;
+  for (int u = 0; u < 4; ++u) ah[u] = al[u] = make_float2(0.f, 0.f);
   const int kbeg = UPPER ? (i0 / GK) * GK : 0, kend = UPPER ? n : min(n, i0 + GT);
   for (int k0 = kbeg; k0 < kend; k0 += GK) {
     for (int e = threadIdx.x; e < GK * GT; e += blockDim.x) {
@@ -245,39 +263,37 @@ __global__ void k_rgemm_df(const Batch b, const MixedWs w, const double2* B0, do
       double a = 0.0;
       if (k < n && i < n) a = UPPER ? (k >= i ? Linv[(size_t)k * N + i] : 0.0) : (k <= i ? Linv[(size_t)i * N + k] : 0.0);
       const double2 bv = (k < n && j < k_p) ? B[(size_t)k + (size_t)j * N] : make_double2(0.0, 0.0);
-      float2 fa;
-      float4 fb;
-      df::split(a, fa.x, fa.y);
-      df::split(bv.x, fb.x, fb.y);
-      df::split(bv.y, fb.z, fb.w);
-      sA[kk][ii] = fa;
-      sB[kk][ii] = fb;
+      float ahi, alo, brh, brl, bih, bil;
+      df::split(a, ahi, alo);
+      df::split(bv.x, brh, brl);
+      df::split(bv.y, bih, bil);
+      RA pa;
+      pa.h = make_float2(ahi, ahi);
+      pa.nh = make_float2(-ahi, -ahi);
+      pa.nl = make_float2(-alo, -alo);
+      sA[kk][ii] = pa;
+      sB[kk][ii] = make_float4(brh, bih, brl, bil);
     }
     __syncthreads();
 #pragma unroll 4
     for (int kk = 0; kk < GK; ++kk) {
-      const float2 a = sA[kk][tx];
+      const RA a = sA[kk][tx];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         if (u >= nu) break;
         const float4 bv = sB[kk][ty + 8 * u];
-        df::mac(acc[u][0], acc[u][1], a.x, a.y, bv.x, bv.y);
-        df::mac(acc[u][2], acc[u][3], a.x, a.y, bv.z, bv.w);
+        df::mac2(ah[u], al[u], a.h, a.nh, a.nl, make_float2(bv.x, bv.y), make_float2(bv.z, bv.w));
       }
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      df::renorm(acc[u][0], acc[u][1]);
-      df::renorm(acc[u][2], acc[u][3]);
-    }
+    for (int u = 0; u < 4; ++u) df::renorm2(ah[u], al[u]);
     __syncthreads();
   }
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int i = i0 + tx, j = j0 + ty + 8 * u;
     if (i < n && j < k_p)
-      out[(size_t)i + (size_t)j * N] = make_double2(df::to_double(acc[u][0], acc[u][1]),
-                                                    df::to_double(acc[u][2], acc[u][3]));
+      out[(size_t)i + (size_t)j * N] = make_double2(df::to_double(ah[u].x, al[u].x), df::to_double(ah[u].y, al[u].y));
   }
 }
 

@@ -90,12 +90,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 // (BF16), by adding and subtracting 1.5 * 2^12 (2^15), whose FP32 ulp is that
 // step; such multiples in [-1, 1] are exact in the 16-bit type. lo = x - hi is
 // exact in FP32 and |lo| <= 2^-12 (2^-9), so its 16-bit rounding costs at most
-// 2^-24 (2^-17) absolute.
+// 2^-24 (2^-17) absolute. The two values go through the packed FP32 pipe
+// operations of sm_100+ (__fadd2_rn, __ffma2_rn: per component the same
+// rounding as the scalar ones), three instructions instead of six.
 template <bool FP16>
 __device__ __forceinline__ void split2(float x0, float x1, uint32_t* hi, uint32_t* lo) {
   constexpr float M = FP16 ? 6144.0f : 49152.0f;
-  const float h0 = __fsub_rn(__fadd_rn(x0, M), M), h1 = __fsub_rn(__fadd_rn(x1, M), M);
-  const float l0 = __fsub_rn(x0, h0), l1 = __fsub_rn(x1, h1);
+  const float2 x = make_float2(x0, x1);
+  const float2 hh = __fadd2_rn(__fadd2_rn(x, make_float2(M, M)), make_float2(-M, -M));
+  const float2 ll = __ffma2_rn(hh, make_float2(-1.0f, -1.0f), x);  // x - hi, exact
+  const float h0 = hh.x, h1 = hh.y, l0 = ll.x, l1 = ll.y;
   if constexpr (FP16) {
     __half2 h = __floats2half2_rn(h0, h1);
     __half2 l = __floats2half2_rn(l0, l1);
