@@ -64,7 +64,9 @@ extern "C" {
                                   operands, so it meets the FP32 path's 1e-5 relative L2 per level
                                   up to ~512 stations (6.5e-6 measured at 512); the error grows with
                                   K = 2 n_st (1.27e-5 measured at 1024), bounded by FP32 summation
-                                  over K terms, 2 n_st 2^-24 */
+                                  over K terms, 2 n_st 2^-24. Both split forms take station
+                                  coordinates below 2^28 wavelengths (|p|/wl); a step with a station
+                                  farther out fails with BIPP_ERR_UNSUPPORTED and adds nothing */
 
 #define BIPP_FILTER_LSQ 0 /* d_e = mu_e (Sec. 2.6, least-squares image) */
 #define BIPP_FILTER_STD 1 /* d_e = 1    (Sec. 2.6, standardised image) */

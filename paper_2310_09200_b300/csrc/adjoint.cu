@@ -489,6 +489,11 @@ int run_tc(int64_t n_pix, const double* d_pix, double wl, int T, int N, int K, i
   if (e == cudaSuccess) e = es;
   if (rc == BIPP_OK) rc = err_of(e);
   if (rc == BIPP_OK && tc_read_status(w) != 0) rc = BIPP_ERR_DEVICE_TIMEOUT;
+  if (rc == BIPP_OK && sc.b.flag) {  // a station beyond the phase's range (k_tc_pack): nothing was computed
+    int fl = 0;
+    if (cudaMemcpy(&fl, sc.b.flag, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) rc = BIPP_ERR_CUDA;
+    else if (fl & kStatusRange) rc = BIPP_ERR_UNSUPPORTED;
+  }
   return rc;
 }
 

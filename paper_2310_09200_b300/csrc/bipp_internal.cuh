@@ -15,6 +15,7 @@ constexpr int kMaxEig = 1024;
 constexpr int kStatusNotPD = 1;         // Cholesky met a non-positive (or NaN) pivot
 constexpr int kStatusNotConverged = 2;  // Jacobi hit its sweep cap
 constexpr int kStatusTimeout = 4;       // a bounded device wait gave up
+constexpr int kStatusRange = 16;        // a station lies beyond the tensor-core phase's range (2^28 wavelengths)
 
 // Device-side view of one batch of T steps. Step t uses the leading
 // nst[t] x nst[t] block of every per-step N x N array (N = n_max).

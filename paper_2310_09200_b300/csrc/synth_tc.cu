@@ -33,13 +33,20 @@
 // and returns.
 //
 // Phase. Only frac(<r, q_i>) matters (q_i = p_i/wl in cycles, |<r, q_i>| up to
-// ~4e4 at 65 km). With R = round(r 2^40) and Q = round(q 2^24) as 64-bit
-// integers, sum_c R_c Q_c = <r, q> 2^64 up to the rounding of R and Q, and
-// its value mod 2^64 is frac(<r, q>) 2^64: the wrapped low 64 bits of the
-// integer products are exact. Only their upper 32 bits are needed, which for
-// each component are hi32(Rlo Qlo) + Rhi Qlo + Rlo Qhi (mod 2^32); dropping
-// the carries out of the three low words costs < 3 2^-32 cycles. Error:
-// 2^-41 |q| + 2^-25 per component (~1e-7 cycles at |q| = 4e4).
+// ~4e4 at 65 km). Per component, r = R 2^-29 + rl (R = round(r 2^29), a
+// 32-bit integer, |rl| <= 2^-30) and q = QH / 8 + ql (QH = round(8 q), a 32-bit
+// integer, |ql| <= 1/16), so that
+//     r q = R QH 2^-32 + r ql + rl q - rl ql.
+// The first term taken mod 1 is the wrapped 32-bit product R QH as a fraction
+// of 2^32 (one integer multiply-add per component: the sum over the three
+// components wraps exactly), the next two are small (|r ql| <= 1/16,
+// |rl q| <= 2^-15) and go to FP32 with ~2^-28 cycles of error, and the last
+// (<= 2^-34) is dropped. Per pixel-station pair: three 32-bit IMADs at half
+// rate and six FP32 FMAs (packed two stations at a time), against the nine
+// IMADs (three of them at quarter rate, mul.hi) of a 64-bit fixed-point sum.
+// Error ~2^-25 cycles (the FP32 rounding of the 32-bit fraction); station
+// coordinates up to 2^28 wavelengths from the origin (farther ones mark the
+// step kStatusRange and the batch commits nothing).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <math.h>
@@ -63,7 +70,8 @@ constexpr int kRows = 128;            // pixels per tile = UMMA M
 constexpr int kStations = 32;         // stations per stage (64 K-elements)
 constexpr int kABytes = kRows * 128;  // one A operand image per stage (hi or lo)
 constexpr int kMaxStages = 4;
-constexpr int kQWin = 16;  // chunks of station words staged per window (two windows in shared memory)
+constexpr int kQWin = 8;  // chunks of station words staged per window (two windows in shared memory)
+constexpr uint32_t kQBytes = 40;  // phase words per station (k_tc_pack: 20 words per pair of stations)
 static_assert((kQWin & (kQWin - 1)) == 0, "window of a power-of-two chunk count");
 
 using namespace tcx;
@@ -85,7 +93,7 @@ template <int MAXL, bool FP16, bool FUSE, int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
     k_synth_tc(Batch b, Pixels px, int n_level, double* img, TcYOut yo, const TcStep* __restrict__ steps,
                const unsigned char* __restrict__ Bpack, const float* __restrict__ scales,
-               const uint32_t* __restrict__ qfix, int qfix_stride, const int2* __restrict__ lwt, int n_stages,
+               const uint32_t* __restrict__ qph, int qph_stride, const int2* __restrict__ lwt, int n_stages,
                int stage_bytes, int ncols_buf, int* status) {
   if (*b.flag) return;  // a step of the batch failed: commit nothing
   extern __shared__ unsigned char smem_raw[];
@@ -140,13 +148,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     // in two buffers after the stage ring: the window after the current one
     // (in tile, step, chunk order) is copied with cp.async while the current
     // one is produced, so the per-stage reads hit shared memory, not L2.
-    constexpr uint32_t kQWinBytes = kQWin * kStations * 32u;
+    constexpr uint32_t kQWinBytes = kQWin * kStations * kQBytes;
     const uint32_t qsm0 = smem0 + (uint32_t)n_stages * (uint32_t)stage_bytes;
     uint32_t qbuf = 0, qphase = 0;
     auto q_prefetch = [&](int tn, int c0, uint32_t buf) {
       const unsigned char* src =
-          reinterpret_cast<const unsigned char*>(qfix + ((size_t)tn * qfix_stride + (size_t)c0 * kStations) * 8);
-      const uint32_t nbytes = (uint32_t)min(kQWin, steps[tn].n_chunks - c0) * kStations * 32u;
+          reinterpret_cast<const unsigned char*>(qph + ((size_t)tn * qph_stride + (size_t)c0 * kStations) * (kQBytes / 4));
+      const uint32_t nbytes = (uint32_t)min(kQWin, steps[tn].n_chunks - c0) * kStations * kQBytes;
       for (uint32_t o = threadIdx.x * 16u; o < nbytes; o += kProdWarps * 32u * 16u)
         cp_async16(qsm0 + buf * kQWinBytes + o, src + o);
       cp_async_commit();
@@ -260,13 +268,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
       const int64_t r = (int64_t)tile * kRows + row;
-      uint32_t rl[3], rh[3];  // R = round(r 2^40)
+      double rx[3];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const long long R = (r < px.n) ? __double2ll_rn(px.xyz[(size_t)c * px.n + r] * 1099511627776.0) : 0ll;
-        rl[c] = (uint32_t)(unsigned long long)R;
-        rh[c] = (uint32_t)((unsigned long long)R >> 32);
-      }
+      for (int c = 0; c < 3; ++c) rx[c] = (r < px.n) ? px.xyz[(size_t)c * px.n + r] : 0.0;
+      const PhasePix pp = phase_pix(rx);
       for (int t = 0; t < T && ok; ++t) {
         const int nch = steps[t].n_chunks;
         uint32_t qcur = 0;
@@ -303,20 +308,17 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t a_hi = smem0 + s * stage_bytes + row * 128;
           const uint32_t a_lo = a_hi + kABytes;
           {
-            // the thread's eight stations side by side (loads, phases, sincos, splits), so
-            // that their independent dependency chains interleave; padded stations have
-            // Q = 0 and zero B rows
-            const uint32_t qs = qcur + (uint32_t)((c & (kQWin - 1)) * kStations + 8 * wg) * 32u;
-            uint4 qa[8];
-            uint2 qb[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              qa[j] = ld_shared_v4(qs + 32u * j);
-              qb[j] = ld_shared_v2(qs + 32u * j + 16u);
-            }
+            // the thread's eight stations side by side (phases, sincos, splits), so that
+            // their independent dependency chains interleave; padded stations have zero
+            // phase words and zero B rows
+            const uint32_t qs = qcur + (uint32_t)((c & (kQWin - 1)) * kStations + 8 * wg) * kQBytes;
             float ph[8], cs[8], sn[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) ph[j] = phase_rad_fixed(rl, rh, qa[j], qb[j]);
+            for (int g = 0; g < 4; ++g) {
+              const float2 p2 = phase_rad_pair(pp, qs + 2u * kQBytes * g);
+              ph[2 * g] = p2.x;
+              ph[2 * g + 1] = p2.y;
+            }
 #pragma unroll
             for (int j = 0; j < 8; ++j) __sincosf(ph[j], &sn[j], &cs[j]);
 #pragma unroll
@@ -491,12 +493,17 @@ __global__ void k_tc_scale(Batch b, float* scales) {
 
 // B chunk c of step t: rows n < ncols (K-major, 128 bytes = 64 K-elements),
 // hi image then lo image, 16-byte pieces XOR-swizzled by (row & 7).
-// Also the chunk's station words for the phase: Q = round(p/wl 2^24) per
-// component as (low, high) 32-bit words, 8 words per station, zero for the
-// padded stations i >= n.
+// Also the chunk's station words for the phase: for the adjoint's kernel,
+// Q = round(p/wl 2^24) per component as (low, high) 32-bit words, 8 words per
+// station; for the synthesis, per pair of stations (a, b) 20 words: QH_x,
+// QH_y, QH_z (QH = round(8 p/wl), 32-bit integers), then 2 pi ql and 2 pi q
+// per component in FP32 (ql = p/wl - QH/8), each word for a then b, and two
+// zero words (header comment). Padded stations i >= n have zero words. A
+// station with |8 p/wl| >= 2^31 marks its step kStatusRange (and the batch
+// flag, so that nothing is committed).
 template <bool FP16>
 __global__ void k_tc_pack(Batch b, const TcStep* steps, unsigned char* Bpack, const float* scales, uint32_t* qfix,
-                          int qfix_stride, int2* lwt) {
+                          uint32_t* qph, int qfix_stride, int2* lwt) {
   const int t = blockIdx.y, c = blockIdx.x;
   const TcStep st = steps[t];
   if (c >= st.n_chunks) return;
@@ -525,6 +532,33 @@ __global__ void k_tc_pack(Batch b, const TcStep* steps, unsigned char* Bpack, co
     uint4* dst = reinterpret_cast<uint4*>(qfix + ((size_t)t * qfix_stride + i) * 8);
     dst[0] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
     dst[1] = make_uint4(wv[4], wv[5], wv[6], wv[7]);
+    uint32_t* g = qph + ((size_t)t * qfix_stride + (i & ~1)) * (kQBytes / 4);
+    const int sl = i & 1;
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      int QH = 0;
+      float ql = 0.f, qf = 0.f;
+      if (i < n) {
+        const double q = b.st[((size_t)t * 3 + k) * N + i] / b.wl[t];
+        const double q8 = rint(8.0 * q);
+        if (fabs(q8) < 2147483647.0) {
+          QH = (int)q8;
+          ql = (float)(6.283185307179586 * (q - 0.125 * q8));
+          qf = (float)(6.283185307179586 * q);
+        } else {
+          bad = true;
+        }
+      }
+      g[2 * k + sl] = (uint32_t)QH;
+      g[6 + 2 * k + sl] = __float_as_uint(ql);
+      g[12 + 2 * k + sl] = __float_as_uint(qf);
+    }
+    g[18 + sl] = 0u;
+    if (bad) {
+      if (b.status) atomicOr(b.status + t, kStatusRange);
+      atomicOr(b.flag, kStatusRange);
+    }
   }
   const double scale = FP16 ? (double)scales[t] : 1.0;
   unsigned char* base = Bpack + st.b_off + (size_t)c * st.ncols * 256;
@@ -597,6 +631,7 @@ int tc_alloc(TcWorkspace* w, int T, int N, int K) {
   if (cudaMalloc(&w->scale, sizeof(float) * T) != cudaSuccess) return -1;
   w->qfix_stride = n_chunks_for(N) * kStations;
   if (cudaMalloc(&w->qfix, sizeof(uint32_t) * 8 * (size_t)T * w->qfix_stride) != cudaSuccess) return -1;
+  if (cudaMalloc(&w->qph, kQBytes * (size_t)T * w->qfix_stride) != cudaSuccess) return -1;
   if (cudaMalloc(&w->lwt, sizeof(int2) * (size_t)T * kTcMaxEig) != cudaSuccess) return -1;
   if (cudaMalloc(&w->status, 2 * sizeof(int)) != cudaSuccess) return -1;
   if (cudaMemset(w->status, 0, 2 * sizeof(int)) != cudaSuccess) return -1;
@@ -610,6 +645,7 @@ void tc_free(TcWorkspace* w) {
   if (w->h_steps) cudaFreeHost(w->h_steps);
   if (w->scale) cudaFree(w->scale);
   if (w->qfix) cudaFree(w->qfix);
+  if (w->qph) cudaFree(w->qph);
   if (w->lwt) cudaFree(w->lwt);
   if (w->status) cudaFree(w->status);
   *w = TcWorkspace{};
@@ -629,7 +665,7 @@ int tc_read_status(TcWorkspace* w) {
 namespace {
 
 int stage_bytes_for(int ncols_max) { return 2 * kABytes + 2 * ncols_max * 128; }
-constexpr int kQStageBytes = 2 * kQWin * kStations * 32;  // the two station-word windows
+constexpr int kQStageBytes = 2 * kQWin * kStations * (int)kQBytes;  // the two station-word windows
 // Dynamic shared memory: the stage ring, the station-word windows and 1 KB of
 // alignment slack, within 227 KB less room for the static barriers.
 constexpr int kDynSmemMax = 227 * 1024 - 1024 - 512;
@@ -687,7 +723,7 @@ int launch_kernel(const Batch& b, const Pixels& px, int n_level, double* img, co
       rc = -7;
       return;
     }
-    k_synth_tc<ML, F16, FS, 0><<<grid, kThreads, smem, s>>>(b, px, n_level, img, TcYOut{}, w->steps, w->B, w->scale, w->qfix,
+    k_synth_tc<ML, F16, FS, 0><<<grid, kThreads, smem, s>>>(b, px, n_level, img, TcYOut{}, w->steps, w->B, w->scale, w->qph,
                                                       w->qfix_stride, w->lwt, n_stages,
                                                      stage_bytes, p.ncols_buf, w->status);
   });
@@ -735,10 +771,10 @@ int tc_enqueue_pack(const Batch& b, const TcPlan& p, TcWorkspace* w, cudaStream_
   if (cudaMemsetAsync(w->status, 0, sizeof(int), s) != cudaSuccess) return -5;
   if (p.fp16) k_tc_scale<<<T, 256, 0, s>>>(b, w->scale);
   if (p.fp16)
-    k_tc_pack<true><<<dim3(p.max_chunks, T), 256, 0, s>>>(b, w->steps, w->B, w->scale, w->qfix, w->qfix_stride,
+    k_tc_pack<true><<<dim3(p.max_chunks, T), 256, 0, s>>>(b, w->steps, w->B, w->scale, w->qfix, w->qph, w->qfix_stride,
                                                           w->lwt);
   else
-    k_tc_pack<false><<<dim3(p.max_chunks, T), 256, 0, s>>>(b, w->steps, w->B, w->scale, w->qfix, w->qfix_stride,
+    k_tc_pack<false><<<dim3(p.max_chunks, T), 256, 0, s>>>(b, w->steps, w->B, w->scale, w->qfix, w->qph, w->qfix_stride,
                                                            w->lwt);
   return cudaGetLastError() == cudaSuccess ? 0 : -5;
 }
@@ -771,7 +807,7 @@ int tc_enqueue_yout(const Batch& b, const Pixels& px, int n_level, const TcPlan&
         return;
       }
       k_synth_tc<ML, F16, FS, 1><<<grid, kThreads, smem, s>>>(b, px, n_level, nullptr, yo, w->steps, w->B, w->scale,
-                                                              w->qfix, w->qfix_stride, w->lwt, p.n_stages,
+                                                              w->qph, w->qfix_stride, w->lwt, p.n_stages,
                                                               stage_bytes, p.ncols_buf, w->status);
     }
   });

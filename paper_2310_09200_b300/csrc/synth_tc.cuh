@@ -31,8 +31,9 @@ struct TcWorkspace {
   TcStep* steps = nullptr;     // [cap_T] device copy of the step table
   TcStep* h_steps = nullptr;   // [cap_T] pinned host step table (source of the copy, graph-safe)
   float* scale = nullptr;      // [cap_T] operand scale of the FP16 variant (W * scale)
-  uint32_t* qfix = nullptr;    // [cap_T][chunks * 32][8] station p/wl in 40.24 fixed point (see k_tc_pack)
-  int qfix_stride = 0;         // stations per step in qfix (32 * chunks of n_max)
+  uint32_t* qfix = nullptr;    // [cap_T][chunks * 32][8] station p/wl in 40.24 fixed point (see k_tc_pack; adjoint)
+  uint32_t* qph = nullptr;     // [cap_T][chunks * 16][20] station words of the synthesis phase, in pairs (k_tc_pack)
+  int qfix_stride = 0;         // stations per step in qfix and qph (32 * chunks of n_max)
   int2* lwt = nullptr;         // [cap_T][kTcMaxEig] (level, FP32 weight / scale^2) per accumulator column pair
   int* status = nullptr;       // [2] device error word (0 = ok), fault-injection word (0 = off)
   int cap_T = 0;

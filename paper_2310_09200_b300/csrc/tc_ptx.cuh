@@ -140,6 +140,44 @@ __device__ __forceinline__ uint2 ld_shared_v2(uint32_t a) {
   return v;
 }
 
+// Per-pixel constants of the 32-bit phase (see the header comment of
+// synth_tc.cu): R = round(r 2^29) per component, and (r, r), (rl, rl) in FP32,
+// rl = r - R 2^-29, duplicated for the packed FP32 operations.
+struct PhasePix {
+  int32_t R[3];
+  float2 rf[3], rl[3];
+};
+__device__ __forceinline__ PhasePix phase_pix(const double (&r)[3]) {
+  PhasePix p;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int R = __double2int_rn(r[c] * 536870912.0);  // |r| <= 1: |R| <= 2^29
+    const float f = (float)r[c], l = (float)(r[c] - (double)R * 1.862645149230957e-09);
+    p.R[c] = R;
+    p.rf[c] = make_float2(f, f);
+    p.rl[c] = make_float2(l, l);
+  }
+  return p;
+}
+// 2 pi <r, q> mod 2 pi, in radians within about [-4.3, 4.3], for the two
+// stations of one 80-byte group of phase words at shared address a (k_tc_pack:
+// QH_x, QH_y, QH_z as 32-bit integers, then 2 pi ql and 2 pi q per component
+// in FP32, each word for station 0 then station 1).
+__device__ __forceinline__ float2 phase_rad_pair(const PhasePix& p, uint32_t a) {
+  const uint4 w0 = ld_shared_v4(a), w1 = ld_shared_v4(a + 16u), w2 = ld_shared_v4(a + 32u),
+              w3 = ld_shared_v4(a + 48u), w4 = ld_shared_v4(a + 64u);
+  const uint32_t acc0 = (uint32_t)p.R[0] * w0.x + (uint32_t)p.R[1] * w0.z + (uint32_t)p.R[2] * w1.x;
+  const uint32_t acc1 = (uint32_t)p.R[0] * w0.y + (uint32_t)p.R[1] * w0.w + (uint32_t)p.R[2] * w1.y;
+  float2 f = __fmul2_rn(p.rf[0], make_float2(__uint_as_float(w1.z), __uint_as_float(w1.w)));
+  f = __ffma2_rn(p.rf[1], make_float2(__uint_as_float(w2.x), __uint_as_float(w2.y)), f);
+  f = __ffma2_rn(p.rf[2], make_float2(__uint_as_float(w2.z), __uint_as_float(w2.w)), f);
+  f = __ffma2_rn(p.rl[0], make_float2(__uint_as_float(w3.x), __uint_as_float(w3.y)), f);
+  f = __ffma2_rn(p.rl[1], make_float2(__uint_as_float(w3.z), __uint_as_float(w3.w)), f);
+  f = __ffma2_rn(p.rl[2], make_float2(__uint_as_float(w4.x), __uint_as_float(w4.y)), f);
+  constexpr float k2pi32 = 1.4629180792671596e-09f;  // 2 pi 2^-32
+  return __ffma2_rn(make_float2((float)(int32_t)acc0, (float)(int32_t)acc1), make_float2(k2pi32, k2pi32), f);
+}
+
 __device__ __forceinline__ void st_shared_v4(uint32_t a, const uint32_t (&w)[4]) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3])
                : "memory");

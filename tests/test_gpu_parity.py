@@ -165,6 +165,27 @@ def test_failed_batch_leaves_images_unchanged():
         assert np.all(ss.get() == 0.0)
 
 
+def test_split_precision_rejects_stations_beyond_the_phase_range():
+    """The tensor-core synthesis forms its phase from 32-bit integer station
+    words (8 p/wl): a step with a station 2^28 wavelengths or more from the
+    origin fails with BIPP_ERR_UNSUPPORTED and the batch adds nothing. The
+    layout is moved as a whole, so the Gram matrix and eigenpairs are those
+    of a good step."""
+    inp = inputs.make_config(0, n_t=2, n_side=8)
+    b = np.array([[-np.inf, np.inf]])
+    far = inp.st_xyz[1] + np.array([2.0 ** 29 * inp.wl, 0.0, 0.0])
+    with bipp_ss.StandardSynthesis(inp.pix, inp.wl, b, n_eig=4, precision="split_fp16") as ss:
+        ss.collect(inp.st_xyz[0], inp.vis[0])
+        before = ss.get()
+        with pytest.raises(bipp_ss.BippError) as e:
+            ss.collect_batch([inp.st_xyz[0], far], inp.vis)
+        assert e.value.code == bipp_ss.BIPP_ERR_UNSUPPORTED
+        assert "step 1" in str(e.value)
+        np.testing.assert_array_equal(ss.get(), before)
+        ss.collect(inp.st_xyz[1], inp.vis[1])  # the handle images again after the failure
+        assert np.all(np.isfinite(ss.get())) and not np.array_equal(ss.get(), before)
+
+
 def test_collect_rejects_bad_sizes():
     inp = inputs.make_config(0, n_t=1, n_side=8)
     b = np.array([[-np.inf, np.inf]])
