@@ -51,11 +51,11 @@ SMS = 148
 SM_MAX_GHZ = 2.032
 FP64_PEAK_FLOPS = SMS * 2 * 2 * SM_MAX_GHZ * 1e9
 FP32_PEAK_FLOPS = SMS * 128 * 2 * SM_MAX_GHZ * 1e9
-# Issue slots: 4 warp instructions per SM per clock. k_synth_tc issues 40 thread
+# Issue slots: 4 warp instructions per SM per clock. k_synth_tc issues 32 thread
 # instructions per pixel-station pair (ncu, profiles/k_synth_tc_ska_low_512st_1024px_10steps.md:
 # phase, sincos, hi/lo split and stores of A in the producers, plus the epilogue).
 ISSUE_THREAD_INSTR_PER_S = SMS * 4 * 32 * SM_MAX_GHZ * 1e9
-SYNTH_TC_INSTR_PER_PAIR = 40
+SYNTH_TC_INSTR_PER_PAIR = 32
 
 
 DTYPES = {"fp64": "f64", "fp32": "f64 eig + f32 synth",

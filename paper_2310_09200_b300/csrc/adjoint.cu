@@ -455,7 +455,7 @@ int run_tc(int64_t n_pix, const double* d_pix, double wl, int T, int N, int K, i
   }
   if (e == cudaSuccess && rc == BIPP_OK && tc_enqueue_pack(sc.b, plan, w, s)) e = cudaErrorLaunchFailure;
   if (e == cudaSuccess && rc == BIPP_OK) {
-    Pixels px{n_pix, d_pix, nullptr};  // the tensor-core kernels form their fixed-point phases from FP64
+    Pixels px{n_pix, d_pix, nullptr};  // the tensor-core kernels form their integer phase words from FP64
     if (!R) {
       e = cudaMemsetAsync(img, 0, sizeof(double) * n_pix * n_level, s);
       if (e == cudaSuccess && tc_enqueue_synth(sc.b, px, n_level, img, plan, w, s)) e = cudaErrorLaunchFailure;
@@ -474,7 +474,7 @@ int run_tc(int64_t n_pix, const double* d_pix, double wl, int T, int N, int K, i
         if (tc_enqueue_yout(sc.b, px, n_level, plan, w, yo, s)) rc = BIPP_ERR_UNSUPPORTED;
       }
       if (e == cudaSuccess && rc == BIPP_OK &&
-          launch_adjoint_tc(px, T, N, K, ncols, w->qfix, w->qfix_stride, Y, nc64, part, grid,
+          launch_adjoint_tc(px, T, N, K, ncols, w->qph, w->qph_stride, Y, nc64, part, grid,
                             reinterpret_cast<double2*>(gW), w->status, s))
         e = cudaErrorLaunchFailure;
       if (e == cudaSuccess && rc == BIPP_OK) {

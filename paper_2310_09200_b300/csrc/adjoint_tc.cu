@@ -14,8 +14,9 @@
 // k_adjoint_tc: one persistent CTA per SM, 18 warps. Per (step t, pass over
 // 128 stations) every CTA accumulates P over its 64-pixel chunks:
 //   warps 0-15 generate A for the chunk: thread = (station, quarter of the 64
-//              pixels); the same 64-bit fixed-point phase and SFU sincos as the
-//              forward kernel, split into BF16 hi + lo, written into two M-tiles
+//              pixels); the same 32-bit integer phase and SFU sincos as the
+//              forward kernel (header comment of synth_tc.cu), two pixels at a
+//              time, split into BF16 hi + lo, written into two M-tiles
 //              of 128 rows (64 stations' cos rows, then their sin rows) x 64
 //              pixels in the UMMA K-major 128-byte swizzled layout. At the end
 //              of each (t, pass) they read the accumulators (tcgen05.ld) and
@@ -47,8 +48,11 @@ constexpr int kASt = 128;                // stations per pass (2 M-tiles of 64 s
 constexpr int kATile = 128 * 128;        // bytes of one M-tile image (128 rows x 128 B)
 constexpr int kAImg = 2 * kATile;        // both M-tiles of one image (hi or lo)
 constexpr int kAStages = 2;
-// Pixel words per stage: word c (0..5) of pixel p at c * kAPw + p + 8 (p / 32): the four
-// quarters of a warp (pixels 16 q + j) then read four different banks.
+// Pixel words per stage: word c (0..8: R = round(r 2^29) per component, then r and
+// rl = r - R 2^-29 in FP32) of pixel p at c * kAPw + p + 8 (p / 32): the four quarters of a
+// warp (pixels 16 q + j) then read four different bank pairs, and the words of pixels
+// 2k, 2k + 1 form one aligned 8-byte pair.
+constexpr int kAPWords = 9;
 constexpr int kAPw = kAPix + 16;
 __device__ __forceinline__ int pw_idx(int c, int p) { return c * kAPw + p + 8 * (p >> 5); }
 
@@ -57,7 +61,7 @@ __device__ __forceinline__ int pw_idx(int c, int p) { return c * kAPw + p + 8 * 
 __host__ __device__ constexpr int adj_stage_bytes(int ncols) { return 2 * kAImg + 2 * ncols * 128; }
 
 __global__ void __launch_bounds__(kAThreads, 1)
-    k_adjoint_tc(Pixels px, int T, int n_st, int ncols, const uint32_t* __restrict__ qfix, int qfix_stride,
+    k_adjoint_tc(Pixels px, int T, int n_st, int ncols, const uint32_t* __restrict__ qph, int qph_stride,
                  const unsigned char* __restrict__ Y, int nc64, float* __restrict__ part, uint32_t idesc1,
                  uint32_t idesc2, int* status) {
   extern __shared__ unsigned char smem_raw[];
@@ -67,7 +71,7 @@ __global__ void __launch_bounds__(kAThreads, 1)
   __shared__ uint32_t s_taddr;
   __shared__ volatile int s_abort;
   const int stage_bytes = adj_stage_bytes(ncols);
-  uint32_t* spix = reinterpret_cast<uint32_t*>(smem + kAStages * stage_bytes);  // [stage][6 words][kAPw]
+  uint32_t* spix = reinterpret_cast<uint32_t*>(smem + kAStages * stage_bytes);  // [stage][kAPWords][kAPw]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t tcols = (uint32_t)max(32, 1 << (32 - __clz(4 * ncols - 1)));  // 2 M-tiles x 2 ncols, power of two
   if (threadIdx.x == 0) {
@@ -117,13 +121,21 @@ __global__ void __launch_bounds__(kAThreads, 1)
     for (int u = 0; u < n_units && ok; ++u) {
       const int t = u / npass, s0 = (u % npass) * kASt;
       const int i = s0 + sl;
-      uint4 qa = make_uint4(0u, 0u, 0u, 0u);
-      uint2 qb = make_uint2(0u, 0u);
+      // the station's phase words (k_tc_pack: QH, 2 pi ql, 2 pi q per component), the FP32
+      // ones duplicated for the packed operations on two pixels
+      uint32_t QH[3] = {0u, 0u, 0u};
+      float2 ql2[3], q2[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) ql2[c] = q2[c] = make_float2(0.f, 0.f);
       if (i < n_st) {
-        const uint4* qp = reinterpret_cast<const uint4*>(qfix + ((size_t)t * qfix_stride + i) * 8);
-        qa = qp[0];
-        const uint4 q1 = qp[1];
-        qb = make_uint2(q1.x, q1.y);
+        const uint32_t* g = qph + ((size_t)t * qph_stride + (i & ~1)) * 10 + (i & 1);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          QH[c] = g[2 * c];
+          const float a = __uint_as_float(g[6 + 2 * c]), b = __uint_as_float(g[12 + 2 * c]);
+          ql2[c] = make_float2(a, a);
+          q2[c] = make_float2(b, b);
+        }
       }
       for (int chunk = blockIdx.x; chunk < nc64; chunk += gridDim.x) {
         const uint32_t s = rs_s, rnd = rs_rnd;
@@ -135,14 +147,15 @@ __global__ void __launch_bounds__(kAThreads, 1)
           ok = false;
           break;
         }
-        // the chunk's pixel words: R = round(r 2^40) as (low, high) per component
-        uint32_t* pw = spix + s * 6 * kAPw;
+        // the chunk's pixel words: R = round(r 2^29), r and rl = r - R 2^-29 per component
+        uint32_t* pw = spix + s * kAPWords * kAPw;
         if (tid < kAPix) {
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            const long long R = __double2ll_rn(pxn[c] * 1099511627776.0);
-            pw[pw_idx(2 * c, tid)] = (uint32_t)(unsigned long long)R;
-            pw[pw_idx(2 * c + 1, tid)] = (uint32_t)((unsigned long long)R >> 32);
+            const int R = __double2int_rn(pxn[c] * 536870912.0);
+            pw[pw_idx(c, tid)] = (uint32_t)R;
+            pw[pw_idx(3 + c, tid)] = __float_as_uint((float)pxn[c]);
+            pw[pw_idx(6 + c, tid)] = __float_as_uint((float)(pxn[c] - (double)R * 1.862645149230957e-09));
           }
         }
         {
@@ -156,11 +169,29 @@ __global__ void __launch_bounds__(kAThreads, 1)
           const int pp0 = quarter * 16 + q * 8;
           float cs[8], sn[8];
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
+          for (int j = 0; j < 8; j += 2) {  // pixels p, p + 1
             const int p = pp0 + j;
-            const uint32_t rl[3] = {pw[pw_idx(0, p)], pw[pw_idx(2, p)], pw[pw_idx(4, p)]};
-            const uint32_t rh[3] = {pw[pw_idx(1, p)], pw[pw_idx(3, p)], pw[pw_idx(5, p)]};
-            __sincosf(phase_rad_fixed(rl, rh, qa, qb), &sn[j], &cs[j]);
+            uint2 R[3];
+            float2 rf[3], rl[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+              R[c] = *reinterpret_cast<const uint2*>(pw + pw_idx(c, p));
+              rf[c] = *reinterpret_cast<const float2*>(pw + pw_idx(3 + c, p));
+              rl[c] = *reinterpret_cast<const float2*>(pw + pw_idx(6 + c, p));
+            }
+            const uint32_t acc0 = R[0].x * QH[0] + R[1].x * QH[1] + R[2].x * QH[2];
+            const uint32_t acc1 = R[0].y * QH[0] + R[1].y * QH[1] + R[2].y * QH[2];
+            float2 f = __fmul2_rn(rf[0], ql2[0]);
+            f = __ffma2_rn(rf[1], ql2[1], f);
+            f = __ffma2_rn(rf[2], ql2[2], f);
+            f = __ffma2_rn(rl[0], q2[0], f);
+            f = __ffma2_rn(rl[1], q2[1], f);
+            f = __ffma2_rn(rl[2], q2[2], f);
+            constexpr float k2pi32 = 1.4629180792671596e-09f;  // 2 pi 2^-32
+            const float2 ph = __ffma2_rn(make_float2((float)(int32_t)acc0, (float)(int32_t)acc1),
+                                         make_float2(k2pi32, k2pi32), f);
+            __sincosf(ph.x, &sn[j], &cs[j]);
+            __sincosf(ph.y, &sn[j + 1], &cs[j + 1]);
           }
           uint32_t ch[4], cl[4], sh[4], sl4[4];
 #pragma unroll
@@ -331,9 +362,9 @@ __global__ void k_adj_tc_reduce(const float* part, int T, int n_cta, int n_st, i
 
 }  // namespace
 
-int adj_tc_smem_bytes(int ncols) { return kAStages * adj_stage_bytes(ncols) + kAStages * 6 * kAPw * 4 + 1024; }
+int adj_tc_smem_bytes(int ncols) { return kAStages * adj_stage_bytes(ncols) + kAStages * kAPWords * kAPw * 4 + 1024; }
 
-int launch_adjoint_tc(const Pixels& px, int T, int n_st, int K, int ncols, const uint32_t* qfix, int qfix_stride,
+int launch_adjoint_tc(const Pixels& px, int T, int n_st, int K, int ncols, const uint32_t* qph, int qph_stride,
                       const unsigned char* Y, int nc64, float* part, int grid, double2* gWp, int* status,
                       cudaStream_t s) {
   if (K > 64 || ncols > 128 || (ncols & 15)) return -1;
@@ -343,7 +374,7 @@ int launch_adjoint_tc(const Pixels& px, int T, int n_st, int K, int ncols, const
   };
   const int smem = adj_tc_smem_bytes(ncols);
   if (cudaFuncSetAttribute(k_adjoint_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return -2;
-  k_adjoint_tc<<<grid, kAThreads, smem, s>>>(px, T, n_st, ncols, qfix, qfix_stride, Y, nc64, part, idesc(ncols),
+  k_adjoint_tc<<<grid, kAThreads, smem, s>>>(px, T, n_st, ncols, qph, qph_stride, Y, nc64, part, idesc(ncols),
                                              idesc(2 * ncols), status);
   k_adj_tc_reduce<<<dim3((n_st * K + 255) / 256, T), 256, 0, s>>>(part, T, grid, n_st, K, ncols, gWp);
   return cudaGetLastError() == cudaSuccess ? 0 : -3;

@@ -710,10 +710,6 @@ static int run_batch(bipp_ss* h, int n_t, int N, const std::vector<int>& nst_v, 
                     (tc ? 1 + (h->opt.precision == BIPP_PREC_SPLIT_FP16) : 0) + (nufft ? h->nu_launches - 1 : 0);
   }
   for (int t = 0; t < n_t; ++t) {
-    if (status[t] & kStatusRange)
-      return fail(h, BIPP_ERR_UNSUPPORTED,
-                  "step %d: a station lies 2^28 wavelengths or more from the origin (beyond the range of the "
-                  "tensor-core synthesis phase)", t);
     if (status[t] & kStatusNotPD)
       return fail(h, BIPP_ERR_GRAM_NOT_PD, "step %d: Gram matrix is not positive definite (Cholesky pivot <= 0 or NaN)", t);
     if (status[t] & kStatusNotConverged)
@@ -724,6 +720,10 @@ static int run_batch(bipp_ss* h, int n_t, int N, const std::vector<int>& nst_v, 
                         t, h->opt.max_jacobi_sweeps)
                  : fail(h, BIPP_ERR_EIG_NOT_CONVERGED, "step %d: Jacobi did not converge in %d sweeps", t,
                         h->opt.max_jacobi_sweeps);
+    if (status[t] & kStatusRange)
+      return fail(h, BIPP_ERR_UNSUPPORTED,
+                  "step %d: a station lies 2^28 wavelengths or more from the origin (beyond the range of the "
+                  "tensor-core synthesis phase)", t);
   }
   if (tc_status) return fail(h, BIPP_ERR_DEVICE_TIMEOUT, "tensor-core synthesis: bounded wait gave up (code %d)", tc_status);
   return BIPP_OK;

@@ -11,7 +11,7 @@
 // Kernel structure (one persistent CTA per SM, 18 warps):
 //   warps 0-15 (4 warpgroups) generate A for a 128-pixel tile on the fly:
 //              thread = pixel row, warpgroup g = stations 8g..8g+7 of the
-//              stage; phase reduction in 64-bit fixed point (below), SFU
+//              stage; phase reduction by 32-bit integer products (below), SFU
 //              sincos, split into hi + lo (BF16 or FP16), written into shared
 //              memory in the UMMA K-major 128-byte swizzled layout (one
 //              128-byte row per pixel, 32 stations per stage). They also run the epilogue: tcgen05.ld of
@@ -493,17 +493,15 @@ __global__ void k_tc_scale(Batch b, float* scales) {
 
 // B chunk c of step t: rows n < ncols (K-major, 128 bytes = 64 K-elements),
 // hi image then lo image, 16-byte pieces XOR-swizzled by (row & 7).
-// Also the chunk's station words for the phase: for the adjoint's kernel,
-// Q = round(p/wl 2^24) per component as (low, high) 32-bit words, 8 words per
-// station; for the synthesis, per pair of stations (a, b) 20 words: QH_x,
-// QH_y, QH_z (QH = round(8 p/wl), 32-bit integers), then 2 pi ql and 2 pi q
-// per component in FP32 (ql = p/wl - QH/8), each word for a then b, and two
-// zero words (header comment). Padded stations i >= n have zero words. A
-// station with |8 p/wl| >= 2^31 marks its step kStatusRange (and the batch
-// flag, so that nothing is committed).
+// Also the chunk's station phase words: per pair of stations (a, b) 20
+// words: QH_x, QH_y, QH_z (QH = round(8 p/wl), 32-bit integers), then 2 pi ql
+// and 2 pi q per component in FP32 (ql = p/wl - QH/8), each word for a then b,
+// and two zero words (header comment). Padded stations i >= n have zero
+// words. A station with |8 p/wl| >= 2^31 marks its step kStatusRange (and the
+// batch flag, so that nothing is committed).
 template <bool FP16>
-__global__ void k_tc_pack(Batch b, const TcStep* steps, unsigned char* Bpack, const float* scales, uint32_t* qfix,
-                          uint32_t* qph, int qfix_stride, int2* lwt) {
+__global__ void k_tc_pack(Batch b, const TcStep* steps, unsigned char* Bpack, const float* scales, uint32_t* qph,
+                          int qph_stride, int2* lwt) {
   const int t = blockIdx.y, c = blockIdx.x;
   const TcStep st = steps[t];
   if (c >= st.n_chunks) return;
@@ -519,20 +517,7 @@ __global__ void k_tc_pack(Batch b, const TcStep* steps, unsigned char* Bpack, co
   }
   if (threadIdx.x < kStations) {
     const int i = c * kStations + threadIdx.x;
-    uint32_t wv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    if (i < n) {
-      const double inv_wl = 1.0 / b.wl[t];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const long long Q = __double2ll_rn(b.st[((size_t)t * 3 + k) * N + i] * inv_wl * 16777216.0);
-        wv[2 * k] = (uint32_t)(unsigned long long)Q;
-        wv[2 * k + 1] = (uint32_t)((unsigned long long)Q >> 32);
-      }
-    }
-    uint4* dst = reinterpret_cast<uint4*>(qfix + ((size_t)t * qfix_stride + i) * 8);
-    dst[0] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
-    dst[1] = make_uint4(wv[4], wv[5], wv[6], wv[7]);
-    uint32_t* g = qph + ((size_t)t * qfix_stride + (i & ~1)) * (kQBytes / 4);
+    uint32_t* g = qph + ((size_t)t * qph_stride + (i & ~1)) * (kQBytes / 4);
     const int sl = i & 1;
     bool bad = false;
 #pragma unroll
@@ -546,8 +531,8 @@ __global__ void k_tc_pack(Batch b, const TcStep* steps, unsigned char* Bpack, co
           QH = (int)q8;
           ql = (float)(6.283185307179586 * (q - 0.125 * q8));
           qf = (float)(6.283185307179586 * q);
-        } else {
-          bad = true;
+        } else if (q8 == q8) {
+          bad = true;  // (a NaN coordinate is left to the Gram matrix's check)
         }
       }
       g[2 * k + sl] = (uint32_t)QH;
@@ -629,9 +614,8 @@ int tc_alloc(TcWorkspace* w, int T, int N, int K) {
   if (cudaMalloc(&w->steps, sizeof(TcStep) * T) != cudaSuccess) return -1;
   if (cudaMallocHost(&w->h_steps, sizeof(TcStep) * T) != cudaSuccess) return -1;
   if (cudaMalloc(&w->scale, sizeof(float) * T) != cudaSuccess) return -1;
-  w->qfix_stride = n_chunks_for(N) * kStations;
-  if (cudaMalloc(&w->qfix, sizeof(uint32_t) * 8 * (size_t)T * w->qfix_stride) != cudaSuccess) return -1;
-  if (cudaMalloc(&w->qph, kQBytes * (size_t)T * w->qfix_stride) != cudaSuccess) return -1;
+  w->qph_stride = n_chunks_for(N) * kStations;
+  if (cudaMalloc(&w->qph, kQBytes * (size_t)T * w->qph_stride) != cudaSuccess) return -1;
   if (cudaMalloc(&w->lwt, sizeof(int2) * (size_t)T * kTcMaxEig) != cudaSuccess) return -1;
   if (cudaMalloc(&w->status, 2 * sizeof(int)) != cudaSuccess) return -1;
   if (cudaMemset(w->status, 0, 2 * sizeof(int)) != cudaSuccess) return -1;
@@ -644,7 +628,6 @@ void tc_free(TcWorkspace* w) {
   if (w->steps) cudaFree(w->steps);
   if (w->h_steps) cudaFreeHost(w->h_steps);
   if (w->scale) cudaFree(w->scale);
-  if (w->qfix) cudaFree(w->qfix);
   if (w->qph) cudaFree(w->qph);
   if (w->lwt) cudaFree(w->lwt);
   if (w->status) cudaFree(w->status);
@@ -724,7 +707,7 @@ int launch_kernel(const Batch& b, const Pixels& px, int n_level, double* img, co
       return;
     }
     k_synth_tc<ML, F16, FS, 0><<<grid, kThreads, smem, s>>>(b, px, n_level, img, TcYOut{}, w->steps, w->B, w->scale, w->qph,
-                                                      w->qfix_stride, w->lwt, n_stages,
+                                                      w->qph_stride, w->lwt, n_stages,
                                                      stage_bytes, p.ncols_buf, w->status);
   });
   return rc;
@@ -771,10 +754,10 @@ int tc_enqueue_pack(const Batch& b, const TcPlan& p, TcWorkspace* w, cudaStream_
   if (cudaMemsetAsync(w->status, 0, sizeof(int), s) != cudaSuccess) return -5;
   if (p.fp16) k_tc_scale<<<T, 256, 0, s>>>(b, w->scale);
   if (p.fp16)
-    k_tc_pack<true><<<dim3(p.max_chunks, T), 256, 0, s>>>(b, w->steps, w->B, w->scale, w->qfix, w->qph, w->qfix_stride,
+    k_tc_pack<true><<<dim3(p.max_chunks, T), 256, 0, s>>>(b, w->steps, w->B, w->scale, w->qph, w->qph_stride,
                                                           w->lwt);
   else
-    k_tc_pack<false><<<dim3(p.max_chunks, T), 256, 0, s>>>(b, w->steps, w->B, w->scale, w->qfix, w->qph, w->qfix_stride,
+    k_tc_pack<false><<<dim3(p.max_chunks, T), 256, 0, s>>>(b, w->steps, w->B, w->scale, w->qph, w->qph_stride,
                                                            w->lwt);
   return cudaGetLastError() == cudaSuccess ? 0 : -5;
 }
@@ -807,7 +790,7 @@ int tc_enqueue_yout(const Batch& b, const Pixels& px, int n_level, const TcPlan&
         return;
       }
       k_synth_tc<ML, F16, FS, 1><<<grid, kThreads, smem, s>>>(b, px, n_level, nullptr, yo, w->steps, w->B, w->scale,
-                                                              w->qph, w->qfix_stride, w->lwt, p.n_stages,
+                                                              w->qph, w->qph_stride, w->lwt, p.n_stages,
                                                               stage_bytes, p.ncols_buf, w->status);
     }
   });

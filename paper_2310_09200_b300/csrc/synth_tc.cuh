@@ -31,9 +31,8 @@ struct TcWorkspace {
   TcStep* steps = nullptr;     // [cap_T] device copy of the step table
   TcStep* h_steps = nullptr;   // [cap_T] pinned host step table (source of the copy, graph-safe)
   float* scale = nullptr;      // [cap_T] operand scale of the FP16 variant (W * scale)
-  uint32_t* qfix = nullptr;    // [cap_T][chunks * 32][8] station p/wl in 40.24 fixed point (see k_tc_pack; adjoint)
-  uint32_t* qph = nullptr;     // [cap_T][chunks * 16][20] station words of the synthesis phase, in pairs (k_tc_pack)
-  int qfix_stride = 0;         // stations per step in qfix and qph (32 * chunks of n_max)
+  uint32_t* qph = nullptr;     // [cap_T][chunks * 16][20] station phase words, in pairs of stations (k_tc_pack)
+  int qph_stride = 0;          // stations per step in qph (32 * chunks of n_max)
   int2* lwt = nullptr;         // [cap_T][kTcMaxEig] (level, FP32 weight / scale^2) per accumulator column pair
   int* status = nullptr;       // [2] device error word (0 = ok), fault-injection word (0 = off)
   int cap_T = 0;
@@ -83,9 +82,9 @@ int tc_enqueue_yout(const Batch& b, const Pixels& px, int n_level, const TcPlan&
                     cudaStream_t s);
 // The adjoint's pixel contraction on the tensor cores (adjoint_tc.cu):
 // grad_W' (n_t blocks of n_eig x n_st complex128, e-major) from Y and the
-// station words of the packed batch; part is scratch of
+// phase words (qph) of the packed batch; part is scratch of
 // n_t * grid * 2 * n_st * ncols floats. n_eig <= 64. Stream-ordered.
-int launch_adjoint_tc(const Pixels& px, int T, int n_st, int K, int ncols, const uint32_t* qfix, int qfix_stride,
+int launch_adjoint_tc(const Pixels& px, int T, int n_st, int K, int ncols, const uint32_t* qph, int qph_stride,
                       const unsigned char* Y, int nc64, float* part, int grid, double2* gWp, int* status,
                       cudaStream_t s);
 int adj_tc_smem_bytes(int ncols);

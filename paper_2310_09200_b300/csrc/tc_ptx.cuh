@@ -1,7 +1,7 @@
 // tc_ptx.cuh — inline-PTX building blocks of the tcgen05 kernels (synth_tc.cu,
 // adjoint_tc.cu): mbarriers with bounded waits, bulk copies, the UMMA
 // shared-memory descriptor, tcgen05.mma / commit / ld, the hi/lo operand
-// split and the fixed-point phase. Internal to libbipp_ss.so.
+// split and the 32-bit integer phase. Internal to libbipp_ss.so.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -111,17 +111,6 @@ __device__ __forceinline__ void split2(float x0, float x1, uint32_t* hi, uint32_
     *hi = *reinterpret_cast<uint32_t*>(&h);
     *lo = *reinterpret_cast<uint32_t*>(&l);
   }
-}
-
-// 2 pi frac(<r, q>) in radians, in [-pi, pi), from the 32-bit words of the
-// fixed-point R (per pixel) and Q (per station); see the header comment of
-// synth_tc.cu.
-__device__ __forceinline__ float phase_rad_fixed(const uint32_t (&rl)[3], const uint32_t (&rh)[3], uint4 qa,
-                                                 uint2 qb) {
-  uint32_t acc = __umulhi(rl[0], qa.x) + rh[0] * qa.x + rl[0] * qa.y;
-  acc += __umulhi(rl[1], qa.z) + rh[1] * qa.z + rl[1] * qa.w;
-  acc += __umulhi(rl[2], qb.x) + rh[2] * qb.x + rl[2] * qb.y;
-  return (float)(int32_t)acc * 1.4629180792671596e-09f;  // 2 pi 2^-32
 }
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
