@@ -471,7 +471,8 @@ int run_tc(int64_t n_pix, const double* d_pix, double wl, int T, int N, int K, i
         yo.R = R;
         yo.Y = Y;
         yo.nc64 = nc64;
-        if (tc_enqueue_yout(sc.b, px, n_level, plan, w, yo, s)) rc = BIPP_ERR_UNSUPPORTED;
+        const int yr = tc_enqueue_yout(sc.b, px, n_level, plan, w, yo, s);
+        if (yr) rc = (yr == -11) ? BIPP_ERR_CUDA : BIPP_ERR_UNSUPPORTED;  // -11: the launch failed
       }
       if (e == cudaSuccess && rc == BIPP_OK &&
           launch_adjoint_tc(px, T, N, K, ncols, w->qph, w->qph_stride, Y, nc64, part, grid,

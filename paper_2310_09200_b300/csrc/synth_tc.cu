@@ -136,7 +136,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp < kProdWarps) {
     // ------------------------------------------------ A producer + epilogue
     const int row = threadIdx.x & (kRows - 1);
-    const int wg = threadIdx.x >> 7;  // warpgroup: stations 8wg..8wg+7 of a stage, column blocks wg + 4j
+    const int wg = threadIdx.x >> 7;  // warpgroup: column blocks wg + 4j of the epilogue
+    // A producer: pixel rows rp and rp + 64 of the tile, stations 4 quad .. 4 quad + 3 of
+    // the stage (one 16-byte piece of each row), so that a warp's station words (the
+    // same for all its lanes) serve two pixels per load
+    const int rp = threadIdx.x & 63, quad = threadIdx.x >> 6;
     uint32_t rs_s = 0, rs_rnd = 0;  // ring slot and round, advanced per chunk
     int unit = 0;
     int pend_tile = -1, pend_t = -1;
@@ -268,10 +272,15 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
       const int64_t r = (int64_t)tile * kRows + row;
-      double rx[3];
+      PhasePix pp[2];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) rx[c] = (r < px.n) ? px.xyz[(size_t)c * px.n + r] : 0.0;
-      const PhasePix pp = phase_pix(rx);
+      for (int k = 0; k < 2; ++k) {
+        const int64_t rk = (int64_t)tile * kRows + rp + 64 * k;
+        double rx[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) rx[c] = (rk < px.n) ? px.xyz[(size_t)c * px.n + rk] : 0.0;
+        pp[k] = phase_pix(rx);
+      }
       for (int t = 0; t < T && ok; ++t) {
         const int nch = steps[t].n_chunks;
         uint32_t qcur = 0;
@@ -305,30 +314,31 @@ __global__ void __launch_bounds__(kThreads, 1)
             ok = false;
             break;
           }
-          const uint32_t a_hi = smem0 + s * stage_bytes + row * 128;
-          const uint32_t a_lo = a_hi + kABytes;
           {
-            // the thread's eight stations side by side (phases, sincos, splits), so that
-            // their independent dependency chains interleave; padded stations have zero
-            // phase words and zero B rows
-            const uint32_t qs = qcur + (uint32_t)((c & (kQWin - 1)) * kStations + 8 * wg) * kQBytes;
-            float ph[8], cs[8], sn[8];
+            // the thread's eight pairs side by side (phases, sincos, splits), so that their
+            // independent dependency chains interleave; padded stations have zero phase
+            // words and zero B rows
+            const uint32_t qs = qcur + (uint32_t)((c & (kQWin - 1)) * kStations + 4 * quad) * kQBytes;
+            float cs[2][4], sn[2][4];
 #pragma unroll
-            for (int g = 0; g < 4; ++g) {
-              const float2 p2 = phase_rad_pair(pp, qs + 2u * kQBytes * g);
-              ph[2 * g] = p2.x;
-              ph[2 * g + 1] = p2.y;
+            for (int g = 0; g < 2; ++g) {
+              const PhaseWords qw = phase_words(qs + 2u * kQBytes * g);
+#pragma unroll
+              for (int k = 0; k < 2; ++k) {
+                const float2 p2 = phase_rad_pair(pp[k], qw);
+                __sincosf(p2.x, &sn[k][2 * g], &cs[k][2 * g]);
+                __sincosf(p2.y, &sn[k][2 * g + 1], &cs[k][2 * g + 1]);
+              }
             }
 #pragma unroll
-            for (int j = 0; j < 8; ++j) __sincosf(ph[j], &sn[j], &cs[j]);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            for (int k = 0; k < 2; ++k) {
+              const int rr = rp + 64 * k;
               uint32_t hw[4], lw[4];
 #pragma unroll
-              for (int j = 0; j < 4; ++j) split2<FP16>(cs[4 * h + j], sn[4 * h + j], &hw[j], &lw[j]);
-              const uint32_t phys = (uint32_t)(((2 * wg + h) ^ (row & 7)) << 4);
-              st_shared_v4(a_hi + phys, hw);
-              st_shared_v4(a_lo + phys, lw);
+              for (int j = 0; j < 4; ++j) split2<FP16>(cs[k][j], sn[k][j], &hw[j], &lw[j]);
+              const uint32_t a_hi = smem0 + s * stage_bytes + (uint32_t)rr * 128u + (uint32_t)((quad ^ (rr & 7)) << 4);
+              st_shared_v4(a_hi, hw);
+              st_shared_v4(a_hi + kABytes, lw);
             }
           }
           fence_async_smem();
@@ -709,6 +719,7 @@ int launch_kernel(const Batch& b, const Pixels& px, int n_level, double* img, co
     k_synth_tc<ML, F16, FS, 0><<<grid, kThreads, smem, s>>>(b, px, n_level, img, TcYOut{}, w->steps, w->B, w->scale, w->qph,
                                                       w->qph_stride, w->lwt, n_stages,
                                                      stage_bytes, p.ncols_buf, w->status);
+    if (cudaGetLastError() != cudaSuccess) rc = -11;  // the launch itself failed
   });
   return rc;
 }
@@ -792,6 +803,7 @@ int tc_enqueue_yout(const Batch& b, const Pixels& px, int n_level, const TcPlan&
       k_synth_tc<ML, F16, FS, 1><<<grid, kThreads, smem, s>>>(b, px, n_level, nullptr, yo, w->steps, w->B, w->scale,
                                                               w->qph, w->qph_stride, w->lwt, p.n_stages,
                                                               stage_bytes, p.ncols_buf, w->status);
+      if (cudaGetLastError() != cudaSuccess) rc = -11;  // the launch itself failed
     }
   });
   return rc;

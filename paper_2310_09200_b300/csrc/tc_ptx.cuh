@@ -148,21 +148,32 @@ __device__ __forceinline__ PhasePix phase_pix(const double (&r)[3]) {
   }
   return p;
 }
-// 2 pi <r, q> mod 2 pi, in radians within about [-4.3, 4.3], for the two
-// stations of one 80-byte group of phase words at shared address a (k_tc_pack:
-// QH_x, QH_y, QH_z as 32-bit integers, then 2 pi ql and 2 pi q per component
-// in FP32, each word for station 0 then station 1).
-__device__ __forceinline__ float2 phase_rad_pair(const PhasePix& p, uint32_t a) {
-  const uint4 w0 = ld_shared_v4(a), w1 = ld_shared_v4(a + 16u), w2 = ld_shared_v4(a + 32u),
-              w3 = ld_shared_v4(a + 48u), w4 = ld_shared_v4(a + 64u);
-  const uint32_t acc0 = (uint32_t)p.R[0] * w0.x + (uint32_t)p.R[1] * w0.z + (uint32_t)p.R[2] * w1.x;
-  const uint32_t acc1 = (uint32_t)p.R[0] * w0.y + (uint32_t)p.R[1] * w0.w + (uint32_t)p.R[2] * w1.y;
-  float2 f = __fmul2_rn(p.rf[0], make_float2(__uint_as_float(w1.z), __uint_as_float(w1.w)));
-  f = __ffma2_rn(p.rf[1], make_float2(__uint_as_float(w2.x), __uint_as_float(w2.y)), f);
-  f = __ffma2_rn(p.rf[2], make_float2(__uint_as_float(w2.z), __uint_as_float(w2.w)), f);
-  f = __ffma2_rn(p.rl[0], make_float2(__uint_as_float(w3.x), __uint_as_float(w3.y)), f);
-  f = __ffma2_rn(p.rl[1], make_float2(__uint_as_float(w3.z), __uint_as_float(w3.w)), f);
-  f = __ffma2_rn(p.rl[2], make_float2(__uint_as_float(w4.x), __uint_as_float(w4.y)), f);
+// The 80-byte group of phase words of two stations (k_tc_pack: QH_x, QH_y,
+// QH_z as 32-bit integers, then 2 pi ql and 2 pi q per component in FP32, each
+// word for station 0 then station 1), from shared address a.
+struct PhaseWords {
+  uint4 w0, w1, w2, w3, w4;
+};
+__device__ __forceinline__ PhaseWords phase_words(uint32_t a) {
+  PhaseWords q;
+  q.w0 = ld_shared_v4(a);
+  q.w1 = ld_shared_v4(a + 16u);
+  q.w2 = ld_shared_v4(a + 32u);
+  q.w3 = ld_shared_v4(a + 48u);
+  q.w4 = ld_shared_v4(a + 64u);
+  return q;
+}
+// 2 pi <r, q> mod 2 pi, in radians within about [-4.3, 4.3], of one pixel and
+// the two stations of a group.
+__device__ __forceinline__ float2 phase_rad_pair(const PhasePix& p, const PhaseWords& q) {
+  const uint32_t acc0 = (uint32_t)p.R[0] * q.w0.x + (uint32_t)p.R[1] * q.w0.z + (uint32_t)p.R[2] * q.w1.x;
+  const uint32_t acc1 = (uint32_t)p.R[0] * q.w0.y + (uint32_t)p.R[1] * q.w0.w + (uint32_t)p.R[2] * q.w1.y;
+  float2 f = __fmul2_rn(p.rf[0], make_float2(__uint_as_float(q.w1.z), __uint_as_float(q.w1.w)));
+  f = __ffma2_rn(p.rf[1], make_float2(__uint_as_float(q.w2.x), __uint_as_float(q.w2.y)), f);
+  f = __ffma2_rn(p.rf[2], make_float2(__uint_as_float(q.w2.z), __uint_as_float(q.w2.w)), f);
+  f = __ffma2_rn(p.rl[0], make_float2(__uint_as_float(q.w3.x), __uint_as_float(q.w3.y)), f);
+  f = __ffma2_rn(p.rl[1], make_float2(__uint_as_float(q.w3.z), __uint_as_float(q.w3.w)), f);
+  f = __ffma2_rn(p.rl[2], make_float2(__uint_as_float(q.w4.x), __uint_as_float(q.w4.y)), f);
   constexpr float k2pi32 = 1.4629180792671596e-09f;  // 2 pi 2^-32
   return __ffma2_rn(make_float2((float)(int32_t)acc0, (float)(int32_t)acc1), make_float2(k2pi32, k2pi32), f);
 }
