@@ -76,12 +76,14 @@ struct bipp_ss {
   float2* d_W32 = nullptr;
   float* d_q = nullptr;
   int* d_nst = nullptr;
+  int* d_order = nullptr;  // [T] steps by descending station count (Batch::order)
   int* d_neig = nullptr;
   int* d_chan = nullptr;
   double* d_wl = nullptr;
   int* d_flag = nullptr;
   // pinned host staging of the per-step tables (sources of graph memcpy nodes)
   int* h_nst = nullptr;
+  int* h_order = nullptr;
   int* h_neig = nullptr;
   int* h_chan = nullptr;
   double* h_wl = nullptr;
@@ -165,18 +167,18 @@ static void free_batch(bipp_ss* h) {
   drop_graph(h);
   void* ptrs[] = {h->d_st, h->d_vis, h->d_G, h->d_Linv, h->d_X, h->d_C, h->d_Q, h->d_mu, h->d_status,
                   h->d_sweeps, h->d_nkept, h->d_sel_mu, h->d_level, h->d_wt, h->d_W64, h->d_W32, h->d_q,
-                  h->d_nst, h->d_neig, h->d_chan, h->d_wl, h->d_flag, h->mx.kp, h->mx.lam, h->mx.tnorm, h->mx.theta,
+                  h->d_nst, h->d_order, h->d_neig, h->d_chan, h->d_wl, h->d_flag, h->mx.kp, h->mx.lam, h->mx.tnorm, h->mx.theta,
                   h->mx.rnorm, h->mx.cnorm, h->mx.st2, h->mx.sw2};
   for (void* p : ptrs) if (p) cudaFree(p);
   h->mx = MixedWs{};
-  void* hp[] = {h->h_nst, h->h_neig, h->h_chan, h->h_wl};
+  void* hp[] = {h->h_nst, h->h_order, h->h_neig, h->h_chan, h->h_wl};
   for (void* p : hp) if (p) cudaFreeHost(p);
   h->d_st = nullptr; h->d_vis = nullptr; h->d_G = nullptr; h->d_Linv = nullptr; h->d_X = nullptr;
   h->d_C = nullptr; h->d_Q = nullptr; h->d_mu = nullptr; h->d_status = nullptr; h->d_sweeps = nullptr;
   h->d_nkept = nullptr; h->d_sel_mu = nullptr; h->d_level = nullptr; h->d_wt = nullptr; h->d_W64 = nullptr;
-  h->d_W32 = nullptr; h->d_q = nullptr; h->d_nst = nullptr; h->d_neig = nullptr; h->d_chan = nullptr;
+  h->d_W32 = nullptr; h->d_q = nullptr; h->d_nst = nullptr; h->d_order = nullptr; h->d_neig = nullptr; h->d_chan = nullptr;
   h->d_wl = nullptr; h->d_flag = nullptr;
-  h->h_nst = nullptr; h->h_neig = nullptr; h->h_chan = nullptr; h->h_wl = nullptr;
+  h->h_nst = nullptr; h->h_order = nullptr; h->h_neig = nullptr; h->h_chan = nullptr; h->h_wl = nullptr;
   tc_free(&h->tc);
   h->cap_T = h->cap_N = h->cap_K = 0;
 }
@@ -206,6 +208,7 @@ static int ensure_batch(bipp_ss* h, int T, int N, int K) {
   CUDA_TRY(h, dalloc(&h->d_W32, (size_t)T * K * N));
   CUDA_TRY(h, dalloc(&h->d_q, (size_t)T * 6 * N));
   CUDA_TRY(h, dalloc(&h->d_nst, (size_t)T));
+  CUDA_TRY(h, dalloc(&h->d_order, (size_t)T));
   CUDA_TRY(h, dalloc(&h->d_neig, (size_t)T));
   CUDA_TRY(h, dalloc(&h->d_chan, (size_t)T));
   CUDA_TRY(h, dalloc(&h->d_wl, (size_t)T));
@@ -219,6 +222,7 @@ static int ensure_batch(bipp_ss* h, int T, int N, int K) {
   CUDA_TRY(h, dalloc(&h->mx.st2, (size_t)T));
   CUDA_TRY(h, dalloc(&h->mx.sw2, (size_t)T));
   CUDA_TRY(h, cudaMallocHost(&h->h_nst, sizeof(int) * T));
+  CUDA_TRY(h, cudaMallocHost(&h->h_order, sizeof(int) * T));
   CUDA_TRY(h, cudaMallocHost(&h->h_neig, sizeof(int) * T));
   CUDA_TRY(h, cudaMallocHost(&h->h_chan, sizeof(int) * T));
   CUDA_TRY(h, cudaMallocHost(&h->h_wl, sizeof(double) * T));
@@ -233,7 +237,7 @@ static int ensure_batch(bipp_ss* h, int T, int N, int K) {
 static Batch make_batch(bipp_ss* h, int T, int N, int K, const double* st, const double2* vis) {
   Batch b;
   b.T = T; b.n_max = N; b.k_max = K;
-  b.nst = h->d_nst; b.neig = h->d_neig; b.wl = h->d_wl; b.chan = h->d_chan;
+  b.nst = h->d_nst; b.neig = h->d_neig; b.wl = h->d_wl; b.chan = h->d_chan; b.order = h->d_order;
   b.st = st; b.vis = vis;
   b.G = h->d_G; b.Linv = h->d_Linv; b.X = h->d_X; b.C = h->d_C; b.Q = h->d_Q; b.mu = h->d_mu;
   b.status = h->d_status; b.sweeps = h->d_sweeps; b.nkept = h->d_nkept;
@@ -462,6 +466,7 @@ static int enqueue_batch(bipp_ss* h, const Batch& b, const TcPlan& plan, cudaStr
   const int gi = h->opt.gram_identity;
   if (part == 0) {
     CUDA_TRY(h, cudaMemcpyAsync(h->d_nst, h->h_nst, sizeof(int) * T, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_order, h->h_order, sizeof(int) * T, cudaMemcpyHostToDevice, s));
     CUDA_TRY(h, cudaMemcpyAsync(h->d_neig, h->h_neig, sizeof(int) * T, cudaMemcpyHostToDevice, s));
     CUDA_TRY(h, cudaMemcpyAsync(h->d_chan, h->h_chan, sizeof(int) * T, cudaMemcpyHostToDevice, s));
     CUDA_TRY(h, cudaMemcpyAsync(h->d_wl, h->h_wl, sizeof(double) * T, cudaMemcpyHostToDevice, s));
@@ -587,7 +592,9 @@ static int run_batch(bipp_ss* h, int n_t, int N, const std::vector<int>& nst_v, 
     h->h_neig[t] = neig_v[t];
     h->h_chan[t] = chan_v[t];
     h->h_wl[t] = h->wl[chan_v[t]];
+    h->h_order[t] = t;
   }
+  std::stable_sort(h->h_order, h->h_order + n_t, [&](int x, int y) { return nst_v[x] > nst_v[y]; });
   Batch b = make_batch(h, n_t, N, K, d_st, d_vis);
   // mixed-precision eigensolve when asked for and its scratch fits the batch buffers
   h->mixed_kp = 0;

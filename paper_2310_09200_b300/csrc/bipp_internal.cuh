@@ -47,7 +47,13 @@ struct Batch {
   float* q;       // [T][6][n_max] station p/wl as float hi/lo: xh,yh,zh,xl,yl,zl
   int* flag;      // [1] OR of all step statuses (synthesis skips the batch if set)
   int eigen;      // 1: one image per kept eigenpair (level = rank) instead of energy levels
+  // [T] the problems by descending station count, or nullptr (identity): the
+  // per-problem kernels of the Gram, reduction and eigensolve stages take
+  // problem order[block], so that in a batch of uneven steps the largest
+  // (longest-running) problems start in the first wave of CTAs
+  const int* order = nullptr;
 };
+__device__ __forceinline__ int prob_of(const int* order, int blk) { return order ? order[blk] : blk; }
 
 // Eigenimages use the level kernels with kEigSlots register slots per thread:
 // every synthesis thread owns a fixed quarter of the <= 64 eigenvectors.

@@ -26,7 +26,7 @@ __device__ __forceinline__ size_t mat_off(int t, int n_max) { return (size_t)t *
 
 // G_ij = sinc(2 ||p_i - p_j|| / wl) with sinc(x) = sin(pi x)/(pi x) (Eq. gram, App. A).
 __global__ void k_gram(Batch b, int gram_identity) {
-  const int t = blockIdx.z;
+  const int t = prob_of(b.order, blockIdx.z);
   const int n = b.nst[t];
   const double wl = b.wl[t];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -51,7 +51,7 @@ __global__ void k_gram(Batch b, int gram_identity) {
 
 // Right-looking Cholesky G = L L^T in place (lower triangle), one CTA per step.
 __global__ void k_cholesky(Batch b) {
-  const int t = blockIdx.x;
+  const int t = prob_of(b.order, blockIdx.x);
   const int n = b.nst[t];
   const int N = b.n_max;
   double* A = b.G + mat_off(t, N);
@@ -97,7 +97,7 @@ constexpr int kChThreads = 512;
 constexpr int kChLd = kChB + 1;
 
 __global__ void __launch_bounds__(kChThreads, 1) k_cholesky_blk(Batch b) {
-  const int t = blockIdx.x;
+  const int t = prob_of(b.order, blockIdx.x);
   const int n = b.nst[t];
   const int N = b.n_max;
   double* A = b.G + mat_off(t, N);
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(kChThreads, 1) k_cholesky_blk(Batch b) {
 constexpr int kTiThreads = 256;
 
 __global__ void __launch_bounds__(kTiThreads) k_trinv_blk(Batch b, int gram_identity) {
-  const int t = blockIdx.y, cb = blockIdx.x;
+  const int t = prob_of(b.order, blockIdx.y), cb = blockIdx.x;
   const int n = b.nst[t];
   const int N = b.n_max;
   const int c0 = cb * 32;
@@ -301,7 +301,7 @@ constexpr int GK = 16;  // k tile
 // FP64 one on B300. Operands are split into hi/lo floats once per tile.
 template <int MODE>
 __global__ void k_reduce_gemm_df(Batch b) {
-  const int t = blockIdx.z;
+  const int t = prob_of(b.order, blockIdx.z);
   const int n = b.nst[t];
   const int N = b.n_max;
   if (b.status[t]) return;
@@ -379,7 +379,7 @@ __global__ void k_reduce_gemm_df(Batch b) {
 // mode 1: C32 = X32 Linv^T (upper tiles, mirrored) into the first half of the X buffer.
 template <int MODE>
 __global__ void k_reduce32(Batch b) {
-  const int t = blockIdx.z;
+  const int t = prob_of(b.order, blockIdx.z);
   const int n = b.nst[t];
   const int N = b.n_max;
   if (b.status[t]) return;
@@ -439,7 +439,7 @@ __global__ void k_reduce32(Batch b) {
 // G = I in the mixed eigensolver: C32 = the Hermitian part of V, in FP32,
 // into the first half of the X buffer.
 __global__ void k_herm32(Batch b) {
-  const int t = blockIdx.z;
+  const int t = prob_of(b.order, blockIdx.z);
   const int n = b.nst[t];
   const int N = b.n_max;
   if (b.status[t]) return;
@@ -455,7 +455,7 @@ __global__ void k_herm32(Batch b) {
 // C <- (C + C^H)/2 (or C <- Hermitian part of V when G = I): removes
 // rounding-level asymmetry before the Jacobi sweeps.
 __global__ void k_hermitize(Batch b, int from_vis) {
-  const int t = blockIdx.z;
+  const int t = prob_of(b.order, blockIdx.z);
   const int n = b.nst[t];
   const int N = b.n_max;
   if (b.status[t]) return;
@@ -483,7 +483,7 @@ __global__ void k_hermitize(Batch b, int from_vis) {
 constexpr int kSelE = 8;
 
 __global__ void k_select(Batch b, int n_level, const double* all_bounds, int filter) {
-  const int t = blockIdx.x, eg = blockIdx.y;
+  const int t = prob_of(b.order, blockIdx.x), eg = blockIdx.y;
   const int n = b.nst[t];
   const int N = b.n_max;
   const int K = b.neig[t];
@@ -672,6 +672,7 @@ void launch_jacobi(const Batch& b, double tol, int max_sweeps, cudaStream_t s) {
   a.ld = b.n_max;
   a.stride = (size_t)b.n_max * b.n_max;
   a.report_nonconv = 1;
+  a.order = b.order;
   launch_jacobi_args(a, b.T, false, tol, max_sweeps, s);
 }
 

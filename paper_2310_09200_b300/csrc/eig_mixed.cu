@@ -608,6 +608,7 @@ void launch_eig_mixed(const Batch& b, const MixedWs& w, double tol, int max_swee
   a.n = b.nst;
   a.ld = N;
   a.stride = 2 * NN;
+  a.order = b.order;
   launch_tridiag32_reduce(a, T, s);
   float2* Q32 = reinterpret_cast<float2*>(Xf + 2 * NN);  // problem stride 2 N^2 float2, as C32
   SelArgs sa;
@@ -626,6 +627,7 @@ void launch_eig_mixed(const Batch& b, const MixedWs& w, double tol, int max_swee
   sa.done = nullptr;
   sa.ld = N;
   sa.stride = 2 * NN;
+  sa.order = b.order;
   const int sm2 = 2 * N * (int)sizeof(float);
   cudaFuncSetAttribute(k_td_topeig, cudaFuncAttributeMaxDynamicSharedMemorySize, sm2);
   k_td_topeig<<<T, kSelThreads, sm2, s>>>(sa);
@@ -652,6 +654,7 @@ void launch_eig_mixed(const Batch& b, const MixedWs& w, double tol, int max_swee
   h.ld = KP;
   h.stride = NN;
   h.report_nonconv = 1;
+  h.order = b.order;
   // pass 0 diagonalises H in FP32: its eigenvectors need only the FP32 stage's accuracy
   // (the correction that follows is FP32); H and U in FP32 in the R^{-1} block, free by then
   JacobiArgs h32 = h;

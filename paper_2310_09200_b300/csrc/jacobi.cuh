@@ -35,6 +35,7 @@ struct JacobiArgs {
   int ld;
   size_t stride;
   int report_nonconv;  // set kStatusNotConverged when the sweep cap is hit
+  const int* order = nullptr;  // [T] problem of each block (Batch::order), or nullptr
 };
 
 namespace jac {
@@ -90,7 +91,7 @@ template <typename R, bool CSM = false>
 __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_t(JacobiArgs a, double tol, int max_sweeps) {
   using C2 = typename CplxOf<R>::T;
   using namespace jac;
-  const int t = blockIdx.x;
+  const int t = prob_of(a.order, blockIdx.x);
   const int n = a.n[t];
   if (a.status[t]) return;
   C2* Q = static_cast<C2*>(a.Q) + (size_t)t * a.stride;

@@ -28,6 +28,7 @@ struct TridiagArgs {
   const int* n;       // [T]
   int ld;
   size_t stride;      // float2 elements between consecutive problems of C
+  const int* order = nullptr;  // [T] problem of each block (Batch::order), or nullptr
 };
 
 // Per-problem scratch layout (in floats): Z at 0, d at ld^2, e at ld^2 + ld,
@@ -72,7 +73,7 @@ __device__ __forceinline__ float2 block_sum2(float2 v, V* red) {
 // Dynamic shared memory: 5 * ld float2 (v_prev, w_prev, v, w, p).
 __global__ void __launch_bounds__(kTdThreads, 1) k_tridiag32(TridiagArgs a) {
   using namespace td;
-  const int t = blockIdx.x;
+  const int t = prob_of(a.order, blockIdx.x);
   if (a.status[t]) return;
   const int n = a.n[t], N = a.ld, tid = threadIdx.x;
   float2* A = a.C + (size_t)t * a.stride;
@@ -236,7 +237,7 @@ constexpr int kTdLoMax = 512;
 
 __global__ void __launch_bounds__(kTdThreads, 1) k_tridiag32_lo(TridiagArgs a) {
   using namespace td;
-  const int t = blockIdx.x;
+  const int t = prob_of(a.order, blockIdx.x);
   if (a.status[t]) return;
   const int n = a.n[t], N = a.ld, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   float2* A = a.C + (size_t)t * a.stride;

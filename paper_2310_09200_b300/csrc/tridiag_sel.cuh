@@ -55,6 +55,7 @@ struct SelArgs {
                        //     early-exit bit kMxDoneBit or any error bit set)
   int ld;              // leading dimension N
   size_t stride;       // float2 elements between the problems' reflector blocks
+  const int* order = nullptr;  // [T] problem of each block (Batch::order), or nullptr
 };
 
 constexpr int kMxDoneBit = 8;  // refinement status bit: kept residuals met the early-exit bound
@@ -118,7 +119,7 @@ __device__ __forceinline__ float guard(float a, float tiny) {
 // ---- kp largest eigenvalues of T by multisection. One CTA per problem.
 // Dynamic shared memory: 2 * ld floats (d, e^2 of T / ||T||_F).
 __global__ void __launch_bounds__(kSelThreads, 1) k_td_topeig(SelArgs a) {
-  const int t = blockIdx.x;
+  const int t = prob_of(a.order, blockIdx.x);
   if (a.status[t]) return;
   const int n = a.n[t], N = a.ld, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int kp = min(n, a.neig[t] + a.pad);
@@ -206,7 +207,7 @@ __global__ void __launch_bounds__(kSelThreads, 1) k_td_topeig(SelArgs a) {
 constexpr int kInvitThreads = 128;
 
 __global__ void __launch_bounds__(kInvitThreads) k_td_invit(SelArgs a, float* lu0, size_t lu_stride, int lu_ld) {
-  const int t = blockIdx.x;
+  const int t = prob_of(a.order, blockIdx.x);
   if (a.status[t]) return;
   const int n = a.n[t], N = a.ld, kp = a.kp[t], tid = threadIdx.x;
   const float* dg = a.tds + (size_t)t * a.sstride + td_off_d(N);
@@ -303,7 +304,7 @@ __global__ void __launch_bounds__(kInvitThreads) k_td_invit(SelArgs a, float* lu
 template <int RB, int RPL, bool ADJ, bool FROM_Z, int CPW>
 __global__ void __launch_bounds__(kTdThreads, 1) k_td_apply(SelArgs a, float2* Q0, size_t qstride, int cols_per_cta) {
   using namespace td;
-  const int t = blockIdx.y;
+  const int t = prob_of(a.order, blockIdx.y);
   if (sel::skip(a, t)) return;
   const int n = a.n[t], N = a.ld, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int c0 = blockIdx.x * cols_per_cta;
@@ -417,7 +418,7 @@ __global__ void __launch_bounds__(kTdThreads, 1) k_td_apply(SelArgs a, float2* Q
 // n x kp block (ld, qstride float2 per problem). Grid (kp_max, T), 256 threads;
 // dynamic shared memory: kp_max float2.
 __global__ void __launch_bounds__(256) k_td_deflate(SelArgs a, float2* S0, size_t qstride) {
-  const int t = blockIdx.y, j = blockIdx.x;
+  const int t = prob_of(a.order, blockIdx.y), j = blockIdx.x;
   if (sel::skip(a, t)) return;
   const int n = a.n[t], N = a.ld, kp = a.kp[t];
   if (j >= kp) return;
@@ -460,7 +461,7 @@ __global__ void __launch_bounds__(256) k_td_deflate(SelArgs a, float2* S0, size_
 // threads; dynamic shared memory: 2 * ld floats.
 __global__ void __launch_bounds__(32) k_td_shiftsolve(SelArgs a, float2* S0, size_t qstride, const double* theta,
                                                     int theta_ld, float* lu0, size_t lu_stride, int lu_ld) {
-  const int t = blockIdx.y;
+  const int t = prob_of(a.order, blockIdx.y);
   if (sel::skip(a, t)) return;
   const int n = a.n[t], N = a.ld, kp = a.kp[t];
   const int j = blockIdx.x * 32 + threadIdx.x;
