@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_after();
       const TcStep st = steps[t];
       const int K = b.nkept[t];
-      const int2* lw = lwt + (size_t)t * kTcMaxEig;
+      const int2* lw = lwt + (size_t)t * kLwtStride;
       const uint32_t tbase = taddr + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(bb * ncols_buf);
       if constexpr (EPI == 1) {
         // Y = d R z: R of this pixel per level, z = accumulator / scale (the weights hold d / scale^2)
@@ -233,15 +233,30 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int i = 0; i < 16; ++i) v[i] += v2[i];
         }
+        // a block of 8 pairs in one level (the usual case: levels are eigenvalue
+        // intervals of pairs in rank order): one weighted sum, one level add
+        const int lb = b.eigen ? -2 : lw[kTcMaxEig + cb].x;
+        if (lb >= 0) {
+          const int4* w4 = reinterpret_cast<const int4*>(lw + cb * 8);  // (level, weight) x 2; weight 0 if not imaged
+          float sacc = 0.0f;
 #pragma unroll
-        for (int p = 0; p < 8; ++p) {
-          const int e = cb * 8 + p;
-          if (e < K) {
-            const int2 lv = lw[e];
-            // eigenimages: slot (cb / 4) * 8 + p of this warpgroup's eigenvectors e = cb * 8 + p
-            if (lv.x >= 0)
-              level_add<MAXL>(lacc, b.eigen ? (cb >> 2) * 8 + p : lv.x,
-                              __int_as_float(lv.y) * fmaf(v[2 * p], v[2 * p], v[2 * p + 1] * v[2 * p + 1]));
+          for (int h = 0; h < 4; ++h) {
+            const int4 q = w4[h];
+            sacc = fmaf(__int_as_float(q.y), fmaf(v[4 * h], v[4 * h], v[4 * h + 1] * v[4 * h + 1]), sacc);
+            sacc = fmaf(__int_as_float(q.w), fmaf(v[4 * h + 2], v[4 * h + 2], v[4 * h + 3] * v[4 * h + 3]), sacc);
+          }
+          level_add<MAXL>(lacc, lb, sacc);
+        } else if (lb == -2) {
+#pragma unroll
+          for (int p = 0; p < 8; ++p) {
+            const int e = cb * 8 + p;
+            if (e < K) {
+              const int2 lv = lw[e];
+              // eigenimages: slot (cb / 4) * 8 + p of this warpgroup's eigenvectors e = cb * 8 + p
+              if (lv.x >= 0)
+                level_add<MAXL>(lacc, b.eigen ? (cb >> 2) * 8 + p : lv.x,
+                                __int_as_float(lv.y) * fmaf(v[2 * p], v[2 * p], v[2 * p + 1] * v[2 * p + 1]));
+            }
           }
         }
       }
@@ -522,7 +537,15 @@ __global__ void k_tc_pack(Batch b, const TcStep* steps, unsigned char* Bpack, co
       int2 v = make_int2(-1, 0);
       if (e < K && b.level[(size_t)t * KM + e] >= 0)
         v = make_int2(b.level[(size_t)t * KM + e], __float_as_int((float)(b.wt[(size_t)t * KM + e] * inv2)));
-      lwt[(size_t)t * kTcMaxEig + e] = v;
+      lwt[(size_t)t * kLwtStride + e] = v;
+    }
+    for (int q = threadIdx.x; q < kTcMaxEig / 8; q += blockDim.x) {  // the blocks' common levels
+      int lv = -1;
+      for (int e = 8 * q; e < 8 * q + 8; ++e) {
+        const int l = (e < K) ? b.level[(size_t)t * KM + e] : -1;
+        if (l >= 0) lv = (lv == -1 || lv == l) ? l : -2;
+      }
+      lwt[(size_t)t * kLwtStride + kTcMaxEig + q] = make_int2(lv, 0);
     }
   }
   if (threadIdx.x < kStations) {
@@ -626,7 +649,7 @@ int tc_alloc(TcWorkspace* w, int T, int N, int K) {
   if (cudaMalloc(&w->scale, sizeof(float) * T) != cudaSuccess) return -1;
   w->qph_stride = n_chunks_for(N) * kStations;
   if (cudaMalloc(&w->qph, kQBytes * (size_t)T * w->qph_stride) != cudaSuccess) return -1;
-  if (cudaMalloc(&w->lwt, sizeof(int2) * (size_t)T * kTcMaxEig) != cudaSuccess) return -1;
+  if (cudaMalloc(&w->lwt, sizeof(int2) * (size_t)T * kLwtStride) != cudaSuccess) return -1;
   if (cudaMalloc(&w->status, 2 * sizeof(int)) != cudaSuccess) return -1;
   if (cudaMemset(w->status, 0, 2 * sizeof(int)) != cudaSuccess) return -1;
   w->cap_T = T;

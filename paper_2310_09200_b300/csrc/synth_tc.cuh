@@ -11,6 +11,10 @@
 namespace bipp {
 
 constexpr int kTcMaxEig = 128;  // eigenvectors per step on the tensor-core path (N = 2*K <= 256)
+// Per step in TcWorkspace::lwt: kTcMaxEig (level, weight) words, then one word per
+// block of 8 accumulator column pairs whose x is the level common to the block's
+// imaged pairs (-1: none imaged, -2: more than one level).
+constexpr int kLwtStride = kTcMaxEig + kTcMaxEig / 8;
 
 // Per-step geometry of the tensor-core GEMM: B operand chunks of 64 K-rows
 // (32 stations) packed at b_off, n_chunks of them, ncols = 2*K rounded up to
@@ -33,7 +37,7 @@ struct TcWorkspace {
   float* scale = nullptr;      // [cap_T] operand scale of the FP16 variant (W * scale)
   uint32_t* qph = nullptr;     // [cap_T][chunks * 16][20] station phase words, in pairs of stations (k_tc_pack)
   int qph_stride = 0;          // stations per step in qph (32 * chunks of n_max)
-  int2* lwt = nullptr;         // [cap_T][kTcMaxEig] (level, FP32 weight / scale^2) per accumulator column pair
+  int2* lwt = nullptr;         // [cap_T][kLwtStride] (level, FP32 weight / scale^2) per accumulator column pair, block levels
   int* status = nullptr;       // [2] device error word (0 = ok), fault-injection word (0 = off)
   int cap_T = 0;
 };
