@@ -186,14 +186,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int p64 = (int)(r & 63);
         unsigned char* yb = yo.Y + ((size_t)t * yo.nc64 + (size_t)chunk) * (size_t)(2 * st.ncols * 128);
         for (int cb = wg; cb < st.ncols / 16; cb += 4) {
-          float v[16];
-          tmem_ld16(tbase + cb * 16, v);  // every lane of the warp takes part (tcgen05.ld is warp-wide)
-          if constexpr (FUSE) {
-            float v2[16];
-            tmem_ld16(tbase + st.ncols + cb * 16, v2);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] += v2[i];
-          }
+          float v[16];  // every lane of the warp takes part (tcgen05.ld is warp-wide)
+          if constexpr (FUSE) tmem_ld16_sum2(tbase + cb * 16, tbase + st.ncols + cb * 16, v);  // + the A_hi B_lo half
+          else tmem_ld16(tbase + cb * 16, v);
 #pragma unroll
           for (int p = 0; p < 8; ++p) {
             const int e = cb * 8 + p;
@@ -226,13 +221,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       for (int cb = wg; cb < st.ncols / 16; cb += 4) {
         float v[16];
-        tmem_ld16(tbase + cb * 16, v);
-        if constexpr (FUSE) {  // the A_hi B_lo half of the accumulator
-          float v2[16];
-          tmem_ld16(tbase + st.ncols + cb * 16, v2);
-#pragma unroll
-          for (int i = 0; i < 16; ++i) v[i] += v2[i];
-        }
+        if constexpr (FUSE) tmem_ld16_sum2(tbase + cb * 16, tbase + st.ncols + cb * 16, v);  // + the A_hi B_lo half
+        else tmem_ld16(tbase + cb * 16, v);
         // a block of 8 pairs in one level (the usual case: levels are eigenvalue
         // intervals of pairs in rank order): one weighted sum, one level add
         const int lb = b.eigen ? -2 : lw[kTcMaxEig + cb].x;
