@@ -8,25 +8,27 @@
 // so that z_e(r) = sum_i exp(-j th_ri) a_ie, followed by the level reduction
 // I_l(r) += sum_{e in l} d_e |z_e(r)|^2 (Algorithm 1) and the sum over steps.
 //
-// Kernel structure (one persistent CTA per SM, 18 warps):
+// Kernel structure (one persistent CTA per SM, 22 warps; 18 for eigenimages):
 //   warps 0-15 (4 warpgroups) generate A for a 128-pixel tile on the fly:
-//              thread = pixel row, warpgroup g = stations 8g..8g+7 of the
+//              thread = pixel rows r and r + 64 by stations 4q..4q+3 of the
 //              stage; phase reduction by 32-bit integer products (below), SFU
 //              sincos, split into hi + lo (BF16 or FP16), written into shared
 //              memory in the UMMA K-major 128-byte swizzled layout (one
-//              128-byte row per pixel, 32 stations per stage). They also run the epilogue: tcgen05.ld of
-//              the FP32 accumulator (pixel row = TMEM lane, warpgroup g takes
-//              column blocks g, g+4, ...), |z|^2, weights and levels in
-//              registers, accumulated over all steps and added to the FP64
-//              image once per tile.
-//   warp 16    allocates TMEM (two accumulator buffers) and issues, per
+//              128-byte row per pixel, 32 stations per stage).
+//   warps 16-19 run the epilogue (EPW): tcgen05.ld of the FP32 accumulator
+//              (pixel row = TMEM lane, every column block), |z|^2, weights and
+//              levels in registers, accumulated over all steps and added to
+//              the FP64 image once per tile. Without them (eigenimages, and
+//              the adjoint's Y stage) the producers run it between units,
+//              warpgroup g taking column blocks g, g+4, ...
+//   next warp  allocates TMEM (two accumulator buffers) and issues, per
 //              16-wide K slice, the split products A_hi*B_hi + A_hi*B_lo +
 //              A_lo*B_hi into FP32 accumulators: with FUSE (2 K <= 128
 //              columns) as two tcgen05.mma, A_hi*[B_hi | B_lo] (N = 2 ncols:
 //              the hi and lo images of B lie side by side) and A_lo*B_hi into
 //              the first half, the halves summed in the epilogue; otherwise as
 //              three MMAs of N = ncols into one accumulator.
-//   warp 17    streams the pre-packed, pre-swizzled B chunks of the step with
+//   last warp  streams the pre-packed, pre-swizzled B chunks of the step with
 //              cp.async.bulk into the stage ring.
 // Stage handoff uses mbarriers; every wait is bounded (clock64 budget) and on
 // expiry sets a device error word, drains its own in-flight work, frees TMEM
@@ -64,8 +66,10 @@ namespace bipp {
 namespace {
 
 constexpr int kProdWarps = 16;  // 4 warpgroups
-constexpr int kThreads = (kProdWarps + 2) * 32;
-constexpr int kMmaWarp = kProdWarps, kLoadWarp = kProdWarps + 1;
+constexpr int kEpiWarps = 4;    // dedicated epilogue warps (EPW): one per quarter of the TMEM lanes
+// Threads of a CTA: producers, [epilogue warps,] the MMA issuer and the B loader.
+__host__ __device__ constexpr int synth_threads(bool epw) { return (kProdWarps + (epw ? kEpiWarps : 0) + 2) * 32; }
+constexpr int kThreads = synth_threads(false);
 constexpr int kRows = 128;            // pixels per tile = UMMA M
 constexpr int kStations = 32;         // stations per stage (64 K-elements)
 constexpr int kABytes = kRows * 128;  // one A operand image per stage (hi or lo)
@@ -89,8 +93,8 @@ __device__ __forceinline__ void level_add(float (&acc)[MAXL], int lev, float v) 
 // pixel, step and accumulator column into yo.Y as BF16 hi/lo images in the
 // K-major, 128-byte-swizzled layout of a UMMA B operand whose K runs over 64
 // pixels (see TcYOut); img is not touched.
-template <int MAXL, bool FP16, bool FUSE, int EPI>
-__global__ void __launch_bounds__(kThreads, 1)
+template <int MAXL, bool FP16, bool FUSE, int EPI, bool EPW>
+__global__ void __launch_bounds__(synth_threads(EPW), 1)
     k_synth_tc(Batch b, Pixels px, int n_level, double* img, TcYOut yo, const TcStep* __restrict__ steps,
                const unsigned char* __restrict__ Bpack, const float* __restrict__ scales,
                const uint32_t* __restrict__ qph, int qph_stride, const int2* __restrict__ lwt, int n_stages,
@@ -104,6 +108,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ volatile int s_abort;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int kMmaWarp = kProdWarps + (EPW ? kEpiWarps : 0), kLoadWarp = kMmaWarp + 1;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kMaxStages; ++s) {
       mbar_init(smem_u32(&bar_fullA[s]), kProdWarps);
@@ -112,7 +117,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(smem_u32(&bar_accf[i]), 1);
-      mbar_init(smem_u32(&bar_acce[i]), kProdWarps);
+      mbar_init(smem_u32(&bar_acce[i]), EPW ? kEpiWarps : kProdWarps);
     }
     mbar_init(smem_u32(&bar_drain), 1);
     mbar_init(smem_u32(&bar_q), kProdWarps);
@@ -133,8 +138,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int n_tiles = (int)((px.n + kRows - 1) / kRows);
   const int T = b.T;
 
-  if (warp < kProdWarps) {
-    // ------------------------------------------------ A producer + epilogue
+  if (warp < kMmaWarp) {
+    // ------------------------------------------------ A producer + epilogue (EPW: warps past the
+    // producers run the epilogue alone, pixel row = their TMEM lane, every column block)
+    const bool epi_warp = EPW && warp >= kProdWarps;
     const int row = threadIdx.x & (kRows - 1);
     const int wg = threadIdx.x >> 7;  // warpgroup: column blocks wg + 4j of the epilogue
     // A producer: pixel rows rp and rp + 64 of the tile, stations 4 quad .. 4 quad + 3 of
@@ -163,9 +170,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         cp_async16(qsm0 + buf * kQWinBytes + o, src + o);
       cp_async_commit();
     };
-    if (blockIdx.x < n_tiles) q_prefetch(0, 0, 0);
+    if (!epi_warp && blockIdx.x < n_tiles) q_prefetch(0, 0, 0);
 
-    auto epilogue = [&](int tile, int t, int u) -> bool {
+    // cb0, cbs: the column blocks cb0, cb0 + cbs, ... of this thread
+    auto epilogue = [&](int tile, int t, int u, int cb0, int cbs) -> bool {
       const int bb = u & 1;
       if (!mbar_wait(smem_u32(&bar_accf[bb]), (uint32_t)((u >> 1) & 1), &s_abort)) return false;
       tc_fence_after();
@@ -185,7 +193,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const bool store = chunk < yo.nc64;
         const int p64 = (int)(r & 63);
         unsigned char* yb = yo.Y + ((size_t)t * yo.nc64 + (size_t)chunk) * (size_t)(2 * st.ncols * 128);
-        for (int cb = wg; cb < st.ncols / 16; cb += 4) {
+        for (int cb = cb0; cb < st.ncols / 16; cb += cbs) {
           float v[16];  // every lane of the warp takes part (tcgen05.ld is warp-wide)
           if constexpr (FUSE) tmem_ld16_sum2(tbase + cb * 16, tbase + st.ncols + cb * 16, v);  // + the A_hi B_lo half
           else tmem_ld16(tbase + cb * 16, v);
@@ -219,7 +227,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) mbar_arrive(smem_u32(&bar_acce[bb]));
         return true;
       }
-      for (int cb = wg; cb < st.ncols / 16; cb += 4) {
+      for (int cb = cb0; cb < st.ncols / 16; cb += cbs) {
         float v[16];
         if constexpr (FUSE) tmem_ld16_sum2(tbase + cb * 16, tbase + st.ncols + cb * 16, v);  // + the A_hi B_lo half
         else tmem_ld16(tbase + cb * 16, v);
@@ -275,8 +283,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       return true;
     };
 
+    if (epi_warp) {  // EPW: the units in the producers' order, each as soon as its accumulator is ready
+      int u = 0;
+      for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x)
+        for (int t = 0; t < T && ok; ++t, ++u) ok = epilogue(tile, t, u, 0, 1);
+    } else
     for (int tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-      const int64_t r = (int64_t)tile * kRows + row;
       PhasePix pp[2];
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
@@ -351,7 +363,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (lane == 0) mbar_arrive(smem_u32(&bar_fullA[s]));
         }
         if (!ok) break;
-        if (pend_tile >= 0 && !epilogue(pend_tile, pend_t, unit - 1)) {
+        if (!EPW && pend_tile >= 0 && !epilogue(pend_tile, pend_t, unit - 1, wg, 4)) {
           ok = false;
           break;
         }
@@ -360,7 +372,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         ++unit;
       }
     }
-    if (ok && pend_tile >= 0) ok = epilogue(pend_tile, pend_t, unit - 1);
+    if (!EPW && ok && pend_tile >= 0) ok = epilogue(pend_tile, pend_t, unit - 1, wg, 4);
     cp_async_wait();  // no copy may still be in flight into shared memory at exit
     if (!ok) s_abort = 1;
   } else if (warp == kMmaWarp) {
@@ -724,15 +736,19 @@ int launch_kernel(const Batch& b, const Pixels& px, int n_level, double* img, co
     constexpr int ML = decltype(L)::value;
     constexpr bool F16 = decltype(FPV)::value;
     constexpr bool FS = decltype(FU)::value;
-    if (cudaFuncSetAttribute(k_synth_tc<ML, F16, FS, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess) {
-      rc = -7;
-      return;
-    }
-    k_synth_tc<ML, F16, FS, 0><<<grid, kThreads, smem, s>>>(b, px, n_level, img, TcYOut{}, w->steps, w->B, w->scale, w->qph,
-                                                      w->qph_stride, w->lwt, n_stages,
-                                                     stage_bytes, p.ncols_buf, w->status);
-    if (cudaGetLastError() != cudaSuccess) rc = -11;  // the launch itself failed
+    // dedicated epilogue warps for energy levels; eigenimages keep the epilogue in the
+    // producers (their up to 64 images fit 16 register slots per thread only split four ways)
+    auto go = [&](auto kern, int threads) {
+      if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        rc = -7;
+        return;
+      }
+      kern<<<grid, threads, smem, s>>>(b, px, n_level, img, TcYOut{}, w->steps, w->B, w->scale, w->qph,
+                                       w->qph_stride, w->lwt, n_stages, stage_bytes, p.ncols_buf, w->status);
+      if (cudaGetLastError() != cudaSuccess) rc = -11;  // the launch itself failed
+    };
+    if (b.eigen) go(k_synth_tc<ML, F16, FS, 0, false>, synth_threads(false));
+    else go(k_synth_tc<ML, F16, FS, 0, true>, synth_threads(true));
   });
   return rc;
 }
@@ -808,12 +824,12 @@ int tc_enqueue_yout(const Batch& b, const Pixels& px, int n_level, const TcPlan&
     if constexpr (ML != 4 || !FS) {  // the adjoint's Y stage is built for <= 4 levels and 2 n_eig <= 128 columns
       rc = -10;
     } else {
-      if (cudaFuncSetAttribute(k_synth_tc<ML, F16, FS, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      if (cudaFuncSetAttribute(k_synth_tc<ML, F16, FS, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
           cudaSuccess) {
         rc = -7;
         return;
       }
-      k_synth_tc<ML, F16, FS, 1><<<grid, kThreads, smem, s>>>(b, px, n_level, nullptr, yo, w->steps, w->B, w->scale,
+      k_synth_tc<ML, F16, FS, 1, false><<<grid, kThreads, smem, s>>>(b, px, n_level, nullptr, yo, w->steps, w->B, w->scale,
                                                               w->qph, w->qph_stride, w->lwt, p.n_stages,
                                                               stage_bytes, p.ncols_buf, w->status);
       if (cudaGetLastError() != cudaSuccess) rc = -11;  // the launch itself failed
