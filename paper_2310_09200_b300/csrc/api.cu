@@ -596,6 +596,9 @@ static int run_batch(bipp_ss* h, int n_t, int N, const std::vector<int>& nst_v, 
   }
   std::stable_sort(h->h_order, h->h_order + n_t, [&](int x, int y) { return nst_v[x] > nst_v[y]; });
   Batch b = make_batch(h, n_t, N, K, d_st, d_vis);
+  bool ident = true;  // steps already largest first (e.g. all of one size): no indirection in the kernels
+  for (int t = 0; t < n_t; ++t) ident = ident && h->h_order[t] == t;
+  if (ident) b.order = nullptr;
   // mixed-precision eigensolve when asked for and its scratch fits the batch buffers
   h->mixed_kp = 0;
   if (h->opt.eig_mode == BIPP_EIG_MIXED) {
