@@ -691,8 +691,10 @@ int max_stages_for(int ncols_max) {
   return std::min(kMaxStages, (kDynSmemMax - kQStageBytes) / stage_bytes_for(ncols_max));
 }
 
-// Autotuned launch shapes: the stage-ring depth and the MMA shape (fused
-// N = 2 ncols, or three MMAs of N = ncols), keyed by (accumulator width,
+// Autotuned launch shapes: the stage-ring depth, the MMA shape (fused
+// N = 2 ncols, or three MMAs of N = ncols) and, for level images, where the
+// epilogue runs (four dedicated warps, or the producers between units; 22 or
+// 18 warps per CTA), keyed by (accumulator width,
 // station-chunk count rounded up to a power of two, operand type): the tuned
 // shape holds for every batch with the same key in this process.
 struct TuneKey {
@@ -703,7 +705,7 @@ struct TuneKey {
 };
 struct TuneVal {
   int n_stages;
-  bool fused;
+  bool fused, epw;
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneVal> g_tuned;
@@ -747,7 +749,7 @@ int launch_kernel(const Batch& b, const Pixels& px, int n_level, double* img, co
                                        w->qph_stride, w->lwt, n_stages, stage_bytes, p.ncols_buf, w->status);
       if (cudaGetLastError() != cudaSuccess) rc = -11;  // the launch itself failed
     };
-    if (b.eigen) go(k_synth_tc<ML, F16, FS, 0, false>, synth_threads(false));
+    if (b.eigen || !p.epw) go(k_synth_tc<ML, F16, FS, 0, false>, synth_threads(false));
     else go(k_synth_tc<ML, F16, FS, 0, true>, synth_threads(true));
   });
   return rc;
@@ -783,6 +785,7 @@ int tc_prepare(const std::vector<int>& nst, const std::vector<int>& neig, bool f
   p->tuned = it != g_tuned.end();
   p->n_stages = p->tuned ? it->second.n_stages : smax;
   set_shape(p, p->tuned ? it->second.fused : true);  // untuned: fused where N = 2 ncols <= 256
+  p->epw = p->tuned ? it->second.epw : true;
   return 0;
 }
 
@@ -860,9 +863,11 @@ int tc_autotune(const Batch& b, const Pixels& px, int n_level, int n_chan_sub, T
   float best_ms = 1e30f;
   int rc = 0;
   const int n_shapes = (2 * p->ncols_max <= 256) ? 2 : 1;
-  for (int f = 0; f < n_shapes && rc == 0; ++f) {
+  const int n_epw = b.eigen ? 1 : 2;  // eigenimages always run the epilogue in the producers
+  for (int f = 0; f < n_shapes * n_epw && rc == 0; ++f) {
     TcPlan q = *p;
-    set_shape(&q, f == 0 && n_shapes == 2);
+    set_shape(&q, f % n_shapes == 0 && n_shapes == 2);
+    q.epw = f / n_shapes == 0;
     for (int ns = 2; ns <= max_stages_for(q.ncols_max) && rc == 0; ++ns) {
       rc = launch_kernel(bs, ps, n_level, scratch, q, ns, w, s);  // warm-up
       cudaEventRecord(e0, s);
@@ -886,7 +891,7 @@ int tc_autotune(const Batch& b, const Pixels& px, int n_level, int n_chan_sub, T
   *p = best;
   p->tuned = true;
   std::lock_guard<std::mutex> lock(g_tune_mu);
-  g_tuned[tune_key(*p)] = TuneVal{p->n_stages, p->fused};
+  g_tuned[tune_key(*p)] = TuneVal{p->n_stages, p->fused, p->epw};
   return 0;
 }
 

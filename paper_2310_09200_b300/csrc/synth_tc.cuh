@@ -61,7 +61,8 @@ struct TcPlan {
   int ncols_buf = 32;   // TMEM columns per accumulator buffer (power of two)
   bool fused = false;   // A_hi [B_hi | B_lo] as one MMA of N = 2 ncols (ncols_max <= 128); autotuned
   int n_stages = 2;     // shared-memory ring depth
-  bool tuned = false;   // n_stages and fused come from the autotuner
+  bool epw = true;      // level images: dedicated epilogue warps (else the producers run the epilogue); autotuned
+  bool tuned = false;   // n_stages, fused and epw come from the autotuner
 };
 
 int tc_alloc(TcWorkspace* w, int T, int N, int K);
@@ -96,7 +97,8 @@ int adj_tc_smem_bytes(int ncols);
 // 2 ncols_max <= 256 (else p stays unfused).
 void tc_plan_force_fused(TcPlan* p);
 // Not capturable (synchronises): time each feasible launch shape (MMA shape:
-// fused N = 2 ncols or three N = ncols MMAs; stage-ring depth) on a subset of
+// fused N = 2 ncols or three N = ncols MMAs; stage-ring depth; epilogue in
+// dedicated warps or in the producers, for level images) on a subset of
 // the packed batch into a scratch image, keep the fastest in p and in a
 // process-wide cache keyed by (ncols_max, chunk count rounded up to a power of
 // two, operand type).
