@@ -300,9 +300,9 @@ __global__ void __launch_bounds__(kInvitThreads) k_td_invit(SelArgs a, float* lu
 // l, l + 32, ... of each), so that the CPW dot products of a reflector and
 // their shuffle reductions overlap. FROM_Z: the block starts as the real
 // columns of Z (k_td_apply then is the back-transformation q_j = H z_j).
-// Grid (column groups of NT / 32 * CPW, T); dynamic shared memory: ld x (RB + 1) float2.
-template <int RB, int RPL, bool ADJ, bool FROM_Z, int CPW, int NT>
-__global__ void __launch_bounds__(NT, 1) k_td_apply(SelArgs a, float2* Q0, size_t qstride, int cols_per_cta) {
+// Grid (column groups of 16 CPW, T); dynamic shared memory: ld x (RB + 1) float2.
+template <int RB, int RPL, bool ADJ, bool FROM_Z, int CPW>
+__global__ void __launch_bounds__(kTdThreads, 1) k_td_apply(SelArgs a, float2* Q0, size_t qstride, int cols_per_cta) {
   using namespace td;
   const int t = prob_of(a.order, blockIdx.y);
   if (sel::skip(a, t)) return;
@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(NT, 1) k_td_apply(SelArgs a, float2* Q0, size_
   __shared__ float2 stau[RB];
   if (FROM_Z) {
     const float* Z = a.Z + (size_t)t * a.sstride;
-    for (int e0 = tid; e0 < n * (c1 - c0); e0 += NT) {
+    for (int e0 = tid; e0 < n * (c1 - c0); e0 += kTdThreads) {
       const int r = e0 % n, c = c0 + e0 / n;
       Q[(size_t)r + (size_t)c * N] = make_float2(Z[(size_t)r + (size_t)c * N], 0.f);
     }
@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(NT, 1) k_td_apply(SelArgs a, float2* Q0, size_
     const int k0 = ADJ ? bi * RB : (nblk - 1 - bi) * RB;
     const int nb = min(RB, nref - k0), mb = n - k0 - 1;  // reflectors k0..k0+nb-1 act on rows k0+1..n-1
     __syncthreads();
-    for (int e0 = tid; e0 < mb * nb; e0 += NT) {
+    for (int e0 = tid; e0 < mb * nb; e0 += kTdThreads) {
       const int r = e0 % mb, j = e0 / mb;
       float2 v = make_float2(0.f, 0.f);
       if (r == j) v = make_float2(1.f, 0.f);
@@ -528,19 +528,17 @@ template <bool ADJ, bool FROM_Z>
 inline void launch_td_apply(const SelArgs& a, float2* Q, size_t qstride, int KP, int T, cudaStream_t s) {
   const int N = a.ld;
   if (N <= 512) {
-    // 20 warps of two columns: kp = 80 takes two CTAs per step (two waves of 1 CTA per SM
-    // for 100 steps on 148 SMs, where three 32-column CTAs took three)
-    constexpr int kCpw = 2, kNt = 640, kCols = kNt / 32 * kCpw;
+    constexpr int kCpw = 2, kCols = kTdThreads / 32 * kCpw;
     const dim3 grd((KP + kCols - 1) / kCols, T);
     const int smb = N * (32 + 1) * (int)sizeof(float2);
-    cudaFuncSetAttribute(k_td_apply<32, 16, ADJ, FROM_Z, kCpw, kNt>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
-    k_td_apply<32, 16, ADJ, FROM_Z, kCpw, kNt><<<grd, kNt, smb, s>>>(a, Q, qstride, kCols);
+    cudaFuncSetAttribute(k_td_apply<32, 16, ADJ, FROM_Z, kCpw>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
+    k_td_apply<32, 16, ADJ, FROM_Z, kCpw><<<grd, kTdThreads, smb, s>>>(a, Q, qstride, kCols);
   } else {
     constexpr int kCols = kTdThreads / 32;
     const dim3 grd((KP + kCols - 1) / kCols, T);
     const int smb = N * (16 + 1) * (int)sizeof(float2);
-    cudaFuncSetAttribute(k_td_apply<16, 32, ADJ, FROM_Z, 1, kTdThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
-    k_td_apply<16, 32, ADJ, FROM_Z, 1, kTdThreads><<<grd, kTdThreads, smb, s>>>(a, Q, qstride, kCols);
+    cudaFuncSetAttribute(k_td_apply<16, 32, ADJ, FROM_Z, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
+    k_td_apply<16, 32, ADJ, FROM_Z, 1><<<grd, kTdThreads, smb, s>>>(a, Q, qstride, kCols);
   }
 }
 
