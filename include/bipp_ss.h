@@ -265,7 +265,9 @@ int bipp_ss_debug_fail_wait(bipp_ss_t h, int32_t on);
  *   precision BIPP_PREC_FP32: exact phase reduction, SFU sincos, FP32 sums on
  *             the CUDA cores; BIPP_PREC_SPLIT_FP16 / _BF16: the tensor-core
  *             synthesis kernel of collect() on W' = diag(conj g) W (n_eig <=
- *             128), to the same accuracy as collect() in that precision.
+ *             128), to the same accuracy as collect() in that precision, with
+ *             the same station range (|p|/wl below 2^28, else
+ *             BIPP_ERR_UNSUPPORTED; the adjoint alike).
  * bipp_ss_synth_levels_device writes d_img (n_pix x n_level FP64, overwritten).
  * 1 <= n_eig <= n_st <= 1024, 1 <= n_level <= 16; another precision returns
  * BIPP_ERR_INVALID_ARG. */
