@@ -137,6 +137,15 @@ def eig_roofline(n: int, kp: int, n_t: int, eig_ms: float, fp32_rate: float, pas
                           "frac = (FP32 flops / rate + double-float instructions / instruction rate) / stage time")}
 
 
+def synth_shape_of(get):
+    """The tensor-core synthesis launch shape of the last collect (the autotuner's
+    pick: ring stages, fused MMA, epilogue warps), or None if it cannot be read."""
+    try:
+        return get()
+    except Exception:
+        return None
+
+
 def measured_peaks() -> dict:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -484,6 +493,7 @@ def batch_main(args, ws, rank, local):
             dt = max_over_ranks(dt, device=dev)
         e2e = {"value": prods * ws / dt, "unit": UNIT, "h2d_bytes_per_step": int(st_p.nbytes + V_p.nbytes),
                "d2h_bytes_per_step": int(img_t.numpy().nbytes)}
+    synth_shape = synth_shape_of(lambda: bipp_ss.bipp_ss_get_synth_shape(h))
     bipp_ss.bipp_ss_destroy(h)
     if rank == 0:
         peaks = measured_peaks()
@@ -506,7 +516,8 @@ def batch_main(args, ws, rank, local):
                            "eigensolve": EIG_DESC.get(args.eig), "l2": "inputs larger than L2"},
                 "stage_ms_per_step": {"gram_chol_reduce": stage[0] / K, "jacobi": stage[1] / K,
                                       "select_pack": stage[2] / K, "synthesis": syn_ms},
-                "roofline": roof, "cpu_baseline": None, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+                "roofline": roof, "cpu_baseline": None, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+                **({"synth_shape": synth_shape} if synth_shape and synth_shape["stages"] else {})}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -849,6 +860,7 @@ def ours_main(args, ws, rank, local):
             dt = max_over_ranks(dt, device=f"cuda:{local}")
         e2e = {"value": prods * ws / dt, "unit": UNIT, "h2d_bytes_per_step": int(st.nbytes + V.nbytes),
                "d2h_bytes_per_step": int(img_h.nbytes)}
+    synth_shape = synth_shape_of(ss.synth_shape)
     ss.close()
 
     cpu = None
@@ -884,6 +896,7 @@ def ours_main(args, ws, rank, local):
                 "synthesis_only_value": prods / (syn_ms / 1e3),
                 "roofline": dominant, "roofline_synthesis": roof_synth, "roofline_jacobi": roof_jacobi,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+                **({"synth_shape": synth_shape} if synth_shape and synth_shape["stages"] else {}),
                 **({"precision_forms": forms} if forms else {})}
         print(json.dumps(line), flush=True)
     if dist:

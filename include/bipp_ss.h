@@ -240,6 +240,15 @@ int bipp_ss_get_timings(bipp_ss_t h, double* out6);
  * width w, out[10] the number of baselines spread. Zeros for STANDARD. */
 int bipp_ss_get_nufft_timings(bipp_ss_t h, double* out11);
 
+/* Launch shape of the tensor-core synthesis of the last collect (split
+ * precisions; the paper has no counterpart: it reports the autotuner's pick):
+ * out[0] shared-memory ring stages, out[1] 1 if A_hi [B_hi | B_lo] ran as one
+ * fused MMA (else three), out[2] 1 if dedicated warps ran the epilogue (else
+ * the producer warps), out[3] 1 if the shape came from the autotuner (0: the
+ * default shape, as on the collect that runs the tuning). All zeros for the
+ * FP32 / FP64 precisions and for NUFFT synthesis. */
+int bipp_ss_get_synth_shape(bipp_ss_t h, int32_t* out4);
+
 /* Fault injection for tests of failure detection (no GPU fault): while on
  * (1), the tensor-core synthesis kernel (BIPP_PREC_SPLIT_*) makes its MMA
  * issuer wait on a shared-memory barrier phase that nothing completes. Its

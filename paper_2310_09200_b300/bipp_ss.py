@@ -53,7 +53,7 @@ EXPORTED = [
     "bipp_ss_synth_adjoint_device", "bipp_ss_create_channels", "bipp_ss_collect_channels",
     "bipp_ss_energy_neig", "bipp_ss_kmeans_bounds", "bipp_ss_get_nufft_timings", "bipp_ss_collect_device_c64",
     "bipp_ss_debug_fail_wait", "bipp_ss_quantile_bounds", "bipp_ss_measure_sincos_rate",
-    "bipp_ss_measure_fma_rates",
+    "bipp_ss_measure_fma_rates", "bipp_ss_get_synth_shape",
 ]
 
 BIPP_NOALLOC_MAX_STATIONS = 128
@@ -105,6 +105,7 @@ def load(path: str | None = None):
     L.bipp_ss_set_images.argtypes = [H, dp]
     L.bipp_ss_last_eigvals.argtypes = [H, i32, i32, ip, ip, dp, ip]
     L.bipp_ss_get_timings.argtypes = [H, dp]
+    L.bipp_ss_get_synth_shape.argtypes = [H, ip]
     L.bipp_ss_get_nufft_timings.argtypes = [H, dp]
     L.bipp_ss_debug_fail_wait.argtypes = [H, i32]
     L.bipp_ss_destroy.argtypes = [H]
@@ -351,6 +352,12 @@ def bipp_ss_get_timings(h) -> dict:
             "launches": int(a[5])}
 
 
+def bipp_ss_get_synth_shape(h) -> dict:
+    a = np.zeros(4, dtype=np.int32)
+    _check(h, load().bipp_ss_get_synth_shape(h, a.ctypes.data_as(C.POINTER(C.c_int32))))
+    return {"stages": int(a[0]), "fused_mma": bool(a[1]), "epilogue_warps": bool(a[2]), "autotuned": bool(a[3])}
+
+
 def bipp_ss_get_nufft_timings(h) -> dict:
     a = np.zeros(11, dtype=np.float64)
     _check(h, load().bipp_ss_get_nufft_timings(h, _dp(a)))
@@ -518,6 +525,9 @@ class StandardSynthesis:
 
     def nufft_timings(self):
         return bipp_ss_get_nufft_timings(self.h)
+
+    def synth_shape(self):
+        return bipp_ss_get_synth_shape(self.h)
 
     def close(self):
         if self.h:

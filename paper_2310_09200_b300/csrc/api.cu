@@ -116,6 +116,7 @@ struct bipp_ss {
   // last batch
   int last_T = 0, last_N = 0, last_K = 0;
   double timings[6] = {0, 0, 0, 0, 0, 0};
+  int synth_shape[4] = {0, 0, 0, 0};  // bipp_ss_get_synth_shape
   cudaEvent_t ev[5] = {};
   std::string err;
 };
@@ -618,9 +619,14 @@ static int run_batch(bipp_ss* h, int n_t, int N, const std::vector<int>& nst_v, 
     if (rc == -3) return fail(h, BIPP_ERR_UNSUPPORTED, "split precisions support n_eig <= %d per step", kTcMaxEig);
     if (rc) return fail(h, BIPP_ERR_CUDA, "tensor-core plan failed (%d)", rc);
   }
+  // the shape this collect's synthesis runs with (the tuning collect runs the default one)
+  h->synth_shape[0] = tc ? plan.n_stages : 0;
+  h->synth_shape[1] = tc && plan.fused ? 1 : 0;
+  h->synth_shape[2] = tc && plan.epw && !h->opt.eigenimages ? 1 : 0;
+  h->synth_shape[3] = tc && plan.tuned ? 1 : 0;
   GraphKey key;
   key.T = n_t; key.N = N; key.K = K; key.st = d_st; key.vis = d_vis; key.stream = s;
-  key.nst = nst_v; key.neig = neig_v; key.chan = chan_v; key.n_stages = tc ? plan.n_stages + (plan.fused ? 16 : 0) : 0;
+  key.nst = nst_v; key.neig = neig_v; key.chan = chan_v; key.n_stages = tc ? plan.n_stages + (plan.fused ? 16 : 0) + (plan.epw ? 32 : 0) : 0;
 
   if (nufft) {
     // host-planned grids and cuFFT: enqueued directly, not captured
@@ -916,6 +922,13 @@ extern "C" int bipp_ss_get_nufft_timings(bipp_ss_t h, double* out11) {
   if (!h) return fail(nullptr, BIPP_ERR_INVALID_ARG, "handle is NULL");
   if (!out11) return fail(h, BIPP_ERR_INVALID_ARG, "out11 is NULL");
   for (int i = 0; i < 11; ++i) out11[i] = h->nu_timings[i];
+  return BIPP_OK;
+}
+
+extern "C" int bipp_ss_get_synth_shape(bipp_ss_t h, int32_t* out4) {
+  if (!h) return fail(nullptr, BIPP_ERR_INVALID_ARG, "handle is NULL");
+  if (!out4) return fail(h, BIPP_ERR_INVALID_ARG, "out4 is NULL");
+  for (int i = 0; i < 4; ++i) out4[i] = h->synth_shape[i];
   return BIPP_OK;
 }
 

@@ -131,6 +131,7 @@ def test_create_rejects_invalid_arguments_before_device_use(lib, case):
 
 def test_null_handle_calls_fail_cleanly(lib):
     assert lib.bipp_ss_collect(None, 3, None, None) == bipp_ss.BIPP_ERR_INVALID_ARG
+    assert lib.bipp_ss_get_synth_shape(None, None) == bipp_ss.BIPP_ERR_INVALID_ARG
     assert lib.bipp_ss_get(None, None) == bipp_ss.BIPP_ERR_INVALID_ARG
     assert lib.bipp_ss_destroy(None) == bipp_ss.BIPP_OK
     assert isinstance(bipp_ss.bipp_ss_last_error(None), str)

@@ -55,3 +55,11 @@ def test_eig_roofline_of_the_default_job():
     assert r["t_roof_ms"]["fp32_stage"] == pytest.approx(t32 * 1e3)
     assert r["t_roof_ms"]["df_refinement"] == pytest.approx(tdf * 1e3)
     assert r["frac"] == pytest.approx((t32 + tdf) / 50e-3)
+
+
+def test_synth_shape_reader_never_raises():
+    """The bench line's synthesis shape is optional: a failing read gives None."""
+    def boom():
+        raise RuntimeError("no handle")
+    assert bench.synth_shape_of(boom) is None
+    assert bench.synth_shape_of(lambda: {"stages": 3}) == {"stages": 3}
