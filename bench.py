@@ -122,7 +122,8 @@ def eig_roofline(n: int, kp: int, n_t: int, eig_ms: float, fp32_rate: float, pas
     Householder reduction (16/3 n^3 flops per step) and the three applications
     of the reflectors to kp columns (4 n^2 kp flops each) at the measured FP32
     FMA rate, plus `passes` refinement passes of double-float products at half
-    that rate in instructions (12 FP32 instructions per real multiply-add): per
+    that rate in operations (12 FP32 operations per real multiply-add, issued as
+    6 packed FP32x2 instructions): per
     pass C X1 = L^{-1} (V (L^{-T} X1)) (6 n^2 kp real multiply-adds) and the
     five n x kp x kp products (20 n kp^2). frac = bound / measured stage time
     (the Sturm counts, solves and small Jacobi are latency chains, not in it)."""
